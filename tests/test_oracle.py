@@ -1,0 +1,344 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a printed
+example, an independent construction (scipy's Sylvester Hadamard matrix, Python
+big integers, brute force), a theorem of the paper, or a published test vector.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.linalg
+import sympy
+
+import oracle
+from tests.conftest import bits_to_int, bits_to_words, read_golden
+
+P = oracle.P_DEFAULT
+
+
+def _pow2_b(d):
+    """b_i = 2^i: the Eq. (1) key then equals the bit mask of g_v AND x."""
+    return [1 << i for i in range(d)]
+
+
+# ----------------------------------------------------------------- worked examples
+
+def test_example1_covering_vectors():
+    """Example 1 (Sec. 2.3): the seven vectors g_v and the single collision at g_4."""
+    g = read_golden("example1_covering.txt")
+    d, r = int(g["d"][0]), int(g["r"][0])
+    m = [int(s, 2) for s in g["m"]]
+    p = oracle.make_params(d, r, m, _pow2_b(d))
+    assert p.W == 8 and p.T == 7
+    ones = bits_to_words("1" * d)
+    x, q = bits_to_words(g["x"][0]), bits_to_words(g["q"][0])
+    for v in range(1, 8):
+        assert oracle.key_direct(p, ones, v - 1) == bits_to_int(g["g%d" % v][0])
+    kx, kq = oracle.keys_direct(p, x)[:, 0], oracle.keys_direct(p, q)[:, 0]
+    coll = [v for v in range(1, 8) if kx[v - 1] == kq[v - 1]]
+    assert coll == [int(g["collide"][0])]
+    assert int(kx[coll[0] - 1]) == bits_to_int(g["value"][0])
+    assert oracle.hamming(x, q) == 2
+
+
+def test_example2_code_matrix_and_collisions():
+    """C_{7,8} and Example 2 (Sec. 3.1): x collides with q only under row 3, y never."""
+    g = read_golden("example2_c78.txt")
+    d, r = int(g["d"][0]), int(g["r"][0])
+    p = oracle.make_params(d, r, list(range(d)), _pow2_b(d))
+    ones = bits_to_words("1" * d)
+    for v in range(1, 8):
+        assert oracle.key_direct(p, ones, v - 1) == bits_to_int(g["C%d" % v][0])
+    x, y, q = (bits_to_words(g[k][0]) for k in ("x", "y", "q"))
+    assert oracle.hamming(x, q) == int(g["dist_xq"][0])
+    assert oracle.hamming(y, q) == int(g["dist_yq"][0])
+    kx, ky, kq = (oracle.keys_direct(p, a)[:, 0] for a in (x, y, q))
+    coll_xq = [v for v in range(1, 8) if kx[v - 1] == kq[v - 1]]
+    assert coll_xq == [int(g["collide_xq"][0])]
+    assert int(kx[coll_xq[0] - 1]) == bits_to_int(g["value_xq"][0])
+    assert g["collide_yq"] == ["none"]
+    assert not any(ky[v] == kq[v] for v in range(7))
+    # the same keys through Algorithm 2
+    pts = np.stack([x, y, q])
+    assert np.array_equal(oracle.keys_fht(p, pts), oracle.keys_direct(p, pts))
+
+
+def test_example3_partition():
+    """Example 3 (Sec. 3.1): permuting 0011 into 0110 and splitting gives 01 and 10."""
+    g = read_golden("example3_preprocessing.txt")
+    q, qp = g["q"][0], g["permuted"][0]
+    # a permutation with q'_i = q_{perm[i]} that turns 0011 into 0110
+    perm = [0, 2, 3, 1]
+    assert "".join(q[j] for j in perm) == qp
+    # t = 2 parts, r = 2 -> r' = 1, W = 4.  m = (1, 3) in each part: row v = 1 has
+    # Had(1)_1 = Had(1)_3 = 1, so with b = (1, 2) the row-1 key spells the part's bits.
+    p = oracle.make_params(4, 2, m=[1, 3, 1, 3], b=[1, 2, 1, 2], t=2, perm=perm)
+    assert p.W == 4 and p.T == 6
+    keys = oracle.keys_direct(p, bits_to_words(q))[:, 0]
+    assert int(keys[0 * 3 + 0]) == bits_to_int(g["part1"][0])
+    assert int(keys[1 * 3 + 0]) == bits_to_int(g["part2"][0])
+
+
+# ----------------------------------------------------------------- Hadamard code
+
+@pytest.mark.parametrize("W", [2, 4, 8, 16, 32])
+def test_code_rows_match_sylvester_hadamard(W):
+    """C = (1 - H) / 2 (Eq. 6) with H the Sylvester Hadamard matrix of scipy."""
+    H = scipy.linalg.hadamard(W)
+    r = W.bit_length() - 2
+    p = oracle.make_params(W, r, list(range(W)), _pow2_b(W))
+    ones = np.full((W + 63) // 64, ~np.uint64(0), np.uint64)
+    if W % 64:
+        ones[-1] = np.uint64((1 << (W % 64)) - 1)
+    for v in range(1, W):
+        want = sum(1 << j for j in range(W) if (1 - H[v, j]) // 2 == 1)
+        assert oracle.key_direct(p, ones, v - 1) == want
+
+
+@pytest.mark.parametrize("W,P_", [(8, 97), (64, 101), (512, 65537), (2048, (1 << 31) - 1), (256, P)])
+def test_fht_route_against_dense_hadamard(W, P_):
+    """Algorithm 2's finish, h = (||q~||_1 - H t)/2 mod P, with H from scipy, t by hand."""
+    rng = np.random.default_rng(W)
+    d = W // 2
+    r = W.bit_length() - 2
+    p = oracle.derive_params(11 + W, d, r, t=1, P=P_)
+    assert p.W == W
+    H = scipy.linalg.hadamard(W).astype(object)
+    pts = rng.integers(0, 2**63, size=(5, (d + 63) // 64), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    got = oracle.keys_fht(p, pts)
+    for i in range(pts.shape[0]):
+        bits = [(int(pts[i, j >> 6]) >> (j & 63)) & 1 for j in range(d)]
+        t = [0] * W
+        for pos in range(d):
+            t[int(p.m[pos])] += int(p.b[pos]) * bits[int(p.perm[pos])]
+        l1 = sum(t)
+        y = H.dot(np.array(t, dtype=object))
+        for v in range(1, W):
+            assert (l1 - y[v]) % 2 == 0
+            assert int(got[v - 1, i]) == ((l1 - y[v]) // 2) % P_
+
+
+# ----------------------------------------------------------------- Lemma 3
+
+@pytest.mark.parametrize("d,r,t,P_", [
+    (64, 3, 1, P),        # general construction (d > W = 16)
+    (128, 8, 1, P),       # specific construction (d <= W = 512)
+    (100, 2, 1, 97),      # general, small prime: many modular wraps
+    (256, 16, 2, P),      # two parts, specific per part
+    (1024, 20, 2, 1009),  # two parts, W = 2048, small prime
+    (300, 7, 3, 65537),   # three parts, general per part (100 > 16)
+    (70, 6, 1, P),        # specific with d not a multiple of 64
+    (5, 0, 1, P),         # r = 0: one table, W = 2
+])
+def test_lemma3_fht_equals_direct(d, r, t, P_):
+    """Lemma 3: Algorithm 2 gives the same keys as Eq. (1) on the covering vectors."""
+    p = oracle.derive_params(1000 + d + r, d, r, t=t, P=P_)
+    rng = np.random.default_rng(d * 31 + r)
+    words = (d + 63) // 64
+    pts = rng.integers(0, 2**63, size=(40, words), dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=(40, words), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    pts[0] = 0
+    assert np.array_equal(oracle.keys_fht(p, pts), oracle.keys_direct(p, pts))
+    assert not oracle.keys_direct(p, pts)[:, 0].any()   # the zero vector hashes to 0 everywhere
+
+
+def test_r0_special_case_is_plain_universal_hash():
+    """r = 0, general map: W = 2, every coordinate goes to column 1, so the one key
+    is Eq. (1) itself, sum_i b_i x_i mod P (checked with Python integers)."""
+    d = 200
+    p = oracle.derive_params(5, d, 0)
+    assert p.W == 2 and p.T == 1 and np.all(p.m == 1)
+    rng = np.random.default_rng(0)
+    pts = rng.integers(0, 2**63, size=(20, 4), dtype=np.uint64)
+    pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    keys = oracle.keys_direct(p, pts)
+    for i in range(20):
+        s = sum(int(p.b[j]) for j in range(d) if (int(pts[i, p.perm[j] >> 6]) >> (int(p.perm[j]) & 63)) & 1)
+        assert int(keys[0, i]) == s % P
+
+
+# ----------------------------------------------------------------- Theorem 1 / 2
+
+def _ball(d, r):
+    for k in range(r + 1):
+        for pos in itertools.combinations(range(d), k):
+            yield pos
+
+
+@pytest.mark.parametrize("d,r", [(4, 1), (6, 2), (8, 2), (10, 3), (12, 3), (20, 2)])
+def test_theorem1_every_map_covers(d, r):
+    """Theorem 1: for any m, every z with |z| <= r has a row v with g_v AND z = 0."""
+    W = 2 << r
+    rng = np.random.default_rng(d * 7 + r)
+    zs = list(_ball(d, r))
+    Z = np.zeros((len(zs), 1), np.uint64)
+    for i, pos in enumerate(zs):
+        Z[i, 0] = sum(1 << j for j in pos)
+    maps = [rng.integers(0, W, size=d) for _ in range(30)]
+    maps.append(np.zeros(d, np.int64))                 # degenerate: every coordinate on column 0
+    maps.append(np.full(d, W - 1, np.int64))           # all on one column
+    for m in maps:
+        p = oracle.make_params(d, r, m, _pow2_b(d))
+        k = oracle.keys_direct(p, Z)                   # key == bit mask of g_v AND z
+        assert np.all((k == 0).any(axis=0))
+
+
+@pytest.mark.parametrize("d,r,t", [(64, 3, 1), (128, 6, 1), (64, 10, 2), (96, 12, 2), (90, 21, 3)])
+def test_near_pairs_always_collide(d, r, t):
+    """Total recall (Theorem 1 with the pigeonhole split of Sec. 3.1): any two points
+    at distance <= r share a key in at least one table, for random b, m and pi."""
+    rng = np.random.default_rng(d + r)
+    words = (d + 63) // 64
+    for trial in range(6):
+        p = oracle.derive_params(trial * 17 + d, d, r, t=t)
+        xs = rng.integers(0, 2**63, size=(50, words), dtype=np.uint64)
+        if d % 64:
+            xs[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+        ys = xs.copy()
+        for i in range(50):
+            k = rng.integers(0, r + 1)
+            for pos in rng.choice(d, size=k, replace=False):
+                ys[i, pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+        kx, ky = oracle.keys_direct(p, xs), oracle.keys_direct(p, ys)
+        assert np.all((kx == ky).any(axis=0))
+
+
+def test_theorem2_expected_collisions_closed_form():
+    """Theorem 2 (2): E[#rows v with g_v(x) = g_v(y)] < 2^(r+1-dist).
+
+    The expectation also has a closed form, pinned here both ways (4 standard
+    errors).  A row v != 0 collides iff every differing position lands on a column
+    j with <a(j), v> = 0; W/2 columns (column 0 among them) have that property.
+      - specific construction (d = W, random permutation): the dist positions land
+        on distinct columns, E = (W-1) C(W/2, dist) / C(W, dist);
+      - general construction with column 0 left out (Sec. 3.3): columns are uniform
+        over 1..W-1, of which W/2-1 qualify, E = (W-1) ((W/2-1)/(W-1))^dist.
+    The printed "sharper" bound 2^(r+1) (1/2 - 2^-(r+1))^dist is below this exact
+    value for dist >= 2, so only Theorem 2's bound is asserted as a bound.
+    """
+    from math import comb
+    rng = np.random.default_rng(3)
+    d, r = 64, 5
+    W = 2 << r
+    for dist in (3, 6, 9):
+        counts = []
+        for trial in range(400):
+            p = oracle.derive_params(trial, d, r)
+            x = rng.integers(0, 2**63, size=(1, 1), dtype=np.uint64)
+            y = x.copy()
+            for pos in rng.choice(d, size=dist, replace=False):
+                y[0, 0] ^= np.uint64(1) << np.uint64(pos)
+            counts.append(int((oracle.keys_direct(p, x) == oracle.keys_direct(p, y)).sum()))
+        mean, se = np.mean(counts), np.std(counts) / np.sqrt(len(counts))
+        exact = (W - 1) * comb(W // 2, dist) / comb(W, dist)
+        assert exact < 2.0 ** (r + 1 - dist)
+        assert abs(mean - exact) <= 4 * se + 1e-9, (dist, mean, exact)
+    d, r = 200, 3
+    W = 2 << r
+    for dist in (1, 2, 4):
+        counts = []
+        for trial in range(400):
+            p = oracle.derive_params(5000 + trial, d, r)
+            x = rng.integers(0, 2**63, size=(1, 4), dtype=np.uint64)
+            x[0, 3] &= np.uint64((1 << 8) - 1)
+            y = x.copy()
+            for pos in rng.choice(d, size=dist, replace=False):
+                y[0, pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+            counts.append(int((oracle.keys_direct(p, x) == oracle.keys_direct(p, y)).sum()))
+        mean, se = np.mean(counts), np.std(counts) / np.sqrt(len(counts))
+        exact = (W - 1) * ((W / 2 - 1) / (W - 1)) ** dist
+        assert exact < 2.0 ** (r + 1 - dist)
+        assert abs(mean - exact) <= 4 * se + 1e-9, (dist, mean, exact)
+
+
+# ----------------------------------------------------------------- parameters / RNG
+
+def test_splitmix64_published_vector():
+    """SplitMix64 from seed 1234567: the generator's published first outputs."""
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+            4593380528125082431, 16408922859458223821]
+    assert [int(v) for v in oracle.splitmix64(1234567, 5)] == want
+
+
+def test_prime_and_params_ranges():
+    assert sympy.isprime(P) and P < 2**50 and not any(sympy.isprime(q) for q in range(P + 1, 2**50))
+    for (d, r) in [(64, 3), (128, 8), (256, 16), (1024, 20), (30, 25)]:
+        p = oracle.derive_params(42, d, r)
+        assert p.t == oracle.default_parts(r) and p.rp == r // p.t and p.W == 2 ** (p.rp + 1)
+        assert sorted(p.perm.tolist()) == list(range(d))
+        if p.t == 1:
+            assert p.perm.tolist() == list(range(d))
+        assert p.part_off[0] == 0 and p.part_off[-1] == d
+        for k in range(p.t):
+            lo, hi = int(p.part_off[k]), int(p.part_off[k + 1])
+            mk = p.m[lo:hi]
+            if hi - lo <= p.W:
+                assert len(set(mk.tolist())) == hi - lo and mk.max() < p.W     # injective: a permutation's prefix
+            else:
+                assert mk.min() >= 1 and mk.max() < p.W                         # column 0 left out
+        assert int(p.b.max()) < P
+        q = oracle.derive_params(42, d, r)
+        assert np.array_equal(p.b, q.b) and np.array_equal(p.m, q.m)
+
+
+def test_partition_rule():
+    """Sec. 4.4: one part below radius 10, two parts for 10..20 (L = 2(2^(r/2+1) - 1))."""
+    assert [oracle.default_parts(r) for r in range(10)] == [1] * 10
+    assert all(oracle.default_parts(r) == 2 for r in range(10, 22))
+    for r in (10, 12, 14, 16):
+        p = oracle.derive_params(1, 256, r)
+        assert p.T == 2 * (2 ** (r // 2 + 1) - 1)
+    assert oracle.derive_params(1, 256, 16).T == 1022       # the paper's L for r = 16
+
+
+# ----------------------------------------------------------------- queries
+
+def test_linear_scan_bruteforce():
+    rng = np.random.default_rng(9)
+    pts = rng.integers(0, 2**63, size=(300, 2), dtype=np.uint64)
+    q = pts[17].copy()
+    q[0] ^= np.uint64(0b1011)
+    for radius in (0, 3, 40, 64, 128):
+        want = [i for i in range(300)
+                if bin(int(pts[i, 0]) ^ int(q[0])).count("1") + bin(int(pts[i, 1]) ^ int(q[1])).count("1") <= radius]
+        assert oracle.linear_scan(pts, q, radius).tolist() == want
+
+
+@pytest.mark.parametrize("d,r,t", [(32, 4, 1), (64, 3, 1), (100, 6, 1), (128, 2, 1), (64, 12, 2), (200, 9, 1)])
+def test_strategy2_equals_linear_scan(d, r, t):
+    """Strategy 2 over the covering tables reports exactly the linear-scan answer
+    (no false negatives, no false positives), for every radius up to r."""
+    rng = np.random.default_rng(d + 100 * r)
+    words = (d + 63) // 64
+    n = 400
+    pts = rng.integers(0, 2**63, size=(n, words), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    pts[5] = pts[4]                                    # a duplicate point
+    p = oracle.derive_params(d * r + 1, d, r, t=t)
+    tables = oracle.build_tables(p, pts)
+    for qi in range(25):
+        q = pts[rng.integers(0, n)].copy()
+        for pos in rng.choice(d, size=rng.integers(0, r + 2), replace=False):
+            q[pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+        for radius in sorted({0, r // 2, r}):
+            ids, ncoll, ncand = oracle.query(p, pts, tables, q, radius)
+            want = oracle.linear_scan(pts, q, radius)
+            assert ids.tolist() == want.tolist()
+            assert ncoll >= ncand >= len(ids)
+
+
+def test_tables_group_equal_keys():
+    rng = np.random.default_rng(1)
+    pts = rng.integers(0, 4, size=(200, 1), dtype=np.uint64)   # many duplicates
+    p = oracle.derive_params(3, 64, 3)
+    keys_all = oracle.keys_direct(p, pts)
+    for tau in (0, 7, 14):
+        keys, ids = oracle.table(p, pts, tau)
+        assert np.all(np.diff(keys.astype(np.float64)) >= 0)
+        assert sorted(ids.tolist()) == list(range(200))
+        assert np.array_equal(keys, keys_all[tau, ids])
