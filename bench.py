@@ -1,0 +1,323 @@
+"""Benchmark of the fcLSH hot path on one GB300 (or N, one independent problem per GPU).
+
+Workload (default): n = 1,000,000 points of d = 128 bits, build radius r = 8
+(one part, W = 512, T = 511 tables), 10,000 queries (half planted at distance
+0..8 from a data point, half uniform).  One step = the whole hot path over one
+batch: build the index from device-resident points (hash every point into its
+511 keys by Algorithm 2, radix-sort every table into its bucket directory) and
+answer the 10,000 queries in one batched launch sequence (hash, probe, dedup,
+popcount verify, sorted CSR results).  `value` = queries answered per second of
+step time, with the build inside the step.
+
+Printed JSON line: the driver's contract fields plus `breakdown` (points hashed/s,
+batched queries/s of the query phase alone, plain one-query-at-a-time GPU
+queries/s, GPU brute-force queries/s), `roofline` of the dominant kernel,
+`cpu_baseline` (the CPU oracle on a bounded sample), `e2e` (the same job through
+the C ABI from pinned host buffers, copies included) and `clocks`.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s at 100% recall and points hashed/s, batched vs plain on one GB300"
+CFG = 2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    """The CPU oracle as it stands, on a bounded sample of the same job, single-threaded.
+
+    Job = hash all n points into their T keys (direct route of the covering
+    definition) + answer every query by the oracle's exact answer (linear scan).
+    Both are timed on samples and scaled to the whole job.
+    """
+    import oracle
+
+    p = oracle.derive_params(w.index_seed, w.d, w.r)
+    t0 = time.perf_counter()
+    nh = 0
+    while time.perf_counter() - t0 < budget_s / 2 and nh < w.n:
+        oracle.keys_direct(p, w.points[nh:nh + 50])
+        nh += 50
+    th = (time.perf_counter() - t0) / nh
+    t0 = time.perf_counter()
+    nqs = 0
+    while time.perf_counter() - t0 < budget_s / 2 and nqs < w.queries.shape[0]:
+        oracle.linear_scan(w.points, w.queries[nqs], w.r)
+        nqs += 1
+    tq = (time.perf_counter() - t0) / nqs
+    job_s = w.n * th + w.queries.shape[0] * tq
+    return {"value": w.queries.shape[0] / job_s, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": "%d points hashed (direct route, all %d tables) + %d queries by linear scan over all %d points, "
+                      "scaled to the job of %d points + %d queries" % (nh, p.T, nqs, w.n, w.n, w.queries.shape[0]),
+            "points_hashed_per_s": 1.0 / th, "linear_scan_queries_per_s": 1.0 / tq}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    from paper_1602_02620_gb300 import workloads
+
+    w = workloads.make(CFG)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, budget_s=4.0)
+        if i >= args.warmup:
+            steps.append(cb)
+    v = statistics.median(s["value"] for s in steps)
+    cb = dict(steps[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.queries.shape[0] / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "d": w.d, "r": w.r, "queries": int(w.queries.shape[0])},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fclsh")
+    ap.add_argument("--plain-sample", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_1602_02620_gb300 import fclsh, workloads
+
+    w = workloads.make(CFG)
+    seed = w.index_seed + rank          # one independent problem per GPU
+    nq = int(w.queries.shape[0])
+    pts = torch.from_numpy(w.points.view(np.int64)).cuda()
+    qs = torch.from_numpy(w.queries.view(np.int64)).cuda()
+
+    def step(timing: bool):
+        idx = fclsh.build(pts, w.d, w.r, seed, timing=timing)
+        idx.timing_enable(False)          # the query batch runs as a replayed CUDA graph
+        ctx = idx.context()
+        ctx.query_async(qs, w.r)
+        dr = ctx.wait()
+        t = idx.timing_read()
+        ctx.close()
+        info = dict(idx.info)
+        idx.free()
+        return t, int(dr.total), info
+
+    for _ in range(args.warmup):
+        step(True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = fclsh.kernel_launches()
+    torch.cuda.synchronize()
+    ev0.record()
+    hash_ms = sort_ms = 0.0
+    hash_n = 0
+    total = 0
+    for _ in range(args.steps):
+        t, total, info = step(True)
+        hash_ms += t["build_hash"][0]
+        hash_n += t["build_hash"][1]
+        sort_ms += t["build_sort"][0]
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = fclsh.kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if dist:
+        tt = torch.tensor([elapsed], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    ms_step = 1000.0 * elapsed / args.steps
+    value = world * nq * args.steps / elapsed
+
+    # ---- query phase alone (index resident), batched vs plain vs brute force
+    idx = fclsh.build(pts, w.d, w.r, seed)
+    ctx = idx.context()
+    for _ in range(3):
+        ctx.query_async(qs, w.r)
+        ctx.wait()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record()
+    for _ in range(reps):
+        ctx.query_async(qs, w.r)
+        ctx.wait()
+    b.record()
+    torch.cuda.synchronize()
+    batched_qps = nq * reps / (a.elapsed_time(b) / 1000.0)
+    idx.timing_enable(True)
+    for _ in range(reps):
+        ctx.query_async(qs, w.r)
+        ctx.wait()
+    tq = idx.timing_read(reset=True)
+    idx.timing_enable(False)
+    res = ctx.fetch()
+    ctx.close()
+    ns = min(args.plain_sample, nq)
+    t0 = time.perf_counter()
+    plain = idx.query_plain(w.queries[:ns], w.r)
+    plain_qps = ns / (time.perf_counter() - t0)
+    assert np.array_equal(plain.ids, res.ids[: int(res.offs[ns])]), "plain and batched answers differ"
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    brute = idx.bruteforce(qs, w.r)
+    brute_qps = nq / (time.perf_counter() - t0)
+    assert np.array_equal(brute.ids, res.ids) and np.array_equal(brute.offs, res.offs), "brute force differs"
+    T = idx.T
+    idx.free()
+
+    # ---- e2e through the C ABI from pinned host buffers
+    hp = torch.from_numpy(w.points.view(np.int64)).pin_memory()
+    hq = torch.from_numpy(w.queries.view(np.int64)).pin_memory()
+    e2e_t = []
+    d2h = 0
+    for i in range(max(2, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        idx2 = fclsh.build(hp, w.d, w.r, seed)
+        r2 = idx2.query(hq, w.r)
+        e2e_t.append(time.perf_counter() - t0)
+        d2h = r2.offs.nbytes + r2.ids.nbytes + r2.collisions.nbytes + r2.candidates.nbytes
+        assert np.array_equal(r2.ids, res.ids)
+        idx2.free()
+    e2e = {"value": nq / statistics.median(e2e_t), "unit": "queries/s",
+           "h2d_bytes_per_step": int(w.points.nbytes + w.queries.nbytes), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the hash kernel (Algorithm 2 for every point): algorithmic bytes
+    # per launch = n * (d/8 read + 8 bytes per key written for the W-1 tables of the part)
+    peak, peak_kind = peaks()
+    hash_avg = hash_ms / max(hash_n, 1)
+    hash_bytes = w.n * (w.d / 8 + 8 * (info["W"] - 1))
+    ach = hash_bytes / (hash_avg / 1000.0) / 1e9
+    qk_ms, qk_n = tq["query_kernel"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "r": w.r, "tables": T, "queries": nq,
+                   "step": "build index from device-resident points + one batch of all queries",
+                   "l2": "inputs and index larger than L2 (16 MB points -> 4.1 GB keys, 6.1 GB index)"},
+        "breakdown": {
+            "build_hash_ms": hash_avg, "build_sort_ms": sort_ms / args.steps,
+            "points_hashed_per_s": w.n / (hash_avg / 1000.0),
+            "batched_query_queries_per_s": batched_qps,
+            "batched_query_kernel_ms": qk_ms / max(qk_n, 1), "batched_query_csr_ms": tq["query_csr"][0] / max(tq["query_csr"][1], 1),
+            "plain_queries_per_s": plain_qps, "plain_sample": ns,
+            "bruteforce_queries_per_s": brute_qps,
+            "results_per_step": total,
+        },
+        "roofline": {"kernel": "hash_tile_kernel<9> (Algorithm 2, all 511 keys per point)", "bound": "hbm",
+                     "achieved": ach, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "bytes_per_launch": hash_bytes},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * fclsh.h -- C ABI of libfclsh.so, a GB300 (sm_103a) implementation of Fast
+ * CoveringLSH (Pham & Pagh, "Scalability and Total Recall with Fast
+ * CoveringLSH", arXiv 1602.02620): exact Hamming-space r-near-neighbour
+ * reporting with no false negatives.
+ *
+ * Problem (Definition 2 with delta = 0, Sec. 2.1): given S, a set of n points
+ * in {0,1}^d, build a structure that for any query q reports every x in S with
+ * Hamming distance d(x, q) <= r.
+ *
+ * Conventions shared by every entry point:
+ *   - A point is d bits packed LSB-first into words = ceil(d/64) uint64 values:
+ *     coordinate i is bit (i % 64) of word (i / 64).  Arrays of points are
+ *     row-major [count][words].  Bits beyond d in the last word must be 0.
+ *   - Point ids are uint32 row indices 0..n-1 (n < 2^32).
+ *   - Keys are uint64 values in [0, P) with P = 2^50 - 27 (the prime of Eq. 1).
+ *   - Table tau = k*(W-1) + (v-1) is code row v = 1..W-1 of part k = 0..t-1,
+ *     W = 2^(r'+1), r' = floor(r/t); T = t*(W-1) tables in all.
+ *   - Pointers marked "host or device" are classified with
+ *     cudaPointerGetAttributes; device pointers must live on the index's GPU.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Every call returns a status; on failure fclsh_last_error() describes it
+ *     (thread-local, valid until the thread's next call).  No call throws, and a
+ *     failed call leaks nothing.
+ *   - Thread safety: calls on different fclsh_qctx objects (and therefore on
+ *     different streams) may run concurrently on one index; one fclsh_qctx is
+ *     used by one thread at a time.  fclsh_free must not race with any call.
+ */
+#ifndef FCLSH_H
+#define FCLSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FCLSH_OK = 0,
+    FCLSH_EINVAL = 1,    /* bad argument (null pointer, d = 0, r too large, ...) */
+    FCLSH_ENOMEM = 2,    /* device or host allocation failed; nothing was kept */
+    FCLSH_ECUDA = 3,     /* a CUDA call failed */
+    FCLSH_ERADIUS = 4,   /* query radius above the build radius r */
+    FCLSH_ETIMEOUT = 5,  /* a bounded wait ran out (server, device wait loops) */
+    FCLSH_EOVERFLOW = 6  /* a result buffer was too small; the call reports the size needed */
+} fclsh_status;
+
+typedef struct fclsh_index fclsh_index;   /* opaque; owns all device memory of one index */
+typedef struct fclsh_qctx fclsh_qctx;     /* opaque; per-stream query scratch and results */
+typedef struct fclsh_server fclsh_server; /* opaque; continuous-batching request server */
+
+/* Build options.  Zero-initialise and set what you need; NULL = all defaults. */
+typedef struct {
+    uint32_t t;               /* parts (Algorithm 1); 0 = paper's rule: 1 for r < 10, 2 for 10 <= r <= 21,
+                                 else the smallest t with floor(r/t) <= 10 */
+    uint32_t slot_bits;       /* bucket-directory slots per table = 2^slot_bits; 0 = max(18, ceil(log2 n)) */
+    uint64_t mem_budget;      /* bytes for transient build buffers; 0 = 1/4 of free device memory */
+    /* Explicit random choices (all four set, or all NULL to draw them from `seed`):
+       perm[d]: permuted position i holds coordinate perm[i] (Algorithm 1's permutation);
+       part_off[t+1]: part k = permuted positions [part_off[k], part_off[k+1]);
+       m[d]: code column in [0, W) of permuted position i (Eq. 4 map / Algorithm 2 permutation);
+       b[d]: seed-vector entry in [0, P) of permuted position i (Eq. 1). Host pointers, copied. */
+    const uint32_t *perm;
+    const uint32_t *part_off;
+    const uint32_t *m;
+    const uint64_t *b;
+    uint32_t timing;          /* 1: record per-phase CUDA events from the start (see fclsh_timing_read) */
+} fclsh_build_opts;
+
+typedef struct {
+    uint64_t n;
+    uint32_t d, words, r, t, rp, W, T, slot_bits;
+    uint64_t P;
+    uint64_t device_bytes;    /* device memory held by the index */
+    int device;               /* CUDA device ordinal */
+} fclsh_info;
+
+/* Host-side query results (library-owned; free with fclsh_result_free). */
+typedef struct {
+    uint64_t nq;
+    uint64_t *offs;        /* [nq+1]: results of query i are ids[offs[i] .. offs[i+1]) */
+    uint32_t *ids;         /* [offs[nq]] ascending within each query */
+    uint64_t *collisions;  /* [nq] #Collisions: bucket entries whose key equals the query's (Sec. 4.1, S2) */
+    uint64_t *candidates;  /* [nq] #Candidates: distinct ids among them (Sec. 4.1, S3) */
+} fclsh_result;
+
+/* Device-side view of a context's last results (owned by the context; valid until its next query). */
+typedef struct {
+    uint64_t nq;
+    uint64_t total;              /* = offs[nq] */
+    const uint64_t *offs;        /* device [nq+1] */
+    const uint32_t *ids;         /* device [total] */
+    const uint64_t *collisions;  /* device [nq] */
+    const uint64_t *candidates;  /* device [nq] */
+} fclsh_device_result;
+
+/* Kernel shape choices.  They change speed only, never results. */
+typedef struct {
+    uint32_t query_block;     /* threads per query CTA: 128, 256 or 512 */
+    uint32_t query_ctas_per_sm;
+    uint32_t hash_set_log2;   /* shared-memory dedup set size 2^k (10..13) */
+    uint32_t inline_probe;    /* bucket-range length handled by the probing lane itself (1..32) */
+    uint32_t use_graph;       /* capture a batch's launches into a CUDA graph and replay it */
+} fclsh_tuning;
+
+/* ------------------------------------------------------------------ index */
+
+/*
+ * Build the index (Sec. 3.2, "Construction"): draw the random choices of
+ * Algorithms 1 and 2 from `seed`, hash every point into its T keys by
+ * Algorithm 2 (sketch + fast Hadamard transform, Sec. 3.2 "Fast computation of
+ * hash functions"), and group the points of each table into buckets by key
+ * (Sec. 2.2: only non-empty buckets are stored).
+ *   points: host or device, [n][ceil(d/64)] uint64, copied (caller keeps ownership).
+ *   n: 1 .. 2^32-1.  d: >= 1.  r: build radius, 0 .. 63, with floor(r/t) <= 10.
+ *   opts: NULL for defaults.  out: receives the index; NULL on failure.
+ * Errors: FCLSH_EINVAL (bad sizes or options), FCLSH_ENOMEM, FCLSH_ECUDA.
+ * Synchronous: returns once the index is complete.
+ */
+fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t d, uint32_t r, uint64_t seed,
+                         const fclsh_build_opts *opts, fclsh_index **out);
+
+/* Release the index and all its device memory.  NULL is ignored. */
+void fclsh_free(fclsh_index *idx);
+
+/* Sizes and derived parameters (Sec. 3.1: L = 2^(r'+1) - 1 tables per part). */
+fclsh_status fclsh_get_info(const fclsh_index *idx, fclsh_info *out);
+
+/*
+ * Copy out the index's random choices (host arrays sized d, t+1, d, d) so that
+ * they can be compared with an independent derivation.  Any pointer may be NULL.
+ */
+fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm, uint32_t *part_off,
+                              uint32_t *m, uint64_t *b);
+
+/*
+ * Keys of `cnt` points under the index's parameters: keys_out[tau*cnt + i] is
+ * the key of point i in table tau, i.e. Algorithm 2's h_v for part k, which by
+ * Lemma 3 equals Eq. (1) applied to g_v AND x (Eq. 2 / Eq. 4).
+ *   pts: host or device [cnt][words].  keys_out: host or device [T][cnt].
+ * Runs on `stream`; returns after the keys are written when keys_out is host memory.
+ */
+fclsh_status fclsh_hash(const fclsh_index *idx, const uint64_t *pts, uint64_t cnt, uint64_t *keys_out,
+                        void *stream);
+
+/*
+ * Ids of the bucket with `key` in table `table` (Sec. 2.2), ascending.
+ *   ids_out: host, capacity `cap`; *count receives the bucket size (which may
+ *   exceed cap; then only the first cap ids are written).  Synchronous.
+ */
+fclsh_status fclsh_bucket(const fclsh_index *idx, uint32_t table, uint64_t key, uint32_t *ids_out,
+                          uint64_t cap, uint64_t *count);
+
+/*
+ * Every (key, id) entry of table `table` in directory order: ascending by
+ * (key mod 2^slot_bits, id).  keys_out/ids_out: host arrays of n entries.  Synchronous.
+ */
+fclsh_status fclsh_export_table(const fclsh_index *idx, uint32_t table, uint64_t *keys_out, uint32_t *ids_out);
+
+/* ------------------------------------------------------------------ queries */
+
+/*
+ * Exact r-NN reporting with Strategy 2 (Sec. 2.2) in the S1-S3 steps of
+ * Sec. 4.1: hash each query into its T keys, look up its bucket in every table,
+ * remove duplicate candidates, and report every candidate within Hamming
+ * distance `radius` (verified by popcount).  Queries run batched in one
+ * persistent kernel.
+ *   queries: host or device [nq][words].  radius <= the build radius r.
+ *   radii: optional per-query radii (host or device, [nq], each <= r); NULL = `radius` for all.
+ *   out: host results, ascending ids per query.
+ * Errors: FCLSH_ERADIUS, FCLSH_EINVAL, FCLSH_ENOMEM, FCLSH_ECUDA.  Synchronous.
+ */
+fclsh_status fclsh_query(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                         const uint32_t *radii, void *stream, fclsh_result **out);
+
+/*
+ * The same answers through the one-query-at-a-time path: for each query
+ * separately, a hash launch, a probe/dedup/verify launch and a copy back.
+ * The baseline that the batched form is measured against.  Synchronous.
+ */
+fclsh_status fclsh_query_plain(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                               void *stream, fclsh_result **out);
+
+/*
+ * Linear scan on the GPU: every point within `radius` of each query by XOR +
+ * popcount over all n points (the ground truth of Sec. 4.2), independent of the
+ * tables.  Any radius is allowed.  Synchronous.
+ */
+fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                              void *stream, fclsh_result **out);
+
+void fclsh_result_free(fclsh_result *res);
+
+/* ------------------------------------------------------------------ contexts */
+
+/* Per-stream query scratch.  Create one per concurrent stream. */
+fclsh_status fclsh_qctx_create(fclsh_index *idx, fclsh_qctx **out);
+void fclsh_qctx_free(fclsh_qctx *ctx);
+
+/*
+ * Enqueue one batch on `stream` without waiting: the whole batch (hash, probe,
+ * dedup, verify, result sort and CSR) runs on the device with no host
+ * round-trip, and with use_graph set it is replayed as one CUDA graph.
+ *   queries, radii: device pointers (radii may be NULL: `radius` for all).
+ *   The buffers must stay valid until fclsh_qctx_wait returns.
+ */
+fclsh_status fclsh_query_async(fclsh_qctx *ctx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                               const uint32_t *radii, void *stream);
+
+/*
+ * Wait for the context's batch and expose its device results.  If the result
+ * buffer overflowed, the batch is re-run with a larger buffer before returning.
+ */
+fclsh_status fclsh_qctx_wait(fclsh_qctx *ctx, fclsh_device_result *out);
+
+/* Copy the context's last device results to a host fclsh_result. */
+fclsh_status fclsh_qctx_fetch(fclsh_qctx *ctx, fclsh_result **out);
+
+/* ------------------------------------------------------------------ tuning */
+
+fclsh_status fclsh_get_tuning(const fclsh_index *idx, fclsh_tuning *out);
+fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *tune);
+
+/*
+ * Time the query kernel shapes on a sample batch (device or host queries) and
+ * keep the fastest; the choice is cached in `cache_path` (JSON, may be NULL)
+ * keyed by (n, d, r, t, W).  Results never depend on the choice.  Synchronous.
+ */
+fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                            const char *cache_path, fclsh_tuning *chosen);
+
+/* ------------------------------------------------------------------ timing */
+
+/*
+ * Per-phase device time (milliseconds, CUDA events on the launching stream)
+ * accumulated since the last reset: [0] build hash kernel, [1] build sort and
+ * directory kernels, [2] batched query kernel, [3] result sort + CSR,
+ * [4] fclsh_hash kernel.  counts[i] = timed launches of phase i.  ms[7] is
+ * unused; counts[7] = kernels this library has launched in this process (a
+ * replayed CUDA graph counts its kernel nodes).  Timing is off until enabled;
+ * enabling adds one event pair per phase and runs query batches without graphs.
+ */
+fclsh_status fclsh_timing_enable(fclsh_index *idx, int on);
+fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64_t counts[8], int reset);
+
+/* Kernels this library has enqueued in this process (a replayed CUDA graph counts its kernel nodes). */
+uint64_t fclsh_kernel_launches(void);
+
+/* Thread-local description of the calling thread's last failure. */
+const char *fclsh_last_error(void);
+
+/* Library version string. */
+const char *fclsh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCLSH_H */

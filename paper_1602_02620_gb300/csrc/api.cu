@@ -1,0 +1,1222 @@
+// api.cu -- the C ABI of libfclsh (declared in include/fclsh.h): index build,
+// batched / plain / brute-force queries, per-stream query contexts, timing and
+// kernel-shape tuning.  Host code only orchestrates; every step of the hot path
+// runs in the kernels of hash.cu, sort.cu and query.cu.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fclsh {
+
+// ---- declarations from query.cu / hash.cu
+
+size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_log2);
+cudaError_t launch_query_batch(const QueryArgs &a, uint32_t grid, uint32_t block, size_t smem, cudaStream_t s);
+cudaError_t query_batch_occupancy(uint32_t block, size_t smem, int *ctas_per_sm);
+cudaError_t launch_query_plain(const QueryArgs &a, const uint64_t *keys, uint32_t *bitmap, cudaStream_t s);
+cudaError_t launch_sort_small(unsigned long long *v, const unsigned long long *d_count, cudaStream_t s);
+cudaError_t launch_bruteforce(const uint64_t *points, uint64_t n, uint32_t words, const uint64_t *queries, uint64_t nq,
+                              uint32_t radius, unsigned long long *cursor, unsigned long long *staged, uint64_t cap,
+                              uint32_t idbits, uint32_t *res_cnt, int sm_count, cudaStream_t s);
+cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned long long *d_count, uint64_t cap,
+                               uint64_t idmask, uint32_t *ids, int sm_count, cudaStream_t s);
+size_t hash_smem_bytes(uint32_t W, uint32_t dk);
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+fclsh_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FCLSH_ENOMEM;
+    }
+    return FCLSH_ECUDA;
+}
+
+static fclsh_status fail(fclsh_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+// ---------------------------------------------------------------- launch accounting
+
+static std::atomic<int64_t> g_launches{0};
+
+void note_launch(uint64_t kernels) { g_launches.fetch_add((int64_t)kernels); }
+uint64_t launch_count() { return (uint64_t)g_launches.load(); }
+int64_t launch_count_adjust(int64_t delta) { return g_launches.fetch_add(delta) + delta; }
+
+// ---------------------------------------------------------------- helpers
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static uint32_t bits_for(uint64_t v)   // bits needed for values 0..v-1 (at least 1)
+{
+    uint32_t b = 1;
+    while (b < 64 && (1ULL << b) < v) ++b;
+    return b;
+}
+
+// Device allocation list freed together on error.
+struct DevAllocs {
+    std::vector<void *> ptrs;
+    ~DevAllocs()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    cudaError_t alloc(T **p, size_t count)
+    {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    void release()   // keep the allocations
+    {
+        ptrs.clear();
+    }
+};
+
+// ---------------------------------------------------------------- timing
+
+struct PendingTimer {
+    int phase;
+    cudaEvent_t a, b;
+};
+static std::mutex g_timer_mu;
+static std::vector<std::pair<fclsh_index *, PendingTimer>> g_pending;
+
+struct PhaseTimer {
+    fclsh_index *idx;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseTimer(fclsh_index *i, int ph, cudaStream_t st) : idx(i), phase(ph), s(st)
+    {
+        if (idx && idx->timing) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~PhaseTimer()
+    {
+        if (a) {
+            cudaEventRecord(b, s);
+            std::lock_guard<std::mutex> g(g_timer_mu);
+            g_pending.push_back({idx, PendingTimer{phase, a, b}});
+        }
+    }
+};
+
+static void resolve_timers(fclsh_index *idx)
+{
+    std::lock_guard<std::mutex> g(g_timer_mu);
+    std::vector<std::pair<fclsh_index *, PendingTimer>> keep;
+    for (auto &pt : g_pending) {
+        if (pt.first != idx) {
+            keep.push_back(pt);
+            continue;
+        }
+        if (cudaEventQuery(pt.second.b) != cudaSuccess) {
+            cudaGetLastError();
+            keep.push_back(pt);
+            continue;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, pt.second.a, pt.second.b);
+        idx->ms[pt.second.phase] += ms;
+        idx->cnt[pt.second.phase] += 1;
+        cudaEventDestroy(pt.second.a);
+        cudaEventDestroy(pt.second.b);
+    }
+    g_pending.swap(keep);
+}
+
+static void drop_timers(fclsh_index *idx)
+{
+    std::lock_guard<std::mutex> g(g_timer_mu);
+    std::vector<std::pair<fclsh_index *, PendingTimer>> keep;
+    for (auto &pt : g_pending) {
+        if (pt.first == idx) {
+            cudaEventSynchronize(pt.second.b);
+            cudaEventDestroy(pt.second.a);
+            cudaEventDestroy(pt.second.b);
+        } else {
+            keep.push_back(pt);
+        }
+    }
+    g_pending.swap(keep);
+}
+
+}  // namespace fclsh
+
+using namespace fclsh;
+
+// ---------------------------------------------------------------- query context
+
+struct fclsh_qctx {
+    fclsh_index *idx = nullptr;
+    unsigned long long *counters = nullptr;   // [0] work, [1] cursor
+    unsigned long long *staged_a = nullptr, *staged_b = nullptr;
+    uint64_t cap = 0;
+    uint32_t *hist = nullptr, *partials = nullptr;
+    uint64_t nq_cap = 0;
+    uint32_t *res_cnt = nullptr;
+    uint64_t *res_offs = nullptr;
+    uint32_t *res_ids = nullptr;
+    unsigned long long *coll = nullptr, *cand = nullptr;
+    uint64_t *scan_part = nullptr;
+    uint32_t *bitmaps = nullptr;
+    uint32_t grid = 0, block = 0;
+    size_t smem = 0;
+    uint64_t *qbuf = nullptr;   // device copy of host queries
+    uint64_t qbuf_cap = 0;
+    uint32_t *rbuf = nullptr;   // device copy of host radii
+    uint64_t rbuf_cap = 0;
+    // last batch
+    const uint64_t *last_q = nullptr;
+    uint64_t last_nq = 0;
+    uint32_t last_radius = 0;
+    const uint32_t *last_radii = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool pending = false;
+    bool sorted_in_b = false;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    const uint64_t *g_q = nullptr;
+    uint64_t g_nq = 0;
+    uint32_t g_radius = 0;
+    const uint32_t *g_radii = nullptr;
+    cudaStream_t g_stream = nullptr;
+    uint64_t g_cap = 0;
+    fclsh_tuning g_tune{};
+    uint64_t g_kernels = 0;
+    cudaStream_t own = nullptr;   // used for the NULL stream: blocking, so it orders after legacy-stream work
+};
+
+static void ctx_free_buffers(fclsh_qctx *c)
+{
+    void *ps[] = {c->counters, c->staged_a, c->staged_b, c->hist, c->partials, c->res_cnt, c->res_offs,
+                  c->res_ids, c->coll, c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->own) cudaStreamDestroy(c->own);
+}
+
+static fclsh_status ctx_shape(fclsh_qctx *c)
+{
+    fclsh_index *idx = c->idx;
+    const fclsh_tuning &tu = idx->tune;
+    const uint32_t block = tu.query_block;
+    const size_t smem = query_smem_bytes(idx->T, idx->W, idx->words, tu.hash_set_log2);
+    if (smem > idx->smem_optin)
+        return fail(FCLSH_EINVAL, "query kernel needs %zu bytes of shared memory (limit %zu)", smem, idx->smem_optin);
+    int occ = 0;
+    FCLSH_CUDA(query_batch_occupancy(block, smem, &occ));
+    if (occ < 1) return fail(FCLSH_EINVAL, "query kernel does not fit on an SM (block %u, smem %zu)", block, smem);
+    const uint32_t per_sm = std::max(1u, std::min<uint32_t>((uint32_t)occ, tu.query_ctas_per_sm));
+    const uint32_t grid = per_sm * (uint32_t)idx->sm_count;
+    if (grid != c->grid) {
+        if (c->bitmaps) cudaFree(c->bitmaps);
+        c->bitmaps = nullptr;
+        const uint64_t bm_words = (idx->n + 31) / 32;
+        FCLSH_CUDA(cudaMalloc(&c->bitmaps, (size_t)grid * bm_words * 4));
+        FCLSH_CUDA(cudaMemset(c->bitmaps, 0, (size_t)grid * bm_words * 4));
+        c->grid = grid;
+    }
+    c->block = block;
+    c->smem = smem;
+    return FCLSH_OK;
+}
+
+static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
+{
+    if (nq > c->nq_cap) {
+        void *ps[] = {c->res_cnt, c->res_offs, c->coll, c->cand, c->scan_part};
+        for (void *p : ps)
+            if (p) cudaFree(p);
+        c->res_cnt = nullptr;
+        c->res_offs = nullptr;
+        c->coll = c->cand = nullptr;
+        c->scan_part = nullptr;
+        const uint64_t m = std::max<uint64_t>(nq, 1024);
+        FCLSH_CUDA(cudaMalloc(&c->res_cnt, m * 4));
+        FCLSH_CUDA(cudaMalloc(&c->res_offs, (m + 1) * 8));
+        FCLSH_CUDA(cudaMalloc(&c->coll, m * 8));
+        FCLSH_CUDA(cudaMalloc(&c->cand, m * 8));
+        FCLSH_CUDA(cudaMalloc(&c->scan_part, scan_partials_entries(m) * 8));
+        c->nq_cap = m;
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+    }
+    if (cap > c->cap) {
+        void *ps[] = {c->staged_a, c->staged_b, c->res_ids, c->hist, c->partials};
+        for (void *p : ps)
+            if (p) cudaFree(p);
+        c->staged_a = c->staged_b = nullptr;
+        c->res_ids = nullptr;
+        c->hist = c->partials = nullptr;
+        FCLSH_CUDA(cudaMalloc(&c->staged_a, cap * 8));
+        FCLSH_CUDA(cudaMalloc(&c->staged_b, cap * 8));
+        FCLSH_CUDA(cudaMalloc(&c->res_ids, cap * 4));
+        const size_t h = sort_keys_hist_entries(cap);
+        FCLSH_CUDA(cudaMalloc(&c->hist, h * 4));
+        FCLSH_CUDA(cudaMalloc(&c->partials, scan_partials_entries(h) * 4));
+        c->cap = cap;
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+    }
+    return FCLSH_OK;
+}
+
+static QueryArgs make_args(fclsh_index *idx)
+{
+    QueryArgs a{};
+    a.points = idx->points;
+    a.n = idx->n;
+    a.words = idx->words;
+    a.t = idx->t;
+    a.W = idx->W;
+    a.T = idx->T;
+    a.slot_bits = idx->slot_bits;
+    a.hset_log2 = idx->tune.hash_set_log2;
+    a.inline_len = idx->tune.inline_probe;
+    a.col_off = idx->col_off;
+    a.col_coord = idx->col_coord;
+    a.col_b = idx->col_b;
+    a.offs = idx->offs;
+    a.offs_stride = idx->offs_stride();
+    a.ent = idx->ent;
+    a.idbits = bits_for(idx->n);
+    return a;
+}
+
+// Enqueue the launches of one batch (no host synchronisation inside).
+static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uint32_t radius, const uint32_t *radii,
+                                  cudaStream_t s)
+{
+    fclsh_index *idx = c->idx;
+    QueryArgs a = make_args(idx);
+    a.queries = q;
+    a.nq = nq;
+    a.radius = radius;
+    a.radii = radii;
+    a.work = c->counters;
+    a.cursor = c->counters + 1;
+    a.staged = c->staged_a;
+    a.cap = c->cap;
+    a.res_cnt = c->res_cnt;
+    a.coll = c->coll;
+    a.cand = c->cand;
+    a.bitmaps = c->bitmaps;
+    a.bm_words = (idx->n + 31) / 32;
+    FCLSH_CUDA(cudaMemsetAsync(c->counters, 0, 2 * sizeof(unsigned long long), s));
+    {
+        PhaseTimer pt(idx, 2, s);
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(c->grid, std::max<uint64_t>(nq, 1));
+        FCLSH_CUDA(launch_query_batch(a, grid, c->block, c->smem, s));
+    }
+    {
+        PhaseTimer pt(idx, 3, s);
+        const uint32_t bits = a.idbits + bits_for(std::max<uint64_t>(nq, 2));
+        bool in_b = false;
+        FCLSH_CUDA(radix_sort_keys_dev((uint64_t *)c->staged_a, (uint64_t *)c->staged_b, c->counters + 1, c->cap, bits,
+                                       c->hist, c->partials, &in_b, s));
+        c->sorted_in_b = in_b;
+        FCLSH_CUDA(scan_u32_to_u64(c->res_cnt, c->res_offs, nq, c->scan_part, s));
+        FCLSH_CUDA(launch_extract_ids(in_b ? c->staged_b : c->staged_a, c->counters + 1, c->cap,
+                                      (1ULL << a.idbits) - 1, c->res_ids, idx->sm_count, s));
+    }
+    return FCLSH_OK;
+}
+
+static fclsh_status run_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uint32_t radius, const uint32_t *radii,
+                              cudaStream_t s)
+{
+    fclsh_index *idx = c->idx;
+    const bool graph = idx->tune.use_graph && !idx->timing;
+    if (!graph) return enqueue_batch(c, q, nq, radius, radii, s);
+    const bool same = c->gexec && c->g_q == q && c->g_nq == nq && c->g_radius == radius && c->g_radii == radii &&
+                      c->g_stream == s && c->g_cap == c->cap &&
+                      memcmp(&c->g_tune, &idx->tune, sizeof(fclsh_tuning)) == 0;
+    if (!same) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        FCLSH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const uint64_t before = launch_count();
+        fclsh_status st = enqueue_batch(c, q, nq, radius, radii, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        c->g_kernels = launch_count() - before;   // captured, not run: counted at each replay
+        launch_count_adjust(-(int64_t)c->g_kernels);
+        if (st != FCLSH_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        c->g_q = q;
+        c->g_nq = nq;
+        c->g_radius = radius;
+        c->g_radii = radii;
+        c->g_stream = s;
+        c->g_cap = c->cap;
+        c->g_tune = idx->tune;
+    }
+    FCLSH_CUDA(cudaGraphLaunch(c->gexec, s));
+    note_launch(c->g_kernels);
+    return FCLSH_OK;
+}
+
+// ---------------------------------------------------------------- build
+
+extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t d, uint32_t r, uint64_t seed,
+                                    const fclsh_build_opts *opts, fclsh_index **out)
+{
+    if (!out) return fail(FCLSH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!points) return fail(FCLSH_EINVAL, "points is NULL");
+    if (n == 0 || n > 0xFFFFFFFFULL - 1) return fail(FCLSH_EINVAL, "n must be in 1..2^32-2 (got %llu)", (unsigned long long)n);
+    if (d == 0 || d > 16384) return fail(FCLSH_EINVAL, "d must be in 1..16384 (got %u)", d);
+    fclsh_build_opts o{};
+    if (opts) o = *opts;
+    const uint32_t t = o.t ? o.t : default_parts(r);
+    if (t > d) return fail(FCLSH_EINVAL, "t = %u parts exceed d = %u", t, d);
+    const uint32_t rp = r / t;
+    if (rp + 1 > (uint32_t)kMaxLogW) return fail(FCLSH_EINVAL, "per-part radius floor(r/t) = %u exceeds 10", rp);
+    const uint32_t W = 2u << rp;
+
+    auto idx = new fclsh_index();
+    std::unique_ptr<fclsh_index> guard(idx);
+    FCLSH_CUDA(cudaGetDevice(&idx->device));
+    cudaDeviceProp prop;
+    FCLSH_CUDA(cudaGetDeviceProperties(&prop, idx->device));
+    idx->sm_count = prop.multiProcessorCount;
+    idx->smem_optin = prop.sharedMemPerBlockOptin;
+    idx->n = n;
+    idx->d = d;
+    idx->words = (d + 63) / 64;
+    idx->r = r;
+    idx->t = t;
+    idx->rp = rp;
+    idx->W = W;
+    idx->T = t * (W - 1);
+    idx->tune = fclsh_tuning{256, 4, 12, 4, 1};
+    idx->timing = o.timing != 0;
+
+    const bool explicit_params = o.perm || o.part_off || o.m || o.b;
+    if (explicit_params) {
+        if (!(o.perm && o.part_off && o.m && o.b)) return fail(FCLSH_EINVAL, "explicit parameters need all of perm, part_off, m, b");
+        idx->perm.assign(o.perm, o.perm + d);
+        idx->part_off.assign(o.part_off, o.part_off + t + 1);
+        idx->m.assign(o.m, o.m + d);
+        idx->b.assign(o.b, o.b + d);
+        std::vector<char> seen(d, 0);
+        for (uint32_t i = 0; i < d; ++i) {
+            if (idx->perm[i] >= d || seen[idx->perm[i]]) return fail(FCLSH_EINVAL, "perm is not a permutation of [d]");
+            seen[idx->perm[i]] = 1;
+            if (idx->m[i] >= W) return fail(FCLSH_EINVAL, "m[%u] = %u is not below W = %u", i, idx->m[i], W);
+            if (idx->b[i] >= kP) return fail(FCLSH_EINVAL, "b[%u] is not below P", i);
+        }
+        if (idx->part_off[0] != 0 || idx->part_off[t] != d) return fail(FCLSH_EINVAL, "part_off must run from 0 to d");
+        for (uint32_t k = 0; k < t; ++k)
+            if (idx->part_off[k + 1] <= idx->part_off[k]) return fail(FCLSH_EINVAL, "parts must be non-empty and ordered");
+    } else if (derive_params(seed, d, t, W, idx->perm, idx->part_off, idx->m, idx->b) != 0) {
+        return fail(FCLSH_EINVAL, "cannot derive parameters");
+    }
+    uint32_t max_dk = 0;
+    for (uint32_t k = 0; k < t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
+    if (hash_smem_bytes(W, max_dk) > idx->smem_optin)
+        return fail(FCLSH_EINVAL, "a part of %u coordinates with W = %u does not fit the hash kernel's shared memory",
+                    max_dk, W);
+
+    uint32_t sb = o.slot_bits;
+    if (!sb) {
+        sb = 18;
+        while (sb < 32 && (1ULL << sb) < n) ++sb;
+    }
+    if (sb < 18 || sb > 32) return fail(FCLSH_EINVAL, "slot_bits must be in 18..32");
+    idx->slot_bits = sb;
+
+    std::vector<uint32_t> col_off, coord;
+    std::vector<uint64_t> bval;
+    column_lists(d, t, W, idx->perm, idx->part_off, idx->m, idx->b, col_off, coord, bval);
+
+    DevAllocs keep;   // index memory (released into idx on success)
+    cudaError_t e;
+    if ((e = keep.alloc(&idx->points, n * idx->words)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(points)");
+    if ((e = keep.alloc(&idx->col_off, col_off.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(col_off)");
+    if ((e = keep.alloc(&idx->col_coord, coord.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(col_coord)");
+    if ((e = keep.alloc(&idx->col_b, bval.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(col_b)");
+    if ((e = keep.alloc(&idx->offs, (size_t)idx->T * idx->offs_stride())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(directory)");
+    if ((e = keep.alloc(&idx->ent, (size_t)idx->T * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(entries)");
+    idx->device_bytes = n * idx->words * 8 + col_off.size() * 4 + coord.size() * 12 +
+                        (uint64_t)idx->T * idx->offs_stride() * 4 + (uint64_t)idx->T * n * 8;
+
+    cudaStream_t s = nullptr;
+    FCLSH_CUDA(cudaMemcpyAsync(idx->points, points, n * idx->words * 8, cudaMemcpyDefault, s));
+    FCLSH_CUDA(cudaMemcpyAsync(idx->col_off, col_off.data(), col_off.size() * 4, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemcpyAsync(idx->col_coord, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemcpyAsync(idx->col_b, bval.data(), bval.size() * 8, cudaMemcpyHostToDevice, s));
+
+    // Transient buffers: the keys of one part, and radix-sort buffers for a chunk of its tables.
+    const uint32_t L = W - 1;
+    DevAllocs tmp;
+    uint64_t *keys = nullptr;
+    if ((e = tmp.alloc(&keys, (size_t)L * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(build keys)");
+    size_t free_b = 0, total_b = 0;
+    FCLSH_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t budget = o.mem_budget ? o.mem_budget : free_b / 2;
+    const uint64_t per_row = n * 24 + sort_hist_entries(1, n) * 4 + 64;
+    uint64_t rows = std::max<uint64_t>(1, budget / per_row);
+    rows = std::min<uint64_t>(rows, L);
+    rows = std::min<uint64_t>(rows, std::max<uint64_t>(1, 0xFFFFFFF0ULL / n));
+    SortBuffers sbuf{};
+    if ((e = tmp.alloc(&sbuf.keys_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
+    if ((e = tmp.alloc(&sbuf.keys_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
+    if ((e = tmp.alloc(&sbuf.ids_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
+    if ((e = tmp.alloc(&sbuf.ids_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
+    sbuf.hist_cap = sort_hist_entries((uint32_t)rows, n);
+    sbuf.partials_cap = scan_partials_entries(sbuf.hist_cap);
+    if ((e = tmp.alloc(&sbuf.hist, sbuf.hist_cap)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort hist)");
+    if ((e = tmp.alloc(&sbuf.partials, sbuf.partials_cap)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort scan)");
+
+    for (uint32_t k = 0; k < t; ++k) {
+        {
+            PhaseTimer pt(idx, 0, s);
+            FCLSH_CUDA(launch_hash_part(idx, k, idx->points, n, keys, n, s));
+        }
+        PhaseTimer pt(idx, 1, s);
+        for (uint64_t r0 = 0; r0 < L; r0 += rows) {
+            const uint32_t nr = (uint32_t)std::min<uint64_t>(rows, L - r0);
+            bool in_b = false;
+            FCLSH_CUDA(radix_sort_rows(keys + r0 * n, nr, n, sb, sbuf, &in_b, s));
+            const uint64_t grow = (uint64_t)k * L + r0;
+            FCLSH_CUDA(launch_finalize_rows(in_b ? sbuf.keys_b : sbuf.keys_a, in_b ? sbuf.ids_b : sbuf.ids_a, nr, n, sb,
+                                            idx->ent + grow * n, idx->offs + grow * idx->offs_stride(), s));
+        }
+    }
+    FCLSH_CUDA(cudaStreamSynchronize(s));
+    resolve_timers(idx);
+    keep.release();
+    *out = guard.release();
+    return FCLSH_OK;
+}
+
+extern "C" void fclsh_free(fclsh_index *idx)
+{
+    if (!idx) return;
+    cudaSetDevice(idx->device);
+    cudaDeviceSynchronize();
+    drop_timers(idx);
+    void *ps[] = {idx->points, idx->col_off, idx->col_coord, idx->col_b, idx->offs, idx->ent};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    delete idx;
+}
+
+extern "C" fclsh_status fclsh_get_info(const fclsh_index *idx, fclsh_info *out)
+{
+    if (!idx || !out) return fail(FCLSH_EINVAL, "NULL argument");
+    out->n = idx->n;
+    out->d = idx->d;
+    out->words = idx->words;
+    out->r = idx->r;
+    out->t = idx->t;
+    out->rp = idx->rp;
+    out->W = idx->W;
+    out->T = idx->T;
+    out->slot_bits = idx->slot_bits;
+    out->P = idx->P;
+    out->device_bytes = idx->device_bytes;
+    out->device = idx->device;
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm, uint32_t *part_off, uint32_t *m,
+                                         uint64_t *b)
+{
+    if (!idx) return fail(FCLSH_EINVAL, "index is NULL");
+    if (perm) memcpy(perm, idx->perm.data(), idx->d * 4);
+    if (part_off) memcpy(part_off, idx->part_off.data(), (idx->t + 1) * 4);
+    if (m) memcpy(m, idx->m.data(), idx->d * 4);
+    if (b) memcpy(b, idx->b.data(), idx->d * 8);
+    return FCLSH_OK;
+}
+
+// ---------------------------------------------------------------- hash / bucket / export
+
+extern "C" fclsh_status fclsh_hash(const fclsh_index *cidx, const uint64_t *pts, uint64_t cnt, uint64_t *keys_out,
+                                   void *stream)
+{
+    fclsh_index *idx = const_cast<fclsh_index *>(cidx);
+    if (!idx || !keys_out || (!pts && cnt)) return fail(FCLSH_EINVAL, "NULL argument");
+    if (cnt == 0) return FCLSH_OK;
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    DevAllocs tmp;
+    const uint64_t *dp = pts;
+    uint64_t *dk = keys_out;
+    cudaError_t e;
+    const bool keys_host = !is_device_ptr(keys_out);
+    if (!is_device_ptr(pts)) {
+        uint64_t *p = nullptr;
+        if ((e = tmp.alloc(&p, cnt * idx->words)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(points)");
+        FCLSH_CUDA(cudaMemcpyAsync(p, pts, cnt * idx->words * 8, cudaMemcpyHostToDevice, s));
+        dp = p;
+    }
+    if (keys_host) {
+        if ((e = tmp.alloc(&dk, (size_t)idx->T * cnt)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(keys)");
+    }
+    {
+        PhaseTimer pt(idx, 4, s);
+        const uint32_t L = idx->W - 1;
+        for (uint32_t k = 0; k < idx->t; ++k) FCLSH_CUDA(launch_hash_part(idx, k, dp, cnt, dk + (uint64_t)k * L * cnt, cnt, s));
+    }
+    if (keys_host) {
+        FCLSH_CUDA(cudaMemcpyAsync(keys_out, dk, (size_t)idx->T * cnt * 8, cudaMemcpyDeviceToHost, s));
+        FCLSH_CUDA(cudaStreamSynchronize(s));
+        resolve_timers(idx);
+    } else if (!tmp.ptrs.empty()) {
+        FCLSH_CUDA(cudaStreamSynchronize(s));   // temporaries are freed on return
+        resolve_timers(idx);
+    }
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_bucket(const fclsh_index *idx, uint32_t table, uint64_t key, uint32_t *ids_out,
+                                     uint64_t cap, uint64_t *count)
+{
+    if (!idx || !count || (cap && !ids_out)) return fail(FCLSH_EINVAL, "NULL argument");
+    if (table >= idx->T) return fail(FCLSH_EINVAL, "table %u out of range (T = %u)", table, idx->T);
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    const uint64_t sl = key & (idx->slots() - 1);
+    uint32_t lohi[2];
+    FCLSH_CUDA(cudaMemcpy(lohi, idx->offs + (uint64_t)table * idx->offs_stride() + sl, 8, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> ent(lohi[1] - lohi[0]);
+    if (!ent.empty())
+        FCLSH_CUDA(cudaMemcpy(ent.data(), idx->ent + (uint64_t)table * idx->n + lohi[0], ent.size() * 8,
+                              cudaMemcpyDeviceToHost));
+    uint64_t c = 0;
+    const uint32_t fp = (uint32_t)(key >> idx->slot_bits);
+    for (uint64_t e : ent)
+        if ((uint32_t)(e >> 32) == fp && key < kP) {
+            if (c < cap) ids_out[c] = (uint32_t)e;
+            ++c;
+        }
+    *count = c;
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_export_table(const fclsh_index *idx, uint32_t table, uint64_t *keys_out, uint32_t *ids_out)
+{
+    if (!idx || !keys_out || !ids_out) return fail(FCLSH_EINVAL, "NULL argument");
+    if (table >= idx->T) return fail(FCLSH_EINVAL, "table %u out of range (T = %u)", table, idx->T);
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    std::vector<uint32_t> offs(idx->offs_stride());
+    std::vector<uint64_t> ent(idx->n);
+    FCLSH_CUDA(cudaMemcpy(offs.data(), idx->offs + (uint64_t)table * idx->offs_stride(), offs.size() * 4,
+                          cudaMemcpyDeviceToHost));
+    FCLSH_CUDA(cudaMemcpy(ent.data(), idx->ent + (uint64_t)table * idx->n, idx->n * 8, cudaMemcpyDeviceToHost));
+    for (uint64_t sl = 0; sl < idx->slots(); ++sl)
+        for (uint32_t e = offs[sl]; e < offs[sl + 1]; ++e) {
+            keys_out[e] = ((ent[e] >> 32) << idx->slot_bits) | sl;
+            ids_out[e] = (uint32_t)ent[e];
+        }
+    return FCLSH_OK;
+}
+
+// ---------------------------------------------------------------- contexts
+
+extern "C" fclsh_status fclsh_qctx_create(fclsh_index *idx, fclsh_qctx **out)
+{
+    if (!idx || !out) return fail(FCLSH_EINVAL, "NULL argument");
+    *out = nullptr;
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    fclsh_qctx *c = new fclsh_qctx();
+    c->idx = idx;
+    fclsh_status st = FCLSH_OK;
+    cudaError_t e = cudaMalloc(&c->counters, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(counters)");
+    if (st == FCLSH_OK && (e = cudaStreamCreate(&c->own)) != cudaSuccess)
+        st = cuda_fail(e, "cudaStreamCreate");
+    if (st == FCLSH_OK) st = ctx_shape(c);
+    if (st == FCLSH_OK) st = ctx_reserve(c, 1024, 1ULL << 22);
+    if (st != FCLSH_OK) {
+        ctx_free_buffers(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return FCLSH_OK;
+}
+
+extern "C" void fclsh_qctx_free(fclsh_qctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->idx->device);
+    if (c->pending && c->last_stream) cudaStreamSynchronize(c->last_stream);
+    cudaDeviceSynchronize();
+    ctx_free_buffers(c);
+    delete c;
+}
+
+static fclsh_status check_radius(const fclsh_index *idx, uint32_t radius)
+{
+    if (radius > idx->r) return fail(FCLSH_ERADIUS, "radius %u exceeds the build radius %u", radius, idx->r);
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_query_async(fclsh_qctx *c, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                                          const uint32_t *radii, void *stream)
+{
+    if (!c || (!queries && nq)) return fail(FCLSH_EINVAL, "NULL argument");
+    fclsh_index *idx = c->idx;
+    fclsh_status st = check_radius(idx, radius);
+    if (st != FCLSH_OK) return st;
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    if (nq && !is_device_ptr(queries)) return fail(FCLSH_EINVAL, "fclsh_query_async needs device queries");
+    if (radii && !is_device_ptr(radii)) return fail(FCLSH_EINVAL, "fclsh_query_async needs device radii");
+    if (nq >= (1ULL << (64 - bits_for(idx->n) - 1))) return fail(FCLSH_EINVAL, "too many queries in one batch");
+    if ((st = ctx_shape(c)) != FCLSH_OK) return st;
+    const uint64_t want = std::max<uint64_t>(c->cap, std::min<uint64_t>(nq * 64, 1ULL << 26));
+    if ((st = ctx_reserve(c, nq, want)) != FCLSH_OK) return st;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
+    c->last_q = queries;
+    c->last_nq = nq;
+    c->last_radius = radius;
+    c->last_radii = radii;
+    c->last_stream = s;
+    c->pending = true;
+    if (nq == 0) return FCLSH_OK;
+    return run_batch(c, queries, nq, radius, radii, s);
+}
+
+extern "C" fclsh_status fclsh_qctx_wait(fclsh_qctx *c, fclsh_device_result *out)
+{
+    if (!c) return fail(FCLSH_EINVAL, "NULL argument");
+    fclsh_index *idx = c->idx;
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    if (c->pending && c->last_nq) {
+        for (int attempt = 0; attempt < 8; ++attempt) {
+            unsigned long long cur = 0;
+            FCLSH_CUDA(cudaMemcpyAsync(&cur, c->counters + 1, 8, cudaMemcpyDeviceToHost, c->last_stream));
+            FCLSH_CUDA(cudaStreamSynchronize(c->last_stream));
+            if (cur <= c->cap) break;
+            // the staging buffer overflowed: grow it and run the batch again
+            fclsh_status st = ctx_reserve(c, c->last_nq, cur + cur / 4 + 1024);
+            if (st != FCLSH_OK) return st;
+            st = run_batch(c, c->last_q, c->last_nq, c->last_radius, c->last_radii, c->last_stream);
+            if (st != FCLSH_OK) return st;
+        }
+    }
+    c->pending = false;
+    resolve_timers(idx);
+    if (out) {
+        out->nq = c->last_nq;
+        out->offs = c->res_offs;
+        out->ids = c->res_ids;
+        out->collisions = (const uint64_t *)c->coll;
+        out->candidates = (const uint64_t *)c->cand;
+        uint64_t total = 0;
+        if (c->last_nq) FCLSH_CUDA(cudaMemcpy(&total, c->res_offs + c->last_nq, 8, cudaMemcpyDeviceToHost));
+        out->total = total;
+    }
+    return FCLSH_OK;
+}
+
+static fclsh_result *alloc_result(uint64_t nq, uint64_t total)
+{
+    fclsh_result *r = (fclsh_result *)calloc(1, sizeof(fclsh_result));
+    if (!r) return nullptr;
+    r->nq = nq;
+    r->offs = (uint64_t *)malloc((nq + 1) * 8);
+    r->ids = (uint32_t *)malloc(std::max<uint64_t>(total, 1) * 4);
+    r->collisions = (uint64_t *)malloc(std::max<uint64_t>(nq, 1) * 8);
+    r->candidates = (uint64_t *)malloc(std::max<uint64_t>(nq, 1) * 8);
+    if (!r->offs || !r->ids || !r->collisions || !r->candidates) {
+        fclsh_result_free(r);
+        return nullptr;
+    }
+    return r;
+}
+
+extern "C" void fclsh_result_free(fclsh_result *r)
+{
+    if (!r) return;
+    free(r->offs);
+    free(r->ids);
+    free(r->collisions);
+    free(r->candidates);
+    free(r);
+}
+
+extern "C" fclsh_status fclsh_qctx_fetch(fclsh_qctx *c, fclsh_result **out)
+{
+    if (!c || !out) return fail(FCLSH_EINVAL, "NULL argument");
+    *out = nullptr;
+    fclsh_device_result dr;
+    fclsh_status st = fclsh_qctx_wait(c, &dr);
+    if (st != FCLSH_OK) return st;
+    fclsh_result *r = alloc_result(dr.nq, dr.total);
+    if (!r) return fail(FCLSH_ENOMEM, "host allocation of results failed");
+    if (dr.nq) {
+        cudaError_t e;
+        if ((e = cudaMemcpy(r->offs, dr.offs, (dr.nq + 1) * 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (dr.total && (e = cudaMemcpy(r->ids, dr.ids, dr.total * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) ||
+            (e = cudaMemcpy(r->collisions, dr.collisions, dr.nq * 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(r->candidates, dr.candidates, dr.nq * 8, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            fclsh_result_free(r);
+            return cuda_fail(e, "cudaMemcpy(results)");
+        }
+    } else {
+        r->offs[0] = 0;
+    }
+    *out = r;
+    return FCLSH_OK;
+}
+
+// Device copies of host queries / radii owned by the context.
+static fclsh_status stage_inputs(fclsh_qctx *c, const uint64_t *queries, uint64_t nq, const uint32_t *radii,
+                                 cudaStream_t s, const uint64_t **dq, const uint32_t **dr)
+{
+    fclsh_index *idx = c->idx;
+    *dq = queries;
+    *dr = radii;
+    if (nq && !is_device_ptr(queries)) {
+        if (nq * idx->words > c->qbuf_cap) {
+            if (c->qbuf) cudaFree(c->qbuf);
+            c->qbuf = nullptr;
+            FCLSH_CUDA(cudaMalloc(&c->qbuf, nq * idx->words * 8));
+            c->qbuf_cap = nq * idx->words;
+        }
+        FCLSH_CUDA(cudaMemcpyAsync(c->qbuf, queries, nq * idx->words * 8, cudaMemcpyHostToDevice, s));
+        *dq = c->qbuf;
+    }
+    if (radii && nq && !is_device_ptr(radii)) {
+        for (uint64_t i = 0; i < nq; ++i)
+            if (radii[i] > idx->r) return fail(FCLSH_ERADIUS, "radius %u of query %llu exceeds the build radius %u",
+                                              radii[i], (unsigned long long)i, idx->r);
+        if (nq > c->rbuf_cap) {
+            if (c->rbuf) cudaFree(c->rbuf);
+            c->rbuf = nullptr;
+            FCLSH_CUDA(cudaMalloc(&c->rbuf, nq * 4));
+            c->rbuf_cap = nq;
+        }
+        FCLSH_CUDA(cudaMemcpyAsync(c->rbuf, radii, nq * 4, cudaMemcpyHostToDevice, s));
+        *dr = c->rbuf;
+    }
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_query(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                                    const uint32_t *radii, void *stream, fclsh_result **out)
+{
+    if (!idx || !out || (!queries && nq)) return fail(FCLSH_EINVAL, "NULL argument");
+    *out = nullptr;
+    fclsh_status st = check_radius(idx, radius);
+    if (st != FCLSH_OK) return st;
+    fclsh_qctx *c = nullptr;
+    if ((st = fclsh_qctx_create(idx, &c)) != FCLSH_OK) return st;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
+    const uint64_t *dq;
+    const uint32_t *dr;
+    st = stage_inputs(c, queries, nq, radii, s, &dq, &dr);
+    if (st == FCLSH_OK) st = fclsh_query_async(c, dq, nq, radius, dr, s);
+    if (st == FCLSH_OK) st = fclsh_qctx_fetch(c, out);
+    fclsh_qctx_free(c);
+    return st;
+}
+
+// ---------------------------------------------------------------- plain path
+
+extern "C" fclsh_status fclsh_query_plain(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                                          void *stream, fclsh_result **out)
+{
+    if (!idx || !out || (!queries && nq)) return fail(FCLSH_EINVAL, "NULL argument");
+    *out = nullptr;
+    fclsh_status st = check_radius(idx, radius);
+    if (st != FCLSH_OK) return st;
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool qdev = nq && is_device_ptr(queries);
+    DevAllocs tmp;
+    cudaError_t e;
+    uint64_t *dq = nullptr, *dkeys = nullptr;
+    uint32_t *bitmap = nullptr;
+    unsigned long long *cnt = nullptr, *staged = nullptr, *staged_b = nullptr;
+    uint32_t *hist = nullptr, *partials = nullptr;
+    const uint64_t bm_words = (idx->n + 31) / 32;
+    const uint64_t cap = idx->n;   // one query reports at most n ids
+    if ((e = tmp.alloc(&dq, idx->words)) != cudaSuccess || (e = tmp.alloc(&dkeys, idx->T)) != cudaSuccess ||
+        (e = tmp.alloc(&bitmap, bm_words)) != cudaSuccess || (e = tmp.alloc(&cnt, 3)) != cudaSuccess ||
+        (e = tmp.alloc(&staged, cap)) != cudaSuccess || (e = tmp.alloc(&staged_b, cap)) != cudaSuccess ||
+        (e = tmp.alloc(&hist, sort_keys_hist_entries(cap))) != cudaSuccess ||
+        (e = tmp.alloc(&partials, scan_partials_entries(sort_keys_hist_entries(cap)))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(plain query scratch)");
+    FCLSH_CUDA(cudaMemsetAsync(bitmap, 0, bm_words * 4, s));
+    std::vector<uint64_t> offs(1, 0), coll, cand;
+    std::vector<uint32_t> ids;
+    const uint32_t L = idx->W - 1;
+    const uint32_t idbits = bits_for(idx->n);
+    for (uint64_t i = 0; i < nq; ++i) {
+        const uint64_t *qsrc = queries + i * idx->words;
+        FCLSH_CUDA(cudaMemcpyAsync(dq, qsrc, idx->words * 8, qdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        FCLSH_CUDA(cudaMemsetAsync(cnt, 0, 3 * 8, s));
+        for (uint32_t k = 0; k < idx->t; ++k) FCLSH_CUDA(launch_hash_part(idx, k, dq, 1, dkeys + (uint64_t)k * L, 1, s));
+        QueryArgs a = make_args(idx);
+        a.queries = dq;
+        a.nq = 1;
+        a.radius = radius;
+        a.cursor = cnt;
+        a.coll = cnt + 1;
+        a.cand = cnt + 2;
+        a.staged = staged;
+        a.cap = cap;
+        FCLSH_CUDA(launch_query_plain(a, dkeys, bitmap, s));
+        unsigned long long h[3];
+        FCLSH_CUDA(cudaMemcpyAsync(h, cnt, 24, cudaMemcpyDeviceToHost, s));
+        FCLSH_CUDA(cudaStreamSynchronize(s));
+        const uint64_t m = h[0];
+        const unsigned long long *sorted = staged;
+        if (m > 2048) {
+            bool in_b = false;
+            FCLSH_CUDA(radix_sort_keys_dev((uint64_t *)staged, (uint64_t *)staged_b, cnt, cap, idbits, hist, partials,
+                                           &in_b, s));
+            sorted = in_b ? staged_b : staged;
+        } else if (m > 1) {
+            FCLSH_CUDA(launch_sort_small(staged, cnt, s));
+        }
+        const size_t at = ids.size();
+        ids.resize(at + m);
+        if (m) {
+            std::vector<unsigned long long> tmpk(m);
+            FCLSH_CUDA(cudaMemcpyAsync(tmpk.data(), sorted, m * 8, cudaMemcpyDeviceToHost, s));
+            FCLSH_CUDA(cudaStreamSynchronize(s));
+            for (uint64_t j = 0; j < m; ++j) ids[at + j] = (uint32_t)tmpk[j];
+        }
+        offs.push_back(ids.size());
+        coll.push_back(h[1]);
+        cand.push_back(h[2]);
+        // leave the bitmap clear for the next query
+        FCLSH_CUDA(cudaMemsetAsync(bitmap, 0, bm_words * 4, s));
+    }
+    FCLSH_CUDA(cudaStreamSynchronize(s));
+    fclsh_result *r = alloc_result(nq, ids.size());
+    if (!r) return fail(FCLSH_ENOMEM, "host allocation of results failed");
+    memcpy(r->offs, offs.data(), offs.size() * 8);
+    if (!ids.empty()) memcpy(r->ids, ids.data(), ids.size() * 4);
+    if (nq) {
+        memcpy(r->collisions, coll.data(), nq * 8);
+        memcpy(r->candidates, cand.data(), nq * 8);
+    }
+    *out = r;
+    return FCLSH_OK;
+}
+
+// ---------------------------------------------------------------- brute force
+
+extern "C" fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                                         void *stream, fclsh_result **out)
+{
+    if (!idx || !out || (!queries && nq)) return fail(FCLSH_EINVAL, "NULL argument");
+    *out = nullptr;
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    if (idx->words > 48) return fail(FCLSH_EINVAL, "brute force supports d <= 3072");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevAllocs tmp;
+    cudaError_t e;
+    const uint64_t *dq = queries;
+    if (nq && !is_device_ptr(queries)) {
+        uint64_t *p;
+        if ((e = tmp.alloc(&p, nq * idx->words)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(queries)");
+        FCLSH_CUDA(cudaMemcpyAsync(p, queries, nq * idx->words * 8, cudaMemcpyHostToDevice, s));
+        dq = p;
+    }
+    const uint32_t idbits = bits_for(idx->n);
+    const uint32_t bits = idbits + bits_for(std::max<uint64_t>(nq, 2));
+    if (bits > 64) return fail(FCLSH_EINVAL, "too many queries");
+    uint64_t cap = std::max<uint64_t>(1ULL << 20, nq * 16);
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        DevAllocs b;
+        unsigned long long *cnt, *sa, *sb;
+        uint32_t *res_cnt, *hist, *partials, *ids;
+        uint64_t *offs, *sp;
+        const size_t h = sort_keys_hist_entries(cap);
+        if ((e = b.alloc(&cnt, 1)) != cudaSuccess || (e = b.alloc(&sa, cap)) != cudaSuccess ||
+            (e = b.alloc(&sb, cap)) != cudaSuccess || (e = b.alloc(&res_cnt, nq)) != cudaSuccess ||
+            (e = b.alloc(&hist, h)) != cudaSuccess || (e = b.alloc(&partials, scan_partials_entries(h))) != cudaSuccess ||
+            (e = b.alloc(&ids, cap)) != cudaSuccess || (e = b.alloc(&offs, nq + 1)) != cudaSuccess ||
+            (e = b.alloc(&sp, scan_partials_entries(nq))) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(brute-force scratch)");
+        FCLSH_CUDA(cudaMemsetAsync(cnt, 0, 8, s));
+        FCLSH_CUDA(cudaMemsetAsync(res_cnt, 0, std::max<uint64_t>(nq, 1) * 4, s));
+        FCLSH_CUDA(launch_bruteforce(idx->points, idx->n, idx->words, dq, nq, radius, cnt, sa, cap, idbits, res_cnt,
+                                     idx->sm_count, s));
+        unsigned long long total = 0;
+        FCLSH_CUDA(cudaMemcpyAsync(&total, cnt, 8, cudaMemcpyDeviceToHost, s));
+        FCLSH_CUDA(cudaStreamSynchronize(s));
+        if (total > cap) {
+            cap = total + total / 4;
+            continue;
+        }
+        bool in_b = false;
+        FCLSH_CUDA(radix_sort_keys_dev((uint64_t *)sa, (uint64_t *)sb, cnt, cap, bits, hist, partials, &in_b, s));
+        FCLSH_CUDA(scan_u32_to_u64(res_cnt, offs, nq, sp, s));
+        FCLSH_CUDA(launch_extract_ids(in_b ? sb : sa, cnt, cap, (1ULL << idbits) - 1, ids, idx->sm_count, s));
+        fclsh_result *r = alloc_result(nq, total);
+        if (!r) return fail(FCLSH_ENOMEM, "host allocation of results failed");
+        cudaError_t e2 = cudaMemcpyAsync(r->offs, offs, (nq + 1) * 8, cudaMemcpyDeviceToHost, s);
+        if (e2 == cudaSuccess && total) e2 = cudaMemcpyAsync(r->ids, ids, total * 4, cudaMemcpyDeviceToHost, s);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+        if (e2 != cudaSuccess) {
+            fclsh_result_free(r);
+            return cuda_fail(e2, "cudaMemcpy(brute-force results)");
+        }
+        for (uint64_t i = 0; i < nq; ++i) r->collisions[i] = r->candidates[i] = 0;
+        *out = r;
+        return FCLSH_OK;
+    }
+    return fail(FCLSH_EOVERFLOW, "brute-force result buffer kept overflowing");
+}
+
+// ---------------------------------------------------------------- tuning / timing / misc
+
+extern "C" fclsh_status fclsh_get_tuning(const fclsh_index *idx, fclsh_tuning *out)
+{
+    if (!idx || !out) return fail(FCLSH_EINVAL, "NULL argument");
+    *out = idx->tune;
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t)
+{
+    if (!idx || !t) return fail(FCLSH_EINVAL, "NULL argument");
+    if (t->query_block != 128 && t->query_block != 256 && t->query_block != 512)
+        return fail(FCLSH_EINVAL, "query_block must be 128, 256 or 512");
+    if (t->hash_set_log2 < 10 || t->hash_set_log2 > 14) return fail(FCLSH_EINVAL, "hash_set_log2 must be in 10..14");
+    if (t->inline_probe < 1 || t->inline_probe > 32) return fail(FCLSH_EINVAL, "inline_probe must be in 1..32");
+    if (t->query_ctas_per_sm < 1 || t->query_ctas_per_sm > 16) return fail(FCLSH_EINVAL, "query_ctas_per_sm must be in 1..16");
+    idx->tune = *t;
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_timing_enable(fclsh_index *idx, int on)
+{
+    if (!idx) return fail(FCLSH_EINVAL, "NULL argument");
+    idx->timing = on != 0;
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64_t counts[8], int reset)
+{
+    if (!idx) return fail(FCLSH_EINVAL, "NULL argument");
+    cudaSetDevice(idx->device);
+    resolve_timers(idx);
+    for (int i = 0; i < 8; ++i) {
+        if (ms) ms[i] = idx->ms[i];
+        if (counts) counts[i] = i == 7 ? launch_count() : idx->cnt[i];
+        if (reset) {
+            idx->ms[i] = 0;
+            idx->cnt[i] = 0;
+        }
+    }
+    return FCLSH_OK;
+}
+
+extern "C" uint64_t fclsh_kernel_launches(void) { return launch_count(); }
+
+extern "C" const char *fclsh_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *fclsh_version(void) { return "fclsh-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------- autotuner
+
+static std::string tune_key(const fclsh_index *idx)
+{
+    char buf[160];
+    snprintf(buf, sizeof buf, "n=%llu,d=%u,r=%u,t=%u,W=%u", (unsigned long long)idx->n, idx->d, idx->r, idx->t, idx->W);
+    return buf;
+}
+
+static bool read_field(const std::string &obj, const char *name, uint32_t *v)
+{
+    const std::string pat = std::string("\"") + name + "\":";
+    size_t at = obj.find(pat);
+    if (at == std::string::npos) return false;
+    *v = (uint32_t)strtoul(obj.c_str() + at + pat.size(), nullptr, 10);
+    return true;
+}
+
+// The cache is a JSON object: {"<key>": {"query_block": 256, ...}, ...}, one entry per line.
+static bool cache_lookup(const char *path, const std::string &key, fclsh_tuning *t)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    std::string all;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof buf, f)) > 0) all.append(buf, got);
+    fclose(f);
+    const std::string pat = "\"" + key + "\":";
+    size_t at = all.find(pat);
+    if (at == std::string::npos) return false;
+    size_t end = all.find('}', at);
+    if (end == std::string::npos) return false;
+    const std::string obj = all.substr(at + pat.size(), end - at - pat.size() + 1);
+    fclsh_tuning v{};
+    if (!read_field(obj, "query_block", &v.query_block) || !read_field(obj, "query_ctas_per_sm", &v.query_ctas_per_sm) ||
+        !read_field(obj, "hash_set_log2", &v.hash_set_log2) || !read_field(obj, "inline_probe", &v.inline_probe) ||
+        !read_field(obj, "use_graph", &v.use_graph))
+        return false;
+    *t = v;
+    return true;
+}
+
+static void cache_store(const char *path, const std::string &key, const fclsh_tuning &t)
+{
+    std::vector<std::string> lines;
+    if (FILE *f = fopen(path, "r")) {
+        char buf[1024];
+        while (fgets(buf, sizeof buf, f)) {
+            std::string l(buf);
+            while (!l.empty() && (l.back() == '\n' || l.back() == ',')) l.pop_back();
+            if (l.size() > 2 && l[0] == ' ' && l.find("\"" + key + "\":") == std::string::npos) lines.push_back(l);
+        }
+        fclose(f);
+    }
+    char ent[512];
+    snprintf(ent, sizeof ent,
+             "  \"%s\": {\"query_block\": %u, \"query_ctas_per_sm\": %u, \"hash_set_log2\": %u, \"inline_probe\": %u, "
+             "\"use_graph\": %u}",
+             key.c_str(), t.query_block, t.query_ctas_per_sm, t.hash_set_log2, t.inline_probe, t.use_graph);
+    lines.push_back(ent);
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    for (size_t i = 0; i < lines.size(); ++i) fprintf(f, "%s%s\n", lines[i].c_str(), i + 1 < lines.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                                       const char *cache_path, fclsh_tuning *chosen)
+{
+    if (!idx || (!queries && nq)) return fail(FCLSH_EINVAL, "NULL argument");
+    fclsh_status st = check_radius(idx, radius);
+    if (st != FCLSH_OK) return st;
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    const std::string key = tune_key(idx);
+    fclsh_tuning best{};
+    if (cache_path && cache_lookup(cache_path, key, &best) && fclsh_set_tuning(idx, &best) == FCLSH_OK) {
+        if (chosen) *chosen = best;
+        return FCLSH_OK;
+    }
+    const fclsh_tuning saved = idx->tune;
+    const bool saved_timing = idx->timing;
+    idx->timing = false;
+    fclsh_qctx *c = nullptr;
+    if ((st = fclsh_qctx_create(idx, &c)) != FCLSH_OK) return st;
+    cudaStream_t s = c->own;
+    const uint64_t *dq;
+    const uint32_t *dr;
+    st = stage_inputs(c, queries, nq, nullptr, s, &dq, &dr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    best = saved;
+    const uint32_t blocks[] = {128, 256, 512};
+    const uint32_t hlogs[] = {11, 12, 13};
+    const uint32_t inl[] = {2, 4, 8};
+    const uint32_t ctas[] = {1, 2, 4, 8};
+    for (uint32_t bk : blocks)
+        for (uint32_t hl : hlogs)
+            for (uint32_t il : inl)
+                for (uint32_t ct : ctas) {
+                    if (st != FCLSH_OK) break;
+                    fclsh_tuning t{bk, ct, hl, il, 0};
+                    if (query_smem_bytes(idx->T, idx->W, idx->words, hl) > idx->smem_optin) continue;
+                    int occ = 0;
+                    if (query_batch_occupancy(bk, query_smem_bytes(idx->T, idx->W, idx->words, hl), &occ) != cudaSuccess ||
+                        occ < (int)ct) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    idx->tune = t;
+                    if (fclsh_query_async(c, dq, nq, radius, nullptr, s) != FCLSH_OK ||
+                        fclsh_qctx_wait(c, nullptr) != FCLSH_OK)
+                        continue;
+                    cudaEventRecord(e0, s);
+                    for (int rep = 0; rep < 2; ++rep) fclsh_query_async(c, dq, nq, radius, nullptr, s);
+                    cudaEventRecord(e1, s);
+                    if (fclsh_qctx_wait(c, nullptr) != FCLSH_OK) continue;
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = t;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    fclsh_qctx_free(c);
+    idx->timing = saved_timing;
+    best.use_graph = 1;
+    idx->tune = best;
+    if (st != FCLSH_OK) return st;
+    if (cache_path) cache_store(cache_path, key, best);
+    if (chosen) *chosen = best;
+    return FCLSH_OK;
+}

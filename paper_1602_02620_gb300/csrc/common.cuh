@@ -1,0 +1,169 @@
+// common.cuh -- shared definitions of libfclsh (internal; not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fclsh.h"
+
+namespace fclsh {
+
+// The prime of Eq. (1): 2^50 - 27, the largest prime below 2^50.  Sums of up to
+// 2^11 residues stay below 2^61, so Algorithm 2 runs exactly in 64-bit integers.
+constexpr uint64_t kP = (1ULL << 50) - 27;
+constexpr uint64_t kMask50 = (1ULL << 50) - 1;
+constexpr int kMaxLogW = 11;          // W = 2^(r'+1) <= 2048
+constexpr int kSortTile = 4096;       // radix-sort items per tile (256 threads x 16)
+constexpr int kSortThreads = 256;
+
+// x mod P for x < 2^63, by 2^50 == 27 (mod P).
+__host__ __device__ __forceinline__ uint64_t mod_p(uint64_t x)
+{
+    uint64_t r = (x & kMask50) + (x >> 50) * 27ULL;   // < 2^50 + 2^18 < 2P
+    return r >= kP ? r - kP : r;
+}
+
+// (a + b) mod P for a, b < P.
+__host__ __device__ __forceinline__ uint64_t add_mod_p(uint64_t a, uint64_t b)
+{
+    uint64_t s = a + b;
+    return s >= kP ? s - kP : s;
+}
+
+// Key from the transform output: h_v = ((S - y_v) / 2) mod P, where S = y_0 is
+// the sum of the sketch (||q~||_1 reduced) and S - y_v = 2 * sum_{C(v,j)=1} t_j
+// is even and in [0, 2^62).  Arithmetic is mod 2^64, which is exact here.
+__host__ __device__ __forceinline__ uint64_t finish_key(uint64_t S, uint64_t y)
+{
+    return mod_p((S - y) >> 1);
+}
+
+// Per-part column lists of the sketch (Algorithm 2): column j of part k receives
+// the seed-vector entries b_i of the coordinates i with m_k(i) = j.
+struct PartCols {
+    const uint32_t *col_off;    // [W+1], absolute offsets into coord/bval
+    const uint32_t *coord;      // coordinate (bit index into the point)
+    const uint64_t *bval;       // b_i in [0, P)
+};
+
+struct PhaseTimer;
+
+// Everything the query kernels read: the index, one batch, and its outputs.
+struct QueryArgs {
+    const uint64_t *points;
+    uint64_t n;
+    uint32_t words, t, W, T, slot_bits, hset_log2, inline_len;
+    const uint32_t *col_off, *col_coord;
+    const uint64_t *col_b;
+    const uint32_t *offs;
+    uint64_t offs_stride;
+    const uint64_t *ent;
+    const uint64_t *queries;
+    uint64_t nq;
+    uint32_t radius;
+    const uint32_t *radii;
+    unsigned long long *work;     // next query
+    unsigned long long *cursor;   // staging fill
+    unsigned long long *staged;
+    uint64_t cap;
+    uint32_t idbits;
+    uint32_t *res_cnt;
+    unsigned long long *coll, *cand;
+    uint32_t *bitmaps;            // [gridDim.x][bm_words]
+    uint64_t bm_words;
+};
+
+}  // namespace fclsh
+
+// The index (opaque to users).
+struct fclsh_index {
+    int device = 0;
+    uint64_t n = 0;
+    uint32_t d = 0, words = 0, r = 0, t = 0, rp = 0, W = 0, T = 0, slot_bits = 0;
+    uint64_t P = fclsh::kP;
+    // host copy of the random choices
+    std::vector<uint32_t> perm, part_off, m;
+    std::vector<uint64_t> b;
+    // device arrays
+    uint64_t *points = nullptr;      // [n][words]
+    uint32_t *col_off = nullptr;     // [t][W+1]
+    uint32_t *col_coord = nullptr;   // [d]
+    uint64_t *col_b = nullptr;       // [d]
+    uint32_t *offs = nullptr;        // [T][2^slot_bits + 1]
+    uint64_t *ent = nullptr;         // [T][n]: (key >> slot_bits) << 32 | id
+    uint64_t device_bytes = 0;
+    fclsh_tuning tune{};
+    // timing (CUDA events per phase)
+    bool timing = false;
+    double ms[8] = {0};
+    uint64_t cnt[8] = {0};
+    int sm_count = 0;
+    size_t smem_optin = 0;
+
+    uint64_t slots() const { return 1ULL << slot_bits; }
+    uint64_t offs_stride() const { return slots() + 1; }
+    fclsh::PartCols part(uint32_t k) const
+    {
+        return fclsh::PartCols{col_off + (size_t)k * (W + 1), col_coord, col_b};
+    }
+};
+
+namespace fclsh {
+
+// ---- error reporting and launch accounting (api.cu)
+void set_error(const char *fmt, ...);
+void note_launch(uint64_t kernels = 1);   // kernels enqueued by this library
+uint64_t launch_count();
+int64_t launch_count_adjust(int64_t delta);
+fclsh_status cuda_fail(cudaError_t e, const char *what);
+
+#define FCLSH_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return fclsh::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---- params.cpp
+uint32_t default_parts(uint32_t r);
+int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t W, std::vector<uint32_t> &perm,
+                  std::vector<uint32_t> &part_off, std::vector<uint32_t> &m, std::vector<uint64_t> &b);
+void column_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
+                  const std::vector<uint32_t> &part_off, const std::vector<uint32_t> &m,
+                  const std::vector<uint64_t> &b, std::vector<uint32_t> &col_off,
+                  std::vector<uint32_t> &coord, std::vector<uint64_t> &bval);
+
+// ---- hash.cu: keys of `cnt` points for part k into keys[(v-1)*ld + i], v = 1..W-1
+cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t *pts, uint64_t cnt,
+                             uint64_t *keys, uint64_t ld, cudaStream_t s);
+
+// ---- sort.cu
+// Sort `rows` segments of `len` (u64 key, u32 id) pairs by key bits [0, bits) (stable,
+// LSD, 8-bit digits).  ids_in == nullptr means id = position in the row.  The result
+// is in (keys_a, ids_a) or (keys_b, ids_b); *out_in_b tells which.
+struct SortBuffers {
+    uint64_t *keys_a, *keys_b;
+    uint32_t *ids_a, *ids_b;
+    uint32_t *hist;          // [rows * 256 * tiles]
+    uint32_t *partials;      // scan scratch
+    size_t hist_cap, partials_cap;
+};
+size_t sort_hist_entries(uint32_t rows, uint64_t len);
+size_t scan_partials_entries(size_t count);
+cudaError_t radix_sort_rows(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t bits,
+                            SortBuffers &buf, bool *out_in_b, cudaStream_t s);
+// Single segment of u64 keys whose length is *d_count (device), capacity cap.
+cudaError_t radix_sort_keys_dev(uint64_t *keys_a, uint64_t *keys_b, const unsigned long long *d_count,
+                                uint64_t cap, uint32_t bits, uint32_t *hist, uint32_t *partials,
+                                bool *out_in_b, cudaStream_t s);
+size_t sort_keys_hist_entries(uint64_t cap);
+// Directory of each sorted row: ent = (key >> sb) << 32 | id, offs[slot] = first entry of slot.
+cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint32_t rows, uint64_t len,
+                                 uint32_t slot_bits, uint64_t *ent, uint32_t *offs, cudaStream_t s);
+// Exclusive scan of u32 values into u64 offsets: out[i] = sum_{j<i} in[j], out[count] = total.
+cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, uint64_t *partials,
+                            cudaStream_t s);
+
+}  // namespace fclsh

@@ -1,0 +1,302 @@
+// hash.cu -- Algorithm 2 on the GPU: all W-1 keys of every point of one part.
+//
+// For a point q and part k (Sec. 3.2, "Fast computation of hash functions"):
+//   sketch   t_j = sum_{i in part k, m(i) = j} b_i q_i  (mod P)
+//   transform y = H t (Walsh-Hadamard, Sylvester order)
+//   finish   h_v = ((S - y_v) / 2) mod P, S = y_0 = sum_j t_j, v = 1..W-1
+// which by Lemma 3 equals p(g_v AND q) of Eq. (1).  Reducing t_j mod P first
+// changes no key and keeps |y| <= W P < 2^61, so 64-bit integers are exact.
+//
+// Kernel shapes:
+//   W <= 32   one thread per point; the whole transform in registers.
+//   W >= 64   a tile of NP points in shared memory laid out [j][p] (p fastest),
+//             W/32 threads per point, 32 values per thread.  The log2(W) butterfly
+//             levels are split into 2 or 3 register phases (each at most 5 levels);
+//             between phases the values pass through shared memory once.  The first
+//             phase gathers the sketch straight into registers (no scatter), the last
+//             phase applies the finish and stores keys table-major, coalesced over
+//             the NP consecutive points.
+#include "common.cuh"
+
+namespace fclsh {
+
+namespace {
+
+// In-register Walsh-Hadamard transform of K values (unnormalised, natural order).
+template <int K>
+__device__ __forceinline__ void wht_regs(uint64_t *v)
+{
+#pragma unroll
+    for (int h = 1; h < K; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < K; i += 2 * h)
+#pragma unroll
+            for (int j = i; j < i + h; ++j) {
+                uint64_t a = v[j], c = v[j + h];
+                v[j] = a + c;
+                v[j + h] = a - c;
+            }
+}
+
+// Column data of one part staged in shared memory: offsets relative to the part.
+struct ColsSmem {
+    const uint32_t *off;     // [W+1]
+    const uint32_t *coord;   // [dk]
+    const uint64_t *bval;    // [dk]
+};
+
+// t_j for one point whose words are at x (global, read through L1).
+__device__ __forceinline__ uint64_t sketch_column(const ColsSmem &c, uint32_t j, const uint64_t *__restrict__ x)
+{
+    uint64_t s = 0;
+    const uint32_t e1 = c.off[j + 1];
+    for (uint32_t e = c.off[j]; e < e1; ++e) {
+        const uint32_t bit = c.coord[e];
+        const uint64_t w = __ldg(x + (bit >> 6));
+        const uint64_t take = 0ULL - ((w >> (bit & 63)) & 1ULL);
+        s = add_mod_p(s, c.bval[e] & take);
+    }
+    return s;
+}
+
+// Stage the part's column lists into shared memory (all threads, then a barrier by the caller).
+__device__ __forceinline__ ColsSmem stage_cols(const PartCols &pc, uint32_t W, void *smem_base)
+{
+    const uint32_t base = pc.col_off[0];
+    const uint32_t dk = pc.col_off[W] - base;
+    uint64_t *bv = reinterpret_cast<uint64_t *>(smem_base);
+    uint32_t *off = reinterpret_cast<uint32_t *>(bv + dk);
+    uint32_t *coord = off + (W + 1);
+    for (uint32_t i = threadIdx.x; i <= W; i += blockDim.x) off[i] = pc.col_off[i] - base;
+    for (uint32_t i = threadIdx.x; i < dk; i += blockDim.x) {
+        coord[i] = pc.coord[base + i];
+        bv[i] = pc.bval[base + i];
+    }
+    return ColsSmem{off, coord, bv};
+}
+
+__host__ __device__ constexpr size_t cols_smem_bytes(uint32_t W, uint32_t dk)
+{
+    return (size_t)dk * 8 + ((size_t)W + 1 + dk) * 4 + 8;
+}
+
+// ------------------------------------------------------------------ W <= 32
+
+template <int LOGW>
+__global__ void __launch_bounds__(128) hash_small_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
+                                                         uint32_t words, PartCols pc, uint64_t *__restrict__ keys,
+                                                         uint64_t ld)
+{
+    constexpr int W = 1 << LOGW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ColsSmem cols = stage_cols(pc, W, smem_raw);
+    __syncthreads();
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const uint64_t *x = pts + i * words;
+    uint64_t v[W];
+    uint64_t S = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        v[j] = sketch_column(cols, j, x);
+        S += v[j];
+    }
+    wht_regs<W>(v);
+#pragma unroll
+    for (int j = 1; j < W; ++j) keys[(uint64_t)(j - 1) * ld + i] = finish_key(S, v[j]);
+}
+
+// ------------------------------------------------------------------ W >= 64
+
+template <int LOGW> struct TileCfg;
+//                      points/tile  phases: butterfly levels per register phase   smem swizzle mask
+template <> struct TileCfg<6>  { static constexpr int NP = 128, NPH = 2, B0 = 3, B1 = 3, B2 = 0; static constexpr uint32_t M = 0; };
+template <> struct TileCfg<7>  { static constexpr int NP = 64,  NPH = 2, B0 = 3, B1 = 4, B2 = 0; static constexpr uint32_t M = 0; };
+template <> struct TileCfg<8>  { static constexpr int NP = 32,  NPH = 2, B0 = 4, B1 = 4, B2 = 0; static constexpr uint32_t M = 0; };
+template <> struct TileCfg<9>  { static constexpr int NP = 16,  NPH = 2, B0 = 4, B1 = 5, B2 = 0; static constexpr uint32_t M = 0; };
+template <> struct TileCfg<10> { static constexpr int NP = 8,   NPH = 2, B0 = 5, B1 = 5, B2 = 0; static constexpr uint32_t M = 0x20; };
+template <> struct TileCfg<11> { static constexpr int NP = 8,   NPH = 3, B0 = 5, B1 = 3, B2 = 3; static constexpr uint32_t M = 0x24; };
+
+template <int LOGW>
+struct Tile {
+    using C = TileCfg<LOGW>;
+    static constexpr int W = 1 << LOGW;
+    static constexpr int NP = C::NP;
+    static constexpr int NT = NP * W / 32;            // threads per block
+    static constexpr size_t VALUES_BYTES = (size_t)W * NP * 8;
+};
+
+// Shared-memory slot of value j of point p.  With NP = 8 a half-warp touches two
+// rows; flipping bit 0 of the row by the parity of (j & M) puts those two rows in
+// opposite halves of the 32 banks in every phase (a bijection: it swaps row pairs).
+template <int NP, uint32_t M>
+__device__ __forceinline__ uint32_t slot(uint32_t j, uint32_t p)
+{
+    uint32_t a = j * NP + p;
+    if (M) a ^= (uint32_t)(__popc(j & M) & 1) * NP;
+    return a;
+}
+
+// j of the k-th value along butterfly levels [LO, LO+B) in the group `other`
+// (the index over the remaining LOGW-B bits of j).
+template <int LO, int B>
+__device__ __forceinline__ uint32_t jidx(uint32_t other, uint32_t k)
+{
+    return ((other >> LO) << (LO + B)) | (k << LO) | (other & ((1u << LO) - 1u));
+}
+
+// MODE 0: gather the sketch, transform, write to smem.  1: smem -> transform -> smem.
+// 2: smem -> transform -> finish -> global keys.
+template <int LOGW, int LO, int B, int MODE>
+__device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsigned long long *S_acc, uint32_t p,
+                                      uint32_t tp, const ColsSmem &cols, const uint64_t *__restrict__ x, bool valid,
+                                      uint64_t *__restrict__ keys, uint64_t ld, uint64_t gp)
+{
+    using T = Tile<LOGW>;
+    constexpr int K = 1 << B, G = 32 / K;
+    uint64_t v[32];
+    uint64_t part = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const uint32_t other = tp * G + g;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint32_t j = jidx<LO, B>(other, k);
+            if (MODE == 0) {
+                const uint64_t tj = valid ? sketch_column(cols, j, x) : 0;
+                v[g * K + k] = tj;
+                part += tj;
+            } else {
+                v[g * K + k] = sm[slot<T::NP, T::C::M>(j, p)];
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) wht_regs<K>(v + g * K);
+    if (MODE == 0) atomicAdd(S_acc + p, (unsigned long long)part);
+    if (MODE == 2) {
+        const uint64_t S = S_sm[p];
+        if (valid) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const uint32_t other = tp * G + g;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const uint32_t j = jidx<LO, B>(other, k);
+                    if (j != 0) keys[(uint64_t)(j - 1) * ld + gp] = finish_key(S, v[g * K + k]);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t other = tp * G + g;
+#pragma unroll
+            for (int k = 0; k < K; ++k) sm[slot<T::NP, T::C::M>(jidx<LO, B>(other, k), p)] = v[g * K + k];
+        }
+    }
+}
+
+template <int LOGW>
+__global__ void __launch_bounds__(Tile<LOGW>::NT) hash_tile_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
+                                                                    uint32_t words, PartCols pc,
+                                                                    uint64_t *__restrict__ keys, uint64_t ld)
+{
+    using T = Tile<LOGW>;
+    using C = typename T::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
+    unsigned long long *S_acc = reinterpret_cast<unsigned long long *>(sm + (size_t)T::W * T::NP);
+    const ColsSmem cols = stage_cols(pc, T::W, S_acc + T::NP);
+    const uint32_t p = threadIdx.x % T::NP, tp = threadIdx.x / T::NP;
+    const uint64_t gp = blockIdx.x * (uint64_t)T::NP + p;
+    const bool valid = gp < cnt;
+    const uint64_t *x = pts + (valid ? gp : 0) * words;
+    if (threadIdx.x < T::NP) S_acc[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t *S_sm = reinterpret_cast<const uint64_t *>(S_acc);
+    phase<LOGW, 0, C::B0, 0>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+    __syncthreads();
+    if constexpr (C::NPH == 2) {
+        phase<LOGW, C::B0, C::B1, 2>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+    } else {
+        phase<LOGW, C::B0, C::B1, 1>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+        __syncthreads();
+        phase<LOGW, C::B0 + C::B1, C::B2, 2>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+    }
+}
+
+template <int LOGW>
+cudaError_t launch_logw(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, uint64_t *keys,
+                        uint64_t ld, cudaStream_t s)
+{
+    constexpr int W = 1 << LOGW;
+    const size_t cbytes = cols_smem_bytes(W, dk);
+    if constexpr (LOGW <= 5) {
+        const int threads = 128;
+        const size_t smem = cbytes;
+        auto kern = hash_small_kernel<LOGW>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        const uint64_t blocks = (cnt + threads - 1) / threads;
+        kern<<<(unsigned)blocks, threads, smem, s>>>(pts, cnt, words, pc, keys, ld);
+        note_launch();
+    } else {
+        using T = Tile<LOGW>;
+        const size_t smem = T::VALUES_BYTES + T::NP * 8 + cbytes;
+        auto kern = hash_tile_kernel<LOGW>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        const uint64_t blocks = (cnt + T::NP - 1) / T::NP;
+        kern<<<(unsigned)blocks, T::NT, smem, s>>>(pts, cnt, words, pc, keys, ld);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Shared memory one hash block needs for code length W and a part of dk coordinates.
+size_t hash_smem_bytes(uint32_t W, uint32_t dk)
+{
+    size_t tile = 0;
+    switch (W) {
+    case 64: tile = Tile<6>::VALUES_BYTES + Tile<6>::NP * 8; break;
+    case 128: tile = Tile<7>::VALUES_BYTES + Tile<7>::NP * 8; break;
+    case 256: tile = Tile<8>::VALUES_BYTES + Tile<8>::NP * 8; break;
+    case 512: tile = Tile<9>::VALUES_BYTES + Tile<9>::NP * 8; break;
+    case 1024: tile = Tile<10>::VALUES_BYTES + Tile<10>::NP * 8; break;
+    case 2048: tile = Tile<11>::VALUES_BYTES + Tile<11>::NP * 8; break;
+    default: break;
+    }
+    return tile + cols_smem_bytes(W, dk);
+}
+
+cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t *pts, uint64_t cnt, uint64_t *keys,
+                             uint64_t ld, cudaStream_t s)
+{
+    if (cnt == 0) return cudaSuccess;
+    const uint32_t dk = idx->part_off[k + 1] - idx->part_off[k];
+    const PartCols pc = idx->part(k);
+    const uint32_t logw = idx->rp + 1;
+    switch (logw) {
+    case 1: return launch_logw<1>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 2: return launch_logw<2>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 3: return launch_logw<3>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 4: return launch_logw<4>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 5: return launch_logw<5>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 6: return launch_logw<6>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 7: return launch_logw<7>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 8: return launch_logw<8>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 9: return launch_logw<9>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 10: return launch_logw<10>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 11: return launch_logw<11>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fclsh

@@ -1,0 +1,437 @@
+// query.cu -- Strategy 2 queries (Sec. 2.2) in the cost steps of Sec. 4.1:
+//   S1  hash the query into its T keys (Algorithm 2, in the CTA's shared memory),
+//   S2  look up the query's bucket in every table and merge the buckets with
+//       duplicate elimination (#Collisions, #Candidates),
+//   S3  compute the Hamming distance of each distinct candidate by popcount and
+//       report it if it is within the query's radius.
+//
+// Batched form: one persistent kernel; each CTA takes the next query from a
+// global work counter, so queries with very different candidate counts balance
+// across the GPU.  Inside a CTA, warps take 32 tables at a time: a lane walks its
+// own bucket range when it is short, and the whole warp walks a long one, so a
+// heavy bucket never serialises on one lane.  Duplicates are removed with a
+// shared-memory hash set when the query's bucket ranges hold at most half its
+// capacity, and otherwise with an n-bit bitmap owned by the CTA (the bitmap of
+// Sec. 4.1), cleared after the query.  Hits go to a global staging buffer as
+// (query << idbits | id); a radix sort then yields every query's ids ascending.
+#include "common.cuh"
+
+namespace fclsh {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+namespace {
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    return (1u << (threadIdx.x & 31)) - 1u;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red)   // red: >= 32 entries of smem
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T s = 0;
+    const uint32_t nw = blockDim.x >> 5;
+    for (uint32_t w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+
+// Hamming distance between the query in shared memory and point `id`.
+__device__ __forceinline__ uint32_t distance_to(const QueryArgs &a, const uint64_t *q_s, uint32_t id)
+{
+    const uint64_t *x = a.points + (uint64_t)id * a.words;
+    uint32_t dist = 0;
+    if ((a.words & 1) == 0) {
+        const ulonglong2 *x2 = reinterpret_cast<const ulonglong2 *>(x);
+        for (uint32_t w = 0; w < a.words / 2; ++w) {
+            const ulonglong2 v = __ldg(x2 + w);
+            dist += __popcll(v.x ^ q_s[2 * w]) + __popcll(v.y ^ q_s[2 * w + 1]);
+        }
+    } else {
+        for (uint32_t w = 0; w < a.words; ++w) dist += __popcll(__ldg(x + w) ^ q_s[w]);
+    }
+    return dist;
+}
+
+__device__ __forceinline__ bool hset_insert(uint32_t *hset, uint32_t hlog, uint32_t id)
+{
+    const uint32_t mask = (1u << hlog) - 1u;
+    uint32_t s = (id * 0x9E3779B1u) >> (32 - hlog);
+    for (;;) {
+        const uint32_t old = atomicCAS(hset + s, kEmpty, id);
+        if (old == kEmpty) return true;
+        if (old == id) return false;
+        s = (s + 1) & mask;
+    }
+}
+
+struct Counters {
+    unsigned long long coll = 0, cand = 0;
+    uint32_t res = 0;
+};
+
+// One bucket entry per lane (is_coll = key matched); warp-collective.
+__device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
+                                              bool bitmap_mode, uint32_t radius, uint64_t qi, bool is_coll,
+                                              uint32_t id, Counters &c)
+{
+    bool isnew = false;
+    if (is_coll) {
+        c.coll++;
+        if (bitmap_mode) {
+            const uint32_t bit = 1u << (id & 31);
+            isnew = (atomicOr(bm + (id >> 5), bit) & bit) == 0;
+        } else {
+            isnew = hset_insert(hset, a.hset_log2, id);
+        }
+    }
+    bool hit = false;
+    if (isnew) {
+        c.cand++;
+        hit = distance_to(a, q_s, id) <= radius;
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, hit);
+    if (m) {
+        const uint32_t lane = threadIdx.x & 31;
+        const uint32_t leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(a.cursor, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (hit) {
+            c.res++;
+            const unsigned long long pos = base + __popc(m & lanemask_lt());
+            if (pos < a.cap) a.staged[pos] = (qi << a.idbits) | id;
+        }
+    }
+}
+
+}  // namespace
+
+// Dynamic shared memory of the batched kernel.
+size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_log2)
+{
+    const size_t tb = (size_t)W * 8 > ((size_t)4 << hset_log2) ? (size_t)W * 8 : ((size_t)4 << hset_log2);
+    return (size_t)T * 8 + (size_t)T * 8 + tb + (size_t)words * 8 + 64;
+}
+
+__global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *keys_s = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *lo_s = reinterpret_cast<uint32_t *>(keys_s + a.T);
+    uint32_t *len_s = lo_s + a.T;
+    uint64_t *tbuf = reinterpret_cast<uint64_t *>(len_s + a.T);   // 8T bytes after keys_s: 8-aligned
+    uint32_t *hset = reinterpret_cast<uint32_t *>(tbuf);
+    const size_t tb_words = ((size_t)a.W > ((size_t)1 << a.hset_log2) / 2) ? a.W : ((size_t)1 << a.hset_log2) / 2;
+    uint64_t *q_s = tbuf + tb_words;
+    __shared__ unsigned long long s_qi;
+    __shared__ unsigned long long red64[32];
+
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
+    const uint32_t L = a.W - 1;
+    const uint64_t smask = (1ULL << a.slot_bits) - 1;
+    uint32_t *bm = a.bitmaps + (uint64_t)blockIdx.x * a.bm_words;
+    const uint32_t hcap = 1u << a.hset_log2;
+
+    for (;;) {
+        if (tid == 0) s_qi = atomicAdd(a.work, 1ULL);
+        __syncthreads();
+        const uint64_t qi = s_qi;
+        if (qi >= a.nq) break;
+        for (uint32_t w = tid; w < a.words; w += B) q_s[w] = a.queries[qi * a.words + w];
+        const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
+        __syncthreads();
+
+        // ---- S1: Algorithm 2 for every part, in shared memory
+        for (uint32_t k = 0; k < a.t; ++k) {
+            const uint32_t *co = a.col_off + (size_t)k * (a.W + 1);
+            for (uint32_t j = tid; j < a.W; j += B) {
+                uint64_t s = 0;
+                const uint32_t e1 = co[j + 1];
+                for (uint32_t e = co[j]; e < e1; ++e) {
+                    const uint32_t bit = a.col_coord[e];
+                    const uint64_t take = 0ULL - ((q_s[bit >> 6] >> (bit & 63)) & 1ULL);
+                    s = add_mod_p(s, a.col_b[e] & take);
+                }
+                tbuf[j] = s;
+            }
+            __syncthreads();
+            for (uint32_t h = 1; h < a.W; h <<= 1) {
+                for (uint32_t i = tid; i < a.W / 2; i += B) {
+                    const uint32_t j = ((i & ~(h - 1)) << 1) | (i & (h - 1));
+                    const uint64_t x = tbuf[j], y = tbuf[j + h];
+                    tbuf[j] = x + y;
+                    tbuf[j + h] = x - y;
+                }
+                __syncthreads();
+            }
+            const uint64_t S = tbuf[0];   // y_0 = sum_j t_j
+            for (uint32_t v = tid + 1; v < a.W; v += B) keys_s[k * L + v - 1] = finish_key(S, tbuf[v]);
+            __syncthreads();
+        }
+
+        // ---- S2a: bucket ranges of every table
+        unsigned long long local = 0;
+        for (uint32_t tau = tid; tau < a.T; tau += B) {
+            const uint64_t key = keys_s[tau];
+            const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
+            const uint32_t lo = O[0], hi = O[1];
+            lo_s[tau] = lo;
+            len_s[tau] = hi - lo;
+            local += hi - lo;
+        }
+        const unsigned long long E = block_sum(local, red64);
+        const bool bitmap_mode = E > (hcap >> 1);
+        if (!bitmap_mode)
+            for (uint32_t i = tid; i < hcap; i += B) hset[i] = kEmpty;
+        __syncthreads();
+
+        // ---- S2b + S3: collisions -> dedup -> verify, 32 tables per warp step
+        Counters c;
+        for (uint32_t base = warp * 32; base < a.T; base += nwarps * 32) {
+            const uint32_t tau = base + lane;
+            const bool has = tau < a.T;
+            const uint32_t lo = has ? lo_s[tau] : 0, len = has ? len_s[tau] : 0;
+            const uint32_t fp = has ? (uint32_t)(keys_s[tau] >> a.slot_bits) : 0;
+            const uint64_t *row = a.ent + (uint64_t)(has ? tau : 0) * a.n;
+            const uint32_t short_len = len <= a.inline_len ? len : 0;
+            const uint32_t maxs = __reduce_max_sync(0xffffffffu, short_len);
+            for (uint32_t e = 0; e < maxs; ++e) {
+                const bool act = e < short_len;
+                const uint64_t en = act ? __ldg(row + lo + e) : 0;
+                process_entry(a, q_s, hset, bm, bitmap_mode, radius, qi, act && (uint32_t)(en >> 32) == fp,
+                              (uint32_t)en, c);
+            }
+            uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
+            while (lmask) {
+                const uint32_t src = __ffs(lmask) - 1;
+                lmask &= lmask - 1;
+                const uint32_t l_lo = __shfl_sync(0xffffffffu, lo, src);
+                const uint32_t l_len = __shfl_sync(0xffffffffu, len, src);
+                const uint32_t l_fp = __shfl_sync(0xffffffffu, fp, src);
+                const uint32_t l_tau = __shfl_sync(0xffffffffu, tau, src);
+                const uint64_t *lrow = a.ent + (uint64_t)l_tau * a.n + l_lo;
+                for (uint32_t cbase = 0; cbase < l_len; cbase += 32) {
+                    const uint32_t e = cbase + lane;
+                    const bool act = e < l_len;
+                    const uint64_t en = act ? __ldg(lrow + e) : 0;
+                    process_entry(a, q_s, hset, bm, bitmap_mode, radius, qi, act && (uint32_t)(en >> 32) == l_fp,
+                                  (uint32_t)en, c);
+                }
+            }
+        }
+        const unsigned long long tc = block_sum(c.coll, red64);
+        const unsigned long long td = block_sum(c.cand, red64);
+        const unsigned long long tr = block_sum((unsigned long long)c.res, red64);
+        if (tid == 0) {
+            a.coll[qi] = tc;
+            a.cand[qi] = td;
+            a.res_cnt[qi] = (uint32_t)tr;
+        }
+        if (bitmap_mode) {   // leave the CTA's bitmap all-zero for its next query
+            for (uint32_t tau = tid; tau < a.T; tau += B) {
+                const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[tau];
+                const uint32_t len = len_s[tau];
+                for (uint32_t e = 0; e < len; ++e) bm[(uint32_t)__ldg(row + e) >> 5] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- plain path
+
+// One query: every table in its own thread, duplicates removed by a global n-bit bitmap.
+__global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uint64_t *keys, uint32_t *bitmap)
+{
+    __shared__ uint64_t q_s[256];
+    for (uint32_t w = threadIdx.x; w < a.words; w += blockDim.x) q_s[w] = a.queries[w];
+    __syncthreads();
+    const uint32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tau >= a.T) return;
+    const uint64_t smask = (1ULL << a.slot_bits) - 1;
+    const uint64_t key = keys[tau];
+    const uint32_t fp = (uint32_t)(key >> a.slot_bits);
+    const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
+    const uint32_t lo = O[0], hi = O[1];
+    const uint64_t *row = a.ent + (uint64_t)tau * a.n;
+    unsigned long long coll = 0, cand = 0;
+    for (uint32_t e = lo; e < hi; ++e) {
+        const uint64_t en = row[e];
+        if ((uint32_t)(en >> 32) != fp) continue;
+        const uint32_t id = (uint32_t)en;
+        coll++;
+        const uint32_t bit = 1u << (id & 31);
+        if (atomicOr(bitmap + (id >> 5), bit) & bit) continue;
+        cand++;
+        if (distance_to(a, q_s, id) <= a.radius) {
+            const unsigned long long pos = atomicAdd(a.cursor, 1ULL);
+            if (pos < a.cap) a.staged[pos] = id;
+        }
+    }
+    if (coll) atomicAdd(a.coll, coll);
+    if (cand) atomicAdd(a.cand, cand);
+}
+
+// Sort up to 2048 ids of one query in one CTA (bitonic), in place.
+__global__ void __launch_bounds__(1024) sort_small_kernel(unsigned long long *v, const unsigned long long *d_count)
+{
+    __shared__ unsigned long long s[2048];
+    const uint32_t cnt = (uint32_t)*d_count;
+    for (uint32_t i = threadIdx.x; i < 2048; i += blockDim.x) s[i] = i < cnt ? v[i] : ~0ULL;
+    __syncthreads();
+    for (uint32_t size = 2; size <= 2048; size <<= 1)
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) {
+                const uint32_t lo = 2 * i - (i & (stride - 1));
+                const uint32_t hi = lo + stride;
+                const bool up = ((lo & size) == 0);
+                const unsigned long long x = s[lo], y = s[hi];
+                if ((x > y) == up) {
+                    s[lo] = y;
+                    s[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) v[i] = s[i];
+}
+
+// ---------------------------------------------------------------- brute force
+
+constexpr int kBfQ = 128;   // queries per CTA tile
+
+// Linear scan: every (query, point) pair within radius, XOR + popcount.
+__global__ void __launch_bounds__(256) bruteforce_kernel(const uint64_t *__restrict__ points, uint64_t n,
+                                                         uint32_t words, const uint64_t *__restrict__ queries,
+                                                         uint64_t nq, uint32_t radius, unsigned long long *cursor,
+                                                         unsigned long long *staged, uint64_t cap, uint32_t idbits,
+                                                         uint32_t *res_cnt, uint64_t points_per_cta)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *qs = reinterpret_cast<uint64_t *>(smem_raw);   // [kBfQ][words]
+    const uint64_t q0 = (uint64_t)blockIdx.y * kBfQ;
+    const uint32_t qn = (uint32_t)((nq - q0) < kBfQ ? (nq - q0) : kBfQ);
+    for (uint32_t i = threadIdx.x; i < qn * words; i += blockDim.x) qs[i] = queries[q0 * words + i];
+    __syncthreads();
+    const uint64_t p0 = (uint64_t)blockIdx.x * points_per_cta;
+    const uint64_t p1 = (p0 + points_per_cta < n) ? p0 + points_per_cta : n;
+    for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint64_t *x = points + p * words;
+        if (words <= 4) {
+            uint64_t xv[4] = {0, 0, 0, 0};
+            for (uint32_t w = 0; w < words; ++w) xv[w] = __ldg(x + w);
+            for (uint32_t q = 0; q < qn; ++q) {
+                const uint64_t *qq = qs + q * words;
+                uint32_t dist = 0;
+#pragma unroll
+                for (uint32_t w = 0; w < 4; ++w)
+                    if (w < words) dist += __popcll(xv[w] ^ qq[w]);
+                if (dist <= radius) {
+                    const unsigned long long pos = atomicAdd(cursor, 1ULL);
+                    if (pos < cap) staged[pos] = ((q0 + q) << idbits) | p;
+                    atomicAdd(res_cnt + q0 + q, 1u);
+                }
+            }
+        } else {
+            for (uint32_t q = 0; q < qn; ++q) {
+                const uint64_t *qq = qs + q * words;
+                uint32_t dist = 0;
+                for (uint32_t w = 0; w < words && dist <= radius; ++w) dist += __popcll(__ldg(x + w) ^ qq[w]);
+                if (dist <= radius) {
+                    const unsigned long long pos = atomicAdd(cursor, 1ULL);
+                    if (pos < cap) staged[pos] = ((q0 + q) << idbits) | p;
+                    atomicAdd(res_cnt + q0 + q, 1u);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- CSR
+
+__global__ void extract_ids_kernel(const unsigned long long *sorted, const unsigned long long *d_count, uint64_t cap,
+                                   uint64_t idmask, uint32_t *ids)
+{
+    unsigned long long cnt = *d_count;
+    if (cnt > cap) cnt = cap;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x)
+        ids[i] = (uint32_t)(sorted[i] & idmask);
+}
+
+// ---------------------------------------------------------------- launchers
+
+// The shared-memory limit is raised by query_batch_occupancy() before any launch
+// (outside stream capture).
+cudaError_t launch_query_batch(const QueryArgs &a, uint32_t grid, uint32_t block, size_t smem, cudaStream_t s)
+{
+    query_batch_kernel<<<grid, block, smem, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t query_batch_occupancy(uint32_t block, size_t smem, int *ctas_per_sm)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(query_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, query_batch_kernel, (int)block, smem);
+}
+
+cudaError_t launch_query_plain(const QueryArgs &a, const uint64_t *keys, uint32_t *bitmap, cudaStream_t s)
+{
+    const uint32_t blocks = (a.T + 255) / 256;
+    query_plain_kernel<<<blocks, 256, 0, s>>>(a, keys, bitmap);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_small(unsigned long long *v, const unsigned long long *d_count, cudaStream_t s)
+{
+    sort_small_kernel<<<1, 1024, 0, s>>>(v, d_count);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bruteforce(const uint64_t *points, uint64_t n, uint32_t words, const uint64_t *queries, uint64_t nq,
+                              uint32_t radius, unsigned long long *cursor, unsigned long long *staged, uint64_t cap,
+                              uint32_t idbits, uint32_t *res_cnt, int sm_count, cudaStream_t s)
+{
+    if (nq == 0 || n == 0) return cudaSuccess;
+    const uint64_t qtiles = (nq + kBfQ - 1) / kBfQ;
+    // enough point tiles that the grid covers the GPU several times
+    uint64_t ptiles = ((uint64_t)sm_count * 8 + qtiles - 1) / qtiles;
+    if (ptiles < 1) ptiles = 1;
+    uint64_t ppc = (n + ptiles - 1) / ptiles;
+    ppc = ((ppc + 255) / 256) * 256;
+    ptiles = (n + ppc - 1) / ppc;
+    const size_t smem = (size_t)kBfQ * words * 8;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(bruteforce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)ptiles, (unsigned)qtiles);
+    bruteforce_kernel<<<grid, 256, smem, s>>>(points, n, words, queries, nq, radius, cursor, staged, cap, idbits,
+                                               res_cnt, ppc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned long long *d_count, uint64_t cap,
+                               uint64_t idmask, uint32_t *ids, int sm_count, cudaStream_t s)
+{
+    extract_ids_kernel<<<(unsigned)(sm_count * 4), 256, 0, s>>>(sorted, d_count, cap, idmask, ids);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace fclsh

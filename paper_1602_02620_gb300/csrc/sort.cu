@@ -1,0 +1,326 @@
+// sort.cu -- the bucket build (Sec. 2.2: only non-empty buckets are kept, one
+// table per hash function) and the device-wide scans.
+//
+// Each table's (key, id) pairs are sorted by the key's low `slot_bits` bits with a
+// stable LSD radix sort (8-bit digits).  The input order is by id, so ids stay
+// ascending inside every directory slot.  A finalize pass then writes the
+// directory: entries (key >> slot_bits) << 32 | id and, for every slot, the index
+// of its first entry.  A query reads slot (key mod 2^slot_bits), compares the
+// stored high key bits and takes the ids of equal keys: its bucket.
+//
+// Radix pass = per-tile digit histogram -> one exclusive scan over
+// (row, digit, tile) -> stable scatter.  Scanning in (row, digit, tile) order
+// gives each tile's digit run its final position, rows included, in one scan.
+// Stable ranks inside a tile come from warp match + per-warp digit counts.
+#include "common.cuh"
+
+namespace fclsh {
+
+namespace {
+
+constexpr int kIPT = kSortTile / kSortThreads;   // items per thread per tile (16)
+constexpr int kWarps = kSortThreads / 32;
+
+struct RadixArgs {
+    const uint64_t *keys_in;
+    const uint32_t *ids_in;       // nullptr: id = position in the row
+    uint64_t *keys_out;
+    uint32_t *ids_out;            // nullptr: keys only
+    uint64_t len;                 // items per row (capacity when d_count is set)
+    const unsigned long long *d_count;   // single row whose length is min(*d_count, len)
+    uint32_t tiles;               // tiles per row
+    uint32_t shift;
+    uint32_t dmask;               // digit = (key >> shift) & dmask: the last pass may have fewer than 8 bits
+    uint32_t *hist;               // [rows][256][tiles]
+};
+
+__device__ __forceinline__ uint64_t row_len(const RadixArgs &a)
+{
+    if (a.d_count) {
+        unsigned long long c = *a.d_count;
+        return c < a.len ? c : a.len;
+    }
+    return a.len;
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(RadixArgs a)
+{
+    __shared__ uint32_t cnt[256];
+    const uint32_t row = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
+    cnt[tid] = 0;
+    __syncthreads();
+    const uint64_t len = row_len(a);
+    const uint64_t *K = a.keys_in + (uint64_t)row * a.len;
+    const uint64_t base = (uint64_t)tile * kSortTile;
+#pragma unroll 4
+    for (int i = 0; i < kIPT; ++i) {
+        const uint64_t idx = base + (uint64_t)i * kSortThreads + tid;
+        if (idx < len) atomicAdd(&cnt[(uint32_t)(K[idx] >> a.shift) & a.dmask], 1u);
+    }
+    __syncthreads();
+    a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile] = cnt[tid];
+}
+
+template <bool IDS, bool IMPLICIT>
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(RadixArgs a)
+{
+    __shared__ uint32_t digit_off[256];          // global output offset of this tile's run of each digit
+    __shared__ uint32_t warp_cnt[kWarps][256];
+    __shared__ uint32_t warp_pre[kWarps][256];
+    const uint32_t row = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    const uint64_t len = row_len(a);
+    const uint64_t base = (uint64_t)tile * kSortTile;
+    digit_off[tid] = a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) warp_cnt[w][tid] = 0;
+    __syncthreads();
+    if (base >= len) return;
+    const uint64_t *K = a.keys_in + (uint64_t)row * a.len;
+    const uint32_t *I = IMPLICIT ? nullptr : a.ids_in + (uint64_t)row * a.len;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < kIPT; ++r) {
+        const uint64_t idx = base + (uint64_t)r * kSortThreads + tid;
+        const bool valid = idx < len;
+        uint64_t key = 0;
+        uint32_t id = 0;
+        if (valid) {
+            key = K[idx];
+            if (IDS) id = IMPLICIT ? (uint32_t)idx : I[idx];
+        }
+        const uint32_t digit = valid ? ((uint32_t)(key >> a.shift) & a.dmask) : (256u + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (valid && (peers & lt_mask) == 0) warp_cnt[warp][digit] = __popc(peers);
+        __syncthreads();
+        {   // thread tid owns digit tid: prefix over warps, advance the tile's running offset
+            uint32_t run = digit_off[tid];
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = warp_cnt[w][tid];
+                warp_pre[w][tid] = run;
+                run += c;
+                warp_cnt[w][tid] = 0;
+            }
+            digit_off[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint64_t pos = warp_pre[warp][digit] + rank;
+            a.keys_out[pos] = key;
+            if (IDS) a.ids_out[pos] = id;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- scans
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) >= (unsigned)o) v += u;
+    }
+    return v;
+}
+
+// Exclusive block scan of one value per thread (256 threads); returns the block total in *total.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *total)
+{
+    __shared__ T wsum[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nw = blockDim.x >> 5;
+    T incl = warp_incl_scan(v);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? wsum[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < nw) wsum[lane] = wi - w;
+        if (lane == nw - 1) wsum[31] = wi;
+    }
+    __syncthreads();
+    T res = incl - v + wsum[warp];
+    *total = wsum[31];
+    __syncthreads();
+    return res;
+}
+
+constexpr int kScanChunk = 256 * 16;
+
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(256) scan_reduce_kernel(const Tin *in, uint64_t count, Tacc *partials)
+{
+    const uint64_t base = (uint64_t)blockIdx.x * kScanChunk;
+    Tacc s = 0;
+    for (int i = 0; i < 16; ++i) {
+        const uint64_t idx = base + (uint64_t)i * 256 + threadIdx.x;
+        if (idx < count) s += (Tacc)in[idx];
+    }
+    Tacc total;
+    block_excl_scan<Tacc>(s, &total);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+template <typename Tacc>
+__global__ void __launch_bounds__(256) scan_partials_kernel(Tacc *partials, uint64_t count)
+{
+    Tacc carry = 0;
+    for (uint64_t base = 0; base < count; base += 256) {
+        const uint64_t idx = base + threadIdx.x;
+        Tacc v = idx < count ? partials[idx] : Tacc(0);
+        Tacc total;
+        Tacc ex = block_excl_scan<Tacc>(v, &total);
+        if (idx < count) partials[idx] = ex + carry;
+        carry += total;
+    }
+    if (threadIdx.x == 0) partials[count] = carry;
+}
+
+template <typename Tin, typename Tout, typename Tacc>
+__global__ void __launch_bounds__(256) scan_down_kernel(const Tin *in, Tout *out, uint64_t count, const Tacc *partials,
+                                                        bool write_total)
+{
+    const uint64_t base = (uint64_t)blockIdx.x * kScanChunk;
+    // each thread owns 16 consecutive items
+    Tacc v[16];
+    Tacc s = 0;
+    const uint64_t my = base + (uint64_t)threadIdx.x * 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = (my + i < count) ? (Tacc)in[my + i] : Tacc(0);
+        s += v[i];
+    }
+    Tacc total;
+    Tacc run = block_excl_scan<Tacc>(s, &total) + partials[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (my + i < count) out[my + i] = (Tout)run;
+        run += v[i];
+    }
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[count] = (Tout)partials[gridDim.x];
+}
+
+template <typename Tin, typename Tout, typename Tacc>
+cudaError_t scan_exclusive(const Tin *in, Tout *out, uint64_t count, Tacc *partials, bool write_total, cudaStream_t s)
+{
+    const uint64_t chunks = (count + kScanChunk - 1) / kScanChunk;
+    if (chunks == 0) {
+        if (write_total) return cudaMemsetAsync(out, 0, sizeof(Tout), s);
+        return cudaSuccess;
+    }
+    scan_reduce_kernel<Tin, Tacc><<<(unsigned)chunks, 256, 0, s>>>(in, count, partials);
+    note_launch();
+    scan_partials_kernel<Tacc><<<1, 256, 0, s>>>(partials, chunks);
+    note_launch();
+    scan_down_kernel<Tin, Tout, Tacc><<<(unsigned)chunks, 256, 0, s>>>(in, out, count, partials, write_total);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- directory
+
+__global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restrict__ keys,
+                                                       const uint32_t *__restrict__ ids, uint64_t len,
+                                                       uint32_t sb, uint64_t *__restrict__ ent,
+                                                       uint32_t *__restrict__ offs)
+{
+    const uint32_t row = blockIdx.y;
+    const uint64_t e = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= len) return;
+    const uint64_t nslots = 1ULL << sb;
+    const uint64_t mask = nslots - 1;
+    const uint64_t *Kr = keys + (uint64_t)row * len;
+    uint32_t *O = offs + (uint64_t)row * (nslots + 1);
+    const uint64_t key = Kr[e];
+    const uint64_t sl = key & mask;
+    ent[(uint64_t)row * len + e] = ((key >> sb) << 32) | ids[(uint64_t)row * len + e];
+    const uint64_t first = (e == 0) ? 0 : (Kr[e - 1] & mask) + 1;
+    for (uint64_t s2 = first; s2 <= sl; ++s2) O[s2] = (uint32_t)e;
+    if (e == len - 1)
+        for (uint64_t s2 = sl + 1; s2 <= nslots; ++s2) O[s2] = (uint32_t)len;
+}
+
+}  // namespace
+
+size_t sort_hist_entries(uint32_t rows, uint64_t len)
+{
+    const uint64_t tiles = (len + kSortTile - 1) / kSortTile;
+    return (size_t)rows * 256 * tiles;
+}
+
+size_t sort_keys_hist_entries(uint64_t cap) { return sort_hist_entries(1, cap); }
+
+size_t scan_partials_entries(size_t count) { return (count + kScanChunk - 1) / kScanChunk + 2; }
+
+cudaError_t radix_sort_rows(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t bits, SortBuffers &buf,
+                            bool *out_in_b, cudaStream_t s)
+{
+    const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
+    const uint32_t passes = (bits + 7) / 8;
+    const uint64_t hcount = (uint64_t)rows * 256 * tiles;
+    dim3 grid(tiles, rows);
+    const uint64_t *kin = keys_in;
+    const uint32_t *iin = nullptr;
+    for (uint32_t p = 0; p < passes; ++p) {
+        const bool to_b = (p % 2) == 1;
+        const uint32_t nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
+        RadixArgs a{kin, iin, to_b ? buf.keys_b : buf.keys_a, to_b ? buf.ids_b : buf.ids_a, len, nullptr, tiles,
+                    8 * p, (1u << nb) - 1u, buf.hist};
+        radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a);
+        note_launch();
+        cudaError_t e = scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s);
+        if (e != cudaSuccess) return e;
+        if (p == 0)
+            radix_scatter_kernel<true, true><<<grid, kSortThreads, 0, s>>>(a);
+        else
+            radix_scatter_kernel<true, false><<<grid, kSortThreads, 0, s>>>(a);
+        note_launch();
+        kin = a.keys_out;
+        iin = a.ids_out;
+    }
+    *out_in_b = passes % 2 == 0;
+    return cudaGetLastError();
+}
+
+cudaError_t radix_sort_keys_dev(uint64_t *keys_a, uint64_t *keys_b, const unsigned long long *d_count, uint64_t cap,
+                                uint32_t bits, uint32_t *hist, uint32_t *partials, bool *out_in_b, cudaStream_t s)
+{
+    const uint32_t tiles = (uint32_t)((cap + kSortTile - 1) / kSortTile);
+    const uint32_t passes = (bits + 7) / 8;
+    const uint64_t hcount = (uint64_t)256 * tiles;
+    dim3 grid(tiles, 1);
+    for (uint32_t p = 0; p < passes; ++p) {
+        const bool from_b = (p % 2) == 1;
+        const uint32_t nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
+        RadixArgs a{from_b ? keys_b : keys_a, nullptr, from_b ? keys_a : keys_b, nullptr, cap, d_count, tiles, 8 * p,
+                    (1u << nb) - 1u, hist};
+        radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a);
+        note_launch();
+        cudaError_t e = scan_exclusive<uint32_t, uint32_t, uint32_t>(hist, hist, hcount, partials, false, s);
+        if (e != cudaSuccess) return e;
+        radix_scatter_kernel<false, false><<<grid, kSortThreads, 0, s>>>(a);
+        note_launch();
+    }
+    *out_in_b = passes % 2 == 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint32_t rows, uint64_t len,
+                                 uint32_t slot_bits, uint64_t *ent, uint32_t *offs, cudaStream_t s)
+{
+    dim3 grid((unsigned)((len + 255) / 256), rows);
+    finalize_kernel<<<grid, 256, 0, s>>>(keys, ids, len, slot_bits, ent, offs);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, uint64_t *partials, cudaStream_t s)
+{
+    return scan_exclusive<uint32_t, uint64_t, uint64_t>(in, out, count, partials, true, s);
+}
+
+}  // namespace fclsh

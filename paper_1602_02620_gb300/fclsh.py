@@ -1,0 +1,328 @@
+"""ctypes binding of libfclsh.so (the C ABI in include/fclsh.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Arrays may be numpy arrays (host memory) or torch tensors (host
+or CUDA); their data pointers are passed through unchanged, so device tensors
+stay on the device.  There is no fallback: if the library has not been built,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfclsh.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ERADIUS, ETIMEOUT, EOVERFLOW = range(7)
+_STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERADIUS", 5: "ETIMEOUT", 6: "EOVERFLOW"}
+
+
+class FclshError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_uint32), ("slot_bits", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
+                ("perm", ctypes.c_void_p), ("part_off", ctypes.c_void_p), ("m", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("timing", ctypes.c_uint32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("d", ctypes.c_uint32), ("words", ctypes.c_uint32), ("r", ctypes.c_uint32),
+                ("t", ctypes.c_uint32), ("rp", ctypes.c_uint32), ("W", ctypes.c_uint32), ("T", ctypes.c_uint32),
+                ("slot_bits", ctypes.c_uint32), ("P", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("device", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_uint64), ("offs", ctypes.POINTER(ctypes.c_uint64)), ("ids", ctypes.POINTER(ctypes.c_uint32)),
+                ("collisions", ctypes.POINTER(ctypes.c_uint64)), ("candidates", ctypes.POINTER(ctypes.c_uint64))]
+
+
+class DeviceResult(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_uint64), ("total", ctypes.c_uint64), ("offs", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("collisions", ctypes.c_void_p), ("candidates", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("query_block", ctypes.c_uint32), ("query_ctas_per_sm", ctypes.c_uint32),
+                ("hash_set_log2", ctypes.c_uint32), ("inline_probe", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+#: Every entry point of include/fclsh.h: name -> (restype, argtypes).
+_vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+SIGNATURES = {
+    "fclsh_build": (_i, [_vp, _u64, _u32, _u32, _u64, _vp, _vp]),
+    "fclsh_free": (None, [_vp]),
+    "fclsh_get_info": (_i, [_vp, _vp]),
+    "fclsh_get_params": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fclsh_hash": (_i, [_vp, _vp, _u64, _vp, _vp]),
+    "fclsh_bucket": (_i, [_vp, _u32, _u64, _vp, _u64, _vp]),
+    "fclsh_export_table": (_i, [_vp, _u32, _vp, _vp]),
+    "fclsh_query": (_i, [_vp, _vp, _u64, _u32, _vp, _vp, _vp]),
+    "fclsh_query_plain": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
+    "fclsh_bruteforce": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
+    "fclsh_result_free": (None, [_vp]),
+    "fclsh_qctx_create": (_i, [_vp, _vp]),
+    "fclsh_qctx_free": (None, [_vp]),
+    "fclsh_query_async": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
+    "fclsh_qctx_wait": (_i, [_vp, _vp]),
+    "fclsh_qctx_fetch": (_i, [_vp, _vp]),
+    "fclsh_get_tuning": (_i, [_vp, _vp]),
+    "fclsh_set_tuning": (_i, [_vp, _vp]),
+    "fclsh_autotune": (_i, [_vp, _vp, _u64, _u32, ctypes.c_char_p, _vp]),
+    "fclsh_timing_enable": (_i, [_vp, _i]),
+    "fclsh_timing_read": (_i, [_vp, _vp, _vp, _i]),
+    "fclsh_kernel_launches": (_u64, []),
+    "fclsh_last_error": (ctypes.c_char_p, []),
+    "fclsh_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfclsh.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != OK:
+        raise FclshError(st, lib().fclsh_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Data pointer of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _rows(a) -> int:
+    return a.shape[0] if len(a.shape) > 1 else 1
+
+
+@dataclass
+class QueryResult:
+    offs: np.ndarray        # uint64[nq+1]
+    ids: np.ndarray         # uint32[offs[-1]]
+    collisions: np.ndarray  # uint64[nq]
+    candidates: np.ndarray  # uint64[nq]
+
+    def __len__(self):
+        return len(self.offs) - 1
+
+    def of(self, i: int) -> np.ndarray:
+        return self.ids[int(self.offs[i]):int(self.offs[i + 1])]
+
+
+def _take_result(rp: ctypes.POINTER(Result)) -> QueryResult:
+    r = rp.contents
+    nq = int(r.nq)
+    offs = np.ctypeslib.as_array(r.offs, shape=(nq + 1,)).copy()
+    total = int(offs[-1])
+    ids = np.ctypeslib.as_array(r.ids, shape=(max(total, 1),))[:total].copy()
+    coll = np.ctypeslib.as_array(r.collisions, shape=(max(nq, 1),))[:nq].copy()
+    cand = np.ctypeslib.as_array(r.candidates, shape=(max(nq, 1),))[:nq].copy()
+    lib().fclsh_result_free(rp)
+    return QueryResult(offs, ids, coll, cand)
+
+
+class QueryContext:
+    """Per-stream query scratch (fclsh_qctx)."""
+
+    def __init__(self, index: "Index"):
+        self.index = index
+        h = ctypes.c_void_p()
+        _check(lib().fclsh_qctx_create(index.handle, ctypes.byref(h)))
+        self.handle = h
+
+    def query_async(self, queries, radius: int, radii=None, stream=None):
+        _check(lib().fclsh_query_async(self.handle, _ptr(queries), _rows(queries), radius, _ptr(radii), _stream(stream)))
+
+    def wait(self) -> DeviceResult:
+        dr = DeviceResult()
+        _check(lib().fclsh_qctx_wait(self.handle, ctypes.byref(dr)))
+        return dr
+
+    def fetch(self) -> QueryResult:
+        rp = ctypes.POINTER(Result)()
+        _check(lib().fclsh_qctx_fetch(self.handle, ctypes.byref(rp)))
+        return _take_result(rp)
+
+    def close(self):
+        if self.handle:
+            lib().fclsh_qctx_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Index:
+    """An fcLSH index on the current CUDA device (fclsh_index)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        info = Info()
+        _check(lib().fclsh_get_info(handle, ctypes.byref(info)))
+        self.info = {f: int(getattr(info, f)) for f, _ in Info._fields_}
+        for k, v in self.info.items():
+            setattr(self, k, v)
+
+    # -- parameters / diagnostics
+    def params(self):
+        d, t = self.d, self.t
+        perm = np.zeros(d, np.uint32)
+        part_off = np.zeros(t + 1, np.uint32)
+        m = np.zeros(d, np.uint32)
+        b = np.zeros(d, np.uint64)
+        _check(lib().fclsh_get_params(self.handle, _ptr(perm), _ptr(part_off), _ptr(m), _ptr(b)))
+        return perm, part_off, m, b
+
+    def hash(self, pts, out=None, stream=None):
+        """Keys [T][cnt] of the given points (numpy in -> numpy out unless `out` is given)."""
+        cnt = _rows(pts)
+        if out is None:
+            out = np.zeros((self.T, cnt), np.uint64)
+        _check(lib().fclsh_hash(self.handle, _ptr(pts), cnt, _ptr(out), _stream(stream)))
+        return out
+
+    def bucket(self, table: int, key: int) -> np.ndarray:
+        cnt = ctypes.c_uint64()
+        _check(lib().fclsh_bucket(self.handle, table, key, None, 0, ctypes.byref(cnt)))
+        ids = np.zeros(max(int(cnt.value), 1), np.uint32)
+        _check(lib().fclsh_bucket(self.handle, table, key, _ptr(ids), ids.shape[0], ctypes.byref(cnt)))
+        return ids[:int(cnt.value)]
+
+    def export_table(self, table: int):
+        keys = np.zeros(self.n, np.uint64)
+        ids = np.zeros(self.n, np.uint32)
+        _check(lib().fclsh_export_table(self.handle, table, _ptr(keys), _ptr(ids)))
+        return keys, ids
+
+    # -- queries
+    def query(self, queries, radius: int, radii=None, stream=None) -> QueryResult:
+        rp = ctypes.POINTER(Result)()
+        _check(lib().fclsh_query(self.handle, _ptr(queries), _rows(queries), radius, _ptr(radii), _stream(stream),
+                                 ctypes.byref(rp)))
+        return _take_result(rp)
+
+    def query_plain(self, queries, radius: int, stream=None) -> QueryResult:
+        rp = ctypes.POINTER(Result)()
+        _check(lib().fclsh_query_plain(self.handle, _ptr(queries), _rows(queries), radius, _stream(stream),
+                                       ctypes.byref(rp)))
+        return _take_result(rp)
+
+    def bruteforce(self, queries, radius: int, stream=None) -> QueryResult:
+        rp = ctypes.POINTER(Result)()
+        _check(lib().fclsh_bruteforce(self.handle, _ptr(queries), _rows(queries), radius, _stream(stream),
+                                      ctypes.byref(rp)))
+        return _take_result(rp)
+
+    def context(self) -> QueryContext:
+        return QueryContext(self)
+
+    # -- tuning / timing
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().fclsh_get_tuning(self.handle, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        _check(lib().fclsh_get_tuning(self.handle, ctypes.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(lib().fclsh_set_tuning(self.handle, ctypes.byref(t)))
+
+    def autotune(self, queries, radius: int, cache_path: str | None = None) -> dict:
+        t = Tuning()
+        _check(lib().fclsh_autotune(self.handle, _ptr(queries), _rows(queries), radius,
+                                    cache_path.encode() if cache_path else None, ctypes.byref(t)))
+        return t.as_dict()
+
+    def timing_enable(self, on: bool = True):
+        _check(lib().fclsh_timing_enable(self.handle, 1 if on else 0))
+
+    def timing_read(self, reset: bool = False):
+        ms = (ctypes.c_double * 8)()
+        cnt = (ctypes.c_uint64 * 8)()
+        _check(lib().fclsh_timing_read(self.handle, ms, cnt, 1 if reset else 0))
+        names = ["build_hash", "build_sort", "query_kernel", "query_csr", "hash"]
+        out = {nm: (float(ms[i]), int(cnt[i])) for i, nm in enumerate(names)}
+        out["launches"] = int(cnt[7])
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().fclsh_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: int | None = None,
+          mem_budget: int | None = None, perm=None, part_off=None, m=None, b=None, timing: bool = False) -> Index:
+    """fclsh_build on host (numpy) or device (torch CUDA) points [n][ceil(d/64)] uint64."""
+    o = BuildOpts()
+    o.t = t or 0
+    o.slot_bits = slot_bits or 0
+    o.mem_budget = mem_budget or 0
+    o.timing = 1 if timing else 0
+    keep = []
+    if perm is not None:
+        arrs = [np.ascontiguousarray(perm, np.uint32), np.ascontiguousarray(part_off, np.uint32),
+                np.ascontiguousarray(m, np.uint32), np.ascontiguousarray(b, np.uint64)]
+        keep += arrs
+        o.perm, o.part_off, o.m, o.b = (a.ctypes.data for a in arrs)
+    h = ctypes.c_void_p()
+    _check(lib().fclsh_build(_ptr(points), _rows(points), d, r, seed, ctypes.byref(o), ctypes.byref(h)))
+    return Index(h)
+
+
+def kernel_launches() -> int:
+    """Kernels the library has enqueued in this process."""
+    return int(lib().fclsh_kernel_launches())
+
+
+def version() -> str:
+    return lib().fclsh_version().decode()

@@ -1,0 +1,249 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Keys, bucket contents and sorted result sets must be bit-exact (all integer
+arithmetic).  Sizes span several kernel tiles with ragged tails; the edge cases
+cover n = 1, empty batches, identical points (one huge bucket), r = 0 and
+radii below the build radius.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_02620_gb300 import workloads as wl
+from tests.conftest import bits_to_int, bits_to_words, read_golden
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_02620_gb300 import fclsh
+
+    fclsh.lib()
+
+
+def F():
+    from paper_1602_02620_gb300 import fclsh
+
+    return fclsh
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def rand_points(rng, n, d):
+    words = (d + 63) // 64
+    a = rng.integers(0, 2**63, size=(n, words), dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=(n, words), dtype=np.uint64)
+    if d % 64:
+        a[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    return a
+
+
+def near(rng, pts, d, kmax, count):
+    q = pts[rng.integers(0, pts.shape[0], size=count)].copy()
+    for i in range(count):
+        for pos in rng.choice(d, size=rng.integers(0, kmax + 1), replace=False):
+            q[i, pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+    return q
+
+
+# (d, r, t, n): W from 2 to 2048; general (d' > W) and specific (d' <= W) constructions
+HASH_CASES = [
+    (64, 0, None, 777),      # W = 2, general
+    (64, 1, None, 1000),     # W = 4
+    (64, 3, None, 3001),     # W = 16, general (the small plain workload's shape)
+    (40, 4, None, 1500),     # W = 32, specific, d not a multiple of 64
+    (100, 5, None, 2049),    # W = 64, general, ragged tile
+    (128, 6, None, 1025),    # W = 128, specific
+    (200, 7, None, 999),     # W = 256, specific
+    (128, 8, None, 1003),    # W = 512, specific (plain n=1M d=128 r=8 shape)
+    (256, 16, None, 517),    # t = 2, W = 512 per part (clustered shape)
+    (1024, 9, None, 300),    # W = 1024, specific, 16 words
+    (1024, 20, None, 211),   # t = 2, W = 2048 (sparse shape)
+    (300, 7, 3, 500),        # t = 3, general per part
+    (2000, 10, 2, 130),      # t = 2, W = 64 per part?  no: r' = 5 -> W = 64, general d' = 1000
+]
+
+
+@pytest.mark.parametrize("d,r,t,n", HASH_CASES)
+def test_params_and_keys_bit_exact(d, r, t, n):
+    rng = np.random.default_rng(d * 1000 + r)
+    pts = rand_points(rng, n, d)
+    pts[0] = 0
+    seed = 12345 + d + r
+    idx = F().build(pts, d, r, seed, t=t)
+    p = oracle.derive_params(seed, d, r, t=t)
+    perm, part_off, m, b = idx.params()
+    assert np.array_equal(perm, p.perm) and np.array_equal(part_off, p.part_off)
+    assert np.array_equal(m, p.m) and np.array_equal(b, p.b)
+    assert idx.T == p.T and idx.W == p.W
+    sample = pts[: min(n, 400)]
+    want = oracle.keys_direct(p, sample)
+    got = idx.hash(sample)                                   # host in, host out
+    assert np.array_equal(got, want)
+    out = torch.zeros((idx.T, sample.shape[0]), dtype=torch.int64, device="cuda")
+    idx.hash(dev(sample), out=out)                           # device in, device out
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
+    idx.free()
+
+
+def test_example1_and_example2_on_gpu():
+    """The worked examples (Sec. 2.3 and 3.1) through the GPU kernels, b_i = 2^i."""
+    g1 = read_golden("example1_covering.txt")
+    m = [int(s, 2) for s in g1["m"]]
+    pts = np.stack([bits_to_words(g1["x"][0]), bits_to_words(g1["q"][0]), bits_to_words("1111")])
+    idx = F().build(pts, 4, 2, 0, perm=[0, 1, 2, 3], part_off=[0, 4], m=m, b=[1, 2, 4, 8])
+    keys = idx.hash(pts)
+    for v in range(1, 8):
+        assert int(keys[v - 1, 2]) == bits_to_int(g1["g%d" % v][0])
+    coll = [v for v in range(1, 8) if keys[v - 1, 0] == keys[v - 1, 1]]
+    assert coll == [4] and int(keys[3, 0]) == bits_to_int(g1["value"][0])
+    idx.free()
+
+    g2 = read_golden("example2_c78.txt")
+    pts = np.stack([bits_to_words(g2[k][0]) for k in ("x", "y", "q")] + [bits_to_words("1" * 8)])
+    idx = F().build(pts, 8, 2, 0, perm=list(range(8)), part_off=[0, 8], m=list(range(8)), b=[1 << i for i in range(8)])
+    keys = idx.hash(pts)
+    for v in range(1, 8):
+        assert int(keys[v - 1, 3]) == bits_to_int(g2["C%d" % v][0])
+    assert [v for v in range(1, 8) if keys[v - 1, 0] == keys[v - 1, 2]] == [3]
+    assert not any(keys[v, 1] == keys[v, 2] for v in range(7))
+    # radius 2 around q reports x (distance 2) and not y (distance 3), found through the tables
+    res = idx.query(pts[2:3], 2)
+    assert res.of(0).tolist() == [0, 2]
+    idx.free()
+
+
+@pytest.mark.parametrize("d,r,n", [(64, 3, 3000), (128, 6, 2500), (256, 12, 1800)])
+def test_bucket_tables_bit_exact(d, r, n):
+    rng = np.random.default_rng(n)
+    pts = rand_points(rng, n, d)
+    pts[10:60] = pts[5]                                      # one bucket of 51 equal points in every table
+    seed = 77 + r
+    idx = F().build(pts, d, r, seed)
+    p = oracle.derive_params(seed, d, r)
+    for tau in sorted({0, 1, p.T // 2, p.T - 1}):
+        keys, ids = idx.export_table(tau)
+        order = np.lexsort((ids, keys))
+        ok, oi = oracle.table(p, pts, tau)
+        assert np.array_equal(keys[order], ok) and np.array_equal(ids[order], oi)
+        for key in {int(ok[0]), int(ok[len(ok) // 2]), int(keys[0])}:
+            want = oi[ok == key]
+            assert np.array_equal(idx.bucket(tau, key), want)
+    assert idx.bucket(0, 12345).size in (0, 1) or True
+    idx.free()
+
+
+QUERY_CASES = [
+    # d, r, t, n, nq, kmax
+    (64, 3, None, 4000, 150, 4),
+    (128, 8, None, 3000, 120, 9),
+    (256, 16, None, 2500, 80, 18),
+    (100, 5, None, 2000, 100, 6),
+    (1024, 20, None, 600, 40, 22),
+    (96, 12, 2, 3000, 100, 14),
+]
+
+
+def _oracle_answers(p, pts, qs, radius, with_counters):
+    tables = oracle.build_tables(p, pts) if with_counters else None
+    out = []
+    for q in qs:
+        if with_counters:
+            out.append(oracle.query(p, pts, tables, q, radius))
+        else:
+            out.append((oracle.linear_scan(pts, q, radius), None, None))
+    return out
+
+
+@pytest.mark.parametrize("d,r,t,n,nq,kmax", QUERY_CASES)
+def test_batched_plain_and_bruteforce_queries(d, r, t, n, nq, kmax):
+    rng = np.random.default_rng(d + r + n)
+    pts = rand_points(rng, n, d)
+    pts[100:140] = pts[7]                                    # duplicates
+    qs = np.concatenate([near(rng, pts, d, kmax, nq - 10), rand_points(rng, 10, d)])
+    seed = 999 + d
+    p = oracle.derive_params(seed, d, r, t=t)
+    idx = F().build(dev(pts), d, r, seed, t=t)
+    small = p.T * n <= 3_000_000
+    ans = _oracle_answers(p, pts, qs, r, small)
+    res = idx.query(dev(qs), r)
+    plain = idx.query_plain(qs, r)
+    brute = idx.bruteforce(dev(qs), r)
+    for i in range(qs.shape[0]):
+        want = ans[i][0]
+        assert np.array_equal(res.of(i), want), i
+        assert np.array_equal(plain.of(i), want), i
+        assert np.array_equal(brute.of(i), oracle.linear_scan(pts, qs[i], r)), i
+        if small:
+            assert int(res.collisions[i]) == ans[i][1] and int(res.candidates[i]) == ans[i][2], i
+            assert int(plain.collisions[i]) == ans[i][1] and int(plain.candidates[i]) == ans[i][2], i
+    # smaller radii and per-query radii over the same index
+    radii = rng.integers(0, r + 1, size=qs.shape[0]).astype(np.uint32)
+    res2 = idx.query(dev(qs), r, radii=torch.from_numpy(radii.view(np.int32)).cuda())
+    for i in range(qs.shape[0]):
+        assert np.array_equal(res2.of(i), oracle.linear_scan(pts, qs[i], int(radii[i])))
+    idx.free()
+
+
+def test_edge_cases():
+    fc = F()
+    rng = np.random.default_rng(5)
+    # n = 1
+    one = rand_points(rng, 1, 64)
+    idx = fc.build(one, 64, 3, 1)
+    assert idx.query(one, 3).of(0).tolist() == [0]
+    assert idx.query(np.zeros((1, 1), np.uint64) ^ ~one, 3).of(0).tolist() == []
+    # empty batch
+    r0 = idx.query(np.zeros((0, 1), np.uint64), 3)
+    assert len(r0) == 0 and r0.offs.tolist() == [0]
+    with pytest.raises(fc.FclshError) as e:
+        idx.query(one, 4)
+    assert e.value.status == fc.ERADIUS
+    idx.free()
+    # all points identical: one bucket of n entries in every table (bitmap dedup path)
+    same = np.repeat(rand_points(rng, 1, 128), 20000, axis=0)
+    idx = fc.build(dev(same), 128, 8, 3)
+    res = idx.query(same[:3], 8)
+    for i in range(3):
+        assert np.array_equal(res.of(i), np.arange(20000, dtype=np.uint32))
+        assert int(res.candidates[i]) == 20000 and int(res.collisions[i]) == 20000 * idx.T
+    idx.free()
+    # r = 0: exact-match queries
+    pts = rand_points(rng, 5000, 64)
+    pts[77] = pts[3]
+    idx = fc.build(pts, 64, 0, 9)
+    res = idx.query(pts[[3, 4]], 0)
+    assert res.of(0).tolist() == [3, 77] and res.of(1).tolist() == [4]
+    idx.free()
+
+
+def test_forced_bitmap_dedup_and_graph_replay():
+    """Shapes change speed only: tiny hash set (bitmap path), other blocks, graphs on/off."""
+    fc = F()
+    pts = wl.points(3, 30_000)
+    qs, _ = wl.queries(3, pts, 200)
+    idx = fc.build(dev(pts), 256, 16, 1003)
+    base = idx.query(dev(qs), 16)
+    for i in range(0, 200, 7):
+        assert np.array_equal(base.of(i), oracle.linear_scan(pts, qs[i], 16))
+    for tune in ({"hash_set_log2": 10, "inline_probe": 1}, {"query_block": 128, "use_graph": 0},
+                 {"query_block": 512, "query_ctas_per_sm": 1, "hash_set_log2": 13, "inline_probe": 32}):
+        idx.set_tuning(**tune)
+        r2 = idx.query(dev(qs), 16)
+        assert np.array_equal(r2.offs, base.offs) and np.array_equal(r2.ids, base.ids)
+        assert np.array_equal(r2.collisions, base.collisions) and np.array_equal(r2.candidates, base.candidates)
+    ctx = idx.context()
+    q = dev(qs)
+    for _ in range(3):                                       # replayed graph, same answers
+        ctx.query_async(q, 16)
+        r3 = ctx.fetch()
+        assert np.array_equal(r3.ids, base.ids)
+    ctx.close()
+    idx.free()
