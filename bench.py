@@ -157,6 +157,8 @@ def main():
     ap.add_argument("--impl", default="fclsh")
     ap.add_argument("--plain-sample", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="fewer points of the same workload (profiling)")
+    ap.add_argument("--nq", type=int, default=None, help="fewer queries of the same workload (profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -176,7 +178,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_1602_02620_gb300 import fclsh, workloads
 
-    w = workloads.make(CFG)
+    w = workloads.make(CFG, n=args.n, nq=args.nq)
     seed = w.index_seed + rank          # one independent problem per GPU
     nq = int(w.queries.shape[0])
     pts = torch.from_numpy(w.points.view(np.int64)).cuda()
@@ -252,6 +254,10 @@ def main():
     res = ctx.fetch()
     ctx.close()
     ns = min(args.plain_sample, nq)
+    if args.n is not None or args.nq is not None:
+        line_name = "%s (reduced: n=%d, queries=%d)" % (w.name, w.n, nq)
+    else:
+        line_name = w.name
     t0 = time.perf_counter()
     plain = idx.query_plain(w.queries[:ns], w.r)
     plain_qps = ns / (time.perf_counter() - t0)
@@ -292,7 +298,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "d": w.d, "r": w.r, "tables": T, "queries": nq,
+        "config": {"workload": line_name, "n": w.n, "d": w.d, "r": w.r, "tables": T, "queries": nq,
                    "step": "build index from device-resident points + one batch of all queries",
                    "l2": "inputs and index larger than L2 (16 MB points -> 4.1 GB keys, 6.1 GB index)"},
         "breakdown": {

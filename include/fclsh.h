@@ -99,7 +99,7 @@ typedef struct {
 typedef struct {
     uint32_t query_block;     /* threads per query CTA: 128, 256 or 512 */
     uint32_t query_ctas_per_sm;
-    uint32_t hash_set_log2;   /* shared-memory dedup set size 2^k (10..13) */
+    uint32_t hash_set_log2;   /* shared-memory dedup set of 2^k ids (10..13) */
     uint32_t inline_probe;    /* bucket-range length handled by the probing lane itself (1..32) */
     uint32_t use_graph;       /* capture a batch's launches into a CUDA graph and replay it */
 } fclsh_tuning;
@@ -216,6 +216,51 @@ fclsh_status fclsh_qctx_wait(fclsh_qctx *ctx, fclsh_device_result *out);
 
 /* Copy the context's last device results to a host fclsh_result. */
 fclsh_status fclsh_qctx_fetch(fclsh_qctx *ctx, fclsh_result **out);
+
+/* ------------------------------------------------------------------ serving */
+
+/* Server options.  Zero fields take the defaults shown. */
+typedef struct {
+    uint32_t slots;              /* device batches in flight, each on its own stream (4) */
+    uint32_t max_batch_queries;  /* queries packed into one device batch (16384) */
+    uint64_t mem_reserve;        /* device bytes a new batch must leave free (0 = none) */
+} fclsh_server_opts;
+
+typedef struct {
+    uint64_t requests, queries, batches, deferred_for_memory;
+    double mean_batch_queries;
+    double p50_ms, p99_ms, max_ms;   /* request latency, submit to results ready */
+    double queries_per_s;            /* completed queries / (last completion - first submit) */
+} fclsh_serve_stats;
+
+/*
+ * Continuous-batching server over a resident index (the served form of the
+ * batched query path).  A scheduler thread packs queued requests into device
+ * batches (requests of different radius share a batch through per-query radii),
+ * admits a batch when a slot is free and the device has the memory it needs, and
+ * retires batches as they finish, so arriving requests join while others run and
+ * batches on different slots overlap on the device.  A query's answer does not
+ * depend on what it was batched with.  The index must outlive the server.
+ */
+fclsh_status fclsh_server_create(fclsh_index *idx, const fclsh_server_opts *opts, fclsh_server **out);
+
+/* Queue a request: `queries` host [nq][words] (copied), one radius <= r for all of them. */
+fclsh_status fclsh_server_submit(fclsh_server *srv, const uint64_t *queries, uint64_t nq, uint32_t radius,
+                                 uint64_t *ticket);
+
+/*
+ * Wait up to timeout_ms (negative = no limit) for a request; on success *out holds
+ * its results (free with fclsh_result_free) and *latency_ms its submit-to-ready time.
+ * FCLSH_ETIMEOUT leaves the request queued; the ticket stays valid.
+ */
+fclsh_status fclsh_server_wait(fclsh_server *srv, uint64_t ticket, int timeout_ms, fclsh_result **out,
+                               double *latency_ms);
+
+/* Counters and latency percentiles of completed requests; reset = 1 starts a new window. */
+fclsh_status fclsh_server_stats(fclsh_server *srv, fclsh_serve_stats *out, int reset);
+
+/* Drain the queue, stop the scheduler and free the server.  NULL is ignored. */
+void fclsh_server_free(fclsh_server *srv);
 
 /* ------------------------------------------------------------------ tuning */
 

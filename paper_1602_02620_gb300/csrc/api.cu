@@ -30,6 +30,8 @@ cudaError_t launch_bruteforce(const uint64_t *points, uint64_t n, uint32_t words
                               uint32_t idbits, uint32_t *res_cnt, int sm_count, cudaStream_t s);
 cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned long long *d_count, uint64_t cap,
                                uint64_t idmask, uint32_t *ids, int sm_count, cudaStream_t s);
+cudaError_t launch_gather_runs(const uint32_t *runs, const uint64_t *run_base, const uint32_t *res_cnt,
+                               const uint64_t *offs, uint64_t nq, uint64_t cap, uint32_t *ids, int sm_count, cudaStream_t s);
 size_t hash_smem_bytes(uint32_t W, uint32_t dk);
 
 // ---------------------------------------------------------------- errors
@@ -197,10 +199,10 @@ using namespace fclsh;
 struct fclsh_qctx {
     fclsh_index *idx = nullptr;
     unsigned long long *counters = nullptr;   // [0] work, [1] cursor
-    unsigned long long *staged_a = nullptr, *staged_b = nullptr;
+    uint32_t *runs = nullptr;                 // [cap] each query's sorted hits
     uint64_t cap = 0;
-    uint32_t *hist = nullptr, *partials = nullptr;
     uint64_t nq_cap = 0;
+    uint64_t *run_base = nullptr;
     uint32_t *res_cnt = nullptr;
     uint64_t *res_offs = nullptr;
     uint32_t *res_ids = nullptr;
@@ -220,7 +222,6 @@ struct fclsh_qctx {
     const uint32_t *last_radii = nullptr;
     cudaStream_t last_stream = nullptr;
     bool pending = false;
-    bool sorted_in_b = false;
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     const uint64_t *g_q = nullptr;
@@ -236,7 +237,7 @@ struct fclsh_qctx {
 
 static void ctx_free_buffers(fclsh_qctx *c)
 {
-    void *ps[] = {c->counters, c->staged_a, c->staged_b, c->hist, c->partials, c->res_cnt, c->res_offs,
+    void *ps[] = {c->counters, c->runs, c->run_base, c->res_cnt, c->res_offs,
                   c->res_ids, c->coll, c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -273,14 +274,16 @@ static fclsh_status ctx_shape(fclsh_qctx *c)
 static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
 {
     if (nq > c->nq_cap) {
-        void *ps[] = {c->res_cnt, c->res_offs, c->coll, c->cand, c->scan_part};
+        void *ps[] = {c->res_cnt, c->res_offs, c->coll, c->cand, c->scan_part, c->run_base};
         for (void *p : ps)
             if (p) cudaFree(p);
         c->res_cnt = nullptr;
         c->res_offs = nullptr;
         c->coll = c->cand = nullptr;
         c->scan_part = nullptr;
+        c->run_base = nullptr;
         const uint64_t m = std::max<uint64_t>(nq, 1024);
+        FCLSH_CUDA(cudaMalloc(&c->run_base, m * 8));
         FCLSH_CUDA(cudaMalloc(&c->res_cnt, m * 4));
         FCLSH_CUDA(cudaMalloc(&c->res_offs, (m + 1) * 8));
         FCLSH_CUDA(cudaMalloc(&c->coll, m * 8));
@@ -293,18 +296,13 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
         }
     }
     if (cap > c->cap) {
-        void *ps[] = {c->staged_a, c->staged_b, c->res_ids, c->hist, c->partials};
+        void *ps[] = {c->runs, c->res_ids};
         for (void *p : ps)
             if (p) cudaFree(p);
-        c->staged_a = c->staged_b = nullptr;
+        c->runs = nullptr;
         c->res_ids = nullptr;
-        c->hist = c->partials = nullptr;
-        FCLSH_CUDA(cudaMalloc(&c->staged_a, cap * 8));
-        FCLSH_CUDA(cudaMalloc(&c->staged_b, cap * 8));
+        FCLSH_CUDA(cudaMalloc(&c->runs, cap * 4));
         FCLSH_CUDA(cudaMalloc(&c->res_ids, cap * 4));
-        const size_t h = sort_keys_hist_entries(cap);
-        FCLSH_CUDA(cudaMalloc(&c->hist, h * 4));
-        FCLSH_CUDA(cudaMalloc(&c->partials, scan_partials_entries(h) * 4));
         c->cap = cap;
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -348,7 +346,8 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
     a.radii = radii;
     a.work = c->counters;
     a.cursor = c->counters + 1;
-    a.staged = c->staged_a;
+    a.runs = c->runs;
+    a.run_base = c->run_base;
     a.cap = c->cap;
     a.res_cnt = c->res_cnt;
     a.coll = c->coll;
@@ -363,14 +362,9 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
     }
     {
         PhaseTimer pt(idx, 3, s);
-        const uint32_t bits = a.idbits + bits_for(std::max<uint64_t>(nq, 2));
-        bool in_b = false;
-        FCLSH_CUDA(radix_sort_keys_dev((uint64_t *)c->staged_a, (uint64_t *)c->staged_b, c->counters + 1, c->cap, bits,
-                                       c->hist, c->partials, &in_b, s));
-        c->sorted_in_b = in_b;
         FCLSH_CUDA(scan_u32_to_u64(c->res_cnt, c->res_offs, nq, c->scan_part, s));
-        FCLSH_CUDA(launch_extract_ids(in_b ? c->staged_b : c->staged_a, c->counters + 1, c->cap,
-                                      (1ULL << a.idbits) - 1, c->res_ids, idx->sm_count, s));
+        FCLSH_CUDA(launch_gather_runs(c->runs, c->run_base, c->res_cnt, c->res_offs, nq, c->cap, c->res_ids,
+                                      idx->sm_count, s));
     }
     return FCLSH_OK;
 }
@@ -515,7 +509,8 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if ((e = tmp.alloc(&keys, (size_t)L * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(build keys)");
     size_t free_b = 0, total_b = 0;
     FCLSH_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    uint64_t budget = o.mem_budget ? o.mem_budget : free_b / 2;
+    const uint64_t budget = o.mem_budget ? o.mem_budget : free_b / 4;
+    // radix-sort buffers for a chunk of tables: (key, id) twice, plus histograms
     const uint64_t per_row = n * 24 + sort_hist_entries(1, n) * 4 + 64;
     uint64_t rows = std::max<uint64_t>(1, budget / per_row);
     rows = std::min<uint64_t>(rows, L);
@@ -1043,7 +1038,7 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     if (!idx || !t) return fail(FCLSH_EINVAL, "NULL argument");
     if (t->query_block != 128 && t->query_block != 256 && t->query_block != 512)
         return fail(FCLSH_EINVAL, "query_block must be 128, 256 or 512");
-    if (t->hash_set_log2 < 10 || t->hash_set_log2 > 14) return fail(FCLSH_EINVAL, "hash_set_log2 must be in 10..14");
+    if (t->hash_set_log2 < 10 || t->hash_set_log2 > 13) return fail(FCLSH_EINVAL, "hash_set_log2 must be in 10..13");
     if (t->inline_probe < 1 || t->inline_probe > 32) return fail(FCLSH_EINVAL, "inline_probe must be in 1..32");
     if (t->query_ctas_per_sm < 1 || t->query_ctas_per_sm > 16) return fail(FCLSH_EINVAL, "query_ctas_per_sm must be in 1..16");
     idx->tune = *t;

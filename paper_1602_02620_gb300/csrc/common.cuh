@@ -67,7 +67,9 @@ struct QueryArgs {
     const uint32_t *radii;
     unsigned long long *work;     // next query
     unsigned long long *cursor;   // staging fill
-    unsigned long long *staged;
+    unsigned long long *staged;   // plain path: hits of one query
+    uint32_t *runs;               // batched path: each query's sorted hits, one contiguous run per query
+    uint64_t *run_base;           // [nq] start of query i's run in `runs`
     uint64_t cap;
     uint32_t idbits;
     uint32_t *res_cnt;

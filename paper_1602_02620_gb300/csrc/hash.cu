@@ -80,6 +80,41 @@ __host__ __device__ constexpr size_t cols_smem_bytes(uint32_t W, uint32_t dk)
     return (size_t)dk * 8 + ((size_t)W + 1 + dk) * 4 + 8;
 }
 
+// Gather modes of the sketch.  GENERAL walks a column's list (general
+// construction, several coordinates per column).  With the specific construction a
+// column holds at most one coordinate, packed with its seed value as
+// b | coord << 50 (b = 0 for an empty column): PACKED_REG keeps the point's
+// words in registers (d <= 256), PACKED_LDG reads them through L1.
+enum GatherMode { GENERAL = 0, PACKED_REG = 1, PACKED_LDG = 2 };
+
+__device__ __forceinline__ const uint64_t *stage_packed(const PartCols &pc, uint32_t W, void *smem_base)
+{
+    uint64_t *pk = reinterpret_cast<uint64_t *>(smem_base);
+    const uint32_t base = pc.col_off[0];
+    for (uint32_t j = threadIdx.x; j < W; j += blockDim.x) {
+        const uint32_t e0 = pc.col_off[j], e1 = pc.col_off[j + 1];
+        pk[j] = e1 > e0 ? (pc.bval[e0] | ((uint64_t)pc.coord[e0] << 50)) : 0ULL;
+    }
+    (void)base;
+    return pk;
+}
+
+struct PointRegs {
+    uint64_t x0, x1, x2, x3;
+    __device__ __forceinline__ uint64_t word(uint32_t c) const
+    {
+        const uint32_t w = c >> 6;
+        return w < 2 ? (w == 0 ? x0 : x1) : (w == 2 ? x2 : x3);
+    }
+};
+
+__device__ __forceinline__ uint64_t packed_value(uint64_t pk, uint64_t word_of_coord)
+{
+    const uint32_t c = (uint32_t)(pk >> 50);
+    const uint64_t take = 0ULL - ((word_of_coord >> (c & 63)) & 1ULL);
+    return pk & kMask50 & take;
+}
+
 // ------------------------------------------------------------------ W <= 32
 
 template <int LOGW>
@@ -124,6 +159,8 @@ struct Tile {
     static constexpr int NP = C::NP;
     static constexpr int NT = NP * W / 32;            // threads per block
     static constexpr size_t VALUES_BYTES = (size_t)W * NP * 8;
+    // blocks per SM the register budget is sized for (forcing 3 spills at 80 registers)
+    static constexpr int MINB = VALUES_BYTES <= 64 * 1024 ? 2 : 1;
 };
 
 // Shared-memory slot of value j of point p.  With NP = 8 a half-warp touches two
@@ -147,10 +184,11 @@ __device__ __forceinline__ uint32_t jidx(uint32_t other, uint32_t k)
 
 // MODE 0: gather the sketch, transform, write to smem.  1: smem -> transform -> smem.
 // 2: smem -> transform -> finish -> global keys.
-template <int LOGW, int LO, int B, int MODE>
+template <int LOGW, int LO, int B, int MODE, int GM>
 __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsigned long long *S_acc, uint32_t p,
-                                      uint32_t tp, const ColsSmem &cols, const uint64_t *__restrict__ x, bool valid,
-                                      uint64_t *__restrict__ keys, uint64_t ld, uint64_t gp)
+                                      uint32_t tp, const ColsSmem &cols, const uint64_t *pk, const PointRegs &xr,
+                                      const uint64_t *__restrict__ x, bool valid, uint64_t *__restrict__ keys,
+                                      uint64_t ld, uint64_t gp)
 {
     using T = Tile<LOGW>;
     constexpr int K = 1 << B, G = 32 / K;
@@ -163,7 +201,14 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
         for (int k = 0; k < K; ++k) {
             const uint32_t j = jidx<LO, B>(other, k);
             if (MODE == 0) {
-                const uint64_t tj = valid ? sketch_column(cols, j, x) : 0;
+                uint64_t tj;
+                if (GM == GENERAL) {
+                    tj = valid ? sketch_column(cols, j, x) : 0;
+                } else {
+                    const uint64_t pj = pk[j];
+                    const uint32_t c = (uint32_t)(pj >> 50);
+                    tj = packed_value(pj, GM == PACKED_REG ? xr.word(c) : (valid ? __ldg(x + (c >> 6)) : 0ULL));
+                }
                 v[g * K + k] = tj;
                 part += tj;
             } else {
@@ -197,8 +242,8 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
     }
 }
 
-template <int LOGW>
-__global__ void __launch_bounds__(Tile<LOGW>::NT) hash_tile_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
+template <int LOGW, int GM>
+__global__ void __launch_bounds__(Tile<LOGW>::NT, Tile<LOGW>::MINB) hash_tile_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
                                                                     uint32_t words, PartCols pc,
                                                                     uint64_t *__restrict__ keys, uint64_t ld)
 {
@@ -207,23 +252,52 @@ __global__ void __launch_bounds__(Tile<LOGW>::NT) hash_tile_kernel(const uint64_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
     unsigned long long *S_acc = reinterpret_cast<unsigned long long *>(sm + (size_t)T::W * T::NP);
-    const ColsSmem cols = stage_cols(pc, T::W, S_acc + T::NP);
+    ColsSmem cols{};
+    const uint64_t *pk = nullptr;
+    if (GM == GENERAL)
+        cols = stage_cols(pc, T::W, S_acc + T::NP);
+    else
+        pk = stage_packed(pc, T::W, S_acc + T::NP);
     const uint32_t p = threadIdx.x % T::NP, tp = threadIdx.x / T::NP;
     const uint64_t gp = blockIdx.x * (uint64_t)T::NP + p;
     const bool valid = gp < cnt;
     const uint64_t *x = pts + (valid ? gp : 0) * words;
+    PointRegs xr{0, 0, 0, 0};
+    if (GM == PACKED_REG && valid) {
+        xr.x0 = __ldg(x);
+        if (words > 1) xr.x1 = __ldg(x + 1);
+        if (words > 2) xr.x2 = __ldg(x + 2);
+        if (words > 3) xr.x3 = __ldg(x + 3);
+    }
     if (threadIdx.x < T::NP) S_acc[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t *S_sm = reinterpret_cast<const uint64_t *>(S_acc);
-    phase<LOGW, 0, C::B0, 0>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+    phase<LOGW, 0, C::B0, 0, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
     __syncthreads();
     if constexpr (C::NPH == 2) {
-        phase<LOGW, C::B0, C::B1, 2>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+        phase<LOGW, C::B0, C::B1, 2, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
     } else {
-        phase<LOGW, C::B0, C::B1, 1>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+        phase<LOGW, C::B0, C::B1, 1, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
         __syncthreads();
-        phase<LOGW, C::B0 + C::B1, C::B2, 2>(sm, S_sm, S_acc, p, tp, cols, x, valid, keys, ld, gp);
+        phase<LOGW, C::B0 + C::B1, C::B2, 2, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
     }
+}
+
+template <int LOGW, int GM>
+cudaError_t launch_tile(size_t cbytes, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, uint64_t *keys,
+                        uint64_t ld, cudaStream_t s)
+{
+    using T = Tile<LOGW>;
+    const size_t smem = T::VALUES_BYTES + T::NP * 8 + cbytes;
+    auto kern = hash_tile_kernel<LOGW, GM>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const uint64_t blocks = (cnt + T::NP - 1) / T::NP;
+    kern<<<(unsigned)blocks, T::NT, smem, s>>>(pts, cnt, words, pc, keys, ld);
+    note_launch();
+    return cudaGetLastError();
 }
 
 template <int LOGW>
@@ -231,10 +305,9 @@ cudaError_t launch_logw(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t
                         uint64_t ld, cudaStream_t s)
 {
     constexpr int W = 1 << LOGW;
-    const size_t cbytes = cols_smem_bytes(W, dk);
     if constexpr (LOGW <= 5) {
+        const size_t smem = cols_smem_bytes(W, dk);
         const int threads = 128;
-        const size_t smem = cbytes;
         auto kern = hash_small_kernel<LOGW>;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -243,19 +316,13 @@ cudaError_t launch_logw(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t
         const uint64_t blocks = (cnt + threads - 1) / threads;
         kern<<<(unsigned)blocks, threads, smem, s>>>(pts, cnt, words, pc, keys, ld);
         note_launch();
+        return cudaGetLastError();
     } else {
-        using T = Tile<LOGW>;
-        const size_t smem = T::VALUES_BYTES + T::NP * 8 + cbytes;
-        auto kern = hash_tile_kernel<LOGW>;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        const uint64_t blocks = (cnt + T::NP - 1) / T::NP;
-        kern<<<(unsigned)blocks, T::NT, smem, s>>>(pts, cnt, words, pc, keys, ld);
-        note_launch();
+        if (dk > (uint32_t)W)   // general construction: column lists
+            return launch_tile<LOGW, GENERAL>(cols_smem_bytes(W, dk), pts, cnt, words, pc, keys, ld, s);
+        if (words <= 4) return launch_tile<LOGW, PACKED_REG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
+        return launch_tile<LOGW, PACKED_LDG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace

@@ -12,13 +12,16 @@
 // heavy bucket never serialises on one lane.  Duplicates are removed with a
 // shared-memory hash set when the query's bucket ranges hold at most half its
 // capacity, and otherwise with an n-bit bitmap owned by the CTA (the bitmap of
-// Sec. 4.1), cleared after the query.  Hits go to a global staging buffer as
-// (query << idbits | id); a radix sort then yields every query's ids ascending.
+// Sec. 4.1), cleared after the query.  Hits collect in shared memory and are
+// sorted there (up to 4,096 per query); a query with more hits walks its buckets
+// again into the bitmap and reads its ids out of it in order.  Each query writes
+// one sorted run; a gather kernel lays the runs out as CSR.
 #include "common.cuh"
 
 namespace fclsh {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kResCap = 4096;   // hits of one query sorted in shared memory
 
 namespace {
 
@@ -40,6 +43,26 @@ __device__ __forceinline__ T block_sum(T v, T *red)   // red: >= 32 entries of s
     const uint32_t nw = blockDim.x >> 5;
     for (uint32_t w = 0; w < nw; ++w) s += red[w];
     return s;
+}
+
+// Exclusive block-wide prefix of one u32 per thread (red: >= 33 u64 of shared memory).
+__device__ __forceinline__ uint64_t block_excl_scan_u32(uint32_t v, unsigned long long *red)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += u;
+    }
+    __syncthreads();
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    uint64_t before = 0;
+    for (uint32_t w = 0; w < warp; ++w) before += red[w];
+    (void)nw;
+    __syncthreads();
+    return before + incl - v;
 }
 
 // Hamming distance between the query in shared memory and point `id`.
@@ -78,8 +101,8 @@ struct Counters {
 
 // One bucket entry per lane (is_coll = key matched); warp-collective.
 __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
-                                              bool bitmap_mode, uint32_t radius, uint64_t qi, bool is_coll,
-                                              uint32_t id, Counters &c)
+                                              bool bitmap_mode, uint32_t radius, bool is_coll, uint32_t id, Counters &c,
+                                              uint32_t *res_s, uint32_t *s_nres)
 {
     bool isnew = false;
     if (is_coll) {
@@ -100,15 +123,53 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
     if (m) {
         const uint32_t lane = threadIdx.x & 31;
         const uint32_t leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(a.cursor, (unsigned long long)__popc(m));
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(s_nres, (uint32_t)__popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (hit) {
             c.res++;
-            const unsigned long long pos = base + __popc(m & lanemask_lt());
-            if (pos < a.cap) a.staged[pos] = (qi << a.idbits) | id;
+            const uint32_t pos = base + __popc(m & lanemask_lt());
+            if (pos < kResCap) res_s[pos] = id;
         }
     }
+}
+
+// Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
+__device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
+{
+    if (cnt <= 1) return;
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    if (cnt <= 32) {   // one warp, shuffles only
+        if (tid < 32) {
+            uint32_t x = tid < cnt ? v[tid] : 0xFFFFFFFFu;
+            for (uint32_t k = 2; k <= 32; k <<= 1)
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                    const bool lower = (tid & j) == 0, up = (tid & k) == 0;
+                    x = (lower == up) ? min(x, y) : max(x, y);
+                }
+            if (tid < cnt) v[tid] = x;
+        }
+        __syncthreads();
+        return;
+    }
+    uint32_t size = 64;
+    while (size < cnt) size <<= 1;
+    for (uint32_t i = cnt + tid; i < size; i += B) v[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t k = 2; k <= size; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = tid; i < size / 2; i += B) {
+                const uint32_t a = 2 * i - (i & (j - 1)), b = a + j;
+                const bool up = (a & k) == 0;
+                const uint32_t x = v[a], y = v[b];
+                if ((x > y) == up) {
+                    v[a] = y;
+                    v[b] = x;
+                }
+            }
+            __syncthreads();
+        }
 }
 
 }  // namespace
@@ -117,7 +178,7 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
 size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_log2)
 {
     const size_t tb = (size_t)W * 8 > ((size_t)4 << hset_log2) ? (size_t)W * 8 : ((size_t)4 << hset_log2);
-    return (size_t)T * 8 + (size_t)T * 8 + tb + (size_t)words * 8 + 64;
+    return (size_t)T * 8 + (size_t)T * 8 + tb + (size_t)words * 8 + (size_t)kResCap * 4 + 64;
 }
 
 __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
@@ -130,7 +191,9 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
     uint32_t *hset = reinterpret_cast<uint32_t *>(tbuf);
     const size_t tb_words = ((size_t)a.W > ((size_t)1 << a.hset_log2) / 2) ? a.W : ((size_t)1 << a.hset_log2) / 2;
     uint64_t *q_s = tbuf + tb_words;
+    uint32_t *res_s = reinterpret_cast<uint32_t *>(q_s + a.words);
     __shared__ unsigned long long s_qi;
+    __shared__ uint32_t s_nres;
     __shared__ unsigned long long red64[32];
 
     const uint32_t tid = threadIdx.x, B = blockDim.x;
@@ -191,6 +254,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         const bool bitmap_mode = E > (hcap >> 1);
         if (!bitmap_mode)
             for (uint32_t i = tid; i < hcap; i += B) hset[i] = kEmpty;
+        if (tid == 0) s_nres = 0;
         __syncthreads();
 
         // ---- S2b + S3: collisions -> dedup -> verify, 32 tables per warp step
@@ -206,8 +270,8 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             for (uint32_t e = 0; e < maxs; ++e) {
                 const bool act = e < short_len;
                 const uint64_t en = act ? __ldg(row + lo + e) : 0;
-                process_entry(a, q_s, hset, bm, bitmap_mode, radius, qi, act && (uint32_t)(en >> 32) == fp,
-                              (uint32_t)en, c);
+                process_entry(a, q_s, hset, bm, bitmap_mode, radius, act && (uint32_t)(en >> 32) == fp,
+                              (uint32_t)en, c, res_s, &s_nres);
             }
             uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
             while (lmask) {
@@ -222,27 +286,86 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                     const uint32_t e = cbase + lane;
                     const bool act = e < l_len;
                     const uint64_t en = act ? __ldg(lrow + e) : 0;
-                    process_entry(a, q_s, hset, bm, bitmap_mode, radius, qi, act && (uint32_t)(en >> 32) == l_fp,
-                                  (uint32_t)en, c);
+                    process_entry(a, q_s, hset, bm, bitmap_mode, radius, act && (uint32_t)(en >> 32) == l_fp,
+                                  (uint32_t)en, c, res_s, &s_nres);
                 }
             }
         }
         const unsigned long long tc = block_sum(c.coll, red64);
         const unsigned long long td = block_sum(c.cand, red64);
-        const unsigned long long tr = block_sum((unsigned long long)c.res, red64);
-        if (tid == 0) {
-            a.coll[qi] = tc;
-            a.cand[qi] = td;
-            a.res_cnt[qi] = (uint32_t)tr;
-        }
-        if (bitmap_mode) {   // leave the CTA's bitmap all-zero for its next query
+        const uint32_t nres = s_nres;   // read after block_sum's barriers
+        __shared__ unsigned long long s_base;
+        if (bitmap_mode) {   // leave the CTA's bitmap all-zero
             for (uint32_t tau = tid; tau < a.T; tau += B) {
                 const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[tau];
                 const uint32_t len = len_s[tau];
                 for (uint32_t e = 0; e < len; ++e) bm[(uint32_t)__ldg(row + e) >> 5] = 0;
             }
+            __syncthreads();
+        }
+        if (nres <= kResCap) {
+            block_sort_u32(res_s, nres);
+            if (tid == 0) s_base = atomicAdd(a.cursor, (unsigned long long)nres);
+            __syncthreads();
+            const unsigned long long base = s_base;
+            for (uint32_t i = tid; i < nres; i += B)
+                if (base + i < a.cap) a.runs[base + i] = res_s[i];
+        } else {
+            // More hits than shared memory holds (only in bitmap mode): mark every hit in
+            // the bitmap, then read the ids out in ascending order and clear it again.
+            for (uint32_t tau = tid; tau < a.T; tau += B) {
+                const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[tau];
+                const uint32_t len = len_s[tau];
+                const uint32_t fp = (uint32_t)(keys_s[tau] >> a.slot_bits);
+                for (uint32_t e = 0; e < len; ++e) {
+                    const uint64_t en = __ldg(row + e);
+                    if ((uint32_t)(en >> 32) != fp) continue;
+                    const uint32_t id = (uint32_t)en;
+                    if (distance_to(a, q_s, id) <= radius) atomicOr(bm + (id >> 5), 1u << (id & 31));
+                }
+            }
+            if (tid == 0) s_base = atomicAdd(a.cursor, (unsigned long long)nres);
+            __syncthreads();
+            const unsigned long long base = s_base;
+            const uint64_t per = (a.bm_words + B - 1) / B;
+            const uint64_t w0 = (uint64_t)tid * per, w1 = min(w0 + per, a.bm_words);
+            uint32_t mine = 0;
+            for (uint64_t w = w0; w < w1; ++w) mine += __popc(bm[w]);
+            const uint32_t before = (uint32_t)block_excl_scan_u32(mine, red64);
+            unsigned long long pos = base + before;
+            for (uint64_t w = w0; w < w1; ++w) {
+                uint32_t bits = bm[w];
+                while (bits) {
+                    const uint32_t b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (pos < a.cap) a.runs[pos] = (uint32_t)(w * 32 + b);
+                    ++pos;
+                }
+                bm[w] = 0;
+            }
+        }
+        if (tid == 0) {
+            a.coll[qi] = tc;
+            a.cand[qi] = td;
+            a.res_cnt[qi] = nres;
+            a.run_base[qi] = s_base;
         }
         __syncthreads();
+    }
+}
+
+// CSR layout of the runs: ids[offs[q] + i] = runs[run_base[q] + i].
+__global__ void __launch_bounds__(256) gather_runs_kernel(const uint32_t *runs, const uint64_t *run_base,
+                                                          const uint32_t *res_cnt, const uint64_t *offs, uint64_t nq,
+                                                          uint64_t cap, uint32_t *ids)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t q = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < nq; q += warps) {
+        const uint64_t src = run_base[q], dst = offs[q];
+        const uint32_t cnt = res_cnt[q];
+        for (uint32_t i = lane; i < cnt; i += 32)
+            if (src + i < cap && dst + i < cap) ids[dst + i] = runs[src + i];
     }
 }
 
@@ -422,6 +545,15 @@ cudaError_t launch_bruteforce(const uint64_t *points, uint64_t n, uint32_t words
     dim3 grid((unsigned)ptiles, (unsigned)qtiles);
     bruteforce_kernel<<<grid, 256, smem, s>>>(points, n, words, queries, nq, radius, cursor, staged, cap, idbits,
                                                res_cnt, ppc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_runs(const uint32_t *runs, const uint64_t *run_base, const uint32_t *res_cnt,
+                               const uint64_t *offs, uint64_t nq, uint64_t cap, uint32_t *ids, int sm_count, cudaStream_t s)
+{
+    if (nq == 0) return cudaSuccess;
+    gather_runs_kernel<<<(unsigned)(sm_count * 4), 256, 0, s>>>(runs, run_base, res_cnt, offs, nq, cap, ids);
     note_launch();
     return cudaGetLastError();
 }

@@ -32,6 +32,7 @@ struct RadixArgs {
     uint32_t shift;
     uint32_t dmask;               // digit = (key >> shift) & dmask: the last pass may have fewer than 8 bits
     uint32_t *hist;               // [rows][256][tiles]
+    uint32_t rows;
 };
 
 __device__ __forceinline__ uint64_t row_len(const RadixArgs &a)
@@ -61,21 +62,42 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(RadixArgs a)
     a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile] = cnt[tid];
 }
 
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *total);
+
+// Stable scatter of one tile.  Ranks come from warp match + per-warp digit counts
+// (tile items are taken in index order: round, warp, lane); each item first goes
+// to its digit-sorted slot in shared memory, then the tile's digit runs are
+// written out as contiguous, coalesced runs.
 template <bool IDS, bool IMPLICIT>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(RadixArgs a)
 {
-    __shared__ uint32_t digit_off[256];          // global output offset of this tile's run of each digit
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kSortTile]
+    uint32_t *si = reinterpret_cast<uint32_t *>(sk + kSortTile);  // [kSortTile] when IDS
+    __shared__ uint32_t local_start[256], global_off[256], run[256];
     __shared__ uint32_t warp_cnt[kWarps][256];
     __shared__ uint32_t warp_pre[kWarps][256];
     const uint32_t row = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
     const uint64_t len = row_len(a);
     const uint64_t base = (uint64_t)tile * kSortTile;
-    digit_off[tid] = a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile];
+    if (base >= len) return;   // uniform: an empty tile has no items
+    {
+        // this tile's count of digit tid, from the scanned (row, digit, tile) prefix
+        const uint64_t idx = ((uint64_t)row * 256 + tid) * a.tiles + tile;
+        const uint64_t hcount = (uint64_t)a.rows * 256 * a.tiles;
+        const uint32_t g0 = a.hist[idx];
+        const uint32_t g1 = idx + 1 < hcount ? a.hist[idx + 1] : (uint32_t)((uint64_t)(a.rows - 1) * a.len + len);
+        global_off[tid] = g0;
+        uint32_t tot;
+        const uint32_t ls = block_excl_scan<uint32_t>(g1 - g0, &tot);
+        local_start[tid] = ls;
+        run[tid] = ls;
+    }
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) warp_cnt[w][tid] = 0;
     __syncthreads();
-    if (base >= len) return;
     const uint64_t *K = a.keys_in + (uint64_t)row * a.len;
     const uint32_t *I = IMPLICIT ? nullptr : a.ids_in + (uint64_t)row * a.len;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -93,23 +115,32 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(RadixArgs a
         const uint32_t rank = __popc(peers & lt_mask);
         if (valid && (peers & lt_mask) == 0) warp_cnt[warp][digit] = __popc(peers);
         __syncthreads();
-        {   // thread tid owns digit tid: prefix over warps, advance the tile's running offset
-            uint32_t run = digit_off[tid];
+        {   // thread tid owns digit tid: prefix over warps, advance the digit's local run
+            uint32_t rc = run[tid];
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) {
                 const uint32_t c = warp_cnt[w][tid];
-                warp_pre[w][tid] = run;
-                run += c;
+                warp_pre[w][tid] = rc;
+                rc += c;
                 warp_cnt[w][tid] = 0;
             }
-            digit_off[tid] = run;
+            run[tid] = rc;
         }
         __syncthreads();
         if (valid) {
-            const uint64_t pos = warp_pre[warp][digit] + rank;
-            a.keys_out[pos] = key;
-            if (IDS) a.ids_out[pos] = id;
+            const uint32_t lp = warp_pre[warp][digit] + rank;
+            sk[lp] = key;
+            if (IDS) si[lp] = id;
         }
+    }
+    __syncthreads();
+    const uint32_t tile_n = (uint32_t)((len - base) < (uint64_t)kSortTile ? (len - base) : (uint64_t)kSortTile);
+    for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
+        const uint64_t key = sk[i];
+        const uint32_t d = (uint32_t)(key >> a.shift) & a.dmask;
+        const uint64_t g = (uint64_t)global_off[d] + (i - local_start[d]);
+        a.keys_out[g] = key;
+        if (IDS) a.ids_out[g] = si[i];
     }
 }
 
@@ -244,7 +275,28 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restric
         for (uint64_t s2 = sl + 1; s2 <= nslots; ++s2) O[s2] = (uint32_t)len;
 }
 
+
 }  // namespace
+
+constexpr size_t kScatterSmemIds = (size_t)kSortTile * 12;
+constexpr size_t kScatterSmemKeys = (size_t)kSortTile * 8;
+
+// The scatter kernels use more than 48 KB of shared memory; raise their limit once.
+static cudaError_t scatter_smem_init()
+{
+    static cudaError_t once = [] {
+        cudaError_t e = cudaFuncSetAttribute(radix_scatter_kernel<true, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmemIds);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(radix_scatter_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kScatterSmemIds);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(radix_scatter_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kScatterSmemKeys);
+        return e;
+    }();
+    return once;
+}
 
 size_t sort_hist_entries(uint32_t rows, uint64_t len)
 {
@@ -259,6 +311,8 @@ size_t scan_partials_entries(size_t count) { return (count + kScanChunk - 1) / k
 cudaError_t radix_sort_rows(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t bits, SortBuffers &buf,
                             bool *out_in_b, cudaStream_t s)
 {
+    cudaError_t e0 = scatter_smem_init();
+    if (e0 != cudaSuccess) return e0;
     const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
     const uint32_t passes = (bits + 7) / 8;
     const uint64_t hcount = (uint64_t)rows * 256 * tiles;
@@ -269,15 +323,15 @@ cudaError_t radix_sort_rows(const uint64_t *keys_in, uint32_t rows, uint64_t len
         const bool to_b = (p % 2) == 1;
         const uint32_t nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
         RadixArgs a{kin, iin, to_b ? buf.keys_b : buf.keys_a, to_b ? buf.ids_b : buf.ids_a, len, nullptr, tiles,
-                    8 * p, (1u << nb) - 1u, buf.hist};
+                    8 * p, (1u << nb) - 1u, buf.hist, rows};
         radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a);
         note_launch();
         cudaError_t e = scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s);
         if (e != cudaSuccess) return e;
         if (p == 0)
-            radix_scatter_kernel<true, true><<<grid, kSortThreads, 0, s>>>(a);
+            radix_scatter_kernel<true, true><<<grid, kSortThreads, kScatterSmemIds, s>>>(a);
         else
-            radix_scatter_kernel<true, false><<<grid, kSortThreads, 0, s>>>(a);
+            radix_scatter_kernel<true, false><<<grid, kSortThreads, kScatterSmemIds, s>>>(a);
         note_launch();
         kin = a.keys_out;
         iin = a.ids_out;
@@ -289,6 +343,8 @@ cudaError_t radix_sort_rows(const uint64_t *keys_in, uint32_t rows, uint64_t len
 cudaError_t radix_sort_keys_dev(uint64_t *keys_a, uint64_t *keys_b, const unsigned long long *d_count, uint64_t cap,
                                 uint32_t bits, uint32_t *hist, uint32_t *partials, bool *out_in_b, cudaStream_t s)
 {
+    cudaError_t e0 = scatter_smem_init();
+    if (e0 != cudaSuccess) return e0;
     const uint32_t tiles = (uint32_t)((cap + kSortTile - 1) / kSortTile);
     const uint32_t passes = (bits + 7) / 8;
     const uint64_t hcount = (uint64_t)256 * tiles;
@@ -297,12 +353,12 @@ cudaError_t radix_sort_keys_dev(uint64_t *keys_a, uint64_t *keys_b, const unsign
         const bool from_b = (p % 2) == 1;
         const uint32_t nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
         RadixArgs a{from_b ? keys_b : keys_a, nullptr, from_b ? keys_a : keys_b, nullptr, cap, d_count, tiles, 8 * p,
-                    (1u << nb) - 1u, hist};
+                    (1u << nb) - 1u, hist, 1};
         radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a);
         note_launch();
         cudaError_t e = scan_exclusive<uint32_t, uint32_t, uint32_t>(hist, hist, hcount, partials, false, s);
         if (e != cudaSuccess) return e;
-        radix_scatter_kernel<false, false><<<grid, kSortThreads, 0, s>>>(a);
+        radix_scatter_kernel<false, false><<<grid, kSortThreads, kScatterSmemKeys, s>>>(a);
         note_launch();
     }
     *out_in_b = passes % 2 == 1;
@@ -324,3 +380,4 @@ cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, u
 }
 
 }  // namespace fclsh
+

@@ -58,6 +58,17 @@ class Tuning(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32), ("mem_reserve", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("queries", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("deferred_for_memory", ctypes.c_uint64), ("mean_batch_queries", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("queries_per_s", ctypes.c_double)]
+
+
 #: Every entry point of include/fclsh.h: name -> (restype, argtypes).
 _vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 SIGNATURES = {
@@ -82,6 +93,11 @@ SIGNATURES = {
     "fclsh_autotune": (_i, [_vp, _vp, _u64, _u32, ctypes.c_char_p, _vp]),
     "fclsh_timing_enable": (_i, [_vp, _i]),
     "fclsh_timing_read": (_i, [_vp, _vp, _vp, _i]),
+    "fclsh_server_create": (_i, [_vp, _vp, _vp]),
+    "fclsh_server_submit": (_i, [_vp, _vp, _u64, _u32, _vp]),
+    "fclsh_server_wait": (_i, [_vp, _u64, _i, _vp, _vp]),
+    "fclsh_server_stats": (_i, [_vp, _vp, _i]),
+    "fclsh_server_free": (None, [_vp]),
     "fclsh_kernel_launches": (_u64, []),
     "fclsh_last_error": (ctypes.c_char_p, []),
     "fclsh_version": (ctypes.c_char_p, []),
@@ -296,6 +312,45 @@ class Index:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server over a resident index (fclsh_server)."""
+
+    def __init__(self, index: "Index", slots: int = 4, max_batch_queries: int = 16384, mem_reserve: int = 0):
+        self.index = index
+        o = ServerOpts(slots, max_batch_queries, mem_reserve)
+        h = ctypes.c_void_p()
+        _check(lib().fclsh_server_create(index.handle, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, queries: np.ndarray, radius: int) -> int:
+        q = np.ascontiguousarray(queries, dtype=np.uint64)
+        t = ctypes.c_uint64()
+        _check(lib().fclsh_server_submit(self.handle, _ptr(q), _rows(q), radius, ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        rp = ctypes.POINTER(Result)()
+        lat = ctypes.c_double()
+        _check(lib().fclsh_server_wait(self.handle, ticket, timeout_ms, ctypes.byref(rp), ctypes.byref(lat)))
+        return _take_result(rp), float(lat.value)
+
+    def stats(self, reset: bool = False) -> dict:
+        s = ServerStats()
+        _check(lib().fclsh_server_stats(self.handle, ctypes.byref(s), 1 if reset else 0))
+        return {f: (float(getattr(s, f)) if t is ctypes.c_double else int(getattr(s, f))) for f, t in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().fclsh_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 
