@@ -190,6 +190,29 @@ fclsh_status fclsh_query_plain(fclsh_index *idx, const uint64_t *queries, uint64
 fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
                               void *stream, fclsh_result **out);
 
+/*
+ * One query through the plain path without allocating: for callers that cannot
+ * call cudaMalloc/cudaFree while they query (code running under an allocator or
+ * memory pool it does not own, or a latency-bound loop where an allocation and
+ * the device synchronisation it can cause are not allowed).  The paper has no
+ * counterpart; this is a packaging of the plain path.
+ *   query: device, one point [words].  radius <= r.
+ *   ids_out: device, capacity cap; receives the ids within `radius`, ascending
+ *   (only the first cap if there are more).  counts_out: device [3]: the number of
+ *   results (it may exceed cap), #Collisions, #Candidates.
+ * All scratch lives in one fixed device array of about 1.1 MB that every GPU
+ * loading the library holds until the process exits, so the call supports
+ * indexes of at most 4,194,304 points and 4,094 tables (d <= 16384) and rejects
+ * larger ones with FCLSH_EINVAL.  It allocates nothing: no cudaMalloc, cudaFree
+ * or allocating library routine.  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).
+ * Every call reuses the same array and clears what it needs, so calls that
+ * overlap on the GPU (other streams, other threads) race: serialise them.
+ * Asynchronous on `stream`.
+ */
+fclsh_status fclsh_query_plain_noalloc(const fclsh_index *idx, const uint64_t *query, uint32_t radius,
+                                       uint32_t *ids_out, uint64_t cap, uint64_t *counts_out, void *stream);
+
 void fclsh_result_free(fclsh_result *res);
 
 /* ------------------------------------------------------------------ contexts */

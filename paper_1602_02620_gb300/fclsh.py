@@ -82,6 +82,7 @@ SIGNATURES = {
     "fclsh_query": (_i, [_vp, _vp, _u64, _u32, _vp, _vp, _vp]),
     "fclsh_query_plain": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
     "fclsh_bruteforce": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
+    "fclsh_query_plain_noalloc": (_i, [_vp, _vp, _u32, _vp, _u64, _vp, _vp]),
     "fclsh_result_free": (None, [_vp]),
     "fclsh_qctx_create": (_i, [_vp, _vp]),
     "fclsh_qctx_free": (None, [_vp]),
@@ -263,6 +264,11 @@ class Index:
         _check(lib().fclsh_query_plain(self.handle, _ptr(queries), _rows(queries), radius, _stream(stream),
                                        ctypes.byref(rp)))
         return _take_result(rp)
+
+    def query_plain_noalloc(self, query, radius: int, ids_out, counts_out, stream=None):
+        """One query without allocating (device query, device outputs); asynchronous on `stream`."""
+        _check(lib().fclsh_query_plain_noalloc(self.handle, _ptr(query), radius, _ptr(ids_out), ids_out.shape[0],
+                                               _ptr(counts_out), _stream(stream)))
 
     def bruteforce(self, queries, radius: int, stream=None) -> QueryResult:
         rp = ctypes.POINTER(Result)()
