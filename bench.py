@@ -127,6 +127,55 @@ def cpu_baseline(w, budget_s: float = 12.0):
             "points_hashed_per_s": 1.0 / th, "linear_scan_queries_per_s": 1.0 / tq}
 
 
+def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: float = 1e6):
+    """Continuous batching on the resident index: a Poisson stream of requests of
+    U{1..4096} queries with radii in {r/4, r/2, 3r/4, r} (rounded), offered at `load`
+    times the batched throughput; then the same requests one at a time."""
+    import threading
+
+    rng = np.random.default_rng(7)
+    sizes = rng.integers(1, 4097, size=n_req)
+    radii_set = sorted({max(1, round(w.r * f)) for f in (0.25, 0.5, 0.75, 1.0)})
+    radii = rng.choice(radii_set, size=n_req)
+    rate = load * batched_qps / float(sizes.mean())
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    nq = w.queries.shape[0]
+    starts = rng.integers(0, max(1, nq - 4096), size=n_req)
+    blocks = [w.queries[int(a):int(a) + int(z)] for a, z in zip(starts, sizes)]
+    srv = fclsh.Server(idx, slots=4, max_batch_queries=16384)
+    tickets = [None] * n_req
+
+    def feed():
+        t0 = time.perf_counter()
+        at = 0.0
+        for i in range(n_req):
+            at += gaps[i]
+            dt = t0 + at - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(blocks[i], int(radii[i]))
+
+    th = threading.Thread(target=feed)
+    th.start()
+    th.join()
+    for t in tickets:
+        srv.wait(t)
+    st = srv.stats()
+    srv.close()
+    one = fclsh.Server(idx, slots=1, max_batch_queries=1)
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        one.wait(one.submit(blocks[i], int(radii[i])))
+    el = time.perf_counter() - t0
+    st1 = one.stats()
+    one.close()
+    return {"requests": n_req, "offered_requests_per_s": rate, "radii": radii_set,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "queries_per_s": st["queries_per_s"],
+            "mean_batch_queries": st["mean_batch_queries"], "batches": st["batches"],
+            "one_at_a_time_queries_per_s": float(sizes.sum()) / el,
+            "one_at_a_time_p50_ms": st1["p50_ms"], "one_at_a_time_p99_ms": st1["p99_ms"]}
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -184,8 +233,15 @@ def main():
     pts = torch.from_numpy(w.points.view(np.int64)).cuda()
     qs = torch.from_numpy(w.queries.view(np.int64)).cuda()
 
+    # kernel shapes for this workload: autotuned once on a sample batch (cached)
+    cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
+    idx0 = fclsh.build(pts, w.d, w.r, seed)
+    tuned = idx0.autotune(qs[: min(nq, 4096)], w.r, cache)
+    idx0.free()
+
     def step(timing: bool):
         idx = fclsh.build(pts, w.d, w.r, seed, timing=timing)
+        idx.set_tuning(**tuned)
         idx.timing_enable(False)          # the query batch runs as a replayed CUDA graph
         ctx = idx.context()
         ctx.query_async(qs, w.r)
@@ -231,6 +287,7 @@ def main():
 
     # ---- query phase alone (index resident), batched vs plain vs brute force
     idx = fclsh.build(pts, w.d, w.r, seed)
+    idx.set_tuning(**tuned)
     ctx = idx.context()
     for _ in range(3):
         ctx.query_async(qs, w.r)
@@ -268,6 +325,7 @@ def main():
     brute_qps = nq / (time.perf_counter() - t0)
     assert np.array_equal(brute.ids, res.ids) and np.array_equal(brute.offs, res.offs), "brute force differs"
     T = idx.T
+    serve = served(fclsh, idx, w, batched_qps=batched_qps)
     idx.free()
 
     # ---- e2e through the C ABI from pinned host buffers
@@ -279,6 +337,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         idx2 = fclsh.build(hp, w.d, w.r, seed)
+        idx2.set_tuning(**tuned)
         r2 = idx2.query(hq, w.r)
         e2e_t.append(time.perf_counter() - t0)
         d2h = r2.offs.nbytes + r2.ids.nbytes + r2.collisions.nbytes + r2.candidates.nbytes
@@ -309,7 +368,9 @@ def main():
             "plain_queries_per_s": plain_qps, "plain_sample": ns,
             "bruteforce_queries_per_s": brute_qps,
             "results_per_step": total,
+            "tuning": tuned,
         },
+        "served": serve,
         "roofline": {"kernel": "hash_tile_kernel<9> (Algorithm 2, all 511 keys per point)", "bound": "hbm",
                      "achieved": ach, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
                      "traffic": None, "bytes_per_launch": hash_bytes},

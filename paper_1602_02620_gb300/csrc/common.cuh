@@ -16,7 +16,7 @@ namespace fclsh {
 constexpr uint64_t kP = (1ULL << 50) - 27;
 constexpr uint64_t kMask50 = (1ULL << 50) - 1;
 constexpr int kMaxLogW = 11;          // W = 2^(r'+1) <= 2048
-constexpr int kSortTile = 4096;       // radix-sort items per tile (256 threads x 16)
+constexpr int kSortTile = 2048;       // radix-sort items per tile (256 threads x 8)
 constexpr int kSortThreads = 256;
 
 // x mod P for x < 2^63, by 2^50 == 27 (mod P).

@@ -53,11 +53,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(RadixArgs a)
     const uint64_t len = row_len(a);
     const uint64_t *K = a.keys_in + (uint64_t)row * a.len;
     const uint64_t base = (uint64_t)tile * kSortTile;
-#pragma unroll 4
-    for (int i = 0; i < kIPT; ++i) {
+    uint32_t dg[kIPT];
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {   // all loads in flight before the shared-memory counts
         const uint64_t idx = base + (uint64_t)i * kSortThreads + tid;
-        if (idx < len) atomicAdd(&cnt[(uint32_t)(K[idx] >> a.shift) & a.dmask], 1u);
+        dg[i] = idx < len ? ((uint32_t)(K[idx] >> a.shift) & a.dmask) : 0xFFFFFFFFu;
     }
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i)
+        if (dg[i] != 0xFFFFFFFFu) atomicAdd(&cnt[dg[i]], 1u);
     __syncthreads();
     a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile] = cnt[tid];
 }
@@ -65,24 +69,30 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(RadixArgs a)
 template <typename T>
 __device__ __forceinline__ T block_excl_scan(T v, T *total);
 
-// Stable scatter of one tile.  Ranks come from warp match + per-warp digit counts
-// (tile items are taken in index order: round, warp, lane); each item first goes
-// to its digit-sorted slot in shared memory, then the tile's digit runs are
+// Stable scatter of one tile (warp-level multisplit).  Warp w owns the tile's
+// items [w*512, (w+1)*512), taken in rounds of 32 in index order: a warp match
+// gives each item its rank among equal digits in the round, and a warp-private
+// counter per digit carries the rank across rounds (no block barrier).  One
+// block-wide prefix over (digit, warp) then fixes every item's place in the
+// tile's digit-sorted order in shared memory, and the tile's digit runs are
 // written out as contiguous, coalesced runs.
 template <bool IDS, bool IMPLICIT>
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(RadixArgs a)
+__global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArgs a)
 {
+    constexpr int R = kIPT;   // rounds per warp: 8 x 32 = 256 items
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kSortTile]
-    uint32_t *si = reinterpret_cast<uint32_t *>(sk + kSortTile);  // [kSortTile] when IDS
-    __shared__ uint32_t local_start[256], global_off[256], run[256];
-    __shared__ uint32_t warp_cnt[kWarps][256];
-    __shared__ uint32_t warp_pre[kWarps][256];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kSortTile] keys in digit order
+    uint32_t *sg = reinterpret_cast<uint32_t *>(sk + kSortTile);  // [kSortTile] their global positions
+    uint32_t *si = sg + kSortTile;                                // [kSortTile] ids, when IDS
+    __shared__ uint32_t local_start[256], global_off[256];
+    __shared__ uint32_t warp_hist[kWarps][256];                   // counts, then each warp's base
     const uint32_t row = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
     const uint64_t len = row_len(a);
     const uint64_t base = (uint64_t)tile * kSortTile;
     if (base >= len) return;   // uniform: an empty tile has no items
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) warp_hist[w][tid] = 0;
     {
         // this tile's count of digit tid, from the scanned (row, digit, tile) prefix
         const uint64_t idx = ((uint64_t)row * 256 + tid) * a.tiles + tile;
@@ -91,55 +101,63 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(RadixArgs a
         const uint32_t g1 = idx + 1 < hcount ? a.hist[idx + 1] : (uint32_t)((uint64_t)(a.rows - 1) * a.len + len);
         global_off[tid] = g0;
         uint32_t tot;
-        const uint32_t ls = block_excl_scan<uint32_t>(g1 - g0, &tot);
-        local_start[tid] = ls;
-        run[tid] = ls;
+        local_start[tid] = block_excl_scan<uint32_t>(g1 - g0, &tot);   // ends with a barrier
     }
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) warp_cnt[w][tid] = 0;
-    __syncthreads();
     const uint64_t *K = a.keys_in + (uint64_t)row * a.len;
     const uint32_t *I = IMPLICIT ? nullptr : a.ids_in + (uint64_t)row * a.len;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int r = 0; r < kIPT; ++r) {
-        const uint64_t idx = base + (uint64_t)r * kSortThreads + tid;
-        const bool valid = idx < len;
-        uint64_t key = 0;
-        uint32_t id = 0;
-        if (valid) {
-            key = K[idx];
-            if (IDS) id = IMPLICIT ? (uint32_t)idx : I[idx];
-        }
-        const uint32_t digit = valid ? ((uint32_t)(key >> a.shift) & a.dmask) : (256u + lane);
-        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
-        const uint32_t rank = __popc(peers & lt_mask);
-        if (valid && (peers & lt_mask) == 0) warp_cnt[warp][digit] = __popc(peers);
-        __syncthreads();
-        {   // thread tid owns digit tid: prefix over warps, advance the digit's local run
-            uint32_t rc = run[tid];
+    const uint64_t wbase = base + (uint64_t)warp * (32 * R);
+    // every load of the warp's sub-tile is issued before the ranking loop, whose
+    // __syncwarp()s would otherwise keep the next round's load from being hoisted
+    uint64_t key[R];
+    uint32_t id[R];
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t c = warp_cnt[w][tid];
-                warp_pre[w][tid] = rc;
-                rc += c;
-                warp_cnt[w][tid] = 0;
-            }
-            run[tid] = rc;
+    for (int r = 0; r < R; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        key[r] = idx < len ? K[idx] : 0;
+        if (IDS) id[r] = IMPLICIT ? (uint32_t)idx : (idx < len ? I[idx] : 0u);
+    }
+    uint32_t lr[R];
+    uint32_t *wh = warp_hist[warp];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        const bool valid = idx < len;
+        const uint32_t digit = valid ? ((uint32_t)(key[r] >> a.shift) & a.dmask) : (256u + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t before = valid ? wh[digit] : 0u;
+        lr[r] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0) wh[digit] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // thread tid owns digit tid: each warp's first place for that digit
+        uint32_t run = local_start[tid];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = warp_hist[w][tid];
+            warp_hist[w][tid] = run;
+            run += c;
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t lp = warp_pre[warp][digit] + rank;
-            sk[lp] = key;
-            if (IDS) si[lp] = id;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        if (idx < len) {
+            const uint32_t digit = (uint32_t)(key[r] >> a.shift) & a.dmask;
+            const uint32_t lp = wh[digit] + lr[r];
+            sk[lp] = key[r];
+            sg[lp] = global_off[digit] + (lp - local_start[digit]);
+            if (IDS) si[lp] = id[r];
         }
     }
     __syncthreads();
     const uint32_t tile_n = (uint32_t)((len - base) < (uint64_t)kSortTile ? (len - base) : (uint64_t)kSortTile);
     for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
-        const uint64_t key = sk[i];
-        const uint32_t d = (uint32_t)(key >> a.shift) & a.dmask;
-        const uint64_t g = (uint64_t)global_off[d] + (i - local_start[d]);
-        a.keys_out[g] = key;
+        const uint32_t g = sg[i];
+        a.keys_out[g] = sk[i];
         if (IDS) a.ids_out[g] = si[i];
     }
 }
@@ -278,8 +296,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restric
 
 }  // namespace
 
-constexpr size_t kScatterSmemIds = (size_t)kSortTile * 12;
-constexpr size_t kScatterSmemKeys = (size_t)kSortTile * 8;
+constexpr size_t kScatterSmemIds = (size_t)kSortTile * 16;
+constexpr size_t kScatterSmemKeys = (size_t)kSortTile * 12;
 
 // The scatter kernels use more than 48 KB of shared memory; raise their limit once.
 static cudaError_t scatter_smem_init()
