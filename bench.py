@@ -61,10 +61,14 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:   # sampler running before the timed region
+                time.sleep(0.01)
+            self.lines.clear()
         except Exception:
             self.proc = None
 
@@ -201,7 +205,7 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fclsh")
     ap.add_argument("--plain-sample", type=int, default=300)
@@ -263,14 +267,16 @@ def main():
     l0 = fclsh.kernel_launches()
     torch.cuda.synchronize()
     ev0.record()
-    hash_ms = sort_ms = 0.0
-    hash_n = 0
+    acc = {}
     total = 0
     for _ in range(args.steps):
         t, total, info = step(True)
-        hash_ms += t["build_hash"][0]
-        hash_n += t["build_hash"][1]
-        sort_ms += t["build_sort"][0]
+        for k in ("build_hash", "build_sort", "build_partition", "build_finish"):
+            a = acc.setdefault(k, [0.0, 0])
+            a[0] += t[k][0]
+            a[1] += t[k][1]
+    hash_ms, hash_n = acc["build_hash"]
+    sort_ms = acc["build_sort"][0]
     ev1.record()
     torch.cuda.synchronize()
     launches = fclsh.kernel_launches() - l0
@@ -346,11 +352,31 @@ def main():
     e2e = {"value": nq / statistics.median(e2e_t), "unit": "queries/s",
            "h2d_bytes_per_step": int(w.points.nbytes + w.queries.nbytes), "d2h_bytes_per_step": int(d2h)}
 
-    # ---- roofline of the hash kernel (Algorithm 2 for every point): algorithmic bytes
-    # per launch = n * (d/8 read + 8 bytes per key written for the W-1 tables of the part)
+    # ---- rooflines (HBM) of the build's kernels, from the CUDA events of the timed steps.
+    # Algorithmic bytes per launch:
+    #   hash (Algorithm 2, one part): n * (d/8 read + 8 B per key for its W-1 tables)
+    #   partition (histogram + scan + scatter): per entry 8 B read twice + 8 B packed write
+    #   segment finish: per entry 8 B read + 8 B written, plus 4 B per directory slot
     peak, peak_kind = peaks()
     hash_avg = hash_ms / max(hash_n, 1)
-    hash_bytes = w.n * (w.d / 8 + 8 * (info["W"] - 1))
+    L = info["W"] - 1
+    entries = w.n * L
+    slots = L * ((1 << info["slot_bits"]) + 1)
+    stages = {
+        "hash_tile_kernel (Algorithm 2, all W-1 keys per point)": (acc["build_hash"], w.n * (w.d / 8 + 8 * L)),
+        "partition pass (radix_hist + scan + radix_scatter, top 8 slot bits)": (acc["build_partition"], 24 * entries),
+        "segment finish (segment_one_kernel + segment_finish_kernel)": (acc["build_finish"], 16 * entries + 4 * slots),
+    }
+    kernels = []
+    for name, ((ms, cnt), nbytes) in stages.items():
+        if cnt == 0:
+            continue
+        avg = ms / cnt
+        gbs = nbytes / (avg / 1000.0) / 1e9
+        kernels.append({"kernel": name, "total_ms": ms, "launches": cnt, "avg_ms": avg, "bytes_per_launch": nbytes,
+                        "achieved_gbs": gbs, "frac": gbs / peak})
+    dom = max(kernels, key=lambda k: k["total_ms"])
+    hash_bytes = w.n * (w.d / 8 + 8 * L)
     ach = hash_bytes / (hash_avg / 1000.0) / 1e9
     qk_ms, qk_n = tq["query_kernel"]
     line = {
@@ -362,6 +388,7 @@ def main():
                    "l2": "inputs and index larger than L2 (16 MB points -> 4.1 GB keys, 6.1 GB index)"},
         "breakdown": {
             "build_hash_ms": hash_avg, "build_sort_ms": sort_ms / args.steps,
+            "hash_roofline_frac": ach / peak,
             "points_hashed_per_s": w.n / (hash_avg / 1000.0),
             "batched_query_queries_per_s": batched_qps,
             "batched_query_kernel_ms": qk_ms / max(qk_n, 1), "batched_query_csr_ms": tq["query_csr"][0] / max(tq["query_csr"][1], 1),
@@ -371,9 +398,10 @@ def main():
             "tuning": tuned,
         },
         "served": serve,
-        "roofline": {"kernel": "hash_tile_kernel<9> (Algorithm 2, all 511 keys per point)", "bound": "hbm",
-                     "achieved": ach, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
-                     "traffic": None, "bytes_per_launch": hash_bytes},
+        "roofline": {"kernel": dom["kernel"], "bound": "hbm", "achieved": dom["achieved_gbs"], "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac"], "traffic": None,
+                     "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_ms": dom["avg_ms"]},
+        "kernels": kernels,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,

@@ -96,19 +96,65 @@ static uint32_t bits_for(uint64_t v)   // bits needed for values 0..v-1 (at leas
     return b;
 }
 
+// Device memory of the library comes from one stream-ordered pool per device that
+// keeps freed memory (release threshold = all of it), so building indexes and
+// query contexts again and again reuses memory instead of mapping it anew.
+static cudaMemPool_t device_pool(int dev)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {nullptr};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ULL;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return cudaMalloc(p, bytes);
+    e = cudaMallocFromPoolAsync(p, bytes, pool, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);   // usable on any stream from here on
+    return e;
+}
+
+void dev_free(void *p)
+{
+    if (!p) return;
+    cudaFreeAsync(p, 0);
+}
+
 // Device allocation list freed together on error.
 struct DevAllocs {
     std::vector<void *> ptrs;
     ~DevAllocs()
     {
-        for (void *p : ptrs) cudaFree(p);
+        if (!ptrs.empty()) cudaDeviceSynchronize();
+        for (void *p : ptrs) dev_free(p);
     }
     template <typename T>
     cudaError_t alloc(T **p, size_t count)
     {
         *p = nullptr;
         if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+        cudaError_t e = dev_alloc((void **)p, count * sizeof(T));
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }
@@ -240,7 +286,7 @@ static void ctx_free_buffers(fclsh_qctx *c)
     void *ps[] = {c->counters, c->runs, c->run_base, c->res_cnt, c->res_offs,
                   c->res_ids, c->coll, c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf};
     for (void *p : ps)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->own) cudaStreamDestroy(c->own);
 }
@@ -259,10 +305,10 @@ static fclsh_status ctx_shape(fclsh_qctx *c)
     const uint32_t per_sm = std::max(1u, std::min<uint32_t>((uint32_t)occ, tu.query_ctas_per_sm));
     const uint32_t grid = per_sm * (uint32_t)idx->sm_count;
     if (grid != c->grid) {
-        if (c->bitmaps) cudaFree(c->bitmaps);
+        if (c->bitmaps) dev_free(c->bitmaps);
         c->bitmaps = nullptr;
         const uint64_t bm_words = (idx->n + 31) / 32;
-        FCLSH_CUDA(cudaMalloc(&c->bitmaps, (size_t)grid * bm_words * 4));
+        FCLSH_CUDA(dev_alloc((void **)&c->bitmaps, (size_t)grid * bm_words * 4));
         FCLSH_CUDA(cudaMemset(c->bitmaps, 0, (size_t)grid * bm_words * 4));
         c->grid = grid;
     }
@@ -276,19 +322,19 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
     if (nq > c->nq_cap) {
         void *ps[] = {c->res_cnt, c->res_offs, c->coll, c->cand, c->scan_part, c->run_base};
         for (void *p : ps)
-            if (p) cudaFree(p);
+            if (p) dev_free(p);
         c->res_cnt = nullptr;
         c->res_offs = nullptr;
         c->coll = c->cand = nullptr;
         c->scan_part = nullptr;
         c->run_base = nullptr;
         const uint64_t m = std::max<uint64_t>(nq, 1024);
-        FCLSH_CUDA(cudaMalloc(&c->run_base, m * 8));
-        FCLSH_CUDA(cudaMalloc(&c->res_cnt, m * 4));
-        FCLSH_CUDA(cudaMalloc(&c->res_offs, (m + 1) * 8));
-        FCLSH_CUDA(cudaMalloc(&c->coll, m * 8));
-        FCLSH_CUDA(cudaMalloc(&c->cand, m * 8));
-        FCLSH_CUDA(cudaMalloc(&c->scan_part, scan_partials_entries(m) * 8));
+        FCLSH_CUDA(dev_alloc((void **)&c->run_base, m * 8));
+        FCLSH_CUDA(dev_alloc((void **)&c->res_cnt, m * 4));
+        FCLSH_CUDA(dev_alloc((void **)&c->res_offs, (m + 1) * 8));
+        FCLSH_CUDA(dev_alloc((void **)&c->coll, m * 8));
+        FCLSH_CUDA(dev_alloc((void **)&c->cand, m * 8));
+        FCLSH_CUDA(dev_alloc((void **)&c->scan_part, scan_partials_entries(m) * 8));
         c->nq_cap = m;
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -298,11 +344,11 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
     if (cap > c->cap) {
         void *ps[] = {c->runs, c->res_ids};
         for (void *p : ps)
-            if (p) cudaFree(p);
+            if (p) dev_free(p);
         c->runs = nullptr;
         c->res_ids = nullptr;
-        FCLSH_CUDA(cudaMalloc(&c->runs, cap * 4));
-        FCLSH_CUDA(cudaMalloc(&c->res_ids, cap * 4));
+        FCLSH_CUDA(dev_alloc((void **)&c->runs, cap * 4));
+        FCLSH_CUDA(dev_alloc((void **)&c->res_ids, cap * 4));
         c->cap = cap;
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -511,19 +557,29 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     FCLSH_CUDA(cudaMemGetInfo(&free_b, &total_b));
     const uint64_t budget = o.mem_budget ? o.mem_budget : free_b / 4;
     // radix-sort buffers for a chunk of tables: (key, id) twice, plus histograms
-    const uint64_t per_row = n * 24 + sort_hist_entries(1, n) * 4 + 64;
+    const bool msd = msd_path_applies(sb);
+    // per table: the partition pass's packed entries (MSD) or two (key, id) buffers (LSD), plus histograms
+    const uint64_t per_row = n * (msd ? 8 : 24) + sort_hist_entries(1, n) * 4 + 64;
     uint64_t rows = std::max<uint64_t>(1, budget / per_row);
     rows = std::min<uint64_t>(rows, L);
     rows = std::min<uint64_t>(rows, std::max<uint64_t>(1, 0xFFFFFFF0ULL / n));
     SortBuffers sbuf{};
     if ((e = tmp.alloc(&sbuf.keys_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
-    if ((e = tmp.alloc(&sbuf.keys_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
-    if ((e = tmp.alloc(&sbuf.ids_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
-    if ((e = tmp.alloc(&sbuf.ids_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
+    if (!msd) {
+        if ((e = tmp.alloc(&sbuf.keys_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
+        if ((e = tmp.alloc(&sbuf.ids_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
+        if ((e = tmp.alloc(&sbuf.ids_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
+    }
     sbuf.hist_cap = sort_hist_entries((uint32_t)rows, n);
     sbuf.partials_cap = scan_partials_entries(sbuf.hist_cap);
     if ((e = tmp.alloc(&sbuf.hist, sbuf.hist_cap)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort hist)");
     if ((e = tmp.alloc(&sbuf.partials, sbuf.partials_cap)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort scan)");
+    unsigned long long *big_cnt = nullptr;
+    uint32_t *big = nullptr;
+    if (msd) {
+        if ((e = tmp.alloc(&big_cnt, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment list)");
+        if ((e = tmp.alloc(&big, rows * 256)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment list)");
+    }
 
     for (uint32_t k = 0; k < t; ++k) {
         {
@@ -533,9 +589,19 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         PhaseTimer pt(idx, 1, s);
         for (uint64_t r0 = 0; r0 < L; r0 += rows) {
             const uint32_t nr = (uint32_t)std::min<uint64_t>(rows, L - r0);
+            const uint64_t grow = (uint64_t)k * L + r0;
+            if (msd) {
+                {
+                    PhaseTimer p5(idx, 5, s);
+                    FCLSH_CUDA(msd_partition(keys + r0 * n, nr, n, sb, sbuf, s));
+                }
+                PhaseTimer p6(idx, 6, s);
+                FCLSH_CUDA(msd_finish(nr, n, sb, sbuf, big_cnt, big, idx->ent + grow * n,
+                                      idx->offs + grow * idx->offs_stride(), idx->sm_count, s));
+                continue;
+            }
             bool in_b = false;
             FCLSH_CUDA(radix_sort_rows(keys + r0 * n, nr, n, sb, sbuf, &in_b, s));
-            const uint64_t grow = (uint64_t)k * L + r0;
             FCLSH_CUDA(launch_finalize_rows(in_b ? sbuf.keys_b : sbuf.keys_a, in_b ? sbuf.ids_b : sbuf.ids_a, nr, n, sb,
                                             idx->ent + grow * n, idx->offs + grow * idx->offs_stride(), s));
         }
@@ -555,7 +621,7 @@ extern "C" void fclsh_free(fclsh_index *idx)
     drop_timers(idx);
     void *ps[] = {idx->points, idx->col_off, idx->col_coord, idx->col_b, idx->offs, idx->ent};
     for (void *p : ps)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     delete idx;
 }
 
@@ -680,7 +746,7 @@ extern "C" fclsh_status fclsh_qctx_create(fclsh_index *idx, fclsh_qctx **out)
     fclsh_qctx *c = new fclsh_qctx();
     c->idx = idx;
     fclsh_status st = FCLSH_OK;
-    cudaError_t e = cudaMalloc(&c->counters, 2 * sizeof(unsigned long long));
+    cudaError_t e = dev_alloc((void **)&c->counters, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(counters)");
     if (st == FCLSH_OK && (e = cudaStreamCreate(&c->own)) != cudaSuccess)
         st = cuda_fail(e, "cudaStreamCreate");
@@ -829,9 +895,9 @@ static fclsh_status stage_inputs(fclsh_qctx *c, const uint64_t *queries, uint64_
     *dr = radii;
     if (nq && !is_device_ptr(queries)) {
         if (nq * idx->words > c->qbuf_cap) {
-            if (c->qbuf) cudaFree(c->qbuf);
+            if (c->qbuf) dev_free(c->qbuf);
             c->qbuf = nullptr;
-            FCLSH_CUDA(cudaMalloc(&c->qbuf, nq * idx->words * 8));
+            FCLSH_CUDA(dev_alloc((void **)&c->qbuf, nq * idx->words * 8));
             c->qbuf_cap = nq * idx->words;
         }
         FCLSH_CUDA(cudaMemcpyAsync(c->qbuf, queries, nq * idx->words * 8, cudaMemcpyHostToDevice, s));
@@ -842,9 +908,9 @@ static fclsh_status stage_inputs(fclsh_qctx *c, const uint64_t *queries, uint64_
             if (radii[i] > idx->r) return fail(FCLSH_ERADIUS, "radius %u of query %llu exceeds the build radius %u",
                                               radii[i], (unsigned long long)i, idx->r);
         if (nq > c->rbuf_cap) {
-            if (c->rbuf) cudaFree(c->rbuf);
+            if (c->rbuf) dev_free(c->rbuf);
             c->rbuf = nullptr;
-            FCLSH_CUDA(cudaMalloc(&c->rbuf, nq * 4));
+            FCLSH_CUDA(dev_alloc((void **)&c->rbuf, nq * 4));
             c->rbuf_cap = nq;
         }
         FCLSH_CUDA(cudaMemcpyAsync(c->rbuf, radii, nq * 4, cudaMemcpyHostToDevice, s));

@@ -161,6 +161,17 @@ cudaError_t radix_sort_keys_dev(uint64_t *keys_a, uint64_t *keys_b, const unsign
                                 uint64_t cap, uint32_t bits, uint32_t *hist, uint32_t *partials,
                                 bool *out_in_b, cudaStream_t s);
 size_t sort_keys_hist_entries(uint64_t cap);
+// Directory of `rows` tables straight from their keys when slot_bits - 8 <= 12: one
+// stable partition by the top 8 slot bits, then one block per (segment, table) that
+// orders the segment by the remaining slot bits in shared memory and writes the
+// directory and the entries (the same layout as radix_sort_rows + finalize).
+// msd_partition packs the partition into buf.keys_a (hist in buf.hist); msd_finish
+// needs big_cnt [1] and big [rows * 256] of scratch for segments longer than 4096.
+bool msd_path_applies(uint32_t slot_bits);
+cudaError_t msd_partition(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
+                          cudaStream_t s);
+cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf, unsigned long long *big_cnt,
+                       uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count, cudaStream_t s);
 // Directory of each sorted row: ent = (key >> sb) << 32 | id, offs[slot] = first entry of slot.
 cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint32_t rows, uint64_t len,
                                  uint32_t slot_bits, uint64_t *ent, uint32_t *offs, cudaStream_t s);

@@ -33,7 +33,19 @@ struct RadixArgs {
     uint32_t dmask;               // digit = (key >> shift) & dmask: the last pass may have fewer than 8 bits
     uint32_t *hist;               // [rows][256][tiles]
     uint32_t rows;
+    uint32_t pack_sb;             // PACK: slot bits of the directory
+    uint32_t pack_idbits;         // PACK: bits of an id
 };
+
+// Packed partition output for the MSD directory path:
+//   bits [52, 52+sub)   the slot's low sub = sb-8 <= 12 bits
+//   bits [idbits, 52)   the key's high bits key >> sb (50-sb bits)
+//   bits [0, idbits)    the id
+__device__ __forceinline__ uint64_t pack_entry(uint64_t key, uint32_t id, uint32_t sb, uint32_t idbits)
+{
+    const uint64_t sub = key & ((1ULL << (sb - 8)) - 1);
+    return (sub << 52) | ((key >> sb) << idbits) | id;
+}
 
 __device__ __forceinline__ uint64_t row_len(const RadixArgs &a)
 {
@@ -76,7 +88,7 @@ __device__ __forceinline__ T block_excl_scan(T v, T *total);
 // block-wide prefix over (digit, warp) then fixes every item's place in the
 // tile's digit-sorted order in shared memory, and the tile's digit runs are
 // written out as contiguous, coalesced runs.
-template <bool IDS, bool IMPLICIT>
+template <bool IDS, bool IMPLICIT, bool PACK = false>
 __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArgs a)
 {
     constexpr int R = kIPT;   // rounds per warp: 8 x 32 = 256 items
@@ -157,8 +169,12 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArg
     const uint32_t tile_n = (uint32_t)((len - base) < (uint64_t)kSortTile ? (len - base) : (uint64_t)kSortTile);
     for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
         const uint32_t g = sg[i];
-        a.keys_out[g] = sk[i];
-        if (IDS) a.ids_out[g] = si[i];
+        if (PACK) {
+            a.keys_out[g] = pack_entry(sk[i], si[i], a.pack_sb, a.pack_idbits);
+        } else {
+            a.keys_out[g] = sk[i];
+            if (IDS) a.ids_out[g] = si[i];
+        }
     }
 }
 
@@ -294,6 +310,310 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restric
 }
 
 
+
+// ---------------------------------------------------------------- directory, second half (MSD path)
+
+constexpr int kSegThreads = 512;
+constexpr int kSegItems = 8;                          // per thread per chunk
+constexpr int kSegChunk = kSegThreads * kSegItems;    // 4096 entries
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSubMaxBits = 12;                       // slot bits below the partition digit
+
+// Stable warp-multisplit ranking of 8 items per lane by a digit < 64: returns
+// each item's position in the chunk's digit-sorted order (chunk items are taken
+// warp by warp, round by round, in index order).
+__device__ __forceinline__ void seg_rank(const uint32_t (&dig)[kSegItems], uint32_t nvalid_warp_base, uint32_t cn,
+                                         uint32_t (&pos)[kSegItems], uint32_t *wh /*[kSegWarps][64]*/,
+                                         uint32_t *dstart /*[64]*/)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t i = tid; i < kSegWarps * 64; i += kSegThreads) wh[i] = 0;
+    __syncthreads();
+    uint32_t *w = wh + warp * 64;
+#pragma unroll
+    for (int r = 0; r < kSegItems; ++r) {
+        const uint32_t idx = nvalid_warp_base + r * 32 + lane;
+        const bool valid = idx < cn;
+        const uint32_t d = valid ? dig[r] : 64u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? w[d] : 0u;
+        pos[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) w[d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (tid < 64) {   // digit tid: chunk-wide start, then each warp's base
+        uint32_t tot = 0;
+        for (int v = 0; v < kSegWarps; ++v) tot += wh[v * 64 + tid];
+        dstart[tid] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int d = 0; d < 64; ++d) {
+            const uint32_t c = dstart[d];
+            dstart[d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (tid < 64) {
+        uint32_t run = dstart[tid];
+        for (int v = 0; v < kSegWarps; ++v) {
+            const uint32_t c = wh[v * 64 + tid];
+            wh[v * 64 + tid] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSegItems; ++r) {
+        const uint32_t idx = nvalid_warp_base + r * 32 + lane;
+        if (idx < cn) pos[r] += w[dig[r]];
+    }
+}
+
+// Exclusive scan in place of v[0..cnt) (cnt <= 4096) by the whole block; optionally
+// also writes out[j] = base + prefix.
+__device__ __forceinline__ void seg_scan(uint32_t *v, uint32_t cnt, uint32_t *wsum, uint32_t *out, uint32_t base)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t per = (cnt + kSegThreads - 1) / kSegThreads;
+    const uint32_t j0 = tid * per;
+    uint32_t loc = 0;
+    for (uint32_t j = j0; j < j0 + per && j < cnt; ++j) loc += v[j];
+    uint32_t incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += u;
+    }
+    __syncthreads();
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - loc;
+    for (uint32_t w = 0; w < warp; ++w) run += wsum[w];
+    for (uint32_t j = j0; j < j0 + per && j < cnt; ++j) {
+        const uint32_t c = v[j];
+        v[j] = run;
+        if (out) out[j] = base + run;
+        run += c;
+    }
+    __syncthreads();
+}
+
+constexpr int kOneThreads = 512;
+constexpr int kOneItems = kSegChunk / kOneThreads;   // 8
+
+// Padded index of per-slot counters: one spare word every 32 keeps a thread's run
+// of consecutive counters (the scans below) off its neighbours' banks.
+__device__ __forceinline__ uint32_t pj(uint32_t j) { return j + (j >> 5); }
+
+// Segment boundaries of the partition: [lo, hi) within row `row` for top digit g.
+__device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t tiles, uint64_t n, uint32_t row,
+                                              uint32_t g, uint64_t *lo, uint64_t *hi)
+{
+    const uint64_t rowbase = (uint64_t)row * n;
+    *lo = hist[((uint64_t)row * 256 + g) * tiles] - rowbase;
+    *hi = g < 255 ? hist[((uint64_t)row * 256 + g + 1) * tiles] - rowbase : n;
+}
+
+// Exclusive scan in place of v[0..cnt) by a 256-thread block; also writes out[j] = base + prefix.
+__device__ __forceinline__ void one_scan(uint32_t *v, uint32_t cnt, uint32_t *wsum, uint32_t *out, uint32_t base)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t per = (cnt + kOneThreads - 1) / kOneThreads;
+    const uint32_t j0 = tid * per;
+    uint32_t loc = 0;
+    for (uint32_t j = j0; j < j0 + per && j < cnt; ++j) loc += v[pj(j)];
+    uint32_t incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - loc;
+    for (uint32_t w = 0; w < warp; ++w) run += wsum[w];
+    for (uint32_t j = j0; j < j0 + per && j < cnt; ++j) {
+        const uint32_t c = v[pj(j)];
+        v[pj(j)] = run;
+        out[j] = base + run;
+        run += c;
+    }
+    __syncthreads();
+}
+
+// One block per (segment, table) for segments of at most one chunk (4096 entries,
+// the common case): the packed entries are placed by shared-memory counters and
+// each slot's run is then ordered by (key bits, id), giving the directory of the
+// segment's 2^sub slots and its entries.  Larger segments are listed for
+// segment_finish_kernel.
+__global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
+                                                                     uint32_t sb, uint32_t idbits,
+                                                                     const uint32_t *__restrict__ hist, uint32_t tiles,
+                                                                     uint64_t *__restrict__ ent,
+                                                                     uint32_t *__restrict__ offs,
+                                                                     unsigned long long *big_cnt, uint32_t *big)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *ck = reinterpret_cast<uint64_t *>(smem_raw);             // [kSegChunk]
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(ck + kSegChunk);       // [nsub + 1]
+    __shared__ uint32_t wsum[32];
+    const uint32_t g = blockIdx.x, row = blockIdx.y, tid = threadIdx.x;
+    const uint32_t subb = sb - 8, nsub = 1u << subb, smask = nsub - 1;
+    const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
+    uint64_t lo, hi;
+    segment_range(hist, tiles, n, row, g, &lo, &hi);
+    const uint64_t len = hi - lo;
+    if (len > (uint64_t)kSegChunk) {
+        if (tid == 0) big[atomicAdd(big_cnt, 1ULL)] = row * 256 + g;
+        return;
+    }
+    const uint32_t cn = (uint32_t)len;
+    const uint64_t rowbase = (uint64_t)row * n;
+    const uint64_t *Pk = packed + rowbase + lo;
+    uint64_t *E = ent + rowbase + lo;
+    uint32_t *O = offs + (uint64_t)row * ((1ULL << sb) + 1) + (uint64_t)g * nsub;
+    if (g == 255 && tid == 0) O[nsub] = (uint32_t)n;
+    uint64_t v[kOneItems];
+    uint32_t rk[kOneItems];
+#pragma unroll
+    for (int r = 0; r < kOneItems; ++r) {
+        const uint32_t idx = tid + r * kOneThreads;
+        v[r] = idx < cn ? Pk[idx] : 0;
+    }
+    for (uint32_t j = tid; j < nsub; j += kOneThreads) cnt[pj(j)] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kOneItems; ++r)
+        if (tid + r * kOneThreads < cn) rk[r] = atomicAdd(&cnt[pj((uint32_t)(v[r] >> 52) & smask)], 1u);
+    if (tid == 0) cnt[pj(nsub)] = cn;
+    __syncthreads();
+    one_scan(cnt, nsub, wsum, O, (uint32_t)lo);   // cnt[j] = first entry of slot j
+#pragma unroll
+    for (int r = 0; r < kOneItems; ++r)
+        if (tid + r * kOneThreads < cn) ck[cnt[pj((uint32_t)(v[r] >> 52) & smask)] + rk[r]] = v[r];
+    __syncthreads();
+    for (uint32_t j = tid; j < nsub; j += kOneThreads) {   // order each slot's run (usually 0-3 entries)
+        const uint32_t a0 = cnt[pj(j)], a1 = cnt[pj(j + 1)];
+        for (uint32_t x = a0 + 1; x < a1; ++x) {
+            const uint64_t cur = ck[x];
+            uint32_t y = x;
+            while (y > a0 && (ck[y - 1] & low52) > (cur & low52)) {
+                ck[y] = ck[y - 1];
+                --y;
+            }
+            ck[y] = cur;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < cn; i += kOneThreads) {
+        const uint64_t x = ck[i];
+        E[i] = ((x & low52) >> idbits) << 32 | (x & idmask);
+    }
+}
+
+// Segments longer than one chunk (listed by segment_one_kernel; clustered or
+// duplicate-heavy data): one block per listed segment writes its directory and
+// entries chunk by chunk, each chunk through two stable shared-memory digit
+// passes, so slot runs of any length stay in id order.
+__global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const uint64_t *__restrict__ packed,
+                                                                        uint64_t n, uint32_t sb, uint32_t idbits,
+                                                                        const uint32_t *__restrict__ hist,
+                                                                        uint32_t tiles, uint64_t *__restrict__ ent,
+                                                                        uint32_t *__restrict__ offs,
+                                                                        const unsigned long long *big_cnt,
+                                                                        const uint32_t *big)
+{
+  const unsigned long long nbig = *big_cnt;
+  for (unsigned long long bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *ck = reinterpret_cast<uint64_t *>(smem_raw);                  // [kSegChunk]
+    uint32_t *sub_off = reinterpret_cast<uint32_t *>(ck + kSegChunk);        // [nsub]
+    uint32_t *ccnt = sub_off + (1u << kSubMaxBits);                          // [nsub + 1]
+    uint32_t *wh = ccnt + (1u << kSubMaxBits) + 1;                           // [kSegWarps][64]
+    __shared__ uint32_t dstart[64];
+    __shared__ uint32_t wsum[32];
+    const uint32_t g = big[bi] & 255, row = big[bi] >> 8, tid = threadIdx.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    const uint32_t subb = sb - 8, nsub = 1u << subb, smask = nsub - 1;
+    const uint32_t b1 = subb / 2, m1 = (1u << b1) - 1;
+    const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
+    const uint64_t rowbase = (uint64_t)row * n;
+    const uint64_t seg_lo = hist[((uint64_t)row * 256 + g) * tiles] - rowbase;
+    const uint64_t seg_hi = g < 255 ? hist[((uint64_t)row * 256 + g + 1) * tiles] - rowbase : n;
+    const uint64_t seg_len = seg_hi - seg_lo;
+    const uint64_t *Pk = packed + rowbase + seg_lo;
+    uint64_t *E = ent + rowbase + seg_lo;
+    uint32_t *O = offs + (uint64_t)row * ((1ULL << sb) + 1) + (uint64_t)g * nsub;
+    auto sub_of = [&](uint64_t v) { return (uint32_t)(v >> 52) & smask; };
+    auto ent_of = [&](uint64_t v) { return ((v & low52) >> idbits) << 32 | (v & idmask); };
+    if (g == 255 && tid == 0) O[nsub] = (uint32_t)n;
+
+    // several chunks: per-slot counts of the whole segment first, then stable passes
+    uint32_t *ci = reinterpret_cast<uint32_t *>(wh + kSegWarps * 64);   // unused in this path
+    (void)ci;
+    for (uint32_t j = tid; j < nsub; j += kSegThreads) sub_off[j] = 0;
+    __syncthreads();
+    for (uint64_t e = tid; e < seg_len; e += kSegThreads) atomicAdd(&sub_off[sub_of(Pk[e])], 1u);
+    __syncthreads();
+    seg_scan(sub_off, nsub, wsum, O, (uint32_t)seg_lo);
+    for (uint64_t cs = 0; cs < seg_len; cs += kSegChunk) {
+        const uint32_t cn = (uint32_t)(seg_len - cs < (uint64_t)kSegChunk ? seg_len - cs : (uint64_t)kSegChunk);
+        const uint32_t wb = warp * (32 * kSegItems);
+        uint64_t key[kSegItems];
+        uint32_t dig[kSegItems], pos[kSegItems];
+#pragma unroll
+        for (int r = 0; r < kSegItems; ++r) {
+            const uint32_t idx = wb + r * 32 + lane;
+            key[r] = idx < cn ? Pk[cs + idx] : 0;
+            dig[r] = sub_of(key[r]) & m1;
+        }
+        for (uint32_t j = tid; j < nsub; j += kSegThreads) ccnt[j] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSegItems; ++r)
+            if (wb + r * 32 + lane < cn) atomicAdd(&ccnt[sub_of(key[r])], 1u);
+        seg_rank(dig, wb, cn, pos, wh, dstart);            // pass 1: low b1 bits of the slot
+#pragma unroll
+        for (int r = 0; r < kSegItems; ++r)
+            if (wb + r * 32 + lane < cn) ck[pos[r]] = key[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSegItems; ++r) {
+            const uint32_t idx = wb + r * 32 + lane;
+            key[r] = idx < cn ? ck[idx] : 0;
+            dig[r] = sub_of(key[r]) >> b1;
+        }
+        seg_rank(dig, wb, cn, pos, wh, dstart);            // pass 2: remaining slot bits
+#pragma unroll
+        for (int r = 0; r < kSegItems; ++r)
+            if (wb + r * 32 + lane < cn) ck[pos[r]] = key[r];
+        seg_scan(ccnt, nsub, wsum, nullptr, 0);             // chunk-relative start of each slot
+        for (uint32_t i = tid; i < cn; i += kSegThreads) {
+            const uint64_t k = ck[i];
+            const uint32_t j = sub_of(k);
+            E[sub_off[j] + (i - ccnt[j])] = ent_of(k);
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < cn; i += kSegThreads) {   // advance each slot by its run in this chunk
+            const uint32_t j = sub_of(ck[i]);
+            if (i == ccnt[j]) {
+                uint32_t c = 1;
+                while (i + c < cn && sub_of(ck[i + c]) == j) ++c;
+                sub_off[j] += c;
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 constexpr size_t kScatterSmemIds = (size_t)kSortTile * 16;
@@ -311,6 +631,9 @@ static cudaError_t scatter_smem_init()
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(radix_scatter_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kScatterSmemKeys);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(radix_scatter_kernel<true, true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmemIds);
         return e;
     }();
     return once;
@@ -399,3 +722,65 @@ cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, u
 
 }  // namespace fclsh
 
+
+namespace fclsh {
+
+size_t segment_finish_smem() { return (size_t)kSegChunk * 8 + ((2u << kSubMaxBits) + 1) * 4 + kSegWarps * 64 * 4; }
+size_t segment_one_smem() { return (size_t)kSegChunk * 8 + ((1u << kSubMaxBits) + (1u << kSubMaxBits) / 32 + 2) * 4; }
+
+bool msd_path_applies(uint32_t slot_bits) { return slot_bits >= 10 && slot_bits - 8 <= (uint32_t)kSubMaxBits; }
+
+static uint32_t id_bits(uint64_t len)
+{
+    uint32_t b = 1;
+    while ((1ULL << b) < len) ++b;
+    return b;
+}
+
+cudaError_t msd_partition(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
+                          cudaStream_t s)
+{
+    cudaError_t e = scatter_smem_init();
+    if (e != cudaSuccess) return e;
+    const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
+    const uint64_t hcount = (uint64_t)rows * 256 * tiles;
+    dim3 grid(tiles, rows);
+    // stable partition of every table by the top 8 slot bits (ids in order), packed output
+    RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - 8, 255u, buf.hist, rows, sb,
+                id_bits(len)};
+    radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a);
+    note_launch();
+    if ((e = scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s)) !=
+        cudaSuccess)
+        return e;
+    radix_scatter_kernel<true, true, true><<<grid, kSortThreads, kScatterSmemIds, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf, unsigned long long *big_cnt,
+                       uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count, cudaStream_t s)
+{
+    static cudaError_t once = [] {
+        cudaError_t e = cudaFuncSetAttribute(segment_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)segment_finish_smem());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(segment_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)segment_one_smem());
+        return e;
+    }();
+    if (once != cudaSuccess) return once;
+    const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
+    const uint32_t idb = id_bits(len);
+    cudaError_t e = cudaMemsetAsync(big_cnt, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    segment_one_kernel<<<dim3(256, rows), kOneThreads, segment_one_smem(), s>>>(buf.keys_a, len, sb, idb, buf.hist,
+                                                                                  tiles, ent, offs, big_cnt, big);
+    note_launch();
+    segment_finish_kernel<<<sm_count, kSegThreads, segment_finish_smem(), s>>>(buf.keys_a, len, sb, idb, buf.hist,
+                                                                                 tiles, ent, offs, big_cnt, big);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace fclsh
