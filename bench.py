@@ -36,6 +36,16 @@ sys.path.insert(0, ROOT)
 METRIC = "queries/s at 100% recall and points hashed/s, batched vs plain on one GB300"
 CFG = 2
 
+# DRAM traffic / algorithmic bytes of each stage, from `ncu --set full` on the same
+# workload at n = 300,000 (profiles/*_n300k_d128_r8.md); traffic scales with the
+# algorithmic bytes.  Set an entry to None when its kernel changes.
+TRAFFIC_RATIO = {
+    "hash": 0.950,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
+    "scatter": 1.017,     # profiles/radix_scatter_kernel_n300k_d128_r8.md
+    "finish": 0.989,      # profiles/segment_one_kernel_n300k_d128_r8.md
+    "hist": None,
+}
+
 
 def peaks():
     try:
@@ -271,7 +281,7 @@ def main():
     total = 0
     for _ in range(args.steps):
         t, total, info = step(True)
-        for k in ("build_hash", "build_sort", "build_partition", "build_finish"):
+        for k in ("build_hash", "build_sort", "build_partition", "build_finish", "build_partition_hist"):
             a = acc.setdefault(k, [0.0, 0])
             a[0] += t[k][0]
             a[1] += t[k][1]
@@ -355,7 +365,8 @@ def main():
     # ---- rooflines (HBM) of the build's kernels, from the CUDA events of the timed steps.
     # Algorithmic bytes per launch:
     #   hash (Algorithm 2, one part): n * (d/8 read + 8 B per key for its W-1 tables)
-    #   partition (histogram + scan + scatter): per entry 8 B read twice + 8 B packed write
+    #   partition scatter (radix_scatter_kernel): per entry 8 B read + 8 B packed write
+    #   partition histogram (radix_hist_kernel + scan): per entry 8 B read
     #   segment finish: per entry 8 B read + 8 B written, plus 4 B per directory slot
     peak, peak_kind = peaks()
     hash_avg = hash_ms / max(hash_n, 1)
@@ -363,18 +374,24 @@ def main():
     entries = w.n * L
     slots = L * ((1 << info["slot_bits"]) + 1)
     stages = {
-        "hash_tile_kernel (Algorithm 2, all W-1 keys per point)": (acc["build_hash"], w.n * (w.d / 8 + 8 * L)),
-        "partition pass (radix_hist + scan + radix_scatter, top 8 slot bits)": (acc["build_partition"], 24 * entries),
-        "segment finish (segment_one_kernel + segment_finish_kernel)": (acc["build_finish"], 16 * entries + 4 * slots),
+        "hash_tile_kernel (Algorithm 2, all W-1 keys per point)": (acc["build_hash"], w.n * (w.d / 8 + 8 * L), "hash"),
+        "radix_scatter_kernel (stable partition by the top 8 slot bits, packed output)":
+            (acc["build_partition"], 16 * entries, "scatter"),
+        "radix_hist_kernel + scan (partition histogram)": (acc["build_partition_hist"], 8 * entries, "hist"),
+        "segment finish (segment_one_kernel + segment_finish_kernel)":
+            (acc["build_finish"], 16 * entries + 4 * slots, "finish"),
     }
+    full_size = args.n is None
     kernels = []
-    for name, ((ms, cnt), nbytes) in stages.items():
+    for name, ((ms, cnt), nbytes, tag) in stages.items():
         if cnt == 0:
             continue
         avg = ms / cnt
         gbs = nbytes / (avg / 1000.0) / 1e9
+        ratio = TRAFFIC_RATIO.get(tag) if full_size else None
         kernels.append({"kernel": name, "total_ms": ms, "launches": cnt, "avg_ms": avg, "bytes_per_launch": nbytes,
-                        "achieved_gbs": gbs, "frac": gbs / peak})
+                        "achieved_gbs": gbs, "frac": gbs / peak,
+                        "traffic": int(ratio * nbytes) if ratio else None})
     dom = max(kernels, key=lambda k: k["total_ms"])
     hash_bytes = w.n * (w.d / 8 + 8 * L)
     ach = hash_bytes / (hash_avg / 1000.0) / 1e9
@@ -399,7 +416,7 @@ def main():
         },
         "served": serve,
         "roofline": {"kernel": dom["kernel"], "bound": "hbm", "achieved": dom["achieved_gbs"], "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac"], "traffic": None,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac"], "traffic": dom["traffic"],
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_ms": dom["avg_ms"]},
         "kernels": kernels,
         "gpu_launches": int(launches),

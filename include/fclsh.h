@@ -304,10 +304,9 @@ fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries, uint64_t 
  * Per-phase device time (milliseconds, CUDA events on the launching stream)
  * accumulated since the last reset: [0] build hash kernel, [1] build sort and
  * directory kernels (all of them), [2] batched query kernel, [3] result CSR,
- * [4] fclsh_hash kernel, [5] build partition pass (part of [1]), [6] build
- * segment-finish kernels (part of [1]).  counts[i] = timed launches of phase i.  ms[7] is
- * unused; counts[7] = kernels this library has launched in this process (a
- * replayed CUDA graph counts its kernel nodes).  Timing is off until enabled;
+ * [4] fclsh_hash kernel, [5] build partition scatter kernel, [6] build
+ * segment-finish kernels, [7] build partition histogram + scan ([5]-[7] are
+ * parts of [1]).  counts[i] = timed launches of phase i.  Timing is off until enabled;
  * enabling adds one event pair per phase and runs query batches without graphs.
  */
 fclsh_status fclsh_timing_enable(fclsh_index *idx, int on);

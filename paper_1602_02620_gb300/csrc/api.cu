@@ -592,8 +592,12 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
             const uint64_t grow = (uint64_t)k * L + r0;
             if (msd) {
                 {
+                    PhaseTimer p7(idx, 7, s);
+                    FCLSH_CUDA(msd_partition_hist(keys + r0 * n, nr, n, sb, sbuf, s));
+                }
+                {
                     PhaseTimer p5(idx, 5, s);
-                    FCLSH_CUDA(msd_partition(keys + r0 * n, nr, n, sb, sbuf, s));
+                    FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, sbuf, s));
                 }
                 PhaseTimer p6(idx, 6, s);
                 FCLSH_CUDA(msd_finish(nr, n, sb, sbuf, big_cnt, big, idx->ent + grow * n,
@@ -1125,7 +1129,7 @@ extern "C" fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64
     resolve_timers(idx);
     for (int i = 0; i < 8; ++i) {
         if (ms) ms[i] = idx->ms[i];
-        if (counts) counts[i] = i == 7 ? launch_count() : idx->cnt[i];
+        if (counts) counts[i] = idx->cnt[i];
         if (reset) {
             idx->ms[i] = 0;
             idx->cnt[i] = 0;

@@ -165,11 +165,14 @@ size_t sort_keys_hist_entries(uint64_t cap);
 // stable partition by the top 8 slot bits, then one block per (segment, table) that
 // orders the segment by the remaining slot bits in shared memory and writes the
 // directory and the entries (the same layout as radix_sort_rows + finalize).
-// msd_partition packs the partition into buf.keys_a (hist in buf.hist); msd_finish
-// needs big_cnt [1] and big [rows * 256] of scratch for segments longer than 4096.
+// msd_partition_hist (histogram + scan into buf.hist) then msd_partition_scatter
+// pack the partition into buf.keys_a; msd_finish needs big_cnt [1] and
+// big [rows * 256] of scratch for segments longer than 4096.
 bool msd_path_applies(uint32_t slot_bits);
-cudaError_t msd_partition(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
-                          cudaStream_t s);
+cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
+                               cudaStream_t s);
+cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
+                                  cudaStream_t s);
 cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf, unsigned long long *big_cnt,
                        uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count, cudaStream_t s);
 // Directory of each sorted row: ent = (key >> sb) << 32 | id, offs[slot] = first entry of slot.

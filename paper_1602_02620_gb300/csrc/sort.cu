@@ -160,21 +160,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArg
         if (idx < len) {
             const uint32_t digit = (uint32_t)(key[r] >> a.shift) & a.dmask;
             const uint32_t lp = wh[digit] + lr[r];
-            sk[lp] = key[r];
+            sk[lp] = PACK ? pack_entry(key[r], id[r], a.pack_sb, a.pack_idbits) : key[r];
             sg[lp] = global_off[digit] + (lp - local_start[digit]);
-            if (IDS) si[lp] = id[r];
+            if (IDS && !PACK) si[lp] = id[r];
         }
     }
     __syncthreads();
     const uint32_t tile_n = (uint32_t)((len - base) < (uint64_t)kSortTile ? (len - base) : (uint64_t)kSortTile);
     for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
         const uint32_t g = sg[i];
-        if (PACK) {
-            a.keys_out[g] = pack_entry(sk[i], si[i], a.pack_sb, a.pack_idbits);
-        } else {
-            a.keys_out[g] = sk[i];
-            if (IDS) a.ids_out[g] = si[i];
-        }
+        a.keys_out[g] = sk[i];
+        if (IDS && !PACK) a.ids_out[g] = si[i];
     }
 }
 
@@ -420,8 +416,8 @@ __device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t til
     *hi = g < 255 ? hist[((uint64_t)row * 256 + g + 1) * tiles] - rowbase : n;
 }
 
-// Exclusive scan in place of v[0..cnt) by a 256-thread block; also writes out[j] = base + prefix.
-__device__ __forceinline__ void one_scan(uint32_t *v, uint32_t cnt, uint32_t *wsum, uint32_t *out, uint32_t base)
+// Exclusive scan in place of the padded counters v[pj(0..cnt)) by the block.
+__device__ __forceinline__ void one_scan(uint32_t *v, uint32_t cnt, uint32_t *wsum)
 {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t per = (cnt + kOneThreads - 1) / kOneThreads;
@@ -441,7 +437,6 @@ __device__ __forceinline__ void one_scan(uint32_t *v, uint32_t cnt, uint32_t *ws
     for (uint32_t j = j0; j < j0 + per && j < cnt; ++j) {
         const uint32_t c = v[pj(j)];
         v[pj(j)] = run;
-        out[j] = base + run;
         run += c;
     }
     __syncthreads();
@@ -493,7 +488,8 @@ __global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint6
         if (tid + r * kOneThreads < cn) rk[r] = atomicAdd(&cnt[pj((uint32_t)(v[r] >> 52) & smask)], 1u);
     if (tid == 0) cnt[pj(nsub)] = cn;
     __syncthreads();
-    one_scan(cnt, nsub, wsum, O, (uint32_t)lo);   // cnt[j] = first entry of slot j
+    one_scan(cnt, nsub, wsum);   // cnt[pj(j)] = first entry of slot j
+    for (uint32_t j = tid; j < nsub; j += kOneThreads) O[j] = (uint32_t)lo + cnt[pj(j)];
 #pragma unroll
     for (int r = 0; r < kOneItems; ++r)
         if (tid + r * kOneThreads < cn) ck[cnt[pj((uint32_t)(v[r] >> 52) & smask)] + rk[r]] = v[r];
@@ -737,23 +733,28 @@ static uint32_t id_bits(uint64_t len)
     return b;
 }
 
-cudaError_t msd_partition(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
-                          cudaStream_t s)
+cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
+                               cudaStream_t s)
+{
+    const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
+    const uint64_t hcount = (uint64_t)rows * 256 * tiles;
+    RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - 8, 255u, buf.hist, rows, sb,
+                id_bits(len)};
+    radix_hist_kernel<<<dim3(tiles, rows), kSortThreads, 0, s>>>(a);
+    note_launch();
+    return scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s);
+}
+
+// Stable partition of every table by the top 8 slot bits (ids in order), packed output.
+cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
+                                  cudaStream_t s)
 {
     cudaError_t e = scatter_smem_init();
     if (e != cudaSuccess) return e;
     const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
-    const uint64_t hcount = (uint64_t)rows * 256 * tiles;
-    dim3 grid(tiles, rows);
-    // stable partition of every table by the top 8 slot bits (ids in order), packed output
     RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - 8, 255u, buf.hist, rows, sb,
                 id_bits(len)};
-    radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a);
-    note_launch();
-    if ((e = scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s)) !=
-        cudaSuccess)
-        return e;
-    radix_scatter_kernel<true, true, true><<<grid, kSortThreads, kScatterSmemIds, s>>>(a);
+    radix_scatter_kernel<true, true, true><<<dim3(tiles, rows), kSortThreads, kScatterSmemIds, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }

@@ -305,10 +305,9 @@ class Index:
         ms = (ctypes.c_double * 8)()
         cnt = (ctypes.c_uint64 * 8)()
         _check(lib().fclsh_timing_read(self.handle, ms, cnt, 1 if reset else 0))
-        names = ["build_hash", "build_sort", "query_kernel", "query_csr", "hash", "build_partition", "build_finish"]
-        out = {nm: (float(ms[i]), int(cnt[i])) for i, nm in enumerate(names)}
-        out["launches"] = int(cnt[7])
-        return out
+        names = ["build_hash", "build_sort", "query_kernel", "query_csr", "hash", "build_partition", "build_finish",
+                 "build_partition_hist"]
+        return {nm: (float(ms[i]), int(cnt[i])) for i, nm in enumerate(names)}
 
     def free(self):
         if self.handle:
