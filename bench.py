@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="fewer points of the same workload (profiling)")
     ap.add_argument("--nq", type=int, default=None, help="fewer queries of the same workload (profiling)")
+    ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4],
+                    help="workload id (default: the n=1M d=128 r=8 plain workload)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -241,7 +243,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_1602_02620_gb300 import fclsh, workloads
 
-    w = workloads.make(CFG, n=args.n, nq=args.nq)
+    w = workloads.make(args.workload, n=args.n, nq=args.nq)
     seed = w.index_seed + rank          # one independent problem per GPU
     nq = int(w.queries.shape[0])
     pts = torch.from_numpy(w.points.view(np.int64)).cuda()
@@ -330,8 +332,8 @@ def main():
     # (2 x 4 B per table) + 8 B per colliding bucket entry + d/8 per distinct candidate + its d/8 bits
     qk_bytes = float(nq * (idx.T * 8 + w.d / 8) + 8 * res.collisions.sum() + (w.d / 8) * res.candidates.sum())
     ns = min(args.plain_sample, nq)
-    if args.n is not None or args.nq is not None:
-        line_name = "%s (reduced: n=%d, queries=%d)" % (w.name, w.n, nq)
+    if args.n is not None or args.nq is not None or args.workload != CFG:
+        line_name = "%s%s" % (w.name, " (reduced: n=%d, queries=%d)" % (w.n, nq) if args.n or args.nq else "")
     else:
         line_name = w.name
     t0 = time.perf_counter()
@@ -385,7 +387,7 @@ def main():
         "segment finish (segment_one_kernel + segment_finish_kernel)":
             (acc["build_finish"], 16 * entries + 4 * slots, "finish"),
     }
-    full_size = args.n is None
+    full_size = args.n is None and args.workload == CFG
     kernels = []
     for name, ((ms, cnt), nbytes, tag) in stages.items():
         if cnt == 0:
