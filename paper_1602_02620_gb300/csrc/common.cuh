@@ -19,6 +19,10 @@ constexpr int kMaxLogW = 11;          // W = 2^(r'+1) <= 2048
 constexpr int kSortTile = 2048;       // radix-sort items per tile (256 threads x 8)
 constexpr int kSortThreads = 256;
 
+// Row stride (u32 words) of a table's directory offsets: 2^sb + 1 are used; the row
+// is padded to a multiple of 4 words so that every row starts 16-byte aligned.
+__host__ __device__ __forceinline__ uint64_t dir_stride(uint32_t sb) { return (1ULL << sb) + 4; }
+
 // x mod P for x < 2^63, by 2^50 == 27 (mod P).
 __host__ __device__ __forceinline__ uint64_t mod_p(uint64_t x)
 {
@@ -94,7 +98,7 @@ struct fclsh_index {
     uint32_t *col_off = nullptr;     // [t][W+1]
     uint32_t *col_coord = nullptr;   // [d]
     uint64_t *col_b = nullptr;       // [d]
-    uint32_t *offs = nullptr;        // [T][2^slot_bits + 1]
+    uint32_t *offs = nullptr;        // [T][dir_stride(slot_bits)]: 2^slot_bits + 1 used
     uint64_t *ent = nullptr;         // [T][n]: (key >> slot_bits) << 32 | id
     uint64_t device_bytes = 0;
     fclsh_tuning tune{};
@@ -106,7 +110,7 @@ struct fclsh_index {
     size_t smem_optin = 0;
 
     uint64_t slots() const { return 1ULL << slot_bits; }
-    uint64_t offs_stride() const { return slots() + 1; }
+    uint64_t offs_stride() const { return fclsh::dir_stride(slot_bits); }
     fclsh::PartCols part(uint32_t k) const
     {
         return fclsh::PartCols{col_off + (size_t)k * (W + 1), col_coord, col_b};

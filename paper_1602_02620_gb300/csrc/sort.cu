@@ -11,14 +11,16 @@
 // Radix pass = per-tile digit histogram -> one exclusive scan over
 // (row, digit, tile) -> stable scatter.  Scanning in (row, digit, tile) order
 // gives each tile's digit run its final position, rows included, in one scan.
-// Stable ranks inside a tile come from warp match + per-warp digit counts.
+// Stable ranks inside a tile come from digit-bit ballots + per-warp digit counts.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fclsh {
 
 namespace {
 
-constexpr int kIPT = kSortTile / kSortThreads;   // items per thread per tile (16)
+constexpr int kIPT = kSortTile / kSortThreads;   // items per thread per tile (8)
 constexpr int kWarps = kSortThreads / 32;
 
 struct RadixArgs {
@@ -81,9 +83,24 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(RadixArgs a)
 template <typename T>
 __device__ __forceinline__ T block_excl_scan(T v, T *total);
 
+// Lanes of the warp whose B-bit digit equals this lane's, among the lanes with
+// `valid` set: one ballot per digit bit narrows the set (a warp-level multisplit).
+template <int B>
+__device__ __forceinline__ uint32_t same_digit_lanes(uint32_t digit, bool valid)
+{
+    uint32_t m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const bool one = (digit >> b) & 1u;
+        const uint32_t v = __ballot_sync(0xffffffffu, one);
+        m &= one ? v : ~v;
+    }
+    return m;
+}
+
 // Stable scatter of one tile (warp-level multisplit).  Warp w owns the tile's
-// items [w*512, (w+1)*512), taken in rounds of 32 in index order: a warp match
-// gives each item its rank among equal digits in the round, and a warp-private
+// items [w*256, (w+1)*256), taken in rounds of 32 in index order: ballots over the
+// digit bits give each item its rank among equal digits in the round, and a warp-private
 // counter per digit carries the rank across rounds (no block barrier).  One
 // block-wide prefix over (digit, warp) then fixes every item's place in the
 // tile's digit-sorted order in shared memory, and the tile's digit runs are
@@ -135,8 +152,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArg
     for (int r = 0; r < R; ++r) {
         const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
         const bool valid = idx < len;
-        const uint32_t digit = valid ? ((uint32_t)(key[r] >> a.shift) & a.dmask) : (256u + lane);
-        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t digit = valid ? ((uint32_t)(key[r] >> a.shift) & a.dmask) : 0u;
+        const uint32_t peers = same_digit_lanes<8>(digit, valid);
         const uint32_t before = valid ? wh[digit] : 0u;
         lr[r] = before + __popc(peers & lt_mask);
         __syncwarp();
@@ -295,7 +312,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restric
     const uint64_t nslots = 1ULL << sb;
     const uint64_t mask = nslots - 1;
     const uint64_t *Kr = keys + (uint64_t)row * len;
-    uint32_t *O = offs + (uint64_t)row * (nslots + 1);
+    uint32_t *O = offs + (uint64_t)row * dir_stride(sb);
     const uint64_t key = Kr[e];
     const uint64_t sl = key & mask;
     ent[(uint64_t)row * len + e] = ((key >> sb) << 32) | ids[(uint64_t)row * len + e];
@@ -331,8 +348,8 @@ __device__ __forceinline__ void seg_rank(const uint32_t (&dig)[kSegItems], uint3
     for (int r = 0; r < kSegItems; ++r) {
         const uint32_t idx = nvalid_warp_base + r * 32 + lane;
         const bool valid = idx < cn;
-        const uint32_t d = valid ? dig[r] : 64u + lane;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = valid ? dig[r] : 0u;
+        const uint32_t peers = same_digit_lanes<6>(d, valid);
         const uint32_t before = valid ? w[d] : 0u;
         pos[r] = before + __popc(peers & lt);
         __syncwarp();
@@ -401,11 +418,14 @@ __device__ __forceinline__ void seg_scan(uint32_t *v, uint32_t cnt, uint32_t *ws
 }
 
 constexpr int kOneThreads = 512;
-constexpr int kOneItems = kSegChunk / kOneThreads;   // 8
+constexpr int kOneWarps = kOneThreads / 32;
+constexpr int kOneItems = kSegChunk / kOneThreads;   // 8 entries per thread
+constexpr int kOneSlots = 8;                         // directory slots owned per thread (2^12 / 512)
 
-// Padded index of per-slot counters: one spare word every 32 keeps a thread's run
-// of consecutive counters (the scans below) off its neighbours' banks.
-__device__ __forceinline__ uint32_t pj(uint32_t j) { return j + (j >> 5); }
+// Padded index of per-slot counters: four spare words after every 32, so that the
+// eight consecutive counters a thread owns start on a 16-byte boundary and the
+// vector accesses of a quarter-warp fall on distinct banks.
+__device__ __forceinline__ uint32_t pj(uint32_t j) { return j + ((j >> 5) << 2); }
 
 // Segment boundaries of the partition: [lo, hi) within row `row` for top digit g.
 __device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t tiles, uint64_t n, uint32_t row,
@@ -416,37 +436,13 @@ __device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t til
     *hi = g < 255 ? hist[((uint64_t)row * 256 + g + 1) * tiles] - rowbase : n;
 }
 
-// Exclusive scan in place of the padded counters v[pj(0..cnt)) by the block.
-__device__ __forceinline__ void one_scan(uint32_t *v, uint32_t cnt, uint32_t *wsum)
-{
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t per = (cnt + kOneThreads - 1) / kOneThreads;
-    const uint32_t j0 = tid * per;
-    uint32_t loc = 0;
-    for (uint32_t j = j0; j < j0 + per && j < cnt; ++j) loc += v[pj(j)];
-    uint32_t incl = loc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (uint32_t)o) incl += u;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    uint32_t run = incl - loc;
-    for (uint32_t w = 0; w < warp; ++w) run += wsum[w];
-    for (uint32_t j = j0; j < j0 + per && j < cnt; ++j) {
-        const uint32_t c = v[pj(j)];
-        v[pj(j)] = run;
-        run += c;
-    }
-    __syncthreads();
-}
-
 // One block per (segment, table) for segments of at most one chunk (4096 entries,
-// the common case): the packed entries are placed by shared-memory counters and
-// each slot's run is then ordered by (key bits, id), giving the directory of the
-// segment's 2^sub slots and its entries.  Larger segments are listed for
-// segment_finish_kernel.
+// the common case).  Entries are counted into their slots with shared-memory
+// atomics; thread i owns the eight consecutive slots [8i, 8i+8): it scans their
+// counts in registers, writes their directory words with two vector stores and,
+// once the entries are placed, orders each of its slots' runs by (key bits, id)
+// (runs are short: Poisson with mean <= 1 for uniform keys).  Larger segments are
+// listed for segment_finish_kernel.
 __global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
                                                                      uint32_t sb, uint32_t idbits,
                                                                      const uint32_t *__restrict__ hist, uint32_t tiles,
@@ -456,9 +452,10 @@ __global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint6
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *ck = reinterpret_cast<uint64_t *>(smem_raw);             // [kSegChunk]
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(ck + kSegChunk);       // [nsub + 1]
-    __shared__ uint32_t wsum[32];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(ck + kSegChunk);       // [pj(nsub)]
+    __shared__ uint32_t wsum[kOneWarps];
     const uint32_t g = blockIdx.x, row = blockIdx.y, tid = threadIdx.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
     const uint32_t subb = sb - 8, nsub = 1u << subb, smask = nsub - 1;
     const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
     uint64_t lo, hi;
@@ -472,7 +469,7 @@ __global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint6
     const uint64_t rowbase = (uint64_t)row * n;
     const uint64_t *Pk = packed + rowbase + lo;
     uint64_t *E = ent + rowbase + lo;
-    uint32_t *O = offs + (uint64_t)row * ((1ULL << sb) + 1) + (uint64_t)g * nsub;
+    uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;   // 16-byte aligned (nsub >= 8)
     if (g == 255 && tid == 0) O[nsub] = (uint32_t)n;
     uint64_t v[kOneItems];
     uint32_t rk[kOneItems];
@@ -481,29 +478,75 @@ __global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint6
         const uint32_t idx = tid + r * kOneThreads;
         v[r] = idx < cn ? Pk[idx] : 0;
     }
-    for (uint32_t j = tid; j < nsub; j += kOneThreads) cnt[pj(j)] = 0;
+    uint4 *cnt4 = reinterpret_cast<uint4 *>(cnt);
+    for (uint32_t i = tid; i < pj(nsub) / 4; i += kOneThreads) cnt4[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kOneItems; ++r)
         if (tid + r * kOneThreads < cn) rk[r] = atomicAdd(&cnt[pj((uint32_t)(v[r] >> 52) & smask)], 1u);
-    if (tid == 0) cnt[pj(nsub)] = cn;
     __syncthreads();
-    one_scan(cnt, nsub, wsum);   // cnt[pj(j)] = first entry of slot j
-    for (uint32_t j = tid; j < nsub; j += kOneThreads) O[j] = (uint32_t)lo + cnt[pj(j)];
+
+    // counts of the owned slots -> their first entries
+    const uint32_t j0 = tid * kOneSlots;
+    const bool owner = j0 < nsub;
+    uint32_t c[kOneSlots], st[kOneSlots];
+    if (owner) {
+        const uint4 x = cnt4[pj(j0) / 4], y = cnt4[pj(j0) / 4 + 1];
+        c[0] = x.x, c[1] = x.y, c[2] = x.z, c[3] = x.w, c[4] = y.x, c[5] = y.y, c[6] = y.z, c[7] = y.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < kOneSlots; ++i) c[i] = 0;
+    }
+    uint32_t tot = 0;
+#pragma unroll
+    for (int i = 0; i < kOneSlots; ++i) {
+        st[i] = tot;
+        tot += c[i];
+    }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wv = lane < (uint32_t)kOneWarps ? wsum[lane] : 0u, wincl = wv;
+#pragma unroll
+    for (int o = 1; o < kOneWarps; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, wincl, o);
+        if (lane >= (uint32_t)o) wincl += u;
+    }
+    const uint32_t before = __shfl_sync(0xffffffffu, wincl - wv, warp) + incl - tot;
+#pragma unroll
+    for (int i = 0; i < kOneSlots; ++i) st[i] += before;
+    if (owner) {
+        cnt4[pj(j0) / 4] = make_uint4(st[0], st[1], st[2], st[3]);
+        cnt4[pj(j0) / 4 + 1] = make_uint4(st[4], st[5], st[6], st[7]);
+        const uint32_t l = (uint32_t)lo;
+        uint4 *O4 = reinterpret_cast<uint4 *>(O + j0);
+        O4[0] = make_uint4(l + st[0], l + st[1], l + st[2], l + st[3]);
+        O4[1] = make_uint4(l + st[4], l + st[5], l + st[6], l + st[7]);
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < kOneItems; ++r)
         if (tid + r * kOneThreads < cn) ck[cnt[pj((uint32_t)(v[r] >> 52) & smask)] + rk[r]] = v[r];
     __syncthreads();
-    for (uint32_t j = tid; j < nsub; j += kOneThreads) {   // order each slot's run (usually 0-3 entries)
-        const uint32_t a0 = cnt[pj(j)], a1 = cnt[pj(j + 1)];
-        for (uint32_t x = a0 + 1; x < a1; ++x) {
-            const uint64_t cur = ck[x];
-            uint32_t y = x;
-            while (y > a0 && (ck[y - 1] & low52) > (cur & low52)) {
-                ck[y] = ck[y - 1];
-                --y;
+    if (owner) {   // order each owned slot's run by (key bits, id)
+#pragma unroll
+        for (int i = 0; i < kOneSlots; ++i) {
+            if (c[i] < 2) continue;
+            const uint32_t a0 = st[i], a1 = st[i] + c[i];
+            for (uint32_t x = a0 + 1; x < a1; ++x) {
+                const uint64_t cur = ck[x];
+                uint32_t y = x;
+                while (y > a0 && (ck[y - 1] & low52) > (cur & low52)) {
+                    ck[y] = ck[y - 1];
+                    --y;
+                }
+                ck[y] = cur;
             }
-            ck[y] = cur;
         }
     }
     __syncthreads();
@@ -545,14 +588,12 @@ __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const ui
     const uint64_t seg_len = seg_hi - seg_lo;
     const uint64_t *Pk = packed + rowbase + seg_lo;
     uint64_t *E = ent + rowbase + seg_lo;
-    uint32_t *O = offs + (uint64_t)row * ((1ULL << sb) + 1) + (uint64_t)g * nsub;
+    uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;
     auto sub_of = [&](uint64_t v) { return (uint32_t)(v >> 52) & smask; };
     auto ent_of = [&](uint64_t v) { return ((v & low52) >> idbits) << 32 | (v & idmask); };
     if (g == 255 && tid == 0) O[nsub] = (uint32_t)n;
 
     // several chunks: per-slot counts of the whole segment first, then stable passes
-    uint32_t *ci = reinterpret_cast<uint32_t *>(wh + kSegWarps * 64);   // unused in this path
-    (void)ci;
     for (uint32_t j = tid; j < nsub; j += kSegThreads) sub_off[j] = 0;
     __syncthreads();
     for (uint64_t e = tid; e < seg_len; e += kSegThreads) atomicAdd(&sub_off[sub_of(Pk[e])], 1u);
@@ -722,9 +763,9 @@ cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, u
 namespace fclsh {
 
 size_t segment_finish_smem() { return (size_t)kSegChunk * 8 + ((2u << kSubMaxBits) + 1) * 4 + kSegWarps * 64 * 4; }
-size_t segment_one_smem() { return (size_t)kSegChunk * 8 + ((1u << kSubMaxBits) + (1u << kSubMaxBits) / 32 + 2) * 4; }
+size_t segment_one_smem() { return (size_t)kSegChunk * 8 + ((1u << kSubMaxBits) + (1u << kSubMaxBits) / 8 + 4) * 4; }
 
-bool msd_path_applies(uint32_t slot_bits) { return slot_bits >= 10 && slot_bits - 8 <= (uint32_t)kSubMaxBits; }
+bool msd_path_applies(uint32_t slot_bits) { return slot_bits >= 11 && slot_bits - 8 <= (uint32_t)kSubMaxBits; }
 
 static uint32_t id_bits(uint64_t len)
 {
@@ -771,6 +812,7 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &bu
         return e;
     }();
     if (once != cudaSuccess) return once;
+    if (reinterpret_cast<uintptr_t>(offs) & 15) return cudaErrorMisalignedAddress;   // vector stores of offsets
     const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
     const uint32_t idb = id_bits(len);
     cudaError_t e = cudaMemsetAsync(big_cnt, 0, sizeof(unsigned long long), s);
