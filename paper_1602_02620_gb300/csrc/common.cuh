@@ -16,7 +16,8 @@ namespace fclsh {
 constexpr uint64_t kP = (1ULL << 50) - 27;
 constexpr uint64_t kMask50 = (1ULL << 50) - 1;
 constexpr int kMaxLogW = 11;          // W = 2^(r'+1) <= 2048
-constexpr int kSortTile = 2048;       // radix-sort items per tile (256 threads x 8)
+constexpr int kSortTile = 8192;       // radix-sort items per histogram tile (one block)
+constexpr int kSortSub = 2048;        // items per scatter sub-tile (256 threads x 8)
 constexpr int kSortThreads = 256;
 
 // Row stride (u32 words) of a table's directory offsets: 2^sb + 1 are used; the row

@@ -1,12 +1,15 @@
 // sort.cu -- the bucket build (Sec. 2.2: only non-empty buckets are kept, one
 // table per hash function) and the device-wide scans.
 //
-// Each table's (key, id) pairs are sorted by the key's low `slot_bits` bits with a
-// stable LSD radix sort (8-bit digits).  The input order is by id, so ids stay
-// ascending inside every directory slot.  A finalize pass then writes the
-// directory: entries (key >> slot_bits) << 32 | id and, for every slot, the index
-// of its first entry.  A query reads slot (key mod 2^slot_bits), compares the
-// stored high key bits and takes the ids of equal keys: its bucket.
+// Directory of a table: entries (key >> slot_bits) << 32 | id grouped by slot
+// (key mod 2^slot_bits) and, for every slot, the index of its first entry.  A
+// query reads its slot, compares the stored high key bits and takes the ids of
+// equal keys: its bucket.  Two builds give it:
+//   * slot_bits <= 20 (MSD): a stable partition of each table by the top 8 slot
+//     bits, then one block per (segment, table) that counts the segment into its
+//     slots in shared memory; a slot's run is ordered by (key bits, id).
+//   * otherwise (LSD): a stable radix sort by the slot bits (8-bit digits) and a
+//     finalize pass; the input is in id order, so a slot's run is ordered by id.
 //
 // Radix pass = per-tile digit histogram -> one exclusive scan over
 // (row, digit, tile) -> stable scatter.  Scanning in (row, digit, tile) order
@@ -20,7 +23,7 @@ namespace fclsh {
 
 namespace {
 
-constexpr int kIPT = kSortTile / kSortThreads;   // items per thread per tile (8)
+constexpr int kIPT = kSortSub / kSortThreads;    // items per thread per sub-tile (8)
 constexpr int kWarps = kSortThreads / 32;
 
 struct RadixArgs {
@@ -67,15 +70,19 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(RadixArgs a)
     const uint64_t len = row_len(a);
     const uint64_t *K = a.keys_in + (uint64_t)row * a.len;
     const uint64_t base = (uint64_t)tile * kSortTile;
-    uint32_t dg[kIPT];
+    constexpr int kBatch = 16;   // loads in flight per thread before their shared-memory counts
 #pragma unroll
-    for (int i = 0; i < kIPT; ++i) {   // all loads in flight before the shared-memory counts
-        const uint64_t idx = base + (uint64_t)i * kSortThreads + tid;
-        dg[i] = idx < len ? ((uint32_t)(K[idx] >> a.shift) & a.dmask) : 0xFFFFFFFFu;
+    for (int b = 0; b < kSortTile / (kSortThreads * kBatch); ++b) {
+        uint32_t dg[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+            const uint64_t idx = base + (uint64_t)(b * kBatch + i) * kSortThreads + tid;
+            dg[i] = idx < len ? ((uint32_t)(K[idx] >> a.shift) & a.dmask) : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i)
+            if (dg[i] != 0xFFFFFFFFu) atomicAdd(&cnt[dg[i]], 1u);
     }
-#pragma unroll
-    for (int i = 0; i < kIPT; ++i)
-        if (dg[i] != 0xFFFFFFFFu) atomicAdd(&cnt[dg[i]], 1u);
     __syncthreads();
     a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile] = cnt[tid];
 }
@@ -98,96 +105,99 @@ __device__ __forceinline__ uint32_t same_digit_lanes(uint32_t digit, bool valid)
     return m;
 }
 
-// Stable scatter of one tile (warp-level multisplit).  Warp w owns the tile's
-// items [w*256, (w+1)*256), taken in rounds of 32 in index order: ballots over the
-// digit bits give each item its rank among equal digits in the round, and a warp-private
-// counter per digit carries the rank across rounds (no block barrier).  One
-// block-wide prefix over (digit, warp) then fixes every item's place in the
-// tile's digit-sorted order in shared memory, and the tile's digit runs are
-// written out as contiguous, coalesced runs.
+// Stable scatter of one tile, in sub-tiles of kSortSub items taken in order.  In a
+// sub-tile, warp w owns the items [w*256, (w+1)*256), taken in rounds of 32 in
+// index order: ballots over the digit bits give each item its rank among equal
+// digits in the round, and a warp-private counter per digit carries the rank
+// across rounds (no block barrier).  One block-wide prefix over (digit, warp) then
+// fixes every item's place in the sub-tile's digit-sorted order in shared memory,
+// and the sub-tile's digit runs are written out as contiguous, coalesced runs.
+// Each digit's global cursor starts at the tile's place from the scanned
+// (row, digit, tile) histogram and advances by the digit's count per sub-tile.
 template <bool IDS, bool IMPLICIT, bool PACK = false>
 __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArgs a)
 {
-    constexpr int R = kIPT;   // rounds per warp: 8 x 32 = 256 items
+    constexpr int R = kIPT;   // rounds per warp and sub-tile: 8 x 32 = 256 items
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kSortTile] keys in digit order
-    uint32_t *sg = reinterpret_cast<uint32_t *>(sk + kSortTile);  // [kSortTile] their global positions
-    uint32_t *si = sg + kSortTile;                                // [kSortTile] ids, when IDS
-    __shared__ uint32_t local_start[256], global_off[256];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kSortSub] keys in digit order
+    uint32_t *sg = reinterpret_cast<uint32_t *>(sk + kSortSub);   // [kSortSub] their global positions
+    uint32_t *si = sg + kSortSub;                                 // [kSortSub] ids, when IDS
+    __shared__ uint32_t global_off[256];
     __shared__ uint32_t warp_hist[kWarps][256];                   // counts, then each warp's base
     const uint32_t row = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
     const uint64_t len = row_len(a);
     const uint64_t base = (uint64_t)tile * kSortTile;
     if (base >= len) return;   // uniform: an empty tile has no items
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) warp_hist[w][tid] = 0;
-    {
-        // this tile's count of digit tid, from the scanned (row, digit, tile) prefix
-        const uint64_t idx = ((uint64_t)row * 256 + tid) * a.tiles + tile;
-        const uint64_t hcount = (uint64_t)a.rows * 256 * a.tiles;
-        const uint32_t g0 = a.hist[idx];
-        const uint32_t g1 = idx + 1 < hcount ? a.hist[idx + 1] : (uint32_t)((uint64_t)(a.rows - 1) * a.len + len);
-        global_off[tid] = g0;
-        uint32_t tot;
-        local_start[tid] = block_excl_scan<uint32_t>(g1 - g0, &tot);   // ends with a barrier
-    }
+    // digit tid's cursor: the tile's first global place for it
+    uint32_t cursor = a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile];
     const uint64_t *K = a.keys_in + (uint64_t)row * a.len;
     const uint32_t *I = IMPLICIT ? nullptr : a.ids_in + (uint64_t)row * a.len;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint64_t wbase = base + (uint64_t)warp * (32 * R);
-    // every load of the warp's sub-tile is issued before the ranking loop, whose
-    // __syncwarp()s would otherwise keep the next round's load from being hoisted
-    uint64_t key[R];
-    uint32_t id[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
-        key[r] = idx < len ? K[idx] : 0;
-        if (IDS) id[r] = IMPLICIT ? (uint32_t)idx : (idx < len ? I[idx] : 0u);
-    }
-    uint32_t lr[R];
     uint32_t *wh = warp_hist[warp];
+    for (uint64_t sbase = base; sbase < len && sbase < base + kSortTile; sbase += kSortSub) {
+        const uint64_t wbase = sbase + (uint64_t)warp * (32 * R);
+        // every load of the warp's part is issued before the ranking loop, whose
+        // __syncwarp()s would otherwise keep the next round's load from being hoisted
+        uint64_t key[R];
+        uint32_t id[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
-        const bool valid = idx < len;
-        const uint32_t digit = valid ? ((uint32_t)(key[r] >> a.shift) & a.dmask) : 0u;
-        const uint32_t peers = same_digit_lanes<8>(digit, valid);
-        const uint32_t before = valid ? wh[digit] : 0u;
-        lr[r] = before + __popc(peers & lt_mask);
-        __syncwarp();
-        if (valid && (peers & lt_mask) == 0) wh[digit] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {   // thread tid owns digit tid: each warp's first place for that digit
-        uint32_t run = local_start[tid];
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = warp_hist[w][tid];
-            warp_hist[w][tid] = run;
-            run += c;
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+            key[r] = idx < len ? K[idx] : 0;
+            if (IDS) id[r] = IMPLICIT ? (uint32_t)idx : (idx < len ? I[idx] : 0u);
         }
-    }
-    __syncthreads();
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
-        if (idx < len) {
-            const uint32_t digit = (uint32_t)(key[r] >> a.shift) & a.dmask;
-            const uint32_t lp = wh[digit] + lr[r];
-            sk[lp] = PACK ? pack_entry(key[r], id[r], a.pack_sb, a.pack_idbits) : key[r];
-            sg[lp] = global_off[digit] + (lp - local_start[digit]);
-            if (IDS && !PACK) si[lp] = id[r];
+        for (int w = 0; w < kWarps; ++w) warp_hist[w][tid] = 0;
+        __syncthreads();   // (also: the previous sub-tile's output is read out)
+        uint32_t lr[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+            const bool valid = idx < len;
+            const uint32_t digit = valid ? ((uint32_t)(key[r] >> a.shift) & a.dmask) : 0u;
+            const uint32_t peers = same_digit_lanes<8>(digit, valid);
+            const uint32_t before = valid ? wh[digit] : 0u;
+            lr[r] = before + __popc(peers & lt_mask);
+            __syncwarp();
+            if (valid && (peers & lt_mask) == 0) wh[digit] = before + __popc(peers);
+            __syncwarp();
         }
-    }
-    __syncthreads();
-    const uint32_t tile_n = (uint32_t)((len - base) < (uint64_t)kSortTile ? (len - base) : (uint64_t)kSortTile);
-    for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
-        const uint32_t g = sg[i];
-        a.keys_out[g] = sk[i];
-        if (IDS && !PACK) a.ids_out[g] = si[i];
+        __syncthreads();
+        {   // thread tid owns digit tid: its count, its place in the sub-tile, each warp's first place
+            uint32_t c = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) c += warp_hist[w][tid];
+            uint32_t tot;
+            uint32_t run = block_excl_scan<uint32_t>(c, &tot);   // barriers inside
+            global_off[tid] = cursor - run;   // global place of sub-tile position p of digit tid: global_off + p
+            cursor += c;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t cw = warp_hist[w][tid];
+                warp_hist[w][tid] = run;
+                run += cw;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+            if (idx < len) {
+                const uint32_t digit = (uint32_t)(key[r] >> a.shift) & a.dmask;
+                const uint32_t lp = wh[digit] + lr[r];
+                sk[lp] = PACK ? pack_entry(key[r], id[r], a.pack_sb, a.pack_idbits) : key[r];
+                sg[lp] = global_off[digit] + lp;
+                if (IDS && !PACK) si[lp] = id[r];
+            }
+        }
+        __syncthreads();
+        const uint32_t sub_n = (uint32_t)((len - sbase) < (uint64_t)kSortSub ? (len - sbase) : (uint64_t)kSortSub);
+        for (uint32_t i = tid; i < sub_n; i += kSortThreads) {
+            const uint32_t g = sg[i];
+            a.keys_out[g] = sk[i];
+            if (IDS && !PACK) a.ids_out[g] = si[i];
+        }
     }
 }
 
@@ -439,11 +449,12 @@ __device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t til
 // One block per (segment, table) for segments of at most one chunk (4096 entries,
 // the common case).  Entries are counted into their slots with shared-memory
 // atomics; thread i owns the eight consecutive slots [8i, 8i+8): it scans their
-// counts in registers, writes their directory words with two vector stores and,
-// once the entries are placed, orders each of its slots' runs by (key bits, id)
-// (runs are short: Poisson with mean <= 1 for uniform keys).  Larger segments are
-// listed for segment_finish_kernel.
-__global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
+// counts in registers and writes their directory words with two vector stores.
+// Each entry is then placed in its slot's run, and every entry finds its final
+// place in the run by counting the run's smaller (key bits, id) (runs are short:
+// Poisson with mean <= 1 for uniform keys), so no run is sorted serially.  Larger
+// segments are listed for segment_finish_kernel.
+__global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
                                                                      uint32_t sb, uint32_t idbits,
                                                                      const uint32_t *__restrict__ hist, uint32_t tiles,
                                                                      uint64_t *__restrict__ ent,
@@ -520,35 +531,41 @@ __global__ void __launch_bounds__(kOneThreads, 2) segment_one_kernel(const uint6
     const uint32_t before = __shfl_sync(0xffffffffu, wincl - wv, warp) + incl - tot;
 #pragma unroll
     for (int i = 0; i < kOneSlots; ++i) st[i] += before;
-    if (owner) {
-        cnt4[pj(j0) / 4] = make_uint4(st[0], st[1], st[2], st[3]);
-        cnt4[pj(j0) / 4 + 1] = make_uint4(st[4], st[5], st[6], st[7]);
+    if (owner) {   // each slot's first entry (low 16 bits) and length (high 16 bits), both <= 4096
+        cnt4[pj(j0) / 4] = make_uint4(st[0] | c[0] << 16, st[1] | c[1] << 16, st[2] | c[2] << 16, st[3] | c[3] << 16);
+        cnt4[pj(j0) / 4 + 1] =
+            make_uint4(st[4] | c[4] << 16, st[5] | c[5] << 16, st[6] | c[6] << 16, st[7] | c[7] << 16);
         const uint32_t l = (uint32_t)lo;
         uint4 *O4 = reinterpret_cast<uint4 *>(O + j0);
         O4[0] = make_uint4(l + st[0], l + st[1], l + st[2], l + st[3]);
         O4[1] = make_uint4(l + st[4], l + st[5], l + st[6], l + st[7]);
     }
     __syncthreads();
+    uint32_t sc[kOneItems];
 #pragma unroll
     for (int r = 0; r < kOneItems; ++r)
-        if (tid + r * kOneThreads < cn) ck[cnt[pj((uint32_t)(v[r] >> 52) & smask)] + rk[r]] = v[r];
-    __syncthreads();
-    if (owner) {   // order each owned slot's run by (key bits, id)
-#pragma unroll
-        for (int i = 0; i < kOneSlots; ++i) {
-            if (c[i] < 2) continue;
-            const uint32_t a0 = st[i], a1 = st[i] + c[i];
-            for (uint32_t x = a0 + 1; x < a1; ++x) {
-                const uint64_t cur = ck[x];
-                uint32_t y = x;
-                while (y > a0 && (ck[y - 1] & low52) > (cur & low52)) {
-                    ck[y] = ck[y - 1];
-                    --y;
-                }
-                ck[y] = cur;
-            }
+        if (tid + r * kOneThreads < cn) {
+            sc[r] = cnt[pj((uint32_t)(v[r] >> 52) & smask)];
+            ck[(sc[r] & 0xFFFFu) + rk[r]] = v[r];   // the run of the slot, in arrival order
         }
-    }
+    __syncthreads();
+    // Final place of each entry: its slot's first entry plus the number of entries of
+    // the run with smaller (key bits, id), so runs come out ordered by (key bits, id).
+#pragma unroll
+    for (int r = 0; r < kOneItems; ++r)
+        if (tid + r * kOneThreads < cn) {
+            const uint32_t s0 = sc[r] & 0xFFFFu, len_run = sc[r] >> 16;
+            uint32_t p = s0;
+            if (len_run > 1) {
+                const uint64_t me = v[r] & low52;
+                for (uint32_t k = s0; k < s0 + len_run; ++k) p += (ck[k] & low52) < me ? 1u : 0u;
+            }
+            sc[r] = p;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kOneItems; ++r)
+        if (tid + r * kOneThreads < cn) ck[sc[r]] = v[r];
     __syncthreads();
     for (uint32_t i = tid; i < cn; i += kOneThreads) {
         const uint64_t x = ck[i];
@@ -653,8 +670,8 @@ __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const ui
 
 }  // namespace
 
-constexpr size_t kScatterSmemIds = (size_t)kSortTile * 16;
-constexpr size_t kScatterSmemKeys = (size_t)kSortTile * 12;
+constexpr size_t kScatterSmemIds = (size_t)kSortSub * 16;
+constexpr size_t kScatterSmemKeys = (size_t)kSortSub * 12;
 
 // The scatter kernels use more than 48 KB of shared memory; raise their limit once.
 static cudaError_t scatter_smem_init()
