@@ -79,6 +79,8 @@ def _lib():
         lib.oracle_table.restype = None
         lib.oracle_query.argtypes = [vp, vp, u64, vp, vp, vp, u32, vp, u64, vp]
         lib.oracle_query.restype = u64
+        lib.oracle_query_rows.argtypes = [vp, vp, u64, vp, vp, vp, u32, u32, vp, u64, vp]
+        lib.oracle_query_rows.restype = u64
         lib.oracle_linear_scan.argtypes = [vp, u64, u32, vp, u32, vp, u64]
         lib.oracle_linear_scan.restype = u64
         lib.oracle_splitmix64.argtypes = [u64, u64, vp]
@@ -222,8 +224,12 @@ def build_tables(p: Params, pts):
     return keys, ids
 
 
-def query(p: Params, pts, tables, q, radius: int):
-    """Strategy 2 query.  Returns (sorted ids, #Collisions, #Candidates)."""
+def query(p: Params, pts, tables, q, radius: int, rows: int = 0):
+    """Strategy 2 query.  Returns (sorted ids, #Collisions, #Candidates).
+
+    rows = 0 probes every table; rows > 0 probes only the code rows v = 1..rows of
+    each part (see probe_rows()), and the counters count those tables only.
+    """
     pts = _pts(pts, p.words)
     q = _pts(q, p.words)
     keys, ids = tables
@@ -231,9 +237,16 @@ def query(p: Params, pts, tables, q, radius: int):
     cap = max(n, 1)
     out = np.zeros(cap, np.uint32)
     counters = np.zeros(2, np.uint64)
-    cnt = _lib().oracle_query(ctypes.byref(p._c()), _ptr(pts), n, _ptr(keys), _ptr(ids),
-                              _ptr(q), radius, _ptr(out), cap, _ptr(counters))
+    cnt = _lib().oracle_query_rows(ctypes.byref(p._c()), _ptr(pts), n, _ptr(keys), _ptr(ids),
+                                   _ptr(q), radius, rows, _ptr(out), cap, _ptr(counters))
     return out[:cnt].copy(), int(counters[0]), int(counters[1])
+
+
+def probe_rows(p: Params, radius: int) -> int:
+    """Code rows per part that a query of this radius must probe: 2^(floor(radius/t)+1) - 1,
+    at most W - 1 (pigeonhole over the t parts, then Theorem 1 on the map m mod 2^(floor(radius/t)+1))."""
+    e = radius // p.t + 1
+    return min(p.W - 1, (1 << e) - 1) if e < 63 else p.W - 1
 
 
 def linear_scan(pts, q, radius: int, words: int | None = None) -> np.ndarray:

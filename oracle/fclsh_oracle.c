@@ -288,17 +288,24 @@ static int u32_cmp(const void *a, const void *b)
 /*
  * Strategy 2 query (Sec. 2.2) with the cost steps of Sec. 4.1:
  *   S1: hash q into its key in every table (direct route);
- *   S2: look up the bucket of q in every table, merge with duplicate removal by
- *       an n-bit bitmap, counting #Collisions and #Candidates;
+ *   S2: look up the bucket of q in every probed table, merge with duplicate
+ *       removal by an n-bit bitmap, counting #Collisions and #Candidates;
  *   S3: compute d(x, q) for each distinct candidate and report it if <= radius.
  * tab_keys/tab_ids are the T sorted tables from oracle_table(), each [n].
+ * rows = 0 probes all W-1 tables of every part (the paper's query).  rows > 0
+ * probes only the code rows v = 1..rows of every part: with rows =
+ * 2^(floor(radius/t)+1) - 1 this is still exact, because a point within radius
+ * of q is within floor(radius/t) of it on some part (pigeonhole, Sec. 3.1), and
+ * Theorem 1 applied to the map m(i) mod 2^(floor(radius/t)+1) gives a row
+ * v < 2^(floor(radius/t)+1) on which the two collide.  The counters then count
+ * the probed tables only.
  * Results are sorted ascending.  Returns the number of results; writes up to
  * cap ids.  counters[0] = #Collisions, counters[1] = #Candidates.
  */
-uint64_t oracle_query(const oracle_params *p, const uint64_t *pts, uint64_t n,
-                      const uint64_t *tab_keys, const uint32_t *tab_ids,
-                      const uint64_t *q, uint32_t radius,
-                      uint32_t *out, uint64_t cap, uint64_t *counters)
+uint64_t oracle_query_rows(const oracle_params *p, const uint64_t *pts, uint64_t n,
+                           const uint64_t *tab_keys, const uint32_t *tab_ids,
+                           const uint64_t *q, uint32_t radius, uint32_t rows,
+                           uint32_t *out, uint64_t cap, uint64_t *counters)
 {
     uint32_t T = num_tables(p);
     uint64_t *qkeys = (uint64_t *)malloc(sizeof(uint64_t) * T);
@@ -310,6 +317,8 @@ uint64_t oracle_query(const oracle_params *p, const uint64_t *pts, uint64_t n,
         qkeys[tau] = oracle_key_direct(p, q, tau);
 
     for (uint32_t tau = 0; tau < T; tau++) {                      /* S2 */
+        uint32_t v = tau % (p->W - 1) + 1;                        /* code row of table tau */
+        if (rows && v > rows) continue;
         const uint64_t *keys = tab_keys + (uint64_t)tau * n;
         const uint32_t *ids = tab_ids + (uint64_t)tau * n;
         for (uint64_t e = lower_bound_u64(keys, n, qkeys[tau]); e < n && keys[e] == qkeys[tau]; e++) {
@@ -336,6 +345,14 @@ uint64_t oracle_query(const oracle_params *p, const uint64_t *pts, uint64_t n,
     free(bitmap);
     free(cand);
     return nres;
+}
+
+uint64_t oracle_query(const oracle_params *p, const uint64_t *pts, uint64_t n,
+                      const uint64_t *tab_keys, const uint32_t *tab_ids,
+                      const uint64_t *q, uint32_t radius,
+                      uint32_t *out, uint64_t cap, uint64_t *counters)
+{
+    return oracle_query_rows(p, pts, n, tab_keys, tab_ids, q, radius, 0, out, cap, counters);
 }
 
 /*

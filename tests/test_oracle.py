@@ -342,3 +342,54 @@ def test_tables_group_equal_keys():
         assert np.all(np.diff(keys.astype(np.float64)) >= 0)
         assert sorted(ids.tolist()) == list(range(200))
         assert np.array_equal(keys, keys_all[tau, ids])
+
+
+@pytest.mark.parametrize("d,r", [(8, 2), (10, 3), (12, 3)])
+def test_row_restricted_probe_covers_exhaustively(d, r):
+    """Rows v < 2^(rho+1) of a code built for r >= rho still cover radius rho (Theorem 1
+    applied to the map m mod 2^(rho+1)); one row fewer does not, for some z."""
+    W = 2 << r
+    rng = np.random.default_rng(d * 31 + r)
+    for rho in range(r + 1):
+        zs = list(_ball(d, rho))
+        Z = np.zeros((len(zs), 1), np.uint64)
+        for i, pos in enumerate(zs):
+            Z[i, 0] = sum(1 << j for j in pos)
+        rows = (2 << rho) - 1
+        seen_gap = False
+        for trial in range(20):
+            m = rng.integers(0, W, size=d)
+            p = oracle.make_params(d, r, m, _pow2_b(d))
+            k = oracle.keys_direct(p, Z)               # key == bit mask of g_v AND z
+            assert oracle.probe_rows(p, rho) == rows
+            assert np.all((k[:rows] == 0).any(axis=0)), (rho, trial)
+            if rho > 0 and not np.all((k[: rows // 2] == 0).any(axis=0)):
+                seen_gap = True
+        assert rho == 0 or seen_gap                    # the bound is needed: fewer rows miss some z
+
+
+@pytest.mark.parametrize("d,r,t", [(64, 6, 1), (64, 12, 2), (96, 14, 2), (90, 21, 3)])
+def test_row_restricted_query_equals_linear_scan(d, r, t):
+    """Strategy 2 probing only rows v <= 2^(floor(rho/t)+1) - 1 of each part still reports
+    exactly the linear-scan answer for every radius rho <= r; its counters are those of the
+    probed tables and never exceed the full query's."""
+    rng = np.random.default_rng(d + 7 * r)
+    words = (d + 63) // 64
+    n = 300
+    pts = rng.integers(0, 2**63, size=(n, words), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    p = oracle.derive_params(d * r + 5, d, r, t=t)
+    tables = oracle.build_tables(p, pts)
+    for qi in range(20):
+        q = pts[rng.integers(0, n)].copy()
+        for pos in rng.choice(d, size=rng.integers(0, r + 1), replace=False):
+            q[pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+        for rho in sorted({0, 1, r // 3, r // 2, r}):
+            rows = oracle.probe_rows(p, rho)
+            ids, ncoll, ncand = oracle.query(p, pts, tables, q, rho, rows=rows)
+            full, fcoll, fcand = oracle.query(p, pts, tables, q, rho)
+            assert ids.tolist() == oracle.linear_scan(pts, q, rho).tolist() == full.tolist()
+            assert ncoll <= fcoll and ncand <= fcand and ncoll >= ncand >= len(ids)
+            if rows == p.W - 1:
+                assert (ncoll, ncand) == (fcoll, fcand)
