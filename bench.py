@@ -141,11 +141,14 @@ def cpu_baseline(w, budget_s: float = 12.0):
             "points_hashed_per_s": 1.0 / th, "linear_scan_queries_per_s": 1.0 / tq}
 
 
-def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: float = 1e6):
+def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: float = 1e6, probe_rows: int = 0):
     """Continuous batching on the resident index: a Poisson stream of requests of
     U{1..4096} queries with radii in {r/4, r/2, 3r/4, r} (rounded), offered at `load`
-    times the batched throughput; then the same requests one at a time."""
+    times the batched throughput; then the same requests one at a time.  probe_rows = 1
+    probes only the code rows each request's radius needs (same ids)."""
     import threading
+
+    idx.set_tuning(probe_rows=probe_rows)
 
     rng = np.random.default_rng(7)
     sizes = rng.integers(1, 4097, size=n_req)
@@ -183,7 +186,8 @@ def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: floa
     el = time.perf_counter() - t0
     st1 = one.stats()
     one.close()
-    return {"requests": n_req, "offered_requests_per_s": rate, "radii": radii_set,
+    idx.set_tuning(probe_rows=0)
+    return {"requests": n_req, "probe_rows": probe_rows, "offered_requests_per_s": rate, "radii": radii_set,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "queries_per_s": st["queries_per_s"],
             "mean_batch_queries": st["mean_batch_queries"], "batches": st["batches"],
             "one_at_a_time_queries_per_s": float(sizes.sum()) / el,
@@ -256,7 +260,7 @@ def main():
     idx0.free()
 
     def step(timing: bool):
-        idx = fclsh.build(pts, w.d, w.r, seed, timing=timing)
+        idx = fclsh.build(pts, w.d, w.r, seed, timing=timing, hash_tile=tuned["hash_tile"])
         idx.set_tuning(**tuned)
         idx.timing_enable(False)          # the query batch runs as a replayed CUDA graph
         ctx = idx.context()
@@ -304,7 +308,7 @@ def main():
     value = world * nq * args.steps / elapsed
 
     # ---- query phase alone (index resident), batched vs plain vs brute force
-    idx = fclsh.build(pts, w.d, w.r, seed)
+    idx = fclsh.build(pts, w.d, w.r, seed, hash_tile=tuned["hash_tile"])
     idx.set_tuning(**tuned)
     ctx = idx.context()
     for _ in range(3):
@@ -347,6 +351,7 @@ def main():
     assert np.array_equal(brute.ids, res.ids) and np.array_equal(brute.offs, res.offs), "brute force differs"
     T = idx.T
     serve = served(fclsh, idx, w, batched_qps=batched_qps)
+    serve_rows = served(fclsh, idx, w, batched_qps=batched_qps, probe_rows=1)
     idx.free()
 
     # ---- e2e through the C ABI from pinned host buffers
@@ -357,7 +362,7 @@ def main():
     for i in range(max(2, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        idx2 = fclsh.build(hp, w.d, w.r, seed)
+        idx2 = fclsh.build(hp, w.d, w.r, seed, hash_tile=tuned["hash_tile"])
         idx2.set_tuning(**tuned)
         r2 = idx2.query(hq, w.r)
         e2e_t.append(time.perf_counter() - t0)
@@ -426,6 +431,7 @@ def main():
             "tuning": tuned,
         },
         "served": serve,
+        "served_row_probe": serve_rows,
         "roofline": {"kernel": dom["kernel"], "bound": "hbm", "achieved": dom["achieved_gbs"], "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac"], "traffic": dom["traffic"],
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_ms": dom["avg_ms"]},

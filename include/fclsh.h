@@ -66,6 +66,8 @@ typedef struct {
     const uint32_t *m;
     const uint64_t *b;
     uint32_t timing;          /* 1: record per-phase CUDA events from the start (see fclsh_timing_read) */
+    uint32_t hash_tile;       /* points per hash block (Algorithm 2 kernel): 0 = the default for W, 1 = twice
+                                 that where it fits shared memory (W <= 1024); speed only */
 } fclsh_build_opts;
 
 typedef struct {
@@ -95,13 +97,23 @@ typedef struct {
     const uint64_t *candidates;  /* device [nq] */
 } fclsh_device_result;
 
-/* Kernel shape choices.  They change speed only, never results. */
+/*
+ * Kernel shape choices, which change speed only, never results, and the probe
+ * rule of queries (probe_rows), which never changes the reported ids.
+ */
 typedef struct {
-    uint32_t query_block;     /* threads per query CTA: 128, 256 or 512 */
+    uint32_t query_block;     /* threads per query CTA: 128, 256 or 512 (verify-block shape) */
     uint32_t query_ctas_per_sm;
     uint32_t hash_set_log2;   /* shared-memory dedup set of 2^k ids (10..13) */
-    uint32_t inline_probe;    /* bucket-range length handled by the probing lane itself (1..32) */
+    uint32_t inline_probe;    /* probe fan-out: a bucket range up to this length is walked by the lane that
+                                 probed it, a longer one by the whole warp (1..32) */
     uint32_t use_graph;       /* capture a batch's launches into a CUDA graph and replay it */
+    uint32_t hash_tile;       /* WHT tile of fclsh_hash (see fclsh_build_opts.hash_tile): 0 or 1 */
+    uint32_t probe_rows;      /* 0: a query probes all T tables (Strategy 2, Sec. 2.2).  1: a query of radius
+                                 rho probes only the code rows v = 1 .. 2^(floor(rho/t)+1) - 1 of each part;
+                                 the ids are the same (pigeonhole over the parts, Sec. 3.1, and Theorem 1
+                                 for the map m mod 2^(floor(rho/t)+1)), and #Collisions / #Candidates count
+                                 the probed tables only.  Not chosen by fclsh_autotune. */
 } fclsh_tuning;
 
 /* ------------------------------------------------------------------ index */
@@ -291,9 +303,13 @@ fclsh_status fclsh_get_tuning(const fclsh_index *idx, fclsh_tuning *out);
 fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *tune);
 
 /*
- * Time the query kernel shapes on a sample batch (device or host queries) and
- * keep the fastest; the choice is cached in `cache_path` (JSON, may be NULL)
- * keyed by (n, d, r, t, W).  Results never depend on the choice.  Synchronous.
+ * Time the kernel shapes on a sample: the query kernel's (verify-block shape,
+ * blocks per SM, dedup set, probe fan-out) on a batch of queries (device or
+ * host), and the hash kernel's WHT tile on the index's first points; keep the
+ * fastest.  The choice is cached in `cache_path` (JSON, may be NULL) keyed by
+ * (n, d, r, t, W).  Results never depend on the choice; probe_rows is kept as
+ * set.  A later build takes the hash tile through fclsh_build_opts.hash_tile.
+ * Synchronous.
  */
 fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
                             const char *cache_path, fclsh_tuning *chosen);

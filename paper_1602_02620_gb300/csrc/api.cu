@@ -32,7 +32,7 @@ cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned 
                                uint64_t idmask, uint32_t *ids, int sm_count, cudaStream_t s);
 cudaError_t launch_gather_runs(const uint32_t *runs, const uint64_t *run_base, const uint32_t *res_cnt,
                                const uint64_t *offs, uint64_t nq, uint64_t cap, uint32_t *ids, int sm_count, cudaStream_t s);
-size_t hash_smem_bytes(uint32_t W, uint32_t dk);
+size_t hash_smem_bytes(uint32_t W, uint32_t dk, uint32_t tile);
 
 // ---------------------------------------------------------------- errors
 
@@ -370,6 +370,7 @@ static QueryArgs make_args(fclsh_index *idx)
     a.slot_bits = idx->slot_bits;
     a.hset_log2 = idx->tune.hash_set_log2;
     a.inline_len = idx->tune.inline_probe;
+    a.probe_rows = idx->tune.probe_rows;
     a.col_off = idx->col_off;
     a.col_coord = idx->col_coord;
     a.col_b = idx->col_b;
@@ -490,7 +491,8 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->rp = rp;
     idx->W = W;
     idx->T = t * (W - 1);
-    idx->tune = fclsh_tuning{256, 4, 12, 4, 1};
+    if (o.hash_tile > 1) return fail(FCLSH_EINVAL, "hash_tile must be 0 or 1");
+    idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0};
     idx->timing = o.timing != 0;
 
     const bool explicit_params = o.perm || o.part_off || o.m || o.b;
@@ -515,7 +517,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     }
     uint32_t max_dk = 0;
     for (uint32_t k = 0; k < t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
-    if (hash_smem_bytes(W, max_dk) > idx->smem_optin)
+    if (hash_smem_bytes(W, max_dk, o.hash_tile) > idx->smem_optin)
         return fail(FCLSH_EINVAL, "a part of %u coordinates with W = %u does not fit the hash kernel's shared memory",
                     max_dk, W);
 
@@ -1111,6 +1113,12 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     if (t->hash_set_log2 < 10 || t->hash_set_log2 > 13) return fail(FCLSH_EINVAL, "hash_set_log2 must be in 10..13");
     if (t->inline_probe < 1 || t->inline_probe > 32) return fail(FCLSH_EINVAL, "inline_probe must be in 1..32");
     if (t->query_ctas_per_sm < 1 || t->query_ctas_per_sm > 16) return fail(FCLSH_EINVAL, "query_ctas_per_sm must be in 1..16");
+    if (t->hash_tile > 1) return fail(FCLSH_EINVAL, "hash_tile must be 0 or 1");
+    if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
+    uint32_t max_dk = 0;
+    for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
+    if (hash_smem_bytes(idx->W, max_dk, t->hash_tile) > idx->smem_optin)
+        return fail(FCLSH_EINVAL, "the hash tile does not fit in shared memory");
     idx->tune = *t;
     return FCLSH_OK;
 }
@@ -1181,7 +1189,7 @@ static bool cache_lookup(const char *path, const std::string &key, fclsh_tuning 
     fclsh_tuning v{};
     if (!read_field(obj, "query_block", &v.query_block) || !read_field(obj, "query_ctas_per_sm", &v.query_ctas_per_sm) ||
         !read_field(obj, "hash_set_log2", &v.hash_set_log2) || !read_field(obj, "inline_probe", &v.inline_probe) ||
-        !read_field(obj, "use_graph", &v.use_graph))
+        !read_field(obj, "use_graph", &v.use_graph) || !read_field(obj, "hash_tile", &v.hash_tile))
         return false;
     *t = v;
     return true;
@@ -1202,8 +1210,8 @@ static void cache_store(const char *path, const std::string &key, const fclsh_tu
     char ent[512];
     snprintf(ent, sizeof ent,
              "  \"%s\": {\"query_block\": %u, \"query_ctas_per_sm\": %u, \"hash_set_log2\": %u, \"inline_probe\": %u, "
-             "\"use_graph\": %u}",
-             key.c_str(), t.query_block, t.query_ctas_per_sm, t.hash_set_log2, t.inline_probe, t.use_graph);
+             "\"use_graph\": %u, \"hash_tile\": %u}",
+             key.c_str(), t.query_block, t.query_ctas_per_sm, t.hash_set_log2, t.inline_probe, t.use_graph, t.hash_tile);
     lines.push_back(ent);
     std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
@@ -1224,7 +1232,8 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
     FCLSH_CUDA(cudaSetDevice(idx->device));
     const std::string key = tune_key(idx);
     fclsh_tuning best{};
-    if (cache_path && cache_lookup(cache_path, key, &best) && fclsh_set_tuning(idx, &best) == FCLSH_OK) {
+    if (cache_path && cache_lookup(cache_path, key, &best) &&
+        (best.probe_rows = idx->tune.probe_rows, fclsh_set_tuning(idx, &best) == FCLSH_OK)) {
         if (chosen) *chosen = best;
         return FCLSH_OK;
     }
@@ -1251,7 +1260,7 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
             for (uint32_t il : inl)
                 for (uint32_t ct : ctas) {
                     if (st != FCLSH_OK) break;
-                    fclsh_tuning t{bk, ct, hl, il, 0};
+                    fclsh_tuning t{bk, ct, hl, il, 0, saved.hash_tile, saved.probe_rows};
                     if (query_smem_bytes(idx->T, idx->W, idx->words, hl) > idx->smem_optin) continue;
                     int occ = 0;
                     if (query_batch_occupancy(bk, query_smem_bytes(idx->T, idx->W, idx->words, hl), &occ) != cudaSuccess ||
@@ -1274,11 +1283,40 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
                         best = t;
                     }
                 }
+    // WHT tile of the hash kernel: both choices on the index's first points (about 256 MB of keys)
+    if (st == FCLSH_OK) {
+        const uint32_t L = idx->W - 1;
+        const uint64_t cnt = std::min<uint64_t>(idx->n, std::max<uint64_t>(4096, (32ULL << 20) / L));
+        uint32_t max_dk = 0;
+        for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
+        uint64_t *kbuf = nullptr;
+        if (dev_alloc((void **)&kbuf, cnt * L * 8) == cudaSuccess) {
+            float best_h = 1e30f;
+            for (uint32_t tl = 0; tl <= 1; ++tl) {
+                if (hash_smem_bytes(idx->W, max_dk, tl) > idx->smem_optin) continue;
+                idx->tune.hash_tile = tl;
+                if (launch_hash_part(idx, 0, idx->points, cnt, kbuf, cnt, s) != cudaSuccess) continue;
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < 3; ++rep) launch_hash_part(idx, 0, idx->points, cnt, kbuf, cnt, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_h) {
+                    best_h = ms;
+                    best.hash_tile = tl;
+                }
+            }
+            dev_free(kbuf);
+        }
+        cudaGetLastError();
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     fclsh_qctx_free(c);
     idx->timing = saved_timing;
     best.use_graph = 1;
+    best.probe_rows = saved.probe_rows;
     idx->tune = best;
     if (st != FCLSH_OK) return st;
     if (cache_path) cache_store(cache_path, key, best);

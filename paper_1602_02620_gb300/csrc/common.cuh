@@ -61,6 +61,7 @@ struct QueryArgs {
     const uint64_t *points;
     uint64_t n;
     uint32_t words, t, W, T, slot_bits, hset_log2, inline_len;
+    uint32_t probe_rows;          // 1: probe only the code rows v < 2^(floor(radius/t)+1) of each part
     const uint32_t *col_off, *col_coord;
     const uint64_t *col_b;
     const uint32_t *offs;
@@ -82,6 +83,26 @@ struct QueryArgs {
     uint32_t *bitmaps;            // [gridDim.x][bm_words]
     uint64_t bm_words;
 };
+
+// Code rows a query of this radius probes in every part: all W-1, or with
+// probe_rows only v = 1..2^(floor(radius/t)+1)-1 (a point within the radius is
+// within floor(radius/t) of the query on some part, Sec. 3.1, and Theorem 1 for
+// the map m mod 2^(floor(radius/t)+1) makes the two collide on one of those rows).
+__device__ __forceinline__ uint32_t rows_per_part(const QueryArgs &a, uint32_t radius)
+{
+    const uint32_t L = a.W - 1;
+    if (!a.probe_rows) return L;
+    const uint32_t e = radius / a.t + 1;
+    const uint32_t rows = e >= 31 ? L : (1u << e) - 1u;
+    return rows < L ? rows : L;
+}
+
+// Table index of the j-th probed table (parts in order, rows 1..nt in each).
+__device__ __forceinline__ uint32_t probed_table(uint32_t j, uint32_t nt, uint32_t L)
+{
+    const uint32_t k = j / nt;
+    return k * L + (j - k * nt);
+}
 
 }  // namespace fclsh
 

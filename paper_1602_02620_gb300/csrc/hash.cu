@@ -152,16 +152,27 @@ template <> struct TileCfg<9>  { static constexpr int NP = 16,  NPH = 2, B0 = 4,
 template <> struct TileCfg<10> { static constexpr int NP = 8,   NPH = 2, B0 = 5, B1 = 5, B2 = 0; static constexpr uint32_t M = 0x20; };
 template <> struct TileCfg<11> { static constexpr int NP = 8,   NPH = 3, B0 = 5, B1 = 3, B2 = 3; static constexpr uint32_t M = 0x24; };
 
-template <int LOGW>
+// A tile of NP_ points: TileCfg's NP (the default) or twice that (a wider tile).
+template <int LOGW, int NP_ = TileCfg<LOGW>::NP>
 struct Tile {
     using C = TileCfg<LOGW>;
     static constexpr int W = 1 << LOGW;
-    static constexpr int NP = C::NP;
+    static constexpr int NP = NP_;
     static constexpr int NT = NP * W / 32;            // threads per block
     static constexpr size_t VALUES_BYTES = (size_t)W * NP * 8;
     // blocks per SM the register budget is sized for (forcing 3 spills at 80 registers)
     static constexpr int MINB = VALUES_BYTES <= 64 * 1024 ? 2 : 1;
+    // the row swizzle matters only when a half-warp spans two rows (NP = 8)
+    static constexpr uint32_t M = NP == 8 ? C::M : 0u;
 };
+
+// Points per tile for the tile choice (0: default, 1: twice that where it fits).
+template <int LOGW>
+constexpr int tile_points(uint32_t choice)
+{
+    constexpr int np = TileCfg<LOGW>::NP;
+    return (choice == 1 && (size_t)(1 << LOGW) * 2 * np * 8 <= 128 * 1024) ? 2 * np : np;
+}
 
 // Shared-memory slot of value j of point p.  With NP = 8 a half-warp touches two
 // rows; flipping bit 0 of the row by the parity of (j & M) puts those two rows in
@@ -184,13 +195,13 @@ __device__ __forceinline__ uint32_t jidx(uint32_t other, uint32_t k)
 
 // MODE 0: gather the sketch, transform, write to smem.  1: smem -> transform -> smem.
 // 2: smem -> transform -> finish -> global keys.
-template <int LOGW, int LO, int B, int MODE, int GM>
+template <int LOGW, int NP, int LO, int B, int MODE, int GM>
 __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsigned long long *S_acc, uint32_t p,
                                       uint32_t tp, const ColsSmem &cols, const uint64_t *pk, const PointRegs &xr,
                                       const uint64_t *__restrict__ x, bool valid, uint64_t *__restrict__ keys,
                                       uint64_t ld, uint64_t gp)
 {
-    using T = Tile<LOGW>;
+    using T = Tile<LOGW, NP>;
     constexpr int K = 1 << B, G = 32 / K;
     uint64_t v[32];
     uint64_t part = 0;
@@ -212,7 +223,7 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
                 v[g * K + k] = tj;
                 part += tj;
             } else {
-                v[g * K + k] = sm[slot<T::NP, T::C::M>(j, p)];
+                v[g * K + k] = sm[slot<T::NP, T::M>(j, p)];
             }
         }
     }
@@ -237,17 +248,17 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
         for (int g = 0; g < G; ++g) {
             const uint32_t other = tp * G + g;
 #pragma unroll
-            for (int k = 0; k < K; ++k) sm[slot<T::NP, T::C::M>(jidx<LO, B>(other, k), p)] = v[g * K + k];
+            for (int k = 0; k < K; ++k) sm[slot<T::NP, T::M>(jidx<LO, B>(other, k), p)] = v[g * K + k];
         }
     }
 }
 
-template <int LOGW, int GM>
-__global__ void __launch_bounds__(Tile<LOGW>::NT, Tile<LOGW>::MINB) hash_tile_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
+template <int LOGW, int NP, int GM>
+__global__ void __launch_bounds__(Tile<LOGW, NP>::NT, Tile<LOGW, NP>::MINB) hash_tile_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
                                                                     uint32_t words, PartCols pc,
                                                                     uint64_t *__restrict__ keys, uint64_t ld)
 {
-    using T = Tile<LOGW>;
+    using T = Tile<LOGW, NP>;
     using C = typename T::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
@@ -272,24 +283,24 @@ __global__ void __launch_bounds__(Tile<LOGW>::NT, Tile<LOGW>::MINB) hash_tile_ke
     if (threadIdx.x < T::NP) S_acc[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t *S_sm = reinterpret_cast<const uint64_t *>(S_acc);
-    phase<LOGW, 0, C::B0, 0, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
+    phase<LOGW, NP, 0, C::B0, 0, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
     __syncthreads();
     if constexpr (C::NPH == 2) {
-        phase<LOGW, C::B0, C::B1, 2, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
+        phase<LOGW, NP, C::B0, C::B1, 2, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
     } else {
-        phase<LOGW, C::B0, C::B1, 1, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
+        phase<LOGW, NP, C::B0, C::B1, 1, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
         __syncthreads();
-        phase<LOGW, C::B0 + C::B1, C::B2, 2, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
+        phase<LOGW, NP, C::B0 + C::B1, C::B2, 2, GM>(sm, S_sm, S_acc, p, tp, cols, pk, xr, x, valid, keys, ld, gp);
     }
 }
 
-template <int LOGW, int GM>
+template <int LOGW, int NP, int GM>
 cudaError_t launch_tile(size_t cbytes, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, uint64_t *keys,
                         uint64_t ld, cudaStream_t s)
 {
-    using T = Tile<LOGW>;
+    using T = Tile<LOGW, NP>;
     const size_t smem = T::VALUES_BYTES + T::NP * 8 + cbytes;
-    auto kern = hash_tile_kernel<LOGW, GM>;
+    auto kern = hash_tile_kernel<LOGW, NP, GM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -300,9 +311,20 @@ cudaError_t launch_tile(size_t cbytes, const uint64_t *pts, uint64_t cnt, uint32
     return cudaGetLastError();
 }
 
+template <int LOGW, int NP>
+cudaError_t launch_gather(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, uint64_t *keys,
+                          uint64_t ld, cudaStream_t s)
+{
+    constexpr int W = 1 << LOGW;
+    if (dk > (uint32_t)W)   // general construction: column lists
+        return launch_tile<LOGW, NP, GENERAL>(cols_smem_bytes(W, dk), pts, cnt, words, pc, keys, ld, s);
+    if (words <= 4) return launch_tile<LOGW, NP, PACKED_REG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
+    return launch_tile<LOGW, NP, PACKED_LDG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
+}
+
 template <int LOGW>
-cudaError_t launch_logw(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, uint64_t *keys,
-                        uint64_t ld, cudaStream_t s)
+cudaError_t launch_logw(uint32_t dk, uint32_t tile, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc,
+                        uint64_t *keys, uint64_t ld, cudaStream_t s)
 {
     constexpr int W = 1 << LOGW;
     if constexpr (LOGW <= 5) {
@@ -318,29 +340,37 @@ cudaError_t launch_logw(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t
         note_launch();
         return cudaGetLastError();
     } else {
-        if (dk > (uint32_t)W)   // general construction: column lists
-            return launch_tile<LOGW, GENERAL>(cols_smem_bytes(W, dk), pts, cnt, words, pc, keys, ld, s);
-        if (words <= 4) return launch_tile<LOGW, PACKED_REG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
-        return launch_tile<LOGW, PACKED_LDG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
+        (void)W;
+        constexpr int np0 = tile_points<LOGW>(0), np1 = tile_points<LOGW>(1);
+        if (tile == 1 && np1 != np0) return launch_gather<LOGW, np1>(dk, pts, cnt, words, pc, keys, ld, s);
+        return launch_gather<LOGW, np0>(dk, pts, cnt, words, pc, keys, ld, s);
     }
 }
 
 }  // namespace
 
-// Shared memory one hash block needs for code length W and a part of dk coordinates.
-size_t hash_smem_bytes(uint32_t W, uint32_t dk)
+template <int LOGW>
+size_t tile_smem(uint32_t tile)
 {
-    size_t tile = 0;
+    const size_t np = (size_t)(tile == 1 ? tile_points<LOGW>(1) : tile_points<LOGW>(0));
+    return ((size_t)1 << LOGW) * np * 8 + np * 8;
+}
+
+// Shared memory one hash block needs for code length W, a part of dk coordinates
+// and the tile choice.
+size_t hash_smem_bytes(uint32_t W, uint32_t dk, uint32_t tile)
+{
+    size_t t = 0;
     switch (W) {
-    case 64: tile = Tile<6>::VALUES_BYTES + Tile<6>::NP * 8; break;
-    case 128: tile = Tile<7>::VALUES_BYTES + Tile<7>::NP * 8; break;
-    case 256: tile = Tile<8>::VALUES_BYTES + Tile<8>::NP * 8; break;
-    case 512: tile = Tile<9>::VALUES_BYTES + Tile<9>::NP * 8; break;
-    case 1024: tile = Tile<10>::VALUES_BYTES + Tile<10>::NP * 8; break;
-    case 2048: tile = Tile<11>::VALUES_BYTES + Tile<11>::NP * 8; break;
+    case 64: t = tile_smem<6>(tile); break;
+    case 128: t = tile_smem<7>(tile); break;
+    case 256: t = tile_smem<8>(tile); break;
+    case 512: t = tile_smem<9>(tile); break;
+    case 1024: t = tile_smem<10>(tile); break;
+    case 2048: t = tile_smem<11>(tile); break;
     default: break;
     }
-    return tile + cols_smem_bytes(W, dk);
+    return t + cols_smem_bytes(W, dk);
 }
 
 cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t *pts, uint64_t cnt, uint64_t *keys,
@@ -350,18 +380,19 @@ cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t 
     const uint32_t dk = idx->part_off[k + 1] - idx->part_off[k];
     const PartCols pc = idx->part(k);
     const uint32_t logw = idx->rp + 1;
+    const uint32_t tl = idx->tune.hash_tile;
     switch (logw) {
-    case 1: return launch_logw<1>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 2: return launch_logw<2>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 3: return launch_logw<3>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 4: return launch_logw<4>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 5: return launch_logw<5>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 6: return launch_logw<6>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 7: return launch_logw<7>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 8: return launch_logw<8>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 9: return launch_logw<9>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 10: return launch_logw<10>(dk, pts, cnt, idx->words, pc, keys, ld, s);
-    case 11: return launch_logw<11>(dk, pts, cnt, idx->words, pc, keys, ld, s);
+    case 1: return launch_logw<1>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 2: return launch_logw<2>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 3: return launch_logw<3>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 4: return launch_logw<4>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 5: return launch_logw<5>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 6: return launch_logw<6>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 7: return launch_logw<7>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 8: return launch_logw<8>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 9: return launch_logw<9>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 10: return launch_logw<10>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 11: return launch_logw<11>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -65,15 +65,16 @@ fclsh_status scratch_address(int device, uint64_t **out)
     return FCLSH_OK;
 }
 
-// Probe every table for one query: mark each distinct candidate in cand_bm and
+// Probe every table of the probe rule for one query: mark each distinct candidate in cand_bm and
 // each candidate within the radius in hit_bm (one thread per table).
 __global__ void __launch_bounds__(256) noalloc_probe_kernel(QueryArgs a, NoallocScratch sc)
 {
     __shared__ uint64_t q_s[256];
     for (uint32_t w = threadIdx.x; w < a.words; w += blockDim.x) q_s[w] = a.queries[w];
     __syncthreads();
-    const uint32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tau >= a.T) return;
+    const uint32_t nt = rows_per_part(a, a.radius), j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.t * nt) return;
+    const uint32_t tau = probed_table(j, nt, a.W - 1);
     const uint64_t key = sc.keys[tau];
     const uint32_t fp = (uint32_t)(key >> a.slot_bits);
     const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & ((1ULL << a.slot_bits) - 1));
@@ -182,7 +183,10 @@ extern "C" fclsh_status fclsh_query_plain_noalloc(const fclsh_index *cidx, const
     a.points = idx->points;
     a.n = idx->n;
     a.words = idx->words;
+    a.t = idx->t;
+    a.W = idx->W;
     a.T = idx->T;
+    a.probe_rows = idx->tune.probe_rows;
     a.slot_bits = idx->slot_bits;
     a.offs = idx->offs;
     a.offs_stride = idx->offs_stride();

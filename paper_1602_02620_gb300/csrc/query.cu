@@ -240,14 +240,16 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             __syncthreads();
         }
 
-        // ---- S2a: bucket ranges of every table
+        // ---- S2a: bucket ranges of every probed table
+        const uint32_t nt = rows_per_part(a, radius), Tq = a.t * nt;
         unsigned long long local = 0;
-        for (uint32_t tau = tid; tau < a.T; tau += B) {
+        for (uint32_t j = tid; j < Tq; j += B) {
+            const uint32_t tau = probed_table(j, nt, L);
             const uint64_t key = keys_s[tau];
             const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
             const uint32_t lo = O[0], hi = O[1];
-            lo_s[tau] = lo;
-            len_s[tau] = hi - lo;
+            lo_s[j] = lo;
+            len_s[j] = hi - lo;
             local += hi - lo;
         }
         const unsigned long long E = block_sum(local, red64);
@@ -259,12 +261,13 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
 
         // ---- S2b + S3: collisions -> dedup -> verify, 32 tables per warp step
         Counters c;
-        for (uint32_t base = warp * 32; base < a.T; base += nwarps * 32) {
-            const uint32_t tau = base + lane;
-            const bool has = tau < a.T;
-            const uint32_t lo = has ? lo_s[tau] : 0, len = has ? len_s[tau] : 0;
+        for (uint32_t base = warp * 32; base < Tq; base += nwarps * 32) {
+            const uint32_t j = base + lane;
+            const bool has = j < Tq;
+            const uint32_t tau = has ? probed_table(j, nt, L) : 0;
+            const uint32_t lo = has ? lo_s[j] : 0, len = has ? len_s[j] : 0;
             const uint32_t fp = has ? (uint32_t)(keys_s[tau] >> a.slot_bits) : 0;
-            const uint64_t *row = a.ent + (uint64_t)(has ? tau : 0) * a.n;
+            const uint64_t *row = a.ent + (uint64_t)tau * a.n;
             const uint32_t short_len = len <= a.inline_len ? len : 0;
             const uint32_t maxs = __reduce_max_sync(0xffffffffu, short_len);
             for (uint32_t e = 0; e < maxs; ++e) {
@@ -296,9 +299,9 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         const uint32_t nres = s_nres;   // read after block_sum's barriers
         __shared__ unsigned long long s_base;
         if (bitmap_mode) {   // leave the CTA's bitmap all-zero
-            for (uint32_t tau = tid; tau < a.T; tau += B) {
-                const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[tau];
-                const uint32_t len = len_s[tau];
+            for (uint32_t j = tid; j < Tq; j += B) {
+                const uint64_t *row = a.ent + (uint64_t)probed_table(j, nt, L) * a.n + lo_s[j];
+                const uint32_t len = len_s[j];
                 for (uint32_t e = 0; e < len; ++e) bm[(uint32_t)__ldg(row + e) >> 5] = 0;
             }
             __syncthreads();
@@ -313,9 +316,10 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         } else {
             // More hits than shared memory holds (only in bitmap mode): mark every hit in
             // the bitmap, then read the ids out in ascending order and clear it again.
-            for (uint32_t tau = tid; tau < a.T; tau += B) {
-                const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[tau];
-                const uint32_t len = len_s[tau];
+            for (uint32_t j = tid; j < Tq; j += B) {
+                const uint32_t tau = probed_table(j, nt, L);
+                const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[j];
+                const uint32_t len = len_s[j];
                 const uint32_t fp = (uint32_t)(keys_s[tau] >> a.slot_bits);
                 for (uint32_t e = 0; e < len; ++e) {
                     const uint64_t en = __ldg(row + e);
@@ -371,14 +375,15 @@ __global__ void __launch_bounds__(256) gather_runs_kernel(const uint32_t *runs, 
 
 // ---------------------------------------------------------------- plain path
 
-// One query: every table in its own thread, duplicates removed by a global n-bit bitmap.
+// One query: every probed table in its own thread, duplicates removed by a global n-bit bitmap.
 __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uint64_t *keys, uint32_t *bitmap)
 {
     __shared__ uint64_t q_s[256];
     for (uint32_t w = threadIdx.x; w < a.words; w += blockDim.x) q_s[w] = a.queries[w];
     __syncthreads();
-    const uint32_t tau = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tau >= a.T) return;
+    const uint32_t nt = rows_per_part(a, a.radius), j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.t * nt) return;
+    const uint32_t tau = probed_table(j, nt, a.W - 1);
     const uint64_t smask = (1ULL << a.slot_bits) - 1;
     const uint64_t key = keys[tau];
     const uint32_t fp = (uint32_t)(key >> a.slot_bits);

@@ -30,7 +30,7 @@ class FclshError(RuntimeError):
 class BuildOpts(ctypes.Structure):
     _fields_ = [("t", ctypes.c_uint32), ("slot_bits", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
                 ("perm", ctypes.c_void_p), ("part_off", ctypes.c_void_p), ("m", ctypes.c_void_p), ("b", ctypes.c_void_p),
-                ("timing", ctypes.c_uint32)]
+                ("timing", ctypes.c_uint32), ("hash_tile", ctypes.c_uint32)]
 
 
 class Info(ctypes.Structure):
@@ -52,7 +52,8 @@ class DeviceResult(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("query_block", ctypes.c_uint32), ("query_ctas_per_sm", ctypes.c_uint32),
-                ("hash_set_log2", ctypes.c_uint32), ("inline_probe", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
+                ("hash_set_log2", ctypes.c_uint32), ("inline_probe", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
+                ("hash_tile", ctypes.c_uint32), ("probe_rows", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -361,13 +362,18 @@ class Server:
 
 
 def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: int | None = None,
-          mem_budget: int | None = None, perm=None, part_off=None, m=None, b=None, timing: bool = False) -> Index:
-    """fclsh_build on host (numpy) or device (torch CUDA) points [n][ceil(d/64)] uint64."""
+          mem_budget: int | None = None, perm=None, part_off=None, m=None, b=None, timing: bool = False,
+          hash_tile: int = 0) -> Index:
+    """fclsh_build on host (numpy) or device (torch CUDA) points [n][ceil(d/64)] uint64.
+
+    hash_tile selects the hash kernel's WHT tile (0 default, 1 twice as many points);
+    fclsh_autotune reports the faster one as tuning()["hash_tile"]."""
     o = BuildOpts()
     o.t = t or 0
     o.slot_bits = slot_bits or 0
     o.mem_budget = mem_budget or 0
     o.timing = 1 if timing else 0
+    o.hash_tile = hash_tile
     keep = []
     if perm is not None:
         arrs = [np.ascontiguousarray(perm, np.uint32), np.ascontiguousarray(part_off, np.uint32),

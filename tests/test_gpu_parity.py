@@ -247,3 +247,88 @@ def test_forced_bitmap_dedup_and_graph_replay():
         assert np.array_equal(r3.ids, base.ids)
     ctx.close()
     idx.free()
+
+
+@pytest.mark.parametrize("d,r,t,n", [(128, 8, None, 2500), (96, 12, 2, 2000), (256, 16, None, 1500)])
+def test_row_restricted_probe_matches_oracle(d, r, t, n):
+    """probe_rows = 1: every radius reports the linear-scan ids, and the counters equal the
+    oracle's query over the rows v <= 2^(floor(radius/t)+1) - 1 of every part (batched,
+    plain, per-query radii and the allocation-free entry point)."""
+    rng = np.random.default_rng(d * 3 + r)
+    pts = rand_points(rng, n, d)
+    pts[50:70] = pts[3]
+    qs = np.concatenate([near(rng, pts, d, r, 40), rand_points(rng, 5, d)])
+    seed = 4242 + d
+    p = oracle.derive_params(seed, d, r, t=t)
+    tables = oracle.build_tables(p, pts)
+    idx = F().build(dev(pts), d, r, seed, t=t)
+    idx.set_tuning(probe_rows=1)
+    for radius in sorted({0, 1, r // 3, r // 2, r}):
+        rows = oracle.probe_rows(p, radius)
+        res = idx.query(dev(qs), radius)
+        plain = idx.query_plain(qs[:8], radius)
+        for i in range(qs.shape[0]):
+            ids, ncoll, ncand = oracle.query(p, pts, tables, qs[i], radius, rows=rows)
+            assert np.array_equal(res.of(i), ids) and np.array_equal(ids, oracle.linear_scan(pts, qs[i], radius))
+            assert (int(res.collisions[i]), int(res.candidates[i])) == (ncoll, ncand), (radius, i)
+            if i < 8:
+                assert np.array_equal(plain.of(i), ids)
+                assert (int(plain.collisions[i]), int(plain.candidates[i])) == (ncoll, ncand)
+        ids_d = torch.zeros(n, dtype=torch.int32, device="cuda")
+        cnt_d = torch.zeros(3, dtype=torch.int64, device="cuda")
+        idx.query_plain_noalloc(dev(qs[0]), radius, ids_d, cnt_d)
+        torch.cuda.synchronize()
+        c0 = cnt_d.cpu().numpy()
+        want0 = oracle.query(p, pts, tables, qs[0], radius, rows=rows)
+        assert np.array_equal(ids_d[: int(c0[0])].cpu().numpy().view(np.uint32), want0[0])
+        assert (int(c0[1]), int(c0[2])) == (want0[1], want0[2])
+    radii = rng.integers(0, r + 1, size=qs.shape[0]).astype(np.uint32)
+    res2 = idx.query(dev(qs), r, radii=torch.from_numpy(radii.view(np.int32)).cuda())
+    for i in range(qs.shape[0]):
+        rad = int(radii[i])
+        ids, ncoll, ncand = oracle.query(p, pts, tables, qs[i], rad, rows=oracle.probe_rows(p, rad))
+        assert np.array_equal(res2.of(i), ids)
+        assert (int(res2.collisions[i]), int(res2.candidates[i])) == (ncoll, ncand)
+    idx.free()
+
+
+@pytest.mark.parametrize("d,r,t", [(100, 5, None), (128, 6, None), (200, 7, None), (128, 8, None),
+                                   (1024, 9, None), (256, 16, None), (2000, 10, 2)])
+def test_wide_hash_tile_is_bit_exact(d, r, t):
+    """hash_tile = 1 (twice the points per WHT block) gives the same keys and the same directory."""
+    rng = np.random.default_rng(d + 5 * r)
+    n = 1333
+    pts = rand_points(rng, n, d)
+    seed = 77 + d
+    p = oracle.derive_params(seed, d, r, t=t)
+    a = F().build(dev(pts), d, r, seed, t=t)
+    b = F().build(dev(pts), d, r, seed, t=t, hash_tile=1)
+    assert b.tuning()["hash_tile"] == 1
+    assert np.array_equal(b.hash(pts[:300]), oracle.keys_direct(p, pts[:300]))
+    for tau in (0, p.T // 2, p.T - 1):
+        ka, ia = a.export_table(tau)
+        kb, ib = b.export_table(tau)
+        assert np.array_equal(ka, kb) and np.array_equal(ia, ib)
+    a.free()
+    b.free()
+
+
+def test_autotune_choices_keep_results(tmp_path):
+    """The autotuner picks query shapes and a WHT tile, caches them, keeps probe_rows, and
+    the chosen shapes give the same answers as the defaults."""
+    fc = F()
+    pts = wl.points(2, 20_000)
+    qs, _ = wl.queries(2, pts, 300)
+    idx = fc.build(dev(pts), 128, 8, 2002)
+    base = idx.query(dev(qs), 8)
+    idx.set_tuning(probe_rows=1)
+    cache = str(tmp_path / "tune.json")
+    chosen = idx.autotune(dev(qs), 8, cache)
+    assert chosen["probe_rows"] == 1 and chosen["hash_tile"] in (0, 1) and chosen["use_graph"] == 1
+    assert idx.tuning() == chosen
+    again = idx.autotune(dev(qs), 8, cache)                      # served from the cache
+    assert again == chosen
+    res = idx.query(dev(qs), 8)
+    assert np.array_equal(res.offs, base.offs) and np.array_equal(res.ids, base.ids)
+    assert np.array_equal(res.collisions, base.collisions)       # radius 8 = r: every row is probed
+    idx.free()

@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_served_answers_alone_equal_mixed():
+@pytest.mark.parametrize("probe_rows", [0, 1])
+def test_served_answers_alone_equal_mixed(probe_rows):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1602_02620_gb300 import fclsh
@@ -31,6 +32,7 @@ def test_served_answers_alone_equal_mixed():
         blocks.append((qs[at:at + size], radius))
         at += size
     idx = fclsh.build(torch.from_numpy(pts.view(np.int64)).cuda(), 256, 16, 5005)
+    idx.set_tuning(probe_rows=probe_rows)
 
     alone = fclsh.Server(idx, slots=1, max_batch_queries=1)
     res_alone = []
