@@ -41,9 +41,9 @@ CFG = 2
 # algorithmic bytes.  Set an entry to None when its kernel changes.
 TRAFFIC_RATIO = {
     "hash": 0.950,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
-    "scatter": 1.017,     # profiles/radix_scatter_kernel_n300k_d128_r8.md
-    "finish": 0.989,      # profiles/segment_one_kernel_n300k_d128_r8.md
-    "hist": None,
+    "scatter": 1.154,     # profiles/radix_scatter_kernel_n300k_d128_r8.md
+    "finish": 0.988,      # profiles/segment_one_kernel_n300k_d128_r8.md
+    "hist": 1.017,        # profiles/radix_hist_kernel_n300k_d128_r8.md
 }
 
 
