@@ -166,7 +166,9 @@ fclsh_status fclsh_bucket(const fclsh_index *idx, uint32_t table, uint64_t key, 
 
 /*
  * Every (key, id) entry of table `table` in directory order: ascending by
- * (key mod 2^slot_bits, id).  keys_out/ids_out: host arrays of n entries.  Synchronous.
+ * key mod 2^slot_bits (the slot); the order of the entries inside one slot is
+ * unspecified (it may differ between two builds of the same index).
+ * keys_out/ids_out: host arrays of n entries.  Synchronous.
  */
 fclsh_status fclsh_export_table(const fclsh_index *idx, uint32_t table, uint64_t *keys_out, uint32_t *ids_out);
 

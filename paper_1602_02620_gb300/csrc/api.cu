@@ -713,14 +713,14 @@ extern "C" fclsh_status fclsh_bucket(const fclsh_index *idx, uint32_t table, uin
     if (!ent.empty())
         FCLSH_CUDA(cudaMemcpy(ent.data(), idx->ent + (uint64_t)table * idx->n + lohi[0], ent.size() * 8,
                               cudaMemcpyDeviceToHost));
-    uint64_t c = 0;
+    // the bucket: the slot's entries with equal high key bits (their order in the run is unspecified)
+    std::vector<uint32_t> ids;
     const uint32_t fp = (uint32_t)(key >> idx->slot_bits);
     for (uint64_t e : ent)
-        if ((uint32_t)(e >> 32) == fp && key < kP) {
-            if (c < cap) ids_out[c] = (uint32_t)e;
-            ++c;
-        }
-    *count = c;
+        if ((uint32_t)(e >> 32) == fp && key < kP) ids.push_back((uint32_t)e);
+    std::sort(ids.begin(), ids.end());
+    for (uint64_t i = 0; i < ids.size() && i < cap; ++i) ids_out[i] = ids[i];
+    *count = ids.size();
     return FCLSH_OK;
 }
 

@@ -38,8 +38,8 @@ struct RadixArgs {
     uint32_t dmask;               // digit = (key >> shift) & dmask: the last pass may have fewer than 8 bits
     uint32_t *hist;               // [rows][256][tiles]
     uint32_t rows;
-    uint32_t pack_sb;             // PACK: slot bits of the directory
-    uint32_t pack_idbits;         // PACK: bits of an id
+    uint32_t pack_sb;             // partition_scatter_kernel: slot bits of the directory
+    uint32_t pack_idbits;         // partition_scatter_kernel: bits of an id
 };
 
 // Packed partition output for the MSD directory path:
@@ -114,7 +114,7 @@ __device__ __forceinline__ uint32_t same_digit_lanes(uint32_t digit, bool valid)
 // and the sub-tile's digit runs are written out as contiguous, coalesced runs.
 // Each digit's global cursor starts at the tile's place from the scanned
 // (row, digit, tile) histogram and advances by the digit's count per sub-tile.
-template <bool IDS, bool IMPLICIT, bool PACK = false>
+template <bool IDS, bool IMPLICIT>
 __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArgs a)
 {
     constexpr int R = kIPT;   // rounds per warp and sub-tile: 8 x 32 = 256 items
@@ -186,9 +186,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArg
             if (idx < len) {
                 const uint32_t digit = (uint32_t)(key[r] >> a.shift) & a.dmask;
                 const uint32_t lp = wh[digit] + lr[r];
-                sk[lp] = PACK ? pack_entry(key[r], id[r], a.pack_sb, a.pack_idbits) : key[r];
+                sk[lp] = key[r];
                 sg[lp] = global_off[digit] + lp;
-                if (IDS && !PACK) si[lp] = id[r];
+                if (IDS) si[lp] = id[r];
             }
         }
         __syncthreads();
@@ -196,8 +196,70 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArg
         for (uint32_t i = tid; i < sub_n; i += kSortThreads) {
             const uint32_t g = sg[i];
             a.keys_out[g] = sk[i];
-            if (IDS && !PACK) a.ids_out[g] = si[i];
+            if (IDS) a.ids_out[g] = si[i];
         }
+    }
+}
+
+// Partition of every table by the top 8 slot bits for the s <= 20 directory path,
+// packed output.  It need not be stable: segment_one_kernel and
+// segment_finish_kernel group a segment by slot whatever its order, and the order
+// inside a slot is not part of the directory.  So a sub-tile is ranked with
+// shared-memory atomics on one counter per digit (no warp-level multisplit),
+// reordered by digit in shared memory and written as contiguous digit runs; each
+// digit's global cursor starts at the tile's place from the scanned (row, digit,
+// tile) histogram and advances by the digit's count per sub-tile.
+__global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(RadixArgs a)
+{
+    constexpr int R = kIPT;   // items per thread and sub-tile
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kSortSub] packed entries in digit order
+    uint32_t *sg = reinterpret_cast<uint32_t *>(sk + kSortSub);   // [kSortSub] their global positions
+    __shared__ uint32_t cnt[256], gofs[256];
+    const uint32_t row = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
+    const uint64_t len = a.len;
+    const uint64_t base = (uint64_t)tile * kSortTile;
+    if (base >= len) return;   // uniform: an empty tile has no items
+    uint32_t cursor = a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile];   // digit tid's next global place
+    const uint64_t *K = a.keys_in + (uint64_t)row * len;
+    for (uint64_t sbase = base; sbase < len && sbase < base + kSortTile; sbase += kSortSub) {
+        uint64_t key[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = sbase + (uint64_t)r * kSortThreads + tid;
+            key[r] = idx < len ? K[idx] : 0;
+        }
+        cnt[tid] = 0;
+        __syncthreads();   // (also: the previous sub-tile's output is read out)
+        uint32_t rk[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = sbase + (uint64_t)r * kSortThreads + tid;
+            if (idx < len) rk[r] = atomicAdd(&cnt[(uint32_t)(key[r] >> a.shift) & 255u], 1u);
+        }
+        __syncthreads();
+        {   // thread tid owns digit tid: its place in the sub-tile and its global offset
+            const uint32_t c = cnt[tid];
+            uint32_t tot;
+            const uint32_t start = block_excl_scan<uint32_t>(c, &tot);   // barriers inside
+            gofs[tid] = cursor - start;   // global place of sub-tile position p of digit tid: gofs + p
+            cnt[tid] = start;
+            cursor += c;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = sbase + (uint64_t)r * kSortThreads + tid;
+            if (idx < len) {
+                const uint32_t digit = (uint32_t)(key[r] >> a.shift) & 255u;
+                const uint32_t lp = cnt[digit] + rk[r];
+                sk[lp] = pack_entry(key[r], (uint32_t)idx, a.pack_sb, a.pack_idbits);
+                sg[lp] = gofs[digit] + lp;
+            }
+        }
+        __syncthreads();
+        const uint32_t sub_n = (uint32_t)((len - sbase) < (uint64_t)kSortSub ? (len - sbase) : (uint64_t)kSortSub);
+        for (uint32_t i = tid; i < sub_n; i += kSortThreads) a.keys_out[sg[i]] = sk[i];
     }
 }
 
@@ -450,10 +512,10 @@ __device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t til
 // the common case).  Entries are counted into their slots with shared-memory
 // atomics; thread i owns the eight consecutive slots [8i, 8i+8): it scans their
 // counts in registers and writes their directory words with two vector stores.
-// Each entry is then placed in its slot's run, and every entry finds its final
-// place in the run by counting the run's smaller (key bits, id) (runs are short:
-// Poisson with mean <= 1 for uniform keys), so no run is sorted serially.  Larger
-// segments are listed for segment_finish_kernel.
+// Each entry is then placed in its slot's run at the place its atomic returned
+// (the order inside a run is not part of the directory), and the segment's
+// entries are written with coalesced stores.  Larger segments are listed for
+// segment_finish_kernel.
 __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
                                                                      uint32_t sb, uint32_t idbits,
                                                                      const uint32_t *__restrict__ hist, uint32_t tiles,
@@ -531,41 +593,18 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
     const uint32_t before = __shfl_sync(0xffffffffu, wincl - wv, warp) + incl - tot;
 #pragma unroll
     for (int i = 0; i < kOneSlots; ++i) st[i] += before;
-    if (owner) {   // each slot's first entry (low 16 bits) and length (high 16 bits), both <= 4096
-        cnt4[pj(j0) / 4] = make_uint4(st[0] | c[0] << 16, st[1] | c[1] << 16, st[2] | c[2] << 16, st[3] | c[3] << 16);
-        cnt4[pj(j0) / 4 + 1] =
-            make_uint4(st[4] | c[4] << 16, st[5] | c[5] << 16, st[6] | c[6] << 16, st[7] | c[7] << 16);
+    if (owner) {   // the owned slots' first entries, for the placement and the directory
+        cnt4[pj(j0) / 4] = make_uint4(st[0], st[1], st[2], st[3]);
+        cnt4[pj(j0) / 4 + 1] = make_uint4(st[4], st[5], st[6], st[7]);
         const uint32_t l = (uint32_t)lo;
         uint4 *O4 = reinterpret_cast<uint4 *>(O + j0);
         O4[0] = make_uint4(l + st[0], l + st[1], l + st[2], l + st[3]);
         O4[1] = make_uint4(l + st[4], l + st[5], l + st[6], l + st[7]);
     }
     __syncthreads();
-    uint32_t sc[kOneItems];
 #pragma unroll
     for (int r = 0; r < kOneItems; ++r)
-        if (tid + r * kOneThreads < cn) {
-            sc[r] = cnt[pj((uint32_t)(v[r] >> 52) & smask)];
-            ck[(sc[r] & 0xFFFFu) + rk[r]] = v[r];   // the run of the slot, in arrival order
-        }
-    __syncthreads();
-    // Final place of each entry: its slot's first entry plus the number of entries of
-    // the run with smaller (key bits, id), so runs come out ordered by (key bits, id).
-#pragma unroll
-    for (int r = 0; r < kOneItems; ++r)
-        if (tid + r * kOneThreads < cn) {
-            const uint32_t s0 = sc[r] & 0xFFFFu, len_run = sc[r] >> 16;
-            uint32_t p = s0;
-            if (len_run > 1) {
-                const uint64_t me = v[r] & low52;
-                for (uint32_t k = s0; k < s0 + len_run; ++k) p += (ck[k] & low52) < me ? 1u : 0u;
-            }
-            sc[r] = p;
-        }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kOneItems; ++r)
-        if (tid + r * kOneThreads < cn) ck[sc[r]] = v[r];
+        if (tid + r * kOneThreads < cn) ck[cnt[pj((uint32_t)(v[r] >> 52) & smask)] + rk[r]] = v[r];
     __syncthreads();
     for (uint32_t i = tid; i < cn; i += kOneThreads) {
         const uint64_t x = ck[i];
@@ -575,8 +614,8 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
 
 // Segments longer than one chunk (listed by segment_one_kernel; clustered or
 // duplicate-heavy data): one block per listed segment writes its directory and
-// entries chunk by chunk, each chunk through two stable shared-memory digit
-// passes, so slot runs of any length stay in id order.
+// entries chunk by chunk, each chunk grouped by slot through two shared-memory
+// digit passes.
 __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const uint64_t *__restrict__ packed,
                                                                         uint64_t n, uint32_t sb, uint32_t idbits,
                                                                         const uint32_t *__restrict__ hist,
@@ -686,8 +725,8 @@ static cudaError_t scatter_smem_init()
             e = cudaFuncSetAttribute(radix_scatter_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kScatterSmemKeys);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(radix_scatter_kernel<true, true, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmemIds);
+            e = cudaFuncSetAttribute(partition_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kScatterSmemKeys);
         return e;
     }();
     return once;
@@ -803,7 +842,7 @@ cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t 
     return scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s);
 }
 
-// Stable partition of every table by the top 8 slot bits (ids in order), packed output.
+// Partition of every table by the top 8 slot bits, packed output.
 cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
                                   cudaStream_t s)
 {
@@ -812,7 +851,7 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
     const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
     RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - 8, 255u, buf.hist, rows, sb,
                 id_bits(len)};
-    radix_scatter_kernel<true, true, true><<<dim3(tiles, rows), kSortThreads, kScatterSmemIds, s>>>(a);
+    partition_scatter_kernel<<<dim3(tiles, rows), kSortThreads, kScatterSmemKeys, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }

@@ -130,6 +130,8 @@ def test_bucket_tables_bit_exact(d, r, n):
     p = oracle.derive_params(seed, d, r)
     for tau in sorted({0, 1, p.T // 2, p.T - 1}):
         keys, ids = idx.export_table(tau)
+        sl = keys & np.uint64((1 << idx.info["slot_bits"]) - 1)
+        assert np.all(np.diff(sl.astype(np.int64)) >= 0)        # entries grouped by slot, slots ascending
         order = np.lexsort((ids, keys))
         ok, oi = oracle.table(p, pts, tau)
         assert np.array_equal(keys[order], ok) and np.array_equal(ids[order], oi)
@@ -305,10 +307,13 @@ def test_wide_hash_tile_is_bit_exact(d, r, t):
     b = F().build(dev(pts), d, r, seed, t=t, hash_tile=1)
     assert b.tuning()["hash_tile"] == 1
     assert np.array_equal(b.hash(pts[:300]), oracle.keys_direct(p, pts[:300]))
-    for tau in (0, p.T // 2, p.T - 1):
+    for tau in (0, p.T // 2, p.T - 1):                          # the same tables (order inside a slot is free)
         ka, ia = a.export_table(tau)
         kb, ib = b.export_table(tau)
-        assert np.array_equal(ka, kb) and np.array_equal(ia, ib)
+        oa, ob = np.lexsort((ia, ka)), np.lexsort((ib, kb))
+        assert np.array_equal(ka[oa], kb[ob]) and np.array_equal(ia[oa], ib[ob])
+        assert np.array_equal(ka & np.uint64((1 << a.info["slot_bits"]) - 1),
+                              np.sort(ka & np.uint64((1 << a.info["slot_bits"]) - 1)))   # grouped by slot
     a.free()
     b.free()
 
