@@ -560,13 +560,16 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     const uint64_t budget = o.mem_budget ? o.mem_budget : free_b / 4;
     // radix-sort buffers for a chunk of tables: (key, id) twice, plus histograms
     const bool msd = msd_path_applies(sb);
-    // per table: the partition pass's packed entries (MSD) or two (key, id) buffers (LSD), plus histograms
-    const uint64_t per_row = n * (msd ? 8 : 24) + sort_hist_entries(1, n) * 4 + 64;
+    // per table: the partition pass's packed entries (MSD: compact, or in bins of `cap` per segment)
+    // or two (key, id) buffers (LSD), plus histograms
+    const uint32_t cap = msd ? msd_bin_capacity(n) : 0;
+    const uint64_t width = msd ? std::max<uint64_t>(n, (uint64_t)256 * cap) : n;   // packed entries per table
+    const uint64_t per_row = (msd ? width * 8 : n * 24) + sort_hist_entries(1, n) * 4 + 257 * 4 + 256 * 4 + 64;
     uint64_t rows = std::max<uint64_t>(1, budget / per_row);
     rows = std::min<uint64_t>(rows, L);
-    rows = std::min<uint64_t>(rows, std::max<uint64_t>(1, 0xFFFFFFF0ULL / n));
+    rows = std::min<uint64_t>(rows, std::max<uint64_t>(1, 0xFFFFFFF0ULL / width));   // 32-bit entry indexes
     SortBuffers sbuf{};
-    if ((e = tmp.alloc(&sbuf.keys_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
+    if ((e = tmp.alloc(&sbuf.keys_a, rows * width)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
     if (!msd) {
         if ((e = tmp.alloc(&sbuf.keys_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
         if ((e = tmp.alloc(&sbuf.ids_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
@@ -581,7 +584,14 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if (msd) {
         if ((e = tmp.alloc(&big_cnt, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment list)");
         if ((e = tmp.alloc(&big, rows * 256)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment list)");
+        if ((e = tmp.alloc(&sbuf.seg_out, rows * 257)) != cudaSuccess ||
+            (e = tmp.alloc(&sbuf.bin_cnt, rows * 256)) != cudaSuccess || (e = tmp.alloc(&sbuf.status, 1)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(segment bounds)");
     }
+    // The s <= 20 path first partitions into fixed-capacity bins (no histogram pass); a
+    // row chunk whose bins overflow (skewed keys) is partitioned again the exact way, and
+    // the remaining chunks go the exact way at once.
+    bool use_bins = msd;
 
     for (uint32_t k = 0; k < t; ++k) {
         {
@@ -593,16 +603,28 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
             const uint32_t nr = (uint32_t)std::min<uint64_t>(rows, L - r0);
             const uint64_t grow = (uint64_t)k * L + r0;
             if (msd) {
-                {
-                    PhaseTimer p7(idx, 7, s);
-                    FCLSH_CUDA(msd_partition_hist(keys + r0 * n, nr, n, sb, sbuf, s));
+                bool binned = false;
+                if (use_bins) {
+                    {
+                        PhaseTimer p5(idx, 5, s);
+                        FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, cap, sbuf, s));
+                    }
+                    uint32_t status = 0;
+                    FCLSH_CUDA(cudaMemcpyAsync(&status, sbuf.status, 4, cudaMemcpyDeviceToHost, s));
+                    FCLSH_CUDA(cudaStreamSynchronize(s));
+                    binned = status == 0;
+                    use_bins = binned;
                 }
-                {
+                if (!binned) {
+                    {
+                        PhaseTimer p7(idx, 7, s);
+                        FCLSH_CUDA(msd_partition_hist(keys + r0 * n, nr, n, sb, sbuf, s));
+                    }
                     PhaseTimer p5(idx, 5, s);
-                    FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, sbuf, s));
+                    FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, 0, sbuf, s));
                 }
                 PhaseTimer p6(idx, 6, s);
-                FCLSH_CUDA(msd_finish(nr, n, sb, sbuf, big_cnt, big, idx->ent + grow * n,
+                FCLSH_CUDA(msd_finish(nr, n, sb, binned ? cap : 0, sbuf, big_cnt, big, idx->ent + grow * n,
                                       idx->offs + grow * idx->offs_stride(), idx->sm_count, s));
                 continue;
             }

@@ -16,6 +16,7 @@
 // gives each tile's digit run its final position, rows included, in one scan.
 // Stable ranks inside a tile come from digit-bit ballots + per-warp digit counts.
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -40,6 +41,9 @@ struct RadixArgs {
     uint32_t rows;
     uint32_t pack_sb;             // partition_scatter_kernel: slot bits of the directory
     uint32_t pack_idbits;         // partition_scatter_kernel: bits of an id
+    uint32_t cap;                 // partition_scatter_kernel: 0 = places from hist; else bins of cap entries
+    uint32_t *bin_cnt;            //   [rows][256] entries reserved in each bin (cap > 0)
+    uint32_t *status;             //   bit 0 set when a bin overflowed (cap > 0)
 };
 
 // Packed partition output for the MSD directory path:
@@ -206,9 +210,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_scatter_kernel(RadixArg
 // segment_finish_kernel group a segment by slot whatever its order, and the order
 // inside a slot is not part of the directory.  So a sub-tile is ranked with
 // shared-memory atomics on one counter per digit (no warp-level multisplit),
-// reordered by digit in shared memory and written as contiguous digit runs; each
-// digit's global cursor starts at the tile's place from the scanned (row, digit,
-// tile) histogram and advances by the digit's count per sub-tile.
+// reordered by digit in shared memory and written as contiguous digit runs.
+// Where the runs go: with cap = 0 each digit's global cursor starts at the tile's
+// place from the scanned (row, digit, tile) histogram and advances by the digit's
+// count per sub-tile.  With cap > 0 (no histogram pass) segment (row, digit) is a
+// bin of cap entries and each sub-tile reserves its run in the bin with one global
+// atomic; a run that would pass the bin's end is dropped and flagged in *status
+// (the caller then rebuilds these tables the exact way).
 __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(RadixArgs a)
 {
     constexpr int R = kIPT;   // items per thread and sub-tile
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
     const uint64_t len = a.len;
     const uint64_t base = (uint64_t)tile * kSortTile;
     if (base >= len) return;   // uniform: an empty tile has no items
-    uint32_t cursor = a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile];   // digit tid's next global place
+    uint32_t cursor = a.cap ? 0u : a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile];   // digit tid's next place
     const uint64_t *K = a.keys_in + (uint64_t)row * len;
     for (uint64_t sbase = base; sbase < len && sbase < base + kSortTile; sbase += kSortSub) {
         uint64_t key[R];
@@ -242,9 +250,19 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
             const uint32_t c = cnt[tid];
             uint32_t tot;
             const uint32_t start = block_excl_scan<uint32_t>(c, &tot);   // barriers inside
-            gofs[tid] = cursor - start;   // global place of sub-tile position p of digit tid: gofs + p
+            if (a.cap == 0) {
+                gofs[tid] = cursor - start;   // global place of sub-tile position p of digit tid: gofs + p
+                cursor += c;
+            } else {
+                const uint32_t at = c ? atomicAdd(a.bin_cnt + (uint64_t)row * 256 + tid, c) : 0u;
+                if (at + c <= a.cap) {
+                    gofs[tid] = (uint32_t)(((uint64_t)row * 256 + tid) * a.cap + at) - start;
+                } else {
+                    gofs[tid] = 0xFFFFFFFFu;   // dropped: the bin is full
+                    atomicOr(a.status, 1u);
+                }
+            }
             cnt[tid] = start;
-            cursor += c;
         }
         __syncthreads();
 #pragma unroll
@@ -253,13 +271,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
             if (idx < len) {
                 const uint32_t digit = (uint32_t)(key[r] >> a.shift) & 255u;
                 const uint32_t lp = cnt[digit] + rk[r];
+                const uint32_t go = gofs[digit];
                 sk[lp] = pack_entry(key[r], (uint32_t)idx, a.pack_sb, a.pack_idbits);
-                sg[lp] = gofs[digit] + lp;
+                sg[lp] = go == 0xFFFFFFFFu ? go : go + lp;
             }
         }
         __syncthreads();
         const uint32_t sub_n = (uint32_t)((len - sbase) < (uint64_t)kSortSub ? (len - sbase) : (uint64_t)kSortSub);
-        for (uint32_t i = tid; i < sub_n; i += kSortThreads) a.keys_out[sg[i]] = sk[i];
+        for (uint32_t i = tid; i < sub_n; i += kSortThreads) {
+            const uint32_t g = sg[i];
+            if (g != 0xFFFFFFFFu) a.keys_out[g] = sk[i];
+        }
     }
 }
 
@@ -499,13 +521,23 @@ constexpr int kOneSlots = 8;                         // directory slots owned pe
 // vector accesses of a quarter-warp fall on distinct banks.
 __device__ __forceinline__ uint32_t pj(uint32_t j) { return j + ((j >> 5) << 2); }
 
-// Segment boundaries of the partition: [lo, hi) within row `row` for top digit g.
-__device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t tiles, uint64_t n, uint32_t row,
-                                              uint32_t g, uint64_t *lo, uint64_t *hi)
+// seg_out[row][g] = first directory entry of segment (row, g) within its row, for
+// g = 0..255, and seg_out[row][256] = n: from the scanned (row, digit, tile)
+// histogram (bin_cnt == nullptr) or by a prefix over the bins' fills.  One block per row.
+__global__ void __launch_bounds__(256) segment_bounds_kernel(const uint32_t *__restrict__ hist, uint32_t tiles,
+                                                             uint64_t n, const uint32_t *__restrict__ bin_cnt,
+                                                             uint32_t *__restrict__ seg_out)
 {
-    const uint64_t rowbase = (uint64_t)row * n;
-    *lo = hist[((uint64_t)row * 256 + g) * tiles] - rowbase;
-    *hi = g < 255 ? hist[((uint64_t)row * 256 + g + 1) * tiles] - rowbase : n;
+    const uint32_t row = blockIdx.x, tid = threadIdx.x;
+    uint32_t v;
+    if (bin_cnt) {
+        uint32_t tot;
+        v = block_excl_scan<uint32_t>(bin_cnt[(uint64_t)row * 256 + tid], &tot);
+    } else {
+        v = hist[((uint64_t)row * 256 + tid) * tiles] - (uint32_t)((uint64_t)row * n);
+    }
+    seg_out[(uint64_t)row * 257 + tid] = v;
+    if (tid == 0) seg_out[(uint64_t)row * 257 + 256] = (uint32_t)n;
 }
 
 // One block per (segment, table) for segments of at most one chunk (4096 entries,
@@ -516,9 +548,12 @@ __device__ __forceinline__ void segment_range(const uint32_t *hist, uint32_t til
 // (the order inside a run is not part of the directory), and the segment's
 // entries are written with coalesced stores.  Larger segments are listed for
 // segment_finish_kernel.
+// Segment (row, g) of the partition: seg_out[row][g] .. seg_out[row][g+1] in the row's
+// directory entries; its packed input starts at row * in_stride + (cap ? g * cap : seg_out[row][g]).
 __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
-                                                                     uint32_t sb, uint32_t idbits,
-                                                                     const uint32_t *__restrict__ hist, uint32_t tiles,
+                                                                     uint64_t in_stride, uint32_t cap, uint32_t sb,
+                                                                     uint32_t idbits,
+                                                                     const uint32_t *__restrict__ seg_out,
                                                                      uint64_t *__restrict__ ent,
                                                                      uint32_t *__restrict__ offs,
                                                                      unsigned long long *big_cnt, uint32_t *big)
@@ -531,16 +566,15 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
     const uint32_t lane = tid & 31, warp = tid >> 5;
     const uint32_t subb = sb - 8, nsub = 1u << subb, smask = nsub - 1;
     const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
-    uint64_t lo, hi;
-    segment_range(hist, tiles, n, row, g, &lo, &hi);
-    const uint64_t len = hi - lo;
-    if (len > (uint64_t)kSegChunk) {
+    const uint32_t lo = seg_out[(uint64_t)row * 257 + g], hi = seg_out[(uint64_t)row * 257 + g + 1];
+    const uint32_t len = hi - lo;
+    if (len > (uint32_t)kSegChunk) {
         if (tid == 0) big[atomicAdd(big_cnt, 1ULL)] = row * 256 + g;
         return;
     }
-    const uint32_t cn = (uint32_t)len;
+    const uint32_t cn = len;
     const uint64_t rowbase = (uint64_t)row * n;
-    const uint64_t *Pk = packed + rowbase + lo;
+    const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)lo);
     uint64_t *E = ent + rowbase + lo;
     uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;   // 16-byte aligned (nsub >= 8)
     if (g == 255 && tid == 0) O[nsub] = (uint32_t)n;
@@ -617,9 +651,10 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
 // entries chunk by chunk, each chunk grouped by slot through two shared-memory
 // digit passes.
 __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const uint64_t *__restrict__ packed,
-                                                                        uint64_t n, uint32_t sb, uint32_t idbits,
-                                                                        const uint32_t *__restrict__ hist,
-                                                                        uint32_t tiles, uint64_t *__restrict__ ent,
+                                                                        uint64_t n, uint64_t in_stride, uint32_t cap,
+                                                                        uint32_t sb, uint32_t idbits,
+                                                                        const uint32_t *__restrict__ seg_out,
+                                                                        uint64_t *__restrict__ ent,
                                                                         uint32_t *__restrict__ offs,
                                                                         const unsigned long long *big_cnt,
                                                                         const uint32_t *big)
@@ -639,10 +674,9 @@ __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const ui
     const uint32_t b1 = subb / 2, m1 = (1u << b1) - 1;
     const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
     const uint64_t rowbase = (uint64_t)row * n;
-    const uint64_t seg_lo = hist[((uint64_t)row * 256 + g) * tiles] - rowbase;
-    const uint64_t seg_hi = g < 255 ? hist[((uint64_t)row * 256 + g + 1) * tiles] - rowbase : n;
+    const uint32_t seg_lo = seg_out[(uint64_t)row * 257 + g], seg_hi = seg_out[(uint64_t)row * 257 + g + 1];
     const uint64_t seg_len = seg_hi - seg_lo;
-    const uint64_t *Pk = packed + rowbase + seg_lo;
+    const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)seg_lo);
     uint64_t *E = ent + rowbase + seg_lo;
     uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;
     auto sub_of = [&](uint64_t v) { return (uint32_t)(v >> 52) & smask; };
@@ -842,22 +876,29 @@ cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t 
     return scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s);
 }
 
-// Partition of every table by the top 8 slot bits, packed output.
-cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
-                                  cudaStream_t s)
+// Partition of every table by the top 8 slot bits, packed output: into places from
+// the scanned histogram (cap = 0), or into bins of cap entries per (row, digit)
+// (no histogram; buf.status bit 0 reports a full bin).
+cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap,
+                                  SortBuffers &buf, cudaStream_t s)
 {
     cudaError_t e = scatter_smem_init();
     if (e != cudaSuccess) return e;
     const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
     RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - 8, 255u, buf.hist, rows, sb,
-                id_bits(len)};
+                id_bits(len), cap, buf.bin_cnt, buf.status};
+    if (cap) {
+        if ((e = cudaMemsetAsync(buf.bin_cnt, 0, (size_t)rows * 256 * 4, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(buf.status, 0, 4, s)) != cudaSuccess) return e;
+    }
     partition_scatter_kernel<<<dim3(tiles, rows), kSortThreads, kScatterSmemKeys, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf, unsigned long long *big_cnt,
-                       uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count, cudaStream_t s)
+cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, SortBuffers &buf,
+                       unsigned long long *big_cnt, uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count,
+                       cudaStream_t s)
 {
     static cudaError_t once = [] {
         cudaError_t e = cudaFuncSetAttribute(segment_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -871,15 +912,30 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &bu
     if (reinterpret_cast<uintptr_t>(offs) & 15) return cudaErrorMisalignedAddress;   // vector stores of offsets
     const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
     const uint32_t idb = id_bits(len);
+    const uint64_t in_stride = cap ? (uint64_t)256 * cap : len;
+    segment_bounds_kernel<<<rows, 256, 0, s>>>(buf.hist, tiles, len, cap ? buf.bin_cnt : nullptr, buf.seg_out);
+    note_launch();
     cudaError_t e = cudaMemsetAsync(big_cnt, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    segment_one_kernel<<<dim3(256, rows), kOneThreads, segment_one_smem(), s>>>(buf.keys_a, len, sb, idb, buf.hist,
-                                                                                  tiles, ent, offs, big_cnt, big);
+    segment_one_kernel<<<dim3(256, rows), kOneThreads, segment_one_smem(), s>>>(buf.keys_a, len, in_stride, cap, sb,
+                                                                                  idb, buf.seg_out, ent, offs, big_cnt,
+                                                                                  big);
     note_launch();
-    segment_finish_kernel<<<sm_count, kSegThreads, segment_finish_smem(), s>>>(buf.keys_a, len, sb, idb, buf.hist,
-                                                                                 tiles, ent, offs, big_cnt, big);
+    segment_finish_kernel<<<sm_count, kSegThreads, segment_finish_smem(), s>>>(buf.keys_a, len, in_stride, cap, sb,
+                                                                                 idb, buf.seg_out, ent, offs, big_cnt,
+                                                                                 big);
     note_launch();
     return cudaGetLastError();
+}
+
+// Entries per bin of the histogram-free partition: the mean segment n/256 plus
+// eight standard deviations of its binomial count (and a margin), so that for
+// keys spread like independent uniform values no bin overflows in practice.
+uint32_t msd_bin_capacity(uint64_t n)
+{
+    const double mean = (double)n / 256.0;
+    const uint64_t c = (uint64_t)(mean + 8.0 * sqrt(mean) + 64.0);
+    return (uint32_t)((c + 3) & ~3ULL);
 }
 
 }  // namespace fclsh
