@@ -41,9 +41,9 @@ CFG = 2
 # algorithmic bytes.  Set an entry to None when its kernel changes.
 TRAFFIC_RATIO = {
     "hash": 0.950,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
-    "scatter": 1.154,     # profiles/radix_scatter_kernel_n300k_d128_r8.md
-    "finish": 0.988,      # profiles/segment_one_kernel_n300k_d128_r8.md
-    "hist": 1.017,        # profiles/radix_hist_kernel_n300k_d128_r8.md
+    "scatter": 0.983,     # profiles/partition_scatter_kernel_n300k_d128_r8.md
+    "finish": 0.999,      # profiles/segment_one_kernel_n300k_d128_r8.md
+    "hist": None,         # (only on the histogram fallback of skewed keys)
 }
 
 
@@ -376,7 +376,7 @@ def main():
     # ---- rooflines (HBM) of the build's kernels, from the CUDA events of the timed steps.
     # Algorithmic bytes per launch:
     #   hash (Algorithm 2, one part): n * (d/8 read + 8 B per key for its W-1 tables)
-    #   partition scatter (radix_scatter_kernel): per entry 8 B read + 8 B packed write
+    #   partition scatter (partition_scatter_kernel): per entry 8 B read + 8 B packed write
     #   partition histogram (radix_hist_kernel + scan): per entry 8 B read
     #   segment finish: per entry 8 B read + 8 B written, plus 4 B per directory slot
     peak, peak_kind = peaks()
@@ -386,7 +386,7 @@ def main():
     slots = L * ((1 << info["slot_bits"]) + 1)
     stages = {
         "hash_tile_kernel (Algorithm 2, all W-1 keys per point)": (acc["build_hash"], w.n * (w.d / 8 + 8 * L), "hash"),
-        "radix_scatter_kernel (stable partition by the top 8 slot bits, packed output)":
+        "partition_scatter_kernel (partition by the top 8 slot bits into bins, packed output)":
             (acc["build_partition"], 16 * entries, "scatter"),
         "radix_hist_kernel + scan (partition histogram)": (acc["build_partition_hist"], 8 * entries, "hist"),
         "segment finish (segment_one_kernel + segment_finish_kernel)":
