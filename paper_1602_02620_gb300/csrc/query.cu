@@ -12,10 +12,12 @@
 // heavy bucket never serialises on one lane.  Duplicates are removed with a
 // shared-memory hash set when the query's bucket ranges hold at most half its
 // capacity, and otherwise with an n-bit bitmap owned by the CTA (the bitmap of
-// Sec. 4.1), cleared after the query.  Hits collect in shared memory and are
-// sorted there (up to 4,096 per query); a query with more hits walks its buckets
-// again into the bitmap and reads its ids out of it in order.  Each query writes
-// one sorted run; a gather kernel lays the runs out as CSR.
+// Sec. 4.1), cleared after the query: a returning atomic per collision tells a new
+// candidate, or, when the ranges hold more entries than the bitmap has words, the
+// collisions only mark it and one sweep of the bitmap then verifies the marked ids.
+// Hits collect in shared memory and are sorted there (up to 4,096 per query); a
+// query with more hits marks them in the bitmap and reads its ids out of it in
+// order.  Each query writes one sorted run; a gather kernel lays the runs out as CSR.
 #include "common.cuh"
 
 namespace fclsh {
@@ -99,26 +101,9 @@ struct Counters {
     uint32_t res = 0;
 };
 
-// One bucket entry per lane (is_coll = key matched); warp-collective.
-__device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
-                                              bool bitmap_mode, uint32_t radius, bool is_coll, uint32_t id, Counters &c,
-                                              uint32_t *res_s, uint32_t *s_nres)
+// Append the lanes' hits to the query's hit list in shared memory; warp-collective.
+__device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, uint32_t *res_s, uint32_t *s_nres)
 {
-    bool isnew = false;
-    if (is_coll) {
-        c.coll++;
-        if (bitmap_mode) {
-            const uint32_t bit = 1u << (id & 31);
-            isnew = (atomicOr(bm + (id >> 5), bit) & bit) == 0;
-        } else {
-            isnew = hset_insert(hset, a.hset_log2, id);
-        }
-    }
-    bool hit = false;
-    if (isnew) {
-        c.cand++;
-        hit = distance_to(a, q_s, id) <= radius;
-    }
     const uint32_t m = __ballot_sync(0xffffffffu, hit);
     if (m) {
         const uint32_t lane = threadIdx.x & 31;
@@ -132,6 +117,36 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
             if (pos < kResCap) res_s[pos] = id;
         }
     }
+}
+
+// Dedup modes of a query: a shared-memory hash set; the CTA's n-bit bitmap with a
+// returning atomic per collision (a new bit = a new candidate, verified at once);
+// or, for very heavy queries, the bitmap marked without returns and swept afterwards.
+enum DedupMode { DEDUP_HSET = 0, DEDUP_BITMAP = 1, DEDUP_MARK = 2 };
+
+// One bucket entry per lane (is_coll = key matched); warp-collective.
+__device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
+                                              int mode, uint32_t radius, bool is_coll, uint32_t id, Counters &c,
+                                              uint32_t *res_s, uint32_t *s_nres)
+{
+    bool isnew = false;
+    if (is_coll) {
+        c.coll++;
+        const uint32_t bit = 1u << (id & 31);
+        if (mode == DEDUP_MARK)
+            atomicOr(bm + (id >> 5), bit);   // result unused: a fire-and-forget reduction
+        else if (mode == DEDUP_BITMAP)
+            isnew = (atomicOr(bm + (id >> 5), bit) & bit) == 0;
+        else
+            isnew = hset_insert(hset, a.hset_log2, id);
+    }
+    if (mode == DEDUP_MARK) return;   // warp-uniform
+    bool hit = false;
+    if (isnew) {
+        c.cand++;
+        hit = distance_to(a, q_s, id) <= radius;
+    }
+    append_hits(hit, id, c, res_s, s_nres);
 }
 
 // Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
@@ -254,6 +269,9 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         }
         const unsigned long long E = block_sum(local, red64);
         const bool bitmap_mode = E > (hcap >> 1);
+        // more bucket entries than bitmap words: mark the bitmap and sweep it once
+        const bool sweep_mode = bitmap_mode && E > a.bm_words;
+        const int mode = sweep_mode ? DEDUP_MARK : (bitmap_mode ? DEDUP_BITMAP : DEDUP_HSET);
         if (!bitmap_mode)
             for (uint32_t i = tid; i < hcap; i += B) hset[i] = kEmpty;
         if (tid == 0) s_nres = 0;
@@ -273,7 +291,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             for (uint32_t e = 0; e < maxs; ++e) {
                 const bool act = e < short_len;
                 const uint64_t en = act ? __ldg(row + lo + e) : 0;
-                process_entry(a, q_s, hset, bm, bitmap_mode, radius, act && (uint32_t)(en >> 32) == fp,
+                process_entry(a, q_s, hset, bm, mode, radius, act && (uint32_t)(en >> 32) == fp,
                               (uint32_t)en, c, res_s, &s_nres);
             }
             uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
@@ -289,16 +307,46 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                     const uint32_t e = cbase + lane;
                     const bool act = e < l_len;
                     const uint64_t en = act ? __ldg(lrow + e) : 0;
-                    process_entry(a, q_s, hset, bm, bitmap_mode, radius, act && (uint32_t)(en >> 32) == l_fp,
+                    process_entry(a, q_s, hset, bm, mode, radius, act && (uint32_t)(en >> 32) == l_fp,
                                   (uint32_t)en, c, res_s, &s_nres);
                 }
+            }
+        }
+        if (sweep_mode) {
+            // S2/S3 for a very heavy query: every candidate is marked; sweep the bitmap
+            // (warps take 32 consecutive words, a lane a word), verify each marked id,
+            // and leave only the hits marked (cleared below)
+            __threadfence();
+            __syncthreads();
+            for (uint64_t w0 = (uint64_t)warp * 32; w0 < a.bm_words; w0 += (uint64_t)nwarps * 32) {
+                const uint64_t wi = w0 + lane;
+                const uint32_t bits = wi < a.bm_words ? __ldcg(bm + wi) : 0u;
+                c.cand += __popc(bits);
+                uint32_t rem = bits, hits = 0;
+                while (__any_sync(0xffffffffu, rem != 0)) {
+                    bool hit = false;
+                    uint32_t id = 0;
+                    if (rem) {
+                        const uint32_t b = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        id = (uint32_t)(wi * 32 + b);
+                        hit = distance_to(a, q_s, id) <= radius;
+                        if (hit) hits |= 1u << b;
+                    }
+                    append_hits(hit, id, c, res_s, &s_nres);
+                }
+                if (bits) bm[wi] = hits;
             }
         }
         const unsigned long long tc = block_sum(c.coll, red64);
         const unsigned long long td = block_sum(c.cand, red64);
         const uint32_t nres = s_nres;   // read after block_sum's barriers
         __shared__ unsigned long long s_base;
-        if (bitmap_mode) {   // leave the CTA's bitmap all-zero
+        if (sweep_mode && nres <= kResCap) {   // the hits are listed: clear their words
+            for (uint32_t i = tid; i < nres; i += B) bm[res_s[i] >> 5] = 0;
+            __syncthreads();
+        }
+        if (bitmap_mode && !sweep_mode) {   // leave the CTA's bitmap all-zero
             for (uint32_t j = tid; j < Tq; j += B) {
                 const uint64_t *row = a.ent + (uint64_t)probed_table(j, nt, L) * a.n + lo_s[j];
                 const uint32_t len = len_s[j];
@@ -315,8 +363,9 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                 if (base + i < a.cap) a.runs[base + i] = res_s[i];
         } else {
             // More hits than shared memory holds (only in bitmap mode): mark every hit in
-            // the bitmap, then read the ids out in ascending order and clear it again.
-            for (uint32_t j = tid; j < Tq; j += B) {
+            // the bitmap (the sweep left exactly the hits marked), then read the ids out in
+            // ascending order and clear it again.
+            for (uint32_t j = sweep_mode ? Tq : tid; j < Tq; j += B) {
                 const uint32_t tau = probed_table(j, nt, L);
                 const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[j];
                 const uint32_t len = len_s[j];
@@ -334,11 +383,11 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             const uint64_t per = (a.bm_words + B - 1) / B;
             const uint64_t w0 = (uint64_t)tid * per, w1 = min(w0 + per, a.bm_words);
             uint32_t mine = 0;
-            for (uint64_t w = w0; w < w1; ++w) mine += __popc(bm[w]);
+            for (uint64_t w = w0; w < w1; ++w) mine += __popc(__ldcg(bm + w));   // marks are made in L2
             const uint32_t before = (uint32_t)block_excl_scan_u32(mine, red64);
             unsigned long long pos = base + before;
             for (uint64_t w = w0; w < w1; ++w) {
-                uint32_t bits = bm[w];
+                uint32_t bits = __ldcg(bm + w);
                 while (bits) {
                     const uint32_t b = __ffs(bits) - 1;
                     bits &= bits - 1;

@@ -337,3 +337,34 @@ def test_autotune_choices_keep_results(tmp_path):
     assert np.array_equal(res.offs, base.offs) and np.array_equal(res.ids, base.ids)
     assert np.array_equal(res.collisions, base.collisions)       # radius 8 = r: every row is probed
     idx.free()
+
+
+@pytest.mark.parametrize("hlog", [10, 13])
+def test_dedup_modes_match_oracle(hlog):
+    """Queries in every dedup mode -- shared-memory set, returning bitmap, mark-and-sweep
+    bitmap (bucket entries beyond the bitmap's word count), and more than 4,096 hits --
+    report the oracle's ids and counters."""
+    rng = np.random.default_rng(hlog)
+    d, r, n = 64, 3, 9000
+    pts = rand_points(rng, n, d)
+    pts[1000:6000] = pts[17]                                  # 5,001 equal points: > 4,096 hits
+    pts[6000:6600] = pts[23]                                  # 601 equal points
+    for i in range(6600, 6900):                               # 300 points near point 29
+        pts[i] = pts[29]
+        pts[i, 0] ^= np.uint64(1) << np.uint64(int(rng.integers(0, 64)))
+    seed = 606
+    p = oracle.derive_params(seed, d, r)
+    tables = oracle.build_tables(p, pts)
+    qs = np.concatenate([pts[[17, 23, 29, 5, 7000]], near(rng, pts, d, r, 40), rand_points(rng, 5, d)])
+    qs[5:15] = pts[17]
+    idx = F().build(dev(pts), d, r, seed)
+    idx.set_tuning(hash_set_log2=hlog)
+    res = idx.query(dev(qs), r)
+    for i in range(qs.shape[0]):
+        ids, ncoll, ncand = oracle.query(p, pts, tables, qs[i], r)
+        assert np.array_equal(res.of(i), ids), i
+        assert (int(res.collisions[i]), int(res.candidates[i])) == (ncoll, ncand), i
+    assert res.of(0).shape[0] > 4096
+    again = idx.query(dev(qs), r)                              # the bitmaps were left clear
+    assert np.array_equal(again.ids, res.ids) and np.array_equal(again.offs, res.offs)
+    idx.free()
