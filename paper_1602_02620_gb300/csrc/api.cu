@@ -277,6 +277,7 @@ struct fclsh_qctx {
     cudaStream_t g_stream = nullptr;
     uint64_t g_cap = 0;
     fclsh_tuning g_tune{};
+    bool g_seen = false;       // the g_* shape ran once eagerly; its next repeat is captured
     uint64_t g_kernels = 0;
     cudaStream_t own = nullptr;   // used for the NULL stream: blocking, so it orders after legacy-stream work
 };
@@ -340,6 +341,7 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
+        c->g_seen = false;
     }
     if (cap > c->cap) {
         void *ps[] = {c->runs, c->res_ids};
@@ -354,6 +356,7 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
+        c->g_seen = false;
     }
     return FCLSH_OK;
 }
@@ -416,20 +419,34 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
     return FCLSH_OK;
 }
 
+// A batch runs eagerly the first time its shape (inputs, sizes, stream, tuning) is
+// seen; when the same shape comes again it is captured into a CUDA graph, which
+// later repeats replay.  One-off batches never pay for a capture.
 static fclsh_status run_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uint32_t radius, const uint32_t *radii,
                               cudaStream_t s)
 {
     fclsh_index *idx = c->idx;
     const bool graph = idx->tune.use_graph && !idx->timing;
     if (!graph) return enqueue_batch(c, q, nq, radius, radii, s);
-    const bool same = c->gexec && c->g_q == q && c->g_nq == nq && c->g_radius == radius && c->g_radii == radii &&
+    const bool same = c->g_q == q && c->g_nq == nq && c->g_radius == radius && c->g_radii == radii &&
                       c->g_stream == s && c->g_cap == c->cap &&
                       memcmp(&c->g_tune, &idx->tune, sizeof(fclsh_tuning)) == 0;
-    if (!same) {
+    if (!same || !c->g_seen) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
+        c->g_q = q;
+        c->g_nq = nq;
+        c->g_radius = radius;
+        c->g_radii = radii;
+        c->g_stream = s;
+        c->g_cap = c->cap;
+        c->g_tune = idx->tune;
+        c->g_seen = true;
+        return enqueue_batch(c, q, nq, radius, radii, s);
+    }
+    if (!c->gexec) {
         cudaGraph_t g = nullptr;
         FCLSH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = launch_count();
@@ -445,13 +462,6 @@ static fclsh_status run_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uin
         e = cudaGraphInstantiate(&c->gexec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        c->g_q = q;
-        c->g_nq = nq;
-        c->g_radius = radius;
-        c->g_radii = radii;
-        c->g_stream = s;
-        c->g_cap = c->cap;
-        c->g_tune = idx->tune;
     }
     FCLSH_CUDA(cudaGraphLaunch(c->gexec, s));
     note_launch(c->g_kernels);
