@@ -569,23 +569,25 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     FCLSH_CUDA(cudaMemGetInfo(&free_b, &total_b));
     const uint64_t budget = o.mem_budget ? o.mem_budget : free_b / 4;
     // radix-sort buffers for a chunk of tables: (key, id) twice, plus histograms
-    const bool msd = msd_path_applies(sb);
+    const bool msd = msd_path_applies(sb, n);
     // per table: the partition pass's packed entries (MSD: compact, or in bins of `cap` per segment)
     // or two (key, id) buffers (LSD), plus histograms
-    const uint32_t cap = msd ? msd_bin_capacity(n) : 0;
-    const uint64_t width = msd ? std::max<uint64_t>(n, (uint64_t)256 * cap) : n;   // packed entries per table
-    const uint64_t per_row = (msd ? width * 8 : n * 24) + sort_hist_entries(1, n) * 4 + 257 * 4 + 256 * 4 + 64;
+    const uint32_t dbits = msd ? msd_dbits(sb) : 8;
+    const uint64_t nd = (uint64_t)1 << dbits;   // segments per table
+    const uint32_t cap = msd ? msd_bin_capacity(n, dbits) : 0;
+    const uint64_t width = msd ? std::max<uint64_t>(n, nd * cap) : n;   // packed entries per table
+    const uint64_t per_row = (msd ? width * 8 : n * 24) + sort_hist_entries(1, n, dbits) * 4 + (2 * nd + 1) * 4 + 64;
     uint64_t rows = std::max<uint64_t>(1, budget / per_row);
     rows = std::min<uint64_t>(rows, L);
     rows = std::min<uint64_t>(rows, std::max<uint64_t>(1, 0xFFFFFFF0ULL / width));   // 32-bit entry indexes
     SortBuffers sbuf{};
     if ((e = tmp.alloc(&sbuf.keys_a, rows * width)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
-    if (!msd) {
+    if (!msd) {   // (key, id) radix buffers of the LSD path
         if ((e = tmp.alloc(&sbuf.keys_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort keys)");
         if ((e = tmp.alloc(&sbuf.ids_a, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
         if ((e = tmp.alloc(&sbuf.ids_b, rows * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort ids)");
     }
-    sbuf.hist_cap = sort_hist_entries((uint32_t)rows, n);
+    sbuf.hist_cap = sort_hist_entries((uint32_t)rows, n, dbits);
     sbuf.partials_cap = scan_partials_entries(sbuf.hist_cap);
     if ((e = tmp.alloc(&sbuf.hist, sbuf.hist_cap)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort hist)");
     if ((e = tmp.alloc(&sbuf.partials, sbuf.partials_cap)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(sort scan)");
@@ -593,14 +595,14 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     uint32_t *big = nullptr;
     if (msd) {
         if ((e = tmp.alloc(&big_cnt, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment list)");
-        if ((e = tmp.alloc(&big, rows * 256)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment list)");
-        if ((e = tmp.alloc(&sbuf.seg_out, rows * 257)) != cudaSuccess ||
-            (e = tmp.alloc(&sbuf.bin_cnt, rows * 256)) != cudaSuccess || (e = tmp.alloc(&sbuf.status, 1)) != cudaSuccess)
+        if ((e = tmp.alloc(&big, rows * nd)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(segment list)");
+        if ((e = tmp.alloc(&sbuf.seg_out, rows * (nd + 1))) != cudaSuccess ||
+            (e = tmp.alloc(&sbuf.bin_cnt, rows * nd)) != cudaSuccess || (e = tmp.alloc(&sbuf.status, 1)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(segment bounds)");
     }
-    // The s <= 20 path first partitions into fixed-capacity bins (no histogram pass); a
-    // row chunk whose bins overflow (skewed keys) is partitioned again the exact way, and
-    // the remaining chunks go the exact way at once.
+    // The partition path first partitions into fixed-capacity bins (no histogram pass).
+    // A row chunk whose bins overflow (skewed keys) is partitioned again the exact way,
+    // with a per-tile digit histogram, and the remaining chunks go that way at once.
     bool use_bins = msd;
 
     for (uint32_t k = 0; k < t; ++k) {

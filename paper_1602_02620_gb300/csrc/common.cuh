@@ -180,7 +180,7 @@ struct SortBuffers {
     // s <= 20 path: segment bounds [rows][257], bin fills [rows][256], and a status word
     uint32_t *seg_out, *bin_cnt, *status;
 };
-size_t sort_hist_entries(uint32_t rows, uint64_t len);
+size_t sort_hist_entries(uint32_t rows, uint64_t len, uint32_t dbits = 8);
 size_t scan_partials_entries(size_t count);
 cudaError_t radix_sort_rows(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t bits,
                             SortBuffers &buf, bool *out_in_b, cudaStream_t s);
@@ -189,17 +189,20 @@ cudaError_t radix_sort_keys_dev(uint64_t *keys_a, uint64_t *keys_b, const unsign
                                 uint64_t cap, uint32_t bits, uint32_t *hist, uint32_t *partials,
                                 bool *out_in_b, cudaStream_t s);
 size_t sort_keys_hist_entries(uint64_t cap);
-// Directory of `rows` tables straight from their keys when slot_bits - 8 <= 12: one
-// partition by the top 8 slot bits, then one block per (segment, table) that groups
+// Directory of `rows` tables straight from their keys when 11 <= slot_bits <= 23: one
+// partition by the top msd_dbits(slot_bits) slot bits (segments of at most 4,096
+// slots), then one block per (segment, table) that groups
 // the segment by the remaining slot bits in shared memory and writes the directory
 // and the entries (the same buckets as radix_sort_rows + finalize).  Exact form:
-// msd_partition_hist (histogram + scan into buf.hist), msd_partition_scatter with
-// cap = 0.  Histogram-free form: msd_partition_scatter with cap =
-// msd_bin_capacity(len) into bins of buf.keys_a (rows * 256 * cap entries); valid
+// msd_partition_hist (histogram + scan into buf.hist, sized sort_hist_entries(rows,
+// len, dbits)), msd_partition_scatter with cap = 0.  Histogram-free form: msd_partition_scatter with
+// cap = msd_bin_capacity(len, dbits) into bins of buf.keys_a (rows * 2^dbits * cap
+// entries); valid
 // when *buf.status reads 0 afterwards, else redo the tables the exact way.  Then
-// msd_finish with the same cap; it needs big_cnt [1] and big [rows * 256] of
-// scratch for segments longer than 4096.
-bool msd_path_applies(uint32_t slot_bits);
+// msd_finish with the same cap; it needs big_cnt [1] and big [rows * 2^dbits] of
+// scratch for segments longer than 4096, seg_out [rows * (2^dbits + 1)] and bin_cnt
+// [rows * 2^dbits].
+bool msd_path_applies(uint32_t slot_bits, uint64_t n);
 cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
                                cudaStream_t s);
 cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap,
@@ -207,8 +210,10 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
 cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, SortBuffers &buf,
                        unsigned long long *big_cnt, uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count,
                        cudaStream_t s);
-// Bin capacity of the histogram-free partition for rows of n entries.
-uint32_t msd_bin_capacity(uint64_t n);
+// Partition digit bits for slot_bits (8 up to 20, then slot_bits - 12) and the bin
+// capacity of the histogram-free partition for rows of n entries.
+uint32_t msd_dbits(uint32_t slot_bits);
+uint32_t msd_bin_capacity(uint64_t n, uint32_t dbits);
 // Directory of each sorted row: ent = (key >> sb) << 32 | id, offs[slot] = first entry of slot.
 cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint32_t rows, uint64_t len,
                                  uint32_t slot_bits, uint64_t *ent, uint32_t *offs, cudaStream_t s);

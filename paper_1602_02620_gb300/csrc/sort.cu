@@ -39,20 +39,21 @@ struct RadixArgs {
     uint32_t dmask;               // digit = (key >> shift) & dmask: the last pass may have fewer than 8 bits
     uint32_t *hist;               // [rows][256][tiles]
     uint32_t rows;
-    uint32_t pack_sb;             // partition_scatter_kernel: slot bits of the directory
-    uint32_t pack_idbits;         // partition_scatter_kernel: bits of an id
+    uint32_t pack_sb;             // partition kernels: slot bits of the directory
+    uint32_t pack_idbits;         // partition kernels: bits of an id
     uint32_t cap;                 // partition_scatter_kernel: 0 = places from hist; else bins of cap entries
     uint32_t *bin_cnt;            //   [rows][256] entries reserved in each bin (cap > 0)
     uint32_t *status;             //   bit 0 set when a bin overflowed (cap > 0)
 };
 
-// Packed partition output for the MSD directory path:
-//   bits [52, 52+sub)   the slot's low sub = sb-8 <= 12 bits
-//   bits [idbits, 52)   the key's high bits key >> sb (50-sb bits)
+// Packed partition output for the MSD directory path (partition digit = the slot's
+// top dbits bits, implied by the segment):
+//   bits [52, 52+sub)   the slot's low sub = sb-dbits <= 12 bits
+//   bits [idbits, 52)   the key's high bits key >> sb (50-sb bits; idbits <= sb + 2)
 //   bits [0, idbits)    the id
-__device__ __forceinline__ uint64_t pack_entry(uint64_t key, uint32_t id, uint32_t sb, uint32_t idbits)
+__device__ __forceinline__ uint64_t pack_entry(uint64_t key, uint32_t id, uint32_t sb, uint32_t idbits, uint32_t dbits)
 {
-    const uint64_t sub = key & ((1ULL << (sb - 8)) - 1);
+    const uint64_t sub = key & ((1ULL << (sb - dbits)) - 1);
     return (sub << 52) | ((key >> sb) << idbits) | id;
 }
 
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
                 const uint32_t digit = (uint32_t)(key[r] >> a.shift) & 255u;
                 const uint32_t lp = cnt[digit] + rk[r];
                 const uint32_t go = gofs[digit];
-                sk[lp] = pack_entry(key[r], (uint32_t)idx, a.pack_sb, a.pack_idbits);
+                sk[lp] = pack_entry(key[r], (uint32_t)idx, a.pack_sb, a.pack_idbits, 8);
                 sg[lp] = go == 0xFFFFFFFFu ? go : go + lp;
             }
         }
@@ -282,6 +283,148 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
             const uint32_t g = sg[i];
             if (g != 0xFFFFFFFFu) a.keys_out[g] = sk[i];
         }
+    }
+}
+
+// Partition of every table by the slot's top D = 9..11 bits (slot_bits 21..23),
+// packed output; segments then hold 2^(slot_bits-D) = 4,096 slots, as at
+// slot_bits = 20.  Into fixed-capacity bins (cap > 0): with 2^D digits a sub-tile's
+// runs are short, so a block first counts its whole tile of kWideTile keys and
+// reserves each digit's run in its bin with one global atomic (the keys are read
+// twice; the second time they come from L2); a run that would pass its bin's end is
+// dropped and flagged.  Exact form (cap = 0): the tile's places come from the
+// scanned per-tile histogram of wide_hist_kernel.  Either way the tile is ranked,
+// reordered and written in sub-tiles of kWideSub.
+constexpr int kWideThreads = 512;
+constexpr int kWideSub = 4096;                 // 8 keys per thread
+constexpr int kWideSubs = 4;
+constexpr int kWideTile = kWideSub * kWideSubs;
+
+// Exact form's digit counts of one wide tile: hist[(row * 2^D + d) * tiles + tile].
+template <int D>
+__global__ void __launch_bounds__(kWideThreads) wide_hist_kernel(RadixArgs a)
+{
+    constexpr uint32_t ND = 1u << D;
+    constexpr int R = kWideSub / kWideThreads;
+    __shared__ uint32_t cnt[ND];
+    const uint32_t row = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
+    const uint64_t len = a.len;
+    const uint64_t base = (uint64_t)tile * kWideTile;
+    const uint64_t *K = a.keys_in + (uint64_t)row * len;
+    for (uint32_t d = tid; d < ND; d += kWideThreads) cnt[d] = 0;
+    __syncthreads();
+    for (int sbk = 0; sbk < kWideSubs; ++sbk) {
+        uint32_t dg[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = base + (uint64_t)sbk * kWideSub + (uint64_t)r * kWideThreads + tid;
+            dg[r] = idx < len ? ((uint32_t)(K[idx] >> a.shift) & (ND - 1)) : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (dg[r] != 0xFFFFFFFFu) atomicAdd(&cnt[dg[r]], 1u);
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d < ND; d += kWideThreads) a.hist[(((uint64_t)row << D) + d) * a.tiles + tile] = cnt[d];
+}
+
+template <int D>
+__global__ void __launch_bounds__(kWideThreads, 2) partition_wide_kernel(RadixArgs a)
+{
+    constexpr uint32_t ND = 1u << D;
+    constexpr int R = kWideSub / kWideThreads;
+    constexpr uint32_t PER = ND / kWideThreads;   // digits per thread in the scans (1, 2 or 4)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kWideSub] packed entries in digit order
+    uint32_t *sg = reinterpret_cast<uint32_t *>(sk + kWideSub);   // [kWideSub] their global positions
+    __shared__ uint32_t cnt[ND], st[ND], cur[ND], gofs[ND];
+    const uint32_t row = blockIdx.y, tid = threadIdx.x;
+    const uint64_t len = a.len;
+    const uint64_t base = (uint64_t)blockIdx.x * kWideTile;
+    if (base >= len) return;   // uniform
+    const uint64_t *K = a.keys_in + (uint64_t)row * len;
+    const uint32_t shift = a.shift;
+    for (uint32_t d = tid; d < ND; d += kWideThreads) {
+        cnt[d] = 0;
+        cur[d] = 0;
+    }
+    __syncthreads();
+    for (int sbk = 0; a.cap && sbk < kWideSubs; ++sbk) {   // bins: the tile's digit counts
+        uint32_t dg[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = base + (uint64_t)sbk * kWideSub + (uint64_t)r * kWideThreads + tid;
+            dg[r] = idx < len ? ((uint32_t)(K[idx] >> shift) & (ND - 1)) : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (dg[r] != 0xFFFFFFFFu) atomicAdd(&cnt[dg[r]], 1u);
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d < ND; d += kWideThreads) {   // reserve the tile's runs in the bins
+        if (a.cap == 0) {   // exact form: the tile's places from the scanned histogram
+            gofs[d] = a.hist[(((uint64_t)row << D) + d) * a.tiles + blockIdx.x];
+            continue;
+        }
+        const uint32_t c = cnt[d];
+        const uint32_t at = c ? atomicAdd(a.bin_cnt + (uint64_t)row * ND + d, c) : 0u;
+        if (at + c <= a.cap) {
+            gofs[d] = (uint32_t)(((uint64_t)row * ND + d) * a.cap + at);
+        } else {
+            gofs[d] = 0xFFFFFFFFu;   // dropped: the bin is full
+            atomicOr(a.status, 1u);
+        }
+    }
+    for (uint64_t sbase = base; sbase < len && sbase < base + kWideTile; sbase += kWideSub) {
+        uint64_t key[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = sbase + (uint64_t)r * kWideThreads + tid;
+            key[r] = idx < len ? K[idx] : 0;
+        }
+        for (uint32_t d = tid; d < ND; d += kWideThreads) cnt[d] = 0;
+        __syncthreads();   // (also: the previous sub-tile's output is read out, cur advanced)
+        uint32_t rk[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = sbase + (uint64_t)r * kWideThreads + tid;
+            if (idx < len) rk[r] = atomicAdd(&cnt[(uint32_t)(key[r] >> shift) & (ND - 1)], 1u);
+        }
+        __syncthreads();
+        {   // thread tid owns digits [tid*PER, tid*PER + PER): their first places in the sub-tile
+            uint32_t c[PER], mine = 0;
+#pragma unroll
+            for (uint32_t i = 0; i < PER; ++i) {
+                c[i] = cnt[tid * PER + i];
+                mine += c[i];
+            }
+            uint32_t tot;
+            uint32_t run = block_excl_scan<uint32_t>(mine, &tot);   // barriers inside
+#pragma unroll
+            for (uint32_t i = 0; i < PER; ++i) {
+                st[tid * PER + i] = run;
+                run += c[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t idx = sbase + (uint64_t)r * kWideThreads + tid;
+            if (idx < len) {
+                const uint32_t digit = (uint32_t)(key[r] >> shift) & (ND - 1);
+                const uint32_t lp = st[digit] + rk[r];
+                const uint32_t go = gofs[digit];
+                sk[lp] = pack_entry(key[r], (uint32_t)idx, a.pack_sb, a.pack_idbits, D);
+                sg[lp] = go == 0xFFFFFFFFu ? go : go + cur[digit] + rk[r];
+            }
+        }
+        __syncthreads();
+        const uint32_t sub_n = (uint32_t)((len - sbase) < (uint64_t)kWideSub ? (len - sbase) : (uint64_t)kWideSub);
+        for (uint32_t i = tid; i < sub_n; i += kWideThreads) {
+            const uint32_t g = sg[i];
+            if (g != 0xFFFFFFFFu) a.keys_out[g] = sk[i];
+        }
+        for (uint32_t d = tid; d < ND; d += kWideThreads) cur[d] += cnt[d];
     }
 }
 
@@ -513,7 +656,8 @@ __device__ __forceinline__ void seg_scan(uint32_t *v, uint32_t cnt, uint32_t *ws
 
 constexpr int kOneThreads = 512;
 constexpr int kOneWarps = kOneThreads / 32;
-constexpr int kOneItems = kSegChunk / kOneThreads;   // 8 entries per thread
+constexpr int kOneItems = 9;                         // entries per thread
+constexpr int kOneCap = kOneThreads * kOneItems;     // 4,608 entries: a full bin of a 4,096-slot segment
 constexpr int kOneSlots = 8;                         // directory slots owned per thread (2^12 / 512)
 
 // Padded index of per-slot counters: four spare words after every 32, so that the
@@ -522,26 +666,36 @@ constexpr int kOneSlots = 8;                         // directory slots owned pe
 __device__ __forceinline__ uint32_t pj(uint32_t j) { return j + ((j >> 5) << 2); }
 
 // seg_out[row][g] = first directory entry of segment (row, g) within its row, for
-// g = 0..255, and seg_out[row][256] = n: from the scanned (row, digit, tile)
-// histogram (bin_cnt == nullptr) or by a prefix over the bins' fills.  One block per row.
+// the 2^dbits segments g of a row, and seg_out[row][2^dbits] = n: from the scanned
+// (row, digit, tile) histogram (bin_cnt == nullptr) or by a prefix over
+// the bins' fills.  One block of 256 threads per row; thread t takes 2^dbits/256
+// consecutive segments.
 __global__ void __launch_bounds__(256) segment_bounds_kernel(const uint32_t *__restrict__ hist, uint32_t tiles,
                                                              uint64_t n, const uint32_t *__restrict__ bin_cnt,
-                                                             uint32_t *__restrict__ seg_out)
+                                                             uint32_t dbits, uint32_t *__restrict__ seg_out)
 {
     const uint32_t row = blockIdx.x, tid = threadIdx.x;
-    uint32_t v;
+    const uint32_t nd = 1u << dbits, per = nd / 256;
+    uint32_t *out = seg_out + (uint64_t)row * (nd + 1);
     if (bin_cnt) {
+        const uint32_t *c = bin_cnt + (uint64_t)row * nd + tid * per;
+        uint32_t mine = 0;
+        for (uint32_t i = 0; i < per; ++i) mine += c[i];
         uint32_t tot;
-        v = block_excl_scan<uint32_t>(bin_cnt[(uint64_t)row * 256 + tid], &tot);
+        uint32_t run = block_excl_scan<uint32_t>(mine, &tot);
+        for (uint32_t i = 0; i < per; ++i) {
+            out[tid * per + i] = run;
+            run += c[i];
+        }
     } else {
-        v = hist[((uint64_t)row * 256 + tid) * tiles] - (uint32_t)((uint64_t)row * n);
+        for (uint32_t i = 0; i < per; ++i)
+            out[tid * per + i] = hist[(((uint64_t)row << dbits) + tid * per + i) * tiles] - (uint32_t)((uint64_t)row * n);
     }
-    seg_out[(uint64_t)row * 257 + tid] = v;
-    if (tid == 0) seg_out[(uint64_t)row * 257 + 256] = (uint32_t)n;
+    if (tid == 0) out[nd] = (uint32_t)n;
 }
 
-// One block per (segment, table) for segments of at most one chunk (4096 entries,
-// the common case).  Entries are counted into their slots with shared-memory
+// One block per (segment, table) for segments of at most kOneCap = 4,608 entries
+// (the common case: a segment of 4,096 slots holds ~n/2^dbits of them).  Entries are counted into their slots with shared-memory
 // atomics; thread i owns the eight consecutive slots [8i, 8i+8): it scans their
 // counts in registers and writes their directory words with two vector stores.
 // Each entry is then placed in its slot's run at the place its atomic returned
@@ -552,24 +706,24 @@ __global__ void __launch_bounds__(256) segment_bounds_kernel(const uint32_t *__r
 // directory entries; its packed input starts at row * in_stride + (cap ? g * cap : seg_out[row][g]).
 __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
                                                                      uint64_t in_stride, uint32_t cap, uint32_t sb,
-                                                                     uint32_t idbits,
+                                                                     uint32_t idbits, uint32_t dbits,
                                                                      const uint32_t *__restrict__ seg_out,
                                                                      uint64_t *__restrict__ ent,
                                                                      uint32_t *__restrict__ offs,
                                                                      unsigned long long *big_cnt, uint32_t *big)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *ck = reinterpret_cast<uint64_t *>(smem_raw);             // [kSegChunk]
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(ck + kSegChunk);       // [pj(nsub)]
+    uint64_t *ck = reinterpret_cast<uint64_t *>(smem_raw);             // [kOneCap]
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(ck + kOneCap);         // [pj(nsub)]
     __shared__ uint32_t wsum[kOneWarps];
     const uint32_t g = blockIdx.x, row = blockIdx.y, tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
-    const uint32_t subb = sb - 8, nsub = 1u << subb, smask = nsub - 1;
+    const uint32_t nd = 1u << dbits, subb = sb - dbits, nsub = 1u << subb, smask = nsub - 1;
     const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
-    const uint32_t lo = seg_out[(uint64_t)row * 257 + g], hi = seg_out[(uint64_t)row * 257 + g + 1];
+    const uint32_t lo = seg_out[(uint64_t)row * (nd + 1) + g], hi = seg_out[(uint64_t)row * (nd + 1) + g + 1];
     const uint32_t len = hi - lo;
-    if (len > (uint32_t)kSegChunk) {
-        if (tid == 0) big[atomicAdd(big_cnt, 1ULL)] = row * 256 + g;
+    if (len > (uint32_t)kOneCap) {
+        if (tid == 0) big[atomicAdd(big_cnt, 1ULL)] = (row << dbits) | g;
         return;
     }
     const uint32_t cn = len;
@@ -577,7 +731,7 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
     const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)lo);
     uint64_t *E = ent + rowbase + lo;
     uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;   // 16-byte aligned (nsub >= 8)
-    if (g == 255 && tid == 0) O[nsub] = (uint32_t)n;
+    if (g == nd - 1 && tid == 0) O[nsub] = (uint32_t)n;
     uint64_t v[kOneItems];
     uint32_t rk[kOneItems];
 #pragma unroll
@@ -652,7 +806,7 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
 // digit passes.
 __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const uint64_t *__restrict__ packed,
                                                                         uint64_t n, uint64_t in_stride, uint32_t cap,
-                                                                        uint32_t sb, uint32_t idbits,
+                                                                        uint32_t sb, uint32_t idbits, uint32_t dbits,
                                                                         const uint32_t *__restrict__ seg_out,
                                                                         uint64_t *__restrict__ ent,
                                                                         uint32_t *__restrict__ offs,
@@ -668,20 +822,20 @@ __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const ui
     uint32_t *wh = ccnt + (1u << kSubMaxBits) + 1;                           // [kSegWarps][64]
     __shared__ uint32_t dstart[64];
     __shared__ uint32_t wsum[32];
-    const uint32_t g = big[bi] & 255, row = big[bi] >> 8, tid = threadIdx.x;
+    const uint32_t nd = 1u << dbits, g = big[bi] & (nd - 1), row = big[bi] >> dbits, tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
-    const uint32_t subb = sb - 8, nsub = 1u << subb, smask = nsub - 1;
+    const uint32_t subb = sb - dbits, nsub = 1u << subb, smask = nsub - 1;
     const uint32_t b1 = subb / 2, m1 = (1u << b1) - 1;
     const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
     const uint64_t rowbase = (uint64_t)row * n;
-    const uint32_t seg_lo = seg_out[(uint64_t)row * 257 + g], seg_hi = seg_out[(uint64_t)row * 257 + g + 1];
+    const uint32_t seg_lo = seg_out[(uint64_t)row * (nd + 1) + g], seg_hi = seg_out[(uint64_t)row * (nd + 1) + g + 1];
     const uint64_t seg_len = seg_hi - seg_lo;
     const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)seg_lo);
     uint64_t *E = ent + rowbase + seg_lo;
     uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;
     auto sub_of = [&](uint64_t v) { return (uint32_t)(v >> 52) & smask; };
     auto ent_of = [&](uint64_t v) { return ((v & low52) >> idbits) << 32 | (v & idmask); };
-    if (g == 255 && tid == 0) O[nsub] = (uint32_t)n;
+    if (g == nd - 1 && tid == 0) O[nsub] = (uint32_t)n;
 
     // several chunks: per-slot counts of the whole segment first, then stable passes
     for (uint32_t j = tid; j < nsub; j += kSegThreads) sub_off[j] = 0;
@@ -766,13 +920,21 @@ static cudaError_t scatter_smem_init()
     return once;
 }
 
-size_t sort_hist_entries(uint32_t rows, uint64_t len)
+size_t sort_hist_entries(uint32_t rows, uint64_t len, uint32_t dbits)
 {
     const uint64_t tiles = (len + kSortTile - 1) / kSortTile;
-    return (size_t)rows * 256 * tiles;
+    const uint64_t wide = dbits > 8 ? ((uint64_t)1 << dbits) * ((len + kWideTile - 1) / kWideTile) : 0;
+    return (size_t)rows * std::max<uint64_t>(256 * tiles, wide);
 }
 
-size_t sort_keys_hist_entries(uint64_t cap) { return sort_hist_entries(1, cap); }
+// Histogram tiles per row of the partition with dbits-bit digits.
+static uint32_t msd_tiles(uint64_t len, uint32_t dbits)
+{
+    const uint64_t t = dbits == 8 ? kSortTile : kWideTile;
+    return (uint32_t)((len + t - 1) / t);
+}
+
+size_t sort_keys_hist_entries(uint64_t cap) { return sort_hist_entries(1, cap, 8); }
 
 size_t scan_partials_entries(size_t count) { return (count + kScanChunk - 1) / kScanChunk + 2; }
 
@@ -853,9 +1015,7 @@ cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, u
 namespace fclsh {
 
 size_t segment_finish_smem() { return (size_t)kSegChunk * 8 + ((2u << kSubMaxBits) + 1) * 4 + kSegWarps * 64 * 4; }
-size_t segment_one_smem() { return (size_t)kSegChunk * 8 + ((1u << kSubMaxBits) + (1u << kSubMaxBits) / 8 + 4) * 4; }
-
-bool msd_path_applies(uint32_t slot_bits) { return slot_bits >= 11 && slot_bits - 8 <= (uint32_t)kSubMaxBits; }
+size_t segment_one_smem() { return (size_t)kOneCap * 8 + ((1u << kSubMaxBits) + (1u << kSubMaxBits) / 8 + 4) * 4; }
 
 static uint32_t id_bits(uint64_t len)
 {
@@ -864,34 +1024,76 @@ static uint32_t id_bits(uint64_t len)
     return b;
 }
 
+bool msd_path_applies(uint32_t slot_bits, uint64_t n)
+{
+    // the packed entry holds sb - dbits <= 12 slot bits, 50 - sb key bits and the id
+    return slot_bits >= 11 && slot_bits <= 23 && id_bits(n) <= slot_bits + 2;
+}
+
+uint32_t msd_dbits(uint32_t slot_bits) { return slot_bits <= 20 ? 8u : slot_bits - (uint32_t)kSubMaxBits; }
+
 cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
                                cudaStream_t s)
 {
-    const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
-    const uint64_t hcount = (uint64_t)rows * 256 * tiles;
-    RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - 8, 255u, buf.hist, rows, sb,
-                id_bits(len)};
-    radix_hist_kernel<<<dim3(tiles, rows), kSortThreads, 0, s>>>(a);
+    const uint32_t dbits = msd_dbits(sb);
+    const uint32_t tiles = msd_tiles(len, dbits);
+    const uint64_t hcount = ((uint64_t)rows << dbits) * tiles;
+    RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - dbits, (1u << dbits) - 1, buf.hist,
+                rows, sb, id_bits(len)};
+    const dim3 grid(tiles, rows);
+    switch (dbits) {
+    case 8: radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a); break;
+    case 9: wide_hist_kernel<9><<<grid, kWideThreads, 0, s>>>(a); break;
+    case 10: wide_hist_kernel<10><<<grid, kWideThreads, 0, s>>>(a); break;
+    case 11: wide_hist_kernel<11><<<grid, kWideThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
     note_launch();
     return scan_exclusive<uint32_t, uint32_t, uint32_t>(buf.hist, buf.hist, hcount, buf.partials, false, s);
 }
 
-// Partition of every table by the top 8 slot bits, packed output: into places from
-// the scanned histogram (cap = 0), or into bins of cap entries per (row, digit)
-// (no histogram; buf.status bit 0 reports a full bin).
+// Partition of every table by the slot's top msd_dbits(sb) bits, packed output: into
+// places from the scanned histogram (cap = 0), or into bins of
+// cap entries per (row, digit) (no histogram; buf.status bit 0 reports a full bin).
 cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap,
                                   SortBuffers &buf, cudaStream_t s)
 {
     cudaError_t e = scatter_smem_init();
     if (e != cudaSuccess) return e;
-    const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
-    RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - 8, 255u, buf.hist, rows, sb,
-                id_bits(len), cap, buf.bin_cnt, buf.status};
+    const uint32_t dbits = msd_dbits(sb);
+    const uint32_t tiles = msd_tiles(len, dbits);
+    RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - dbits, (1u << dbits) - 1, buf.hist,
+                rows, sb, id_bits(len), cap, buf.bin_cnt, buf.status};
     if (cap) {
-        if ((e = cudaMemsetAsync(buf.bin_cnt, 0, (size_t)rows * 256 * 4, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(buf.bin_cnt, 0, ((size_t)rows << dbits) * 4, s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(buf.status, 0, 4, s)) != cudaSuccess) return e;
     }
-    partition_scatter_kernel<<<dim3(tiles, rows), kSortThreads, kScatterSmemKeys, s>>>(a);
+    if (dbits == 8) {
+        partition_scatter_kernel<<<dim3(tiles, rows), kSortThreads, kScatterSmemKeys, s>>>(a);
+    } else {
+        const dim3 grid(tiles, rows);
+        constexpr size_t smem = (size_t)kWideSub * 12;
+        static cudaError_t once = [] {   // static digit tables + dynamic sub-tile exceed 48 KB
+            cudaError_t r = cudaFuncSetAttribute(partition_wide_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(partition_wide_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(partition_wide_kernel<11>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+            return r;
+        }();
+        if (once != cudaSuccess) return once;
+        if (dbits == 9)
+            partition_wide_kernel<9><<<grid, kWideThreads, smem, s>>>(a);
+        else if (dbits == 10)
+            partition_wide_kernel<10><<<grid, kWideThreads, smem, s>>>(a);
+        else if (dbits == 11)
+            partition_wide_kernel<11><<<grid, kWideThreads, smem, s>>>(a);
+        else
+            return cudaErrorInvalidValue;
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -900,6 +1102,7 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
                        unsigned long long *big_cnt, uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count,
                        cudaStream_t s)
 {
+    const uint32_t dbits = msd_dbits(sb);
     static cudaError_t once = [] {
         cudaError_t e = cudaFuncSetAttribute(segment_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)segment_finish_smem());
@@ -910,31 +1113,32 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
     }();
     if (once != cudaSuccess) return once;
     if (reinterpret_cast<uintptr_t>(offs) & 15) return cudaErrorMisalignedAddress;   // vector stores of offsets
-    const uint32_t tiles = (uint32_t)((len + kSortTile - 1) / kSortTile);
+    const uint32_t tiles = msd_tiles(len, dbits);
     const uint32_t idb = id_bits(len);
-    const uint64_t in_stride = cap ? (uint64_t)256 * cap : len;
-    segment_bounds_kernel<<<rows, 256, 0, s>>>(buf.hist, tiles, len, cap ? buf.bin_cnt : nullptr, buf.seg_out);
+    const uint64_t in_stride = cap ? ((uint64_t)1 << dbits) * cap : len;
+    segment_bounds_kernel<<<rows, 256, 0, s>>>(buf.hist, tiles, len, cap ? buf.bin_cnt : nullptr, dbits, buf.seg_out);
     note_launch();
     cudaError_t e = cudaMemsetAsync(big_cnt, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    segment_one_kernel<<<dim3(256, rows), kOneThreads, segment_one_smem(), s>>>(buf.keys_a, len, in_stride, cap, sb,
-                                                                                  idb, buf.seg_out, ent, offs, big_cnt,
-                                                                                  big);
+    segment_one_kernel<<<dim3(1u << dbits, rows), kOneThreads, segment_one_smem(), s>>>(
+        buf.keys_a, len, in_stride, cap, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
     note_launch();
-    segment_finish_kernel<<<sm_count, kSegThreads, segment_finish_smem(), s>>>(buf.keys_a, len, in_stride, cap, sb,
-                                                                                 idb, buf.seg_out, ent, offs, big_cnt,
-                                                                                 big);
+    segment_finish_kernel<<<sm_count, kSegThreads, segment_finish_smem(), s>>>(
+        buf.keys_a, len, in_stride, cap, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
     note_launch();
     return cudaGetLastError();
 }
 
-// Entries per bin of the histogram-free partition: the mean segment n/256 plus
-// eight standard deviations of its binomial count (and a margin), so that for
-// keys spread like independent uniform values no bin overflows in practice.
-uint32_t msd_bin_capacity(uint64_t n)
+// Entries per bin of the histogram-free partition: the mean segment n/2^dbits plus
+// eight standard deviations of its binomial count, an eighth of the mean for keys
+// that repeat (a clustered data set puts tens of points on one key in every table;
+// its fullest bins run ~10 standard deviations over the mean), and a margin.  Bins
+// still overflow when a few keys carry a large share of a table (e.g. the empty sum
+// of sparse points); those tables take the exact histogram path.
+uint32_t msd_bin_capacity(uint64_t n, uint32_t dbits)
 {
-    const double mean = (double)n / 256.0;
-    const uint64_t c = (uint64_t)(mean + 8.0 * sqrt(mean) + 64.0);
+    const double mean = (double)n / (double)(1u << dbits);
+    const uint64_t c = (uint64_t)(mean + mean / 8.0 + 8.0 * sqrt(mean) + 64.0);
     return (uint32_t)((c + 3) & ~3ULL);
 }
 

@@ -368,3 +368,37 @@ def test_dedup_modes_match_oracle(hlog):
     again = idx.query(dev(qs), r)                              # the bitmaps were left clear
     assert np.array_equal(again.ids, res.ids) and np.array_equal(again.offs, res.offs)
     idx.free()
+
+
+@pytest.mark.parametrize("slot_bits", [21, 22, 23])
+@pytest.mark.parametrize("skewed", [False, True])
+def test_wide_partition_directory_matches_oracle(slot_bits, skewed):
+    """Directories with 2^21..2^23 slots per table (partition by the slot's top 9..11 bits)
+    hold the oracle's buckets, through the bins and, with many equal keys, through the
+    exact histogram fallback; queries over them match the oracle."""
+    rng = np.random.default_rng(slot_bits + 100 * skewed)
+    d, r, n = 128, 6, 5000
+    pts = rand_points(rng, n, d)
+    if skewed:
+        pts[100:1600] = pts[3]                                   # 1,501 equal points: bins overflow
+    seed = 31 + slot_bits
+    p = oracle.derive_params(seed, d, r)
+    idx = F().build(dev(pts), d, r, seed, slot_bits=slot_bits)
+    assert idx.info["slot_bits"] == slot_bits
+    for tau in sorted({0, 1, p.T // 2, p.T - 1}):
+        keys, ids = idx.export_table(tau)
+        sl = keys & np.uint64((1 << slot_bits) - 1)
+        assert np.all(np.diff(sl.astype(np.int64)) >= 0)
+        order = np.lexsort((ids, keys))
+        ok, oi = oracle.table(p, pts, tau)
+        assert np.array_equal(keys[order], ok) and np.array_equal(ids[order], oi)
+        for key in {int(ok[0]), int(ok[len(ok) // 2]), int(keys[3])}:
+            assert np.array_equal(idx.bucket(tau, key), oi[ok == key])
+    qs = np.concatenate([near(rng, pts, d, r, 30), pts[[3]]])
+    tables = oracle.build_tables(p, pts)
+    res = idx.query(dev(qs), r)
+    for i in range(qs.shape[0]):
+        want, ncoll, ncand = oracle.query(p, pts, tables, qs[i], r)
+        assert np.array_equal(res.of(i), want)
+        assert (int(res.collisions[i]), int(res.candidates[i])) == (ncoll, ncand)
+    idx.free()
