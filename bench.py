@@ -41,6 +41,7 @@ CFG = 2
 # algorithmic bytes.  Set an entry to None when its kernel changes.
 TRAFFIC_RATIO = {
     "hash": 0.950,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
+    "hash_mma": 0.954,    # profiles/hash_mma_kernel_w512_n300k_d128_r8.md
     "scatter": 0.983,     # profiles/partition_scatter_kernel_n300k_d128_r8.md
     "finish": 0.999,      # profiles/segment_one_kernel_n300k_d128_r8.md
     "hist": None,         # (only on the histogram fallback of skewed keys)
@@ -417,8 +418,10 @@ def main():
     L = info["W"] - 1
     entries = w.n * L
     slots = L * ((1 << info["slot_bits"]) + 1)
+    hash_stage = ("hash_mma_kernel (tensor-core contraction, all W-1 keys per point)", "hash_mma") \
+        if tuned["hash_tile"] == 2 else ("hash_tile_kernel (Algorithm 2, all W-1 keys per point)", "hash")
     stages = {
-        "hash_tile_kernel (Algorithm 2, all W-1 keys per point)": (acc["build_hash"], w.n * (w.d / 8 + 8 * L), "hash"),
+        hash_stage[0]: (acc["build_hash"], w.n * (w.d / 8 + 8 * L), hash_stage[1]),
         "partition_scatter_kernel (partition by the top 8 slot bits into bins, packed output)":
             (acc["build_partition"], 16 * entries, "scatter"),
         "radix_hist_kernel + scan (partition histogram)": (acc["build_partition_hist"], 8 * entries, "hist"),

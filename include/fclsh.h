@@ -66,8 +66,10 @@ typedef struct {
     const uint32_t *m;
     const uint64_t *b;
     uint32_t timing;          /* 1: record per-phase CUDA events from the start (see fclsh_timing_read) */
-    uint32_t hash_tile;       /* points per hash block (Algorithm 2 kernel): 0 = the default for W, 1 = twice
-                                 that where it fits shared memory (W <= 1024); speed only */
+    uint32_t hash_tile;       /* the hash kernel, speed only (same keys): 0 = Algorithm 2 with the default WHT
+                                 tile, 1 = twice the points per tile where it fits (W <= 1024), 2 = the
+                                 O(dL) route as an exact tensor-core contraction (W >= 64, parts of at most
+                                 128 coordinates) */
 } fclsh_build_opts;
 
 typedef struct {
@@ -108,7 +110,7 @@ typedef struct {
     uint32_t inline_probe;    /* probe fan-out: a bucket range up to this length is walked by the lane that
                                  probed it, a longer one by the whole warp (1..32) */
     uint32_t use_graph;       /* capture a batch's launches into a CUDA graph and replay it */
-    uint32_t hash_tile;       /* WHT tile of fclsh_hash (see fclsh_build_opts.hash_tile): 0 or 1 */
+    uint32_t hash_tile;       /* hash kernel of fclsh_hash and of later builds (fclsh_build_opts.hash_tile): 0, 1, 2 */
     uint32_t probe_rows;      /* 0: a query probes all T tables (Strategy 2, Sec. 2.2).  1: a query of radius
                                  rho probes only the code rows v = 1 .. 2^(floor(rho/t)+1) - 1 of each part;
                                  the ids are the same (pigeonhole over the parts, Sec. 3.1, and Theorem 1
@@ -307,8 +309,8 @@ fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *tune);
 /*
  * Time the kernel shapes on a sample: the query kernel's (verify-block shape,
  * blocks per SM, dedup set, probe fan-out) on a batch of queries (device or
- * host), and the hash kernel's WHT tile on the index's first points; keep the
- * fastest.  The choice is cached in `cache_path` (JSON, may be NULL) keyed by
+ * host), and the hash kernel (WHT tiles, and the tensor-core contraction where it
+ * applies) on the index's first points; keep the fastest.  The choice is cached in `cache_path` (JSON, may be NULL) keyed by
  * (n, d, r, t, W).  Results never depend on the choice; probe_rows is kept as
  * set.  A later build takes the hash tile through fclsh_build_opts.hash_tile.
  * Synchronous.

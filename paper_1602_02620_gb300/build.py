@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libfclsh.so")
 
-SOURCES = ["api.cu", "hash.cu", "sort.cu", "query.cu", "params.cpp", "server.cpp", "noalloc.cu"]
+SOURCES = ["api.cu", "hash.cu", "hash_mma.cu", "sort.cu", "query.cu", "params.cpp", "server.cpp", "noalloc.cu"]
 HEADERS = ["common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

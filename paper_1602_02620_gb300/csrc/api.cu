@@ -470,6 +470,53 @@ static fclsh_status run_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uin
 
 // ---------------------------------------------------------------- build
 
+// The tensor-core hash's operands (coordinate lists and G's fp16 chunks), built once.
+static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s)
+{
+    if (idx->mma_g) return FCLSH_OK;
+    if (!idx->mma_k)
+        return fail(FCLSH_EINVAL, "the tensor-core hash needs W >= 64 and parts of at most 128 coordinates");
+    const uint32_t K = idx->mma_k, t = idx->t;
+    std::vector<uint32_t> coord((size_t)t * K, 0xFFFFFFFFu);
+    for (uint32_t k = 0; k < t; ++k)
+        for (uint32_t i = idx->part_off[k]; i < idx->part_off[k + 1]; ++i)
+            coord[(size_t)k * K + (i - idx->part_off[k])] = idx->perm[i];
+    const size_t per = hash_mma_operand_entries(K, idx->W);
+    DevAllocs tmp, keep;
+    uint32_t *dm = nullptr;
+    uint64_t *db = nullptr;
+    cudaError_t e;
+    if ((e = keep.alloc(&idx->mma_coord, coord.size())) != cudaSuccess ||
+        (e = keep.alloc(&idx->mma_g, per * t)) != cudaSuccess || (e = tmp.alloc(&dm, idx->d)) != cudaSuccess ||
+        (e = tmp.alloc(&db, idx->d)) != cudaSuccess) {
+        idx->mma_coord = nullptr;
+        idx->mma_g = nullptr;
+        return cuda_fail(e, "cudaMalloc(tensor-core hash operands)");
+    }
+    FCLSH_CUDA(cudaMemcpyAsync(idx->mma_coord, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemcpyAsync(dm, idx->m.data(), idx->d * 4, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemcpyAsync(db, idx->b.data(), idx->d * 8, cudaMemcpyHostToDevice, s));
+    for (uint32_t k = 0; k < t; ++k) {
+        const uint32_t lo = idx->part_off[k];
+        FCLSH_CUDA(build_mma_operand(dm + lo, db + lo, idx->part_off[k + 1] - lo, K, idx->W, idx->mma_g + k * per, s));
+    }
+    FCLSH_CUDA(cudaStreamSynchronize(s));
+    keep.release();
+    idx->device_bytes += coord.size() * 4 + per * t * 2;
+    return FCLSH_OK;
+}
+
+// Bit 0 of the index's status word: a kernel's bounded wait ran out (reset on read).
+static fclsh_status check_status(fclsh_index *idx, cudaStream_t s)
+{
+    uint32_t st = 0;
+    FCLSH_CUDA(cudaMemcpyAsync(&st, idx->status, 4, cudaMemcpyDeviceToHost, s));
+    FCLSH_CUDA(cudaStreamSynchronize(s));
+    if (!st) return FCLSH_OK;
+    FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
+    return fail(FCLSH_ETIMEOUT, "a kernel's wait for its tensor-core or copy completion ran out");
+}
+
 extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t d, uint32_t r, uint64_t seed,
                                     const fclsh_build_opts *opts, fclsh_index **out)
 {
@@ -501,7 +548,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->rp = rp;
     idx->W = W;
     idx->T = t * (W - 1);
-    if (o.hash_tile > 1) return fail(FCLSH_EINVAL, "hash_tile must be 0 or 1");
+    if (o.hash_tile > 2) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1 or 2");
     idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0};
     idx->timing = o.timing != 0;
 
@@ -527,6 +574,9 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     }
     uint32_t max_dk = 0;
     for (uint32_t k = 0; k < t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
+    idx->mma_k = hash_mma_k(W, max_dk);
+    if (o.hash_tile == 2 && !idx->mma_k)
+        return fail(FCLSH_EINVAL, "hash_tile 2 (tensor cores) needs W >= 64 and parts of at most 128 coordinates");
     if (hash_smem_bytes(W, max_dk, o.hash_tile) > idx->smem_optin)
         return fail(FCLSH_EINVAL, "a part of %u coordinates with W = %u does not fit the hash kernel's shared memory",
                     max_dk, W);
@@ -559,6 +609,12 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     FCLSH_CUDA(cudaMemcpyAsync(idx->col_off, col_off.data(), col_off.size() * 4, cudaMemcpyHostToDevice, s));
     FCLSH_CUDA(cudaMemcpyAsync(idx->col_coord, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
     FCLSH_CUDA(cudaMemcpyAsync(idx->col_b, bval.data(), bval.size() * 8, cudaMemcpyHostToDevice, s));
+    if ((e = keep.alloc(&idx->status, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+    FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
+    if (o.hash_tile == 2) {
+        fclsh_status st = ensure_mma_operands(idx, s);
+        if (st != FCLSH_OK) return st;
+    }
 
     // Transient buffers: the keys of one part, and radix-sort buffers for a chunk of its tables.
     const uint32_t L = W - 1;
@@ -647,6 +703,10 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         }
     }
     FCLSH_CUDA(cudaStreamSynchronize(s));
+    {
+        fclsh_status st = check_status(idx, s);
+        if (st != FCLSH_OK) return st;
+    }
     resolve_timers(idx);
     keep.release();
     *out = guard.release();
@@ -659,7 +719,8 @@ extern "C" void fclsh_free(fclsh_index *idx)
     cudaSetDevice(idx->device);
     cudaDeviceSynchronize();
     drop_timers(idx);
-    void *ps[] = {idx->points, idx->col_off, idx->col_coord, idx->col_b, idx->offs, idx->ent};
+    void *ps[] = {idx->points, idx->col_off, idx->col_coord, idx->col_b, idx->offs, idx->ent, idx->mma_coord, idx->mma_g,
+                  idx->status};
     for (void *p : ps)
         if (p) dev_free(p);
     delete idx;
@@ -727,9 +788,11 @@ extern "C" fclsh_status fclsh_hash(const fclsh_index *cidx, const uint64_t *pts,
         FCLSH_CUDA(cudaMemcpyAsync(keys_out, dk, (size_t)idx->T * cnt * 8, cudaMemcpyDeviceToHost, s));
         FCLSH_CUDA(cudaStreamSynchronize(s));
         resolve_timers(idx);
+        return check_status(idx, s);
     } else if (!tmp.ptrs.empty()) {
         FCLSH_CUDA(cudaStreamSynchronize(s));   // temporaries are freed on return
         resolve_timers(idx);
+        return check_status(idx, s);
     }
     return FCLSH_OK;
 }
@@ -1147,7 +1210,11 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     if (t->hash_set_log2 < 10 || t->hash_set_log2 > 13) return fail(FCLSH_EINVAL, "hash_set_log2 must be in 10..13");
     if (t->inline_probe < 1 || t->inline_probe > 32) return fail(FCLSH_EINVAL, "inline_probe must be in 1..32");
     if (t->query_ctas_per_sm < 1 || t->query_ctas_per_sm > 16) return fail(FCLSH_EINVAL, "query_ctas_per_sm must be in 1..16");
-    if (t->hash_tile > 1) return fail(FCLSH_EINVAL, "hash_tile must be 0 or 1");
+    if (t->hash_tile > 2) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1 or 2");
+    if (t->hash_tile == 2) {
+        fclsh_status st = ensure_mma_operands(idx, nullptr);
+        if (st != FCLSH_OK) return st;
+    }
     if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
     uint32_t max_dk = 0;
     for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
@@ -1317,17 +1384,19 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
                         best = t;
                     }
                 }
-    // WHT tile of the hash kernel: both choices on the index's first points (about 256 MB of keys)
+    // the hash kernel: WHT tiles and the tensor-core contraction on the index's first points
+    // (about 2 GB of keys: enough blocks that the timing reflects a full build)
     if (st == FCLSH_OK) {
         const uint32_t L = idx->W - 1;
-        const uint64_t cnt = std::min<uint64_t>(idx->n, std::max<uint64_t>(4096, (32ULL << 20) / L));
+        const uint64_t cnt = std::min<uint64_t>(idx->n, std::max<uint64_t>(4096, (256ULL << 20) / L));
         uint32_t max_dk = 0;
         for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
         uint64_t *kbuf = nullptr;
         if (dev_alloc((void **)&kbuf, cnt * L * 8) == cudaSuccess) {
             float best_h = 1e30f;
-            for (uint32_t tl = 0; tl <= 1; ++tl) {
-                if (hash_smem_bytes(idx->W, max_dk, tl) > idx->smem_optin) continue;
+            for (uint32_t tl = 0; tl <= 2; ++tl) {
+                if (tl < 2 && hash_smem_bytes(idx->W, max_dk, tl) > idx->smem_optin) continue;
+                if (tl == 2 && (!idx->mma_k || ensure_mma_operands(idx, s) != FCLSH_OK)) continue;
                 idx->tune.hash_tile = tl;
                 if (launch_hash_part(idx, 0, idx->points, cnt, kbuf, cnt, s) != cudaSuccess) continue;
                 cudaEventRecord(e0, s);

@@ -122,6 +122,12 @@ struct fclsh_index {
     uint64_t *col_b = nullptr;       // [d]
     uint32_t *offs = nullptr;        // [T][dir_stride(slot_bits)]: 2^slot_bits + 1 used
     uint64_t *ent = nullptr;         // [T][n]: (key >> slot_bits) << 32 | id
+    // tensor-core hash (hash_tile 2): padded coordinates per part, their lists [t][mma_k]
+    // and G's fp16 chunks [t][...]; built on first use
+    uint32_t mma_k = 0;
+    uint32_t *mma_coord = nullptr;
+    uint16_t *mma_g = nullptr;
+    uint32_t *status = nullptr;      // [1] device word: bit 0 = a kernel's bounded wait ran out
     uint64_t device_bytes = 0;
     fclsh_tuning tune{};
     // timing (CUDA events per phase)
@@ -164,8 +170,19 @@ void column_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t
                   std::vector<uint32_t> &coord, std::vector<uint64_t> &bval);
 
 // ---- hash.cu: keys of `cnt` points for part k into keys[(v-1)*ld + i], v = 1..W-1
+// (the Walsh-Hadamard kernels for hash_tile 0/1, hash_mma.cu's contraction for 2)
 cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t *pts, uint64_t cnt,
                              uint64_t *keys, uint64_t ld, cudaStream_t s);
+
+// ---- hash_mma.cu
+uint32_t hash_mma_k(uint32_t W, uint32_t max_dk);   // 0: the contraction does not apply
+uint32_t hash_mma_chunks(uint32_t W);
+size_t hash_mma_operand_entries(uint32_t K, uint32_t W);
+cudaError_t build_mma_operand(const uint32_t *m, const uint64_t *b, uint32_t dk, uint32_t K, uint32_t W,
+                              uint16_t *gmat, cudaStream_t s);
+cudaError_t launch_hash_mma(const uint32_t *coord, const uint16_t *gmat, uint32_t K, uint32_t W, const uint64_t *pts,
+                            uint64_t cnt, uint32_t words, uint64_t *keys, uint64_t ld, uint32_t *status,
+                            cudaStream_t s);
 
 // ---- sort.cu
 // Sort `rows` segments of `len` (u64 key, u32 id) pairs by key bits [0, bits) (stable,

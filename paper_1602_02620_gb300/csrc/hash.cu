@@ -379,6 +379,12 @@ cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t 
     if (cnt == 0) return cudaSuccess;
     const uint32_t dk = idx->part_off[k + 1] - idx->part_off[k];
     const PartCols pc = idx->part(k);
+    if (idx->tune.hash_tile == 2) {   // tensor-core contraction (operands built by the caller)
+        if (!idx->mma_g) return cudaErrorInvalidValue;
+        return launch_hash_mma(idx->mma_coord + (size_t)k * idx->mma_k,
+                               idx->mma_g + (size_t)k * hash_mma_operand_entries(idx->mma_k, idx->W), idx->mma_k,
+                               idx->W, pts, cnt, idx->words, keys, ld, idx->status, s);
+    }
     const uint32_t logw = idx->rp + 1;
     const uint32_t tl = idx->tune.hash_tile;
     switch (logw) {

@@ -294,18 +294,26 @@ def test_row_restricted_probe_matches_oracle(d, r, t, n):
     idx.free()
 
 
+@pytest.mark.parametrize("tile", [1, 2])
 @pytest.mark.parametrize("d,r,t", [(100, 5, None), (128, 6, None), (200, 7, None), (128, 8, None),
-                                   (1024, 9, None), (256, 16, None), (2000, 10, 2)])
-def test_wide_hash_tile_is_bit_exact(d, r, t):
-    """hash_tile = 1 (twice the points per WHT block) gives the same keys and the same directory."""
+                                   (1024, 9, None), (256, 16, None), (2000, 10, 2), (96, 12, 2), (128, 9, 3)])
+def test_hash_tiles_are_bit_exact(d, r, t, tile):
+    """hash_tile = 1 (twice the points per WHT block) and hash_tile = 2 (the O(dL) route as an
+    exact tensor-core contraction) give the oracle's keys and the same directory."""
+    fc = F()
     rng = np.random.default_rng(d + 5 * r)
     n = 1333
     pts = rand_points(rng, n, d)
     seed = 77 + d
     p = oracle.derive_params(seed, d, r, t=t)
-    a = F().build(dev(pts), d, r, seed, t=t)
-    b = F().build(dev(pts), d, r, seed, t=t, hash_tile=1)
-    assert b.tuning()["hash_tile"] == 1
+    max_dk = int(np.max(np.diff(p.part_off)))
+    if tile == 2 and (p.W < 64 or max_dk > 128):
+        with pytest.raises(fc.FclshError):
+            fc.build(dev(pts), d, r, seed, t=t, hash_tile=2)
+        return
+    a = fc.build(dev(pts), d, r, seed, t=t)
+    b = fc.build(dev(pts), d, r, seed, t=t, hash_tile=tile)
+    assert b.tuning()["hash_tile"] == tile
     assert np.array_equal(b.hash(pts[:300]), oracle.keys_direct(p, pts[:300]))
     for tau in (0, p.T // 2, p.T - 1):                          # the same tables (order inside a slot is free)
         ka, ia = a.export_table(tau)
