@@ -260,6 +260,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="fewer points of the same workload (profiling)")
     ap.add_argument("--nq", type=int, default=None, help="fewer queries of the same workload (profiling)")
+    ap.add_argument("--hash-tile", type=int, default=None, choices=(0, 1, 2),
+                    help="force the hash kernel (0/1: WHT tiles, 2: tensor-core contraction) instead of the tuned one")
     ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4],
                     help="workload id (default: the n=1M d=128 r=8 plain workload)")
     args = ap.parse_args()
@@ -292,6 +294,8 @@ def main():
     idx0 = fclsh.build(pts, w.d, w.r, seed)
     tuned = idx0.autotune(qs[: min(nq, 4096)], w.r, cache)
     idx0.free()
+    if args.hash_tile is not None:
+        tuned["hash_tile"] = args.hash_tile
 
     def step(timing: bool):
         idx = fclsh.build(pts, w.d, w.r, seed, timing=timing, hash_tile=tuned["hash_tile"])
