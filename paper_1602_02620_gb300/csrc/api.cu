@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstring>
 #include <atomic>
 #include <memory>
 #include <mutex>
@@ -141,12 +142,28 @@ void dev_free(void *p)
     cudaFreeAsync(p, 0);
 }
 
-// Device allocation list freed together on error.
+// Allocation ordered on the legacy stream only: for memory that this stream alone uses
+// until the caller synchronises it (the build), so no synchronisation here.
+static cudaError_t dev_alloc_ordered(void **p, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return cudaMalloc(p, bytes);
+    return cudaMallocFromPoolAsync(p, bytes, pool, 0);
+}
+
+// Device allocation list freed together on error.  `ordered`: every use is on the
+// legacy stream, so allocation and release are stream-ordered and never synchronise.
 struct DevAllocs {
     std::vector<void *> ptrs;
+    bool ordered = false;
+    DevAllocs() = default;
+    explicit DevAllocs(bool on_legacy_stream) : ordered(on_legacy_stream) {}
     ~DevAllocs()
     {
-        if (!ptrs.empty()) cudaDeviceSynchronize();
+        if (!ordered && !ptrs.empty()) cudaDeviceSynchronize();
         for (void *p : ptrs) dev_free(p);
     }
     template <typename T>
@@ -154,7 +171,7 @@ struct DevAllocs {
     {
         *p = nullptr;
         if (count == 0) count = 1;
-        cudaError_t e = dev_alloc((void **)p, count * sizeof(T));
+        cudaError_t e = ordered ? dev_alloc_ordered((void **)p, count * sizeof(T)) : dev_alloc((void **)p, count * sizeof(T));
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }
@@ -471,6 +488,7 @@ static fclsh_status run_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uin
 // ---------------------------------------------------------------- build
 
 // The tensor-core hash's operands (coordinate lists and G's fp16 chunks), built once.
+// s == nullptr (the build, on the legacy stream): stream-ordered, no synchronisation.
 static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s)
 {
     if (idx->mma_g) return FCLSH_OK;
@@ -482,25 +500,27 @@ static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s)
         for (uint32_t i = idx->part_off[k]; i < idx->part_off[k + 1]; ++i)
             coord[(size_t)k * K + (i - idx->part_off[k])] = idx->perm[i];
     const size_t per = hash_mma_operand_entries(K, idx->W);
-    DevAllocs tmp, keep;
-    uint32_t *dm = nullptr;
-    uint64_t *db = nullptr;
+    DevAllocs tmp(s == nullptr), keep(s == nullptr);
+    std::vector<uint64_t> mb(idx->d + (idx->d + 1) / 2);   // b values, then m (32-bit)
+    std::memcpy(mb.data(), idx->b.data(), idx->d * 8);
+    std::memcpy(reinterpret_cast<uint32_t *>(mb.data() + idx->d), idx->m.data(), idx->d * 4);
+    uint64_t *dmb = nullptr;
     cudaError_t e;
     if ((e = keep.alloc(&idx->mma_coord, coord.size())) != cudaSuccess ||
-        (e = keep.alloc(&idx->mma_g, per * t)) != cudaSuccess || (e = tmp.alloc(&dm, idx->d)) != cudaSuccess ||
-        (e = tmp.alloc(&db, idx->d)) != cudaSuccess) {
+        (e = keep.alloc(&idx->mma_g, per * t)) != cudaSuccess || (e = tmp.alloc(&dmb, mb.size())) != cudaSuccess) {
         idx->mma_coord = nullptr;
         idx->mma_g = nullptr;
         return cuda_fail(e, "cudaMalloc(tensor-core hash operands)");
     }
+    const uint64_t *db = dmb;
+    const uint32_t *dm = reinterpret_cast<const uint32_t *>(dmb + idx->d);
     FCLSH_CUDA(cudaMemcpyAsync(idx->mma_coord, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
-    FCLSH_CUDA(cudaMemcpyAsync(dm, idx->m.data(), idx->d * 4, cudaMemcpyHostToDevice, s));
-    FCLSH_CUDA(cudaMemcpyAsync(db, idx->b.data(), idx->d * 8, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemcpyAsync(dmb, mb.data(), mb.size() * 8, cudaMemcpyHostToDevice, s));
     for (uint32_t k = 0; k < t; ++k) {
         const uint32_t lo = idx->part_off[k];
         FCLSH_CUDA(build_mma_operand(dm + lo, db + lo, idx->part_off[k + 1] - lo, K, idx->W, idx->mma_g + k * per, s));
     }
-    FCLSH_CUDA(cudaStreamSynchronize(s));
+    if (s) FCLSH_CUDA(cudaStreamSynchronize(s));
     keep.release();
     idx->device_bytes += coord.size() * 4 + per * t * 2;
     return FCLSH_OK;
@@ -593,12 +613,19 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     std::vector<uint64_t> bval;
     column_lists(d, t, W, idx->perm, idx->part_off, idx->m, idx->b, col_off, coord, bval);
 
-    DevAllocs keep;   // index memory (released into idx on success)
+    DevAllocs keep(true);   // index memory (released into idx on success); the build runs on the legacy stream
     cudaError_t e;
     if ((e = keep.alloc(&idx->points, n * idx->words)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(points)");
-    if ((e = keep.alloc(&idx->col_off, col_off.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(col_off)");
-    if ((e = keep.alloc(&idx->col_coord, coord.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(col_coord)");
-    if ((e = keep.alloc(&idx->col_b, bval.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(col_b)");
+    // the part's column lists in one block (one copy): b values, offsets, coordinates
+    std::vector<uint64_t> block(bval.size() + (col_off.size() + coord.size() + 1) / 2, 0);
+    std::memcpy(block.data(), bval.data(), bval.size() * 8);
+    std::memcpy(reinterpret_cast<uint32_t *>(block.data() + bval.size()), col_off.data(), col_off.size() * 4);
+    std::memcpy(reinterpret_cast<uint32_t *>(block.data() + bval.size()) + col_off.size(), coord.data(), coord.size() * 4);
+    uint64_t *dblock = nullptr;
+    if ((e = keep.alloc(&dblock, block.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(column lists)");
+    idx->col_b = dblock;
+    idx->col_off = reinterpret_cast<uint32_t *>(dblock + bval.size());
+    idx->col_coord = idx->col_off + col_off.size();
     if ((e = keep.alloc(&idx->offs, (size_t)idx->T * idx->offs_stride())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(directory)");
     if ((e = keep.alloc(&idx->ent, (size_t)idx->T * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(entries)");
     idx->device_bytes = n * idx->words * 8 + col_off.size() * 4 + coord.size() * 12 +
@@ -606,9 +633,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
 
     cudaStream_t s = nullptr;
     FCLSH_CUDA(cudaMemcpyAsync(idx->points, points, n * idx->words * 8, cudaMemcpyDefault, s));
-    FCLSH_CUDA(cudaMemcpyAsync(idx->col_off, col_off.data(), col_off.size() * 4, cudaMemcpyHostToDevice, s));
-    FCLSH_CUDA(cudaMemcpyAsync(idx->col_coord, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
-    FCLSH_CUDA(cudaMemcpyAsync(idx->col_b, bval.data(), bval.size() * 8, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemcpyAsync(dblock, block.data(), block.size() * 8, cudaMemcpyHostToDevice, s));
     if ((e = keep.alloc(&idx->status, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
     FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
     if (o.hash_tile == 2) {
@@ -618,7 +643,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
 
     // Transient buffers: the keys of one part, and radix-sort buffers for a chunk of its tables.
     const uint32_t L = W - 1;
-    DevAllocs tmp;
+    DevAllocs tmp(true);
     uint64_t *keys = nullptr;
     if ((e = tmp.alloc(&keys, (size_t)L * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(build keys)");
     size_t free_b = 0, total_b = 0;
@@ -719,7 +744,7 @@ extern "C" void fclsh_free(fclsh_index *idx)
     cudaSetDevice(idx->device);
     cudaDeviceSynchronize();
     drop_timers(idx);
-    void *ps[] = {idx->points, idx->col_off, idx->col_coord, idx->col_b, idx->offs, idx->ent, idx->mma_coord, idx->mma_g,
+    void *ps[] = {idx->points, idx->col_b /* the column-list block */, idx->offs, idx->ent, idx->mma_coord, idx->mma_g,
                   idx->status};
     for (void *p : ps)
         if (p) dev_free(p);

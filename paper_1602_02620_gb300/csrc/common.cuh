@@ -117,7 +117,7 @@ struct fclsh_index {
     std::vector<uint64_t> b;
     // device arrays
     uint64_t *points = nullptr;      // [n][words]
-    uint32_t *col_off = nullptr;     // [t][W+1]
+    uint32_t *col_off = nullptr;     // [t][W+1]  (col_b, col_off, col_coord: one allocation, owned via col_b)
     uint32_t *col_coord = nullptr;   // [d]
     uint64_t *col_b = nullptr;       // [d]
     uint32_t *offs = nullptr;        // [T][dir_stride(slot_bits)]: 2^slot_bits + 1 used
