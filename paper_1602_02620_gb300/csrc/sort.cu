@@ -333,12 +333,13 @@ __global__ void __launch_bounds__(kWideThreads, 2) partition_wide_kernel(RadixAr
 {
     constexpr uint32_t ND = 1u << D;
     constexpr int R = kWideSub / kWideThreads;
-    constexpr uint32_t PER = ND / kWideThreads;   // digits per thread in the scans (1, 2 or 4)
+    constexpr uint32_t PER = ND >= kWideThreads ? ND / kWideThreads : 1;   // digits per thread in the scans
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);        // [kWideSub] packed entries in digit order
     uint32_t *sg = reinterpret_cast<uint32_t *>(sk + kWideSub);   // [kWideSub] their global positions
     __shared__ uint32_t cnt[ND], st[ND], cur[ND], gofs[ND];
     const uint32_t row = blockIdx.y, tid = threadIdx.x;
+    const bool owner = tid * PER < ND;   // thread tid takes digits [tid*PER, tid*PER + PER) in the scans
     const uint64_t len = a.len;
     const uint64_t base = (uint64_t)blockIdx.x * kWideTile;
     if (base >= len) return;   // uniform
@@ -395,14 +396,14 @@ __global__ void __launch_bounds__(kWideThreads, 2) partition_wide_kernel(RadixAr
             uint32_t c[PER], mine = 0;
 #pragma unroll
             for (uint32_t i = 0; i < PER; ++i) {
-                c[i] = cnt[tid * PER + i];
+                c[i] = owner ? cnt[tid * PER + i] : 0u;
                 mine += c[i];
             }
             uint32_t tot;
             uint32_t run = block_excl_scan<uint32_t>(mine, &tot);   // barriers inside
 #pragma unroll
             for (uint32_t i = 0; i < PER; ++i) {
-                st[tid * PER + i] = run;
+                if (owner) st[tid * PER + i] = run;
                 run += c[i];
             }
         }
