@@ -67,7 +67,7 @@ def _lib():
     if _lib_handle is None:
         lib = ctypes.CDLL(build())
         u64, u32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
-        lib.oracle_derive_params.argtypes = [u64, u32, u32, u32, u64, vp, vp, vp, vp]
+        lib.oracle_derive_params.argtypes = [u64, u32, u32, u32, u32, u64, vp, vp, vp, vp]
         lib.oracle_derive_params.restype = ctypes.c_int
         lib.oracle_key_direct.argtypes = [vp, vp, u32]
         lib.oracle_key_direct.restype = u64
@@ -118,12 +118,13 @@ class Params:
     d: int
     r: int          # build radius
     t: int          # parts (Algorithm 1)
-    rp: int         # per-part radius r' = floor(r / t)
+    rp: int         # per-part radius r' = floor(r * rep / t)
     W: int          # code length 2^(r'+1)
-    perm: np.ndarray      # uint32[d]: permuted position i holds coordinate perm[i]
+    perm: np.ndarray      # uint32[D]: position i of the pre-processed vector holds coordinate perm[i]
     part_off: np.ndarray  # uint32[t+1]
-    m: np.ndarray         # uint32[d]: code column of permuted position i
-    b: np.ndarray         # uint64[d]: seed-vector entry of permuted position i
+    m: np.ndarray         # uint32[D]: code column of position i
+    b: np.ndarray         # uint64[D]: seed-vector entry of position i
+    rep: int = 1          # replication factor of Algorithm 1 (D = d * rep positions)
 
     @property
     def words(self) -> int:
@@ -146,32 +147,39 @@ class Params:
                        _ptr(self.perm), _ptr(self.part_off), _ptr(self.m), _ptr(self.b))
 
 
-def derive_params(seed: int, d: int, r: int, t: int | None = None, P: int = P_DEFAULT) -> Params:
-    """Draw the index's random choices from ``seed`` (see fclsh_oracle.c for the order)."""
+def derive_params(seed: int, d: int, r: int, t: int | None = None, P: int = P_DEFAULT, rep: int = 1) -> Params:
+    """Draw the index's random choices from ``seed`` (see fclsh_oracle.c for the order).
+
+    rep > 1 replicates every vector rep times first (Algorithm 1 for cr < log n); the
+    index then covers radius r * rep of the replicated vectors."""
     if t is None:
-        t = default_parts(r)
-    rp = r // t
+        t = 1 if rep > 1 else default_parts(r)
+    rp = r * rep // t
     W = 2 << rp
-    perm = np.zeros(d, np.uint32)
+    D = d * rep
+    perm = np.zeros(D, np.uint32)
     part_off = np.zeros(t + 1, np.uint32)
-    m = np.zeros(d, np.uint32)
-    b = np.zeros(d, np.uint64)
-    rc = _lib().oracle_derive_params(seed, d, t, W, P, _ptr(perm), _ptr(part_off), _ptr(m), _ptr(b))
+    m = np.zeros(D, np.uint32)
+    b = np.zeros(D, np.uint64)
+    rc = _lib().oracle_derive_params(seed, d, t, rep, W, P, _ptr(perm), _ptr(part_off), _ptr(m), _ptr(b))
     if rc != 0:
-        raise ValueError("bad parameters d=%d r=%d t=%d" % (d, r, t))
-    return Params(P, d, r, t, rp, W, perm, part_off, m, b)
+        raise ValueError("bad parameters d=%d r=%d t=%d rep=%d" % (d, r, t, rep))
+    return Params(P, d, r, t, rp, W, perm, part_off, m, b, rep)
 
 
-def make_params(d: int, r: int, m, b, P: int = P_DEFAULT, t: int = 1, perm=None, part_off=None) -> Params:
-    """Explicit parameters (e.g. the worked examples of Sec. 2.3 and 3.1)."""
-    rp = r // t
+def make_params(d: int, r: int, m, b, P: int = P_DEFAULT, t: int = 1, perm=None, part_off=None,
+                rep: int = 1) -> Params:
+    """Explicit parameters (e.g. the worked examples of Sec. 2.3 and 3.1); m and b have
+    d * rep entries, and without a perm position i reads coordinate i mod d."""
+    rp = r * rep // t
     W = 2 << rp
-    perm = np.arange(d, dtype=np.uint32) if perm is None else np.ascontiguousarray(perm, np.uint32)
+    D = d * rep
+    perm = (np.arange(D, dtype=np.uint32) % d) if perm is None else np.ascontiguousarray(perm, np.uint32)
     if part_off is None:
-        blk = d // t
-        part_off = [k * blk for k in range(t)] + [d]
+        blk = D // t
+        part_off = [k * blk for k in range(t)] + [D]
     return Params(P, d, r, t, rp, W, perm, np.ascontiguousarray(part_off, np.uint32),
-                  np.ascontiguousarray(m, np.uint32), np.ascontiguousarray(b, np.uint64))
+                  np.ascontiguousarray(m, np.uint32), np.ascontiguousarray(b, np.uint64), rep)
 
 
 def _pts(pts, words: int) -> np.ndarray:
@@ -243,9 +251,10 @@ def query(p: Params, pts, tables, q, radius: int, rows: int = 0):
 
 
 def probe_rows(p: Params, radius: int) -> int:
-    """Code rows per part that a query of this radius must probe: 2^(floor(radius/t)+1) - 1,
-    at most W - 1 (pigeonhole over the t parts, then Theorem 1 on the map m mod 2^(floor(radius/t)+1))."""
-    e = radius // p.t + 1
+    """Code rows per part that a query of this radius must probe: 2^(floor(radius*rep/t)+1) - 1,
+    at most W - 1 (pigeonhole over the t parts, or distance radius*rep between the replicated
+    vectors, then Theorem 1 on the map m mod 2^(floor(radius*rep/t)+1))."""
+    e = radius * p.rep // p.t + 1
     return min(p.W - 1, (1 << e) - 1) if e < 63 else p.W - 1
 
 

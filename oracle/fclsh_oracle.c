@@ -31,14 +31,17 @@ typedef __int128 i128;
 /* Parameters of one fcLSH index.  All arrays are owned by the caller. */
 typedef struct {
     uint64_t P;              /* the prime of Eq. (1) */
-    uint32_t d;              /* dimensionality before partitioning */
+    uint32_t d;              /* dimensionality of the input points */
     uint32_t t;              /* number of parts (Algorithm 1); 1 = no partitioning */
     uint32_t W;              /* code length 2^(r'+1) */
     uint32_t words;          /* uint64 words per packed point = ceil(d/64) */
-    const uint32_t *perm;    /* [d]  pi: position i of the permuted vector is coordinate perm[i] */
-    const uint32_t *part_off;/* [t+1] part k = permuted positions [part_off[k], part_off[k+1]) */
-    const uint32_t *m;       /* [d]  m_k(i) in [0, W) for permuted position i (column of the code) */
-    const uint64_t *b;       /* [d]  b_k(i) in [0, P) for permuted position i (Eq. 1; the seed vector of Algorithm 2) */
+    /* Positions: the D entries of the pre-processed vector (Algorithm 1).  D = d
+       without replication (a permutation of the coordinates), D = d * rep with it
+       (the vector written rep times in a row).  The arrays have D entries. */
+    const uint32_t *perm;    /* [D]  position i of the pre-processed vector is coordinate perm[i] */
+    const uint32_t *part_off;/* [t+1] part k = positions [part_off[k], part_off[k+1]) */
+    const uint32_t *m;       /* [D]  m_k(i) in [0, W) for position i (column of the code) */
+    const uint64_t *b;       /* [D]  b_k(i) in [0, P) for position i (Eq. 1; the seed vector of Algorithm 2) */
 } oracle_params;
 
 /* ---------------------------------------------------------------- SplitMix64 */
@@ -81,28 +84,35 @@ static void fisher_yates(uint64_t *state, uint32_t *a, uint32_t len)
 }
 
 /*
- * Draw pi, m_k and b_k from `seed` (Algorithm 1 permutation; Algorithm 2 choices of b and m).
+ * Draw pi, m_k and b_k from `seed` (Algorithm 1 pre-processing; Algorithm 2 choices of b and m).
+ * Pre-processing (Algorithm 1): with rep > 1 (needs t = 1) the vector is replicated:
+ * q^(rep) = q q ... q, so position i is coordinate i mod d, and nothing is drawn
+ * (Example 3: 0011 replicated twice is 00110011).  Otherwise the positions are the
+ * coordinates, permuted when t > 1.
  * Order of draws: (i) if t > 1, pi by Fisher-Yates over [d]; (ii) for each part k
- * in order: m_k, then b_k.  Part k < t-1 takes floor(d/t) consecutive permuted
- * positions and the last part takes the remainder (Algorithm 1, partitioning).
+ * in order: m_k, then b_k.  Part k < t-1 takes floor(D/t) consecutive positions
+ * and the last part takes the remainder (Algorithm 1, partitioning).
  *   - d'_k <= W (specific construction, Algorithm 2): sigma = Fisher-Yates
  *     permutation of [W]; m_k(i) = sigma(i) for i < d'_k.
  *   - d'_k > W (general construction, Eq. 4): m_k(i) = 1 + next() % (W-1), i.e.
  *     uniform over the columns 1..W-1; column 0 is left out (Sec. 3.3, the sharper
  *     bound after Lemma 1).
  *   - b_k(i) uniform in [0, P) by rejection.
- * Returns 0 on success, -1 on bad arguments.
+ * The arrays perm, m, b hold D = d * rep entries.  Returns 0 on success, -1 on bad arguments.
  */
-int oracle_derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t W, uint64_t P,
+int oracle_derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t rep, uint32_t W, uint64_t P,
                          uint32_t *perm, uint32_t *part_off, uint32_t *m, uint64_t *b)
 {
-    if (d == 0 || t == 0 || t > d || W < 2 || (W & (W - 1)) != 0 || P < 2) return -1;
+    if (d == 0 || t == 0 || t > d || rep == 0 || (rep > 1 && t > 1) || W < 2 || (W & (W - 1)) != 0 || P < 2)
+        return -1;
     uint64_t state = seed;
-    for (uint32_t i = 0; i < d; i++) perm[i] = i;
+    uint32_t D = d * rep;
+    for (uint32_t copy = 0; copy < rep; copy++)          /* replication: copy after copy */
+        for (uint32_t c = 0; c < d; c++) perm[copy * d + c] = c;
     if (t > 1) fisher_yates(&state, perm, d);
-    uint32_t block = d / t;
+    uint32_t block = D / t;
     for (uint32_t k = 0; k < t; k++) part_off[k] = k * block;
-    part_off[t] = d;
+    part_off[t] = D;
     uint32_t *sigma = (uint32_t *)malloc(sizeof(uint32_t) * W);
     if (!sigma) return -1;
     for (uint32_t k = 0; k < t; k++) {

@@ -80,6 +80,120 @@ def test_example3_partition():
     assert int(keys[1 * 3 + 0]) == bits_to_int(g["part2"][0])
 
 
+def test_example3_replication():
+    """Example 3 (Sec. 3.1): replicating 0011 twice gives 00110011.  The derived positions
+    of a replicated index read those bits, and with every position on column 1 and
+    b_i = 2^i the row-1 key spells the replicated vector."""
+    g = read_golden("example3_preprocessing.txt")
+    q, q2 = g["q"][0], g["replicated2"][0]
+    p = oracle.derive_params(9, 4, 1, rep=2)
+    assert p.rep == 2 and p.t == 1 and p.rp == 2 and p.W == 8 and p.perm.shape == (8,)
+    assert "".join(q[int(c)] for c in p.perm) == q2
+    p = oracle.make_params(4, 1, m=[1] * 8, b=_pow2_b(8), rep=2)
+    assert int(oracle.keys_direct(p, bits_to_words(q))[0, 0]) == bits_to_int(q2)
+    assert int(oracle.keys_fht(p, bits_to_words(q))[0, 0]) == bits_to_int(q2)
+
+
+def _repeat_bits(pts, d, rep):
+    """Each packed d-bit row written rep times in a row, repacked (plain numpy bit ops)."""
+    words = (d + 63) // 64
+    bits = np.unpackbits(pts.view(np.uint8).reshape(-1, words * 8), axis=1, bitorder="little")[:, :d]
+    rb = np.concatenate([bits] * rep, axis=1)
+    D = d * rep
+    W2 = (D + 63) // 64
+    padded = np.zeros((rb.shape[0], W2 * 64), np.uint8)
+    padded[:, :D] = rb
+    return np.packbits(padded, axis=1, bitorder="little").view(np.uint64).reshape(-1, W2)
+
+
+@pytest.mark.parametrize("d,r,rep", [(10, 1, 4), (40, 2, 3), (24, 3, 2), (100, 2, 2), (70, 1, 5), (17, 4, 2)])
+def test_replication_equals_index_of_repeated_vectors(d, r, rep):
+    """Algorithm 1, cr < log n: a replicated index gives every point the keys that a plain
+    index on the explicitly repeated d*rep-bit vectors gives, with the same m and b and
+    radius r*rep (covering both the specific, d*rep <= W, and general construction)."""
+    rng = np.random.default_rng(d * 13 + rep)
+    p = oracle.derive_params(d + 100 * rep, d, r, rep=rep)
+    assert p.rp == r * rep and p.W == 2 << (r * rep)
+    pts = rng.integers(0, 2**63, size=(60, (d + 63) // 64), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    plain = oracle.make_params(d * rep, r * rep, m=p.m, b=p.b)
+    assert plain.W == p.W
+    want = oracle.keys_direct(plain, _repeat_bits(pts, d, rep))
+    assert np.array_equal(oracle.keys_direct(p, pts), want)
+    assert np.array_equal(oracle.keys_fht(p, pts), want)
+
+
+@pytest.mark.parametrize("d,r,rep", [(6, 1, 3), (5, 2, 2), (8, 1, 4), (7, 2, 2), (12, 1, 2)])
+def test_replication_total_recall_exhaustive(d, r, rep):
+    """Lemma 4 (1): with replication every z with |z| <= r still collides with 0 in some
+    table, for random m and b (the replicated z has rep*|z| <= r' ones, Theorem 1)."""
+    zs = list(_ball(d, r))
+    Z = np.zeros((len(zs), 1), np.uint64)
+    for i, pos in enumerate(zs):
+        Z[i, 0] = sum(1 << j for j in pos)
+    for trial in range(25):
+        p = oracle.derive_params(trial * 7 + d, d, r, rep=rep)
+        k = oracle.keys_direct(p, Z)
+        assert np.all((k == 0).any(axis=0)), trial
+
+
+def test_replication_expected_collisions():
+    """Lemma 4 (2), replication: a pair at distance D0 collides in fewer than
+    2 * 2^(rep r) * 2^(-rep D0) tables on average.  The rep*D0 differing positions have
+    independent columns, so the expectation has the closed forms of Theorem 2 with
+    rep*D0 in place of the distance; both are pinned (4 standard errors)."""
+    from math import comb
+    rng = np.random.default_rng(11)
+    for d, r, rep, general in ((12, 2, 2, False), (60, 1, 3, True)):
+        W = 2 << (r * rep)
+        assert (d * rep > W) == general
+        for dist in (1, 2, 3):
+            k = rep * dist
+            counts = []
+            for trial in range(300):
+                p = oracle.derive_params(7000 + trial, d, r, rep=rep)
+                x = rng.integers(0, 2**63, size=(1, 1), dtype=np.uint64)
+                x[0, 0] &= np.uint64((1 << d) - 1)
+                y = x.copy()
+                for pos in rng.choice(d, size=dist, replace=False):
+                    y[0, 0] ^= np.uint64(1) << np.uint64(pos)
+                counts.append(int((oracle.keys_direct(p, x) == oracle.keys_direct(p, y)).sum()))
+            mean, se = np.mean(counts), np.std(counts) / np.sqrt(len(counts))
+            if general:
+                exact = (W - 1) * ((W / 2 - 1) / (W - 1)) ** k
+            else:
+                exact = (W - 1) * comb(W // 2, k) / comb(W, k)
+            assert exact < 2 * 2.0 ** (rep * r) * 2.0 ** (-rep * dist)
+            assert abs(mean - exact) <= 4 * se + 1e-9, (d, rep, dist, mean, exact)
+
+
+@pytest.mark.parametrize("d,r,rep", [(32, 2, 3), (48, 3, 2), (100, 2, 2), (64, 1, 4)])
+def test_replicated_query_equals_linear_scan(d, r, rep):
+    """Strategy 2 on a replicated index reports the linear-scan answer for every radius
+    rho <= r, probing all tables or only rows v < 2^(rho*rep+1)."""
+    rng = np.random.default_rng(d + 3 * rep)
+    words = (d + 63) // 64
+    n = 250
+    pts = rng.integers(0, 2**63, size=(n, words), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    pts[5:9] = pts[4]
+    p = oracle.derive_params(d * r + rep, d, r, rep=rep)
+    tables = oracle.build_tables(p, pts)
+    for qi in range(15):
+        q = pts[rng.integers(0, n)].copy()
+        for pos in rng.choice(d, size=rng.integers(0, r + 2), replace=False):
+            q[pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+        for rho in range(r + 1):
+            rows = oracle.probe_rows(p, rho)
+            assert rows == min(p.W - 1, (2 << (rho * rep)) - 1)
+            ids, ncoll, ncand = oracle.query(p, pts, tables, q, rho, rows=rows)
+            full, fcoll, fcand = oracle.query(p, pts, tables, q, rho)
+            assert ids.tolist() == oracle.linear_scan(pts, q, rho).tolist() == full.tolist()
+            assert ncoll <= fcoll and ncand <= fcand and ncoll >= ncand >= len(ids)
+
+
 # ----------------------------------------------------------------- Hadamard code
 
 @pytest.mark.parametrize("W", [2, 4, 8, 16, 32])
