@@ -56,11 +56,13 @@ typedef struct {
                                  else the smallest t with floor(r/t) <= 10 */
     uint32_t slot_bits;       /* bucket-directory slots per table = 2^slot_bits; 0 = max(18, ceil(log2 n)) */
     uint64_t mem_budget;      /* bytes for transient build buffers; 0 = 1/4 of free device memory */
-    /* Explicit random choices (all four set, or all NULL to draw them from `seed`):
-       perm[d]: permuted position i holds coordinate perm[i] (Algorithm 1's permutation);
-       part_off[t+1]: part k = permuted positions [part_off[k], part_off[k+1]);
-       m[d]: code column in [0, W) of permuted position i (Eq. 4 map / Algorithm 2 permutation);
-       b[d]: seed-vector entry in [0, P) of permuted position i (Eq. 1). Host pointers, copied. */
+    /* Explicit random choices (all four set, or all NULL to draw them from `seed`), over the
+       D = d * replicate positions of the (replicated) vector:
+       perm[D]: position i holds coordinate perm[i] (Algorithm 1's permutation; with replication
+                it must be i mod d, copy i / d of the vector);
+       part_off[t+1]: part k = positions [part_off[k], part_off[k+1]);
+       m[D]: code column in [0, W) of position i (Eq. 4 map / Algorithm 2 permutation);
+       b[D]: seed-vector entry in [0, P) of position i (Eq. 1). Host pointers, copied. */
     const uint32_t *perm;
     const uint32_t *part_off;
     const uint32_t *m;
@@ -70,6 +72,15 @@ typedef struct {
                                  tile, 1 = twice the points per tile where it fits (W <= 1024), 2 = the
                                  O(dL) route as an exact tensor-core contraction (W >= 64, parts of at most
                                  128 coordinates) */
+    uint32_t replicate;       /* Algorithm 1's replication for cr < log n: every point and query is repeated
+                                 this many times (0 or 1 = none; needs t <= 1).  The index then covers
+                                 radius r * replicate of the repeated vectors: W = 2^(r*replicate + 1),
+                                 r * replicate <= 10.  Queries still use radii <= r of the original vectors. */
+    double approx_c;          /* > 0 with t = 0 and replicate = 0: choose t and replicate by Algorithm 1 for
+                                 this approximation factor c, with log = log2 n: replicate floor(log2 n / (c r))
+                                 times when c r < log2 n (capped so that r * replicate <= 10), else
+                                 ceil(c r / log2 n) parts; without replication t is raised until
+                                 floor(r/t) <= 10.  0 = the rule of t. */
 } fclsh_build_opts;
 
 typedef struct {
@@ -78,6 +89,7 @@ typedef struct {
     uint64_t P;
     uint64_t device_bytes;    /* device memory held by the index */
     int device;               /* CUDA device ordinal */
+    uint32_t rep;             /* replication factor (1 = none); rp = r * rep / t is the covered radius per part */
 } fclsh_info;
 
 /* Host-side query results (library-owned; free with fclsh_result_free). */
@@ -112,10 +124,11 @@ typedef struct {
     uint32_t use_graph;       /* capture a batch's launches into a CUDA graph and replay it */
     uint32_t hash_tile;       /* hash kernel of fclsh_hash and of later builds (fclsh_build_opts.hash_tile): 0, 1, 2 */
     uint32_t probe_rows;      /* 0: a query probes all T tables (Strategy 2, Sec. 2.2).  1: a query of radius
-                                 rho probes only the code rows v = 1 .. 2^(floor(rho/t)+1) - 1 of each part;
-                                 the ids are the same (pigeonhole over the parts, Sec. 3.1, and Theorem 1
-                                 for the map m mod 2^(floor(rho/t)+1)), and #Collisions / #Candidates count
-                                 the probed tables only.  Not chosen by fclsh_autotune. */
+                                 rho probes only the code rows v = 1 .. 2^(floor(rho*rep/t)+1) - 1 of each
+                                 part; the ids are the same (pigeonhole over the parts, Sec. 3.1, or the
+                                 distance rho*rep of the replicated vectors, and Theorem 1 for the map
+                                 m mod 2^(floor(rho*rep/t)+1)), and #Collisions / #Candidates count the
+                                 probed tables only.  Not chosen by fclsh_autotune. */
 } fclsh_tuning;
 
 /* ------------------------------------------------------------------ index */
@@ -142,8 +155,9 @@ void fclsh_free(fclsh_index *idx);
 fclsh_status fclsh_get_info(const fclsh_index *idx, fclsh_info *out);
 
 /*
- * Copy out the index's random choices (host arrays sized d, t+1, d, d) so that
- * they can be compared with an independent derivation.  Any pointer may be NULL.
+ * Copy out the index's random choices (host arrays sized D, t+1, D, D with
+ * D = d * rep positions) so that they can be compared with an independent
+ * derivation.  Any pointer may be NULL.
  */
 fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm, uint32_t *part_off,
                               uint32_t *m, uint64_t *b);

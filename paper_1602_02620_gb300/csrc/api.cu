@@ -391,6 +391,7 @@ static QueryArgs make_args(fclsh_index *idx)
     a.hset_log2 = idx->tune.hash_set_log2;
     a.inline_len = idx->tune.inline_probe;
     a.probe_rows = idx->tune.probe_rows;
+    a.rep = idx->rep;
     a.col_off = idx->col_off;
     a.col_coord = idx->col_coord;
     a.col_b = idx->col_b;
@@ -501,9 +502,10 @@ static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s)
             coord[(size_t)k * K + (i - idx->part_off[k])] = idx->perm[i];
     const size_t per = hash_mma_operand_entries(K, idx->W);
     DevAllocs tmp(s == nullptr), keep(s == nullptr);
-    std::vector<uint64_t> mb(idx->d + (idx->d + 1) / 2);   // b values, then m (32-bit)
-    std::memcpy(mb.data(), idx->b.data(), idx->d * 8);
-    std::memcpy(reinterpret_cast<uint32_t *>(mb.data() + idx->d), idx->m.data(), idx->d * 4);
+    const uint32_t D = idx->positions();
+    std::vector<uint64_t> mb(D + (D + 1) / 2);   // b values, then m (32-bit)
+    std::memcpy(mb.data(), idx->b.data(), (size_t)D * 8);
+    std::memcpy(reinterpret_cast<uint32_t *>(mb.data() + D), idx->m.data(), (size_t)D * 4);
     uint64_t *dmb = nullptr;
     cudaError_t e;
     if ((e = keep.alloc(&idx->mma_coord, coord.size())) != cudaSuccess ||
@@ -513,7 +515,7 @@ static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s)
         return cuda_fail(e, "cudaMalloc(tensor-core hash operands)");
     }
     const uint64_t *db = dmb;
-    const uint32_t *dm = reinterpret_cast<const uint32_t *>(dmb + idx->d);
+    const uint32_t *dm = reinterpret_cast<const uint32_t *>(dmb + D);
     FCLSH_CUDA(cudaMemcpyAsync(idx->mma_coord, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
     FCLSH_CUDA(cudaMemcpyAsync(dmb, mb.data(), mb.size() * 8, cudaMemcpyHostToDevice, s));
     for (uint32_t k = 0; k < t; ++k) {
@@ -547,11 +549,18 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if (d == 0 || d > 16384) return fail(FCLSH_EINVAL, "d must be in 1..16384 (got %u)", d);
     fclsh_build_opts o{};
     if (opts) o = *opts;
-    const uint32_t t = o.t ? o.t : default_parts(r);
+    if (!(o.approx_c >= 0.0)) return fail(FCLSH_EINVAL, "approx_c must be >= 0");
+    uint32_t t = o.t, rep = o.replicate ? o.replicate : 1;
+    if (o.approx_c > 0.0 && !o.t && !o.replicate) algorithm1_rule(n, r, o.approx_c, &t, &rep);
+    if (!t) t = rep > 1 ? 1 : default_parts(r);
+    if (rep > 32) return fail(FCLSH_EINVAL, "replicate must be at most 32 (got %u)", rep);
+    if (rep > 1 && t > 1) return fail(FCLSH_EINVAL, "replication and partitioning exclude each other (t = %u, replicate = %u)", t, rep);
     if (t > d) return fail(FCLSH_EINVAL, "t = %u parts exceed d = %u", t, d);
-    const uint32_t rp = r / t;
-    if (rp + 1 > (uint32_t)kMaxLogW) return fail(FCLSH_EINVAL, "per-part radius floor(r/t) = %u exceeds 10", rp);
+    const uint32_t rp = r * rep / t;
+    if (rp + 1 > (uint32_t)kMaxLogW)
+        return fail(FCLSH_EINVAL, "per-part radius floor(r*replicate/t) = %u exceeds 10", rp);
     const uint32_t W = 2u << rp;
+    const uint32_t D = d * rep;   // positions of the (replicated) vector
 
     auto idx = new fclsh_index();
     std::unique_ptr<fclsh_index> guard(idx);
@@ -565,6 +574,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->words = (d + 63) / 64;
     idx->r = r;
     idx->t = t;
+    idx->rep = rep;
     idx->rp = rp;
     idx->W = W;
     idx->T = t * (W - 1);
@@ -575,21 +585,25 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     const bool explicit_params = o.perm || o.part_off || o.m || o.b;
     if (explicit_params) {
         if (!(o.perm && o.part_off && o.m && o.b)) return fail(FCLSH_EINVAL, "explicit parameters need all of perm, part_off, m, b");
-        idx->perm.assign(o.perm, o.perm + d);
+        idx->perm.assign(o.perm, o.perm + D);
         idx->part_off.assign(o.part_off, o.part_off + t + 1);
-        idx->m.assign(o.m, o.m + d);
-        idx->b.assign(o.b, o.b + d);
+        idx->m.assign(o.m, o.m + D);
+        idx->b.assign(o.b, o.b + D);
         std::vector<char> seen(d, 0);
-        for (uint32_t i = 0; i < d; ++i) {
-            if (idx->perm[i] >= d || seen[idx->perm[i]]) return fail(FCLSH_EINVAL, "perm is not a permutation of [d]");
-            seen[idx->perm[i]] = 1;
+        for (uint32_t i = 0; i < D; ++i) {
+            if (rep > 1) {
+                if (idx->perm[i] != i % d) return fail(FCLSH_EINVAL, "with replication perm[i] must be i mod d");
+            } else {
+                if (idx->perm[i] >= d || seen[idx->perm[i]]) return fail(FCLSH_EINVAL, "perm is not a permutation of [d]");
+                seen[idx->perm[i]] = 1;
+            }
             if (idx->m[i] >= W) return fail(FCLSH_EINVAL, "m[%u] = %u is not below W = %u", i, idx->m[i], W);
             if (idx->b[i] >= kP) return fail(FCLSH_EINVAL, "b[%u] is not below P", i);
         }
-        if (idx->part_off[0] != 0 || idx->part_off[t] != d) return fail(FCLSH_EINVAL, "part_off must run from 0 to d");
+        if (idx->part_off[0] != 0 || idx->part_off[t] != D) return fail(FCLSH_EINVAL, "part_off must run from 0 to D");
         for (uint32_t k = 0; k < t; ++k)
             if (idx->part_off[k + 1] <= idx->part_off[k]) return fail(FCLSH_EINVAL, "parts must be non-empty and ordered");
-    } else if (derive_params(seed, d, t, W, idx->perm, idx->part_off, idx->m, idx->b) != 0) {
+    } else if (derive_params(seed, d, t, rep, W, idx->perm, idx->part_off, idx->m, idx->b) != 0) {
         return fail(FCLSH_EINVAL, "cannot derive parameters");
     }
     uint32_t max_dk = 0;
@@ -611,7 +625,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
 
     std::vector<uint32_t> col_off, coord;
     std::vector<uint64_t> bval;
-    column_lists(d, t, W, idx->perm, idx->part_off, idx->m, idx->b, col_off, coord, bval);
+    column_lists(D, t, W, idx->perm, idx->part_off, idx->m, idx->b, col_off, coord, bval);
 
     DevAllocs keep(true);   // index memory (released into idx on success); the build runs on the legacy stream
     cudaError_t e;
@@ -766,6 +780,7 @@ extern "C" fclsh_status fclsh_get_info(const fclsh_index *idx, fclsh_info *out)
     out->P = idx->P;
     out->device_bytes = idx->device_bytes;
     out->device = idx->device;
+    out->rep = idx->rep;
     return FCLSH_OK;
 }
 
@@ -773,10 +788,11 @@ extern "C" fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm,
                                          uint64_t *b)
 {
     if (!idx) return fail(FCLSH_EINVAL, "index is NULL");
-    if (perm) memcpy(perm, idx->perm.data(), idx->d * 4);
+    const size_t D = idx->positions();
+    if (perm) memcpy(perm, idx->perm.data(), D * 4);
     if (part_off) memcpy(part_off, idx->part_off.data(), (idx->t + 1) * 4);
-    if (m) memcpy(m, idx->m.data(), idx->d * 4);
-    if (b) memcpy(b, idx->b.data(), idx->d * 8);
+    if (m) memcpy(m, idx->m.data(), D * 4);
+    if (b) memcpy(b, idx->b.data(), D * 8);
     return FCLSH_OK;
 }
 
@@ -1283,7 +1299,8 @@ extern "C" const char *fclsh_version(void) { return "fclsh-gb300 0.1 (sm_103a)";
 static std::string tune_key(const fclsh_index *idx)
 {
     char buf[160];
-    snprintf(buf, sizeof buf, "n=%llu,d=%u,r=%u,t=%u,W=%u", (unsigned long long)idx->n, idx->d, idx->r, idx->t, idx->W);
+    snprintf(buf, sizeof buf, "n=%llu,d=%u,r=%u,t=%u,rep=%u,W=%u", (unsigned long long)idx->n, idx->d, idx->r, idx->t,
+             idx->rep, idx->W);
     return buf;
 }
 

@@ -61,7 +61,8 @@ struct QueryArgs {
     const uint64_t *points;
     uint64_t n;
     uint32_t words, t, W, T, slot_bits, hset_log2, inline_len;
-    uint32_t probe_rows;          // 1: probe only the code rows v < 2^(floor(radius/t)+1) of each part
+    uint32_t probe_rows;          // 1: probe only the code rows v < 2^(floor(radius*rep/t)+1) of each part
+    uint32_t rep;                 // replication factor of Algorithm 1 (1 = none)
     const uint32_t *col_off, *col_coord;
     const uint64_t *col_b;
     const uint32_t *offs;
@@ -85,14 +86,15 @@ struct QueryArgs {
 };
 
 // Code rows a query of this radius probes in every part: all W-1, or with
-// probe_rows only v = 1..2^(floor(radius/t)+1)-1 (a point within the radius is
-// within floor(radius/t) of the query on some part, Sec. 3.1, and Theorem 1 for
-// the map m mod 2^(floor(radius/t)+1) makes the two collide on one of those rows).
+// probe_rows only v = 1..2^(floor(radius*rep/t)+1)-1 (a point within the radius is
+// within floor(radius/t) of the query on some part, Sec. 3.1, or within radius*rep
+// of it after replicating both rep times, and Theorem 1 for the map
+// m mod 2^(that radius + 1) makes the two collide on one of those rows).
 __device__ __forceinline__ uint32_t rows_per_part(const QueryArgs &a, uint32_t radius)
 {
     const uint32_t L = a.W - 1;
     if (!a.probe_rows) return L;
-    const uint32_t e = radius / a.t + 1;
+    const uint32_t e = radius * a.rep / a.t + 1;
     const uint32_t rows = e >= 31 ? L : (1u << e) - 1u;
     return rows < L ? rows : L;
 }
@@ -111,15 +113,16 @@ struct fclsh_index {
     int device = 0;
     uint64_t n = 0;
     uint32_t d = 0, words = 0, r = 0, t = 0, rp = 0, W = 0, T = 0, slot_bits = 0;
+    uint32_t rep = 1;                // Algorithm 1 replication: positions D = d * rep, position i reads coordinate perm[i]
     uint64_t P = fclsh::kP;
-    // host copy of the random choices
+    // host copy of the random choices, one entry per position ([D])
     std::vector<uint32_t> perm, part_off, m;
     std::vector<uint64_t> b;
     // device arrays
     uint64_t *points = nullptr;      // [n][words]
     uint32_t *col_off = nullptr;     // [t][W+1]  (col_b, col_off, col_coord: one allocation, owned via col_b)
-    uint32_t *col_coord = nullptr;   // [d]
-    uint64_t *col_b = nullptr;       // [d]
+    uint32_t *col_coord = nullptr;   // [D]
+    uint64_t *col_b = nullptr;       // [D]
     uint32_t *offs = nullptr;        // [T][dir_stride(slot_bits)]: 2^slot_bits + 1 used
     uint64_t *ent = nullptr;         // [T][n]: (key >> slot_bits) << 32 | id
     // tensor-core hash (hash_tile 2): padded coordinates per part, their lists [t][mma_k]
@@ -137,6 +140,7 @@ struct fclsh_index {
     int sm_count = 0;
     size_t smem_optin = 0;
 
+    uint32_t positions() const { return d * rep; }
     uint64_t slots() const { return 1ULL << slot_bits; }
     uint64_t offs_stride() const { return fclsh::dir_stride(slot_bits); }
     fclsh::PartCols part(uint32_t k) const
@@ -162,9 +166,10 @@ fclsh_status cuda_fail(cudaError_t e, const char *what);
 
 // ---- params.cpp
 uint32_t default_parts(uint32_t r);
-int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t W, std::vector<uint32_t> &perm,
+void algorithm1_rule(uint64_t n, uint32_t r, double c, uint32_t *t, uint32_t *rep);
+int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t rep, uint32_t W, std::vector<uint32_t> &perm,
                   std::vector<uint32_t> &part_off, std::vector<uint32_t> &m, std::vector<uint64_t> &b);
-void column_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
+void column_lists(uint32_t D, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
                   const std::vector<uint32_t> &part_off, const std::vector<uint32_t> &m,
                   const std::vector<uint64_t> &b, std::vector<uint32_t> &col_off,
                   std::vector<uint32_t> &coord, std::vector<uint64_t> &bval);

@@ -187,6 +187,7 @@ extern "C" fclsh_status fclsh_query_plain_noalloc(const fclsh_index *cidx, const
     a.W = idx->W;
     a.T = idx->T;
     a.probe_rows = idx->tune.probe_rows;
+    a.rep = idx->rep;
     a.slot_bits = idx->slot_bits;
     a.offs = idx->offs;
     a.offs_stride = idx->offs_stride();

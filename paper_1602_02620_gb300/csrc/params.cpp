@@ -7,9 +7,15 @@
 // t > 1 (Fisher-Yates from the top), then for every part k in turn its map m_k
 // followed by its seed vector b_k.  Uniform values below P take the top 50 bits
 // of a draw and reject values >= P.
+//
+// Replication (Algorithm 1, cr < log n): the vector is repeated rep times, so
+// there are D = d * rep positions and position i reads coordinate i mod d (copy
+// i / d); it takes no draws and needs t = 1.  Positions then play the role that
+// coordinates play without replication.
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -65,19 +71,48 @@ uint32_t default_parts(uint32_t r)
     return t;
 }
 
-int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t W, std::vector<uint32_t> &perm,
+// Algorithm 1's choice for approximation factor c, reading its log as log2 (the
+// covering family has 2^(r+1) tables and a far pair collides in a table with
+// probability 2^-distance, so c r = log2 n balances them like classic LSH):
+// replicate floor(log2 n / (c r)) times when c r < log2 n, partition into
+// ceil(c r / log2 n) parts when c r > log2 n.  The kernels cover at most radius
+// 10 per part, so replication is capped at floor(10 / r) copies and t is raised
+// until floor(r / t) <= 10; both keep every guarantee (any t and rep are exact).
+void algorithm1_rule(uint64_t n, uint32_t r, double c, uint32_t *t, uint32_t *rep)
+{
+    *t = 1;
+    *rep = 1;
+    if (r == 0) return;
+    const double lg = std::log2((double)(n < 2 ? 2 : n));
+    const double cr = c * r;
+    uint32_t parts = 1;
+    if (cr < lg) {
+        uint32_t R = (uint32_t)std::floor(lg / cr);
+        if (R > 10 / r) R = 10 / r;
+        *rep = R < 1 ? 1 : R;
+    } else if (cr > lg) {
+        parts = (uint32_t)std::ceil(cr / lg);
+    }
+    if (*rep == 1) {
+        while (r / parts > 10) ++parts;
+        *t = parts;
+    }
+}
+
+int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t rep, uint32_t W, std::vector<uint32_t> &perm,
                   std::vector<uint32_t> &part_off, std::vector<uint32_t> &m, std::vector<uint64_t> &b)
 {
-    if (d == 0 || t == 0 || t > d || W < 2 || (W & (W - 1))) return -1;
+    if (d == 0 || t == 0 || t > d || rep == 0 || (rep > 1 && t > 1) || W < 2 || (W & (W - 1))) return -1;
     SplitMix64 g(seed);
-    perm.resize(d);
-    for (uint32_t i = 0; i < d; ++i) perm[i] = i;
+    const uint32_t D = d * rep;
+    perm.resize(D);
+    for (uint32_t i = 0; i < D; ++i) perm[i] = i % d;
     if (t > 1) shuffle(g, perm);
     part_off.resize(t + 1);
-    for (uint32_t k = 0; k < t; ++k) part_off[k] = k * (d / t);
-    part_off[t] = d;
-    m.assign(d, 0);
-    b.assign(d, 0);
+    for (uint32_t k = 0; k < t; ++k) part_off[k] = k * (D / t);
+    part_off[t] = D;
+    m.assign(D, 0);
+    b.assign(D, 0);
     std::vector<uint32_t> sigma(W);
     for (uint32_t k = 0; k < t; ++k) {
         const uint32_t lo = part_off[k], dk = part_off[k + 1] - lo;
@@ -93,7 +128,7 @@ int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t W, std::vector
     return 0;
 }
 
-void column_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
+void column_lists(uint32_t D, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
                   const std::vector<uint32_t> &part_off, const std::vector<uint32_t> &m,
                   const std::vector<uint64_t> &b, std::vector<uint32_t> &col_off,
                   std::vector<uint32_t> &coord, std::vector<uint64_t> &bval)
@@ -101,8 +136,8 @@ void column_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t
     // Counting sort of the permuted positions of each part by their column m(i);
     // stable, so a column lists its positions in increasing order.
     col_off.assign((size_t)t * (W + 1), 0);
-    coord.assign(d, 0);
-    bval.assign(d, 0);
+    coord.assign(D, 0);
+    bval.assign(D, 0);
     for (uint32_t k = 0; k < t; ++k) {
         uint32_t *off = col_off.data() + (size_t)k * (W + 1);
         const uint32_t lo = part_off[k], hi = part_off[k + 1];

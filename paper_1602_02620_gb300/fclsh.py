@@ -30,14 +30,15 @@ class FclshError(RuntimeError):
 class BuildOpts(ctypes.Structure):
     _fields_ = [("t", ctypes.c_uint32), ("slot_bits", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
                 ("perm", ctypes.c_void_p), ("part_off", ctypes.c_void_p), ("m", ctypes.c_void_p), ("b", ctypes.c_void_p),
-                ("timing", ctypes.c_uint32), ("hash_tile", ctypes.c_uint32)]
+                ("timing", ctypes.c_uint32), ("hash_tile", ctypes.c_uint32), ("replicate", ctypes.c_uint32),
+                ("approx_c", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("d", ctypes.c_uint32), ("words", ctypes.c_uint32), ("r", ctypes.c_uint32),
                 ("t", ctypes.c_uint32), ("rp", ctypes.c_uint32), ("W", ctypes.c_uint32), ("T", ctypes.c_uint32),
                 ("slot_bits", ctypes.c_uint32), ("P", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("rep", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -224,11 +225,12 @@ class Index:
 
     # -- parameters / diagnostics
     def params(self):
-        d, t = self.d, self.t
-        perm = np.zeros(d, np.uint32)
+        """(perm, part_off, m, b) over the D = d * rep positions of the (replicated) vector."""
+        D, t = self.d * self.rep, self.t
+        perm = np.zeros(D, np.uint32)
         part_off = np.zeros(t + 1, np.uint32)
-        m = np.zeros(d, np.uint32)
-        b = np.zeros(d, np.uint64)
+        m = np.zeros(D, np.uint32)
+        b = np.zeros(D, np.uint64)
         _check(lib().fclsh_get_params(self.handle, _ptr(perm), _ptr(part_off), _ptr(m), _ptr(b)))
         return perm, part_off, m, b
 
@@ -363,13 +365,17 @@ class Server:
 
 def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: int | None = None,
           mem_budget: int | None = None, perm=None, part_off=None, m=None, b=None, timing: bool = False,
-          hash_tile: int = 0) -> Index:
+          hash_tile: int = 0, replicate: int = 0, approx_c: float = 0.0) -> Index:
     """fclsh_build on host (numpy) or device (torch CUDA) points [n][ceil(d/64)] uint64.
 
-    hash_tile selects the hash kernel's WHT tile (0 default, 1 twice as many points);
-    fclsh_autotune reports the faster one as tuning()["hash_tile"]."""
+    hash_tile selects the hash kernel (0 default WHT tile, 1 twice as many points, 2 the
+    tensor-core contraction); fclsh_autotune reports the fastest as tuning()["hash_tile"].
+    replicate repeats every vector that many times (Algorithm 1, cr < log n); approx_c > 0
+    with neither t nor replicate set chooses both by Algorithm 1."""
     o = BuildOpts()
     o.t = t or 0
+    o.replicate = replicate or 0
+    o.approx_c = float(approx_c)
     o.slot_bits = slot_bits or 0
     o.mem_budget = mem_budget or 0
     o.timing = 1 if timing else 0
