@@ -71,7 +71,10 @@ typedef struct {
     uint32_t hash_tile;       /* the hash kernel, speed only (same keys): 0 = Algorithm 2 with the default WHT
                                  tile, 1 = twice the points per tile where it fits (W <= 1024), 2 = the
                                  O(dL) route as an exact tensor-core contraction (W >= 64, parts of at most
-                                 128 coordinates) */
+                                 128 coordinates), 3 = Algorithm 2 with the sketch built by scattering each
+                                 point's set bits (O(nnz) per part, Sec. 3.2; any d, while no code column
+                                 of a part holds more than 16,383 positions).  0 and 1 stage the part's
+                                 column lists in shared memory; a build whose lists do not fit takes 3. */
     uint32_t replicate;       /* Algorithm 1's replication for cr < log n: every point and query is repeated
                                  this many times (0 or 1 = none; needs t <= 1).  The index then covers
                                  radius r * replicate of the repeated vectors: W = 2^(r*replicate + 1),
@@ -122,7 +125,7 @@ typedef struct {
     uint32_t inline_probe;    /* probe fan-out: a bucket range up to this length is walked by the lane that
                                  probed it, a longer one by the whole warp (1..32) */
     uint32_t use_graph;       /* capture a batch's launches into a CUDA graph and replay it */
-    uint32_t hash_tile;       /* hash kernel of fclsh_hash and of later builds (fclsh_build_opts.hash_tile): 0, 1, 2 */
+    uint32_t hash_tile;       /* hash kernel of fclsh_hash and of later builds (fclsh_build_opts.hash_tile): 0..3 */
     uint32_t probe_rows;      /* 0: a query probes all T tables (Strategy 2, Sec. 2.2).  1: a query of radius
                                  rho probes only the code rows v = 1 .. 2^(floor(rho*rep/t)+1) - 1 of each
                                  part; the ids are the same (pigeonhole over the parts, Sec. 3.1, or the
@@ -140,7 +143,8 @@ typedef struct {
  * hash functions"), and group the points of each table into buckets by key
  * (Sec. 2.2: only non-empty buckets are stored).
  *   points: host or device, [n][ceil(d/64)] uint64, copied (caller keeps ownership).
- *   n: 1 .. 2^32-1.  d: >= 1.  r: build radius, 0 .. 63, with floor(r/t) <= 10.
+ *   n: 1 .. 2^32-1.  d: 1 .. 262,144; bits past d in a point's last word must be 0.
+ *   r: build radius, 0 .. 63, with floor(r*replicate/t) <= 10.
  *   opts: NULL for defaults.  out: receives the index; NULL on failure.
  * Errors: FCLSH_EINVAL (bad sizes or options), FCLSH_ENOMEM, FCLSH_ECUDA.
  * Synchronous: returns once the index is complete.
@@ -215,7 +219,7 @@ fclsh_status fclsh_query_plain(fclsh_index *idx, const uint64_t *queries, uint64
 /*
  * Linear scan on the GPU: every point within `radius` of each query by XOR +
  * popcount over all n points (the ground truth of Sec. 4.2), independent of the
- * tables.  Any radius is allowed.  Synchronous.
+ * tables.  Any radius is allowed; d <= 3,072 (FCLSH_EINVAL beyond).  Synchronous.
  */
 fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
                               void *stream, fclsh_result **out);
@@ -232,7 +236,7 @@ fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_
  *   results (it may exceed cap), #Collisions, #Candidates.
  * All scratch lives in one fixed device array of about 1.1 MB that every GPU
  * loading the library holds until the process exits, so the call supports
- * indexes of at most 4,194,304 points and 4,094 tables (d <= 16384) and rejects
+ * indexes of at most 4,194,304 points, 4,094 tables and d <= 16,384, and rejects
  * larger ones with FCLSH_EINVAL.  It allocates nothing: no cudaMalloc, cudaFree
  * or allocating library routine.  The first call on a device looks up the
  * array's device address (make that first call before any stream capture).

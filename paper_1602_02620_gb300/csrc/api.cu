@@ -546,7 +546,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     *out = nullptr;
     if (!points) return fail(FCLSH_EINVAL, "points is NULL");
     if (n == 0 || n > 0xFFFFFFFFULL - 1) return fail(FCLSH_EINVAL, "n must be in 1..2^32-2 (got %llu)", (unsigned long long)n);
-    if (d == 0 || d > 16384) return fail(FCLSH_EINVAL, "d must be in 1..16384 (got %u)", d);
+    if (d == 0 || d > kMaxD) return fail(FCLSH_EINVAL, "d must be in 1..%u (got %u)", kMaxD, d);
     fclsh_build_opts o{};
     if (opts) o = *opts;
     if (!(o.approx_c >= 0.0)) return fail(FCLSH_EINVAL, "approx_c must be >= 0");
@@ -578,7 +578,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->rp = rp;
     idx->W = W;
     idx->T = t * (W - 1);
-    if (o.hash_tile > 2) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1 or 2");
+    if (o.hash_tile > 3) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1, 2 or 3");
     idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0};
     idx->timing = o.timing != 0;
 
@@ -611,9 +611,23 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->mma_k = hash_mma_k(W, max_dk);
     if (o.hash_tile == 2 && !idx->mma_k)
         return fail(FCLSH_EINVAL, "hash_tile 2 (tensor cores) needs W >= 64 and parts of at most 128 coordinates");
-    if (hash_smem_bytes(W, max_dk, o.hash_tile) > idx->smem_optin)
-        return fail(FCLSH_EINVAL, "a part of %u coordinates with W = %u does not fit the hash kernel's shared memory",
-                    max_dk, W);
+    // coordinate lists of the scatter sketch (hash_tile 3)
+    std::vector<uint32_t> sc_off, sc_col;
+    std::vector<uint64_t> sc_bv;
+    coord_lists(d, t, W, idx->perm, idx->part_off, idx->m, idx->b, sc_off, sc_col, sc_bv, &idx->sc_pop);
+    const bool scatter_fits = idx->sc_pop <= kScatterMaxPop;
+    if (o.hash_tile < 2 && hash_smem_bytes(W, max_dk, o.hash_tile) > idx->smem_optin) {
+        // the part's column lists do not fit in shared memory: sketch by scattering set bits
+        if (!scatter_fits)
+            return fail(FCLSH_EINVAL,
+                        "a part of %u positions with W = %u fits neither the hash kernel's shared memory nor the "
+                        "scatter sketch (a column holds %u > %u positions)",
+                        max_dk, W, idx->sc_pop, kScatterMaxPop);
+        idx->tune.hash_tile = 3;
+    }
+    if (o.hash_tile == 3 && !scatter_fits)
+        return fail(FCLSH_EINVAL, "hash_tile 3 (scatter sketch) needs at most %u positions per column (have %u)",
+                    kScatterMaxPop, idx->sc_pop);
 
     uint32_t sb = o.slot_bits;
     if (!sb) {
@@ -640,14 +654,28 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->col_b = dblock;
     idx->col_off = reinterpret_cast<uint32_t *>(dblock + bval.size());
     idx->col_coord = idx->col_off + col_off.size();
+    std::vector<uint64_t> sblock;
+    if (scatter_fits) {   // b values, then offsets, then columns
+        sblock.assign(sc_bv.size() + (sc_off.size() + sc_col.size() + 1) / 2, 0);
+        std::memcpy(sblock.data(), sc_bv.data(), sc_bv.size() * 8);
+        std::memcpy(reinterpret_cast<uint32_t *>(sblock.data() + sc_bv.size()), sc_off.data(), sc_off.size() * 4);
+        std::memcpy(reinterpret_cast<uint32_t *>(sblock.data() + sc_bv.size()) + sc_off.size(), sc_col.data(),
+                    sc_col.size() * 4);
+        uint64_t *sdev = nullptr;
+        if ((e = keep.alloc(&sdev, sblock.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(coordinate lists)");
+        idx->sc_b = sdev;
+        idx->sc_off = reinterpret_cast<uint32_t *>(sdev + sc_bv.size());
+        idx->sc_col = idx->sc_off + sc_off.size();
+    }
     if ((e = keep.alloc(&idx->offs, (size_t)idx->T * idx->offs_stride())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(directory)");
     if ((e = keep.alloc(&idx->ent, (size_t)idx->T * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(entries)");
-    idx->device_bytes = n * idx->words * 8 + col_off.size() * 4 + coord.size() * 12 +
+    idx->device_bytes = n * idx->words * 8 + col_off.size() * 4 + coord.size() * 12 + sblock.size() * 8 +
                         (uint64_t)idx->T * idx->offs_stride() * 4 + (uint64_t)idx->T * n * 8;
 
     cudaStream_t s = nullptr;
     FCLSH_CUDA(cudaMemcpyAsync(idx->points, points, n * idx->words * 8, cudaMemcpyDefault, s));
     FCLSH_CUDA(cudaMemcpyAsync(dblock, block.data(), block.size() * 8, cudaMemcpyHostToDevice, s));
+    if (idx->sc_b) FCLSH_CUDA(cudaMemcpyAsync(idx->sc_b, sblock.data(), sblock.size() * 8, cudaMemcpyHostToDevice, s));
     if ((e = keep.alloc(&idx->status, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
     FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
     if (o.hash_tile == 2) {
@@ -758,7 +786,8 @@ extern "C" void fclsh_free(fclsh_index *idx)
     cudaSetDevice(idx->device);
     cudaDeviceSynchronize();
     drop_timers(idx);
-    void *ps[] = {idx->points, idx->col_b /* the column-list block */, idx->offs, idx->ent, idx->mma_coord, idx->mma_g,
+    void *ps[] = {idx->points, idx->col_b /* the column-list block */, idx->sc_b /* the coordinate-list block */,
+                  idx->offs, idx->ent, idx->mma_coord, idx->mma_g,
                   idx->status};
     for (void *p : ps)
         if (p) dev_free(p);
@@ -1251,7 +1280,10 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     if (t->hash_set_log2 < 10 || t->hash_set_log2 > 13) return fail(FCLSH_EINVAL, "hash_set_log2 must be in 10..13");
     if (t->inline_probe < 1 || t->inline_probe > 32) return fail(FCLSH_EINVAL, "inline_probe must be in 1..32");
     if (t->query_ctas_per_sm < 1 || t->query_ctas_per_sm > 16) return fail(FCLSH_EINVAL, "query_ctas_per_sm must be in 1..16");
-    if (t->hash_tile > 2) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1 or 2");
+    if (t->hash_tile > 3) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1, 2 or 3");
+    if (t->hash_tile == 3 && !idx->scatter_ok())
+        return fail(FCLSH_EINVAL, "hash_tile 3 (scatter sketch) needs at most %u positions per column (have %u)",
+                    kScatterMaxPop, idx->sc_pop);
     if (t->hash_tile == 2) {
         fclsh_status st = ensure_mma_operands(idx, nullptr);
         if (st != FCLSH_OK) return st;
@@ -1259,7 +1291,7 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
     uint32_t max_dk = 0;
     for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
-    if (hash_smem_bytes(idx->W, max_dk, t->hash_tile) > idx->smem_optin)
+    if (t->hash_tile != 2 && hash_smem_bytes(idx->W, max_dk, t->hash_tile) > idx->smem_optin)
         return fail(FCLSH_EINVAL, "the hash tile does not fit in shared memory");
     idx->tune = *t;
     return FCLSH_OK;
@@ -1436,9 +1468,10 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
         uint64_t *kbuf = nullptr;
         if (dev_alloc((void **)&kbuf, cnt * L * 8) == cudaSuccess) {
             float best_h = 1e30f;
-            for (uint32_t tl = 0; tl <= 2; ++tl) {
-                if (tl < 2 && hash_smem_bytes(idx->W, max_dk, tl) > idx->smem_optin) continue;
+            for (uint32_t tl = 0; tl <= 3; ++tl) {
+                if (tl != 2 && hash_smem_bytes(idx->W, max_dk, tl) > idx->smem_optin) continue;
                 if (tl == 2 && (!idx->mma_k || ensure_mma_operands(idx, s) != FCLSH_OK)) continue;
+                if (tl == 3 && !idx->scatter_ok()) continue;
                 idx->tune.hash_tile = tl;
                 if (launch_hash_part(idx, 0, idx->points, cnt, kbuf, cnt, s) != cudaSuccess) continue;
                 cudaEventRecord(e0, s);

@@ -16,6 +16,11 @@ namespace fclsh {
 constexpr uint64_t kP = (1ULL << 50) - 27;
 constexpr uint64_t kMask50 = (1ULL << 50) - 1;
 constexpr int kMaxLogW = 11;          // W = 2^(r'+1) <= 2048
+constexpr uint32_t kMaxD = 262144;    // bits per point
+constexpr uint32_t kPackedMaxD = 16384;   // coordinates the packed specific-construction gather can name (14 bits)
+// The scatter sketch adds b values (< 2^50) of one column into 64 bits without
+// reducing: exact while a column of a part holds at most this many positions.
+constexpr uint32_t kScatterMaxPop = 16383;
 constexpr int kSortTile = 8192;       // radix-sort items per histogram tile (one block)
 constexpr int kSortSub = 2048;        // items per scatter sub-tile (256 threads x 8)
 constexpr int kSortThreads = 256;
@@ -52,6 +57,16 @@ struct PartCols {
     const uint32_t *col_off;    // [W+1], absolute offsets into coord/bval
     const uint32_t *coord;      // coordinate (bit index into the point)
     const uint64_t *bval;       // b_i in [0, P)
+};
+
+// Coordinate lists of one part for the scatter sketch: the positions of the part
+// that read coordinate c are entries off[c] .. off[c+1], each with its code column
+// col[e] and seed value b[e] (absolute entry indexes).
+struct CoordLists {
+    const uint32_t *off;        // [d+1]
+    const uint32_t *col;
+    const uint64_t *b;
+    uint32_t d;                 // bits of a point; set bits past d are ignored
 };
 
 struct PhaseTimer;
@@ -123,6 +138,11 @@ struct fclsh_index {
     uint32_t *col_off = nullptr;     // [t][W+1]  (col_b, col_off, col_coord: one allocation, owned via col_b)
     uint32_t *col_coord = nullptr;   // [D]
     uint64_t *col_b = nullptr;       // [D]
+    // coordinate lists of the scatter sketch (hash_tile 3): sc_off [t][d+1], sc_col [D],
+    // sc_b [D] (one allocation, owned via sc_b); sc_pop = the fullest column of any part
+    uint32_t *sc_off = nullptr, *sc_col = nullptr;
+    uint64_t *sc_b = nullptr;
+    uint32_t sc_pop = 0;
     uint32_t *offs = nullptr;        // [T][dir_stride(slot_bits)]: 2^slot_bits + 1 used
     uint64_t *ent = nullptr;         // [T][n]: (key >> slot_bits) << 32 | id
     // tensor-core hash (hash_tile 2): padded coordinates per part, their lists [t][mma_k]
@@ -147,6 +167,11 @@ struct fclsh_index {
     {
         return fclsh::PartCols{col_off + (size_t)k * (W + 1), col_coord, col_b};
     }
+    fclsh::CoordLists coords(uint32_t k) const
+    {
+        return fclsh::CoordLists{sc_off + (size_t)k * (d + 1), sc_col, sc_b, d};
+    }
+    bool scatter_ok() const { return sc_b != nullptr && sc_pop <= fclsh::kScatterMaxPop; }
 };
 
 namespace fclsh {
@@ -169,6 +194,10 @@ uint32_t default_parts(uint32_t r);
 void algorithm1_rule(uint64_t n, uint32_t r, double c, uint32_t *t, uint32_t *rep);
 int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t rep, uint32_t W, std::vector<uint32_t> &perm,
                   std::vector<uint32_t> &part_off, std::vector<uint32_t> &m, std::vector<uint64_t> &b);
+void coord_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
+                 const std::vector<uint32_t> &part_off, const std::vector<uint32_t> &m,
+                 const std::vector<uint64_t> &b, std::vector<uint32_t> &off, std::vector<uint32_t> &col,
+                 std::vector<uint64_t> &bval, uint32_t *max_pop);
 void column_lists(uint32_t D, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
                   const std::vector<uint32_t> &part_off, const std::vector<uint32_t> &m,
                   const std::vector<uint64_t> &b, std::vector<uint32_t> &col_off,

@@ -85,7 +85,7 @@ __host__ __device__ constexpr size_t cols_smem_bytes(uint32_t W, uint32_t dk)
 // column holds at most one coordinate, packed with its seed value as
 // b | coord << 50 (b = 0 for an empty column): PACKED_REG keeps the point's
 // words in registers (d <= 256), PACKED_LDG reads them through L1.
-enum GatherMode { GENERAL = 0, PACKED_REG = 1, PACKED_LDG = 2 };
+enum GatherMode { GENERAL = 0, PACKED_REG = 1, PACKED_LDG = 2, SCATTER = 3 };
 
 __device__ __forceinline__ const uint64_t *stage_packed(const PartCols &pc, uint32_t W, void *smem_base)
 {
@@ -134,6 +134,55 @@ __global__ void __launch_bounds__(128) hash_small_kernel(const uint64_t *__restr
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         v[j] = sketch_column(cols, j, x);
+        S += v[j];
+    }
+    wht_regs<W>(v);
+#pragma unroll
+    for (int j = 1; j < W; ++j) keys[(uint64_t)(j - 1) * ld + i] = finish_key(S, v[j]);
+}
+
+// W <= 32 with the scatter sketch (hash_tile 3, or parts too long for staged
+// column lists): 128 points per block, sketch [j][p] in shared memory.  Warp w
+// walks the words of its 32 points (a lane a word), and each set coordinate adds
+// the seed values of its positions to their columns; then thread p transforms its
+// point's sketch in registers.  Sums stay below 2^64 while no column of the part
+// holds more than 16,383 positions (checked by the host).
+template <int LOGW>
+__global__ void __launch_bounds__(128, 4) hash_small_scatter_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
+                                                                 uint32_t words, CoordLists cl,
+                                                                 uint64_t *__restrict__ keys, uint64_t ld)
+{
+    constexpr int W = 1 << LOGW, NP = 128;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem_raw);   // [W][NP]
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(W * NP); i += NP) sk[i] = 0ULL;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t p0 = blockIdx.x * (uint64_t)NP;
+    for (uint32_t pi = 0; pi < 32; ++pi) {
+        const uint32_t p = warp * 32 + pi;
+        if (p0 + p >= cnt) break;
+        const uint64_t *x = pts + (p0 + p) * words;
+        for (uint32_t w = lane; w < words; w += 32) {
+            uint64_t bits = __ldg(x + w);
+            if (w == words - 1 && (cl.d & 63)) bits &= (1ULL << (cl.d & 63)) - 1;   // coordinates < d only
+            while (bits) {
+                const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
+                bits &= bits - 1;
+                const uint32_t e1 = __ldg(cl.off + c + 1);
+                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
+                    atomicAdd(sk + (size_t)__ldg(cl.col + e) * NP + p, (unsigned long long)__ldg(cl.b + e));
+            }
+        }
+    }
+    __syncwarp();
+    const uint64_t i = p0 + threadIdx.x;
+    if (i >= cnt) return;
+    uint64_t v[W];
+    uint64_t S = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        v[j] = mod_p(sk[(size_t)j * NP + threadIdx.x]);
         S += v[j];
     }
     wht_regs<W>(v);
@@ -213,7 +262,9 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
             const uint32_t j = jidx<LO, B>(other, k);
             if (MODE == 0) {
                 uint64_t tj;
-                if (GM == GENERAL) {
+                if (GM == SCATTER) {
+                    tj = mod_p(sm[slot<T::NP, T::M>(j, p)]);
+                } else if (GM == GENERAL) {
                     tj = valid ? sketch_column(cols, j, x) : 0;
                 } else {
                     const uint64_t pj = pk[j];
@@ -253,9 +304,36 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
     }
 }
 
+// The tile's sketch by scattering (SCATTER mode): zero the values, then every
+// thread takes (point, word) items, p-major so that a warp reads consecutive words
+// of one point, and adds the seed values of each set coordinate's positions to
+// their columns with shared-memory atomics.
+template <int NP, uint32_t M>
+__device__ __forceinline__ void scatter_sketch(uint64_t *sm, uint32_t W, const uint64_t *__restrict__ pts,
+                                               uint64_t cnt, uint32_t words, uint64_t p0, const CoordLists &cl)
+{
+    for (uint32_t i = threadIdx.x; i < W * (uint32_t)NP; i += blockDim.x) sm[i] = 0ULL;
+    __syncthreads();
+    const uint32_t items = (uint32_t)NP * words;
+    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+        const uint32_t p = it / words, w = it - p * words;
+        if (p0 + p >= cnt) break;   // items are p-major: later items of this thread are later points
+        uint64_t bits = __ldg(pts + (p0 + p) * words + w);
+        if (w == words - 1 && (cl.d & 63)) bits &= (1ULL << (cl.d & 63)) - 1;   // coordinates < d only
+        while (bits) {
+            const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
+            bits &= bits - 1;
+            const uint32_t e1 = __ldg(cl.off + c + 1);
+            for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
+                atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(__ldg(cl.col + e), p)),
+                          (unsigned long long)__ldg(cl.b + e));
+        }
+    }
+}
+
 template <int LOGW, int NP, int GM>
 __global__ void __launch_bounds__(Tile<LOGW, NP>::NT, Tile<LOGW, NP>::MINB) hash_tile_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
-                                                                    uint32_t words, PartCols pc,
+                                                                    uint32_t words, PartCols pc, CoordLists cl,
                                                                     uint64_t *__restrict__ keys, uint64_t ld)
 {
     using T = Tile<LOGW, NP>;
@@ -265,7 +343,9 @@ __global__ void __launch_bounds__(Tile<LOGW, NP>::NT, Tile<LOGW, NP>::MINB) hash
     unsigned long long *S_acc = reinterpret_cast<unsigned long long *>(sm + (size_t)T::W * T::NP);
     ColsSmem cols{};
     const uint64_t *pk = nullptr;
-    if (GM == GENERAL)
+    if (GM == SCATTER)
+        scatter_sketch<T::NP, T::M>(sm, T::W, pts, cnt, words, blockIdx.x * (uint64_t)T::NP, cl);
+    else if (GM == GENERAL)
         cols = stage_cols(pc, T::W, S_acc + T::NP);
     else
         pk = stage_packed(pc, T::W, S_acc + T::NP);
@@ -295,8 +375,8 @@ __global__ void __launch_bounds__(Tile<LOGW, NP>::NT, Tile<LOGW, NP>::MINB) hash
 }
 
 template <int LOGW, int NP, int GM>
-cudaError_t launch_tile(size_t cbytes, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, uint64_t *keys,
-                        uint64_t ld, cudaStream_t s)
+cudaError_t launch_tile(size_t cbytes, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, CoordLists cl,
+                        uint64_t *keys, uint64_t ld, cudaStream_t s)
 {
     using T = Tile<LOGW, NP>;
     const size_t smem = T::VALUES_BYTES + T::NP * 8 + cbytes;
@@ -306,27 +386,38 @@ cudaError_t launch_tile(size_t cbytes, const uint64_t *pts, uint64_t cnt, uint32
         if (e != cudaSuccess) return e;
     }
     const uint64_t blocks = (cnt + T::NP - 1) / T::NP;
-    kern<<<(unsigned)blocks, T::NT, smem, s>>>(pts, cnt, words, pc, keys, ld);
+    kern<<<(unsigned)blocks, T::NT, smem, s>>>(pts, cnt, words, pc, cl, keys, ld);
     note_launch();
     return cudaGetLastError();
 }
 
 template <int LOGW, int NP>
-cudaError_t launch_gather(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, uint64_t *keys,
-                          uint64_t ld, cudaStream_t s)
+cudaError_t launch_gather(uint32_t dk, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc, CoordLists cl,
+                          uint64_t *keys, uint64_t ld, cudaStream_t s)
 {
     constexpr int W = 1 << LOGW;
-    if (dk > (uint32_t)W)   // general construction: column lists
-        return launch_tile<LOGW, NP, GENERAL>(cols_smem_bytes(W, dk), pts, cnt, words, pc, keys, ld, s);
-    if (words <= 4) return launch_tile<LOGW, NP, PACKED_REG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
-    return launch_tile<LOGW, NP, PACKED_LDG>((size_t)W * 8, pts, cnt, words, pc, keys, ld, s);
+    if (dk > (uint32_t)W || words * 64u > kPackedMaxD)   // column lists (general construction, or coordinates past 14 bits)
+        return launch_tile<LOGW, NP, GENERAL>(cols_smem_bytes(W, dk), pts, cnt, words, pc, cl, keys, ld, s);
+    if (words <= 4) return launch_tile<LOGW, NP, PACKED_REG>((size_t)W * 8, pts, cnt, words, pc, cl, keys, ld, s);
+    return launch_tile<LOGW, NP, PACKED_LDG>((size_t)W * 8, pts, cnt, words, pc, cl, keys, ld, s);
 }
 
 template <int LOGW>
 cudaError_t launch_logw(uint32_t dk, uint32_t tile, const uint64_t *pts, uint64_t cnt, uint32_t words, PartCols pc,
-                        uint64_t *keys, uint64_t ld, cudaStream_t s)
+                        CoordLists cl, uint64_t *keys, uint64_t ld, cudaStream_t s)
 {
     constexpr int W = 1 << LOGW;
+    if (tile == 3) {   // scatter sketch
+        if constexpr (LOGW <= 5) {
+            const size_t smem = (size_t)W * 128 * 8;
+            hash_small_scatter_kernel<LOGW><<<(unsigned)((cnt + 127) / 128), 128, smem, s>>>(pts, cnt, words, cl,
+                                                                                                keys, ld);
+            note_launch();
+            return cudaGetLastError();
+        } else {
+            return launch_tile<LOGW, tile_points<LOGW>(0), SCATTER>(0, pts, cnt, words, pc, cl, keys, ld, s);
+        }
+    }
     if constexpr (LOGW <= 5) {
         const size_t smem = cols_smem_bytes(W, dk);
         const int threads = 128;
@@ -342,8 +433,8 @@ cudaError_t launch_logw(uint32_t dk, uint32_t tile, const uint64_t *pts, uint64_
     } else {
         (void)W;
         constexpr int np0 = tile_points<LOGW>(0), np1 = tile_points<LOGW>(1);
-        if (tile == 1 && np1 != np0) return launch_gather<LOGW, np1>(dk, pts, cnt, words, pc, keys, ld, s);
-        return launch_gather<LOGW, np0>(dk, pts, cnt, words, pc, keys, ld, s);
+        if (tile == 1 && np1 != np0) return launch_gather<LOGW, np1>(dk, pts, cnt, words, pc, cl, keys, ld, s);
+        return launch_gather<LOGW, np0>(dk, pts, cnt, words, pc, cl, keys, ld, s);
     }
 }
 
@@ -357,9 +448,10 @@ size_t tile_smem(uint32_t tile)
 }
 
 // Shared memory one hash block needs for code length W, a part of dk coordinates
-// and the tile choice.
+// and the tile choice (3: the scatter sketch, which stages no column lists).
 size_t hash_smem_bytes(uint32_t W, uint32_t dk, uint32_t tile)
 {
+    if (tile == 3) return W <= 32 ? (size_t)W * 128 * 8 : hash_smem_bytes(W, 0, 0) - cols_smem_bytes(W, 0);
     size_t t = 0;
     switch (W) {
     case 64: t = tile_smem<6>(tile); break;
@@ -387,18 +479,20 @@ cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t 
     }
     const uint32_t logw = idx->rp + 1;
     const uint32_t tl = idx->tune.hash_tile;
+    if (tl == 3 && !idx->scatter_ok()) return cudaErrorInvalidValue;
+    const CoordLists cl = tl == 3 ? idx->coords(k) : CoordLists{nullptr, nullptr, nullptr, 0};
     switch (logw) {
-    case 1: return launch_logw<1>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 2: return launch_logw<2>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 3: return launch_logw<3>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 4: return launch_logw<4>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 5: return launch_logw<5>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 6: return launch_logw<6>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 7: return launch_logw<7>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 8: return launch_logw<8>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 9: return launch_logw<9>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 10: return launch_logw<10>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
-    case 11: return launch_logw<11>(dk, tl, pts, cnt, idx->words, pc, keys, ld, s);
+    case 1: return launch_logw<1>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 2: return launch_logw<2>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 3: return launch_logw<3>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 4: return launch_logw<4>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 5: return launch_logw<5>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 6: return launch_logw<6>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 7: return launch_logw<7>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 8: return launch_logw<8>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 9: return launch_logw<9>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 10: return launch_logw<10>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
+    case 11: return launch_logw<11>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -158,4 +158,40 @@ void column_lists(uint32_t D, uint32_t t, uint32_t W, const std::vector<uint32_t
     }
 }
 
+void coord_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
+                 const std::vector<uint32_t> &part_off, const std::vector<uint32_t> &m,
+                 const std::vector<uint64_t> &b, std::vector<uint32_t> &off, std::vector<uint32_t> &col,
+                 std::vector<uint64_t> &bval, uint32_t *max_pop)
+{
+    // The same positions as column_lists, grouped by the coordinate they read
+    // (counting sort per part, stable), for a sketch that visits a point's set bits.
+    const uint32_t D = (uint32_t)perm.size();
+    off.assign((size_t)t * (d + 1), 0);
+    col.assign(D, 0);
+    bval.assign(D, 0);
+    uint32_t pop = 0;
+    for (uint32_t k = 0; k < t; ++k) {
+        uint32_t *o = off.data() + (size_t)k * (d + 1);
+        const uint32_t lo = part_off[k], hi = part_off[k + 1];
+        std::vector<uint32_t> cnt(d, 0), colpop(W, 0);
+        for (uint32_t i = lo; i < hi; ++i) {
+            cnt[perm[i]]++;
+            pop = std::max(pop, ++colpop[m[i]]);
+        }
+        uint32_t run = lo;
+        for (uint32_t c = 0; c < d; ++c) {
+            o[c] = run;
+            run += cnt[c];
+        }
+        o[d] = run;
+        std::vector<uint32_t> fill(o, o + d);
+        for (uint32_t i = lo; i < hi; ++i) {
+            const uint32_t at = fill[perm[i]]++;
+            col[at] = m[i];
+            bval[at] = b[i];
+        }
+    }
+    *max_pop = pop;
+}
+
 }  // namespace fclsh

@@ -425,9 +425,10 @@ __global__ void __launch_bounds__(256) gather_runs_kernel(const uint32_t *runs, 
 // ---------------------------------------------------------------- plain path
 
 // One query: every probed table in its own thread, duplicates removed by a global n-bit bitmap.
+// The query's words sit in dynamic shared memory (words * 8 bytes).
 __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uint64_t *keys, uint32_t *bitmap)
 {
-    __shared__ uint64_t q_s[256];
+    extern __shared__ uint64_t q_s[];
     for (uint32_t w = threadIdx.x; w < a.words; w += blockDim.x) q_s[w] = a.queries[w];
     __syncthreads();
     const uint32_t nt = rows_per_part(a, a.radius), j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,7 +568,7 @@ cudaError_t query_batch_occupancy(uint32_t block, size_t smem, int *ctas_per_sm)
 cudaError_t launch_query_plain(const QueryArgs &a, const uint64_t *keys, uint32_t *bitmap, cudaStream_t s)
 {
     const uint32_t blocks = (a.T + 255) / 256;
-    query_plain_kernel<<<blocks, 256, 0, s>>>(a, keys, bitmap);
+    query_plain_kernel<<<blocks, 256, (size_t)a.words * 8, s>>>(a, keys, bitmap);   // <= 32 KB (d <= 262,144)
     note_launch();
     return cudaGetLastError();
 }

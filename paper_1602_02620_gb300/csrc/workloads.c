@@ -12,6 +12,7 @@
  * uniforms u, and a bit is set iff u < thr, thr = round(p * 65536).
  * Points are packed LSB-first: coordinate j is word j/64, bit j%64.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -159,6 +160,38 @@ uint64_t wl_near_duplicates(uint64_t key, uint64_t *pts, uint64_t n, uint32_t d,
         cnt++;
     }
     return cnt;
+}
+
+/* Uniform double in [0, 1) from the top 53 bits of a draw. */
+static inline double unit(uint64_t u) { return (double)(u >> 11) * (1.0 / 9007199254740992.0); }
+
+/*
+ * Sparse high-dimensional points with skewed coordinate popularity (the shape of
+ * bag-of-words and rating vectors): point gi draws its sub-stream key k = U(key, gi),
+ * sets L = min(d/2, lmin + floor(-lmean * ln(1 - u))) coordinates with u = unit(U(k, 0))
+ * (a geometric-like length), each c = floor(d * v^2) with v = unit(U(k, j)), j = 1, 2, ...,
+ * skipping coordinates already set (low coordinates are the popular ones).
+ */
+void wl_sparse_skewed(uint64_t key, uint64_t first, uint64_t n, uint32_t d, uint32_t lmin, uint32_t lmean,
+                      uint64_t *out)
+{
+    uint32_t words = words_of(d);
+    memset(out, 0, sizeof(uint64_t) * n * words);
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t k = U(key, first + i);
+        uint64_t *row = out + i * words;
+        double len = (double)lmin - (double)lmean * log(1.0 - unit(U(k, 0)));
+        uint32_t L = len > (double)(d / 2) ? d / 2 : (uint32_t)len;
+        uint32_t got = 0;
+        for (uint64_t j = 1; got < L; j++) {
+            double v = unit(U(k, j));
+            uint32_t c = (uint32_t)((double)d * v * v);
+            if (c >= d) c = d - 1;
+            if (row[c >> 6] >> (c & 63) & 1ULL) continue;
+            row[c >> 6] |= 1ULL << (c & 63);
+            got++;
+        }
+    }
 }
 
 /* n draws U(key, first + i) (raw 64-bit values, for request streams). */

@@ -7,7 +7,7 @@ their shapes: uniform 128-bit image codes (SIFT-like), clustered 256-bit codes
 (text-like).  This module holds none of the index's arithmetic; the C part
 (``csrc/workloads.c``) only generates bits.
 
-Five workloads (sizes as named):
+Seven workloads (sizes as named):
 
 ====  ==========  =====  ==  =========  ==========================================
 name  n           d      r   queries    data / queries
@@ -17,6 +17,8 @@ name  n           d      r   queries    data / queries
 3     4,000,000   256    16  100,000    4,096 centres, flip p=0.05; queries centre + flip p~U[0.02,0.08]
 4     2,000,000   1,024  20  50,000     density 0.02, 20% near-dups at 1..20; 50% near-dup queries, 50% random
 5     8,000,000   256    16  stream     as 3; requests of U{1..4096} queries, radius in {4,8,12,16}
+6     40,000      28,102 29  1,000      sparse, skewed popularity, ~150 set bits (Enron-like); 10% near-dups
+7     234,834     140,214 13 2,000      sparse, skewed popularity, ~85 set bits (MovieLens-like); 10% near-dups
 ====  ==========  =====  ==  =========  ==========================================
 """
 from __future__ import annotations
@@ -40,7 +42,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -59,6 +61,8 @@ def _lib():
         lib.wl_near_duplicates.argtypes = [u64, vp, u64, u32, u32, u32, u32]
         lib.wl_near_duplicates.restype = u64
         lib.wl_raw.argtypes = [u64, u64, u64, vp]
+        lib.wl_sparse_skewed.argtypes = [u64, u64, u64, u32, u32, u32, vp]
+        lib.wl_sparse_skewed.restype = None
         for f in ("wl_uniform", "wl_bernoulli", "wl_clustered", "wl_planted", "wl_raw"):
             getattr(lib, f).restype = None
         _lib_handle = lib
@@ -89,6 +93,11 @@ CONFIGS = {
     5: dict(name="served-clustered n=8000000 d=256 r=16", n=8_000_000, d=256, r=16, nq=0, seed=5,
             kind="clustered", centres=4096, p_data=0.05, p_query=(0.02, 0.08),
             req_size=(1, 4096), req_radii=(4, 8, 12, 16)),
+    # very high-dimensional sparse sets of the shapes of Enron and MovieLens (Table 2)
+    6: dict(name="highd-enron n=40000 d=28102 r=29", n=40_000, d=28_102, r=29, nq=1_000, seed=6,
+            kind="sparse_skewed", lmin=20, lmean=130, dup_frac=0.1, dup_k=(1, 29), plant=(0, 29)),
+    7: dict(name="highd-movielens n=234834 d=140214 r=13", n=234_834, d=140_214, r=13, nq=2_000, seed=7,
+            kind="sparse_skewed", lmin=15, lmean=70, dup_frac=0.1, dup_k=(1, 13), plant=(0, 13)),
 }
 
 
@@ -144,6 +153,10 @@ def points(cfg_id: int, n: int | None = None) -> np.ndarray:
         lib.wl_bernoulli(_key(seed, S_DATA), 0, n, d, thr16(cfg["density"]), _p(out))
         lo, hi = cfg["dup_k"]
         lib.wl_near_duplicates(_key(seed, S_NEARDUP), _p(out), n, d, thr16(cfg["dup_frac"]), lo, hi)
+    elif cfg["kind"] == "sparse_skewed":
+        lib.wl_sparse_skewed(_key(seed, S_DATA), 0, n, d, cfg["lmin"], cfg["lmean"], _p(out))
+        lo, hi = cfg["dup_k"]
+        lib.wl_near_duplicates(_key(seed, S_NEARDUP), _p(out), n, d, thr16(cfg["dup_frac"]), lo, hi)
     else:
         raise ValueError(cfg["kind"])
     return out
@@ -159,7 +172,7 @@ def queries(cfg_id: int, pts: np.ndarray, nq: int | None = None, first: int = 0)
     meta = {}
     lib = _lib()
     n = pts.shape[0]
-    if cfg["kind"] in ("uniform", "sparse"):
+    if cfg["kind"] in ("uniform", "sparse", "sparse_skewed"):
         # even global query index -> planted near a data point, odd -> fresh random
         idx = np.arange(first, first + nq)
         planted = (idx % 2) == 0
@@ -176,6 +189,9 @@ def queries(cfg_id: int, pts: np.ndarray, nq: int | None = None, first: int = 0)
                 src[i], kk[i] = s[0], k[0]
             elif cfg["kind"] == "uniform":
                 lib.wl_uniform(_key(seed, S_Q_UNIFORM), g // 2, 1, d, _p(out[i:i + 1]))
+            elif cfg["kind"] == "sparse_skewed":
+                lib.wl_sparse_skewed(_key(seed, S_Q_UNIFORM), g // 2, 1, d, cfg["lmin"], cfg["lmean"],
+                                     _p(out[i:i + 1]))
             else:
                 lib.wl_bernoulli(_key(seed, S_Q_UNIFORM), g // 2, 1, d, thr16(cfg["density"]), _p(out[i:i + 1]))
         meta.update(planted=planted, src=src, k=kk)

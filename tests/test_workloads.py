@@ -58,3 +58,23 @@ def test_request_stream():
     assert 0.3 < t[-1] / 0.5 < 3.0
     assert {r[2] for r in reqs} <= {4, 8, 12, 16}
     assert all(1 <= r[1] <= 4096 for r in reqs)
+
+
+def test_sparse_skewed_highd():
+    """The Enron- and MovieLens-shaped sets: d bits, ~lmin + lmean set bits, low coordinates
+    popular, near-duplicate planted queries at the stated distances, prefix-stable."""
+    for cfg, mean_lo, mean_hi in ((6, 120, 175), (7, 65, 105)):
+        c = wl.CONFIGS[cfg]
+        pts = wl.points(cfg, 3000)
+        assert pts.shape == (3000, (c["d"] + 63) // 64)
+        assert np.array_equal(wl.points(cfg, 500), pts[:500])
+        nnz = _popcount_rows(pts[:600])
+        assert mean_lo < nnz.mean() < mean_hi and nnz.min() >= c["lmin"]
+        last = pts[:, -1]
+        assert not np.any(last >> np.uint64(c["d"] % 64)) if c["d"] % 64 else True   # no bit past d
+        bits = np.unpackbits(pts[:600].view(np.uint8), axis=1, bitorder="little")[:, : c["d"]]
+        lowq, highq = bits[:, : c["d"] // 4].sum(), bits[:, 3 * c["d"] // 4:].sum()
+        assert lowq > 2.5 * highq                               # density ~ 1/sqrt(c): skewed to low c
+        q, meta = wl.queries(cfg, pts, 30)
+        for i in np.nonzero(meta["planted"])[0]:
+            assert oracle.hamming(pts[meta["src"][i]], q[i]) == meta["k"][i] <= c["r"]
