@@ -392,6 +392,12 @@ static QueryArgs make_args(fclsh_index *idx)
     a.inline_len = idx->tune.inline_probe;
     a.probe_rows = idx->tune.probe_rows;
     a.rep = idx->rep;
+    a.d = idx->d;
+    // long parts: the query's sketch from its set bits (O(nnz)) rather than from every position
+    a.s1_scatter = idx->scatter_ok() && idx->positions() / idx->t >= kS1ScatterPositions;
+    a.sc_off = idx->sc_off;
+    a.sc_col = idx->sc_col;
+    a.sc_b = idx->sc_b;
     a.col_off = idx->col_off;
     a.col_coord = idx->col_coord;
     a.col_b = idx->col_b;

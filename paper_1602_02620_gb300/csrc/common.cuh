@@ -21,6 +21,8 @@ constexpr uint32_t kPackedMaxD = 16384;   // coordinates the packed specific-con
 // The scatter sketch adds b values (< 2^50) of one column into 64 bits without
 // reducing: exact while a column of a part holds at most this many positions.
 constexpr uint32_t kScatterMaxPop = 16383;
+constexpr uint32_t kS1ScatterPositions = 2048;   // parts at least this long: query sketch by scatter
+constexpr uint32_t kWarpVerifyWords = 32;        // points of at least this many words: one warp per distance
 constexpr int kSortTile = 8192;       // radix-sort items per histogram tile (one block)
 constexpr int kSortSub = 2048;        // items per scatter sub-tile (256 threads x 8)
 constexpr int kSortThreads = 256;
@@ -78,6 +80,12 @@ struct QueryArgs {
     uint32_t words, t, W, T, slot_bits, hset_log2, inline_len;
     uint32_t probe_rows;          // 1: probe only the code rows v < 2^(floor(radius*rep/t)+1) of each part
     uint32_t rep;                 // replication factor of Algorithm 1 (1 = none)
+    uint32_t d;                   // bits per point
+    // S1 by scattering the query's set bits through the coordinate lists (long parts),
+    // else by walking the column lists
+    uint32_t s1_scatter;
+    const uint32_t *sc_off, *sc_col;
+    const uint64_t *sc_b;
     const uint32_t *col_off, *col_coord;
     const uint64_t *col_b;
     const uint32_t *offs;

@@ -163,15 +163,22 @@ __global__ void __launch_bounds__(128, 4) hash_small_scatter_kernel(const uint64
         const uint32_t p = warp * 32 + pi;
         if (p0 + p >= cnt) break;
         const uint64_t *x = pts + (p0 + p) * words;
-        for (uint32_t w = lane; w < words; w += 32) {
-            uint64_t bits = __ldg(x + w);
-            if (w == words - 1 && (cl.d & 63)) bits &= (1ULL << (cl.d & 63)) - 1;   // coordinates < d only
-            while (bits) {
-                const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
-                bits &= bits - 1;
-                const uint32_t e1 = __ldg(cl.off + c + 1);
-                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
-                    atomicAdd(sk + (size_t)__ldg(cl.col + e) * NP + p, (unsigned long long)__ldg(cl.b + e));
+        for (uint32_t w0 = lane; w0 < words; w0 += 128) {   // four words in flight per lane
+            uint64_t wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wv[u] = w0 + 32 * u < words ? __ldg(x + w0 + 32 * u) : 0ULL;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t w = w0 + 32 * u;
+                uint64_t bits = wv[u];
+                if (w == words - 1 && (cl.d & 63)) bits &= (1ULL << (cl.d & 63)) - 1;   // coordinates < d only
+                while (bits) {
+                    const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
+                    bits &= bits - 1;
+                    const uint32_t e1 = __ldg(cl.off + c + 1);
+                    for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
+                        atomicAdd(sk + (size_t)__ldg(cl.col + e) * NP + p, (unsigned long long)__ldg(cl.b + e));
+                }
             }
         }
     }
@@ -314,19 +321,32 @@ __device__ __forceinline__ void scatter_sketch(uint64_t *sm, uint32_t W, const u
 {
     for (uint32_t i = threadIdx.x; i < W * (uint32_t)NP; i += blockDim.x) sm[i] = 0ULL;
     __syncthreads();
-    const uint32_t items = (uint32_t)NP * words;
-    for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
-        const uint32_t p = it / words, w = it - p * words;
-        if (p0 + p >= cnt) break;   // items are p-major: later items of this thread are later points
-        uint64_t bits = __ldg(pts + (p0 + p) * words + w);
-        if (w == words - 1 && (cl.d & 63)) bits &= (1ULL << (cl.d & 63)) - 1;   // coordinates < d only
-        while (bits) {
-            const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
-            bits &= bits - 1;
-            const uint32_t e1 = __ldg(cl.off + c + 1);
-            for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
-                atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(__ldg(cl.col + e), p)),
-                          (unsigned long long)__ldg(cl.b + e));
+    // items of the tile's real points only; eight words in flight per thread
+    const uint64_t real = cnt - p0 < (uint64_t)NP ? cnt - p0 : (uint64_t)NP;
+    const uint32_t items = (uint32_t)real * words;
+    constexpr int U = 8;
+    for (uint32_t it0 = threadIdx.x; it0 < items; it0 += U * blockDim.x) {
+        uint64_t wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t it = it0 + u * blockDim.x;
+            wv[u] = it < items ? __ldg(pts + p0 * words + it) : 0ULL;   // the tile's rows are contiguous
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t it = it0 + u * blockDim.x;
+            uint64_t bits = wv[u];
+            if (!bits) continue;
+            const uint32_t p = it / words, w = it - p * words;
+            if (w == words - 1 && (cl.d & 63)) bits &= (1ULL << (cl.d & 63)) - 1;   // coordinates < d only
+            while (bits) {
+                const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
+                bits &= bits - 1;
+                const uint32_t e1 = __ldg(cl.off + c + 1);
+                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(__ldg(cl.col + e), p)),
+                              (unsigned long long)__ldg(cl.b + e));
+            }
         }
     }
 }

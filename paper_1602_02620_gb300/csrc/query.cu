@@ -142,7 +142,35 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
     }
     if (mode == DEDUP_MARK) return;   // warp-uniform
     bool hit = false;
-    if (isnew) {
+    if (a.words >= kWarpVerifyWords) {   // long points: the warp reads each new candidate together
+        const uint32_t lane = threadIdx.x & 31;
+        uint32_t need = __ballot_sync(0xffffffffu, isnew);
+        while (need) {
+            const uint32_t src = __ffs(need) - 1;
+            need &= need - 1;
+            const uint64_t *x = a.points + (uint64_t)__shfl_sync(0xffffffffu, id, src) * a.words;
+            // 256 words per step, eight independent loads per lane; stop once the
+            // distance so far exceeds the radius (warp-uniform)
+            uint32_t dist = 0, wb = 0;   // wb: warp-uniform base of the step
+            for (; wb + 256 <= a.words; wb += 256) {
+                uint64_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldg(x + wb + lane + 32 * u);
+                uint32_t part = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) part += __popcll(v[u] ^ q_s[wb + lane + 32 * u]);
+                dist += __reduce_add_sync(0xffffffffu, part);
+                if (dist > radius) break;
+            }
+            if (dist <= radius) {
+                uint32_t part = 0;
+                for (uint32_t w = wb + lane; w < a.words; w += 32) part += __popcll(__ldg(x + w) ^ q_s[w]);
+                dist += __reduce_add_sync(0xffffffffu, part);
+            }
+            if (lane == src) hit = dist <= radius;
+        }
+        if (isnew) c.cand++;
+    } else if (isnew) {
         c.cand++;
         hit = distance_to(a, q_s, id) <= radius;
     }
@@ -229,16 +257,37 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
 
         // ---- S1: Algorithm 2 for every part, in shared memory
         for (uint32_t k = 0; k < a.t; ++k) {
-            const uint32_t *co = a.col_off + (size_t)k * (a.W + 1);
-            for (uint32_t j = tid; j < a.W; j += B) {
-                uint64_t s = 0;
-                const uint32_t e1 = co[j + 1];
-                for (uint32_t e = co[j]; e < e1; ++e) {
-                    const uint32_t bit = a.col_coord[e];
-                    const uint64_t take = 0ULL - ((q_s[bit >> 6] >> (bit & 63)) & 1ULL);
-                    s = add_mod_p(s, a.col_b[e] & take);
+            if (a.s1_scatter) {
+                // sketch from the query's set bits: each adds its positions' seed values to
+                // their columns (64-bit sums, exact while a column holds <= 16,383 positions)
+                for (uint32_t j = tid; j < a.W; j += B) tbuf[j] = 0;
+                __syncthreads();
+                const uint32_t *off = a.sc_off + (size_t)k * (a.d + 1);
+                for (uint32_t w = tid; w < a.words; w += B) {
+                    uint64_t bits = q_s[w];
+                    if (w == a.words - 1 && (a.d & 63)) bits &= (1ULL << (a.d & 63)) - 1;
+                    while (bits) {
+                        const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
+                        bits &= bits - 1;
+                        for (uint32_t e = off[c]; e < off[c + 1]; ++e)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(tbuf + a.sc_col[e]),
+                                      (unsigned long long)a.sc_b[e]);
+                    }
                 }
-                tbuf[j] = s;
+                __syncthreads();
+                for (uint32_t j = tid; j < a.W; j += B) tbuf[j] = mod_p(tbuf[j]);
+            } else {
+                const uint32_t *co = a.col_off + (size_t)k * (a.W + 1);
+                for (uint32_t j = tid; j < a.W; j += B) {
+                    uint64_t s = 0;
+                    const uint32_t e1 = co[j + 1];
+                    for (uint32_t e = co[j]; e < e1; ++e) {
+                        const uint32_t bit = a.col_coord[e];
+                        const uint64_t take = 0ULL - ((q_s[bit >> 6] >> (bit & 63)) & 1ULL);
+                        s = add_mod_p(s, a.col_b[e] & take);
+                    }
+                    tbuf[j] = s;
+                }
             }
             __syncthreads();
             for (uint32_t h = 1; h < a.W; h <<= 1) {

@@ -105,6 +105,15 @@ def test_scatter_sketch_matches_oracle(d, r, t, n):
     order = np.lexsort((ids, keys))
     ok, oi = oracle.table(p, pts, p.T - 1)
     assert np.array_equal(keys[order], ok) and np.array_equal(ids[order], oi)
+    # queries (S1 by scatter for parts of >= 2,048 positions, one warp per distance for
+    # points of >= 32 words) report the linear-scan answer
+    qs = pts[rng.integers(0, n, size=24)].copy()
+    for i in range(24):
+        for c in rng.choice(d, size=int(rng.integers(0, r + 2)), replace=False):
+            qs[i, c >> 6] ^= np.uint64(1) << np.uint64(c & 63)
+    res = idx.query(qs, r)
+    for i in range(24):
+        assert res.of(i).tolist() == oracle.linear_scan(pts, qs[i], r).tolist()
     # the gather kernels give the same keys where their column lists fit
     try:
         idx.set_tuning(**dict(idx.tuning(), hash_tile=0))
