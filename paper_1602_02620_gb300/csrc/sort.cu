@@ -231,12 +231,22 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
     if (base >= len) return;   // uniform: an empty tile has no items
     uint32_t cursor = a.cap ? 0u : a.hist[((uint64_t)row * 256 + tid) * a.tiles + tile];   // digit tid's next place
     const uint64_t *K = a.keys_in + (uint64_t)row * len;
+    uint64_t nxt[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint64_t idx = base + (uint64_t)r * kSortThreads + tid;
+        nxt[r] = idx < len ? K[idx] : 0;
+    }
     for (uint64_t sbase = base; sbase < len && sbase < base + kSortTile; sbase += kSortSub) {
         uint64_t key[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint64_t idx = sbase + (uint64_t)r * kSortThreads + tid;
-            key[r] = idx < len ? K[idx] : 0;
+        for (int r = 0; r < R; ++r) key[r] = nxt[r];
+        if (sbase + kSortSub < base + kSortTile) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint64_t idx = sbase + kSortSub + (uint64_t)r * kSortThreads + tid;
+                nxt[r] = idx < len ? K[idx] : 0;
+            }
         }
         cnt[tid] = 0;
         __syncthreads();   // (also: the previous sub-tile's output is read out)
