@@ -42,7 +42,7 @@ CFG = 2
 TRAFFIC_RATIO = {
     "hash": 0.950,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
     "hash_mma": 0.954,    # profiles/hash_mma_kernel_w512_n300k_d128_r8.md
-    "scatter": None,      # profiles/partition_scatter_kernel_n300k_d128_r8.md (kernel changed since)
+    "scatter": 0.983,     # profiles/partition_scatter_kernel_n300k_d128_r8.md
     "finish": 0.999,      # profiles/segment_one_kernel_n300k_d128_r8.md
     "hist": None,         # (only on the histogram fallback of skewed keys)
 }
