@@ -175,6 +175,62 @@ def cpu_baseline(cfg: int, n, nq, budget_s: float = 12.0, cores: int | None = No
             "single_core_value": nqall / one_job_s}
 
 
+HASH_ROUTES = ((0, "wht"), (1, "wht_wide_tile"), (3, "wht_scatter_sketch"), (2, "direct_tensor_cores"),
+               (4, "direct_cuda_cores"))
+
+
+def hash_routes(fclsh, idx, pts, reps: int = 3):
+    """Points hashed per second into all T keys by every hash kernel that applies to the
+    index: Algorithm 2 (sketch + WHT: tiles 0, 1, 3) against the direct O(dL) route of Eq. 1
+    (the basic covering construction: tensor cores, tile 2; CUDA cores, tile 4) -- the
+    paper's fcLSH / bcLSH comparison of hash computation time (Sec. 4.3)."""
+    import torch
+
+    n = min(int(pts.shape[0]), max(4096, (1 << 28) // idx.T))   # at most 2 GB of keys
+    pts = pts[:n]
+    keys = torch.empty((idx.T, n), dtype=torch.int64, device="cuda")
+    saved = idx.tuning()
+    out = {}
+    for tl, name in HASH_ROUTES:
+        try:
+            idx.set_tuning(**dict(saved, hash_tile=tl))
+        except fclsh.FclshError:
+            continue
+        idx.hash(pts, out=keys)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            idx.hash(pts, out=keys)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"ms": ms, "points": n, "points_per_s": n / (ms / 1000.0)}
+    idx.set_tuning(**saved)
+    del keys
+    return out
+
+
+def hash_ablation(fclsh, n: int = 65_536):
+    """The paper's hash-time experiment on synthetic data of n = 64K points (Sec. 4.3):
+    d = 128 with r = 3..7, and r = 5 with d = 32..512, every hash route."""
+    import torch
+    from paper_1602_02620_gb300 import workloads
+
+    rows = []
+    for d, r in [(128, 3), (128, 4), (128, 5), (128, 6), (128, 7), (32, 5), (64, 5), (256, 5), (512, 5)]:
+        words = (d + 63) // 64
+        a = np.zeros((n, words), np.uint64)
+        workloads._lib().wl_uniform(workloads._key(100 + d, r), 0, n, d, a.ctypes.data)
+        pts = torch.from_numpy(a.view(np.int64)).cuda()
+        idx = fclsh.build(pts, d, r, 7)
+        routes = hash_routes(fclsh, idx, pts)
+        rows.append({"d": d, "r": r, "W": idx.W, "tables": idx.T,
+                     "points_per_s": {k: v["points_per_s"] for k, v in routes.items()}})
+        idx.free()
+    return {"n": n, "data": "uniform bits", "rows": rows}
+
+
 def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: float = 1e6, probe_rows: int = 0):
     """Continuous batching on the resident index: a Poisson stream of requests of
     U{1..4096} queries with radii in {r/4, r/2, 3r/4, r} (rounded), offered at `load`
@@ -260,7 +316,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="fewer points of the same workload (profiling)")
     ap.add_argument("--nq", type=int, default=None, help="fewer queries of the same workload (profiling)")
-    ap.add_argument("--hash-tile", type=int, default=None, choices=(0, 1, 2, 3),
+    ap.add_argument("--hash-tile", type=int, default=None, choices=(0, 1, 2, 3, 4),
                     help="force the hash kernel (0/1: WHT tiles, 2: tensor-core contraction) instead of the tuned one")
     ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 6, 7],
                     help="workload id (default: the n=1M d=128 r=8 plain workload)")
@@ -392,6 +448,7 @@ def main():
     T = idx.T
     serve = served(fclsh, idx, w, batched_qps=batched_qps)
     serve_rows = served(fclsh, idx, w, batched_qps=batched_qps, probe_rows=1)
+    routes = hash_routes(fclsh, idx, pts)
     idx.free()
 
     # ---- e2e through the C ABI from pinned host buffers
@@ -475,6 +532,8 @@ def main():
         },
         "served": serve,
         "served_row_probe": serve_rows,
+        "hash_routes": routes,
+        "hash_ablation": hash_ablation(fclsh) if not args.n and not args.nq else None,
         "roofline": {"kernel": dom["kernel"], "bound": "hbm", "achieved": dom["achieved_gbs"], "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac"], "traffic": dom["traffic"],
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_ms": dom["avg_ms"]},

@@ -74,7 +74,11 @@ typedef struct {
                                  128 coordinates), 3 = Algorithm 2 with the sketch built by scattering each
                                  point's set bits (O(nnz) per part, Sec. 3.2; any d, while no code column
                                  of a part holds more than 16,383 positions).  0 and 1 stage the part's
-                                 column lists in shared memory; a build whose lists do not fit takes 3. */
+                                 column lists in shared memory; a build whose lists do not fit takes 3.
+                                 4 = the O(dL) route on CUDA cores (Eq. 1 on g_v AND x for every table, no
+                                 transform: the basic covering construction, kept as the baseline the
+                                 paper compares Algorithm 2 against; parts of at most 4,096 positions;
+                                 never chosen by fclsh_autotune). */
     uint32_t replicate;       /* Algorithm 1's replication for cr < log n: every point and query is repeated
                                  this many times (0 or 1 = none; needs t <= 1).  The index then covers
                                  radius r * replicate of the repeated vectors: W = 2^(r*replicate + 1),
@@ -125,7 +129,7 @@ typedef struct {
     uint32_t inline_probe;    /* probe fan-out: a bucket range up to this length is walked by the lane that
                                  probed it, a longer one by the whole warp (1..32) */
     uint32_t use_graph;       /* capture a batch's launches into a CUDA graph and replay it */
-    uint32_t hash_tile;       /* hash kernel of fclsh_hash and of later builds (fclsh_build_opts.hash_tile): 0..3 */
+    uint32_t hash_tile;       /* hash kernel of fclsh_hash and of later builds (fclsh_build_opts.hash_tile): 0..4 */
     uint32_t probe_rows;      /* 0: a query probes all T tables (Strategy 2, Sec. 2.2).  1: a query of radius
                                  rho probes only the code rows v = 1 .. 2^(floor(rho*rep/t)+1) - 1 of each
                                  part; the ids are the same (pigeonhole over the parts, Sec. 3.1, or the

@@ -584,7 +584,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->rp = rp;
     idx->W = W;
     idx->T = t * (W - 1);
-    if (o.hash_tile > 3) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1, 2 or 3");
+    if (o.hash_tile > 4) return fail(FCLSH_EINVAL, "hash_tile must be 0..4");
     idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0};
     idx->timing = o.timing != 0;
 
@@ -634,6 +634,8 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if (o.hash_tile == 3 && !scatter_fits)
         return fail(FCLSH_EINVAL, "hash_tile 3 (scatter sketch) needs at most %u positions per column (have %u)",
                     kScatterMaxPop, idx->sc_pop);
+    if (o.hash_tile == 4 && max_dk > kDirectMaxPositions)
+        return fail(FCLSH_EINVAL, "hash_tile 4 (direct route) needs parts of at most %u positions", kDirectMaxPositions);
 
     uint32_t sb = o.slot_bits;
     if (!sb) {
@@ -661,7 +663,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->col_off = reinterpret_cast<uint32_t *>(dblock + bval.size());
     idx->col_coord = idx->col_off + col_off.size();
     std::vector<uint64_t> sblock;
-    if (scatter_fits) {   // b values, then offsets, then columns
+    {   // b values, then offsets, then columns
         sblock.assign(sc_bv.size() + (sc_off.size() + sc_col.size() + 1) / 2, 0);
         std::memcpy(sblock.data(), sc_bv.data(), sc_bv.size() * 8);
         std::memcpy(reinterpret_cast<uint32_t *>(sblock.data() + sc_bv.size()), sc_off.data(), sc_off.size() * 4);
@@ -1286,7 +1288,7 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     if (t->hash_set_log2 < 10 || t->hash_set_log2 > 13) return fail(FCLSH_EINVAL, "hash_set_log2 must be in 10..13");
     if (t->inline_probe < 1 || t->inline_probe > 32) return fail(FCLSH_EINVAL, "inline_probe must be in 1..32");
     if (t->query_ctas_per_sm < 1 || t->query_ctas_per_sm > 16) return fail(FCLSH_EINVAL, "query_ctas_per_sm must be in 1..16");
-    if (t->hash_tile > 3) return fail(FCLSH_EINVAL, "hash_tile must be 0, 1, 2 or 3");
+    if (t->hash_tile > 4) return fail(FCLSH_EINVAL, "hash_tile must be 0..4");
     if (t->hash_tile == 3 && !idx->scatter_ok())
         return fail(FCLSH_EINVAL, "hash_tile 3 (scatter sketch) needs at most %u positions per column (have %u)",
                     kScatterMaxPop, idx->sc_pop);
@@ -1297,6 +1299,8 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
     uint32_t max_dk = 0;
     for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
+    if (t->hash_tile == 4 && max_dk > kDirectMaxPositions)
+        return fail(FCLSH_EINVAL, "hash_tile 4 (direct route) needs parts of at most %u positions", kDirectMaxPositions);
     if (t->hash_tile != 2 && hash_smem_bytes(idx->W, max_dk, t->hash_tile) > idx->smem_optin)
         return fail(FCLSH_EINVAL, "the hash tile does not fit in shared memory");
     idx->tune = *t;

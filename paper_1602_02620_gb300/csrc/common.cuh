@@ -22,6 +22,7 @@ constexpr uint32_t kPackedMaxD = 16384;   // coordinates the packed specific-con
 // reducing: exact while a column of a part holds at most this many positions.
 constexpr uint32_t kScatterMaxPop = 16383;
 constexpr uint32_t kS1ScatterPositions = 2048;   // parts at least this long: query sketch by scatter
+constexpr uint32_t kDirectMaxPositions = 4096;   // longest part of the direct route (hash_tile 4)
 constexpr uint32_t kWarpVerifyWords = 32;        // points of at least this many words: one warp per distance
 constexpr int kSortTile = 8192;       // radix-sort items per histogram tile (one block)
 constexpr int kSortSub = 2048;        // items per scatter sub-tile (256 threads x 8)

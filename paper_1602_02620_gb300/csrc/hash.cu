@@ -197,6 +197,59 @@ __global__ void __launch_bounds__(128, 4) hash_small_scatter_kernel(const uint64
     for (int j = 1; j < W; ++j) keys[(uint64_t)(j - 1) * ld + i] = finish_key(S, v[j]);
 }
 
+// ------------------------------------------------------------------ direct route (bcLSH)
+
+// The O(d'L) route of Eq. (1) on CUDA cores, without the transform: key v of a point
+// is sum over its set positions i of b_i * <a(m(i)), v> mod P, i.e. Eq. (1) applied to
+// g_v AND x (the basic covering construction; Lemma 3's other side).  A block takes
+// kDirectPoints points: it lists every point's set positions (column, seed value)
+// in shared memory through the coordinate lists, then each thread computes keys
+// (table v, point p) with p fastest, so that a warp's stores cover consecutive points.
+constexpr int kDirectPoints = 4;
+constexpr int kDirectThreads = 256;
+
+__global__ void __launch_bounds__(kDirectThreads) hash_direct_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
+                                                                     uint32_t words, CoordLists cl, uint32_t W,
+                                                                     uint32_t maxpos, uint64_t *__restrict__ keys,
+                                                                     uint64_t ld)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *lb = reinterpret_cast<uint64_t *>(smem_raw);                       // [kDirectPoints][maxpos]
+    uint16_t *lc = reinterpret_cast<uint16_t *>(lb + (size_t)kDirectPoints * maxpos);
+    __shared__ uint32_t len[kDirectPoints];
+    const uint64_t p0 = blockIdx.x * (uint64_t)kDirectPoints;
+    if (threadIdx.x < kDirectPoints) len[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t real = (uint32_t)(cnt - p0 < (uint64_t)kDirectPoints ? cnt - p0 : (uint64_t)kDirectPoints);
+    for (uint32_t it = threadIdx.x; it < real * words; it += blockDim.x) {
+        const uint32_t p = it / words, w = it - p * words;
+        uint64_t bits = __ldg(pts + p0 * words + it);
+        if (w == words - 1 && (cl.d & 63)) bits &= (1ULL << (cl.d & 63)) - 1;   // coordinates < d only
+        while (bits) {
+            const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
+            bits &= bits - 1;
+            const uint32_t e1 = __ldg(cl.off + c + 1);
+            for (uint32_t e = __ldg(cl.off + c); e < e1; ++e) {
+                const uint32_t at = atomicAdd(&len[p], 1u);   // < maxpos: a point has at most the part's positions
+                lb[(size_t)p * maxpos + at] = __ldg(cl.b + e);
+                lc[(size_t)p * maxpos + at] = (uint16_t)__ldg(cl.col + e);
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t pairs = (W - 1) * (uint32_t)kDirectPoints;
+    for (uint32_t j = threadIdx.x; j < pairs; j += blockDim.x) {
+        const uint32_t p = j % kDirectPoints, v = j / kDirectPoints + 1;
+        if (p >= real) continue;
+        const uint64_t *b = lb + (size_t)p * maxpos;
+        const uint16_t *col = lc + (size_t)p * maxpos;
+        uint64_t key = 0;
+        for (uint32_t e = 0, n = len[p]; e < n; ++e)
+            if (__popc(v & col[e]) & 1) key = add_mod_p(key, b[e]);   // (g_v AND x)_i = <a(m(i)), v> x_i
+        keys[(uint64_t)(v - 1) * ld + p0 + p] = key;
+    }
+}
+
 // ------------------------------------------------------------------ W >= 64
 
 template <int LOGW> struct TileCfg;
@@ -468,9 +521,11 @@ size_t tile_smem(uint32_t tile)
 }
 
 // Shared memory one hash block needs for code length W, a part of dk coordinates
-// and the tile choice (3: the scatter sketch, which stages no column lists).
+// and the tile choice (3: the scatter sketch, which stages no column lists; 4: the
+// direct route's lists of set positions).
 size_t hash_smem_bytes(uint32_t W, uint32_t dk, uint32_t tile)
 {
+    if (tile == 4) return (size_t)kDirectPoints * dk * 10;
     if (tile == 3) return W <= 32 ? (size_t)W * 128 * 8 : hash_smem_bytes(W, 0, 0) - cols_smem_bytes(W, 0);
     size_t t = 0;
     switch (W) {
@@ -499,6 +554,19 @@ cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t 
     }
     const uint32_t logw = idx->rp + 1;
     const uint32_t tl = idx->tune.hash_tile;
+    if (tl == 4) {   // direct route: lists of at most dk set positions per point
+        if (!idx->sc_b || dk > kDirectMaxPositions) return cudaErrorInvalidValue;
+        const size_t smem = hash_smem_bytes(idx->W, dk, 4);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(hash_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        hash_direct_kernel<<<(unsigned)((cnt + kDirectPoints - 1) / kDirectPoints), kDirectThreads, smem, s>>>(
+            pts, cnt, idx->words, idx->coords(k), idx->W, dk, keys, ld);
+        note_launch();
+        return cudaGetLastError();
+    }
     if (tl == 3 && !idx->scatter_ok()) return cudaErrorInvalidValue;
     const CoordLists cl = tl == 3 ? idx->coords(k) : CoordLists{nullptr, nullptr, nullptr, 0};
     switch (logw) {

@@ -369,8 +369,9 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
     """fclsh_build on host (numpy) or device (torch CUDA) points [n][ceil(d/64)] uint64.
 
     hash_tile selects the hash kernel (0 default WHT tile, 1 twice as many points, 2 the
-    tensor-core contraction, 3 the scatter sketch over set bits); fclsh_autotune reports the
-    fastest as tuning()["hash_tile"], and a build whose column lists do not fit takes 3.
+    tensor-core contraction, 3 the scatter sketch over set bits, 4 the direct O(dL) route on
+    CUDA cores); fclsh_autotune reports the fastest of 0..3 as tuning()["hash_tile"], and a
+    build whose column lists do not fit takes 3.
     replicate repeats every vector that many times (Algorithm 1, cr < log n); approx_c > 0
     with neither t nor replicate set chooses both by Algorithm 1."""
     o = BuildOpts()

@@ -294,12 +294,13 @@ def test_row_restricted_probe_matches_oracle(d, r, t, n):
     idx.free()
 
 
-@pytest.mark.parametrize("tile", [1, 2])
+@pytest.mark.parametrize("tile", [1, 2, 4])
 @pytest.mark.parametrize("d,r,t", [(100, 5, None), (128, 6, None), (200, 7, None), (128, 8, None),
                                    (1024, 9, None), (256, 16, None), (2000, 10, 2), (96, 12, 2), (128, 9, 3)])
 def test_hash_tiles_are_bit_exact(d, r, t, tile):
-    """hash_tile = 1 (twice the points per WHT block) and hash_tile = 2 (the O(dL) route as an
-    exact tensor-core contraction) give the oracle's keys and the same directory."""
+    """hash_tile = 1 (twice the points per WHT block), hash_tile = 2 (the O(dL) route as an
+    exact tensor-core contraction) and hash_tile = 4 (the O(dL) route on CUDA cores, the basic
+    construction without the transform) give the oracle's keys and the same directory."""
     fc = F()
     rng = np.random.default_rng(d + 5 * r)
     n = 1333
