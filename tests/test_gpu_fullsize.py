@@ -1,12 +1,14 @@
 """Parity at the full workload sizes, in the launch configuration the benchmark times.
 
-For each workload the index is built from device-resident points with the
-default (benchmark) settings.  The oracle then checks what it can compute one by
+For each workload the index is built from device-resident points in the
+benchmark's configuration (the autotuner's kernel shapes and hash kernel).  The oracle then checks what it can compute one by
 one at that size: the parameters, every key of sampled points in every table,
 complete buckets of sampled tables, and sampled queries' answers (linear scan,
 the plain definition).  All queries are checked against the GPU linear scan
 (an independent kernel), and every reported id is re-verified on the host.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -14,6 +16,8 @@ import oracle
 from paper_1602_02620_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 torch = pytest.importorskip("torch")
 
@@ -37,7 +41,16 @@ def test_full_size_workload(cfg):
     seed = c["seed"] + 1000
     d, r = c["d"], c["r"]
     p = oracle.derive_params(seed, d, r)
-    idx = fclsh.build(torch.from_numpy(pts.view(np.int64)).cuda(), d, r, seed)
+    # the benchmark's launch configuration: kernel shapes and hash kernel from the autotuner
+    # (the same cache file bench.py uses), then an index built with them
+    pts_dev = torch.from_numpy(pts.view(np.int64)).cuda()
+    q_dev = torch.from_numpy(qs.view(np.int64)).cuda()
+    cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
+    idx0 = fclsh.build(pts_dev, d, r, seed)
+    tuned = idx0.autotune(q_dev[: min(nq, 4096)], r, cache)
+    idx0.free()
+    idx = fclsh.build(pts_dev, d, r, seed, hash_tile=tuned["hash_tile"])
+    idx.set_tuning(**tuned)
     assert idx.n == c["n"] and idx.T == p.T
 
     perm, part_off, m, b = idx.params()
@@ -53,7 +66,6 @@ def test_full_size_workload(cfg):
         for key in probe[:20]:
             assert np.array_equal(idx.bucket(tau, int(key)), oi[ok == key]), (tau, int(key))
 
-    q_dev = torch.from_numpy(qs.view(np.int64)).cuda()
     res = idx.query(q_dev, r)                                     # the batched path, as benchmarked
     brute = idx.bruteforce(q_dev, r)
     assert np.array_equal(res.offs, brute.offs) and np.array_equal(res.ids, brute.ids)
