@@ -357,6 +357,18 @@ fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64_t counts[8
 /* Kernels this library has enqueued in this process (a replayed CUDA graph counts its kernel nodes). */
 uint64_t fclsh_kernel_launches(void);
 
+/*
+ * Testing aids for the out-of-memory paths (no counterpart in the paper).
+ * fclsh_debug_fail_alloc(k): the k-th device allocation of this library from now on
+ * (k = 0: the next one) fails as if the device were out of memory, once; k < 0 turns
+ * the injection off.  Calls then return FCLSH_ENOMEM and must release what they took.
+ * fclsh_debug_pool_used: bytes of the current device's library memory pool in use,
+ * after a device synchronisation (freed memory stays reserved by the pool but is not
+ * counted), so that a test can check that a failed call leaked nothing.
+ */
+fclsh_status fclsh_debug_fail_alloc(int64_t after);
+fclsh_status fclsh_debug_pool_used(uint64_t *bytes);
+
 /* Thread-local description of the calling thread's last failure. */
 const char *fclsh_last_error(void);
 

@@ -124,8 +124,23 @@ static cudaMemPool_t device_pool(int dev)
     return pools[dev];
 }
 
+// Allocation-failure injection for tests of the out-of-memory paths: while >= 0, the
+// device allocation that finds it at 0 fails with cudaErrorMemoryAllocation (and the
+// countdown stops); each earlier one decrements it.
+static std::atomic<int64_t> g_fail_alloc{-1};
+
+static bool injected_alloc_failure()
+{
+    int64_t v = g_fail_alloc.load();
+    while (v >= 0) {
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
 cudaError_t dev_alloc(void **p, size_t bytes)
 {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -146,6 +161,7 @@ void dev_free(void *p)
 // until the caller synchronises it (the build), so no synchronisation here.
 static cudaError_t dev_alloc_ordered(void **p, size_t bytes)
 {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -325,6 +341,12 @@ static fclsh_status ctx_shape(fclsh_qctx *c)
     if (grid != c->grid) {
         if (c->bitmaps) dev_free(c->bitmaps);
         c->bitmaps = nullptr;
+        c->grid = 0;   // a failed allocation below leaves no shape that looks usable
+        if (c->gexec) {   // a captured batch refers to the old bitmaps
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        c->g_seen = false;
         const uint64_t bm_words = (idx->n + 31) / 32;
         FCLSH_CUDA(dev_alloc((void **)&c->bitmaps, (size_t)grid * bm_words * 4));
         FCLSH_CUDA(cudaMemset(c->bitmaps, 0, (size_t)grid * bm_words * 4));
@@ -346,6 +368,7 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
         c->coll = c->cand = nullptr;
         c->scan_part = nullptr;
         c->run_base = nullptr;
+        c->nq_cap = 0;   // a failed allocation below leaves no capacity that looks usable
         const uint64_t m = std::max<uint64_t>(nq, 1024);
         FCLSH_CUDA(dev_alloc((void **)&c->run_base, m * 8));
         FCLSH_CUDA(dev_alloc((void **)&c->res_cnt, m * 4));
@@ -366,6 +389,7 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
             if (p) dev_free(p);
         c->runs = nullptr;
         c->res_ids = nullptr;
+        c->cap = 0;
         FCLSH_CUDA(dev_alloc((void **)&c->runs, cap * 4));
         FCLSH_CUDA(dev_alloc((void **)&c->res_ids, cap * 4));
         c->cap = cap;
@@ -496,7 +520,9 @@ static fclsh_status run_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uin
 
 // The tensor-core hash's operands (coordinate lists and G's fp16 chunks), built once.
 // s == nullptr (the build, on the legacy stream): stream-ordered, no synchronisation.
-static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s)
+// owner: the build's allocation list, which keeps the operands on success and frees
+// them if the build fails later (nullptr: the index owns them from here on).
+static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s, DevAllocs *owner = nullptr)
 {
     if (idx->mma_g) return FCLSH_OK;
     if (!idx->mma_k)
@@ -507,29 +533,31 @@ static fclsh_status ensure_mma_operands(fclsh_index *idx, cudaStream_t s)
         for (uint32_t i = idx->part_off[k]; i < idx->part_off[k + 1]; ++i)
             coord[(size_t)k * K + (i - idx->part_off[k])] = idx->perm[i];
     const size_t per = hash_mma_operand_entries(K, idx->W);
-    DevAllocs tmp(s == nullptr), keep(s == nullptr);
+    DevAllocs tmp(s == nullptr), own(s == nullptr);
+    DevAllocs &keep = owner ? *owner : own;
     const uint32_t D = idx->positions();
     std::vector<uint64_t> mb(D + (D + 1) / 2);   // b values, then m (32-bit)
     std::memcpy(mb.data(), idx->b.data(), (size_t)D * 8);
     std::memcpy(reinterpret_cast<uint32_t *>(mb.data() + D), idx->m.data(), (size_t)D * 4);
     uint64_t *dmb = nullptr;
+    uint32_t *mc = nullptr;   // the index takes these only once they are complete
+    uint16_t *mg = nullptr;
     cudaError_t e;
-    if ((e = keep.alloc(&idx->mma_coord, coord.size())) != cudaSuccess ||
-        (e = keep.alloc(&idx->mma_g, per * t)) != cudaSuccess || (e = tmp.alloc(&dmb, mb.size())) != cudaSuccess) {
-        idx->mma_coord = nullptr;
-        idx->mma_g = nullptr;
+    if ((e = keep.alloc(&mc, coord.size())) != cudaSuccess || (e = keep.alloc(&mg, per * t)) != cudaSuccess ||
+        (e = tmp.alloc(&dmb, mb.size())) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(tensor-core hash operands)");
-    }
     const uint64_t *db = dmb;
     const uint32_t *dm = reinterpret_cast<const uint32_t *>(dmb + D);
-    FCLSH_CUDA(cudaMemcpyAsync(idx->mma_coord, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemcpyAsync(mc, coord.data(), coord.size() * 4, cudaMemcpyHostToDevice, s));
     FCLSH_CUDA(cudaMemcpyAsync(dmb, mb.data(), mb.size() * 8, cudaMemcpyHostToDevice, s));
     for (uint32_t k = 0; k < t; ++k) {
         const uint32_t lo = idx->part_off[k];
-        FCLSH_CUDA(build_mma_operand(dm + lo, db + lo, idx->part_off[k + 1] - lo, K, idx->W, idx->mma_g + k * per, s));
+        FCLSH_CUDA(build_mma_operand(dm + lo, db + lo, idx->part_off[k + 1] - lo, K, idx->W, mg + k * per, s));
     }
     if (s) FCLSH_CUDA(cudaStreamSynchronize(s));
-    keep.release();
+    own.release();
+    idx->mma_coord = mc;
+    idx->mma_g = mg;
     idx->device_bytes += coord.size() * 4 + per * t * 2;
     return FCLSH_OK;
 }
@@ -687,7 +715,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if ((e = keep.alloc(&idx->status, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
     FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
     if (o.hash_tile == 2) {
-        fclsh_status st = ensure_mma_operands(idx, s);
+        fclsh_status st = ensure_mma_operands(idx, s, &keep);
         if (st != FCLSH_OK) return st;
     }
 
@@ -1078,6 +1106,7 @@ static fclsh_status stage_inputs(fclsh_qctx *c, const uint64_t *queries, uint64_
         if (nq * idx->words > c->qbuf_cap) {
             if (c->qbuf) dev_free(c->qbuf);
             c->qbuf = nullptr;
+            c->qbuf_cap = 0;
             FCLSH_CUDA(dev_alloc((void **)&c->qbuf, nq * idx->words * 8));
             c->qbuf_cap = nq * idx->words;
         }
@@ -1091,6 +1120,7 @@ static fclsh_status stage_inputs(fclsh_qctx *c, const uint64_t *queries, uint64_
         if (nq > c->rbuf_cap) {
             if (c->rbuf) dev_free(c->rbuf);
             c->rbuf = nullptr;
+            c->rbuf_cap = 0;
             FCLSH_CUDA(dev_alloc((void **)&c->rbuf, nq * 4));
             c->rbuf_cap = nq;
         }
@@ -1331,6 +1361,26 @@ extern "C" fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64
 }
 
 extern "C" uint64_t fclsh_kernel_launches(void) { return launch_count(); }
+
+extern "C" fclsh_status fclsh_debug_fail_alloc(int64_t after)
+{
+    g_fail_alloc.store(after < 0 ? -1 : after);
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_debug_pool_used(uint64_t *bytes)
+{
+    if (!bytes) return fail(FCLSH_EINVAL, "NULL argument");
+    int dev = 0;
+    FCLSH_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return fail(FCLSH_ECUDA, "no memory pool on device %d", dev);
+    uint64_t used = 0;   // the attribute is a 64-bit unsigned count
+    FCLSH_CUDA(cudaDeviceSynchronize());   // stream-ordered frees have completed
+    FCLSH_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    *bytes = (uint64_t)used;
+    return FCLSH_OK;
+}
 
 extern "C" const char *fclsh_last_error(void) { return g_err.c_str(); }
 

@@ -102,6 +102,8 @@ SIGNATURES = {
     "fclsh_server_stats": (_i, [_vp, _vp, _i]),
     "fclsh_server_free": (None, [_vp]),
     "fclsh_kernel_launches": (_u64, []),
+    "fclsh_debug_fail_alloc": (_i, [ctypes.c_int64]),
+    "fclsh_debug_pool_used": (_i, [_vp]),
     "fclsh_last_error": (ctypes.c_char_p, []),
     "fclsh_version": (ctypes.c_char_p, []),
 }
@@ -391,6 +393,18 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
     h = ctypes.c_void_p()
     _check(lib().fclsh_build(_ptr(points), _rows(points), d, r, seed, ctypes.byref(o), ctypes.byref(h)))
     return Index(h)
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Make the after-th device allocation of the library fail as out of memory (< 0: off)."""
+    _check(lib().fclsh_debug_fail_alloc(after))
+
+
+def debug_pool_used() -> int:
+    """Bytes of the library's device memory pool in use (after a device synchronisation)."""
+    v = ctypes.c_uint64()
+    _check(lib().fclsh_debug_pool_used(ctypes.byref(v)))
+    return int(v.value)
 
 
 def kernel_launches() -> int:
