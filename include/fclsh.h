@@ -163,6 +163,18 @@ void fclsh_free(fclsh_index *idx);
 fclsh_status fclsh_get_info(const fclsh_index *idx, fclsh_info *out);
 
 /*
+ * Checkpoint and resume (no counterpart in the paper): fclsh_save writes the index's
+ * parameters (sizes, the random choices of Algorithms 1 and 2, the tuning) and its
+ * points to `path`, with a checksum; fclsh_load reads such a file and rebuilds the
+ * index on the current device from them (the same keys and buckets as the saved
+ * index; the bucket tables are not stored, since rebuilding them on the GPU is faster
+ * than reading them).  Errors: FCLSH_EINVAL for a file that cannot be opened, is not
+ * an index file, is truncated or fails its checksum; FCLSH_ENOMEM; FCLSH_ECUDA.
+ */
+fclsh_status fclsh_save(const fclsh_index *idx, const char *path);
+fclsh_status fclsh_load(const char *path, fclsh_index **out);
+
+/*
  * Copy out the index's random choices (host arrays sized D, t+1, D, D with
  * D = d * rep positions) so that they can be compared with an independent
  * derivation.  Any pointer may be NULL.

@@ -1360,6 +1360,158 @@ extern "C" fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64
     return FCLSH_OK;
 }
 
+// ---------------------------------------------------------------- save / load
+
+// File layout (little-endian): the 8-byte magic, a header of u32 fields {d, r, t, rep,
+// slot_bits, hash_tile, W, version} and u64 {n, P}, the tuning (7 x u32), the random
+// choices perm[D], part_off[t+1], m[D] (u32) and b[D] (u64), the points [n][words]
+// (u64), and an FNV-1a 64 checksum of everything before it.  The tables are not
+// stored: loading rebuilds them from the points with the stored choices (the same
+// keys and buckets), which on the GPU is faster than reading them back.
+static const char kMagic[8] = {'F', 'C', 'L', 'S', 'H', 'I', 'X', '1'};
+constexpr uint32_t kFileVersion = 1;
+
+struct Fnv64 {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    void add(const void *p, size_t len)
+    {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < len; ++i) h = (h ^ c[i]) * 0x100000001b3ULL;
+    }
+};
+
+struct FileWriter {
+    FILE *f = nullptr;
+    Fnv64 sum;
+    bool ok = true;
+    void put(const void *p, size_t len)
+    {
+        if (ok && len && fwrite(p, 1, len, f) != len) ok = false;
+        sum.add(p, len);
+    }
+};
+
+struct FileReader {
+    FILE *f = nullptr;
+    Fnv64 sum;
+    bool ok = true;
+    void get(void *p, size_t len)
+    {
+        if (ok && len && fread(p, 1, len, f) != len) ok = false;
+        if (ok) sum.add(p, len);
+    }
+};
+
+extern "C" fclsh_status fclsh_save(const fclsh_index *idx, const char *path)
+{
+    if (!idx || !path) return fail(FCLSH_EINVAL, "NULL argument");
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    FileWriter w;
+    w.f = fopen(path, "wb");
+    if (!w.f) return fail(FCLSH_EINVAL, "cannot open %s for writing", path);
+    const uint32_t hdr[8] = {idx->d, idx->r, idx->t, idx->rep, idx->slot_bits, idx->tune.hash_tile, idx->W,
+                             kFileVersion};
+    const uint64_t hdr64[2] = {idx->n, idx->P};
+    const uint32_t tune[7] = {idx->tune.query_block, idx->tune.query_ctas_per_sm, idx->tune.hash_set_log2,
+                              idx->tune.inline_probe, idx->tune.use_graph, idx->tune.hash_tile,
+                              idx->tune.probe_rows};
+    w.put(kMagic, 8);
+    w.put(hdr, sizeof hdr);
+    w.put(hdr64, sizeof hdr64);
+    w.put(tune, sizeof tune);
+    const size_t D = idx->positions();
+    w.put(idx->perm.data(), D * 4);
+    w.put(idx->part_off.data(), (idx->t + 1) * 4);
+    w.put(idx->m.data(), D * 4);
+    w.put(idx->b.data(), D * 8);
+    // the points, through a host buffer of at most 64 MB
+    const uint64_t total = idx->n * idx->words;
+    const uint64_t chunk = std::min<uint64_t>(total, 8ULL << 20);
+    std::vector<uint64_t> buf(chunk);
+    for (uint64_t at = 0; at < total && w.ok; at += chunk) {
+        const uint64_t len = std::min<uint64_t>(chunk, total - at);
+        cudaError_t e = cudaMemcpy(buf.data(), idx->points + at, len * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            fclose(w.f);
+            return cuda_fail(e, "cudaMemcpy(points)");
+        }
+        w.put(buf.data(), len * 8);
+    }
+    const uint64_t sum = w.sum.h;
+    if (w.ok && fwrite(&sum, 1, 8, w.f) != 8) w.ok = false;
+    if (fclose(w.f) != 0) w.ok = false;
+    if (!w.ok) return fail(FCLSH_EINVAL, "writing %s failed", path);
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_load(const char *path, fclsh_index **out)
+{
+    if (!path || !out) return fail(FCLSH_EINVAL, "NULL argument");
+    *out = nullptr;
+    FileReader rd;
+    rd.f = fopen(path, "rb");
+    if (!rd.f) return fail(FCLSH_EINVAL, "cannot open %s", path);
+    std::unique_ptr<FILE, int (*)(FILE *)> closer(rd.f, fclose);
+    char magic[8];
+    uint32_t hdr[8];
+    uint64_t hdr64[2];
+    uint32_t tune[7];
+    rd.get(magic, 8);
+    if (!rd.ok || memcmp(magic, kMagic, 8) != 0) return fail(FCLSH_EINVAL, "%s is not an fclsh index file", path);
+    rd.get(hdr, sizeof hdr);
+    rd.get(hdr64, sizeof hdr64);
+    rd.get(tune, sizeof tune);
+    if (!rd.ok) return fail(FCLSH_EINVAL, "%s: truncated header", path);
+    const uint32_t d = hdr[0], r = hdr[1], t = hdr[2], rep = hdr[3], sb = hdr[4], tile = hdr[5], W = hdr[6];
+    const uint64_t n = hdr64[0];
+    if (hdr[7] != kFileVersion) return fail(FCLSH_EINVAL, "%s: file version %u, expected %u", path, hdr[7], kFileVersion);
+    if (hdr64[1] != kP) return fail(FCLSH_EINVAL, "%s: the prime differs from this library's", path);
+    if (d == 0 || d > kMaxD || t == 0 || t > d || rep == 0 || rep > 32 || n == 0 || n > 0xFFFFFFFFULL - 1 ||
+        W < 2 || W > (1u << kMaxLogW) || (W & (W - 1)))
+        return fail(FCLSH_EINVAL, "%s: header out of range", path);
+    const uint64_t words = (d + 63) / 64, D = (uint64_t)d * rep;
+    std::vector<uint32_t> perm(D), part_off(t + 1), m(D);
+    std::vector<uint64_t> b(D), pts;
+    rd.get(perm.data(), D * 4);
+    rd.get(part_off.data(), (t + 1) * 4);
+    rd.get(m.data(), D * 4);
+    rd.get(b.data(), D * 8);
+    if (!rd.ok) return fail(FCLSH_EINVAL, "%s: truncated parameters", path);
+    try {
+        pts.resize(n * words);
+    } catch (const std::bad_alloc &) {
+        return fail(FCLSH_ENOMEM, "host memory for %llu points", (unsigned long long)n);
+    }
+    rd.get(pts.data(), pts.size() * 8);
+    uint64_t sum = 0;
+    const uint64_t want = rd.sum.h;
+    if (!rd.ok || fread(&sum, 1, 8, rd.f) != 8) return fail(FCLSH_EINVAL, "%s: truncated", path);
+    if (sum != want) return fail(FCLSH_EINVAL, "%s: checksum mismatch (the file is damaged)", path);
+    fclsh_build_opts o{};
+    o.t = t;
+    o.replicate = rep;
+    o.slot_bits = sb;
+    o.hash_tile = tile;
+    o.perm = perm.data();
+    o.part_off = part_off.data();
+    o.m = m.data();
+    o.b = b.data();
+    fclsh_index *idx = nullptr;
+    fclsh_status st = fclsh_build(pts.data(), n, d, r, 0, &o, &idx);
+    if (st != FCLSH_OK) return st;
+    if (idx->W != W) {
+        fclsh_free(idx);
+        return fail(FCLSH_EINVAL, "%s: code length %u does not follow from its header", path, W);
+    }
+    const fclsh_tuning tu{tune[0], tune[1], tune[2], tune[3], tune[4], tune[5], tune[6]};
+    if ((st = fclsh_set_tuning(idx, &tu)) != FCLSH_OK) {
+        fclsh_free(idx);
+        return st;
+    }
+    *out = idx;
+    return FCLSH_OK;
+}
+
 extern "C" uint64_t fclsh_kernel_launches(void) { return launch_count(); }
 
 extern "C" fclsh_status fclsh_debug_fail_alloc(int64_t after)

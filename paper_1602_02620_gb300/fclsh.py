@@ -102,6 +102,8 @@ SIGNATURES = {
     "fclsh_server_stats": (_i, [_vp, _vp, _i]),
     "fclsh_server_free": (None, [_vp]),
     "fclsh_kernel_launches": (_u64, []),
+    "fclsh_save": (_i, [_vp, ctypes.c_char_p]),
+    "fclsh_load": (_i, [ctypes.c_char_p, _vp]),
     "fclsh_debug_fail_alloc": (_i, [ctypes.c_int64]),
     "fclsh_debug_pool_used": (_i, [_vp]),
     "fclsh_last_error": (ctypes.c_char_p, []),
@@ -224,6 +226,11 @@ class Index:
         self.info = {f: int(getattr(info, f)) for f, _ in Info._fields_}
         for k, v in self.info.items():
             setattr(self, k, v)
+
+    # -- checkpoint
+    def save(self, path: str) -> None:
+        """fclsh_save: parameters, tuning and points to `path` (load() rebuilds the tables)."""
+        _check(lib().fclsh_save(self.handle, os.fsencode(path)))
 
     # -- parameters / diagnostics
     def params(self):
@@ -405,6 +412,13 @@ def debug_pool_used() -> int:
     v = ctypes.c_uint64()
     _check(lib().fclsh_debug_pool_used(ctypes.byref(v)))
     return int(v.value)
+
+
+def load(path: str) -> Index:
+    """fclsh_load: rebuild an index saved by Index.save on the current device."""
+    h = ctypes.c_void_p()
+    _check(lib().fclsh_load(os.fsencode(path), ctypes.byref(h)))
+    return Index(h)
 
 
 def kernel_launches() -> int:
