@@ -17,6 +17,8 @@
 
 #include "common.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace fclsh {
 
 // ---- declarations from query.cu / hash.cu
@@ -195,6 +197,16 @@ struct DevAllocs {
     {
         ptrs.clear();
     }
+};
+
+// ---------------------------------------------------------------- tracing
+
+// NVTX range for profilers and tracers (free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // ---------------------------------------------------------------- timing
@@ -576,6 +588,7 @@ static fclsh_status check_status(fclsh_index *idx, cudaStream_t s)
 extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t d, uint32_t r, uint64_t seed,
                                     const fclsh_build_opts *opts, fclsh_index **out)
 {
+    NvtxRange nv("fclsh_build");
     if (!out) return fail(FCLSH_EINVAL, "out is NULL");
     *out = nullptr;
     if (!points) return fail(FCLSH_EINVAL, "points is NULL");
@@ -766,9 +779,11 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
 
     for (uint32_t k = 0; k < t; ++k) {
         {
+            NvtxRange nh("fclsh_build: hash part");
             PhaseTimer pt(idx, 0, s);
             FCLSH_CUDA(launch_hash_part(idx, k, idx->points, n, keys, n, s));
         }
+        NvtxRange ns("fclsh_build: bucket tables of the part");
         PhaseTimer pt(idx, 1, s);
         for (uint64_t r0 = 0; r0 < L; r0 += rows) {
             const uint32_t nr = (uint32_t)std::min<uint64_t>(rows, L - r0);
@@ -989,6 +1004,7 @@ static fclsh_status check_radius(const fclsh_index *idx, uint32_t radius)
 extern "C" fclsh_status fclsh_query_async(fclsh_qctx *c, const uint64_t *queries, uint64_t nq, uint32_t radius,
                                           const uint32_t *radii, void *stream)
 {
+    NvtxRange nv("fclsh_query_async");
     if (!c || (!queries && nq)) return fail(FCLSH_EINVAL, "NULL argument");
     fclsh_index *idx = c->idx;
     fclsh_status st = check_radius(idx, radius);
@@ -1013,6 +1029,7 @@ extern "C" fclsh_status fclsh_query_async(fclsh_qctx *c, const uint64_t *queries
 
 extern "C" fclsh_status fclsh_qctx_wait(fclsh_qctx *c, fclsh_device_result *out)
 {
+    NvtxRange nv("fclsh_qctx_wait");
     if (!c) return fail(FCLSH_EINVAL, "NULL argument");
     fclsh_index *idx = c->idx;
     FCLSH_CUDA(cudaSetDevice(idx->device));
@@ -1154,6 +1171,7 @@ extern "C" fclsh_status fclsh_query(fclsh_index *idx, const uint64_t *queries, u
 extern "C" fclsh_status fclsh_query_plain(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
                                           void *stream, fclsh_result **out)
 {
+    NvtxRange nv("fclsh_query_plain");
     if (!idx || !out || (!queries && nq)) return fail(FCLSH_EINVAL, "NULL argument");
     *out = nullptr;
     fclsh_status st = check_radius(idx, radius);
