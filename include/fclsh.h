@@ -381,6 +381,15 @@ uint64_t fclsh_kernel_launches(void);
 fclsh_status fclsh_debug_fail_alloc(int64_t after);
 fclsh_status fclsh_debug_pool_used(uint64_t *bytes);
 
+/*
+ * Testing aid for the bounded waits (no counterpart in the paper): while `on`, the
+ * tensor-core hash kernel (hash_tile 2) never requests its first operand chunk, so
+ * its waits run out after about two seconds; the kernel then stops, releases its
+ * tensor memory and flags the index, and the call returns FCLSH_ETIMEOUT.  The
+ * device stays usable.
+ */
+fclsh_status fclsh_debug_withhold_hash_loads(int on);
+
 /* Thread-local description of the calling thread's last failure. */
 const char *fclsh_last_error(void);
 

@@ -1532,6 +1532,16 @@ extern "C" fclsh_status fclsh_load(const char *path, fclsh_index **out)
 
 extern "C" uint64_t fclsh_kernel_launches(void) { return launch_count(); }
 
+static std::atomic<uint32_t> g_withhold{0};
+
+uint32_t fclsh::debug_withhold_loads() { return g_withhold.load(); }
+
+extern "C" fclsh_status fclsh_debug_withhold_hash_loads(int on)
+{
+    g_withhold.store(on ? 1u : 0u);
+    return FCLSH_OK;
+}
+
 extern "C" fclsh_status fclsh_debug_fail_alloc(int64_t after)
 {
     g_fail_alloc.store(after < 0 ? -1 : after);

@@ -198,6 +198,10 @@ fclsh_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return fclsh::cuda_fail(e_, #call); \
     } while (0)
 
+// Testing aid (api.cu): nonzero while the tensor-core hash is told to withhold its first
+// operand copy, so that its bounded waits run out (fclsh_debug_withhold_hash_loads).
+uint32_t debug_withhold_loads();
+
 // ---- params.cpp
 uint32_t default_parts(uint32_t r);
 void algorithm1_rule(uint64_t n, uint32_t r, double c, uint32_t *t, uint32_t *rep);

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t
                                                                   uint32_t K, const uint16_t *__restrict__ gmat,
                                                                   uint32_t chunks, uint32_t L,
                                                                   uint64_t *__restrict__ keys, uint64_t ld,
-                                                                  uint32_t *status)
+                                                                  uint32_t *status, uint32_t withhold_first)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t gfull[2], afull[2], aempty[2];
@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t
             }
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             s_abort = 0;
-            bulk_load(gb(0), gmat, tile_bytes, &gfull[0]);
+            // withhold_first (tests of the bounded waits): chunk 0 is never requested, so the
+            // first waits run out and the kernel reports it in *status
+            if (!withhold_first) bulk_load(gb(0), gmat, tile_bytes, &gfull[0]);
             if (chunks > 1) bulk_load(gb(1), gmat + (size_t)K * kMmaN, tile_bytes, &gfull[1]);
         }
     } else {
@@ -369,7 +371,7 @@ cudaError_t launch_hash_mma(const uint32_t *coord, const uint16_t *gmat, uint32_
     if (once != cudaSuccess) return once;
     const uint64_t blocks = (cnt + kMmaM - 1) / kMmaM;
     hash_mma_kernel<<<(unsigned)blocks, kMmaThreads, smem, s>>>(pts, cnt, words, coord, K, gmat, hash_mma_chunks(W),
-                                                                 W - 1, keys, ld, status);
+                                                                 W - 1, keys, ld, status, debug_withhold_loads());
     note_launch();
     return cudaGetLastError();
 }

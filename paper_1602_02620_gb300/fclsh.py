@@ -106,6 +106,7 @@ SIGNATURES = {
     "fclsh_load": (_i, [ctypes.c_char_p, _vp]),
     "fclsh_debug_fail_alloc": (_i, [ctypes.c_int64]),
     "fclsh_debug_pool_used": (_i, [_vp]),
+    "fclsh_debug_withhold_hash_loads": (_i, [ctypes.c_int]),
     "fclsh_last_error": (ctypes.c_char_p, []),
     "fclsh_version": (ctypes.c_char_p, []),
 }
@@ -405,6 +406,11 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
 def debug_fail_alloc(after: int) -> None:
     """Make the after-th device allocation of the library fail as out of memory (< 0: off)."""
     _check(lib().fclsh_debug_fail_alloc(after))
+
+
+def debug_withhold_hash_loads(on: bool) -> None:
+    """Make the tensor-core hash kernel's bounded waits run out (tests of ETIMEOUT)."""
+    _check(lib().fclsh_debug_withhold_hash_loads(1 if on else 0))
 
 
 def debug_pool_used() -> int:
