@@ -159,6 +159,23 @@ fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t d, uint32_
 /* Release the index and all its device memory.  NULL is ignored. */
 void fclsh_free(fclsh_index *idx);
 
+/*
+ * Sparse points (no counterpart in the paper, which takes bit vectors): row i is the set
+ * of coordinates indices[indptr[i] .. indptr[i+1]) (CSR; any order, repeats allowed).
+ * fclsh_pack_sparse writes the n rows as bit vectors out[n][ceil(d/64)] (host or device;
+ * device work on `stream`, synchronous on return); fclsh_build_sparse packs them on the
+ * device and builds the index exactly as fclsh_build would from the packed rows.
+ *   indptr: host or device [n+1] uint64, non-decreasing, indptr[n] <= nnz.
+ *   indices: host or device [nnz] uint32, each < d.
+ * Errors: FCLSH_EINVAL for NULL pointers, d out of 1..262,144, bounds that run backwards
+ * or past nnz, or a coordinate >= d (detected on the device; nothing out of range is written).
+ */
+fclsh_status fclsh_pack_sparse(const uint64_t *indptr, const uint32_t *indices, uint64_t n, uint64_t nnz,
+                               uint32_t d, uint64_t *out, void *stream);
+fclsh_status fclsh_build_sparse(const uint64_t *indptr, const uint32_t *indices, uint64_t n, uint64_t nnz,
+                                uint32_t d, uint32_t r, uint64_t seed, const fclsh_build_opts *opts,
+                                fclsh_index **out);
+
 /* Sizes and derived parameters (Sec. 3.1: L = 2^(r'+1) - 1 tables per part). */
 fclsh_status fclsh_get_info(const fclsh_index *idx, fclsh_info *out);
 

@@ -36,6 +36,8 @@ cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned 
 cudaError_t launch_gather_runs(const uint32_t *runs, const uint64_t *run_base, const uint32_t *res_cnt,
                                const uint64_t *offs, uint64_t nq, uint64_t cap, uint32_t *ids, int sm_count, cudaStream_t s);
 size_t hash_smem_bytes(uint32_t W, uint32_t dk, uint32_t tile);
+cudaError_t launch_pack_sparse(const uint64_t *indptr, const uint32_t *indices, uint64_t n, uint64_t nnz, uint32_t d,
+                               uint64_t *out, uint32_t *bad, int sm_count, cudaStream_t s);
 
 // ---------------------------------------------------------------- errors
 
@@ -1376,6 +1378,69 @@ extern "C" fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64
         }
     }
     return FCLSH_OK;
+}
+
+// ---------------------------------------------------------------- sparse input
+
+extern "C" fclsh_status fclsh_pack_sparse(const uint64_t *indptr, const uint32_t *indices, uint64_t n, uint64_t nnz,
+                                          uint32_t d, uint64_t *out, void *stream)
+{
+    if ((n && (!indptr || !out)) || (nnz && !indices)) return fail(FCLSH_EINVAL, "NULL argument");
+    if (d == 0 || d > kMaxD) return fail(FCLSH_EINVAL, "d must be in 1..%u (got %u)", kMaxD, d);
+    if (n == 0) return FCLSH_OK;
+    int dev = 0;
+    FCLSH_CUDA(cudaGetDevice(&dev));
+    int sms = 0;
+    FCLSH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t words = (d + 63) / 64;
+    DevAllocs tmp;
+    cudaError_t e;
+    const uint64_t *dp = indptr;
+    const uint32_t *di = indices;
+    uint64_t *dout = out;
+    uint32_t *bad = nullptr;
+    if (!is_device_ptr(indptr)) {
+        uint64_t *p = nullptr;
+        if ((e = tmp.alloc(&p, n + 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(indptr)");
+        FCLSH_CUDA(cudaMemcpyAsync(p, indptr, (n + 1) * 8, cudaMemcpyHostToDevice, s));
+        dp = p;
+    }
+    if (nnz && !is_device_ptr(indices)) {
+        uint32_t *p = nullptr;
+        if ((e = tmp.alloc(&p, nnz)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(indices)");
+        FCLSH_CUDA(cudaMemcpyAsync(p, indices, nnz * 4, cudaMemcpyHostToDevice, s));
+        di = p;
+    }
+    const bool out_host = !is_device_ptr(out);
+    if (out_host && (e = tmp.alloc(&dout, n * words)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(points)");
+    if ((e = tmp.alloc(&bad, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+    FCLSH_CUDA(cudaMemsetAsync(bad, 0, 4, s));
+    FCLSH_CUDA(launch_pack_sparse(dp, di, n, nnz, d, dout, bad, sms, s));
+    uint32_t hb = 0;
+    FCLSH_CUDA(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
+    if (out_host) FCLSH_CUDA(cudaMemcpyAsync(out, dout, n * words * 8, cudaMemcpyDeviceToHost, s));
+    FCLSH_CUDA(cudaStreamSynchronize(s));
+    if (hb & 1) return fail(FCLSH_EINVAL, "indptr must be non-decreasing and end at most at nnz");
+    if (hb & 2) return fail(FCLSH_EINVAL, "a coordinate in indices is not below d = %u", d);
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_build_sparse(const uint64_t *indptr, const uint32_t *indices, uint64_t n, uint64_t nnz,
+                                           uint32_t d, uint32_t r, uint64_t seed, const fclsh_build_opts *opts,
+                                           fclsh_index **out)
+{
+    if (!out) return fail(FCLSH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n == 0 || n > 0xFFFFFFFFULL - 1) return fail(FCLSH_EINVAL, "n must be in 1..2^32-2 (got %llu)", (unsigned long long)n);
+    if (d == 0 || d > kMaxD) return fail(FCLSH_EINVAL, "d must be in 1..%u (got %u)", kMaxD, d);
+    DevAllocs tmp;
+    uint64_t *pts = nullptr;
+    cudaError_t e;
+    if ((e = tmp.alloc(&pts, n * ((d + 63) / 64))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(points)");
+    fclsh_status st = fclsh_pack_sparse(indptr, indices, n, nnz, d, pts, nullptr);
+    if (st != FCLSH_OK) return st;
+    return fclsh_build(pts, n, d, r, seed, opts, out);
 }
 
 // ---------------------------------------------------------------- save / load

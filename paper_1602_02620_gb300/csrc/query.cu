@@ -670,4 +670,48 @@ cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- sparse input
+
+// Rows given as lists of set coordinates (CSR: row i = indices[indptr[i] .. indptr[i+1]))
+// packed into bit vectors: one warp per row, each lane setting the bits of its entries
+// with atomic ORs into the zeroed row.  Entries past nnz, coordinates >= d and rows whose
+// bounds run backwards are skipped and flagged in *bad.
+__global__ void __launch_bounds__(256) pack_sparse_kernel(const uint64_t *__restrict__ indptr,
+                                                          const uint32_t *__restrict__ indices, uint64_t n,
+                                                          uint64_t nnz, uint32_t d, uint32_t words,
+                                                          unsigned long long *__restrict__ out, uint32_t *bad)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const uint64_t lo = indptr[i], hi = indptr[i + 1];
+        if (hi < lo || hi > nnz) {
+            if (lane == 0) atomicOr(bad, 1u);
+            continue;
+        }
+        unsigned long long *row = out + i * words;
+        for (uint64_t e = lo + lane; e < hi; e += 32) {
+            const uint32_t c = indices[e];
+            if (c >= d) {
+                atomicOr(bad, 2u);
+                continue;
+            }
+            atomicOr(row + (c >> 6), 1ULL << (c & 63));
+        }
+    }
+}
+
+cudaError_t launch_pack_sparse(const uint64_t *indptr, const uint32_t *indices, uint64_t n, uint64_t nnz, uint32_t d,
+                               uint64_t *out, uint32_t *bad, int sm_count, cudaStream_t s)
+{
+    const uint32_t words = (d + 63) / 64;
+    cudaError_t e = cudaMemsetAsync(out, 0, n * words * 8, s);
+    if (e != cudaSuccess || n == 0) return e;
+    const uint64_t blocks = std::min<uint64_t>((n + 7) / 8, (uint64_t)sm_count * 16);
+    pack_sparse_kernel<<<(unsigned)blocks, 256, 0, s>>>(indptr, indices, n, nnz, d, words,
+                                                        reinterpret_cast<unsigned long long *>(out), bad);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace fclsh

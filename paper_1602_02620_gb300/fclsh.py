@@ -103,6 +103,8 @@ SIGNATURES = {
     "fclsh_server_free": (None, [_vp]),
     "fclsh_kernel_launches": (_u64, []),
     "fclsh_save": (_i, [_vp, ctypes.c_char_p]),
+    "fclsh_pack_sparse": (_i, [_vp, _vp, _u64, _u64, _u32, _vp, _vp]),
+    "fclsh_build_sparse": (_i, [_vp, _vp, _u64, _u64, _u32, _u32, _u64, _vp, _vp]),
     "fclsh_load": (_i, [ctypes.c_char_p, _vp]),
     "fclsh_debug_fail_alloc": (_i, [ctypes.c_int64]),
     "fclsh_debug_pool_used": (_i, [_vp]),
@@ -384,6 +386,16 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
     build whose column lists do not fit takes 3.
     replicate repeats every vector that many times (Algorithm 1, cr < log n); approx_c > 0
     with neither t nor replicate set chooses both by Algorithm 1."""
+    keep = []
+    o = _build_opts(t=t, slot_bits=slot_bits, mem_budget=mem_budget, perm=perm, part_off=part_off, m=m, b=b,
+                    timing=timing, hash_tile=hash_tile, replicate=replicate, approx_c=approx_c, keep=keep)
+    h = ctypes.c_void_p()
+    _check(lib().fclsh_build(_ptr(points), _rows(points), d, r, seed, ctypes.byref(o), ctypes.byref(h)))
+    return Index(h)
+
+
+def _build_opts(t=None, slot_bits=None, mem_budget=None, perm=None, part_off=None, m=None, b=None,
+                timing=False, hash_tile=0, replicate=0, approx_c=0.0, keep=None) -> BuildOpts:
     o = BuildOpts()
     o.t = t or 0
     o.replicate = replicate or 0
@@ -392,15 +404,13 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
     o.mem_budget = mem_budget or 0
     o.timing = 1 if timing else 0
     o.hash_tile = hash_tile
-    keep = []
     if perm is not None:
         arrs = [np.ascontiguousarray(perm, np.uint32), np.ascontiguousarray(part_off, np.uint32),
                 np.ascontiguousarray(m, np.uint32), np.ascontiguousarray(b, np.uint64)]
-        keep += arrs
+        if keep is not None:
+            keep += arrs
         o.perm, o.part_off, o.m, o.b = (a.ctypes.data for a in arrs)
-    h = ctypes.c_void_p()
-    _check(lib().fclsh_build(_ptr(points), _rows(points), d, r, seed, ctypes.byref(o), ctypes.byref(h)))
-    return Index(h)
+    return o
 
 
 def debug_fail_alloc(after: int) -> None:
@@ -418,6 +428,29 @@ def debug_pool_used() -> int:
     v = ctypes.c_uint64()
     _check(lib().fclsh_debug_pool_used(ctypes.byref(v)))
     return int(v.value)
+
+
+def pack_sparse(indptr, indices, d: int, out=None, stream=None):
+    """fclsh_pack_sparse: CSR rows (numpy or torch CUDA) -> bit vectors [n][ceil(d/64)] uint64
+    (numpy unless `out` is given)."""
+    n = int(indptr.shape[0]) - 1
+    nnz = int(indices.shape[0])
+    if out is None:
+        out = np.zeros((max(n, 0), (d + 63) // 64), np.uint64)
+    _check(lib().fclsh_pack_sparse(_ptr(indptr), _ptr(indices), max(n, 0), nnz, d, _ptr(out), _stream(stream)))
+    return out
+
+
+def build_sparse(indptr, indices, d: int, r: int, seed: int, **kw) -> Index:
+    """fclsh_build_sparse: an index of CSR rows (indptr [n+1] uint64, indices [nnz] uint32);
+    keyword options as for build() (t, replicate, approx_c, slot_bits, hash_tile, timing)."""
+    keep = []
+    o = _build_opts(keep=keep, **kw)
+    h = ctypes.c_void_p()
+    n = int(indptr.shape[0]) - 1
+    _check(lib().fclsh_build_sparse(_ptr(indptr), _ptr(indices), n, int(indices.shape[0]), d, r, seed,
+                                    ctypes.byref(o), ctypes.byref(h)))
+    return Index(h)
 
 
 def load(path: str) -> Index:

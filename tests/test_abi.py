@@ -93,3 +93,16 @@ def test_load_rejects_bad_files_without_a_gpu(tmp_path):
     else:
         assert st == fclsh.OK
         lib.fclsh_free(h)
+
+
+def test_sparse_argument_errors_without_a_gpu():
+    import ctypes
+    from paper_1602_02620_gb300 import fclsh
+
+    lib = fclsh.lib()
+    h = ctypes.c_void_p()
+    assert lib.fclsh_pack_sparse(None, None, 3, 0, 64, None, None) == fclsh.EINVAL      # NULL rows
+    buf = (ctypes.c_uint64 * 4)()
+    assert lib.fclsh_pack_sparse(buf, buf, 1, 0, 0, buf, None) == fclsh.EINVAL           # d = 0
+    assert lib.fclsh_build_sparse(buf, buf, 0, 0, 64, 3, 1, None, ctypes.byref(h)) == fclsh.EINVAL   # n = 0
+    assert lib.fclsh_build_sparse(buf, buf, 1, 0, 300_000, 3, 1, None, ctypes.byref(h)) == fclsh.EINVAL
