@@ -471,6 +471,33 @@ def main():
         idx2.free()
     e2e = {"value": nq / statistics.median(e2e_t), "unit": "queries/s",
            "h2d_bytes_per_step": int(w.points.nbytes + w.queries.nbytes), "d2h_bytes_per_step": int(d2h)}
+    if workloads.CONFIGS[args.workload]["kind"] == "sparse_skewed":
+        # sparse data the way a user holds it: CSR rows of set coordinates, packed on the device
+        def csr(a):
+            bits = np.unpackbits(a.view(np.uint8).reshape(a.shape[0], -1), axis=1, bitorder="little")[:, : w.d]
+            rows, cols = np.nonzero(bits)
+            ptr = np.zeros(a.shape[0] + 1, np.uint64)
+            np.add.at(ptr, rows + 1, 1)
+            return (torch.from_numpy(np.cumsum(ptr).astype(np.uint64).view(np.int64)).pin_memory(),
+                    torch.from_numpy(cols.astype(np.uint32).view(np.int32)).pin_memory())
+        pi, pc = csr(w.points)
+        qi, qc = csr(w.queries)
+        qdev = torch.empty((nq, w.words), dtype=torch.int64, device="cuda")
+        e2e_s = []
+        for i in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            idx2 = fclsh.build_sparse(pi, pc, w.d, w.r, seed, hash_tile=tuned["hash_tile"])
+            idx2.set_tuning(**tuned)
+            fclsh.pack_sparse(qi, qc, w.d, out=qdev)
+            r2 = idx2.query(qdev, w.r)
+            e2e_s.append(time.perf_counter() - t0)
+            assert np.array_equal(r2.ids, res.ids)
+            idx2.free()
+        e2e["sparse_input"] = {"value": nq / statistics.median(e2e_s), "unit": "queries/s",
+                               "h2d_bytes_per_step": int(pi.numel() * 8 + pc.numel() * 4 + qi.numel() * 8 +
+                                                         qc.numel() * 4),
+                               "d2h_bytes_per_step": int(d2h)}
 
     qk_ms, qk_n = tq["query_kernel"]
     # ---- rooflines (HBM) of the build's kernels, from the CUDA events of the timed steps.

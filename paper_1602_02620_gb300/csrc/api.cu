@@ -774,6 +774,23 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
             (e = tmp.alloc(&sbuf.bin_cnt, rows * nd)) != cudaSuccess || (e = tmp.alloc(&sbuf.status, 1)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(segment bounds)");
     }
+    // Long points with the scatter sketch: their set coordinates are listed once (one pass over
+    // the packed words, ~4 B per set bit), and every part's sketch reads the list.
+    uint32_t *pidx = nullptr, *plen = nullptr;
+    uint64_t *pstart = nullptr;
+    if (idx->tune.hash_tile == 3 && idx->words >= kCsrMinWords) {
+        const uint64_t cap = n * idx->words * 2;   // room for one set bit in 32
+        unsigned long long *cursor = nullptr;
+        if ((e = tmp.alloc(&pidx, cap)) != cudaSuccess || (e = tmp.alloc(&pstart, n)) != cudaSuccess ||
+            (e = tmp.alloc(&plen, n)) != cudaSuccess || (e = tmp.alloc(&cursor, 1)) != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(set coordinates)");
+        FCLSH_CUDA(launch_extract_set_bits(idx->points, n, idx->words, d, cap, pidx, pstart, plen, cursor,
+                                           idx->sm_count, s));
+        unsigned long long total = 0;
+        FCLSH_CUDA(cudaMemcpyAsync(&total, cursor, 8, cudaMemcpyDeviceToHost, s));
+        FCLSH_CUDA(cudaStreamSynchronize(s));
+        if (total > cap) pidx = nullptr;   // denser than one bit in 32: the sketch reads the packed words
+    }
     // The partition path first partitions into fixed-capacity bins (no histogram pass).
     // A row chunk whose bins overflow (skewed keys) is partitioned again the exact way,
     // with a per-tile digit histogram, and the remaining chunks go that way at once.
@@ -783,7 +800,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         {
             NvtxRange nh("fclsh_build: hash part");
             PhaseTimer pt(idx, 0, s);
-            FCLSH_CUDA(launch_hash_part(idx, k, idx->points, n, keys, n, s));
+            FCLSH_CUDA(launch_hash_part(idx, k, idx->points, n, keys, n, s, pidx, pstart, plen));
         }
         NvtxRange ns("fclsh_build: bucket tables of the part");
         PhaseTimer pt(idx, 1, s);

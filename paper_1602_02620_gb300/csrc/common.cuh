@@ -23,6 +23,7 @@ constexpr uint32_t kPackedMaxD = 16384;   // coordinates the packed specific-con
 constexpr uint32_t kScatterMaxPop = 16383;
 constexpr uint32_t kS1ScatterPositions = 2048;   // parts at least this long: query sketch by scatter
 constexpr uint32_t kDirectMaxPositions = 4096;   // longest part of the direct route (hash_tile 4)
+constexpr uint32_t kCsrMinWords = 64;            // points of at least this many words: list set bits once per build
 constexpr uint32_t kWarpVerifyWords = 32;        // points of at least this many words: one warp per distance
 constexpr int kSortTile = 8192;       // radix-sort items per histogram tile (one block)
 constexpr int kSortSub = 2048;        // items per scatter sub-tile (256 threads x 8)
@@ -70,6 +71,11 @@ struct CoordLists {
     const uint32_t *col;
     const uint64_t *b;
     uint32_t d;                 // bits of a point; set bits past d are ignored
+    // optional: the points' set coordinates, point i's at pidx[pstart[i] .. pstart[i] + plen[i])
+    // (then the sketch reads these instead of the packed words)
+    const uint32_t *pidx = nullptr;
+    const uint64_t *pstart = nullptr;
+    const uint32_t *plen = nullptr;
 };
 
 struct PhaseTimer;
@@ -219,7 +225,16 @@ void column_lists(uint32_t D, uint32_t t, uint32_t W, const std::vector<uint32_t
 // ---- hash.cu: keys of `cnt` points for part k into keys[(v-1)*ld + i], v = 1..W-1
 // (the Walsh-Hadamard kernels for hash_tile 0/1, hash_mma.cu's contraction for 2)
 cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t *pts, uint64_t cnt,
-                             uint64_t *keys, uint64_t ld, cudaStream_t s);
+                             uint64_t *keys, uint64_t ld, cudaStream_t s,
+                             const uint32_t *pidx = nullptr, const uint64_t *pstart = nullptr,
+                             const uint32_t *plen = nullptr);
+// The points' set coordinates in one pass (warp per point): point i's at idx[start[i] ..
+// start[i] + len[i]), ascending, places reserved with an atomic on *cursor (which ends at
+// the total).  When the total passes cap, nothing past cap is written and the caller
+// keeps to the packed words.
+cudaError_t launch_extract_set_bits(const uint64_t *pts, uint64_t n, uint32_t words, uint32_t d, uint64_t cap,
+                                   uint32_t *idx, uint64_t *start, uint32_t *len, unsigned long long *cursor,
+                                   int sm_count, cudaStream_t s);
 
 // ---- hash_mma.cu
 uint32_t hash_mma_k(uint32_t W, uint32_t max_dk);   // 0: the contraction does not apply

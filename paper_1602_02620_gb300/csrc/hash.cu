@@ -162,6 +162,17 @@ __global__ void __launch_bounds__(128, 4) hash_small_scatter_kernel(const uint64
     for (uint32_t pi = 0; pi < 32; ++pi) {
         const uint32_t p = warp * 32 + pi;
         if (p0 + p >= cnt) break;
+        if (cl.pidx) {   // the point's set coordinates are listed: a lane per coordinate
+            const uint32_t *ci = cl.pidx + cl.pstart[p0 + p];
+            const uint32_t len = cl.plen[p0 + p];
+            for (uint32_t j = lane; j < len; j += 32) {
+                const uint32_t c = ci[j];
+                const uint32_t e1 = __ldg(cl.off + c + 1);
+                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
+                    atomicAdd(sk + (size_t)__ldg(cl.col + e) * NP + p, (unsigned long long)__ldg(cl.b + e));
+            }
+            continue;
+        }
         const uint64_t *x = pts + (p0 + p) * words;
         for (uint32_t w0 = lane; w0 < words; w0 += 128) {   // four words in flight per lane
             uint64_t wv[4];
@@ -374,8 +385,22 @@ __device__ __forceinline__ void scatter_sketch(uint64_t *sm, uint32_t W, const u
 {
     for (uint32_t i = threadIdx.x; i < W * (uint32_t)NP; i += blockDim.x) sm[i] = 0ULL;
     __syncthreads();
-    // items of the tile's real points only; eight words in flight per thread
     const uint64_t real = cnt - p0 < (uint64_t)NP ? cnt - p0 : (uint64_t)NP;
+    if (cl.pidx) {   // the points' set coordinates are listed: threads take them point by point
+        for (uint32_t p = 0; p < (uint32_t)real; ++p) {
+            const uint32_t *ci = cl.pidx + cl.pstart[p0 + p];
+            const uint32_t len = cl.plen[p0 + p];
+            for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
+                const uint32_t c = ci[j];
+                const uint32_t e1 = __ldg(cl.off + c + 1);
+                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(__ldg(cl.col + e), p)),
+                              (unsigned long long)__ldg(cl.b + e));
+            }
+        }
+        return;
+    }
+    // items of the tile's real points only; eight words in flight per thread
     const uint32_t items = (uint32_t)real * words;
     constexpr int U = 8;
     for (uint32_t it0 = threadIdx.x; it0 < items; it0 += U * blockDim.x) {
@@ -541,7 +566,8 @@ size_t hash_smem_bytes(uint32_t W, uint32_t dk, uint32_t tile)
 }
 
 cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t *pts, uint64_t cnt, uint64_t *keys,
-                             uint64_t ld, cudaStream_t s)
+                             uint64_t ld, cudaStream_t s, const uint32_t *pidx, const uint64_t *pstart,
+                             const uint32_t *plen)
 {
     if (cnt == 0) return cudaSuccess;
     const uint32_t dk = idx->part_off[k + 1] - idx->part_off[k];
@@ -568,7 +594,12 @@ cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t 
         return cudaGetLastError();
     }
     if (tl == 3 && !idx->scatter_ok()) return cudaErrorInvalidValue;
-    const CoordLists cl = tl == 3 ? idx->coords(k) : CoordLists{nullptr, nullptr, nullptr, 0};
+    CoordLists cl = tl == 3 ? idx->coords(k) : CoordLists{nullptr, nullptr, nullptr, 0};
+    if (tl == 3 && pidx) {
+        cl.pidx = pidx;
+        cl.pstart = pstart;
+        cl.plen = plen;
+    }
     switch (logw) {
     case 1: return launch_logw<1>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
     case 2: return launch_logw<2>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
@@ -583,6 +614,72 @@ cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t 
     case 11: return launch_logw<11>(dk, tl, pts, cnt, idx->words, pc, cl, keys, ld, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+namespace {
+
+// One warp per point: popcounts of its words (bits past d masked), one atomic reserving
+// the point's run, then the set coordinates written in ascending order, 32 words a step
+// with a warp scan of the lanes' counts.
+__global__ void __launch_bounds__(256) extract_set_bits_kernel(const uint64_t *__restrict__ pts, uint64_t n,
+                                                               uint32_t words, uint32_t d, uint64_t cap,
+                                                               uint32_t *__restrict__ idx, uint64_t *__restrict__ start,
+                                                               uint32_t *__restrict__ len, unsigned long long *cursor)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t lastmask = (d & 63) ? (1ULL << (d & 63)) - 1 : ~0ULL;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const uint64_t *x = pts + i * words;
+        uint32_t mine = 0;
+        for (uint32_t w = lane; w < words; w += 32) {
+            uint64_t v = __ldg(x + w);
+            if (w == words - 1) v &= lastmask;
+            mine += __popcll(v);
+        }
+        const uint32_t total = __reduce_add_sync(0xffffffffu, mine);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane == 0) {
+            start[i] = base;
+            len[i] = total;
+        }
+        if (base + total > cap) continue;   // no room: the caller keeps to the packed words
+        uint64_t at = base;
+        for (uint32_t w0 = 0; w0 < words; w0 += 32) {
+            const uint32_t w = w0 + lane;
+            uint64_t v = w < words ? __ldg(x + w) : 0ULL;
+            if (w == words - 1) v &= lastmask;
+            const uint32_t c = __popcll(v);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += u;
+            }
+            uint64_t pos = at + incl - c;
+            while (v) {
+                idx[pos++] = w * 64 + (uint32_t)(__ffsll((long long)v) - 1);
+                v &= v - 1;
+            }
+            at += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_extract_set_bits(const uint64_t *pts, uint64_t n, uint32_t words, uint32_t d, uint64_t cap,
+                                   uint32_t *idx, uint64_t *start, uint32_t *len, unsigned long long *cursor,
+                                   int sm_count, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    const uint64_t blocks = std::min<uint64_t>((n + 7) / 8, (uint64_t)sm_count * 16);
+    extract_set_bits_kernel<<<(unsigned)blocks, 256, 0, s>>>(pts, n, words, d, cap, idx, start, len, cursor);
+    note_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace fclsh

@@ -83,10 +83,11 @@ def test_highd_keys_tables_queries(cfg, n):
     (300, 7, 3, 1200),         # general construction per part
     (40_000, 4, None, 800),    # W = 32 over 40,000 positions (column lists too long to stage)
     (20_000, 13, 2, 900),      # W = 128, two parts of 10,000
+    (8_192, 4, None, 700),     # dense long points: too many set bits to list, the packed words are read
 ])
 def test_scatter_sketch_matches_oracle(d, r, t, n):
     rng = np.random.default_rng(d + r)
-    if d > 4096:   # sparse rows (a few hundred set bits), like the high-dimensional sets
+    if d > 8192:   # sparse rows (a few hundred set bits), like the high-dimensional sets
         pts = np.zeros((n, (d + 63) // 64), np.uint64)
         for i in range(n):
             for c in rng.choice(d, size=int(rng.integers(20, 300)), replace=False):
