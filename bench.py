@@ -124,7 +124,7 @@ def _cpu_worker(job):
     from paper_1602_02620_gb300 import workloads
 
     w = workloads.make(cfg, n=n, nq=nq)
-    p = oracle.derive_params(w.index_seed, w.d, w.r)
+    p = oracle.derive_params(w.index_seed, w.d, w.r, rep=workloads.build_options(cfg).get("replicate", 1))
     nqall = w.queries.shape[0]
     h0, q0 = (k * w.n) // cores, (k * nqall) // cores
     t0 = time.perf_counter()
@@ -321,7 +321,7 @@ def main():
     ap.add_argument("--nq", type=int, default=None, help="fewer queries of the same workload (profiling)")
     ap.add_argument("--hash-tile", type=int, default=None, choices=(0, 1, 2, 3, 4),
                     help="force the hash kernel (0/1: WHT tiles, 2: tensor-core contraction) instead of the tuned one")
-    ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 6, 7],
+    ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 6, 7, 8],
                     help="workload id (default: the n=1M d=128 r=8 plain workload)")
     args = ap.parse_args()
 
@@ -350,14 +350,15 @@ def main():
 
     # kernel shapes for this workload: autotuned once on a sample batch (cached)
     cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
-    idx0 = fclsh.build(pts, w.d, w.r, seed)
+    bopts = workloads.build_options(args.workload)   # e.g. replication
+    idx0 = fclsh.build(pts, w.d, w.r, seed, **bopts)
     tuned = idx0.autotune(qs[: min(nq, 4096)], w.r, cache)
     idx0.free()
     if args.hash_tile is not None:
         tuned["hash_tile"] = args.hash_tile
 
     def step(timing: bool):
-        idx = fclsh.build(pts, w.d, w.r, seed, timing=timing, hash_tile=tuned["hash_tile"])
+        idx = fclsh.build(pts, w.d, w.r, seed, timing=timing, hash_tile=tuned["hash_tile"], **bopts)
         idx.set_tuning(**tuned)
         idx.timing_enable(False)          # the query batch runs as a replayed CUDA graph
         ctx = idx.context()
@@ -405,7 +406,7 @@ def main():
     value = world * nq * args.steps / elapsed
 
     # ---- query phase alone (index resident), batched vs plain vs brute force
-    idx = fclsh.build(pts, w.d, w.r, seed, hash_tile=tuned["hash_tile"])
+    idx = fclsh.build(pts, w.d, w.r, seed, hash_tile=tuned["hash_tile"], **bopts)
     idx.set_tuning(**tuned)
     ctx = idx.context()
     for _ in range(3):
@@ -462,7 +463,7 @@ def main():
     for i in range(max(2, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        idx2 = fclsh.build(hp, w.d, w.r, seed, hash_tile=tuned["hash_tile"])
+        idx2 = fclsh.build(hp, w.d, w.r, seed, hash_tile=tuned["hash_tile"], **bopts)
         idx2.set_tuning(**tuned)
         r2 = idx2.query(hq, w.r)
         e2e_t.append(time.perf_counter() - t0)
@@ -487,7 +488,7 @@ def main():
         for i in range(max(2, args.steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            idx2 = fclsh.build_sparse(pi, pc, w.d, w.r, seed, hash_tile=tuned["hash_tile"])
+            idx2 = fclsh.build_sparse(pi, pc, w.d, w.r, seed, hash_tile=tuned["hash_tile"], **bopts)
             idx2.set_tuning(**tuned)
             fclsh.pack_sparse(qi, qc, w.d, out=qdev)
             r2 = idx2.query(qdev, w.r)

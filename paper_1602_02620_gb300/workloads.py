@@ -7,7 +7,7 @@ their shapes: uniform 128-bit image codes (SIFT-like), clustered 256-bit codes
 (text-like).  This module holds none of the index's arithmetic; the C part
 (``csrc/workloads.c``) only generates bits.
 
-Seven workloads (sizes as named):
+Eight workloads (sizes as named):
 
 ====  ==========  =====  ==  =========  ==========================================
 name  n           d      r   queries    data / queries
@@ -19,6 +19,7 @@ name  n           d      r   queries    data / queries
 5     8,000,000   256    16  stream     as 3; requests of U{1..4096} queries, radius in {4,8,12,16}
 6     40,000      28,102 29  1,000      sparse, skewed popularity, ~150 set bits (Enron-like); 10% near-dups
 7     234,834     140,214 13 2,000      sparse, skewed popularity, ~85 set bits (MovieLens-like); 10% near-dups
+8     1,000,000   128    2   10,000     as 2 with k in 0..2, indexed with 4 copies of each vector (Algorithm 1)
 ====  ==========  =====  ==  =========  ==========================================
 """
 from __future__ import annotations
@@ -98,7 +99,16 @@ CONFIGS = {
             kind="sparse_skewed", lmin=20, lmean=130, dup_frac=0.1, dup_k=(1, 29), plant=(0, 29)),
     7: dict(name="highd-movielens n=234834 d=140214 r=13", n=234_834, d=140_214, r=13, nq=2_000, seed=7,
             kind="sparse_skewed", lmin=15, lmean=70, dup_frac=0.1, dup_k=(1, 13), plant=(0, 13)),
+    # Algorithm 1's replication for a small radius: the bench workload's points at r = 2, four copies
+    # (the paper's synthetic setting for r = 2), 511 tables as at r = 8 without replication
+    8: dict(name="replicated n=1000000 d=128 r=2 (4 copies)", n=1_000_000, d=128, r=2, nq=10_000, seed=8,
+            kind="uniform", plant=(0, 2), build={"replicate": 4}),
 }
+
+
+def build_options(cfg_id: int) -> dict:
+    """Index options a workload is defined with (e.g. replication), as keyword arguments."""
+    return dict(CONFIGS[cfg_id].get("build", {}))
 
 
 @dataclass

@@ -28,7 +28,7 @@ def _popcount_rows(a: np.ndarray) -> np.ndarray:
     return _POP[a.view(np.uint8)].reshape(a.shape[0], -1).sum(axis=1)
 
 
-@pytest.mark.parametrize("cfg", [2, 3, 4, 5])
+@pytest.mark.parametrize("cfg", [2, 3, 4, 5, 8])
 def test_full_size_workload(cfg):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -40,16 +40,17 @@ def test_full_size_workload(cfg):
     qs, _ = wl.queries(cfg, pts, nq)
     seed = c["seed"] + 1000
     d, r = c["d"], c["r"]
-    p = oracle.derive_params(seed, d, r)
+    bopts = wl.build_options(cfg)                                 # e.g. replication
+    p = oracle.derive_params(seed, d, r, rep=bopts.get("replicate", 1))
     # the benchmark's launch configuration: kernel shapes and hash kernel from the autotuner
     # (the same cache file bench.py uses), then an index built with them
     pts_dev = torch.from_numpy(pts.view(np.int64)).cuda()
     q_dev = torch.from_numpy(qs.view(np.int64)).cuda()
     cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
-    idx0 = fclsh.build(pts_dev, d, r, seed)
+    idx0 = fclsh.build(pts_dev, d, r, seed, **bopts)
     tuned = idx0.autotune(q_dev[: min(nq, 4096)], r, cache)
     idx0.free()
-    idx = fclsh.build(pts_dev, d, r, seed, hash_tile=tuned["hash_tile"])
+    idx = fclsh.build(pts_dev, d, r, seed, hash_tile=tuned["hash_tile"], **bopts)
     idx.set_tuning(**tuned)
     assert idx.n == c["n"] and idx.T == p.T
 

@@ -78,3 +78,12 @@ def test_sparse_skewed_highd():
         q, meta = wl.queries(cfg, pts, 30)
         for i in np.nonzero(meta["planted"])[0]:
             assert oracle.hamming(pts[meta["src"][i]], q[i]) == meta["k"][i] <= c["r"]
+
+
+def test_replicated_workload_options():
+    """Workload 8 is workload 2's shape at r = 2, indexed with four copies (Algorithm 1)."""
+    assert wl.build_options(8) == {"replicate": 4}
+    assert wl.build_options(2) == {}
+    w = wl.make(8, n=2000, nq=20)
+    for i in np.nonzero(w.meta["planted"])[0]:
+        assert oracle.hamming(w.points[w.meta["src"][i]], w.queries[i]) == w.meta["k"][i] <= 2
