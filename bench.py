@@ -116,15 +116,25 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_WORKER_CACHE = {}
+
+
 def _cpu_worker(job):
     """One oracle process: time hashing (direct route) and linear-scan queries on its own
-    slice of the job for about budget_s seconds; returns the counts and the seconds taken."""
+    slice of the job for about budget_s seconds; returns the counts and the seconds taken.
+    The workload and its parameters are made once per process (a pool is reused across steps)."""
     cfg, n, nq, k, cores, budget_s = job
     import oracle
     from paper_1602_02620_gb300 import workloads
 
-    w = workloads.make(cfg, n=n, nq=nq)
-    p = oracle.derive_params(w.index_seed, w.d, w.r, rep=workloads.build_options(cfg).get("replicate", 1))
+    key = (cfg, n, nq)
+    if key not in _WORKER_CACHE:
+        w0 = workloads.make(cfg, n=n, nq=nq)
+        p0 = oracle.derive_params(w0.index_seed, w0.d, w0.r,
+                                  rep=workloads.build_options(cfg).get("replicate", 1))
+        _WORKER_CACHE.clear()
+        _WORKER_CACHE[key] = (w0, p0)
+    w, p = _WORKER_CACHE[key]
     nqall = w.queries.shape[0]
     h0, q0 = (k * w.n) // cores, (k * nqall) // cores
     t0 = time.perf_counter()
@@ -143,7 +153,7 @@ def _cpu_worker(job):
     return nh, th, nqs, tq, int(p.T)
 
 
-def cpu_baseline(cfg: int, n, nq, budget_s: float = 12.0, cores: int | None = None):
+def cpu_baseline(cfg: int, n, nq, budget_s: float = 12.0, cores: int | None = None, pool=None):
     """The CPU oracle as it stands, on a bounded sample of the same job, on the host's cores.
 
     Job = hash all n points into their T keys (direct route of the covering
@@ -158,11 +168,13 @@ def cpu_baseline(cfg: int, n, nq, budget_s: float = 12.0, cores: int | None = No
     w = workloads.make(cfg, n=n, nq=nq)
     cores = cores or os.cpu_count() or 1
     jobs = [(cfg, n, nq, k, cores, budget_s) for k in range(cores)]
-    if cores == 1:
+    if pool is not None:
+        res = pool.map(_cpu_worker, jobs)
+    elif cores == 1:
         res = [_cpu_worker(jobs[0])]
     else:
-        with mp.get_context("spawn").Pool(cores) as pool:
-            res = pool.map(_cpu_worker, jobs)
+        with mp.get_context("spawn").Pool(cores) as own:
+            res = own.map(_cpu_worker, jobs)
     hash_rate = sum(r[0] / r[1] for r in res)
     query_rate = sum(r[2] / r[3] for r in res)
     nqall = w.queries.shape[0]
@@ -287,24 +299,49 @@ def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: floa
             "one_at_a_time_p50_ms": st1["p50_ms"], "one_at_a_time_p99_ms": st1["p99_ms"]}
 
 
+def workload_config(w, tables: int, nq: int, name: str) -> dict:
+    """The `config` object of a JSON line (the same for both arms)."""
+    sb = 18
+    while sb < 32 and (1 << sb) < w.n:
+        sb += 1
+    pts_b = w.points.nbytes
+    index_b = tables * w.n * 8 + tables * ((1 << sb) + 4) * 4
+    return {"workload": name, "n": w.n, "d": w.d, "r": w.r, "tables": tables, "queries": nq,
+            "step": "build index from device-resident points + one batch of all queries",
+            "l2": "inputs and index larger than L2 (%.3g MB of points -> %.3g GB of keys, %.3g GB index)"
+                  % (pts_b / 1e6, w.n * tables * 8 / 1e9, index_b / 1e9)}
+
+
 def run_reference(args, rank: int):
+    """The CPU oracle timed on the host's cores on the same workload (one pool of spawned
+    processes for all steps; each step a bounded sample, the whole run a few minutes)."""
     if rank != 0:
         return
+    import multiprocessing as mp
+
+    import oracle
     from paper_1602_02620_gb300 import workloads
 
-    w = workloads.make(CFG)
+    w = workloads.make(args.workload, n=args.n, nq=args.nq)
+    T = oracle.derive_params(w.index_seed, w.d, w.r,
+                             rep=workloads.build_options(args.workload).get("replicate", 1)).T
+    total = args.warmup + args.steps
+    budget = max(0.5, min(4.0, 150.0 / max(total, 1)))   # seconds of oracle work per step
+    cores = os.cpu_count() or 1
     steps = []
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(CFG, None, None, budget_s=4.0)
-        if i >= args.warmup:
-            steps.append(cb)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for i in range(total):
+            cb = cpu_baseline(args.workload, args.n, args.nq, budget_s=budget, cores=cores, pool=pool)
+            if i >= args.warmup:
+                steps.append(cb)
     v = statistics.median(s["value"] for s in steps)
     cb = dict(steps[-1])
     cb["value"] = v
+    nq = int(w.queries.shape[0])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.queries.shape[0] / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * nq / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "d": w.d, "r": w.r, "queries": int(w.queries.shape[0])},
+            "config": workload_config(w, T, nq, w.name),
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -552,9 +589,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": line_name, "n": w.n, "d": w.d, "r": w.r, "tables": T, "queries": nq,
-                   "step": "build index from device-resident points + one batch of all queries",
-                   "l2": "inputs and index larger than L2 (16 MB points -> 4.1 GB keys, 6.1 GB index)"},
+        "config": workload_config(w, T, nq, line_name),
         "breakdown": {
             "build_hash_ms": hash_avg, "build_sort_ms": sort_ms / args.steps,
             "hash_roofline_frac": ach / peak,
