@@ -308,8 +308,8 @@ def workload_config(w, tables: int, nq: int, name: str) -> dict:
     index_b = tables * w.n * 8 + tables * ((1 << sb) + 4) * 4
     return {"workload": name, "n": w.n, "d": w.d, "r": w.r, "tables": tables, "queries": nq,
             "step": "build index from device-resident points + one batch of all queries",
-            "l2": "inputs and index larger than L2 (%.3g MB of points -> %.3g GB of keys, %.3g GB index)"
-                  % (pts_b / 1e6, w.n * tables * 8 / 1e9, index_b / 1e9)}
+            "l2": "inputs and index %s than L2 (129 MB): %.3g MB of points -> %.3g GB of keys, %.3g GB index"
+                  % ("larger" if index_b > 129e6 else "smaller", pts_b / 1e6, w.n * tables * 8 / 1e9, index_b / 1e9)}
 
 
 def run_reference(args, rank: int):
