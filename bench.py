@@ -552,11 +552,14 @@ def main():
     hash_stage = {2: ("hash_mma_kernel (tensor-core contraction, all W-1 keys per point)", "hash_mma"),
                   3: ("hash_tile_kernel (Algorithm 2, sketch scattered from set bits)", "hash_scatter")}.get(
         tuned["hash_tile"], ("hash_tile_kernel (Algorithm 2, all W-1 keys per point)", "hash"))
+    dbits = info["slot_bits"] - 12   # partition digit bits: a segment spans 4,096 slots
+    part_name = ("partition_scatter_kernel (partition by the top 8 slot bits into bins, packed output)" if dbits == 8
+                 else "partition_wide_kernel<%d> (partition by the top %d slot bits into bins, packed output)"
+                 % (dbits, dbits))
     stages = {
         hash_stage[0]: (acc["build_hash"], w.n * (w.d / 8 + 8 * L), hash_stage[1]),
-        "partition_scatter_kernel (partition by the top 8 slot bits into bins, packed output)":
-            (acc["build_partition"], 16 * entries, "scatter"),
-        "radix_hist_kernel + scan (partition histogram)": (acc["build_partition_hist"], 8 * entries, "hist"),
+        part_name: (acc["build_partition"], 16 * entries, "scatter" if dbits == 8 else "scatter_wide"),
+        "partition histogram + scan (exact fallback)": (acc["build_partition_hist"], 8 * entries, "hist"),
         "segment finish (segment_one_kernel + segment_finish_kernel)":
             (acc["build_finish"], 16 * entries + 4 * slots, "finish"),
     }

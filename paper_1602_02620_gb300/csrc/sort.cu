@@ -686,19 +686,22 @@ __global__ void __launch_bounds__(256) segment_bounds_kernel(const uint32_t *__r
                                                              uint32_t dbits, uint32_t *__restrict__ seg_out)
 {
     const uint32_t row = blockIdx.x, tid = threadIdx.x;
-    const uint32_t nd = 1u << dbits, per = nd / 256;
+    const uint32_t nd = 1u << dbits, per = nd >= 256 ? nd / 256 : 1;
+    const bool owner = tid * per < nd;   // fewer segments than threads: the first nd threads take one each
     uint32_t *out = seg_out + (uint64_t)row * (nd + 1);
     if (bin_cnt) {
         const uint32_t *c = bin_cnt + (uint64_t)row * nd + tid * per;
         uint32_t mine = 0;
-        for (uint32_t i = 0; i < per; ++i) mine += c[i];
+        if (owner)
+            for (uint32_t i = 0; i < per; ++i) mine += c[i];
         uint32_t tot;
         uint32_t run = block_excl_scan<uint32_t>(mine, &tot);
-        for (uint32_t i = 0; i < per; ++i) {
-            out[tid * per + i] = run;
-            run += c[i];
-        }
-    } else {
+        if (owner)
+            for (uint32_t i = 0; i < per; ++i) {
+                out[tid * per + i] = run;
+                run += c[i];
+            }
+    } else if (owner) {
         for (uint32_t i = 0; i < per; ++i)
             out[tid * per + i] = hist[(((uint64_t)row << dbits) + tid * per + i) * tiles] - (uint32_t)((uint64_t)row * n);
     }
@@ -934,7 +937,7 @@ static cudaError_t scatter_smem_init()
 size_t sort_hist_entries(uint32_t rows, uint64_t len, uint32_t dbits)
 {
     const uint64_t tiles = (len + kSortTile - 1) / kSortTile;
-    const uint64_t wide = dbits > 8 ? ((uint64_t)1 << dbits) * ((len + kWideTile - 1) / kWideTile) : 0;
+    const uint64_t wide = dbits != 8 ? ((uint64_t)1 << dbits) * ((len + kWideTile - 1) / kWideTile) : 0;
     return (size_t)rows * std::max<uint64_t>(256 * tiles, wide);
 }
 
@@ -1041,7 +1044,9 @@ bool msd_path_applies(uint32_t slot_bits, uint64_t n)
     return slot_bits >= 11 && slot_bits <= 23 && id_bits(n) <= slot_bits + 2;
 }
 
-uint32_t msd_dbits(uint32_t slot_bits) { return slot_bits <= 20 ? 8u : slot_bits - (uint32_t)kSubMaxBits; }
+// Partition digits: a segment always spans 2^12 = 4,096 directory slots (s = 18..23: 6..11 digit
+// bits; 8-bit digits take partition_scatter_kernel, the others partition_wide_kernel).
+uint32_t msd_dbits(uint32_t slot_bits) { return slot_bits - (uint32_t)kSubMaxBits; }
 
 cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
                                cudaStream_t s)
@@ -1053,6 +1058,8 @@ cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t 
                 rows, sb, id_bits(len)};
     const dim3 grid(tiles, rows);
     switch (dbits) {
+    case 6: wide_hist_kernel<6><<<grid, kWideThreads, 0, s>>>(a); break;
+    case 7: wide_hist_kernel<7><<<grid, kWideThreads, 0, s>>>(a); break;
     case 8: radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a); break;
     case 9: wide_hist_kernel<9><<<grid, kWideThreads, 0, s>>>(a); break;
     case 10: wide_hist_kernel<10><<<grid, kWideThreads, 0, s>>>(a); break;
@@ -1085,8 +1092,14 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
         const dim3 grid(tiles, rows);
         constexpr size_t smem = (size_t)kWideSub * 12;
         static cudaError_t once = [] {   // static digit tables + dynamic sub-tile exceed 48 KB
-            cudaError_t r = cudaFuncSetAttribute(partition_wide_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t r = cudaFuncSetAttribute(partition_wide_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(partition_wide_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(partition_wide_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
             if (r == cudaSuccess)
                 r = cudaFuncSetAttribute(partition_wide_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -1096,7 +1109,11 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
             return r;
         }();
         if (once != cudaSuccess) return once;
-        if (dbits == 9)
+        if (dbits == 6)
+            partition_wide_kernel<6><<<grid, kWideThreads, smem, s>>>(a);
+        else if (dbits == 7)
+            partition_wide_kernel<7><<<grid, kWideThreads, smem, s>>>(a);
+        else if (dbits == 9)
             partition_wide_kernel<9><<<grid, kWideThreads, smem, s>>>(a);
         else if (dbits == 10)
             partition_wide_kernel<10><<<grid, kWideThreads, smem, s>>>(a);
