@@ -507,3 +507,61 @@ def test_row_restricted_query_equals_linear_scan(d, r, t):
             assert ncoll <= fcoll and ncand <= fcand and ncoll >= ncand >= len(ids)
             if rows == p.W - 1:
                 assert (ncoll, ncand) == (fcoll, fcand)
+
+
+@pytest.mark.parametrize("d,r,t,rep", [(64, 3, 1, 1), (96, 12, 2, 1), (32, 2, 1, 3), (128, 6, 1, 1)])
+def test_counters_follow_their_definitions(d, r, t, rep):
+    """#Collisions and #Candidates of Sec. 4.1, recomputed from their definitions: the number
+    of (table, point) pairs whose key equals the query's in that table, and the number of
+    distinct points among them -- with the keys from the Algorithm 2 route and plain numpy
+    (the oracle's query takes the direct route's tables and its own merge)."""
+    rng = np.random.default_rng(d + r + rep)
+    words = (d + 63) // 64
+    n = 300
+    pts = rng.integers(0, 2**63, size=(n, words), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    pts[10:20] = pts[3]                                # repeated points collide in every table
+    p = oracle.derive_params(d + 7, d, r, t=t, rep=rep)
+    tables = oracle.build_tables(p, pts)
+    keys = oracle.keys_fht(p, pts)                     # [T][n]
+    for qi in range(12):
+        q = pts[rng.integers(0, n)].copy()
+        for pos in rng.choice(d, size=rng.integers(0, r + 3), replace=False):
+            q[pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+        qk = oracle.keys_fht(p, q)[:, 0]
+        hit = keys == qk[:, None]                      # [T][n]: point collides with q in the table
+        for rows in (0, oracle.probe_rows(p, r // 2)):
+            sel = hit if rows == 0 else hit.reshape(p.t, p.L, n)[:, :rows, :].reshape(-1, n)
+            ids, ncoll, ncand = oracle.query(p, pts, tables, q, r // 2 if rows else r, rows=rows)
+            assert ncoll == int(sel.sum())
+            assert ncand == int(sel.any(axis=0).sum())
+
+
+def test_oracle_routes_agree_on_random_parameters():
+    """Lemma 3 (direct route == Algorithm 2) and total recall on parameters drawn at random
+    (dimension, radius, parts or copies, seed)."""
+    hypothesis = pytest.importorskip("hypothesis")
+    st = hypothesis.strategies
+
+    @hypothesis.settings(max_examples=40, deadline=None)
+    @hypothesis.given(d=st.integers(1, 200), r=st.integers(0, 12), parts=st.integers(1, 3),
+                      rep=st.integers(1, 3), seed=st.integers(0, 2**40))
+    def check(d, r, parts, rep, seed):
+        t = min(parts, d) if rep == 1 else 1
+        if (r * rep) // t > 6:                         # keep W <= 128 so that the case stays fast
+            return
+        p = oracle.derive_params(seed, d, r, t=t, rep=rep)
+        rng = np.random.default_rng(seed % 1000)
+        words = (d + 63) // 64
+        pts = rng.integers(0, 2**63, size=(8, words), dtype=np.uint64)
+        if d % 64:
+            pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+        kd, kf = oracle.keys_direct(p, pts), oracle.keys_fht(p, pts)
+        assert np.array_equal(kd, kf)
+        y = pts[:1].copy()                              # a point within r of pts[0] collides somewhere
+        for pos in rng.choice(d, size=min(d, r), replace=False):
+            y[0, pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+        assert (oracle.keys_direct(p, y)[:, 0] == kd[:, 0]).any()
+
+    check()
