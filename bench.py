@@ -301,7 +301,7 @@ def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: floa
 
 def workload_config(w, tables: int, nq: int, name: str) -> dict:
     """The `config` object of a JSON line (the same for both arms)."""
-    sb = 18
+    sb = 13
     while sb < 32 and (1 << sb) < w.n:
         sb += 1
     pts_b = w.points.nbytes

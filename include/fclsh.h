@@ -54,7 +54,9 @@ typedef struct fclsh_server fclsh_server; /* opaque; continuous-batching request
 typedef struct {
     uint32_t t;               /* parts (Algorithm 1); 0 = paper's rule: 1 for r < 10, 2 for 10 <= r <= 21,
                                  else the smallest t with floor(r/t) <= 10 */
-    uint32_t slot_bits;       /* bucket-directory slots per table = 2^slot_bits; 0 = max(18, ceil(log2 n)) */
+    uint32_t slot_bits;       /* bucket-directory slots per table = 2^slot_bits, 13..32; 0 = max(13, ceil(log2 n)).
+                                 Below 18 a directory entry keeps 14 + slot_bits id bits, so slot_bits must
+                                 leave room for the ids of all n points */
     uint64_t mem_budget;      /* bytes for transient build buffers; 0 = 1/4 of free device memory */
     /* Explicit random choices (all four set, or all NULL to draw them from `seed`), over the
        D = d * replicate positions of the (replicated) vector:

@@ -430,6 +430,7 @@ static QueryArgs make_args(fclsh_index *idx)
     a.inline_len = idx->tune.inline_probe;
     a.probe_rows = idx->tune.probe_rows;
     a.rep = idx->rep;
+    a.ent_ib = idx->ent_ib;
     a.d = idx->d;
     // long parts: the query's sketch from its set bits (O(nnz)) rather than from every position
     a.s1_scatter = idx->scatter_ok() && idx->positions() / idx->t >= kS1ScatterPositions;
@@ -681,12 +682,17 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         return fail(FCLSH_EINVAL, "hash_tile 4 (direct route) needs parts of at most %u positions", kDirectMaxPositions);
 
     uint32_t sb = o.slot_bits;
-    if (!sb) {
-        sb = 18;
+    if (!sb) {   // about one slot per point
+        sb = 13;
         while (sb < 32 && (1ULL << sb) < n) ++sb;
     }
-    if (sb < 18 || sb > 32) return fail(FCLSH_EINVAL, "slot_bits must be in 18..32");
+    if (sb < 13 || sb > 32) return fail(FCLSH_EINVAL, "slot_bits must be in 13..32");
+    // an entry holds the key's top 50 - s bits above the id: below s = 18 the id gets 14 + s bits
+    if (bits_for(n) > entry_id_bits(sb))
+        return fail(FCLSH_EINVAL, "slot_bits %u leaves %u id bits, too few for %llu points", sb, entry_id_bits(sb),
+                    (unsigned long long)n);
     idx->slot_bits = sb;
+    idx->ent_ib = entry_id_bits(sb);
 
     std::vector<uint32_t> col_off, coord;
     std::vector<uint64_t> bval;
@@ -952,9 +958,11 @@ extern "C" fclsh_status fclsh_bucket(const fclsh_index *idx, uint32_t table, uin
                               cudaMemcpyDeviceToHost));
     // the bucket: the slot's entries with equal high key bits (their order in the run is unspecified)
     std::vector<uint32_t> ids;
-    const uint32_t fp = (uint32_t)(key >> idx->slot_bits);
+    const uint64_t fp = key >> idx->slot_bits;
+    const uint32_t ib = idx->ent_ib;
+    const uint64_t idmask = (1ULL << ib) - 1;
     for (uint64_t e : ent)
-        if ((uint32_t)(e >> 32) == fp && key < kP) ids.push_back((uint32_t)e);
+        if ((e >> ib) == fp && key < kP) ids.push_back((uint32_t)(e & idmask));
     std::sort(ids.begin(), ids.end());
     for (uint64_t i = 0; i < ids.size() && i < cap; ++i) ids_out[i] = ids[i];
     *count = ids.size();
@@ -971,10 +979,12 @@ extern "C" fclsh_status fclsh_export_table(const fclsh_index *idx, uint32_t tabl
     FCLSH_CUDA(cudaMemcpy(offs.data(), idx->offs + (uint64_t)table * idx->offs_stride(), offs.size() * 4,
                           cudaMemcpyDeviceToHost));
     FCLSH_CUDA(cudaMemcpy(ent.data(), idx->ent + (uint64_t)table * idx->n, idx->n * 8, cudaMemcpyDeviceToHost));
+    const uint32_t ib = idx->ent_ib;
+    const uint64_t idmask = (1ULL << ib) - 1;
     for (uint64_t sl = 0; sl < idx->slots(); ++sl)
         for (uint32_t e = offs[sl]; e < offs[sl + 1]; ++e) {
-            keys_out[e] = ((ent[e] >> 32) << idx->slot_bits) | sl;
-            ids_out[e] = (uint32_t)ent[e];
+            keys_out[e] = ((ent[e] >> ib) << idx->slot_bits) | sl;
+            ids_out[e] = (uint32_t)(ent[e] & idmask);
         }
     return FCLSH_OK;
 }

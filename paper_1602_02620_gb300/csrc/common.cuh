@@ -88,6 +88,7 @@ struct QueryArgs {
     uint32_t probe_rows;          // 1: probe only the code rows v < 2^(floor(radius*rep/t)+1) of each part
     uint32_t rep;                 // replication factor of Algorithm 1 (1 = none)
     uint32_t d;                   // bits per point
+    uint32_t ent_ib;              // id bits of a directory entry: entry = (key >> slot_bits) << ent_ib | id
     // S1 by scattering the query's set bits through the coordinate lists (long parts),
     // else by walking the column lists
     uint32_t s1_scatter;
@@ -114,6 +115,18 @@ struct QueryArgs {
     uint32_t *bitmaps;            // [gridDim.x][bm_words]
     uint64_t bm_words;
 };
+
+// A directory entry holds the key's high 50 - s bits above an ent_ib-bit id: 32 id bits
+// from s = 18 on, 14 + s below (so that the entry stays within 64 bits).
+__host__ __device__ __forceinline__ uint32_t entry_id_bits(uint32_t slot_bits)
+{
+    return slot_bits >= 18 ? 32u : 14u + slot_bits;
+}
+__device__ __forceinline__ uint64_t entry_fp(uint64_t en, uint32_t ib) { return en >> ib; }
+__device__ __forceinline__ uint32_t entry_id(uint64_t en, uint32_t ib)
+{
+    return (uint32_t)(en & ((1ULL << ib) - 1));
+}
 
 // Code rows a query of this radius probes in every part: all W-1, or with
 // probe_rows only v = 1..2^(floor(radius*rep/t)+1)-1 (a point within the radius is
@@ -144,6 +157,7 @@ struct fclsh_index {
     uint64_t n = 0;
     uint32_t d = 0, words = 0, r = 0, t = 0, rp = 0, W = 0, T = 0, slot_bits = 0;
     uint32_t rep = 1;                // Algorithm 1 replication: positions D = d * rep, position i reads coordinate perm[i]
+    uint32_t ent_ib = 32;            // id bits of a directory entry (entry_id_bits(slot_bits))
     uint64_t P = fclsh::kP;
     // host copy of the random choices, one entry per position ([D])
     std::vector<uint32_t> perm, part_off, m;

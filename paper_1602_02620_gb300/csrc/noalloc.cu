@@ -76,15 +76,15 @@ __global__ void __launch_bounds__(256) noalloc_probe_kernel(QueryArgs a, Noalloc
     if (j >= a.t * nt) return;
     const uint32_t tau = probed_table(j, nt, a.W - 1);
     const uint64_t key = sc.keys[tau];
-    const uint32_t fp = (uint32_t)(key >> a.slot_bits);
+    const uint64_t fp = key >> a.slot_bits;
     const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & ((1ULL << a.slot_bits) - 1));
     const uint32_t lo = O[0], hi = O[1];
     const uint64_t *row = a.ent + (uint64_t)tau * a.n;
     unsigned long long coll = 0, cand = 0;
     for (uint32_t e = lo; e < hi; ++e) {
         const uint64_t en = row[e];
-        if ((uint32_t)(en >> 32) != fp) continue;
-        const uint32_t id = (uint32_t)en;
+        if (entry_fp(en, a.ent_ib) != fp) continue;
+        const uint32_t id = entry_id(en, a.ent_ib);
         coll++;
         const uint32_t bit = 1u << (id & 31);
         if (atomicOr(sc.cand_bm + (id >> 5), bit) & bit) continue;
@@ -188,6 +188,7 @@ extern "C" fclsh_status fclsh_query_plain_noalloc(const fclsh_index *cidx, const
     a.T = idx->T;
     a.probe_rows = idx->tune.probe_rows;
     a.rep = idx->rep;
+    a.ent_ib = idx->ent_ib;
     a.slot_bits = idx->slot_bits;
     a.offs = idx->offs;
     a.offs_stride = idx->offs_stride();

@@ -333,15 +333,15 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             const bool has = j < Tq;
             const uint32_t tau = has ? probed_table(j, nt, L) : 0;
             const uint32_t lo = has ? lo_s[j] : 0, len = has ? len_s[j] : 0;
-            const uint32_t fp = has ? (uint32_t)(keys_s[tau] >> a.slot_bits) : 0;
+            const uint64_t fp = has ? keys_s[tau] >> a.slot_bits : 0;
             const uint64_t *row = a.ent + (uint64_t)tau * a.n;
             const uint32_t short_len = len <= a.inline_len ? len : 0;
             const uint32_t maxs = __reduce_max_sync(0xffffffffu, short_len);
             for (uint32_t e = 0; e < maxs; ++e) {
                 const bool act = e < short_len;
                 const uint64_t en = act ? __ldg(row + lo + e) : 0;
-                process_entry(a, q_s, hset, bm, mode, radius, act && (uint32_t)(en >> 32) == fp,
-                              (uint32_t)en, c, res_s, &s_nres);
+                process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == fp,
+                              entry_id(en, a.ent_ib), c, res_s, &s_nres);
             }
             uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
             while (lmask) {
@@ -349,15 +349,15 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                 lmask &= lmask - 1;
                 const uint32_t l_lo = __shfl_sync(0xffffffffu, lo, src);
                 const uint32_t l_len = __shfl_sync(0xffffffffu, len, src);
-                const uint32_t l_fp = __shfl_sync(0xffffffffu, fp, src);
+                const uint64_t l_fp = __shfl_sync(0xffffffffu, fp, src);
                 const uint32_t l_tau = __shfl_sync(0xffffffffu, tau, src);
                 const uint64_t *lrow = a.ent + (uint64_t)l_tau * a.n + l_lo;
                 for (uint32_t cbase = 0; cbase < l_len; cbase += 32) {
                     const uint32_t e = cbase + lane;
                     const bool act = e < l_len;
                     const uint64_t en = act ? __ldg(lrow + e) : 0;
-                    process_entry(a, q_s, hset, bm, mode, radius, act && (uint32_t)(en >> 32) == l_fp,
-                                  (uint32_t)en, c, res_s, &s_nres);
+                    process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == l_fp,
+                                  entry_id(en, a.ent_ib), c, res_s, &s_nres);
                 }
             }
         }
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             for (uint32_t j = tid; j < Tq; j += B) {
                 const uint64_t *row = a.ent + (uint64_t)probed_table(j, nt, L) * a.n + lo_s[j];
                 const uint32_t len = len_s[j];
-                for (uint32_t e = 0; e < len; ++e) bm[(uint32_t)__ldg(row + e) >> 5] = 0;
+                for (uint32_t e = 0; e < len; ++e) bm[entry_id(__ldg(row + e), a.ent_ib) >> 5] = 0;
             }
             __syncthreads();
         }
@@ -418,11 +418,11 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                 const uint32_t tau = probed_table(j, nt, L);
                 const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[j];
                 const uint32_t len = len_s[j];
-                const uint32_t fp = (uint32_t)(keys_s[tau] >> a.slot_bits);
+                const uint64_t fp = keys_s[tau] >> a.slot_bits;
                 for (uint32_t e = 0; e < len; ++e) {
                     const uint64_t en = __ldg(row + e);
-                    if ((uint32_t)(en >> 32) != fp) continue;
-                    const uint32_t id = (uint32_t)en;
+                    if (entry_fp(en, a.ent_ib) != fp) continue;
+                    const uint32_t id = entry_id(en, a.ent_ib);
                     if (distance_to(a, q_s, id) <= radius) atomicOr(bm + (id >> 5), 1u << (id & 31));
                 }
             }
@@ -485,15 +485,15 @@ __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uin
     const uint32_t tau = probed_table(j, nt, a.W - 1);
     const uint64_t smask = (1ULL << a.slot_bits) - 1;
     const uint64_t key = keys[tau];
-    const uint32_t fp = (uint32_t)(key >> a.slot_bits);
+    const uint64_t fp = key >> a.slot_bits;
     const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
     const uint32_t lo = O[0], hi = O[1];
     const uint64_t *row = a.ent + (uint64_t)tau * a.n;
     unsigned long long coll = 0, cand = 0;
     for (uint32_t e = lo; e < hi; ++e) {
         const uint64_t en = row[e];
-        if ((uint32_t)(en >> 32) != fp) continue;
-        const uint32_t id = (uint32_t)en;
+        if (entry_fp(en, a.ent_ib) != fp) continue;
+        const uint32_t id = entry_id(en, a.ent_ib);
         coll++;
         const uint32_t bit = 1u << (id & 31);
         if (atomicOr(bitmap + (id >> 5), bit) & bit) continue;

@@ -1,7 +1,7 @@
 // sort.cu -- the bucket build (Sec. 2.2: only non-empty buckets are kept, one
 // table per hash function) and the device-wide scans.
 //
-// Directory of a table: entries (key >> slot_bits) << 32 | id grouped by slot
+// Directory of a table: entries (key >> slot_bits) << entry_id_bits(slot_bits) | id grouped by slot
 // (key mod 2^slot_bits) and, for every slot, the index of its first entry.  A
 // query reads its slot, compares the stored high key bits and takes the ids of
 // equal keys: its bucket.  Two builds give it:
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restric
     uint32_t *O = offs + (uint64_t)row * dir_stride(sb);
     const uint64_t key = Kr[e];
     const uint64_t sl = key & mask;
-    ent[(uint64_t)row * len + e] = ((key >> sb) << 32) | ids[(uint64_t)row * len + e];
+    ent[(uint64_t)row * len + e] = ((key >> sb) << entry_id_bits(sb)) | ids[(uint64_t)row * len + e];
     const uint64_t first = (e == 0) ? 0 : (Kr[e - 1] & mask) + 1;
     for (uint64_t s2 = first; s2 <= sl; ++s2) O[s2] = (uint32_t)e;
     if (e == len - 1)
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
     __syncthreads();
     for (uint32_t i = tid; i < cn; i += kOneThreads) {
         const uint64_t x = ck[i];
-        E[i] = ((x & low52) >> idbits) << 32 | (x & idmask);
+        E[i] = ((x & low52) >> idbits) << entry_id_bits(sb) | (x & idmask);
     }
 }
 
@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const ui
     uint64_t *E = ent + rowbase + seg_lo;
     uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;
     auto sub_of = [&](uint64_t v) { return (uint32_t)(v >> 52) & smask; };
-    auto ent_of = [&](uint64_t v) { return ((v & low52) >> idbits) << 32 | (v & idmask); };
+    auto ent_of = [&](uint64_t v) { return ((v & low52) >> idbits) << entry_id_bits(sb) | (v & idmask); };
     if (g == nd - 1 && tid == 0) O[nsub] = (uint32_t)n;
 
     // several chunks: per-slot counts of the whole segment first, then stable passes
@@ -1044,7 +1044,7 @@ bool msd_path_applies(uint32_t slot_bits, uint64_t n)
     return slot_bits >= 11 && slot_bits <= 23 && id_bits(n) <= slot_bits + 2;
 }
 
-// Partition digits: a segment always spans 2^12 = 4,096 directory slots (s = 18..23: 6..11 digit
+// Partition digits: a segment always spans 2^12 = 4,096 directory slots (s = 13..23: 1..11 digit
 // bits; 8-bit digits take partition_scatter_kernel, the others partition_wide_kernel).
 uint32_t msd_dbits(uint32_t slot_bits) { return slot_bits - (uint32_t)kSubMaxBits; }
 
@@ -1058,6 +1058,11 @@ cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t 
                 rows, sb, id_bits(len)};
     const dim3 grid(tiles, rows);
     switch (dbits) {
+    case 1: wide_hist_kernel<1><<<grid, kWideThreads, 0, s>>>(a); break;
+    case 2: wide_hist_kernel<2><<<grid, kWideThreads, 0, s>>>(a); break;
+    case 3: wide_hist_kernel<3><<<grid, kWideThreads, 0, s>>>(a); break;
+    case 4: wide_hist_kernel<4><<<grid, kWideThreads, 0, s>>>(a); break;
+    case 5: wide_hist_kernel<5><<<grid, kWideThreads, 0, s>>>(a); break;
     case 6: wide_hist_kernel<6><<<grid, kWideThreads, 0, s>>>(a); break;
     case 7: wide_hist_kernel<7><<<grid, kWideThreads, 0, s>>>(a); break;
     case 8: radix_hist_kernel<<<grid, kSortThreads, 0, s>>>(a); break;
@@ -1092,35 +1097,36 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
         const dim3 grid(tiles, rows);
         constexpr size_t smem = (size_t)kWideSub * 12;
         static cudaError_t once = [] {   // static digit tables + dynamic sub-tile exceed 48 KB
-            cudaError_t r = cudaFuncSetAttribute(partition_wide_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (r == cudaSuccess)
-                r = cudaFuncSetAttribute(partition_wide_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-            if (r == cudaSuccess)
-                r = cudaFuncSetAttribute(partition_wide_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-            if (r == cudaSuccess)
-                r = cudaFuncSetAttribute(partition_wide_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-            if (r == cudaSuccess)
-                r = cudaFuncSetAttribute(partition_wide_kernel<11>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+            cudaError_t r = cudaSuccess;
+            auto allow = [&](auto kern) {
+                if (r == cudaSuccess) r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            };
+            allow(partition_wide_kernel<1>);
+            allow(partition_wide_kernel<2>);
+            allow(partition_wide_kernel<3>);
+            allow(partition_wide_kernel<4>);
+            allow(partition_wide_kernel<5>);
+            allow(partition_wide_kernel<6>);
+            allow(partition_wide_kernel<7>);
+            allow(partition_wide_kernel<9>);
+            allow(partition_wide_kernel<10>);
+            allow(partition_wide_kernel<11>);
             return r;
         }();
         if (once != cudaSuccess) return once;
-        if (dbits == 6)
-            partition_wide_kernel<6><<<grid, kWideThreads, smem, s>>>(a);
-        else if (dbits == 7)
-            partition_wide_kernel<7><<<grid, kWideThreads, smem, s>>>(a);
-        else if (dbits == 9)
-            partition_wide_kernel<9><<<grid, kWideThreads, smem, s>>>(a);
-        else if (dbits == 10)
-            partition_wide_kernel<10><<<grid, kWideThreads, smem, s>>>(a);
-        else if (dbits == 11)
-            partition_wide_kernel<11><<<grid, kWideThreads, smem, s>>>(a);
-        else
-            return cudaErrorInvalidValue;
+        switch (dbits) {
+        case 1: partition_wide_kernel<1><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 2: partition_wide_kernel<2><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 3: partition_wide_kernel<3><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 4: partition_wide_kernel<4><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 5: partition_wide_kernel<5><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 6: partition_wide_kernel<6><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 7: partition_wide_kernel<7><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 9: partition_wide_kernel<9><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 10: partition_wide_kernel<10><<<grid, kWideThreads, smem, s>>>(a); break;
+        case 11: partition_wide_kernel<11><<<grid, kWideThreads, smem, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     note_launch();
     return cudaGetLastError();

@@ -379,12 +379,13 @@ def test_dedup_modes_match_oracle(hlog):
     idx.free()
 
 
-@pytest.mark.parametrize("slot_bits", [21, 22, 23])
+@pytest.mark.parametrize("slot_bits", [13, 14, 16, 17, 18, 19, 21, 22, 23])
 @pytest.mark.parametrize("skewed", [False, True])
 def test_wide_partition_directory_matches_oracle(slot_bits, skewed):
-    """Directories with 2^21..2^23 slots per table (partition by the slot's top 9..11 bits)
-    hold the oracle's buckets, through the bins and, with many equal keys, through the
-    exact histogram fallback; queries over them match the oracle."""
+    """Directories with 2^13..2^23 slots per table (partition by the slot's top 1..11 bits;
+    below 2^18 slots the entries keep 14 + s id bits) hold the oracle's buckets, through the
+    bins and, with many equal keys, through the exact histogram fallback; queries over them
+    match the oracle."""
     rng = np.random.default_rng(slot_bits + 100 * skewed)
     d, r, n = 128, 6, 5000
     pts = rand_points(rng, n, d)
