@@ -139,18 +139,25 @@ def _cpu_worker(job):
     h0, q0 = (k * w.n) // cores, (k * nqall) // cores
     t0 = time.perf_counter()
     nh = 0
-    while time.perf_counter() - t0 < budget_s / 2 and nh < w.n:
+    while time.perf_counter() - t0 < budget_s * 0.45 and nh < w.n:
         a = (h0 + nh) % w.n
         oracle.keys_direct(p, w.points[a:a + 50])
         nh += min(50, w.n - a)
     th = time.perf_counter() - t0
+    t0 = time.perf_counter()                        # the oracle's Algorithm 2 route, for reference
+    nf = 0
+    while time.perf_counter() - t0 < budget_s * 0.1 and nf < w.n:
+        a = (h0 + nf) % w.n
+        oracle.keys_fht(p, w.points[a:a + 50])
+        nf += min(50, w.n - a)
+    tf = time.perf_counter() - t0
     t0 = time.perf_counter()
     nqs = 0
-    while time.perf_counter() - t0 < budget_s / 2 and nqs < nqall:
+    while time.perf_counter() - t0 < budget_s * 0.45 and nqs < nqall:
         oracle.linear_scan(w.points, w.queries[(q0 + nqs) % nqall], w.r)
         nqs += 1
     tq = time.perf_counter() - t0
-    return nh, th, nqs, tq, int(p.T)
+    return nh, th, nqs, tq, int(p.T), nf, tf
 
 
 def cpu_baseline(cfg: int, n, nq, budget_s: float = 12.0, cores: int | None = None, pool=None):
@@ -187,6 +194,7 @@ def cpu_baseline(cfg: int, n, nq, budget_s: float = 12.0, cores: int | None = No
                       "on %d processes, scaled to the job of %d points + %d queries"
                       % (nh, T, nqs, w.n, cores, w.n, nqall),
             "points_hashed_per_s": hash_rate, "linear_scan_queries_per_s": query_rate,
+            "points_hashed_per_s_algorithm2": sum(r[5] / r[6] for r in res if r[6] > 0),
             "single_core_value": nqall / one_job_s}
 
 
