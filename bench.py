@@ -116,6 +116,16 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def query_count(cfg: int, nq):
+    """Queries of a run: as given, else the workload's own count; the served workload draws
+    its requests from a pool of 20,000 queries."""
+    from paper_1602_02620_gb300 import workloads
+
+    if nq is None and workloads.CONFIGS[cfg]["nq"] == 0:
+        return 20_000
+    return nq
+
+
 _WORKER_CACHE = {}
 
 
@@ -172,6 +182,7 @@ def cpu_baseline(cfg: int, n, nq, budget_s: float = 12.0, cores: int | None = No
     import multiprocessing as mp
     from paper_1602_02620_gb300 import workloads
 
+    nq = query_count(cfg, nq)
     w = workloads.make(cfg, n=n, nq=nq)
     cores = cores or os.cpu_count() or 1
     jobs = [(cfg, n, nq, k, cores, budget_s) for k in range(cores)]
@@ -330,7 +341,7 @@ def run_reference(args, rank: int):
     import oracle
     from paper_1602_02620_gb300 import workloads
 
-    w = workloads.make(args.workload, n=args.n, nq=args.nq)
+    w = workloads.make(args.workload, n=args.n, nq=query_count(args.workload, args.nq))
     T = oracle.derive_params(w.index_seed, w.d, w.r,
                              rep=workloads.build_options(args.workload).get("replicate", 1)).T
     total = args.warmup + args.steps
@@ -366,7 +377,7 @@ def main():
     ap.add_argument("--nq", type=int, default=None, help="fewer queries of the same workload (profiling)")
     ap.add_argument("--hash-tile", type=int, default=None, choices=(0, 1, 2, 3, 4),
                     help="force the hash kernel (0/1: WHT tiles, 2: tensor-core contraction) instead of the tuned one")
-    ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 6, 7, 8],
+    ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 5, 6, 7, 8],
                     help="workload id (default: the n=1M d=128 r=8 plain workload)")
     args = ap.parse_args()
 
@@ -387,7 +398,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_1602_02620_gb300 import fclsh, workloads
 
-    w = workloads.make(args.workload, n=args.n, nq=args.nq)
+    w = workloads.make(args.workload, n=args.n, nq=query_count(args.workload, args.nq))
     seed = w.index_seed + rank          # one independent problem per GPU
     nq = int(w.queries.shape[0])
     pts = torch.from_numpy(w.points.view(np.int64)).cuda()
