@@ -377,6 +377,8 @@ def main():
     ap.add_argument("--nq", type=int, default=None, help="fewer queries of the same workload (profiling)")
     ap.add_argument("--hash-tile", type=int, default=None, choices=(0, 1, 2, 3, 4),
                     help="force the hash kernel (0/1: WHT tiles, 2: tensor-core contraction) instead of the tuned one")
+    ap.add_argument("--slot-bits", type=int, default=None,
+                    help="directory slot bits (to profile a smaller instance in the full-size directory layout)")
     ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 5, 6, 7, 8],
                     help="workload id (default: the n=1M d=128 r=8 plain workload)")
     args = ap.parse_args()
@@ -407,6 +409,8 @@ def main():
     # kernel shapes for this workload: autotuned once on a sample batch (cached)
     cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
     bopts = workloads.build_options(args.workload)   # e.g. replication
+    if args.slot_bits:
+        bopts["slot_bits"] = args.slot_bits
     idx0 = fclsh.build(pts, w.d, w.r, seed, **bopts)
     tuned = idx0.autotune(qs[: min(nq, 4096)], w.r, cache)
     idx0.free()
@@ -584,16 +588,23 @@ def main():
     }
     full_size = args.n is None and args.workload == CFG
     kernels = []
-    for name, ((ms, cnt), nbytes, tag) in stages.items():
+    parts_timed = info["t"] * args.steps      # every part of every timed step
+    for name, ((ms, cnt), part_bytes, tag) in stages.items():
         if cnt == 0:
             continue
         avg = ms / cnt
+        if tag == "hist":    # runs only on the chunks whose bins overflowed: their entries are not counted here
+            kernels.append({"kernel": name, "total_ms": ms, "launches": cnt, "avg_ms": avg, "bytes_per_launch": None,
+                            "achieved_gbs": None, "frac": None, "traffic": None})
+            continue
+        # a part's tables may be processed in several chunks (launches): bytes per launch on average
+        nbytes = part_bytes * parts_timed / cnt
         gbs = nbytes / (avg / 1000.0) / 1e9
         ratio = TRAFFIC_RATIO.get(tag) if full_size else None
         kernels.append({"kernel": name, "total_ms": ms, "launches": cnt, "avg_ms": avg, "bytes_per_launch": nbytes,
                         "achieved_gbs": gbs, "frac": gbs / peak,
                         "traffic": int(ratio * nbytes) if ratio else None})
-    dom = max(kernels, key=lambda k: k["total_ms"])
+    dom = max((k for k in kernels if k["frac"] is not None), key=lambda k: k["total_ms"])
     qk_avg = qk_ms / max(qk_n, 1)
     qk_gbs = qk_bytes / (qk_avg / 1000.0) / 1e9
     qratio = TRAFFIC_RATIO.get("query") if full_size else None
