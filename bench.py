@@ -43,7 +43,7 @@ TRAFFIC_RATIO = {
     "hash": 0.951,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
     "hash_mma": 0.953,    # profiles/hash_mma_kernel_w512_n300k_d128_r8.md
     "scatter": 0.983,     # profiles/partition_scatter_kernel_n300k_d128_r8.md
-    "finish": 0.999,      # profiles/segment_one_kernel_n300k_d128_r8.md
+    "finish": 1.020,      # profiles/segment_one_kernel_n300k_d128_r8.md
     # query_batch_kernel at full size (1 pass, profiles/query_batch_kernel_plain_n1M_d128_r8.md):
     # 1.123 GB of DRAM traffic per launch against 45.7 MB of algorithmic bytes (random sectors)
     "query": 24.59,
