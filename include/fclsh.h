@@ -15,7 +15,8 @@
  *   - Point ids are uint32 row indices 0..n-1 (n < 2^32).
  *   - Keys are uint64 values in [0, P) with P = 2^50 - 27 (the prime of Eq. 1).
  *   - Table tau = k*(W-1) + (v-1) is code row v = 1..W-1 of part k = 0..t-1,
- *     W = 2^(r'+1), r' = floor(r/t); T = t*(W-1) tables in all.
+ *     W = 2^(r'+1), r' = floor(r * rep / t) (rep = the replication factor of
+ *     Algorithm 1, 1 without replication); T = t*(W-1) tables in all.
  *   - Pointers marked "host or device" are classified with
  *     cudaPointerGetAttributes; device pointers must live on the index's GPU.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
