@@ -608,7 +608,7 @@ def main():
     qk_avg = qk_ms / max(qk_n, 1)
     qk_gbs = qk_bytes / (qk_avg / 1000.0) / 1e9
     qratio = TRAFFIC_RATIO.get("query") if full_size else None
-    qk = {"kernel": "query_batch_kernel (S1-S3 for the 10,000-query batch)", "total_ms": qk_ms,
+    qk = {"kernel": "query_batch_kernel (S1-S3 for the %s-query batch)" % format(nq, ","), "total_ms": qk_ms,
           "launches": qk_n, "avg_ms": qk_avg, "bytes_per_launch": qk_bytes, "achieved_gbs": qk_gbs,
           "frac": qk_gbs / peak, "traffic": int(qratio * qk_bytes) if qratio else None,
           "note": "random 32 B sectors: two dependent reads per (query, table)"}
