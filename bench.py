@@ -51,6 +51,36 @@ TRAFFIC_RATIO = {
 }
 
 
+# Points of at least this many words hashed by the scatter sketch are first listed as their set
+# coordinates (one pass per build); every part's hash then reads the list (the library's rule).
+CSR_MIN_WORDS = 64
+
+
+def set_bits(points: np.ndarray) -> int:
+    """Total set bits of packed uint64 points."""
+    flat = np.ascontiguousarray(points).view(np.uint64).reshape(-1)
+    count = getattr(np, "bitwise_count", None)
+    if count is not None:
+        return int(count(flat).sum(dtype=np.uint64))
+    table = np.array([bin(i).count("1") for i in range(256)], np.uint8)
+    return int(table[flat.view(np.uint8)].sum(dtype=np.uint64))
+
+
+def hash_part_bytes(w, L: int, hash_tile: int) -> float:
+    """Algorithmic bytes of one hash launch (one part): 8 B per key for its L tables and every
+    point, plus what the kernel reads of the points -- the packed words (d/8 B per point), or,
+    for long points under the scatter sketch, their list of set coordinates (4 B per set bit and
+    12 B of start and length per point).  The listing pass itself reads the packed words once per
+    build, before the first part; it is not part of this launch."""
+    keys = 8.0 * L * w.n
+    words = (w.d + 63) // 64
+    if hash_tile == 3 and words >= CSR_MIN_WORDS:
+        nnz = set_bits(w.points)
+        if nnz <= 2 * w.n * words:   # the list's room; denser points keep the packed words
+            return 4.0 * nnz + 12.0 * w.n + keys
+    return w.n * w.d / 8.0 + keys
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -563,7 +593,7 @@ def main():
     qk_ms, qk_n = tq["query_kernel"]
     # ---- rooflines (HBM) of the build's kernels, from the CUDA events of the timed steps.
     # Algorithmic bytes per launch:
-    #   hash (Algorithm 2, one part): n * (d/8 read + 8 B per key for its W-1 tables)
+    #   hash (Algorithm 2, one part): hash_part_bytes (points read + 8 B per key for its W-1 tables)
     #   partition scatter (partition_scatter_kernel): per entry 8 B read + 8 B packed write
     #   partition histogram (radix_hist_kernel + scan): per entry 8 B read
     #   segment finish: per entry 8 B read + 8 B written, plus 4 B per directory slot
@@ -572,6 +602,7 @@ def main():
     L = info["W"] - 1
     entries = w.n * L
     slots = L * ((1 << info["slot_bits"]) + 1)
+    hash_bytes = hash_part_bytes(w, L, tuned["hash_tile"])
     hash_stage = {2: ("hash_mma_kernel (tensor-core contraction, all W-1 keys per point)", "hash_mma"),
                   3: ("hash_tile_kernel (Algorithm 2, sketch scattered from set bits)", "hash_scatter")}.get(
         tuned["hash_tile"], ("hash_tile_kernel (Algorithm 2, all W-1 keys per point)", "hash"))
@@ -580,7 +611,7 @@ def main():
                  else "partition_wide_kernel<%d> (partition by the top %d slot bits into bins, packed output)"
                  % (dbits, dbits))
     stages = {
-        hash_stage[0]: (acc["build_hash"], w.n * (w.d / 8 + 8 * L), hash_stage[1]),
+        hash_stage[0]: (acc["build_hash"], hash_bytes, hash_stage[1]),
         part_name: (acc["build_partition"], 16 * entries, "scatter" if dbits == 8 else "scatter_wide"),
         "partition histogram + scan (exact fallback)": (acc["build_partition_hist"], 8 * entries, "hist"),
         "segment finish (segment_one_kernel + segment_finish_kernel)":
@@ -616,7 +647,6 @@ def main():
         qk["dram_gbs"] = qratio * qk_bytes / (qk_avg / 1000.0) / 1e9
         qk["dram_frac"] = qk["dram_gbs"] / peak
     kernels.append(qk)
-    hash_bytes = w.n * (w.d / 8 + 8 * L)
     ach = hash_bytes / (hash_avg / 1000.0) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
