@@ -195,6 +195,20 @@ fclsh_status fclsh_save(const fclsh_index *idx, const char *path);
 fclsh_status fclsh_load(const char *path, fclsh_index **out);
 
 /*
+ * The shape and random choices that fclsh_build(points, n, d, r, seed, opts) draws, computed
+ * on the host, with no GPU and no points: Algorithm 1's t parts or rep copies (opts->t,
+ * opts->replicate, the rule for opts->approx_c, else one part below r = 10 and two from 10,
+ * Sec. 4.4), W = 2^(r'+1) with r' = floor(r * rep / t), and the permutation, part offsets,
+ * map m and seed vector b of Algorithms 1 and 2 in the draw order the library uses.
+ * shape[0..2] receives t, rep and W.  perm, m (uint32) and b (uint64) have D = d * rep
+ * entries and part_off t + 1; each may be NULL (all NULL: only the shape), so a caller can
+ * learn the sizes first.  Errors: FCLSH_EINVAL for the arguments fclsh_build rejects before
+ * it touches the device, and for explicit parameter arrays in opts.
+ */
+fclsh_status fclsh_derive_params(uint64_t n, uint32_t d, uint32_t r, uint64_t seed, const fclsh_build_opts *opts,
+                                 uint32_t shape[3], uint32_t *perm, uint32_t *part_off, uint32_t *m, uint64_t *b);
+
+/*
  * Copy out the index's random choices (host arrays sized D, t+1, D, D with
  * D = d * rep positions) so that they can be compared with an independent
  * derivation.  Any pointer may be NULL.

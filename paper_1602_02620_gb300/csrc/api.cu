@@ -588,6 +588,55 @@ static fclsh_status check_status(fclsh_index *idx, cudaStream_t s)
     return fail(FCLSH_ETIMEOUT, "a kernel's wait for its tensor-core or copy completion ran out");
 }
 
+// Algorithm 1's shape of an index: t parts or rep copies (from the options, the rule for
+// approx_c, or the default of Sec. 4.4) and the covered radius per part r' = floor(r rep / t).
+static fclsh_status index_shape(uint64_t n, uint32_t d, uint32_t r, const fclsh_build_opts &o, uint32_t *t_out,
+                                uint32_t *rep_out, uint32_t *rp_out)
+{
+    if (!(o.approx_c >= 0.0)) return fail(FCLSH_EINVAL, "approx_c must be >= 0");
+    uint32_t t = o.t, rep = o.replicate ? o.replicate : 1;
+    if (o.approx_c > 0.0 && !o.t && !o.replicate) algorithm1_rule(n, r, o.approx_c, &t, &rep);
+    if (!t) t = rep > 1 ? 1 : default_parts(r);
+    if (rep > 32) return fail(FCLSH_EINVAL, "replicate must be at most 32 (got %u)", rep);
+    if (rep > 1 && t > 1) return fail(FCLSH_EINVAL, "replication and partitioning exclude each other (t = %u, replicate = %u)", t, rep);
+    if (t > d) return fail(FCLSH_EINVAL, "t = %u parts exceed d = %u", t, d);
+    const uint32_t rp = r * rep / t;
+    if (rp + 1 > (uint32_t)kMaxLogW)
+        return fail(FCLSH_EINVAL, "per-part radius floor(r*replicate/t) = %u exceeds 10", rp);
+    *t_out = t;
+    *rep_out = rep;
+    *rp_out = rp;
+    return FCLSH_OK;
+}
+
+extern "C" fclsh_status fclsh_derive_params(uint64_t n, uint32_t d, uint32_t r, uint64_t seed,
+                                            const fclsh_build_opts *opts, uint32_t shape[3], uint32_t *perm,
+                                            uint32_t *part_off, uint32_t *m, uint64_t *b)
+{
+    if (!shape) return fail(FCLSH_EINVAL, "shape is NULL");
+    if (n == 0 || n > 0xFFFFFFFFULL - 1) return fail(FCLSH_EINVAL, "n must be in 1..2^32-2 (got %llu)", (unsigned long long)n);
+    if (d == 0 || d > kMaxD) return fail(FCLSH_EINVAL, "d must be in 1..%u (got %u)", kMaxD, d);
+    fclsh_build_opts o{};
+    if (opts) o = *opts;
+    if (o.perm || o.part_off || o.m || o.b) return fail(FCLSH_EINVAL, "explicit parameters are not derived");
+    uint32_t t = 0, rep = 0, rp = 0;
+    const fclsh_status st = index_shape(n, d, r, o, &t, &rep, &rp);
+    if (st != FCLSH_OK) return st;
+    const uint32_t W = 2u << rp;
+    shape[0] = t;
+    shape[1] = rep;
+    shape[2] = W;
+    if (!perm && !part_off && !m && !b) return FCLSH_OK;
+    std::vector<uint32_t> vp, vo, vm;
+    std::vector<uint64_t> vb;
+    if (derive_params(seed, d, t, rep, W, vp, vo, vm, vb) != 0) return fail(FCLSH_EINVAL, "cannot derive parameters");
+    if (perm) memcpy(perm, vp.data(), vp.size() * 4);
+    if (part_off) memcpy(part_off, vo.data(), vo.size() * 4);
+    if (m) memcpy(m, vm.data(), vm.size() * 4);
+    if (b) memcpy(b, vb.data(), vb.size() * 8);
+    return FCLSH_OK;
+}
+
 extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t d, uint32_t r, uint64_t seed,
                                     const fclsh_build_opts *opts, fclsh_index **out)
 {
@@ -599,16 +648,11 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if (d == 0 || d > kMaxD) return fail(FCLSH_EINVAL, "d must be in 1..%u (got %u)", kMaxD, d);
     fclsh_build_opts o{};
     if (opts) o = *opts;
-    if (!(o.approx_c >= 0.0)) return fail(FCLSH_EINVAL, "approx_c must be >= 0");
-    uint32_t t = o.t, rep = o.replicate ? o.replicate : 1;
-    if (o.approx_c > 0.0 && !o.t && !o.replicate) algorithm1_rule(n, r, o.approx_c, &t, &rep);
-    if (!t) t = rep > 1 ? 1 : default_parts(r);
-    if (rep > 32) return fail(FCLSH_EINVAL, "replicate must be at most 32 (got %u)", rep);
-    if (rep > 1 && t > 1) return fail(FCLSH_EINVAL, "replication and partitioning exclude each other (t = %u, replicate = %u)", t, rep);
-    if (t > d) return fail(FCLSH_EINVAL, "t = %u parts exceed d = %u", t, d);
-    const uint32_t rp = r * rep / t;
-    if (rp + 1 > (uint32_t)kMaxLogW)
-        return fail(FCLSH_EINVAL, "per-part radius floor(r*replicate/t) = %u exceeds 10", rp);
+    uint32_t t = 0, rep = 0, rp = 0;
+    {
+        const fclsh_status st = index_shape(n, d, r, o, &t, &rep, &rp);
+        if (st != FCLSH_OK) return st;
+    }
     const uint32_t W = 2u << rp;
     const uint32_t D = d * rep;   // positions of the (replicated) vector
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "fclsh_free": (None, [_vp]),
     "fclsh_get_info": (_i, [_vp, _vp]),
     "fclsh_get_params": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fclsh_derive_params": (_i, [_u64, _u32, _u32, _u64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fclsh_hash": (_i, [_vp, _vp, _u64, _vp, _vp]),
     "fclsh_bucket": (_i, [_vp, _u32, _u64, _vp, _u64, _vp]),
     "fclsh_export_table": (_i, [_vp, _u32, _vp, _vp]),
@@ -392,6 +393,23 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
     h = ctypes.c_void_p()
     _check(lib().fclsh_build(_ptr(points), _rows(points), d, r, seed, ctypes.byref(o), ctypes.byref(h)))
     return Index(h)
+
+
+def derive_params(n: int, d: int, r: int, seed: int, t: int | None = None, replicate: int = 0,
+                  approx_c: float = 0.0) -> dict:
+    """fclsh_derive_params: the shape (t, rep, W) and the random choices (perm, part_off, m, b over
+    the D = d * rep positions) that fclsh_build would use for n points, computed on the host."""
+    o = _build_opts(t=t, replicate=replicate, approx_c=approx_c)
+    shape = np.zeros(3, np.uint32)
+    _check(lib().fclsh_derive_params(n, d, r, seed, ctypes.byref(o), _ptr(shape), None, None, None, None))
+    t_, rep, W = (int(v) for v in shape)
+    perm = np.zeros(d * rep, np.uint32)
+    part_off = np.zeros(t_ + 1, np.uint32)
+    m = np.zeros(d * rep, np.uint32)
+    b = np.zeros(d * rep, np.uint64)
+    _check(lib().fclsh_derive_params(n, d, r, seed, ctypes.byref(o), _ptr(shape), _ptr(perm), _ptr(part_off),
+                                     _ptr(m), _ptr(b)))
+    return {"t": t_, "rep": rep, "W": W, "perm": perm, "part_off": part_off, "m": m, "b": b}
 
 
 def _build_opts(t=None, slot_bits=None, mem_budget=None, perm=None, part_off=None, m=None, b=None,

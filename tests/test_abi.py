@@ -106,3 +106,77 @@ def test_sparse_argument_errors_without_a_gpu():
     assert lib.fclsh_pack_sparse(buf, buf, 1, 0, 0, buf, None) == fclsh.EINVAL           # d = 0
     assert lib.fclsh_build_sparse(buf, buf, 0, 0, 64, 3, 1, None, ctypes.byref(h)) == fclsh.EINVAL   # n = 0
     assert lib.fclsh_build_sparse(buf, buf, 1, 0, 300_000, 3, 1, None, ctypes.byref(h)) == fclsh.EINVAL
+
+
+def _algorithm1_rule(n, r, c):
+    """The reading of Algorithm 1's rule the library states (log = log2; copies capped at
+    floor(10 / r); parts raised until floor(r / t) <= 10), written out for the test."""
+    import math
+
+    if r == 0:
+        return 1, 1
+    lg = math.log2(max(n, 2))
+    rep, parts = 1, 1
+    if c * r < lg:
+        rep = max(1, min(math.floor(lg / (c * r)), 10 // r))
+    elif c * r > lg:
+        parts = math.ceil(c * r / lg)
+    if rep > 1:
+        return 1, rep
+    while r // parts > 10:
+        parts += 1
+    return parts, 1
+
+
+def test_host_parameters_match_the_oracle_without_a_gpu():
+    """fclsh_derive_params, the host half of fclsh_build, draws the same shape, permutation,
+    parts, map and seed vector as the oracle's independent derivation."""
+    import numpy as np
+
+    import oracle
+    from paper_1602_02620_gb300 import fclsh
+
+    cases = [(64, 3, None, 0), (128, 8, None, 0), (256, 16, None, 0), (1024, 20, None, 0), (300, 7, 3, 0),
+             (100, 2, 1, 3), (17, 4, None, 2), (28_102, 29, None, 0), (140_214, 13, None, 0), (96, 32, None, 0),
+             (5, 0, None, 0), (70, 6, None, 0), (128, 2, None, 4)]
+    for i, (d, r, t, rep) in enumerate(cases):
+        seed = 1000 + 7 * i
+        got = fclsh.derive_params(10_000, d, r, seed, t=t, replicate=rep)
+        want = oracle.derive_params(seed, d, r, t=t, rep=rep or 1)
+        assert (got["t"], got["rep"], got["W"]) == (want.t, want.rep, want.W), (d, r, t, rep)
+        for k in ("perm", "part_off", "m", "b"):
+            assert np.array_equal(got[k], getattr(want, k)), (d, r, t, rep, k)
+
+
+def test_algorithm1_rule_and_rejections_without_a_gpu():
+    """approx_c picks copies or parts by the stated rule; the shapes fclsh_build rejects on the
+    host are rejected the same way by fclsh_derive_params, and accepted ones pass both."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_1602_02620_gb300 import fclsh
+
+    for n in (1_000, 1_000_000, 100_000_000):
+        for r in (0, 1, 2, 3, 5, 8, 13, 20, 40):
+            for c in (0.5, 1.0, 1.5, 2.0, 3.0):
+                got = fclsh.derive_params(n, 256, r, 1, approx_c=c)
+                assert (got["t"], got["rep"]) == _algorithm1_rule(n, r, c), (n, r, c)
+    lib = fclsh.lib()
+    pts = np.zeros(64, np.uint64)
+    h = ctypes.c_void_p()
+    shape = np.zeros(3, np.uint32)
+    for d, r, kw, ok in [(64, 3, {}, True), (64, 3, {"t": 2, "replicate": 2}, False), (8, 3, {"t": 9}, False),
+                         (256, 25, {"t": 2}, False), (64, 2, {"replicate": 33}, False), (64, 11, {"t": 1}, False),
+                         (64, 3, {"approx_c": -1.0}, False), (0, 3, {}, False), (300_000, 3, {}, False)]:
+        o = fclsh._build_opts(**kw)
+        st = lib.fclsh_derive_params(100, d, r, 5, ctypes.byref(o), shape.ctypes.data, None, None, None, None)
+        assert (st == fclsh.OK) == ok, (d, r, kw, fclsh.last_error() if hasattr(fclsh, "last_error") else st)
+        sb = lib.fclsh_build(pts.ctypes.data, 1, d, r, 5, ctypes.byref(o), ctypes.byref(h))
+        if not ok:
+            assert sb == fclsh.EINVAL, (d, r, kw)
+        elif not torch.cuda.is_available():
+            assert sb == fclsh.ECUDA, (d, r, kw)     # past the host checks, the build needs a device
+        elif sb == fclsh.OK:
+            lib.fclsh_free(h)
