@@ -159,7 +159,8 @@ typedef struct {
 fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t d, uint32_t r, uint64_t seed,
                          const fclsh_build_opts *opts, fclsh_index **out);
 
-/* Release the index and all its device memory.  NULL is ignored. */
+/* Release the index (its points, random choices and the bucket tables of Sec. 2.2) and all
+   its device memory.  NULL is ignored.  No other call on the index may run concurrently. */
 void fclsh_free(fclsh_index *idx);
 
 /*
@@ -209,9 +210,11 @@ fclsh_status fclsh_derive_params(uint64_t n, uint32_t d, uint32_t r, uint64_t se
                                  uint32_t shape[3], uint32_t *perm, uint32_t *part_off, uint32_t *m, uint64_t *b);
 
 /*
- * Copy out the index's random choices (host arrays sized D, t+1, D, D with
- * D = d * rep positions) so that they can be compared with an independent
- * derivation.  Any pointer may be NULL.
+ * Copy out the index's random choices: perm and part_off (Algorithm 1's permutation and
+ * parts), m (Algorithm 2's permutation or the map of Eq. 4) and b (the seed vector of
+ * Eq. 1), host arrays sized D, t+1, D, D with D = d * rep positions, so that they can be
+ * compared with an independent derivation.  Any array pointer may be NULL.
+ * Errors: FCLSH_EINVAL for a NULL index.
  */
 fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm, uint32_t *part_off,
                               uint32_t *m, uint64_t *b);
@@ -222,6 +225,8 @@ fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm, uint32_t *
  * Lemma 3 equals Eq. (1) applied to g_v AND x (Eq. 2 / Eq. 4).
  *   pts: host or device [cnt][words].  keys_out: host or device [T][cnt].
  * Runs on `stream`; returns after the keys are written when keys_out is host memory.
+ * Errors: FCLSH_EINVAL (NULL pointers), FCLSH_ENOMEM, FCLSH_ECUDA, FCLSH_ETIMEOUT (a
+ * bounded wait of the tensor-core hash ran out; the index stays usable).
  */
 fclsh_status fclsh_hash(const fclsh_index *idx, const uint64_t *pts, uint64_t cnt, uint64_t *keys_out,
                         void *stream);
@@ -230,15 +235,17 @@ fclsh_status fclsh_hash(const fclsh_index *idx, const uint64_t *pts, uint64_t cn
  * Ids of the bucket with `key` in table `table` (Sec. 2.2), ascending.
  *   ids_out: host, capacity `cap`; *count receives the bucket size (which may
  *   exceed cap; then only the first cap ids are written).  Synchronous.
+ * Errors: FCLSH_EINVAL (NULL pointers, table >= T), FCLSH_ECUDA.
  */
 fclsh_status fclsh_bucket(const fclsh_index *idx, uint32_t table, uint64_t key, uint32_t *ids_out,
                           uint64_t cap, uint64_t *count);
 
 /*
- * Every (key, id) entry of table `table` in directory order: ascending by
- * key mod 2^slot_bits (the slot); the order of the entries inside one slot is
- * unspecified (it may differ between two builds of the same index).
+ * Every (key, id) entry of table `table` (one hash table of Sec. 2.2) in directory
+ * order: ascending by key mod 2^slot_bits (the slot); the order of the entries inside
+ * one slot is unspecified (it may differ between two builds of the same index).
  * keys_out/ids_out: host arrays of n entries.  Synchronous.
+ * Errors: FCLSH_EINVAL (NULL pointers, table >= T), FCLSH_ENOMEM, FCLSH_ECUDA.
  */
 fclsh_status fclsh_export_table(const fclsh_index *idx, uint32_t table, uint64_t *keys_out, uint32_t *ids_out);
 
@@ -259,9 +266,11 @@ fclsh_status fclsh_query(fclsh_index *idx, const uint64_t *queries, uint64_t nq,
                          const uint32_t *radii, void *stream, fclsh_result **out);
 
 /*
- * The same answers through the one-query-at-a-time path: for each query
- * separately, a hash launch, a probe/dedup/verify launch and a copy back.
- * The baseline that the batched form is measured against.  Synchronous.
+ * The same answers (Strategy 2, Sec. 2.2, steps S1-S3 of Sec. 4.1) through the
+ * one-query-at-a-time path: for each query separately, a hash launch, a
+ * probe/dedup/verify launch and a copy back.  The baseline that the batched form is
+ * measured against.  Arguments and results as fclsh_query (one radius for all).
+ * Errors: FCLSH_ERADIUS, FCLSH_EINVAL, FCLSH_ENOMEM, FCLSH_ECUDA.  Synchronous.
  */
 fclsh_status fclsh_query_plain(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
                                void *stream, fclsh_result **out);
@@ -278,8 +287,8 @@ fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_
  * One query through the plain path without allocating: for callers that cannot
  * call cudaMalloc/cudaFree while they query (code running under an allocator or
  * memory pool it does not own, or a latency-bound loop where an allocation and
- * the device synchronisation it can cause are not allowed).  The paper has no
- * counterpart; this is a packaging of the plain path.
+ * the device synchronisation it can cause are not allowed).  No counterpart in the
+ * paper as an entry point: a packaging of the plain path (Strategy 2, Sec. 2.2).
  *   query: device, one point [words].  radius <= r.
  *   ids_out: device, capacity cap; receives the ids within `radius`, ascending
  *   (only the first cap if there are more).  counts_out: device [3]: the number of
@@ -292,16 +301,26 @@ fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_
  * array's device address (make that first call before any stream capture).
  * Every call reuses the same array and clears what it needs, so calls that
  * overlap on the GPU (other streams, other threads) race: serialise them.
- * Asynchronous on `stream`.
+ * Asynchronous on `stream`.  Errors: FCLSH_ERADIUS, FCLSH_EINVAL (NULL or host
+ * pointers, an index past the limits above), FCLSH_ECUDA.
  */
 fclsh_status fclsh_query_plain_noalloc(const fclsh_index *idx, const uint64_t *query, uint32_t radius,
                                        uint32_t *ids_out, uint64_t cap, uint64_t *counts_out, void *stream);
 
+/* Free a host result of fclsh_query, fclsh_query_plain, fclsh_bruteforce, fclsh_qctx_fetch
+   or fclsh_server_wait (the library owns it until then; no counterpart in the paper).
+   NULL is ignored. */
 void fclsh_result_free(fclsh_result *res);
 
 /* ------------------------------------------------------------------ contexts */
 
-/* Per-stream query scratch.  Create one per concurrent stream. */
+/*
+ * Per-stream query scratch of the batched form (no counterpart in the paper: the
+ * device buffers a batch of Strategy 2 queries needs, reused between batches).
+ * Create one per concurrent stream; it must not outlive its index.  fclsh_qctx_free
+ * waits for the context's work and releases it (NULL is ignored).
+ * Errors: FCLSH_EINVAL (NULL pointers), FCLSH_ENOMEM, FCLSH_ECUDA.
+ */
 fclsh_status fclsh_qctx_create(fclsh_index *idx, fclsh_qctx **out);
 void fclsh_qctx_free(fclsh_qctx *ctx);
 
@@ -311,17 +330,23 @@ void fclsh_qctx_free(fclsh_qctx *ctx);
  * round-trip, and with use_graph set it is replayed as one CUDA graph.
  *   queries, radii: device pointers (radii may be NULL: `radius` for all).
  *   The buffers must stay valid until fclsh_qctx_wait returns.
+ * The answers are those of fclsh_query (Strategy 2, Sec. 2.2; S1-S3 of Sec. 4.1).
+ * Errors: FCLSH_ERADIUS, FCLSH_EINVAL (NULL or host pointers), FCLSH_ENOMEM, FCLSH_ECUDA.
  */
 fclsh_status fclsh_query_async(fclsh_qctx *ctx, const uint64_t *queries, uint64_t nq, uint32_t radius,
                                const uint32_t *radii, void *stream);
 
 /*
- * Wait for the context's batch and expose its device results.  If the result
- * buffer overflowed, the batch is re-run with a larger buffer before returning.
+ * Wait for the context's batch (no counterpart in the paper) and expose its device
+ * results (owned by the context, valid until its next batch).  If the result buffer
+ * overflowed, the batch is re-run with a larger buffer before returning.
+ * Errors: FCLSH_EINVAL, FCLSH_ENOMEM, FCLSH_ECUDA.
  */
 fclsh_status fclsh_qctx_wait(fclsh_qctx *ctx, fclsh_device_result *out);
 
-/* Copy the context's last device results to a host fclsh_result. */
+/* Copy the context's last device results to a host fclsh_result (free it with
+   fclsh_result_free; no counterpart in the paper).  Errors: FCLSH_EINVAL, FCLSH_ENOMEM,
+   FCLSH_ECUDA. */
 fclsh_status fclsh_qctx_fetch(fclsh_qctx *ctx, fclsh_result **out);
 
 /* ------------------------------------------------------------------ serving */
@@ -347,30 +372,44 @@ typedef struct {
  * admits a batch when a slot is free and the device has the memory it needs, and
  * retires batches as they finish, so arriving requests join while others run and
  * batches on different slots overlap on the device.  A query's answer does not
- * depend on what it was batched with.  The index must outlive the server.
+ * depend on what it was batched with.  The index must outlive the server.  No
+ * counterpart in the paper (an execution pattern; the answers are Strategy 2's).
+ * Errors: FCLSH_EINVAL (NULL pointers), FCLSH_ENOMEM, FCLSH_ECUDA.
  */
 fclsh_status fclsh_server_create(fclsh_index *idx, const fclsh_server_opts *opts, fclsh_server **out);
 
-/* Queue a request: `queries` host [nq][words] (copied), one radius <= r for all of them. */
+/* Queue a request (no counterpart in the paper): `queries` host [nq][words] (copied), one
+   radius <= r for all of them; *ticket identifies it.
+   Errors: FCLSH_ERADIUS, FCLSH_EINVAL, FCLSH_ENOMEM. */
 fclsh_status fclsh_server_submit(fclsh_server *srv, const uint64_t *queries, uint64_t nq, uint32_t radius,
                                  uint64_t *ticket);
 
 /*
- * Wait up to timeout_ms (negative = no limit) for a request; on success *out holds
- * its results (free with fclsh_result_free) and *latency_ms its submit-to-ready time.
- * FCLSH_ETIMEOUT leaves the request queued; the ticket stays valid.
+ * Wait up to timeout_ms (negative = no limit) for a request (no counterpart in the
+ * paper); on success *out holds its results (free with fclsh_result_free) and
+ * *latency_ms its submit-to-ready time.  FCLSH_ETIMEOUT leaves the request queued; the
+ * ticket stays valid.  Other errors: FCLSH_EINVAL (NULL pointers, unknown ticket),
+ * FCLSH_ENOMEM, or the status of the request's batch if that failed.
  */
 fclsh_status fclsh_server_wait(fclsh_server *srv, uint64_t ticket, int timeout_ms, fclsh_result **out,
                                double *latency_ms);
 
-/* Counters and latency percentiles of completed requests; reset = 1 starts a new window. */
+/* Counters and latency percentiles of completed requests (no counterpart in the paper);
+   reset = 1 starts a new window.  Errors: FCLSH_EINVAL (NULL pointers). */
 fclsh_status fclsh_server_stats(fclsh_server *srv, fclsh_serve_stats *out, int reset);
 
-/* Drain the queue, stop the scheduler and free the server.  NULL is ignored. */
+/* Drain the queue, stop the scheduler and free the server (no counterpart in the paper).
+   NULL is ignored. */
 void fclsh_server_free(fclsh_server *srv);
 
 /* ------------------------------------------------------------------ tuning */
 
+/*
+ * Read or set the index's kernel shapes and probe rule (fclsh_tuning; no counterpart in
+ * the paper: they change speed only, never the reported ids).  fclsh_set_tuning checks
+ * every field (ranges above; a hash tile the index's parts cannot use) and returns
+ * FCLSH_EINVAL without changing anything if one is out of range.
+ */
 fclsh_status fclsh_get_tuning(const fclsh_index *idx, fclsh_tuning *out);
 fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *tune);
 
@@ -381,7 +420,8 @@ fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *tune);
  * applies) on the index's first points; keep the fastest.  The choice is cached in `cache_path` (JSON, may be NULL) keyed by
  * (n, d, r, t, W).  Results never depend on the choice; probe_rows is kept as
  * set.  A later build takes the hash tile through fclsh_build_opts.hash_tile.
- * Synchronous.
+ * No counterpart in the paper (results never depend on it).  Synchronous.
+ * Errors: FCLSH_ERADIUS, FCLSH_EINVAL, FCLSH_ENOMEM, FCLSH_ECUDA.
  */
 fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries, uint64_t nq, uint32_t radius,
                             const char *cache_path, fclsh_tuning *chosen);
@@ -396,11 +436,13 @@ fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries, uint64_t 
  * segment-finish kernels, [7] build partition histogram + scan ([5]-[7] are
  * parts of [1]).  counts[i] = timed launches of phase i.  Timing is off until enabled;
  * enabling adds one event pair per phase and runs query batches without graphs.
+ * Measurement aid (no counterpart in the paper).  Errors: FCLSH_EINVAL, FCLSH_ECUDA.
  */
 fclsh_status fclsh_timing_enable(fclsh_index *idx, int on);
 fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64_t counts[8], int reset);
 
-/* Kernels this library has enqueued in this process (a replayed CUDA graph counts its kernel nodes). */
+/* Kernels this library has enqueued in this process (a replayed CUDA graph counts its kernel
+   nodes).  Measurement aid (no counterpart in the paper). */
 uint64_t fclsh_kernel_launches(void);
 
 /*
@@ -424,10 +466,11 @@ fclsh_status fclsh_debug_pool_used(uint64_t *bytes);
  */
 fclsh_status fclsh_debug_withhold_hash_loads(int on);
 
-/* Thread-local description of the calling thread's last failure. */
+/* Thread-local description of the calling thread's last failure (no counterpart in the
+   paper).  The string is owned by the library and valid until the thread's next call. */
 const char *fclsh_last_error(void);
 
-/* Library version string. */
+/* Library version string (static; no counterpart in the paper). */
 const char *fclsh_version(void);
 
 #ifdef __cplusplus

@@ -25,6 +25,24 @@ def test_library_exports_every_declared_symbol():
     assert "sm_103a" in fclsh.version()
 
 
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment in include/fclsh.h names the passage of the paper that
+    defines it (section, algorithm, equation, definition, lemma, theorem, strategy, example,
+    table) or says that it has no counterpart in the paper."""
+    src = open(os.path.join(ROOT, "include", "fclsh.h")).read()
+    cite = re.compile(r"Sec\.|Algorithm|Eq\.|Definition|Lemma|Theorem|Strategy|Example|Table|no\s+counterpart",
+                      re.I)
+    last, missing = None, []
+    for m in re.finditer(r"/\*.*?\*/|\b(?:fclsh_status|void|const char \*|uint64_t)\s*\*?\s*(fclsh_[a-z0-9_]+)\s*\(",
+                         src, re.S):
+        if m.group(0).startswith("/*"):
+            last = re.sub(r"\s*\n\s*\*?\s*", " ", m.group(0))
+            continue
+        if not (last and cite.search(last)):
+            missing.append(m.group(1))
+    assert not missing, missing
+
+
 def test_errors_without_touching_the_gpu():
     """Argument checks fail cleanly before any device call."""
     import ctypes
