@@ -303,7 +303,7 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
 cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, SortBuffers &buf,
                        unsigned long long *big_cnt, uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count,
                        cudaStream_t s);
-// Partition digit bits for slot_bits (8 up to 20, then slot_bits - 12) and the bin
+// Partition digit bits for slot_bits (slot_bits - 12: segments of 4,096 slots) and the bin
 // capacity of the histogram-free partition for rows of n entries.
 uint32_t msd_dbits(uint32_t slot_bits);
 uint32_t msd_bin_capacity(uint64_t n, uint32_t dbits);

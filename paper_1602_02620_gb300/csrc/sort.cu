@@ -5,9 +5,11 @@
 // (key mod 2^slot_bits) and, for every slot, the index of its first entry.  A
 // query reads its slot, compares the stored high key bits and takes the ids of
 // equal keys: its bucket.  Two builds give it:
-//   * slot_bits <= 20 (MSD): a stable partition of each table by the top 8 slot
-//     bits, then one block per (segment, table) that counts the segment into its
-//     slots in shared memory; a slot's run is ordered by (key bits, id).
+//   * slot_bits <= 23 (MSD): a partition of each table by the top slot_bits - 12 slot
+//     bits (segments of 4,096 slots), into fixed-capacity bins or, where a bin would
+//     overflow, by an exact histogram; then one block per (segment, table) that counts
+//     the segment into its slots in shared memory.  The order inside a slot's run is
+//     the order its shared-memory atomics returned (a run is a set).
 //   * otherwise (LSD): a stable radix sort by the slot bits (8-bit digits) and a
 //     finalize pass; the input is in id order, so a slot's run is ordered by id.
 //
