@@ -4,12 +4,12 @@ Workload (default): n = 1,000,000 points of d = 128 bits, build radius r = 8
 (one part, W = 512, T = 511 tables), 10,000 queries (half planted at distance
 0..8 from a data point, half uniform).  One step = the whole hot path over one
 batch: build the index from device-resident points (hash every point into its
-511 keys by Algorithm 2, radix-sort every table into its bucket directory) and
+511 keys by Algorithm 2, partition and group every table into its bucket directory) and
 answer the 10,000 queries in one batched launch sequence (hash, probe, dedup,
 popcount verify, sorted CSR results).  `value` = queries answered per second of
 step time, with the build inside the step.
 
-Printed JSON line: the driver's contract fields plus `breakdown` (points hashed/s,
+Printed JSON line: metric, value, unit, sizes and timing fields, plus `breakdown` (points hashed/s,
 batched queries/s of the query phase alone, plain one-query-at-a-time GPU
 queries/s, GPU brute-force queries/s), `roofline` of the dominant kernel,
 `cpu_baseline` (the CPU oracle on a bounded sample), `e2e` (the same job through
