@@ -10,7 +10,7 @@
  * coordinate at a time, 128-bit integers wherever a sum could grow, and no
  * blocking, fusion or reordering beyond what the paper's definitions state.
  *
- * Conventions (readings of the paper, listed in the design doc):
+ * Conventions (readings of the paper where it leaves a choice open):
  *   - A point is d bits packed LSB-first into ceil(d/64) uint64 words:
  *     coordinate i lives in word i/64, bit i%64.
  *   - Hadamard code entry C(v, j) = <a(j), v> mod 2 = parity(v & j), i.e. the
