@@ -33,10 +33,12 @@ constexpr int kSortThreads = 256;
 // is padded to a multiple of 4 words so that every row starts 16-byte aligned.
 __host__ __device__ __forceinline__ uint64_t dir_stride(uint32_t sb) { return (1ULL << sb) + 4; }
 
-// x mod P for x < 2^63, by 2^50 == 27 (mod P).
+// x mod P for any 64-bit x, by 2^50 == 27 (mod P): x >> 50 < 2^14, so the folded value is
+// below 2^50 + 27 * 2^14 < 2P and one conditional subtraction finishes (the scatter sketch's
+// unreduced column sums, up to 16,383 (P - 1) < 2^64, rely on the full range).
 __host__ __device__ __forceinline__ uint64_t mod_p(uint64_t x)
 {
-    uint64_t r = (x & kMask50) + (x >> 50) * 27ULL;   // < 2^50 + 2^18 < 2P
+    uint64_t r = (x & kMask50) + (x >> 50) * 27ULL;   // < 2^50 + 27 * 2^14 < 2P
     return r >= kP ? r - kP : r;
 }
 
