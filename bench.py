@@ -1,13 +1,14 @@
 """Benchmark of the fcLSH hot path on one GB300 (or N, one independent problem per GPU).
 
-Workload (default): n = 1,000,000 points of d = 128 bits, build radius r = 8
-(one part, W = 512, T = 511 tables), 10,000 queries (half planted at distance
-0..8 from a data point, half uniform).  One step = the whole hot path over one
-batch: build the index from device-resident points (hash every point into its
-511 keys by Algorithm 2, partition and group every table into its bucket directory) and
-answer the 10,000 queries in one batched launch sequence (hash, probe, dedup,
-popcount verify, sorted CSR results).  `value` = queries answered per second of
-step time, with the build inside the step.
+Workload (default): the batched sparse-fingerprint workload, n = 2,000,000 points of
+d = 1,024 bits (bit density 0.02, 20% near-duplicates), build radius r = 20 (two parts
+of 512 coordinates, W = 2,048, T = 4,094 tables), 50,000 queries (half near-duplicates at
+distance 0..20, half fresh) answered in one batch.  One step = the whole hot path over one
+batch: build the index from device-resident points (hash every point into its 4,094 keys,
+partition and group every table into its bucket directory) and answer the batch in one
+persistent launch sequence (hash, probe, dedup, popcount verify, sorted CSR results).
+`value` = queries answered per second of step time, with the build inside the step.
+`--workload N` selects another workload (2: n = 1M, d = 128, r = 8, one part, 511 tables).
 
 Printed JSON line: metric, value, unit, sizes and timing fields, plus `breakdown` (points hashed/s,
 batched queries/s of the query phase alone, plain one-query-at-a-time GPU
@@ -34,20 +35,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "queries/s at 100% recall and points hashed/s, batched vs plain on one GB300"
-CFG = 2
+CFG = 4
 
-# DRAM traffic / algorithmic bytes of each stage, from `ncu --set full` on the same
-# workload at n = 300,000 (profiles/*_n300k_d128_r8.md); traffic scales with the
-# algorithmic bytes.  Set an entry to None when its kernel changes.
+# DRAM traffic / algorithmic bytes of each stage per workload, from ncu captures of the same
+# kernels (profiles/); traffic scales with the algorithmic bytes.  An entry is None (traffic
+# reported as null) until it is captured, and is reset to None when its kernel changes.
 TRAFFIC_RATIO = {
-    "hash": 0.951,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
-    "hash_mma": 0.953,    # profiles/hash_mma_kernel_w512_n300k_d128_r8.md
-    "scatter": 0.983,     # profiles/partition_scatter_kernel_n300k_d128_r8.md
-    "finish": 1.020,      # profiles/segment_one_kernel_n300k_d128_r8.md
-    # query_batch_kernel at full size (1 pass, profiles/query_batch_kernel_plain_n1M_d128_r8.md):
-    # 1.123 GB of DRAM traffic per launch against 45.7 MB of algorithmic bytes (random sectors)
-    "query": 24.59,
-    "hist": None,         # (only on the histogram fallback of skewed keys)
+    2: {
+        "hash": 0.951,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
+        "hash_mma": 0.953,    # profiles/hash_mma_kernel_w512_n300k_d128_r8.md
+        "scatter": 0.983,     # profiles/partition_scatter_kernel_n300k_d128_r8.md
+        "finish": 1.020,      # profiles/segment_one_kernel_n300k_d128_r8.md
+        "query": None,
+        "hist": None,
+    },
+    4: {},
 }
 
 
@@ -389,6 +391,7 @@ def run_reference(args, rank: int):
     nq = int(w.queries.shape[0])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * nq / v,
+            "ms_per_step_kind": "extrapolated from a bounded sample (see cpu_baseline.sample)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(w, T, nq, w.name),
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -398,7 +401,7 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fclsh")
     ap.add_argument("--plain-sample", type=int, default=300)
@@ -410,7 +413,7 @@ def main():
     ap.add_argument("--slot-bits", type=int, default=None,
                     help="directory slot bits (to profile a smaller instance in the full-size directory layout)")
     ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 5, 6, 7, 8],
-                    help="workload id (default: the n=1M d=128 r=8 plain workload)")
+                    help="workload id (default: 4, the n=2M d=1024 r=20 batched sparse workload)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -448,17 +451,24 @@ def main():
         tuned["hash_tile"] = args.hash_tile
 
     def step(timing: bool):
+        """One step: build + the batch on a fresh context (its first batch runs eagerly, so
+        per-phase timing costs it nothing); CUDA events on the legacy stream mark the build,
+        the batch and the teardown (the library's streams are blocking, so they order)."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
         idx = fclsh.build(pts, w.d, w.r, seed, timing=timing, hash_tile=tuned["hash_tile"], **bopts)
+        ev[1].record()
         idx.set_tuning(**tuned)
-        idx.timing_enable(False)          # the query batch runs as a replayed CUDA graph
         ctx = idx.context()
         ctx.query_async(qs, w.r)
         dr = ctx.wait()
+        ev[2].record()
         t = idx.timing_read()
         ctx.close()
         info = dict(idx.info)
         idx.free()
-        return t, int(dr.total), info
+        ev[3].record()
+        return t, int(dr.total), info, ev
 
     for _ in range(args.warmup):
         step(True)
@@ -472,10 +482,13 @@ def main():
     torch.cuda.synchronize()
     ev0.record()
     acc = {}
+    marks = []
     total = 0
     for _ in range(args.steps):
-        t, total, info = step(True)
-        for k in ("build_hash", "build_sort", "build_partition", "build_finish", "build_partition_hist"):
+        t, total, info, ev = step(True)
+        marks.append(ev)
+        for k in ("build_hash", "build_sort", "build_partition", "build_finish", "build_partition_hist",
+                  "query_kernel", "query_csr"):
             a = acc.setdefault(k, [0.0, 0])
             a[0] += t[k][0]
             a[1] += t[k][1]
@@ -484,6 +497,21 @@ def main():
     ev1.record()
     torch.cuda.synchronize()
     launches = fclsh.kernel_launches() - l0
+    # where a step's time goes (averages over the timed steps)
+    per = lambda k: acc[k][0] / args.steps
+    build_ms = sum(e[0].elapsed_time(e[1]) for e in marks) / args.steps
+    batch_ms = sum(e[1].elapsed_time(e[2]) for e in marks) / args.steps
+    teardown_ms = sum(e[2].elapsed_time(e[3]) for e in marks) / args.steps
+    step_breakdown = {
+        "build_ms": build_ms, "build_hash_kernels_ms": per("build_hash"),
+        "build_sort_kernels_ms": per("build_sort"),
+        "build_other_ms": build_ms - per("build_hash") - per("build_sort"),
+        "batch_ms": batch_ms, "batch_query_kernel_ms": per("query_kernel"), "batch_csr_ms": per("query_csr"),
+        "batch_other_ms": batch_ms - per("query_kernel") - per("query_csr"),
+        "teardown_ms": teardown_ms,
+        "note": "build_other: allocations, parameter copies, memsets and the status read of the build; "
+                "batch_other: context set-up and the result-size read; teardown: freeing the context and index",
+    }
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -550,7 +578,8 @@ def main():
     hq = torch.from_numpy(w.queries.view(np.int64)).pin_memory()
     e2e_t = []
     d2h = 0
-    for i in range(max(2, args.steps)):
+    e2e_reps = max(2, min(args.steps, 5))
+    for i in range(e2e_reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         idx2 = fclsh.build(hp, w.d, w.r, seed, hash_tile=tuned["hash_tile"], **bopts)
@@ -575,7 +604,7 @@ def main():
         qi, qc = csr(w.queries)
         qdev = torch.empty((nq, w.words), dtype=torch.int64, device="cuda")
         e2e_s = []
-        for i in range(max(2, args.steps)):
+        for i in range(e2e_reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             idx2 = fclsh.build_sparse(pi, pc, w.d, w.r, seed, hash_tile=tuned["hash_tile"], **bopts)
@@ -590,7 +619,6 @@ def main():
                                                          qc.numel() * 4),
                                "d2h_bytes_per_step": int(d2h)}
 
-    qk_ms, qk_n = tq["query_kernel"]
     # ---- rooflines (HBM) of the build's kernels, from the CUDA events of the timed steps.
     # Algorithmic bytes per launch:
     #   hash (Algorithm 2, one part): hash_part_bytes (points read + 8 B per key for its W-1 tables)
@@ -617,7 +645,8 @@ def main():
         "segment finish (segment_one_kernel + segment_finish_kernel)":
             (acc["build_finish"], 16 * entries + 4 * slots, "finish"),
     }
-    full_size = args.n is None and args.workload == CFG
+    # traffic ratios apply to the full-size workload they were captured on
+    ratios = TRAFFIC_RATIO.get(args.workload, {}) if args.n is None and args.nq is None else {}
     kernels = []
     parts_timed = info["t"] * args.steps      # every part of every timed step
     for name, ((ms, cnt), part_bytes, tag) in stages.items():
@@ -631,22 +660,33 @@ def main():
         # a part's tables may be processed in several chunks (launches): bytes per launch on average
         nbytes = part_bytes * parts_timed / cnt
         gbs = nbytes / (avg / 1000.0) / 1e9
-        ratio = TRAFFIC_RATIO.get(tag) if full_size else None
+        ratio = ratios.get(tag)
         kernels.append({"kernel": name, "total_ms": ms, "launches": cnt, "avg_ms": avg, "bytes_per_launch": nbytes,
                         "achieved_gbs": gbs, "frac": gbs / peak,
                         "traffic": int(ratio * nbytes) if ratio else None})
-    dom = max((k for k in kernels if k["frac"] is not None), key=lambda k: k["total_ms"])
+    # the batch's query kernel inside the timed steps (one launch per step, plus a second
+    # pass for a step whose results passed the context's buffer)
+    qk_ms, qk_n = acc["query_kernel"]
     qk_avg = qk_ms / max(qk_n, 1)
-    qk_gbs = qk_bytes / (qk_avg / 1000.0) / 1e9
-    qratio = TRAFFIC_RATIO.get("query") if full_size else None
+    qk_bytes_launch = qk_bytes * args.steps / max(qk_n, 1)
+    qk_gbs = qk_bytes_launch / (qk_avg / 1000.0) / 1e9
+    qratio = ratios.get("query")
     qk = {"kernel": "query_batch_kernel (S1-S3 for the %s-query batch)" % format(nq, ","), "total_ms": qk_ms,
-          "launches": qk_n, "avg_ms": qk_avg, "bytes_per_launch": qk_bytes, "achieved_gbs": qk_gbs,
-          "frac": qk_gbs / peak, "traffic": int(qratio * qk_bytes) if qratio else None,
-          "note": "random 32 B sectors: two dependent reads per (query, table)"}
+          "launches": qk_n, "avg_ms": qk_avg, "bytes_per_launch": qk_bytes_launch, "achieved_gbs": qk_gbs,
+          "frac": qk_gbs / peak, "traffic": int(qratio * qk_bytes_launch) if qratio else None,
+          "note": "random 32 B sectors: a directory read and a bucket run per (query, table), a point per candidate"}
     if qratio:   # as DRAM sees it: the measured traffic over the live launch time
-        qk["dram_gbs"] = qratio * qk_bytes / (qk_avg / 1000.0) / 1e9
+        qk["dram_gbs"] = qratio * qk_bytes_launch / (qk_avg / 1000.0) / 1e9
         qk["dram_frac"] = qk["dram_gbs"] / peak
     kernels.append(qk)
+    csr_ms, csr_n = acc["query_csr"]
+    kernels.append({"kernel": "result CSR (scan + gather_runs_kernel)", "total_ms": csr_ms, "launches": csr_n,
+                    "avg_ms": csr_ms / max(csr_n, 1), "bytes_per_launch": None, "achieved_gbs": None,
+                    "frac": None, "traffic": None})
+    dom = max((k for k in kernels if k["frac"] is not None), key=lambda k: k["total_ms"])
+    kernels_ms = sum(k["total_ms"] for k in kernels) / args.steps
+    step_breakdown["kernels_ms"] = kernels_ms
+    step_breakdown["kernels_share_of_step"] = kernels_ms / ms_step
     ach = hash_bytes / (hash_avg / 1000.0) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -658,7 +698,10 @@ def main():
             "hash_roofline_frac": ach / peak,
             "points_hashed_per_s": w.n / (hash_avg / 1000.0),
             "batched_query_queries_per_s": batched_qps,
-            "batched_query_kernel_ms": qk_ms / max(qk_n, 1), "batched_query_csr_ms": tq["query_csr"][0] / max(tq["query_csr"][1], 1),
+            "batched_query_kernel_ms": tq["query_kernel"][0] / max(tq["query_kernel"][1], 1),
+            "batched_query_csr_ms": tq["query_csr"][0] / max(tq["query_csr"][1], 1),
+            "collisions_per_query": float(res.collisions.mean()), "candidates_per_query": float(res.candidates.mean()),
+            "results_per_query": float(np.diff(res.offs).mean()),
             "plain_queries_per_s": plain_qps, "plain_sample": ns,
             "bruteforce_queries_per_s": brute_qps,
             "results_per_step": total,
@@ -672,6 +715,7 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac"], "traffic": dom["traffic"],
                      "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_ms": dom["avg_ms"]},
         "kernels": kernels,
+        "step_breakdown": step_breakdown,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,

@@ -145,10 +145,14 @@ typedef struct {
 
 /*
  * Build the index (Sec. 3.2, "Construction"): draw the random choices of
- * Algorithms 1 and 2 from `seed`, hash every point into its T keys by
- * Algorithm 2 (sketch + fast Hadamard transform, Sec. 3.2 "Fast computation of
- * hash functions"), and group the points of each table into buckets by key
- * (Sec. 2.2: only non-empty buckets are stored).
+ * Algorithms 1 and 2 from `seed`, hash every point into its T keys, and group the
+ * points of each table into buckets by key (Sec. 2.2: only non-empty buckets are
+ * stored).  The keys are those of Eq. 1 on g_v AND x; opts->hash_tile picks the
+ * route that computes them: Algorithm 2 (sketch + fast Hadamard transform, Sec. 3.2
+ * "Fast computation of hash functions"; tiles 0, 1, 3, the default) or the direct
+ * O(dL) sum of Eq. 1 as an exact tensor-core contraction (tile 2) or on CUDA cores
+ * (tile 4).  Lemma 3 makes every route give the same keys; fclsh_autotune reports the
+ * fastest of 0..3 for a later build.
  *   points: host or device, [n][ceil(d/64)] uint64, copied (caller keeps ownership).
  *   n: 1 .. 2^32-1.  d: 1 .. 262,144; bits past d in a point's last word must be 0.
  *   r: build radius, 0 .. 63, with floor(r*replicate/t) <= 10.
@@ -249,6 +253,17 @@ fclsh_status fclsh_bucket(const fclsh_index *idx, uint32_t table, uint64_t key, 
  */
 fclsh_status fclsh_export_table(const fclsh_index *idx, uint32_t table, uint64_t *keys_out, uint32_t *ids_out);
 
+/*
+ * The keys the build stored for the given points, read back from every table's directory
+ * (a diagnostic: the tables of Sec. 2.2 keep each point under its key by Eq. 1, and this
+ * returns that key, so that it can be compared with an independent computation).
+ *   ids: host [cnt] distinct point ids < n.  keys_out: host [T][cnt]: keys_out[tau*cnt + j]
+ *   is the key of point ids[j] in table tau; an id missing from a table reads 2^64 - 1.
+ * Synchronous.  Errors: FCLSH_EINVAL (NULL pointers, an id >= n or given twice),
+ * FCLSH_ENOMEM, FCLSH_ECUDA.
+ */
+fclsh_status fclsh_export_keys(const fclsh_index *idx, const uint32_t *ids, uint64_t cnt, uint64_t *keys_out);
+
 /* ------------------------------------------------------------------ queries */
 
 /*
@@ -288,7 +303,7 @@ fclsh_status fclsh_bruteforce(fclsh_index *idx, const uint64_t *queries, uint64_
  * call cudaMalloc/cudaFree while they query (code running under an allocator or
  * memory pool it does not own, or a latency-bound loop where an allocation and
  * the device synchronisation it can cause are not allowed).  No counterpart in the
- * paper as an entry point: a packaging of the plain path (Strategy 2, Sec. 2.2).
+ * paper: it packages the plain path above for such callers.
  *   query: device, one point [words].  radius <= r.
  *   ids_out: device, capacity cap; receives the ids within `radius`, ascending
  *   (only the first cap if there are more).  counts_out: device [3]: the number of
@@ -458,11 +473,12 @@ fclsh_status fclsh_debug_fail_alloc(int64_t after);
 fclsh_status fclsh_debug_pool_used(uint64_t *bytes);
 
 /*
- * Testing aid for the bounded waits (no counterpart in the paper): while `on`, the
- * tensor-core hash kernel (hash_tile 2) never requests its first operand chunk, so
- * its waits run out after about two seconds; the kernel then stops, releases its
- * tensor memory and flags the index, and the call returns FCLSH_ETIMEOUT.  The
- * device stays usable.
+ * Testing aid for the bounded waits (no counterpart in the paper): while on = c + 1 > 0,
+ * the tensor-core hash kernel (hash_tile 2) never requests its operand chunk c (on = 1:
+ * the first), so its wait for that chunk runs out after about two seconds; the kernel
+ * then waits (bounded) for the tensor-core work and copies it already issued, releases
+ * its tensor memory and flags the index, and the call returns FCLSH_ETIMEOUT.  The
+ * device stays usable.  on <= 0 turns it off.
  */
 fclsh_status fclsh_debug_withhold_hash_loads(int on);
 

@@ -14,7 +14,8 @@ first use); this module only marshals numpy arrays:
 * ``keys_fht``       -- the same keys by Algorithm 2 (sketch + fast Hadamard
   transform); Lemma 3 says the two agree for every b and P.
 * ``build_tables`` / ``query`` -- bucket tables and the Strategy 2 query with the
-  S1/S2/S3 steps of Sec. 4.1, including #Collisions and #Candidates.
+  S1/S2/S3 steps of Sec. 4.1, including #Collisions and #Candidates;
+  ``query_listed`` runs the same query given only the tables it probes.
 * ``linear_scan``    -- the plain definition of the answer (Definition 2).
 """
 from __future__ import annotations
@@ -81,6 +82,8 @@ def _lib():
         lib.oracle_query.restype = u64
         lib.oracle_query_rows.argtypes = [vp, vp, u64, vp, vp, vp, u32, u32, vp, u64, vp]
         lib.oracle_query_rows.restype = u64
+        lib.oracle_query_listed.argtypes = [vp, vp, u64, vp, vp, vp, vp, u32, u32, vp, u64, vp]
+        lib.oracle_query_listed.restype = u64
         lib.oracle_linear_scan.argtypes = [vp, u64, u32, vp, u32, vp, u64]
         lib.oracle_linear_scan.restype = u64
         lib.oracle_splitmix64.argtypes = [u64, u64, vp]
@@ -247,6 +250,39 @@ def query(p: Params, pts, tables, q, radius: int, rows: int = 0):
     counters = np.zeros(2, np.uint64)
     cnt = _lib().oracle_query_rows(ctypes.byref(p._c()), _ptr(pts), n, _ptr(keys), _ptr(ids),
                                    _ptr(q), radius, rows, _ptr(out), cap, _ptr(counters))
+    return out[:cnt].copy(), int(counters[0]), int(counters[1])
+
+
+def probed_tables(p: Params, rows: int) -> list:
+    """Tables a query probes with ``rows`` code rows per part (0 = all T)."""
+    L = p.W - 1
+    if rows == 0 or rows >= L:
+        return list(range(p.T))
+    return [k * L + v - 1 for k in range(p.t) for v in range(1, rows + 1)]
+
+
+def query_listed(p: Params, pts, tables: dict, q, radius: int, rows: int = 0):
+    """Strategy 2 query like ``query`` with only some tables given: ``tables`` maps a
+    table index to its (keys, ids) from ``table``; every probed table must be present.
+    Returns (sorted ids, #Collisions, #Candidates)."""
+    pts = _pts(pts, p.words)
+    q = _pts(q, p.words)
+    n = pts.shape[0]
+    taus = sorted(tables)
+    missing = set(probed_tables(p, rows)) - set(taus)
+    if missing:
+        raise ValueError("probed tables not given: %s" % sorted(missing)[:8])
+    keys = np.stack([np.ascontiguousarray(tables[t][0], np.uint64) for t in taus])
+    ids = np.stack([np.ascontiguousarray(tables[t][1], np.uint32) for t in taus])
+    row = np.full(p.T, 0xFFFFFFFF, np.uint32)
+    row[taus] = np.arange(len(taus), dtype=np.uint32)
+    cap = max(n, 1)
+    out = np.zeros(cap, np.uint32)
+    counters = np.zeros(2, np.uint64)
+    cnt = _lib().oracle_query_listed(ctypes.byref(p._c()), _ptr(pts), n, _ptr(keys), _ptr(ids), _ptr(row),
+                                     _ptr(q), radius, rows, _ptr(out), cap, _ptr(counters))
+    if cnt == (1 << 64) - 1:
+        raise ValueError("a probed table was not given")
     return out[:cnt].copy(), int(counters[0]), int(counters[1])
 
 

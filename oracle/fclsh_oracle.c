@@ -311,9 +311,12 @@ static int u32_cmp(const void *a, const void *b)
  * the probed tables only.
  * Results are sorted ascending.  Returns the number of results; writes up to
  * cap ids.  counters[0] = #Collisions, counters[1] = #Candidates.
+ * tab_row (may be NULL): table tau is row tab_row[tau] of tab_keys/tab_ids, so that a
+ * caller can pass only the probed tables; NULL means row tau.  A probed table without a
+ * row (tab_row[tau] = 0xFFFFFFFF) makes the query fail: it returns UINT64_MAX.
  */
-uint64_t oracle_query_rows(const oracle_params *p, const uint64_t *pts, uint64_t n,
-                           const uint64_t *tab_keys, const uint32_t *tab_ids,
+static uint64_t query_core(const oracle_params *p, const uint64_t *pts, uint64_t n,
+                           const uint64_t *tab_keys, const uint32_t *tab_ids, const uint32_t *tab_row,
                            const uint64_t *q, uint32_t radius, uint32_t rows,
                            uint32_t *out, uint64_t cap, uint64_t *counters)
 {
@@ -329,8 +332,10 @@ uint64_t oracle_query_rows(const oracle_params *p, const uint64_t *pts, uint64_t
     for (uint32_t tau = 0; tau < T; tau++) {                      /* S2 */
         uint32_t v = tau % (p->W - 1) + 1;                        /* code row of table tau */
         if (rows && v > rows) continue;
-        const uint64_t *keys = tab_keys + (uint64_t)tau * n;
-        const uint32_t *ids = tab_ids + (uint64_t)tau * n;
+        uint64_t row = tab_row ? tab_row[tau] : tau;
+        if (row == 0xFFFFFFFFu) { ncoll = UINT64_MAX; break; }   /* a probed table was not given */
+        const uint64_t *keys = tab_keys + row * n;
+        const uint32_t *ids = tab_ids + row * n;
         for (uint64_t e = lower_bound_u64(keys, n, qkeys[tau]); e < n && keys[e] == qkeys[tau]; e++) {
             uint32_t id = ids[e];
             ncoll++;
@@ -341,6 +346,12 @@ uint64_t oracle_query_rows(const oracle_params *p, const uint64_t *pts, uint64_t
         }
     }
 
+    if (ncoll == UINT64_MAX) {
+        free(qkeys);
+        free(bitmap);
+        free(cand);
+        return UINT64_MAX;
+    }
     for (uint64_t c = 0; c < ncand; c++) {                        /* S3 */
         uint32_t id = cand[c];
         if (hamming(q, pts + (uint64_t)id * p->words, p->words) <= (int)radius) {
@@ -355,6 +366,23 @@ uint64_t oracle_query_rows(const oracle_params *p, const uint64_t *pts, uint64_t
     free(bitmap);
     free(cand);
     return nres;
+}
+
+uint64_t oracle_query_rows(const oracle_params *p, const uint64_t *pts, uint64_t n,
+                           const uint64_t *tab_keys, const uint32_t *tab_ids,
+                           const uint64_t *q, uint32_t radius, uint32_t rows,
+                           uint32_t *out, uint64_t cap, uint64_t *counters)
+{
+    return query_core(p, pts, n, tab_keys, tab_ids, NULL, q, radius, rows, out, cap, counters);
+}
+
+/* The same query with only some tables given (tab_row as in query_core). */
+uint64_t oracle_query_listed(const oracle_params *p, const uint64_t *pts, uint64_t n,
+                             const uint64_t *tab_keys, const uint32_t *tab_ids, const uint32_t *tab_row,
+                             const uint64_t *q, uint32_t radius, uint32_t rows,
+                             uint32_t *out, uint64_t cap, uint64_t *counters)
+{
+    return query_core(p, pts, n, tab_keys, tab_ids, tab_row, q, radius, rows, out, cap, counters);
 }
 
 uint64_t oracle_query(const oracle_params *p, const uint64_t *pts, uint64_t n,

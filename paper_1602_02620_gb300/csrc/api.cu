@@ -84,7 +84,7 @@ int64_t launch_count_adjust(int64_t delta) { return g_launches.fetch_add(delta) 
 
 // ---------------------------------------------------------------- helpers
 
-static bool is_device_ptr(const void *p)
+bool is_device_ptr(const void *p)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -416,6 +416,34 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
     return FCLSH_OK;
 }
 
+// Grow the runs to `cap` ids keeping the first c->cap of them (the CSR ids buffer is
+// rebuilt by the gather); a captured batch refers to the old buffers and is dropped.
+static fclsh_status ctx_grow_runs(fclsh_qctx *c, uint64_t cap, cudaStream_t s)
+{
+    if (cap <= c->cap) return FCLSH_OK;
+    uint32_t *runs = nullptr, *ids = nullptr;
+    cudaError_t e = dev_alloc((void **)&runs, cap * 4);
+    if (e == cudaSuccess) e = dev_alloc((void **)&ids, cap * 4);
+    if (e == cudaSuccess && c->cap) e = cudaMemcpyAsync(runs, c->runs, c->cap * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        dev_free(runs);
+        dev_free(ids);
+        return cuda_fail(e, "growing the query results");
+    }
+    dev_free(c->runs);
+    dev_free(c->res_ids);
+    c->runs = runs;
+    c->res_ids = ids;
+    c->cap = cap;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    c->g_seen = false;
+    return FCLSH_OK;
+}
+
 static QueryArgs make_args(fclsh_index *idx)
 {
     QueryArgs a{};
@@ -448,8 +476,10 @@ static QueryArgs make_args(fclsh_index *idx)
 }
 
 // Enqueue the launches of one batch (no host synchronisation inside).
+// redo_cap != 0: the second pass after the runs overflowed a buffer of redo_cap ids (see
+// QueryArgs::redo_cap); the cursor keeps the first pass's total.
 static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq, uint32_t radius, const uint32_t *radii,
-                                  cudaStream_t s)
+                                  cudaStream_t s, uint64_t redo_cap = 0)
 {
     fclsh_index *idx = c->idx;
     QueryArgs a = make_args(idx);
@@ -467,7 +497,8 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
     a.cand = c->cand;
     a.bitmaps = c->bitmaps;
     a.bm_words = (idx->n + 31) / 32;
-    FCLSH_CUDA(cudaMemsetAsync(c->counters, 0, 2 * sizeof(unsigned long long), s));
+    a.redo_cap = redo_cap;
+    FCLSH_CUDA(cudaMemsetAsync(c->counters, 0, (redo_cap ? 1 : 2) * sizeof(unsigned long long), s));
     {
         PhaseTimer pt(idx, 2, s);
         const uint32_t grid = (uint32_t)std::min<uint64_t>(c->grid, std::max<uint64_t>(nq, 1));
@@ -1033,6 +1064,34 @@ extern "C" fclsh_status fclsh_export_table(const fclsh_index *idx, uint32_t tabl
     return FCLSH_OK;
 }
 
+extern "C" fclsh_status fclsh_export_keys(const fclsh_index *idx, const uint32_t *ids, uint64_t cnt, uint64_t *keys_out)
+{
+    if (!idx || (cnt && (!ids || !keys_out))) return fail(FCLSH_EINVAL, "NULL argument");
+    if (cnt == 0) return FCLSH_OK;
+    if (cnt > 0xFFFFFFFEULL) return fail(FCLSH_EINVAL, "too many ids");
+    std::vector<uint32_t> slot(idx->n, 0xFFFFFFFFu);
+    for (uint64_t j = 0; j < cnt; ++j) {
+        if (ids[j] >= idx->n) return fail(FCLSH_EINVAL, "id %u out of range (n = %llu)", ids[j], (unsigned long long)idx->n);
+        if (slot[ids[j]] != 0xFFFFFFFFu) return fail(FCLSH_EINVAL, "id %u given twice", ids[j]);
+        slot[ids[j]] = (uint32_t)j;
+    }
+    FCLSH_CUDA(cudaSetDevice(idx->device));
+    DevAllocs tmp;
+    uint32_t *dslot = nullptr;
+    uint64_t *dkeys = nullptr;
+    cudaError_t e;
+    if ((e = tmp.alloc(&dslot, idx->n)) != cudaSuccess || (e = tmp.alloc(&dkeys, (size_t)idx->T * cnt)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(key read-back)");
+    cudaStream_t s = nullptr;
+    FCLSH_CUDA(cudaMemcpyAsync(dslot, slot.data(), idx->n * 4, cudaMemcpyHostToDevice, s));
+    FCLSH_CUDA(cudaMemsetAsync(dkeys, 0xFF, (size_t)idx->T * cnt * 8, s));   // ids a table misses read 2^64 - 1
+    FCLSH_CUDA(launch_export_keys(idx->offs, idx->offs_stride(), idx->ent, idx->n, idx->T, idx->slot_bits, idx->ent_ib,
+                                  dslot, cnt, dkeys, idx->sm_count, s));
+    FCLSH_CUDA(cudaMemcpyAsync(keys_out, dkeys, (size_t)idx->T * cnt * 8, cudaMemcpyDeviceToHost, s));
+    FCLSH_CUDA(cudaStreamSynchronize(s));
+    return FCLSH_OK;
+}
+
 // ---------------------------------------------------------------- contexts
 
 extern "C" fclsh_status fclsh_qctx_create(fclsh_index *idx, fclsh_qctx **out)
@@ -1087,7 +1146,10 @@ extern "C" fclsh_status fclsh_query_async(fclsh_qctx *c, const uint64_t *queries
     if (radii && !is_device_ptr(radii)) return fail(FCLSH_EINVAL, "fclsh_query_async needs device radii");
     if (nq >= (1ULL << (64 - bits_for(idx->n) - 1))) return fail(FCLSH_EINVAL, "too many queries in one batch");
     if ((st = ctx_shape(c)) != FCLSH_OK) return st;
-    const uint64_t want = std::max<uint64_t>(c->cap, std::min<uint64_t>(nq * 64, 1ULL << 26));
+    // room for 512 hits per query (up to 2^28 ids, 2 GB with the CSR copy): dense workloads
+    // average hundreds of neighbours per query, and a batch that passes it runs its
+    // overflowed queries a second time
+    const uint64_t want = std::max<uint64_t>(c->cap, std::min<uint64_t>(nq * 512, 1ULL << 28));
     if ((st = ctx_reserve(c, nq, want)) != FCLSH_OK) return st;
     cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
     c->last_q = queries;
@@ -1107,16 +1169,19 @@ extern "C" fclsh_status fclsh_qctx_wait(fclsh_qctx *c, fclsh_device_result *out)
     fclsh_index *idx = c->idx;
     FCLSH_CUDA(cudaSetDevice(idx->device));
     if (c->pending && c->last_nq) {
-        for (int attempt = 0; attempt < 8; ++attempt) {
-            unsigned long long cur = 0;
-            FCLSH_CUDA(cudaMemcpyAsync(&cur, c->counters + 1, 8, cudaMemcpyDeviceToHost, c->last_stream));
+        unsigned long long cur = 0;
+        FCLSH_CUDA(cudaMemcpyAsync(&cur, c->counters + 1, 8, cudaMemcpyDeviceToHost, c->last_stream));
+        FCLSH_CUDA(cudaStreamSynchronize(c->last_stream));
+        if (cur > c->cap) {
+            // The runs passed the buffer: every query reserved its run all the same (the cursor
+            // is the batch's total), so grow the buffer to the total, keep the runs that fitted,
+            // and run only the queries whose run passed the old end again, into their places.
+            const uint64_t old_cap = c->cap;
+            fclsh_status st = ctx_grow_runs(c, cur + 1024, c->last_stream);
+            if (st != FCLSH_OK) return st;
+            st = enqueue_batch(c, c->last_q, c->last_nq, c->last_radius, c->last_radii, c->last_stream, old_cap);
+            if (st != FCLSH_OK) return st;
             FCLSH_CUDA(cudaStreamSynchronize(c->last_stream));
-            if (cur <= c->cap) break;
-            // the staging buffer overflowed: grow it and run the batch again
-            fclsh_status st = ctx_reserve(c, c->last_nq, cur + cur / 4 + 1024);
-            if (st != FCLSH_OK) return st;
-            st = run_batch(c, c->last_q, c->last_nq, c->last_radius, c->last_radii, c->last_stream);
-            if (st != FCLSH_OK) return st;
         }
     }
     c->pending = false;
@@ -1674,7 +1739,7 @@ uint32_t fclsh::debug_withhold_loads() { return g_withhold.load(); }
 
 extern "C" fclsh_status fclsh_debug_withhold_hash_loads(int on)
 {
-    g_withhold.store(on ? 1u : 0u);
+    g_withhold.store(on > 0 ? (uint32_t)on : 0u);
     return FCLSH_OK;
 }
 

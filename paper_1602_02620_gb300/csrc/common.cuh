@@ -111,6 +111,10 @@ struct QueryArgs {
     uint32_t *runs;               // batched path: each query's sorted hits, one contiguous run per query
     uint64_t *run_base;           // [nq] start of query i's run in `runs`
     uint64_t cap;
+    // 0: a query reserves its run with an atomic on *cursor.  Else a second pass after the
+    // runs overflowed a buffer of redo_cap ids: only the queries whose run passed redo_cap run
+    // again, into the places they reserved (run_base, res_cnt from the first pass).
+    uint64_t redo_cap;
     uint32_t idbits;
     uint32_t *res_cnt;
     unsigned long long *coll, *cand;
@@ -213,6 +217,9 @@ void note_launch(uint64_t kernels = 1);   // kernels enqueued by this library
 uint64_t launch_count();
 int64_t launch_count_adjust(int64_t delta);
 fclsh_status cuda_fail(cudaError_t e, const char *what);
+// Device or managed memory (cudaPointerGetAttributes; allocates nothing).  Host memory,
+// registered or not, and unknown pointers are not.
+bool is_device_ptr(const void *p);
 
 #define FCLSH_CUDA(call)                                   \
     do {                                                   \
@@ -220,8 +227,8 @@ fclsh_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return fclsh::cuda_fail(e_, #call); \
     } while (0)
 
-// Testing aid (api.cu): nonzero while the tensor-core hash is told to withhold its first
-// operand copy, so that its bounded waits run out (fclsh_debug_withhold_hash_loads).
+// Testing aid (api.cu): c + 1 while the tensor-core hash is told to withhold its operand
+// copy of chunk c, so that its bounded waits run out (fclsh_debug_withhold_hash_loads); 0 = off.
 uint32_t debug_withhold_loads();
 
 // ---- params.cpp
@@ -312,6 +319,11 @@ uint32_t msd_bin_capacity(uint64_t n, uint32_t dbits);
 // Directory of each sorted row: ent = (key >> sb) << 32 | id, offs[slot] = first entry of slot.
 cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint32_t rows, uint64_t len,
                                  uint32_t slot_bits, uint64_t *ent, uint32_t *offs, cudaStream_t s);
+// Keys stored in the directory for sampled point ids: keys[tau * cnt + slot_of_id[id]] for every
+// entry of every table whose id has slot_of_id[id] != ~0 (read-back for parity checks).
+cudaError_t launch_export_keys(const uint32_t *offs, uint64_t offs_stride, const uint64_t *ent, uint64_t n, uint32_t T,
+                               uint32_t sb, uint32_t ib, const uint32_t *slot_of_id, uint64_t cnt, uint64_t *keys,
+                               int sm_count, cudaStream_t s);
 // Exclusive scan of u32 values into u64 offsets: out[i] = sum_{j<i} in[j], out[count] = total.
 cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, uint64_t *partials,
                             cudaStream_t s);

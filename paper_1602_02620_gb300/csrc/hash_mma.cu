@@ -173,13 +173,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // TMEM and (lane 0) moves G's chunks and issues the MMAs.  Barriers per buffer b:
 // gfull[b] (chunk landed), afull[b] (MMAs done: accumulator ready, G buffer free),
 // aempty[b] (16 warps have read the accumulator).  Every wait is bounded; a wait that
-// runs out sets s_abort and every loop stops at its next check.
+// runs out sets s_abort and every loop stops at its next check.  Before the tensor memory
+// is released after a stop, the producer waits (bounded again) for the MMAs it committed
+// and the bulk copies it requested, so that none of them writes TMEM or shared memory
+// after the block has let them go.
 __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
                                                                   uint32_t words, const uint32_t *__restrict__ coord,
                                                                   uint32_t K, const uint16_t *__restrict__ gmat,
                                                                   uint32_t chunks, uint32_t L,
                                                                   uint64_t *__restrict__ keys, uint64_t ld,
-                                                                  uint32_t *status, uint32_t withhold_first)
+                                                                  uint32_t *status, uint32_t withhold)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t gfull[2], afull[2], aempty[2];
@@ -193,6 +196,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t
     unsigned char *xa = base;
     auto gb = [&](uint32_t i) { return base + (1 + i) * tile_bytes; };   // the two G chunk buffers
     const uint64_t p0 = (uint64_t)blockIdx.x * kMmaM;
+    // producer's record for a clean stop: the last chunk whose MMAs were committed, and per
+    // G buffer the chunk whose copy was requested and not yet waited for (-1: none)
+    int32_t last_commit = -1, pending0 = -1, pending1 = -1;
 
     if (warp == kConsumerWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
@@ -207,10 +213,16 @@ __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t
             }
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             s_abort = 0;
-            // withhold_first (tests of the bounded waits): chunk 0 is never requested, so the
-            // first waits run out and the kernel reports it in *status
-            if (!withhold_first) bulk_load(gb(0), gmat, tile_bytes, &gfull[0]);
-            if (chunks > 1) bulk_load(gb(1), gmat + (size_t)K * kMmaN, tile_bytes, &gfull[1]);
+            // withhold = c + 1 (tests of the bounded waits): chunk c is never requested, so the
+            // wait for it runs out and the kernel reports it in *status
+            if (withhold != 1) {
+                bulk_load(gb(0), gmat, tile_bytes, &gfull[0]);
+                pending0 = 0;
+            }
+            if (chunks > 1 && withhold != 2) {
+                bulk_load(gb(1), gmat + (size_t)K * kMmaN, tile_bytes, &gfull[1]);
+                pending1 = 1;
+            }
         }
     } else {
         // X's tile: thread (p, quarter) writes a quarter of point p's K coordinates as fp16 0/1
@@ -241,14 +253,19 @@ __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t
                     s_abort = 1;
                     break;
                 }
+                if (b) pending1 = -1; else pending0 = -1;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 issue_chunk(tmem, b * kMmaN, saddr(xa), saddr(gb(b)), K, &afull[b]);
+                last_commit = (int32_t)c;
                 if (c + 2 < chunks) {   // G buffer b is free once these MMAs are done
                     if (!mbar_wait(&afull[b], (c >> 1) & 1u)) {
                         s_abort = 1;
                         break;
                     }
-                    bulk_load(gb(b), gmat + (size_t)(c + 2) * K * kMmaN, tile_bytes, &gfull[b]);
+                    if (withhold != c + 3) {
+                        bulk_load(gb(b), gmat + (size_t)(c + 2) * K * kMmaN, tile_bytes, &gfull[b]);
+                        if (b) pending1 = (int32_t)(c + 2); else pending0 = (int32_t)(c + 2);
+                    }
                 }
             }
         }
@@ -297,6 +314,13 @@ __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t
     __syncthreads();
     if (tid == 0 && s_abort) atomicOr(status, 1u);
     if (warp == kConsumerWarps) {
+        if (lane == 0 && s_abort) {   // drain what was issued before letting TMEM and shared memory go
+            // the last commit arrives once every MMA before it is done (they complete in order)
+            if (last_commit >= 0) mbar_wait(&afull[last_commit & 1], ((uint32_t)last_commit >> 1) & 1u);
+            if (pending0 >= 0) mbar_wait(&gfull[0], ((uint32_t)pending0 >> 1) & 1u);
+            if (pending1 >= 0) mbar_wait(&gfull[1], ((uint32_t)pending1 >> 1) & 1u);
+        }
+        __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }

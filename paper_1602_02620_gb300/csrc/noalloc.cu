@@ -168,6 +168,12 @@ extern "C" fclsh_status fclsh_query_plain_noalloc(const fclsh_index *cidx, const
         return FCLSH_EINVAL;
     }
     FCLSH_CUDA(cudaSetDevice(idx->device));
+    // the kernels read the query and write the outputs on the device: host memory is refused
+    // here rather than faulting there
+    if (!is_device_ptr(query) || !is_device_ptr(counts_out) || (cap && !is_device_ptr(ids_out))) {
+        set_error("fclsh_query_plain_noalloc needs device memory for query, ids_out and counts_out");
+        return FCLSH_EINVAL;
+    }
     uint64_t *base = nullptr;
     fclsh_status st = scratch_address(idx->device, &base);
     if (st != FCLSH_OK) return st;

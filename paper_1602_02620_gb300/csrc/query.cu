@@ -251,6 +251,10 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         __syncthreads();
         const uint64_t qi = s_qi;
         if (qi >= a.nq) break;
+        if (a.redo_cap && a.run_base[qi] + a.res_cnt[qi] <= a.redo_cap) {   // its run fitted (block-uniform)
+            __syncthreads();
+            continue;
+        }
         for (uint32_t w = tid; w < a.words; w += B) q_s[w] = a.queries[qi * a.words + w];
         const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
         __syncthreads();
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         }
         if (nres <= kResCap) {
             block_sort_u32(res_s, nres);
-            if (tid == 0) s_base = atomicAdd(a.cursor, (unsigned long long)nres);
+            if (tid == 0) s_base = a.redo_cap ? a.run_base[qi] : atomicAdd(a.cursor, (unsigned long long)nres);
             __syncthreads();
             const unsigned long long base = s_base;
             for (uint32_t i = tid; i < nres; i += B)
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                     if (distance_to(a, q_s, id) <= radius) atomicOr(bm + (id >> 5), 1u << (id & 31));
                 }
             }
-            if (tid == 0) s_base = atomicAdd(a.cursor, (unsigned long long)nres);
+            if (tid == 0) s_base = a.redo_cap ? a.run_base[qi] : atomicAdd(a.cursor, (unsigned long long)nres);
             __syncthreads();
             const unsigned long long base = s_base;
             const uint64_t per = (a.bm_words + B - 1) / B;

@@ -1178,4 +1178,43 @@ uint32_t msd_bin_capacity(uint64_t n, uint32_t dbits)
     return (uint32_t)((c + 3) & ~3ULL);
 }
 
+// ---------------------------------------------------------------- directory read-back
+
+// The keys the build stored for sampled points (a diagnostic): every (table, slot) walks
+// its run, and an entry whose id is sampled (slot_of_id[id] = its place in the sample, else
+// ~0) writes its key, the stored high bits above the slot bits, to keys[table][place].
+__global__ void __launch_bounds__(256) export_keys_kernel(const uint32_t *__restrict__ offs, uint64_t offs_stride,
+                                                          const uint64_t *__restrict__ ent, uint64_t n, uint32_t T,
+                                                          uint32_t sb, uint32_t ib,
+                                                          const uint32_t *__restrict__ slot_of_id, uint64_t cnt,
+                                                          uint64_t *__restrict__ keys)
+{
+    const uint64_t slots = 1ULL << sb, total = (uint64_t)T * slots;
+    const uint64_t idmask = (1ULL << ib) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t tau = i >> sb, sl = i & (slots - 1);
+        const uint32_t *O = offs + tau * offs_stride + sl;
+        const uint32_t lo = O[0], hi = O[1];
+        const uint64_t *row = ent + tau * n;
+        for (uint32_t e = lo; e < hi && e < n; ++e) {
+            const uint64_t en = row[e];
+            const uint64_t id = en & idmask;
+            if (id >= n) continue;
+            const uint32_t j = slot_of_id[id];
+            if (j != 0xFFFFFFFFu && j < cnt) keys[tau * cnt + j] = ((en >> ib) << sb) | sl;
+        }
+    }
+}
+
+cudaError_t launch_export_keys(const uint32_t *offs, uint64_t offs_stride, const uint64_t *ent, uint64_t n, uint32_t T,
+                               uint32_t sb, uint32_t ib, const uint32_t *slot_of_id, uint64_t cnt, uint64_t *keys,
+                               int sm_count, cudaStream_t s)
+{
+    export_keys_kernel<<<(unsigned)(sm_count * 8), 256, 0, s>>>(offs, offs_stride, ent, n, T, sb, ib, slot_of_id, cnt,
+                                                                 keys);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace fclsh

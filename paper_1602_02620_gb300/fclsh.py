@@ -82,6 +82,7 @@ SIGNATURES = {
     "fclsh_hash": (_i, [_vp, _vp, _u64, _vp, _vp]),
     "fclsh_bucket": (_i, [_vp, _u32, _u64, _vp, _u64, _vp]),
     "fclsh_export_table": (_i, [_vp, _u32, _vp, _vp]),
+    "fclsh_export_keys": (_i, [_vp, _vp, _u64, _vp]),
     "fclsh_query": (_i, [_vp, _vp, _u64, _u32, _vp, _vp, _vp]),
     "fclsh_query_plain": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
     "fclsh_bruteforce": (_i, [_vp, _vp, _u64, _u32, _vp, _vp]),
@@ -268,6 +269,13 @@ class Index:
         _check(lib().fclsh_export_table(self.handle, table, _ptr(keys), _ptr(ids)))
         return keys, ids
 
+    def export_keys(self, ids) -> np.ndarray:
+        """Keys [T][len(ids)] the build stored for the given point ids, read back from the tables."""
+        ids = np.ascontiguousarray(ids, np.uint32)
+        out = np.zeros((self.T, ids.shape[0]), np.uint64)
+        _check(lib().fclsh_export_keys(self.handle, _ptr(ids), ids.shape[0], _ptr(out)))
+        return out
+
     # -- queries
     def query(self, queries, radius: int, radii=None, stream=None) -> QueryResult:
         rp = ctypes.POINTER(Result)()
@@ -282,8 +290,25 @@ class Index:
         return _take_result(rp)
 
     def query_plain_noalloc(self, query, radius: int, ids_out, counts_out, stream=None):
-        """One query without allocating (device query, device outputs); asynchronous on `stream`."""
-        _check(lib().fclsh_query_plain_noalloc(self.handle, _ptr(query), radius, _ptr(ids_out), ids_out.shape[0],
+        """One query without allocating (device query, device outputs); asynchronous on `stream`.
+
+        query: CUDA tensor of at least `words` 64-bit words; ids_out: CUDA int32/uint32 tensor
+        (its length is the capacity); counts_out: CUDA int64 tensor of at least 3 elements."""
+        def bad(why):
+            raise FclshError(EINVAL, "query_plain_noalloc: " + why)
+
+        for name, a in (("query", query), ("ids_out", ids_out), ("counts_out", counts_out)):
+            if not getattr(a, "is_cuda", False):
+                bad("%s must be a CUDA tensor" % name)
+            if not a.is_contiguous():
+                bad("%s must be contiguous" % name)
+        if query.numel() * query.element_size() < 8 * self.words:
+            bad("query holds fewer than %d 64-bit words" % self.words)
+        if str(ids_out.dtype) not in ("torch.int32", "torch.uint32"):
+            bad("ids_out must be int32 or uint32 (got %s)" % ids_out.dtype)
+        if str(counts_out.dtype) != "torch.int64" or counts_out.numel() < 3:
+            bad("counts_out must be int64 with at least 3 elements")
+        _check(lib().fclsh_query_plain_noalloc(self.handle, _ptr(query), radius, _ptr(ids_out), ids_out.numel(),
                                                _ptr(counts_out), _stream(stream)))
 
     def bruteforce(self, queries, radius: int, stream=None) -> QueryResult:
@@ -436,9 +461,10 @@ def debug_fail_alloc(after: int) -> None:
     _check(lib().fclsh_debug_fail_alloc(after))
 
 
-def debug_withhold_hash_loads(on: bool) -> None:
-    """Make the tensor-core hash kernel's bounded waits run out (tests of ETIMEOUT)."""
-    _check(lib().fclsh_debug_withhold_hash_loads(1 if on else 0))
+def debug_withhold_hash_loads(on, chunk: int = 0) -> None:
+    """Make the tensor-core hash kernel's bounded waits run out (tests of ETIMEOUT): while on,
+    its operand chunk `chunk` is never requested (chunk 0: before any MMA is issued)."""
+    _check(lib().fclsh_debug_withhold_hash_loads(chunk + 1 if on else 0))
 
 
 def debug_pool_used() -> int:

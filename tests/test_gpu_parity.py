@@ -412,3 +412,39 @@ def test_wide_partition_directory_matches_oracle(slot_bits, skewed):
         assert np.array_equal(res.of(i), want)
         assert (int(res.collisions[i]), int(res.candidates[i])) == (ncoll, ncand)
     idx.free()
+
+
+@pytest.mark.parametrize("dup,nq", [(2000, 2200), (20_000, 260)])
+def test_result_overflow_reruns_only_the_queries_past_the_buffer(dup, nq):
+    """A batch whose hits pass a fresh context's result buffer (2^22 ids): every query reserved
+    its run all the same, the buffer grows to the batch's total keeping the runs that fitted,
+    and only the queries whose run passed the old end run again.  Queries near a point
+    repeated `dup` times have about `dup` hits each (the shared-memory sort below 4,096 hits,
+    the bitmap read-out above).  Every answer equals the linear scan, and the same batch on
+    the grown context (eager, then replayed as a graph) gives the same ids and counters."""
+    rng = np.random.default_rng(dup)
+    d, r = 64, 3
+    n = dup + 3000
+    pts = rand_points(rng, n, d)
+    pts[:dup] = pts[0]
+    qs = near(rng, pts[:1], d, r, nq)
+    idx = F().build(pts, d, r, 31)
+    ctx = idx.context()
+    ctx.query_async(dev(qs), r)
+    first = ctx.fetch()
+    assert int(first.offs[-1]) > (1 << 22)                     # the batch did pass the buffer
+    for i in range(nq):
+        assert np.array_equal(first.of(i), oracle.linear_scan(pts, qs[i], r)), i
+    q_dev = dev(qs)
+    for _ in range(3):                                         # no overflow now; the third is a graph replay
+        ctx.query_async(q_dev, r)
+        again = ctx.fetch()
+        assert np.array_equal(again.offs, first.offs) and np.array_equal(again.ids, first.ids)
+        assert np.array_equal(again.collisions, first.collisions)
+        assert np.array_equal(again.candidates, first.candidates)
+    ctx.close()
+    plain = idx.query_plain(qs[:3], r)
+    for i in range(3):
+        assert np.array_equal(plain.of(i), first.of(i))
+        assert plain.collisions[i] == first.collisions[i] and plain.candidates[i] == first.candidates[i]
+    idx.free()

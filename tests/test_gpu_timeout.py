@@ -60,3 +60,29 @@ def test_hash_wait_runs_out_and_the_index_stays_usable():
     again = fc.build(pts, d, r, 3, hash_tile=2)
     assert np.array_equal(again.hash(pts[:200]), want)
     again.free()
+
+
+def test_hash_wait_runs_out_after_mmas_were_issued():
+    """The third operand chunk is withheld: the MMAs of the first two chunks and the copy of
+    the fourth are in flight when the wait runs out; the kernel drains them before it
+    releases its tensor memory, and the index then hashes and queries correctly."""
+    from paper_1602_02620_gb300 import fclsh as fc
+
+    rng = np.random.default_rng(2)
+    d, r, n = 128, 8, 3000                                    # W = 512: 22 chunks of 24 tables
+    pts = rng.integers(0, 2**63, size=(n, 2), dtype=np.uint64)
+    idx = fc.build(pts, d, r, 5, hash_tile=2)
+    p = oracle.derive_params(5, d, r)
+    want = oracle.keys_direct(p, pts[:300])
+    fc.debug_withhold_hash_loads(True, chunk=2)
+    try:
+        with pytest.raises(fc.FclshError) as e:
+            idx.hash(pts[:300])
+        assert e.value.status == fc.ETIMEOUT
+    finally:
+        fc.debug_withhold_hash_loads(False)
+    assert np.array_equal(idx.hash(pts[:300]), want)
+    res = idx.query(pts[:20], r)
+    for i in range(20):
+        assert res.of(i).tolist() == oracle.linear_scan(pts, pts[i], r).tolist()
+    idx.free()

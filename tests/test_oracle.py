@@ -538,6 +538,38 @@ def test_counters_follow_their_definitions(d, r, t, rep):
             assert ncand == int(sel.any(axis=0).sum())
 
 
+@pytest.mark.parametrize("d,r,t", [(64, 6, 1), (96, 12, 2), (90, 21, 3)])
+def test_listed_query_follows_the_definitions(d, r, t):
+    """The query given only the tables it probes: its ids are the linear scan's at the query's
+    radius (total recall through the probed rows, Theorem 1 and the pigeonhole of Sec. 3.1),
+    and #Collisions / #Candidates are recomputed from their definitions (Sec. 4.1) with the
+    Algorithm 2 keys and plain numpy.  A probed table that is not given is an error."""
+    rng = np.random.default_rng(d * 3 + r)
+    words = (d + 63) // 64
+    n = 400
+    pts = rng.integers(0, 2**63, size=(n, words), dtype=np.uint64)
+    if d % 64:
+        pts[:, -1] &= np.uint64((1 << (d % 64)) - 1)
+    pts[20:40] = pts[7]
+    p = oracle.derive_params(d + 11, d, r, t=t)
+    keys = oracle.keys_fht(p, pts)
+    for radius in (0, 2, r // 2):
+        rows = oracle.probe_rows(p, radius)
+        taus = oracle.probed_tables(p, rows)
+        tables = {tau: oracle.table(p, pts, tau) for tau in taus}
+        for qi in range(6):
+            q = pts[rng.integers(0, n)].copy()
+            for pos in rng.choice(d, size=rng.integers(0, radius + 2), replace=False):
+                q[pos >> 6] ^= np.uint64(1) << np.uint64(pos & 63)
+            ids, ncoll, ncand = oracle.query_listed(p, pts, tables, q, radius, rows=rows)
+            assert np.array_equal(ids, oracle.linear_scan(pts, q, radius))
+            hit = keys[taus] == oracle.keys_fht(p, q)[taus, 0][:, None]
+            assert ncoll == int(hit.sum()) and ncand == int(hit.any(axis=0).sum())
+        if rows < p.W - 1:
+            with pytest.raises(ValueError):
+                oracle.query_listed(p, pts, {tau: tables[tau] for tau in taus[1:]}, pts[0], radius, rows=rows)
+
+
 def test_oracle_routes_agree_on_random_parameters():
     """Lemma 3 (direct route == Algorithm 2) and total recall on parameters drawn at random
     (dimension, radius, parts or copies, seed)."""
