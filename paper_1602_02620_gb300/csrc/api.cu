@@ -460,6 +460,8 @@ static QueryArgs make_args(fclsh_index *idx)
     a.rep = idx->rep;
     a.ent_ib = idx->ent_ib;
     a.d = idx->d;
+    a.sig = idx->tune.verify_filter ? idx->sig : nullptr;
+    a.sig_block = idx->sig_block;
     // long parts: the query's sketch from its set bits (O(nnz)) rather than from every position
     a.s1_scatter = idx->scatter_ok() && idx->positions() / idx->t >= kS1ScatterPositions;
     a.sc_off = idx->sc_off;
@@ -704,7 +706,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->W = W;
     idx->T = t * (W - 1);
     if (o.hash_tile > 4) return fail(FCLSH_EINVAL, "hash_tile must be 0..4");
-    idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0};
+    idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0, 0};
     idx->timing = o.timing != 0;
 
     const bool explicit_params = o.perm || o.part_off || o.m || o.b;
@@ -810,6 +812,21 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if (idx->sc_b) FCLSH_CUDA(cudaMemcpyAsync(idx->sc_b, sblock.data(), sblock.size() * 8, cudaMemcpyHostToDevice, s));
     if ((e = keep.alloc(&idx->status, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
     FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
+    // block-occupancy signatures of the points (S3's pre-filter) and their popcount total,
+    // which decides the filter's default: on when the points average at most d/8 set bits
+    idx->sig_block = (d + 63) / 64;
+    if ((e = keep.alloc(&idx->sig, n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(signatures)");
+    idx->device_bytes += n * 8;
+    unsigned long long *d_pop = nullptr, pop_total = 0;
+    {
+        DevAllocs one(true);
+        if ((e = one.alloc(&d_pop, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(popcount total)");
+        FCLSH_CUDA(cudaMemsetAsync(d_pop, 0, 8, s));
+        FCLSH_CUDA(launch_point_sig(idx->points, n, idx->words, d, idx->sig_block, idx->sig, d_pop, idx->sm_count, s));
+        FCLSH_CUDA(cudaMemcpyAsync(&pop_total, d_pop, 8, cudaMemcpyDeviceToHost, s));
+        FCLSH_CUDA(cudaStreamSynchronize(s));
+    }
+    idx->tune.verify_filter = (double)pop_total <= (double)n * d / 8.0 ? 1u : 0u;
     if (o.hash_tile == 2) {
         fclsh_status st = ensure_mma_operands(idx, s, &keep);
         if (st != FCLSH_OK) return st;
@@ -874,8 +891,11 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     }
     // The partition path first partitions into fixed-capacity bins (no histogram pass).
     // A row chunk whose bins overflow (skewed keys) is partitioned again the exact way,
-    // with a per-tile digit histogram, and the remaining chunks go that way at once.
+    // with a per-tile digit histogram, and the remaining chunks go that way at once.  The
+    // first binned chunk is a single table, so that data whose every table overflows (the
+    // empty-sum bucket of sparse points) loses one table's partition, not a chunk's.
     bool use_bins = msd;
+    bool bins_tried = false;
 
     for (uint32_t k = 0; k < t; ++k) {
         {
@@ -885,8 +905,8 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         }
         NvtxRange ns("fclsh_build: bucket tables of the part");
         PhaseTimer pt(idx, 1, s);
-        for (uint64_t r0 = 0; r0 < L; r0 += rows) {
-            const uint32_t nr = (uint32_t)std::min<uint64_t>(rows, L - r0);
+        for (uint64_t r0 = 0; r0 < L;) {
+            const uint32_t nr = (uint32_t)std::min<uint64_t>(msd && use_bins && !bins_tried ? 1 : rows, L - r0);
             const uint64_t grow = (uint64_t)k * L + r0;
             if (msd) {
                 bool binned = false;
@@ -900,6 +920,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
                     FCLSH_CUDA(cudaStreamSynchronize(s));
                     binned = status == 0;
                     use_bins = binned;
+                    bins_tried = true;
                 }
                 if (!binned) {
                     {
@@ -912,12 +933,14 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
                 PhaseTimer p6(idx, 6, s);
                 FCLSH_CUDA(msd_finish(nr, n, sb, binned ? cap : 0, sbuf, big_cnt, big, idx->ent + grow * n,
                                       idx->offs + grow * idx->offs_stride(), idx->sm_count, s));
+                r0 += nr;
                 continue;
             }
             bool in_b = false;
             FCLSH_CUDA(radix_sort_rows(keys + r0 * n, nr, n, sb, sbuf, &in_b, s));
             FCLSH_CUDA(launch_finalize_rows(in_b ? sbuf.keys_b : sbuf.keys_a, in_b ? sbuf.ids_b : sbuf.ids_a, nr, n, sb,
                                             idx->ent + grow * n, idx->offs + grow * idx->offs_stride(), s));
+            r0 += nr;
         }
     }
     FCLSH_CUDA(cudaStreamSynchronize(s));
@@ -938,7 +961,7 @@ extern "C" void fclsh_free(fclsh_index *idx)
     cudaDeviceSynchronize();
     drop_timers(idx);
     void *ps[] = {idx->points, idx->col_b /* the column-list block */, idx->sc_b /* the coordinate-list block */,
-                  idx->offs, idx->ent, idx->mma_coord, idx->mma_g,
+                  idx->offs, idx->ent, idx->mma_coord, idx->mma_g, idx->sig,
                   idx->status};
     for (void *p : ps)
         if (p) dev_free(p);
@@ -1483,6 +1506,7 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
         if (st != FCLSH_OK) return st;
     }
     if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
+    if (t->verify_filter > 1) return fail(FCLSH_EINVAL, "verify_filter must be 0 or 1");
     uint32_t max_dk = 0;
     for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
     if (t->hash_tile == 4 && max_dk > kDirectMaxPositions)
@@ -1722,7 +1746,7 @@ extern "C" fclsh_status fclsh_load(const char *path, fclsh_index **out)
         fclsh_free(idx);
         return fail(FCLSH_EINVAL, "%s: code length %u does not follow from its header", path, W);
     }
-    const fclsh_tuning tu{tune[0], tune[1], tune[2], tune[3], tune[4], tune[5], tune[6]};
+    const fclsh_tuning tu{tune[0], tune[1], tune[2], tune[3], tune[4], tune[5], tune[6], idx->tune.verify_filter};
     if ((st = fclsh_set_tuning(idx, &tu)) != FCLSH_OK) {
         fclsh_free(idx);
         return st;
@@ -1805,7 +1829,8 @@ static bool cache_lookup(const char *path, const std::string &key, fclsh_tuning 
     fclsh_tuning v{};
     if (!read_field(obj, "query_block", &v.query_block) || !read_field(obj, "query_ctas_per_sm", &v.query_ctas_per_sm) ||
         !read_field(obj, "hash_set_log2", &v.hash_set_log2) || !read_field(obj, "inline_probe", &v.inline_probe) ||
-        !read_field(obj, "use_graph", &v.use_graph) || !read_field(obj, "hash_tile", &v.hash_tile))
+        !read_field(obj, "use_graph", &v.use_graph) || !read_field(obj, "hash_tile", &v.hash_tile) ||
+        !read_field(obj, "verify_filter", &v.verify_filter))
         return false;
     *t = v;
     return true;
@@ -1826,8 +1851,9 @@ static void cache_store(const char *path, const std::string &key, const fclsh_tu
     char ent[512];
     snprintf(ent, sizeof ent,
              "  \"%s\": {\"query_block\": %u, \"query_ctas_per_sm\": %u, \"hash_set_log2\": %u, \"inline_probe\": %u, "
-             "\"use_graph\": %u, \"hash_tile\": %u}",
-             key.c_str(), t.query_block, t.query_ctas_per_sm, t.hash_set_log2, t.inline_probe, t.use_graph, t.hash_tile);
+             "\"use_graph\": %u, \"hash_tile\": %u, \"verify_filter\": %u}",
+             key.c_str(), t.query_block, t.query_ctas_per_sm, t.hash_set_log2, t.inline_probe, t.use_graph, t.hash_tile,
+             t.verify_filter);
     lines.push_back(ent);
     std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
@@ -1876,7 +1902,7 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
             for (uint32_t il : inl)
                 for (uint32_t ct : ctas) {
                     if (st != FCLSH_OK) break;
-                    fclsh_tuning t{bk, ct, hl, il, 0, saved.hash_tile, saved.probe_rows};
+                    fclsh_tuning t{bk, ct, hl, il, 0, saved.hash_tile, saved.probe_rows, saved.verify_filter};
                     if (query_smem_bytes(idx->T, idx->W, idx->words, hl) > idx->smem_optin) continue;
                     int occ = 0;
                     if (query_batch_occupancy(bk, query_smem_bytes(idx->T, idx->W, idx->words, hl), &occ) != cudaSuccess ||
@@ -1899,6 +1925,25 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
                         best = t;
                     }
                 }
+    // S3's signature pre-filter, on and off, with the chosen shape
+    if (st == FCLSH_OK) {
+        float ms_f[2] = {1e30f, 1e30f};
+        for (uint32_t vf = 0; vf <= 1; ++vf) {
+            fclsh_tuning t = best;
+            t.use_graph = 0;
+            t.verify_filter = vf;
+            idx->tune = t;
+            if (fclsh_query_async(c, dq, nq, radius, nullptr, s) != FCLSH_OK || fclsh_qctx_wait(c, nullptr) != FCLSH_OK)
+                continue;
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 2; ++rep) fclsh_query_async(c, dq, nq, radius, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (fclsh_qctx_wait(c, nullptr) != FCLSH_OK) continue;
+            cudaEventElapsedTime(&ms_f[vf], e0, e1);
+        }
+        if (ms_f[0] < 1e30f || ms_f[1] < 1e30f) best.verify_filter = ms_f[1] <= ms_f[0] ? 1u : 0u;
+        idx->tune = best;
+    }
     // the hash kernel: WHT tiles and the tensor-core contraction on the index's first points
     // (about 2 GB of keys: enough blocks that the timing reflects a full build)
     if (st == FCLSH_OK) {

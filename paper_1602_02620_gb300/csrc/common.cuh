@@ -120,6 +120,11 @@ struct QueryArgs {
     unsigned long long *coll, *cand;
     uint32_t *bitmaps;            // [gridDim.x][bm_words]
     uint64_t bm_words;
+    // S3 pre-filter (nullptr = off): sig[id] has bit j set when point id has a set coordinate
+    // in block j = coordinates [j * sig_block, (j + 1) * sig_block); a candidate whose distance
+    // lower bound from the two signatures passes the radius is rejected without reading it
+    const uint64_t *sig;
+    uint32_t sig_block;
 };
 
 // A directory entry holds the key's high 50 - s bits above an ent_ib-bit id: 32 id bits
@@ -133,6 +138,36 @@ __device__ __forceinline__ uint32_t entry_id(uint64_t en, uint32_t ib)
 {
     return (uint32_t)(en & ((1ULL << ib) - 1));
 }
+
+#if defined(__CUDACC__)   // device intrinsics: CUDA translation units only
+// Set coordinates of the packed vector x in [lo, hi) (lo < hi).
+__device__ __forceinline__ uint32_t popc_range(const uint64_t *x, uint32_t lo, uint32_t hi)
+{
+    const uint32_t w0 = lo >> 6, w1 = (hi - 1) >> 6;
+    uint32_t c = 0;
+    for (uint32_t w = w0; w <= w1; ++w) {
+        uint64_t v = x[w];
+        if (w == w0) v &= ~0ULL << (lo & 63);
+        if (w == w1 && (hi & 63)) v &= (1ULL << (hi & 63)) - 1;
+        c += __popcll(v);
+    }
+    return c;
+}
+
+// Lower bound on the Hamming distance of x and q from their block-occupancy signatures:
+// every block where only x has set coordinates differs in at least one, and every block
+// where only q has them differs in all of q's (pcq[j], q's count in block j).
+__device__ __forceinline__ uint32_t sig_bound(uint64_t sx, uint64_t sq, const uint8_t *pcq)
+{
+    uint32_t lb = __popcll(sx & ~sq);
+    uint64_t m = sq & ~sx;
+    while (m) {
+        lb += pcq[__ffsll((long long)m) - 1];
+        m &= m - 1;
+    }
+    return lb;
+}
+#endif
 
 // Code rows a query of this radius probes in every part: all W-1, or with
 // probe_rows only v = 1..2^(floor(radius*rep/t)+1)-1 (a point within the radius is
@@ -186,6 +221,8 @@ struct fclsh_index {
     uint32_t *mma_coord = nullptr;
     uint16_t *mma_g = nullptr;
     uint32_t *status = nullptr;      // [1] device word: bit 0 = a kernel's bounded wait ran out
+    uint64_t *sig = nullptr;         // [n] block-occupancy signature of every point (S3 pre-filter)
+    uint32_t sig_block = 1;          // coordinates per signature block: ceil(d / 64)
     uint64_t device_bytes = 0;
     fclsh_tuning tune{};
     // timing (CUDA events per phase)
@@ -324,6 +361,10 @@ cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint
 cudaError_t launch_export_keys(const uint32_t *offs, uint64_t offs_stride, const uint64_t *ent, uint64_t n, uint32_t T,
                                uint32_t sb, uint32_t ib, const uint32_t *slot_of_id, uint64_t cnt, uint64_t *keys,
                                int sm_count, cudaStream_t s);
+// Block-occupancy signatures of n points (bit j: a set coordinate in [j B, (j + 1) B) with
+// B = sig_block) and the total of their popcounts added to *pop_total.
+cudaError_t launch_point_sig(const uint64_t *pts, uint64_t n, uint32_t words, uint32_t d, uint32_t sig_block,
+                             uint64_t *sig, unsigned long long *pop_total, int sm_count, cudaStream_t s);
 // Exclusive scan of u32 values into u64 offsets: out[i] = sum_{j<i} in[j], out[count] = total.
 cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, uint64_t *partials,
                             cudaStream_t s);

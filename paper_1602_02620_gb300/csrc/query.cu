@@ -125,9 +125,16 @@ __device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, 
 enum DedupMode { DEDUP_HSET = 0, DEDUP_BITMAP = 1, DEDUP_MARK = 2 };
 
 // One bucket entry per lane (is_coll = key matched); warp-collective.
+// S3's pre-filter: false when the signature bound already puts point id beyond the radius.
+__device__ __forceinline__ bool sig_pass(const QueryArgs &a, uint32_t id, uint64_t sq, const uint8_t *pcq,
+                                         uint32_t radius)
+{
+    return !a.sig || sig_bound(__ldg(a.sig + id), sq, pcq) <= radius;
+}
+
 __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
                                               int mode, uint32_t radius, bool is_coll, uint32_t id, Counters &c,
-                                              uint32_t *res_s, uint32_t *s_nres)
+                                              uint32_t *res_s, uint32_t *s_nres, uint64_t sq, const uint8_t *pcq)
 {
     bool isnew = false;
     if (is_coll) {
@@ -144,7 +151,7 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
     bool hit = false;
     if (a.words >= kWarpVerifyWords) {   // long points: the warp reads each new candidate together
         const uint32_t lane = threadIdx.x & 31;
-        uint32_t need = __ballot_sync(0xffffffffu, isnew);
+        uint32_t need = __ballot_sync(0xffffffffu, isnew && sig_pass(a, id, sq, pcq, radius));
         while (need) {
             const uint32_t src = __ffs(need) - 1;
             need &= need - 1;
@@ -172,7 +179,7 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
         if (isnew) c.cand++;
     } else if (isnew) {
         c.cand++;
-        hit = distance_to(a, q_s, id) <= radius;
+        hit = sig_pass(a, id, sq, pcq, radius) && distance_to(a, q_s, id) <= radius;
     }
     append_hits(hit, id, c, res_s, s_nres);
 }
@@ -238,6 +245,8 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
     __shared__ unsigned long long s_qi;
     __shared__ uint32_t s_nres;
     __shared__ unsigned long long red64[32];
+    __shared__ uint8_t s_pcq[64];                 // the query's set coordinates per signature block
+    __shared__ __align__(8) uint32_t s_sigq[2];   // the query's block-occupancy signature
 
     const uint32_t tid = threadIdx.x, B = blockDim.x;
     const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
@@ -258,6 +267,13 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         for (uint32_t w = tid; w < a.words; w += B) q_s[w] = a.queries[qi * a.words + w];
         const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
         __syncthreads();
+        if (a.sig && tid < 64) {   // warps 0 and 1 (blocks have >= 128 threads); read after S1's barriers
+            const uint32_t lo = tid * a.sig_block;
+            const uint32_t pc = lo < a.d ? popc_range(q_s, lo, min(lo + a.sig_block, a.d)) : 0u;
+            s_pcq[tid] = (uint8_t)min(pc, 255u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, pc > 0);
+            if (lane == 0) s_sigq[warp] = bal;
+        }
 
         // ---- S1: Algorithm 2 for every part, in shared memory
         for (uint32_t k = 0; k < a.t; ++k) {
@@ -331,6 +347,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         __syncthreads();
 
         // ---- S2b + S3: collisions -> dedup -> verify, 32 tables per warp step
+        const uint64_t sq = a.sig ? ((uint64_t)s_sigq[1] << 32 | s_sigq[0]) : 0;
         Counters c;
         for (uint32_t base = warp * 32; base < Tq; base += nwarps * 32) {
             const uint32_t j = base + lane;
@@ -345,7 +362,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                 const bool act = e < short_len;
                 const uint64_t en = act ? __ldg(row + lo + e) : 0;
                 process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == fp,
-                              entry_id(en, a.ent_ib), c, res_s, &s_nres);
+                              entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_pcq);
             }
             uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
             while (lmask) {
@@ -361,7 +378,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                     const bool act = e < l_len;
                     const uint64_t en = act ? __ldg(lrow + e) : 0;
                     process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == l_fp,
-                                  entry_id(en, a.ent_ib), c, res_s, &s_nres);
+                                  entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_pcq);
                 }
             }
         }
@@ -383,7 +400,7 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                         const uint32_t b = __ffs(rem) - 1;
                         rem &= rem - 1;
                         id = (uint32_t)(wi * 32 + b);
-                        hit = distance_to(a, q_s, id) <= radius;
+                        hit = sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius;
                         if (hit) hits |= 1u << b;
                     }
                     append_hits(hit, id, c, res_s, &s_nres);
@@ -427,7 +444,8 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                     const uint64_t en = __ldg(row + e);
                     if (entry_fp(en, a.ent_ib) != fp) continue;
                     const uint32_t id = entry_id(en, a.ent_ib);
-                    if (distance_to(a, q_s, id) <= radius) atomicOr(bm + (id >> 5), 1u << (id & 31));
+                    if (sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius)
+                        atomicOr(bm + (id >> 5), 1u << (id & 31));
                 }
             }
             if (tid == 0) s_base = a.redo_cap ? a.run_base[qi] : atomicAdd(a.cursor, (unsigned long long)nres);
@@ -482,8 +500,19 @@ __global__ void __launch_bounds__(256) gather_runs_kernel(const uint32_t *runs, 
 __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uint64_t *keys, uint32_t *bitmap)
 {
     extern __shared__ uint64_t q_s[];
+    __shared__ uint8_t s_pcq[64];
+    __shared__ __align__(8) uint32_t s_sigq[2];
     for (uint32_t w = threadIdx.x; w < a.words; w += blockDim.x) q_s[w] = a.queries[w];
     __syncthreads();
+    if (a.sig && threadIdx.x < 64) {   // the query's signature (warps 0 and 1 of 256 threads)
+        const uint32_t lo = threadIdx.x * a.sig_block;
+        const uint32_t pc = lo < a.d ? popc_range(q_s, lo, min(lo + a.sig_block, a.d)) : 0u;
+        s_pcq[threadIdx.x] = (uint8_t)min(pc, 255u);
+        const uint32_t bal = __ballot_sync(0xffffffffu, pc > 0);
+        if ((threadIdx.x & 31) == 0) s_sigq[threadIdx.x >> 5] = bal;
+    }
+    __syncthreads();
+    const uint64_t sq = a.sig ? ((uint64_t)s_sigq[1] << 32 | s_sigq[0]) : 0;
     const uint32_t nt = rows_per_part(a, a.radius), j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.t * nt) return;
     const uint32_t tau = probed_table(j, nt, a.W - 1);
@@ -502,7 +531,7 @@ __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uin
         const uint32_t bit = 1u << (id & 31);
         if (atomicOr(bitmap + (id >> 5), bit) & bit) continue;
         cand++;
-        if (distance_to(a, q_s, id) <= a.radius) {
+        if (sig_pass(a, id, sq, s_pcq, a.radius) && distance_to(a, q_s, id) <= a.radius) {
             const unsigned long long pos = atomicAdd(a.cursor, 1ULL);
             if (pos < a.cap) a.staged[pos] = id;
         }
@@ -670,6 +699,45 @@ cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned 
                                uint64_t idmask, uint32_t *ids, int sm_count, cudaStream_t s)
 {
     extract_ids_kernel<<<(unsigned)(sm_count * 4), 256, 0, s>>>(sorted, d_count, cap, idmask, ids);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- point signatures
+
+// One warp per point: lane l counts blocks l and l + 32 (B coordinates each), the ballots
+// give the point's 64-bit block-occupancy signature; the popcounts are summed per warp and
+// added to *pop_total once per warp.
+__global__ void __launch_bounds__(256) point_sig_kernel(const uint64_t *__restrict__ pts, uint64_t n, uint32_t words,
+                                                        uint32_t d, uint32_t B, uint64_t *__restrict__ sig,
+                                                        unsigned long long *pop_total)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long pop = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const uint64_t *x = pts + i * words;
+        uint32_t half[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t lo = (lane + 32u * h) * B;
+            const uint32_t c = lo < d ? popc_range(x, lo, min(lo + B, d)) : 0u;
+            pop += c;
+            half[h] = __ballot_sync(0xffffffffu, c > 0);
+        }
+        if (lane == 0) sig[i] = (uint64_t)half[1] << 32 | half[0];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pop += __shfl_xor_sync(0xffffffffu, pop, o);
+    if (lane == 0 && pop) atomicAdd(pop_total, pop);
+}
+
+cudaError_t launch_point_sig(const uint64_t *pts, uint64_t n, uint32_t words, uint32_t d, uint32_t sig_block,
+                             uint64_t *sig, unsigned long long *pop_total, int sm_count, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((n + 7) / 8, (uint64_t)sm_count * 16);
+    point_sig_kernel<<<(unsigned)blocks, 256, 0, s>>>(pts, n, words, d, sig_block, sig, pop_total);
     note_launch();
     return cudaGetLastError();
 }

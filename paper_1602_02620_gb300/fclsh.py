@@ -54,7 +54,7 @@ class DeviceResult(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("query_block", ctypes.c_uint32), ("query_ctas_per_sm", ctypes.c_uint32),
                 ("hash_set_log2", ctypes.c_uint32), ("inline_probe", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
-                ("hash_tile", ctypes.c_uint32), ("probe_rows", ctypes.c_uint32)]
+                ("hash_tile", ctypes.c_uint32), ("probe_rows", ctypes.c_uint32), ("verify_filter", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

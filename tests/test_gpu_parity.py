@@ -448,3 +448,48 @@ def test_result_overflow_reruns_only_the_queries_past_the_buffer(dup, nq):
         assert np.array_equal(plain.of(i), first.of(i))
         assert plain.collisions[i] == first.collisions[i] and plain.candidates[i] == first.candidates[i]
     idx.free()
+
+
+def sparse_points(rng, n, d, density):
+    """Bernoulli(density) bits packed LSB-first, with a tenth of the points near-duplicates."""
+    bits = rng.random((n, d)) < density
+    for i in range(n // 10):
+        j = rng.integers(0, n)
+        bits[i] = bits[j]
+        bits[i, rng.choice(d, size=rng.integers(1, 6), replace=False)] ^= True
+    words = (d + 63) // 64
+    padded = np.zeros((n, words * 64), np.uint8)
+    padded[:, :d] = bits
+    return np.packbits(padded, axis=1, bitorder="little").view(np.uint64).reshape(n, words)
+
+
+# (d, r, n, density): one coordinate per signature block (d < 64), 16, 47 (d not a multiple
+# of 64) and 63 coordinates per block (blocks across word boundaries)
+@pytest.mark.parametrize("d,r,n,density", [(40, 4, 2000, 0.15), (1024, 12, 2500, 0.02), (3000, 12, 1500, 0.01),
+                                           (4000, 7, 800, 0.02)])
+def test_signature_filter_keeps_ids_and_counters(d, r, n, density):
+    """S3's signature pre-filter, on and off, in the batched and plain paths: every query's ids,
+    #Collisions and #Candidates equal the oracle's Strategy 2 query at the build radius and at
+    half of it (the bound never rejects a point within the radius)."""
+    rng = np.random.default_rng(d + n)
+    pts = sparse_points(rng, n, d, density)
+    qs = np.concatenate([near(rng, pts, d, r, 40), sparse_points(rng, 20, d, density)])
+    seed = 900 + d
+    idx = F().build(pts, d, r, seed)
+    assert idx.tuning()["verify_filter"] == 1                  # sparse points: on by default
+    p = oracle.derive_params(seed, d, r)
+    tables = oracle.build_tables(p, pts)
+    for radius in (r, r // 2):
+        want = [oracle.query(p, pts, tables, q, radius) for q in qs]
+        assert sum(len(w[0]) for w in want) > 0
+        for vf in (1, 0):
+            idx.set_tuning(verify_filter=vf)
+            for res in (idx.query(dev(qs), radius), idx.query_plain(qs, radius)):
+                for i, (ids, ncoll, ncand) in enumerate(want):
+                    assert np.array_equal(res.of(i), ids), (vf, radius, i)
+                    assert int(res.collisions[i]) == ncoll and int(res.candidates[i]) == ncand, (vf, radius, i)
+    idx.free()
+    dense = rand_points(rng, 500, 256)
+    idx = F().build(dense, 256, 6, 3)
+    assert idx.tuning()["verify_filter"] == 0                  # dense points: off by default
+    idx.free()
