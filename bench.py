@@ -398,6 +398,70 @@ def run_reference(args, rank: int):
     print(json.dumps(line))
 
 
+def run_sharded(args, w, seed, rank: int, world: int, local: int, dist):
+    """Strong scaling over points (the sharding of the index by point ids): rank k builds its
+    contiguous id range with the same seed and Algorithm 1's shape of the whole set, answers
+    the whole batch, and the per-shard answers (sorted, offset to global ids) are gathered and
+    merged on every rank.  One step = the build of every shard + the batch + the gather."""
+    import torch
+    from paper_1602_02620_gb300 import fclsh, shard
+
+    nq = int(w.queries.shape[0])
+    lo, hi = shard.shard_range(w.n, rank, world)
+    pts = torch.from_numpy(w.points[lo:hi].view(np.int64)).cuda()
+    qs = torch.from_numpy(w.queries.view(np.int64)).cuda()
+    bopts = workloads_build_options(args.workload)
+
+    tables = []
+
+    def step():
+        sh = shard.ShardedIndex(pts, w.n, w.d, w.r, seed, rank, world, **bopts)
+        if sh.index is not None and not tables:
+            tables.append(sh.index.T)
+        res = sh.query(qs, w.r)
+        sh.free()
+        return res
+
+    for _ in range(max(args.warmup, 1)):
+        res = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = fclsh.kernel_launches()
+    ev0.record()
+    for _ in range(args.steps):
+        res = step()
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = fclsh.kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if dist:
+        tt = torch.tensor([elapsed], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = nq * args.steps / elapsed
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": dict(workload_config(w, tables[0] if tables else 0, nq, w.name + " (sharded by points)"),
+                           parallelism="points sharded over %d GPUs, answers gathered" % world),
+            "results_per_step": int(res.offs[-1]), "gpu_launches": int(launches),
+        }))
+    if dist:
+        dist.destroy_process_group()
+
+
+def workloads_build_options(cfg: int) -> dict:
+    from paper_1602_02620_gb300 import workloads
+
+    return workloads.build_options(cfg)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,6 +476,9 @@ def main():
                     help="force the hash kernel (0/1: WHT tiles, 2: tensor-core contraction) instead of the tuned one")
     ap.add_argument("--slot-bits", type=int, default=None,
                     help="directory slot bits (to profile a smaller instance in the full-size directory layout)")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1: shard the points (each rank indexes a contiguous id range with the same seed, "
+                         "answers the whole batch, and the answers are gathered); strong scaling")
     ap.add_argument("--workload", type=int, default=CFG, choices=[1, 2, 3, 4, 5, 6, 7, 8],
                     help="workload id (default: 4, the n=2M d=1024 r=20 batched sparse workload)")
     args = ap.parse_args()
@@ -434,8 +501,13 @@ def main():
     from paper_1602_02620_gb300 import fclsh, workloads
 
     w = workloads.make(args.workload, n=args.n, nq=query_count(args.workload, args.nq))
-    seed = w.index_seed + rank          # one independent problem per GPU
+    # every rank builds with the same seed: without --shard each GPU holds its own replica of the
+    # index and answers its own batch (weak scaling); with --shard it holds one contiguous id range
+    seed = w.index_seed
     nq = int(w.queries.shape[0])
+    if args.shard:
+        run_sharded(args, w, seed, rank, world, local, dist)
+        return
     pts = torch.from_numpy(w.points.view(np.int64)).cuda()
     qs = torch.from_numpy(w.queries.view(np.int64)).cuda()
 

@@ -91,6 +91,18 @@ typedef struct {
                                  times when c r < log2 n (capped so that r * replicate <= 10), else
                                  ceil(c r / log2 n) parts; without replication t is raised until
                                  floor(r/t) <= 10.  0 = the rule of t. */
+    /* Classic bit-sampling LSH instead of covering LSH (the baseline the paper compares against,
+       Sec. 2.2 and 4.2; it has false negatives): selected by classic_k > 0 or classic_delta > 0.
+       Table j samples classic_k coordinates s_j(1..k) uniformly with replacement and keys a point
+       by Eq. 1 on them, key_j(x) = (sum_i b_i x_{s_j(i)}) mod P, one seed vector b for all
+       tables.  classic_tables = L (0 = the covering index's table count for (n, d, r), as
+       Sec. 4.2 sets it; other counts up to 2,047); classic_k = 0 takes the rule of Sec. 4.2,
+       k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)) with delta = classic_delta.  Draws from
+       `seed`: every table's k samples (next() mod d) in table order, then b.  Queries use the
+       same calls; probe_rows and hash_tile do not apply. */
+    uint32_t classic_tables;
+    uint32_t classic_k;
+    double classic_delta;
 } fclsh_build_opts;
 
 typedef struct {
@@ -220,11 +232,19 @@ fclsh_status fclsh_derive_params(uint64_t n, uint32_t d, uint32_t r, uint64_t se
                                  uint32_t shape[3], uint32_t *perm, uint32_t *part_off, uint32_t *m, uint64_t *b);
 
 /*
+ * A classic LSH index's random choices (the baseline of Sec. 4.2): *k receives the samples per
+ * table; samples (host, [T][k], may be NULL) the sampled coordinates of every table in draw
+ * order; b (host, [k], may be NULL) the seed vector of Eq. 1.  Errors: FCLSH_EINVAL for a NULL
+ * index or k, or a covering-LSH index.
+ */
+fclsh_status fclsh_get_classic_params(const fclsh_index *idx, uint32_t *k, uint32_t *samples, uint64_t *b);
+
+/*
  * Copy out the index's random choices: perm and part_off (Algorithm 1's permutation and
  * parts), m (Algorithm 2's permutation or the map of Eq. 4) and b (the seed vector of
  * Eq. 1), host arrays sized D, t+1, D, D with D = d * rep positions, so that they can be
  * compared with an independent derivation.  Any array pointer may be NULL.
- * Errors: FCLSH_EINVAL for a NULL index.
+ * Errors: FCLSH_EINVAL for a NULL index or a classic LSH index.
  */
 fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm, uint32_t *part_off,
                               uint32_t *m, uint64_t *b);

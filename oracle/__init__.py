@@ -17,6 +17,8 @@ first use); this module only marshals numpy arrays:
   S1/S2/S3 steps of Sec. 4.1, including #Collisions and #Candidates;
   ``query_listed`` runs the same query given only the tables it probes.
 * ``linear_scan``    -- the plain definition of the answer (Definition 2).
+* ``classic_*``      -- classic bit-sampling LSH (Sec. 2.2), the baseline with false
+  negatives that the paper compares against (Sec. 4.2): parameters, keys, query.
 """
 from __future__ import annotations
 
@@ -304,6 +306,80 @@ def linear_scan(pts, q, radius: int, words: int | None = None) -> np.ndarray:
     out = np.zeros(cap, np.uint32)
     cnt = _lib().oracle_linear_scan(_ptr(pts), n, words, _ptr(q), radius, _ptr(out), cap)
     return out[:cnt].copy()
+
+
+# ---------------------------------------------------------------- classic bit-sampling LSH
+
+def classic_rule_k(L: int, r: int, d: int, delta: float) -> int:
+    """Bit samples per table of classic LSH by the rule of Sec. 4.2:
+    k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)) -- the k at which a point at distance r
+    escapes all L tables with probability about delta."""
+    import math
+
+    return max(1, math.ceil(math.log1p(-(delta ** (1.0 / L))) / math.log1p(-r / d)))
+
+
+@dataclass
+class ClassicParams:
+    """Classic LSH (Sec. 2.2): table j samples coordinates samples[j] (k of them, with
+    replacement); its key is Eq. 1 on the sampled bits with the seed vector b."""
+
+    P: int
+    d: int
+    samples: np.ndarray   # uint32[L][k]
+    b: np.ndarray         # uint64[k]
+
+    @property
+    def L(self) -> int:
+        return self.samples.shape[0]
+
+
+def classic_params(seed: int, d: int, L: int, k: int, P: int = P_DEFAULT) -> ClassicParams:
+    """Draws from SplitMix64 started at seed: every table's k samples next() mod d, table by
+    table, then the k entries of b uniform below P (the top bits of a draw, rejected if >= P)."""
+    bits = (P - 1).bit_length()
+    need = L * k + k + 64
+    out = splitmix64(seed, need)
+    samples = (out[: L * k] % np.uint64(d)).astype(np.uint32).reshape(L, k)
+    b, at = [], L * k
+    while len(b) < k:
+        if at == len(out):
+            out = splitmix64(seed, 2 * len(out))
+        u = int(out[at]) >> (64 - bits)
+        at += 1
+        if u < P:
+            b.append(u)
+    return ClassicParams(P, d, samples, np.array(b, np.uint64))
+
+
+def _bits(pts, d: int) -> np.ndarray:
+    a = np.ascontiguousarray(pts, dtype=np.uint64)
+    a = a.reshape(-1, (d + 63) // 64)
+    return np.unpackbits(a.view(np.uint8).reshape(a.shape[0], -1), axis=1, bitorder="little")[:, :d]
+
+
+def classic_keys(cp: ClassicParams, pts) -> np.ndarray:
+    """uint64[L][n]: key_j(x) = (sum_i b_i x_{samples[j][i]}) mod P (Eq. 1 on the sampled bits;
+    the sum of k < 2^13 values below 2^50 is exact in 64 bits)."""
+    assert cp.samples.shape[1] < (1 << 13)
+    x = _bits(pts, cp.d).astype(np.uint64)
+    keys = np.zeros((cp.L, x.shape[0]), np.uint64)
+    for j in range(cp.L):
+        keys[j] = (x[:, cp.samples[j]] @ cp.b) % np.uint64(cp.P)
+    return keys
+
+
+def classic_query(cp: ClassicParams, pts, keys: np.ndarray, q, radius: int):
+    """Strategy 2 over the classic tables (Sec. 2.2): the points whose key equals the query's
+    in some table are the candidates; those within `radius` are reported.  Returns (sorted ids,
+    #Collisions, #Candidates) as the covering query does."""
+    qk = classic_keys(cp, q)[:, 0]
+    hit = keys == qk[:, None]
+    cand = hit.any(axis=0)
+    x = _bits(pts, cp.d)
+    dist = (x != _bits(q, cp.d)[0]).sum(axis=1)
+    ids = np.nonzero(cand & (dist <= radius))[0].astype(np.uint32)
+    return ids, int(hit.sum()), int(cand.sum())
 
 
 def hamming(a, b) -> int:

@@ -308,6 +308,8 @@ struct fclsh_qctx {
     uint64_t qbuf_cap = 0;
     uint32_t *rbuf = nullptr;   // device copy of host radii
     uint64_t rbuf_cap = 0;
+    uint64_t *qkeys = nullptr;  // classic LSH: the batch's query keys [T][nq], hashed before the query kernel
+    uint64_t qkeys_cap = 0;
     // last batch
     const uint64_t *last_q = nullptr;
     uint64_t last_nq = 0;
@@ -332,7 +334,7 @@ struct fclsh_qctx {
 static void ctx_free_buffers(fclsh_qctx *c)
 {
     void *ps[] = {c->counters, c->runs, c->run_base, c->res_cnt, c->res_offs,
-                  c->res_ids, c->coll, c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf};
+                  c->res_ids, c->coll, c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf, c->qkeys};
     for (void *p : ps)
         if (p) dev_free(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -500,6 +502,12 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
     a.bitmaps = c->bitmaps;
     a.bm_words = (idx->n + 31) / 32;
     a.redo_cap = redo_cap;
+    if (idx->classic_k) {   // S1 of classic LSH: the queries' keys by the classic hash kernel
+        const uint32_t L = idx->W - 1;
+        for (uint32_t k = 0; k < idx->t; ++k)
+            FCLSH_CUDA(launch_hash_part(idx, k, q, nq, c->qkeys + (uint64_t)k * L * nq, nq, s));
+        a.qkeys = c->qkeys;
+    }
     FCLSH_CUDA(cudaMemsetAsync(c->counters, 0, (redo_cap ? 1 : 2) * sizeof(unsigned long long), s));
     {
         PhaseTimer pt(idx, 2, s);
@@ -686,7 +694,28 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         const fclsh_status st = index_shape(n, d, r, o, &t, &rep, &rp);
         if (st != FCLSH_OK) return st;
     }
-    const uint32_t W = 2u << rp;
+    // classic bit-sampling LSH (the baseline of Sec. 4.2): the covering index's table count
+    // (2^(r+1) - 1 per part, as Sec. 4.2 sets it) unless classic_tables says otherwise, in t
+    // chunks of W - 1 tables; k sampled coordinates per table by the rule of Sec. 4.2
+    const bool classic = o.classic_k > 0 || o.classic_delta > 0.0;
+    uint32_t Wc = 2u << rp, ck = 0;
+    if (classic) {
+        if (o.perm || o.part_off || o.m || o.b) return fail(FCLSH_EINVAL, "classic LSH draws its own samples");
+        if (rep > 1) return fail(FCLSH_EINVAL, "classic LSH takes no replication");
+        if (o.hash_tile) return fail(FCLSH_EINVAL, "classic LSH has its own hash kernel (hash_tile must be 0)");
+        const uint32_t Tcov = t * (Wc - 1);
+        const uint32_t L = o.classic_tables ? o.classic_tables : Tcov;
+        if (L != Tcov) {
+            if (L > 2047) return fail(FCLSH_EINVAL, "classic_tables above 2,047 must equal the covering table count %u", Tcov);
+            t = 1;
+            Wc = L + 1;
+        }
+        ck = o.classic_k ? o.classic_k : classic_rule_k(L, r, d, o.classic_delta);
+        if (ck == 0 || ck > 8192)
+            return fail(FCLSH_EINVAL, "classic LSH needs 1 <= k <= 8192 (got %u; the rule needs 0 < r < d and 0 < delta < 1)",
+                        ck);
+    }
+    const uint32_t W = Wc;
     const uint32_t D = d * rep;   // positions of the (replicated) vector
 
     auto idx = new fclsh_index();
@@ -708,9 +737,13 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if (o.hash_tile > 4) return fail(FCLSH_EINVAL, "hash_tile must be 0..4");
     idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0, 0};
     idx->timing = o.timing != 0;
+    idx->classic_k = ck;
+    idx->classic_delta = o.classic_delta;
 
     const bool explicit_params = o.perm || o.part_off || o.m || o.b;
-    if (explicit_params) {
+    if (classic) {
+        classic_params(seed, d, idx->T, ck, idx->cl_samples, idx->cl_seed);
+    } else if (explicit_params) {
         if (!(o.perm && o.part_off && o.m && o.b)) return fail(FCLSH_EINVAL, "explicit parameters need all of perm, part_off, m, b");
         idx->perm.assign(o.perm, o.perm + D);
         idx->part_off.assign(o.part_off, o.part_off + t + 1);
@@ -734,16 +767,16 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         return fail(FCLSH_EINVAL, "cannot derive parameters");
     }
     uint32_t max_dk = 0;
-    for (uint32_t k = 0; k < t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
-    idx->mma_k = hash_mma_k(W, max_dk);
+    for (uint32_t k = 0; k < (classic ? 0u : t); ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
+    idx->mma_k = classic ? 0 : hash_mma_k(W, max_dk);
     if (o.hash_tile == 2 && !idx->mma_k)
         return fail(FCLSH_EINVAL, "hash_tile 2 (tensor cores) needs W >= 64 and parts of at most 128 coordinates");
     // coordinate lists of the scatter sketch (hash_tile 3)
     std::vector<uint32_t> sc_off, sc_col;
     std::vector<uint64_t> sc_bv;
-    coord_lists(d, t, W, idx->perm, idx->part_off, idx->m, idx->b, sc_off, sc_col, sc_bv, &idx->sc_pop);
+    if (!classic) coord_lists(d, t, W, idx->perm, idx->part_off, idx->m, idx->b, sc_off, sc_col, sc_bv, &idx->sc_pop);
     const bool scatter_fits = idx->sc_pop <= kScatterMaxPop;
-    if (o.hash_tile < 2 && hash_smem_bytes(W, max_dk, o.hash_tile) > idx->smem_optin) {
+    if (!classic && o.hash_tile < 2 && hash_smem_bytes(W, max_dk, o.hash_tile) > idx->smem_optin) {
         // the part's column lists do not fit in shared memory: sketch by scattering set bits
         if (!scatter_fits)
             return fail(FCLSH_EINVAL,
@@ -771,9 +804,14 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->slot_bits = sb;
     idx->ent_ib = entry_id_bits(sb);
 
+    // the sketch's column lists (covering LSH), or classic LSH's per-table lists of sampled
+    // coordinates and summed seed values, uploaded as one block either way
     std::vector<uint32_t> col_off, coord;
     std::vector<uint64_t> bval;
-    column_lists(D, t, W, idx->perm, idx->part_off, idx->m, idx->b, col_off, coord, bval);
+    if (classic)
+        classic_lists(idx->T, ck, idx->cl_samples, idx->cl_seed, col_off, coord, bval);
+    else
+        column_lists(D, t, W, idx->perm, idx->part_off, idx->m, idx->b, col_off, coord, bval);
 
     DevAllocs keep(true);   // index memory (released into idx on success); the build runs on the legacy stream
     cudaError_t e;
@@ -788,8 +826,13 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->col_b = dblock;
     idx->col_off = reinterpret_cast<uint32_t *>(dblock + bval.size());
     idx->col_coord = idx->col_off + col_off.size();
+    if (classic) {   // the same block holds the classic lists
+        idx->cl_b = idx->col_b;
+        idx->cl_off = idx->col_off;
+        idx->cl_coord = idx->col_coord;
+    }
     std::vector<uint64_t> sblock;
-    {   // b values, then offsets, then columns
+    if (!classic) {   // b values, then offsets, then columns
         sblock.assign(sc_bv.size() + (sc_off.size() + sc_col.size() + 1) / 2, 0);
         std::memcpy(sblock.data(), sc_bv.data(), sc_bv.size() * 8);
         std::memcpy(reinterpret_cast<uint32_t *>(sblock.data() + sc_bv.size()), sc_off.data(), sc_off.size() * 4);
@@ -987,10 +1030,21 @@ extern "C" fclsh_status fclsh_get_info(const fclsh_index *idx, fclsh_info *out)
     return FCLSH_OK;
 }
 
+extern "C" fclsh_status fclsh_get_classic_params(const fclsh_index *idx, uint32_t *k, uint32_t *samples, uint64_t *b)
+{
+    if (!idx || !k) return fail(FCLSH_EINVAL, "NULL argument");
+    if (!idx->classic_k) return fail(FCLSH_EINVAL, "not a classic LSH index");
+    *k = idx->classic_k;
+    if (samples) memcpy(samples, idx->cl_samples.data(), idx->cl_samples.size() * 4);
+    if (b) memcpy(b, idx->cl_seed.data(), idx->cl_seed.size() * 8);
+    return FCLSH_OK;
+}
+
 extern "C" fclsh_status fclsh_get_params(const fclsh_index *idx, uint32_t *perm, uint32_t *part_off, uint32_t *m,
                                          uint64_t *b)
 {
     if (!idx) return fail(FCLSH_EINVAL, "index is NULL");
+    if (idx->classic_k) return fail(FCLSH_EINVAL, "a classic LSH index has no covering parameters (fclsh_get_classic_params)");
     const size_t D = idx->positions();
     if (perm) memcpy(perm, idx->perm.data(), D * 4);
     if (part_off) memcpy(part_off, idx->part_off.data(), (idx->t + 1) * 4);
@@ -1174,6 +1228,18 @@ extern "C" fclsh_status fclsh_query_async(fclsh_qctx *c, const uint64_t *queries
     // overflowed queries a second time
     const uint64_t want = std::max<uint64_t>(c->cap, std::min<uint64_t>(nq * 512, 1ULL << 28));
     if ((st = ctx_reserve(c, nq, want)) != FCLSH_OK) return st;
+    if (idx->classic_k && (uint64_t)idx->T * nq > c->qkeys_cap) {
+        dev_free(c->qkeys);
+        c->qkeys = nullptr;
+        c->qkeys_cap = 0;
+        FCLSH_CUDA(dev_alloc((void **)&c->qkeys, (size_t)idx->T * nq * 8));
+        c->qkeys_cap = (uint64_t)idx->T * nq;
+        if (c->gexec) {   // a captured batch refers to the old buffer
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        c->g_seen = false;
+    }
     cudaStream_t s = stream ? (cudaStream_t)stream : c->own;
     c->last_q = queries;
     c->last_nq = nq;
@@ -1507,6 +1573,12 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     }
     if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
     if (t->verify_filter > 1) return fail(FCLSH_EINVAL, "verify_filter must be 0 or 1");
+    if (idx->classic_k && (t->hash_tile || t->probe_rows))
+        return fail(FCLSH_EINVAL, "a classic LSH index has one hash kernel and no row rule (hash_tile, probe_rows = 0)");
+    if (idx->classic_k) {
+        idx->tune = *t;
+        return FCLSH_OK;
+    }
     uint32_t max_dk = 0;
     for (uint32_t k = 0; k < idx->t; ++k) max_dk = std::max(max_dk, idx->part_off[k + 1] - idx->part_off[k]);
     if (t->hash_tile == 4 && max_dk > kDirectMaxPositions)
@@ -1648,6 +1720,7 @@ struct FileReader {
 extern "C" fclsh_status fclsh_save(const fclsh_index *idx, const char *path)
 {
     if (!idx || !path) return fail(FCLSH_EINVAL, "NULL argument");
+    if (idx->classic_k) return fail(FCLSH_EINVAL, "a classic LSH index is not saved (rebuild it from its points)");
     FCLSH_CUDA(cudaSetDevice(idx->device));
     FileWriter w;
     w.f = fopen(path, "wb");
@@ -1945,8 +2018,9 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
         idx->tune = best;
     }
     // the hash kernel: WHT tiles and the tensor-core contraction on the index's first points
-    // (about 2 GB of keys: enough blocks that the timing reflects a full build)
-    if (st == FCLSH_OK) {
+    // (about 2 GB of keys: enough blocks that the timing reflects a full build); classic LSH
+    // has one hash kernel
+    if (st == FCLSH_OK && !idx->classic_k) {
         const uint32_t L = idx->W - 1;
         const uint64_t cnt = std::min<uint64_t>(idx->n, std::max<uint64_t>(4096, (256ULL << 20) / L));
         uint32_t max_dk = 0;

@@ -125,6 +125,8 @@ struct QueryArgs {
     // lower bound from the two signatures passes the radius is rejected without reading it
     const uint64_t *sig;
     uint32_t sig_block;
+    // S1 done by a hash launch before the kernel (classic LSH): the queries' keys [T][nq]
+    const uint64_t *qkeys;
 };
 
 // A directory entry holds the key's high 50 - s bits above an ent_ib-bit id: 32 id bits
@@ -221,6 +223,15 @@ struct fclsh_index {
     uint32_t *mma_coord = nullptr;
     uint16_t *mma_g = nullptr;
     uint32_t *status = nullptr;      // [1] device word: bit 0 = a kernel's bounded wait ran out
+    // classic bit-sampling LSH (the baseline of Sec. 4.2) instead of covering LSH when classic_k > 0:
+    // T = t (W - 1) tables, table j keyed by Eq. 1 on classic_k sampled coordinates; per table the
+    // distinct coordinates and their summed seed values cl_coord / cl_b [cl_off[j] .. cl_off[j+1])
+    uint32_t classic_k = 0;
+    double classic_delta = 0.0;
+    std::vector<uint32_t> cl_samples;   // host [T][classic_k]
+    std::vector<uint64_t> cl_seed;      // host [classic_k]
+    uint32_t *cl_off = nullptr, *cl_coord = nullptr;   // one allocation, owned via cl_b
+    uint64_t *cl_b = nullptr;
     uint64_t *sig = nullptr;         // [n] block-occupancy signature of every point (S3 pre-filter)
     uint32_t sig_block = 1;          // coordinates per signature block: ceil(d / 64)
     uint64_t device_bytes = 0;
@@ -273,6 +284,11 @@ uint32_t default_parts(uint32_t r);
 void algorithm1_rule(uint64_t n, uint32_t r, double c, uint32_t *t, uint32_t *rep);
 int derive_params(uint64_t seed, uint32_t d, uint32_t t, uint32_t rep, uint32_t W, std::vector<uint32_t> &perm,
                   std::vector<uint32_t> &part_off, std::vector<uint32_t> &m, std::vector<uint64_t> &b);
+uint32_t classic_rule_k(uint32_t L, uint32_t r, uint32_t d, double delta);
+void classic_params(uint64_t seed, uint32_t d, uint32_t L, uint32_t k, std::vector<uint32_t> &samples,
+                    std::vector<uint64_t> &b);
+void classic_lists(uint32_t L, uint32_t k, const std::vector<uint32_t> &samples, const std::vector<uint64_t> &b,
+                   std::vector<uint32_t> &off, std::vector<uint32_t> &coord, std::vector<uint64_t> &bsum);
 void coord_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t> &perm,
                  const std::vector<uint32_t> &part_off, const std::vector<uint32_t> &m,
                  const std::vector<uint64_t> &b, std::vector<uint32_t> &off, std::vector<uint32_t> &col,

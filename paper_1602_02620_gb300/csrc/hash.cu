@@ -261,6 +261,53 @@ __global__ void __launch_bounds__(kDirectThreads) hash_direct_kernel(const uint6
     }
 }
 
+// ------------------------------------------------------------------ classic bit-sampling LSH
+
+// Keys of classic LSH (Sec. 2.2, Eq. 1 on k sampled coordinates): a block takes 128 points,
+// stages their words in shared memory (rows padded by one word) when they fit, and thread p
+// computes point p's key in every table of [tau0, tau0 + nt) from the table's list of
+// distinct sampled coordinates and summed seed values: sum of bsum over the set ones, mod P
+// (the sum of at most 8,192 values below 2^50 stays below 2^63).  A warp's stores cover 32
+// consecutive points of one table.
+constexpr int kClassicPoints = 128;
+constexpr uint32_t kClassicSmemWords = 64;   // points of up to 64 words are staged
+
+__global__ void __launch_bounds__(kClassicPoints) classic_hash_kernel(const uint64_t *__restrict__ pts, uint64_t cnt,
+                                                                      uint32_t words, const uint32_t *__restrict__ off,
+                                                                      const uint32_t *__restrict__ coord,
+                                                                      const uint64_t *__restrict__ bsum, uint32_t tau0,
+                                                                      uint32_t nt, uint64_t *__restrict__ keys,
+                                                                      uint64_t ld)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *xs = reinterpret_cast<uint64_t *>(smem_raw);   // [kClassicPoints][words + 1] when staged
+    const uint64_t p0 = blockIdx.x * (uint64_t)kClassicPoints;
+    const uint32_t real = (uint32_t)(cnt - p0 < (uint64_t)kClassicPoints ? cnt - p0 : (uint64_t)kClassicPoints);
+    const bool staged = words <= kClassicSmemWords;
+    const uint32_t stride = words + 1;
+    if (staged) {
+        for (uint32_t it = threadIdx.x; it < real * words; it += blockDim.x) {
+            const uint32_t p = it / words, w = it - p * words;
+            xs[(size_t)p * stride + w] = __ldg(pts + p0 * words + it);
+        }
+        __syncthreads();
+    }
+    const uint32_t p = threadIdx.x;
+    if (p >= real) return;
+    const uint64_t *xg = pts + (p0 + p) * words;
+    const uint64_t *xsm = xs + (size_t)p * stride;
+    for (uint32_t j = 0; j < nt; ++j) {
+        const uint32_t e0 = __ldg(off + tau0 + j), e1 = __ldg(off + tau0 + j + 1);
+        uint64_t s = 0;
+        for (uint32_t e = e0; e < e1; ++e) {
+            const uint32_t c = __ldg(coord + e);
+            const uint64_t w = staged ? xsm[c >> 6] : __ldg(xg + (c >> 6));
+            s += __ldg(bsum + e) & (0ULL - ((w >> (c & 63)) & 1ULL));
+        }
+        keys[(uint64_t)j * ld + p0 + p] = mod_p(s);
+    }
+}
+
 // ------------------------------------------------------------------ W >= 64
 
 template <int LOGW> struct TileCfg;
@@ -570,6 +617,19 @@ cudaError_t launch_hash_part(const fclsh_index *idx, uint32_t k, const uint64_t 
                              const uint32_t *plen)
 {
     if (cnt == 0) return cudaSuccess;
+    if (idx->classic_k) {   // classic bit-sampling LSH: part k = tables k (W-1) .. (k+1)(W-1)-1
+        const uint32_t L = idx->W - 1;
+        const size_t smem = idx->words <= kClassicSmemWords ? (size_t)kClassicPoints * (idx->words + 1) * 8 : 0;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(classic_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        classic_hash_kernel<<<(unsigned)((cnt + kClassicPoints - 1) / kClassicPoints), kClassicPoints, smem, s>>>(
+            pts, cnt, idx->words, idx->cl_off, idx->cl_coord, idx->cl_b, k * L, L, keys, ld);
+        note_launch();
+        return cudaGetLastError();
+    }
     const uint32_t dk = idx->part_off[k + 1] - idx->part_off[k];
     const PartCols pc = idx->part(k);
     if (idx->tune.hash_tile == 2) {   // tensor-core contraction (operands built by the caller)

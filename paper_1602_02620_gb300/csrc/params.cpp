@@ -194,4 +194,59 @@ void coord_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t>
     *max_pop = pop;
 }
 
+// ---------------------------------------------------------------- classic bit-sampling LSH
+
+// Classic LSH for Hamming space (Sec. 2.2): a hash function samples one coordinate, and
+// table j concatenates k of them, g_j = (x_{s_j(1)}, ..., x_{s_j(k)}), keyed by Eq. 1:
+// key_j(x) = (sum_i b_i x_{s_j(i)}) mod P with one seed vector b of k entries for every
+// table.  k follows the rule of Sec. 4.2, k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)),
+// which makes a point at distance r a false negative with probability about delta.
+uint32_t classic_rule_k(uint32_t L, uint32_t r, uint32_t d, double delta)
+{
+    if (r == 0 || r >= d || L == 0 || !(delta > 0.0 && delta < 1.0)) return 0;
+    const double num = std::log1p(-std::pow(delta, 1.0 / (double)L));
+    const double den = std::log1p(-(double)r / (double)d);
+    const double k = std::ceil(num / den);
+    return k < 1.0 ? 1u : (k > 8192.0 ? 8192u : (uint32_t)k);
+}
+
+// Draw order from `seed`: for table j = 0..L-1 in turn, its k samples s_j(i) = next() mod d
+// (coordinates with replacement, as independent draws from the bit-sampling family), then the
+// k entries of b, uniform below P.
+void classic_params(uint64_t seed, uint32_t d, uint32_t L, uint32_t k, std::vector<uint32_t> &samples,
+                    std::vector<uint64_t> &b)
+{
+    SplitMix64 g(seed);
+    samples.resize((size_t)L * k);
+    for (size_t i = 0; i < samples.size(); ++i) samples[i] = (uint32_t)g.below(d);
+    b.resize(k);
+    for (uint32_t i = 0; i < k; ++i) b[i] = g.residue();
+}
+
+// Per table: the distinct sampled coordinates, ascending, each with the sum of its b entries
+// mod P (a coordinate drawn twice counts twice in Eq. 1), so that key_j(x) = sum over the
+// list of bsum x_c mod P.
+void classic_lists(uint32_t L, uint32_t k, const std::vector<uint32_t> &samples, const std::vector<uint64_t> &b,
+                   std::vector<uint32_t> &off, std::vector<uint32_t> &coord, std::vector<uint64_t> &bsum)
+{
+    off.assign((size_t)L + 1, 0);
+    coord.clear();
+    bsum.clear();
+    std::vector<std::pair<uint32_t, uint64_t>> row(k);
+    for (uint32_t j = 0; j < L; ++j) {
+        for (uint32_t i = 0; i < k; ++i) row[i] = {samples[(size_t)j * k + i], b[i]};
+        std::sort(row.begin(), row.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+        off[j] = (uint32_t)coord.size();
+        for (uint32_t i = 0; i < k; ++i) {
+            if (!coord.empty() && coord.size() > off[j] && coord.back() == row[i].first) {
+                bsum.back() = add_mod_p(bsum.back(), row[i].second);
+            } else {
+                coord.push_back(row[i].first);
+                bsum.push_back(row[i].second);
+            }
+        }
+    }
+    off[L] = (uint32_t)coord.size();
+}
+
 }  // namespace fclsh

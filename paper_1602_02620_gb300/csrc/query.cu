@@ -275,8 +275,13 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             if (lane == 0) s_sigq[warp] = bal;
         }
 
-        // ---- S1: Algorithm 2 for every part, in shared memory
-        for (uint32_t k = 0; k < a.t; ++k) {
+        // ---- S1: Algorithm 2 for every part, in shared memory (or the keys a hash launch
+        // computed before the kernel)
+        if (a.qkeys) {
+            for (uint32_t tau = tid; tau < a.T; tau += B) keys_s[tau] = a.qkeys[(uint64_t)tau * a.nq + qi];
+            __syncthreads();
+        }
+        for (uint32_t k = 0; k < (a.qkeys ? 0u : a.t); ++k) {
             if (a.s1_scatter) {
                 // sketch from the query's set bits: each adds its positions' seed values to
                 // their columns (64-bit sums, exact while a column holds <= 16,383 positions)

@@ -31,7 +31,8 @@ class BuildOpts(ctypes.Structure):
     _fields_ = [("t", ctypes.c_uint32), ("slot_bits", ctypes.c_uint32), ("mem_budget", ctypes.c_uint64),
                 ("perm", ctypes.c_void_p), ("part_off", ctypes.c_void_p), ("m", ctypes.c_void_p), ("b", ctypes.c_void_p),
                 ("timing", ctypes.c_uint32), ("hash_tile", ctypes.c_uint32), ("replicate", ctypes.c_uint32),
-                ("approx_c", ctypes.c_double)]
+                ("approx_c", ctypes.c_double), ("classic_tables", ctypes.c_uint32), ("classic_k", ctypes.c_uint32),
+                ("classic_delta", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = {
     "fclsh_free": (None, [_vp]),
     "fclsh_get_info": (_i, [_vp, _vp]),
     "fclsh_get_params": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "fclsh_get_classic_params": (_i, [_vp, _vp, _vp, _vp]),
     "fclsh_derive_params": (_i, [_u64, _u32, _u32, _u64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fclsh_hash": (_i, [_vp, _vp, _u64, _vp, _vp]),
     "fclsh_bucket": (_i, [_vp, _u32, _u64, _vp, _u64, _vp]),
@@ -248,6 +250,15 @@ class Index:
         _check(lib().fclsh_get_params(self.handle, _ptr(perm), _ptr(part_off), _ptr(m), _ptr(b)))
         return perm, part_off, m, b
 
+    def classic_params(self):
+        """(samples [T][k], b [k]) of a classic LSH index."""
+        k = ctypes.c_uint32()
+        _check(lib().fclsh_get_classic_params(self.handle, ctypes.byref(k), None, None))
+        samples = np.zeros((self.T, int(k.value)), np.uint32)
+        b = np.zeros(int(k.value), np.uint64)
+        _check(lib().fclsh_get_classic_params(self.handle, ctypes.byref(k), _ptr(samples), _ptr(b)))
+        return samples, b
+
     def hash(self, pts, out=None, stream=None):
         """Keys [T][cnt] of the given points (numpy in -> numpy out unless `out` is given)."""
         cnt = _rows(pts)
@@ -403,7 +414,8 @@ class Server:
 
 def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: int | None = None,
           mem_budget: int | None = None, perm=None, part_off=None, m=None, b=None, timing: bool = False,
-          hash_tile: int = 0, replicate: int = 0, approx_c: float = 0.0) -> Index:
+          hash_tile: int = 0, replicate: int = 0, approx_c: float = 0.0, classic_tables: int = 0,
+          classic_k: int = 0, classic_delta: float = 0.0) -> Index:
     """fclsh_build on host (numpy) or device (torch CUDA) points [n][ceil(d/64)] uint64.
 
     hash_tile selects the hash kernel (0 default WHT tile, 1 twice as many points, 2 the
@@ -411,10 +423,14 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
     CUDA cores); fclsh_autotune reports the fastest of 0..3 as tuning()["hash_tile"], and a
     build whose column lists do not fit takes 3.
     replicate repeats every vector that many times (Algorithm 1, cr < log n); approx_c > 0
-    with neither t nor replicate set chooses both by Algorithm 1."""
+    with neither t nor replicate set chooses both by Algorithm 1.
+    classic_k > 0 or classic_delta > 0 builds classic bit-sampling LSH instead (the paper's
+    baseline with false negatives): classic_tables tables (0 = the covering table count) of
+    classic_k sampled coordinates (0 = the rule of Sec. 4.2 for classic_delta)."""
     keep = []
     o = _build_opts(t=t, slot_bits=slot_bits, mem_budget=mem_budget, perm=perm, part_off=part_off, m=m, b=b,
-                    timing=timing, hash_tile=hash_tile, replicate=replicate, approx_c=approx_c, keep=keep)
+                    timing=timing, hash_tile=hash_tile, replicate=replicate, approx_c=approx_c, keep=keep,
+                    classic_tables=classic_tables, classic_k=classic_k, classic_delta=classic_delta)
     h = ctypes.c_void_p()
     _check(lib().fclsh_build(_ptr(points), _rows(points), d, r, seed, ctypes.byref(o), ctypes.byref(h)))
     return Index(h)
@@ -438,8 +454,12 @@ def derive_params(n: int, d: int, r: int, seed: int, t: int | None = None, repli
 
 
 def _build_opts(t=None, slot_bits=None, mem_budget=None, perm=None, part_off=None, m=None, b=None,
-                timing=False, hash_tile=0, replicate=0, approx_c=0.0, keep=None) -> BuildOpts:
+                timing=False, hash_tile=0, replicate=0, approx_c=0.0, keep=None, classic_tables=0, classic_k=0,
+                classic_delta=0.0) -> BuildOpts:
     o = BuildOpts()
+    o.classic_tables = classic_tables or 0
+    o.classic_k = classic_k or 0
+    o.classic_delta = float(classic_delta)
     o.t = t or 0
     o.replicate = replicate or 0
     o.approx_c = float(approx_c)

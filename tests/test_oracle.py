@@ -597,3 +597,86 @@ def test_oracle_routes_agree_on_random_parameters():
         assert (oracle.keys_direct(p, y)[:, 0] == kd[:, 0]).any()
 
     check()
+
+
+# ---------------------------------------------------------------- classic bit-sampling LSH
+
+def test_classic_key_collides_exactly_when_the_sampled_bits_agree():
+    """Eq. 1 on the sampled bits (Sec. 2.2): with b_i = 2^i and distinct samples the key is the
+    sampled bit string read as an integer, so two points share a table's key exactly when they
+    agree on that table's samples; a coordinate drawn twice counts twice."""
+    rng = np.random.default_rng(3)
+    d, k = 90, 40
+    samples = np.stack([rng.choice(d, size=k, replace=False) for _ in range(30)]).astype(np.uint32)
+    cp = oracle.ClassicParams(P, d, samples, np.array([1 << i for i in range(k)], np.uint64))
+    x = rng.integers(0, 2**63, size=(200, 2), dtype=np.uint64)
+    x[:, 1] &= np.uint64((1 << (d - 64)) - 1)
+    y = x.copy()                                       # y differs from x in one random coordinate
+    for i, c in enumerate(rng.integers(0, d, size=200)):
+        y[i, c >> 6] ^= np.uint64(1) << np.uint64(c & 63)
+    kx, ky = oracle.classic_keys(cp, x), oracle.classic_keys(cp, y)
+    bx, by = oracle._bits(x, d), oracle._bits(y, d)
+    agree = np.stack([(bx[:, s] == by[:, s]).all(axis=1) for s in samples])
+    assert np.array_equal(kx == ky, agree) and agree.any() and (~agree).any()
+    twice = oracle.ClassicParams(P, d, np.array([[5, 5, 7]], np.uint32), np.array([1, 2, 4], np.uint64))
+    pt = np.zeros((1, 2), np.uint64)
+    pt[0, 0] = np.uint64((1 << 5) | (1 << 7))
+    assert int(oracle.classic_keys(twice, pt)[0, 0]) == 1 + 2 + 4
+
+
+def test_classic_collision_probability_is_sampling_with_replacement():
+    """A pair at distance delta shares a table's key with probability (1 - delta/d)^k when the k
+    coordinates are drawn independently (with replacement); drawing them without replacement
+    would give C(d - delta, k) / C(d, k), which the tolerance tells apart."""
+    from math import comb
+
+    d, k, L = 40, 8, 8000
+    cp = oracle.classic_params(77, d, L, k)
+    rng = np.random.default_rng(5)
+    x = rng.integers(0, 2**40, size=(1, 1), dtype=np.uint64)
+    for delta in (1, 4, 10):
+        y = x.copy()
+        for c in rng.choice(d, size=delta, replace=False):
+            y[0, 0] ^= np.uint64(1) << np.uint64(c)
+        frac = float((oracle.classic_keys(cp, x) == oracle.classic_keys(cp, y)).mean())
+        p = (1 - delta / d) ** k
+        se = (p * (1 - p) / L) ** 0.5
+        assert abs(frac - p) < 3 * se + 1e-9, (delta, frac, p)
+        if delta == 10:
+            assert abs(frac - comb(d - delta, k) / comb(d, k)) > 3 * se
+
+
+def test_classic_rule_k_is_the_smallest_k_reaching_the_false_negative_ratio():
+    """k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)) (Sec. 4.2): a point at distance r escapes
+    all L tables with probability (1 - (1 - r/d)^k)^L, which first reaches delta at this k."""
+    for L in (15, 127, 511, 4094):
+        for r, d in ((3, 64), (8, 128), (20, 1024), (6, 64)):
+            for delta in (0.1, 0.01):
+                k = oracle.classic_rule_k(L, r, d, delta)
+                p = 1 - r / d
+                assert (1 - p ** k) ** L >= delta * (1 - 1e-9)
+                assert k == 1 or (1 - p ** (k - 1)) ** L < delta
+
+
+def test_classic_query_has_false_negatives_at_about_delta():
+    """Classic LSH reports only true neighbours (Strategy 2 verifies), counts each candidate
+    once, and misses a point planted at distance r with probability about delta -- the recall
+    below 1 of Tables 3 and 4 that covering LSH removes."""
+    rng = np.random.default_rng(9)
+    d, r, n, L, delta = 64, 6, 400, 127, 0.1
+    k = oracle.classic_rule_k(L, r, d, delta)
+    cp = oracle.classic_params(21, d, L, k)
+    pts = rng.integers(0, 2**63, size=(n, 1), dtype=np.uint64) * np.uint64(2)
+    keys = oracle.classic_keys(cp, pts)
+    misses = 0
+    for i in range(n):
+        q = pts[i].copy()
+        for c in rng.choice(d, size=r, replace=False):
+            q[0] ^= np.uint64(1) << np.uint64(c)
+        ids, ncoll, ncand = oracle.classic_query(cp, pts, keys, q, r)
+        truth = oracle.linear_scan(pts, q, r)
+        assert set(ids.tolist()) <= set(truth.tolist()) and ncand <= ncoll
+        misses += int(i not in ids.tolist())
+    miss_p = (1 - (1 - r / d) ** k) ** L
+    assert abs(misses / n - miss_p) < 4 * (miss_p * (1 - miss_p) / n) ** 0.5 + 0.01, (misses, miss_p)
+    assert misses > 0
