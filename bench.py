@@ -298,14 +298,15 @@ def hash_ablation(fclsh, n: int = 65_536):
 
 
 def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: float = 1e6, probe_rows: int = 0):
-    """Continuous batching on the resident index: a Poisson stream of requests of
-    U{1..4096} queries with radii in {r/4, r/2, 3r/4, r} (rounded), offered at `load`
-    times the batched throughput; then the same requests one at a time.  probe_rows = 1
-    probes only the code rows each request's radius needs (same ids)."""
+    """Continuous batching on the resident index: a Poisson stream of requests of U{1..4096}
+    queries with radii in {r/4, r/2, 3r/4, r} (rounded), offered at `load` times the batched
+    throughput, through the server (4 slots, batches of up to 16,384 queries) and, with the
+    same arrival times, through a server that runs one request per batch on one slot; then
+    each request alone (submitted when the server is idle: its latency without queueing).
+    probe_rows = 1 probes only the code rows each request's radius needs (same ids)."""
     import threading
 
     idx.set_tuning(probe_rows=probe_rows)
-
     rng = np.random.default_rng(7)
     sizes = rng.integers(1, 4097, size=n_req)
     radii_set = sorted({max(1, round(w.r * f)) for f in (0.25, 0.5, 0.75, 1.0)})
@@ -315,39 +316,83 @@ def served(fclsh, idx, w, n_req: int = 160, load: float = 0.5, batched_qps: floa
     nq = w.queries.shape[0]
     starts = rng.integers(0, max(1, nq - 4096), size=n_req)
     blocks = [w.queries[int(a):int(a) + int(z)] for a, z in zip(starts, sizes)]
+
+    def open_loop(srv):
+        tickets = [None] * n_req
+
+        def feed():
+            t0 = time.perf_counter()
+            at = 0.0
+            for i in range(n_req):
+                at += gaps[i]
+                dt = t0 + at - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[i] = srv.submit(blocks[i], int(radii[i]))
+
+        th = threading.Thread(target=feed)
+        th.start()
+        th.join()
+        for t in tickets:
+            srv.wait(t)
+        return srv.stats()
+
     srv = fclsh.Server(idx, slots=4, max_batch_queries=16384)
-    tickets = [None] * n_req
-
-    def feed():
-        t0 = time.perf_counter()
-        at = 0.0
-        for i in range(n_req):
-            at += gaps[i]
-            dt = t0 + at - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            tickets[i] = srv.submit(blocks[i], int(radii[i]))
-
-    th = threading.Thread(target=feed)
-    th.start()
-    th.join()
-    for t in tickets:
-        srv.wait(t)
-    st = srv.stats()
+    st = open_loop(srv)
     srv.close()
     one = fclsh.Server(idx, slots=1, max_batch_queries=1)
-    t0 = time.perf_counter()
-    for i in range(n_req):
-        one.wait(one.submit(blocks[i], int(radii[i])))
-    el = time.perf_counter() - t0
-    st1 = one.stats()
+    st1 = open_loop(one)
     one.close()
+    alone = fclsh.Server(idx, slots=1, max_batch_queries=1)
+    for i in range(n_req):
+        alone.wait(alone.submit(blocks[i], int(radii[i])))
+    sta = alone.stats()
+    alone.close()
     idx.set_tuning(probe_rows=0)
-    return {"requests": n_req, "probe_rows": probe_rows, "offered_requests_per_s": rate, "radii": radii_set,
+    return {"requests": n_req, "probe_rows": probe_rows, "load": load,
+            "offered_queries_per_s": rate * float(sizes.mean()), "radii": radii_set,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "queries_per_s": st["queries_per_s"],
             "mean_batch_queries": st["mean_batch_queries"], "batches": st["batches"],
-            "one_at_a_time_queries_per_s": float(sizes.sum()) / el,
-            "one_at_a_time_p50_ms": st1["p50_ms"], "one_at_a_time_p99_ms": st1["p99_ms"]}
+            "one_at_a_time_queries_per_s": st1["queries_per_s"], "one_at_a_time_p50_ms": st1["p50_ms"],
+            "one_at_a_time_p99_ms": st1["p99_ms"],
+            "alone_p50_ms": sta["p50_ms"], "alone_p99_ms": sta["p99_ms"]}
+
+
+def serve_sweep(args):
+    """Offered load swept from a quarter to one and a half times the batched throughput on the
+    workload's resident index (built once), every query answered both ways (served, one request
+    per batch) from the same Poisson arrivals; one JSON line."""
+    import torch
+    from paper_1602_02620_gb300 import fclsh, workloads
+
+    w = workloads.make(args.workload, n=args.n, nq=query_count(args.workload, args.nq))
+    pts = torch.from_numpy(w.points.view(np.int64)).cuda()
+    qs = torch.from_numpy(w.queries.view(np.int64)).cuda()
+    bopts = workloads.build_options(args.workload)
+    cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
+    idx = fclsh.build(pts, w.d, w.r, w.index_seed, **bopts)
+    tuned = idx.autotune(qs[: min(qs.shape[0], 4096)], w.r, cache)
+    ctx = idx.context()
+    for _ in range(3):
+        ctx.query_async(qs, w.r)
+        ctx.wait()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        ctx.query_async(qs, w.r)
+        ctx.wait()
+    b.record()
+    torch.cuda.synchronize()
+    ctx.close()
+    batched_qps = qs.shape[0] * 5 / (a.elapsed_time(b) / 1000.0)
+    rows = []
+    for probe_rows in (0, 1):
+        for load in (0.25, 0.5, 1.0, 1.5):
+            rows.append(served(fclsh, idx, w, n_req=args.serve_requests, load=load, batched_qps=batched_qps,
+                               probe_rows=probe_rows))
+    idx.free()
+    print(json.dumps({"serve_sweep": {"workload": w.name, "batched_queries_per_s": batched_qps, "tuning": tuned,
+                                      "rows": rows}}))
 
 
 def workload_config(w, tables: int, nq: int, name: str) -> dict:
@@ -476,6 +521,9 @@ def main():
                     help="force the hash kernel (0/1: WHT tiles, 2: tensor-core contraction) instead of the tuned one")
     ap.add_argument("--slot-bits", type=int, default=None,
                     help="directory slot bits (to profile a smaller instance in the full-size directory layout)")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="only the served form: offered load 0.25x..1.5x the batched throughput, one JSON line")
+    ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1: shard the points (each rank indexes a contiguous id range with the same seed, "
                          "answers the whole batch, and the answers are gathered); strong scaling")
@@ -488,6 +536,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.serve_sweep:
+        serve_sweep(args)
         return
 
     import torch

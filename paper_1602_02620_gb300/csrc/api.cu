@@ -1171,6 +1171,32 @@ extern "C" fclsh_status fclsh_export_keys(const fclsh_index *idx, const uint32_t
 
 // ---------------------------------------------------------------- contexts
 
+// Device buffers of a context's last batch (valid from fclsh_query_async until the next one;
+// the result ids are complete once the counters read back show at most `cap` hits).
+void fclsh::qctx_result_ptrs(const fclsh_qctx *c, const uint64_t **offs, const uint32_t **ids,
+                             const uint64_t **coll, const uint64_t **cand, const unsigned long long **hits,
+                             uint64_t *cap)
+{
+    *offs = c->res_offs;
+    *ids = c->res_ids;
+    *coll = (const uint64_t *)c->coll;
+    *cand = (const uint64_t *)c->cand;
+    *hits = c->counters + 1;
+    *cap = c->cap;
+}
+
+// Device bytes fclsh_query_async would add to the context for a batch of nq queries.
+uint64_t fclsh::qctx_grow_bytes(const fclsh_qctx *c, uint64_t nq)
+{
+    const fclsh_index *idx = c->idx;
+    uint64_t b = 0;
+    if (nq > c->nq_cap) b += std::max<uint64_t>(nq, 1024) * (8 + 4 + 8 + 8 + 8 + 8) + 64;
+    const uint64_t want = std::min<uint64_t>(nq * 512, 1ULL << 28);
+    if (want > c->cap) b += want * 8;
+    if (idx->classic_k && (uint64_t)idx->T * nq > c->qkeys_cap) b += (uint64_t)idx->T * nq * 8;
+    return b;
+}
+
 extern "C" fclsh_status fclsh_qctx_create(fclsh_index *idx, fclsh_qctx **out)
 {
     if (!idx || !out) return fail(FCLSH_EINVAL, "NULL argument");

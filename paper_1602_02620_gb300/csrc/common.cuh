@@ -275,6 +275,16 @@ bool is_device_ptr(const void *p);
         if (e_ != cudaSuccess) return fclsh::cuda_fail(e_, #call); \
     } while (0)
 
+// Query contexts (api.cu) as the server drives them: the device buffers of the last batch
+// (result offsets, ids, counters, and the hit count whose excess over `cap` means the ids
+// are not complete until fclsh_qctx_wait reruns the overflowed queries), and the device
+// bytes a batch of nq queries would add to the context.
+void qctx_result_ptrs(const fclsh_qctx *c, const uint64_t **offs, const uint32_t **ids, const uint64_t **coll,
+                      const uint64_t **cand, const unsigned long long **hits, uint64_t *cap);
+uint64_t qctx_grow_bytes(const fclsh_qctx *c, uint64_t nq);
+cudaError_t dev_alloc(void **p, size_t bytes);   // the library's device memory pool
+void dev_free(void *p);
+
 // Testing aid (api.cu): c + 1 while the tensor-core hash is told to withhold its operand
 // copy of chunk c, so that its bounded waits run out (fclsh_debug_withhold_hash_loads); 0 = off.
 uint32_t debug_withhold_loads();

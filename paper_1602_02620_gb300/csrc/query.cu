@@ -184,6 +184,122 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
     append_hits(hit, id, c, res_s, s_nres);
 }
 
+// ---- S2b/S3 over the query's bucket entries as one list: run j (the j-th probed table's
+// bucket range) holds list positions [off_s[j], off_s[j+1]), off_s being the exclusive
+// prefix of the run lengths.  A chunk gives every thread kU positions at once, so that the
+// block has kU independent entry loads per thread in flight, then kU independent dedup
+// atomics, and then verifies the chunk's new candidates together (S3).
+constexpr int kU = 4;
+constexpr uint32_t kCandCap = 512u * kU;   // new candidates of one chunk (blocks of up to 512 threads)
+
+// The run holding list position pos: the last j < nruns with off[j] <= pos (off[0] = 0).
+__device__ __forceinline__ uint32_t run_of(const uint32_t *off, uint32_t nruns, uint32_t pos)
+{
+    uint32_t lo = 0, hi = nruns;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= pos) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct Chunk {
+    uint64_t en[kU];
+    uint32_t tau[kU];   // the entry's table, 0xFFFFFFFF past the list's end
+};
+
+// The entries at list positions base + k * blockDim.x + threadIdx.x, k < kU (loads issued back to back).
+__device__ __forceinline__ void load_chunk(const QueryArgs &a, const uint32_t *lo_s, const uint32_t *off_s,
+                                           uint32_t Tq, uint32_t nt, uint32_t L, uint32_t E, uint32_t base, Chunk &ch)
+{
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        const uint32_t pos = base + (uint32_t)k * blockDim.x + threadIdx.x;
+        ch.tau[k] = 0xFFFFFFFFu;
+        ch.en[k] = 0;
+        if (pos < E) {
+            const uint32_t j = run_of(off_s, Tq, pos);
+            const uint32_t tau = probed_table(j, nt, L);
+            ch.tau[k] = tau;
+            ch.en[k] = __ldg(a.ent + (uint64_t)tau * a.n + lo_s[j] + (pos - off_s[j]));
+        }
+    }
+}
+
+// Append the lanes' new candidates to the chunk's list; warp-collective.
+__device__ __forceinline__ void push_cand(bool isnew, uint32_t id, uint32_t *cand_s, uint32_t *s_ncand)
+{
+    const uint32_t m = __ballot_sync(0xffffffffu, isnew);
+    if (!m) return;
+    const uint32_t lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(s_ncand, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (isnew) cand_s[base + __popc(m & lanemask_lt())] = id;
+}
+
+// Distance of point id read by the whole warp (long points): 256 words per step, eight
+// independent loads per lane, stopping once the partial distance exceeds the radius.
+// Every lane returns the same value; warp-collective.
+__device__ __forceinline__ uint32_t warp_distance(const QueryArgs &a, const uint64_t *q_s, uint32_t id, uint32_t radius)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t *x = a.points + (uint64_t)id * a.words;
+    uint32_t dist = 0, wb = 0;
+    for (; wb + 256 <= a.words; wb += 256) {
+        uint64_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(x + wb + lane + 32 * u);
+        uint32_t part = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) part += __popcll(v[u] ^ q_s[wb + lane + 32 * u]);
+        dist += __reduce_add_sync(0xffffffffu, part);
+        if (dist > radius) return dist;
+    }
+    uint32_t part = 0;
+    for (uint32_t w = wb + lane; w < a.words; w += 32) part += __popcll(__ldg(x + w) ^ q_s[w]);
+    return dist + __reduce_add_sync(0xffffffffu, part);
+}
+
+// S3 for the candidates cand_s[0..m) (block-wide, uniform control flow): each is counted
+// once in #Candidates and reported if within the radius; hitmask (optional) gets the
+// hits' bits for the bitmap words [w0, w0 + blockDim.x).
+__device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s, uint32_t m,
+                                            uint32_t radius, uint64_t sq, const uint8_t *pcq, Counters &c,
+                                            uint32_t *res_s, uint32_t *s_nres, uint32_t *hitmask, uint64_t w0)
+{
+    const uint32_t B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (a.words >= kWarpVerifyWords) {   // a warp per candidate: coalesced reads of long points
+        const uint32_t nwarps = B >> 5;
+        for (uint32_t i0 = 0; i0 < m; i0 += nwarps) {
+            const uint32_t i = i0 + warp;
+            const bool ok = i < m;
+            const uint32_t id = ok ? cand_s[i] : 0;
+            bool hit = false;
+            if (ok) {
+                if (lane == 0) c.cand++;
+                hit = sig_pass(a, id, sq, pcq, radius) && warp_distance(a, q_s, id, radius) <= radius;
+            }
+            append_hits(hit && lane == 0, id, c, res_s, s_nres);
+            if (hit && lane == 0 && hitmask) atomicOr(hitmask + ((id >> 5) - w0), 1u << (id & 31));
+        }
+        return;
+    }
+    for (uint32_t i0 = 0; i0 < m; i0 += B) {
+        const uint32_t i = i0 + tid;
+        const bool ok = i < m;
+        const uint32_t id = ok ? cand_s[i] : 0;
+        bool hit = false;
+        if (ok) {
+            c.cand++;
+            hit = sig_pass(a, id, sq, pcq, radius) && distance_to(a, q_s, id) <= radius;
+        }
+        append_hits(hit, id, c, res_s, s_nres);
+        if (hit && hitmask) atomicOr(hitmask + ((id >> 5) - w0), 1u << (id & 31));
+    }
+}
+
 // Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
 __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
 {
@@ -228,7 +344,8 @@ __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
 size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_log2)
 {
     const size_t tb = (size_t)W * 8 > ((size_t)4 << hset_log2) ? (size_t)W * 8 : ((size_t)4 << hset_log2);
-    return (size_t)T * 8 + (size_t)T * 8 + tb + (size_t)words * 8 + (size_t)kResCap * 4 + 64;
+    return (size_t)T * 8 + (size_t)T * 8 + tb + (size_t)words * 8 + (size_t)kResCap * 4 + (size_t)kCandCap * 4 +
+           512 * 4 + 64;
 }
 
 __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
@@ -242,8 +359,10 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
     const size_t tb_words = ((size_t)a.W > ((size_t)1 << a.hset_log2) / 2) ? a.W : ((size_t)1 << a.hset_log2) / 2;
     uint64_t *q_s = tbuf + tb_words;
     uint32_t *res_s = reinterpret_cast<uint32_t *>(q_s + a.words);
+    uint32_t *cand_s = res_s + kResCap;        // a chunk's new candidates
+    uint32_t *hitmask_s = cand_s + kCandCap;   // the sweep's hits, per bitmap word of a chunk
     __shared__ unsigned long long s_qi;
-    __shared__ uint32_t s_nres;
+    __shared__ uint32_t s_nres, s_ncand;
     __shared__ unsigned long long red64[32];
     __shared__ uint8_t s_pcq[64];                 // the query's set coordinates per signature block
     __shared__ __align__(8) uint32_t s_sigq[2];   // the query's block-occupancy signature
@@ -346,71 +465,140 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         // more bucket entries than bitmap words: mark the bitmap and sweep it once
         const bool sweep_mode = bitmap_mode && E > a.bm_words;
         const int mode = sweep_mode ? DEDUP_MARK : (bitmap_mode ? DEDUP_BITMAP : DEDUP_HSET);
+        // the bucket entries as one list (positions in 32 bits; a query past that walks its
+        // runs lane by lane instead)
+        const bool listed = E <= 0xFFFFFFFFull - (unsigned long long)B * kU;
+        const uint32_t E32 = listed ? (uint32_t)E : 0u;
+        uint32_t *off_s = len_s;   // len_s becomes the runs' exclusive prefix
+        if (listed) {
+            const uint32_t per = (Tq + B - 1) / B, j0 = tid * per, j1 = min(j0 + per, Tq);
+            uint32_t mine = 0;
+            for (uint32_t j = j0; j < j1; ++j) mine += len_s[j];
+            uint32_t run = (uint32_t)block_excl_scan_u32(mine, red64);
+            for (uint32_t j = j0; j < j1; ++j) {
+                const uint32_t len = len_s[j];
+                off_s[j] = run;
+                run += len;
+            }
+        }
         if (!bitmap_mode)
             for (uint32_t i = tid; i < hcap; i += B) hset[i] = kEmpty;
-        if (tid == 0) s_nres = 0;
+        if (tid == 0) {
+            s_nres = 0;
+            s_ncand = 0;
+        }
         __syncthreads();
 
-        // ---- S2b + S3: collisions -> dedup -> verify, 32 tables per warp step
+        // ---- S2b + S3 (chunks of the list): collisions -> dedup -> verify of the new candidates
         const uint64_t sq = a.sig ? ((uint64_t)s_sigq[1] << 32 | s_sigq[0]) : 0;
         Counters c;
-        for (uint32_t base = warp * 32; base < Tq; base += nwarps * 32) {
-            const uint32_t j = base + lane;
-            const bool has = j < Tq;
-            const uint32_t tau = has ? probed_table(j, nt, L) : 0;
-            const uint32_t lo = has ? lo_s[j] : 0, len = has ? len_s[j] : 0;
-            const uint64_t fp = has ? keys_s[tau] >> a.slot_bits : 0;
-            const uint64_t *row = a.ent + (uint64_t)tau * a.n;
-            const uint32_t short_len = len <= a.inline_len ? len : 0;
-            const uint32_t maxs = __reduce_max_sync(0xffffffffu, short_len);
-            for (uint32_t e = 0; e < maxs; ++e) {
-                const bool act = e < short_len;
-                const uint64_t en = act ? __ldg(row + lo + e) : 0;
-                process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == fp,
-                              entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_pcq);
+        const uint64_t fp_shift = a.slot_bits;
+        for (uint32_t base = 0; base < E32; base += B * kU) {
+            Chunk ch;
+            load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+            uint32_t ids[kU], old[kU];
+            bool coll[kU];
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                coll[k] = ch.tau[k] != 0xFFFFFFFFu && entry_fp(ch.en[k], a.ent_ib) == (keys_s[ch.tau[k]] >> fp_shift);
+                ids[k] = entry_id(ch.en[k], a.ent_ib);
+                old[k] = 0;
             }
-            uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
-            while (lmask) {
-                const uint32_t src = __ffs(lmask) - 1;
-                lmask &= lmask - 1;
-                const uint32_t l_lo = __shfl_sync(0xffffffffu, lo, src);
-                const uint32_t l_len = __shfl_sync(0xffffffffu, len, src);
-                const uint64_t l_fp = __shfl_sync(0xffffffffu, fp, src);
-                const uint32_t l_tau = __shfl_sync(0xffffffffu, tau, src);
-                const uint64_t *lrow = a.ent + (uint64_t)l_tau * a.n + l_lo;
-                for (uint32_t cbase = 0; cbase < l_len; cbase += 32) {
-                    const uint32_t e = cbase + lane;
-                    const bool act = e < l_len;
-                    const uint64_t en = act ? __ldg(lrow + e) : 0;
-                    process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == l_fp,
+            if (mode == DEDUP_MARK) {   // mark only (fire-and-forget reductions); the sweep verifies
+#pragma unroll
+                for (int k = 0; k < kU; ++k)
+                    if (coll[k]) {
+                        c.coll++;
+                        atomicOr(bm + (ids[k] >> 5), 1u << (ids[k] & 31));
+                    }
+                continue;   // block-uniform
+            }
+#pragma unroll
+            for (int k = 0; k < kU; ++k)   // the chunk's dedup operations, issued back to back
+                if (coll[k]) {
+                    c.coll++;
+                    const uint32_t bit = 1u << (ids[k] & 31);
+                    if (mode == DEDUP_BITMAP)
+                        old[k] = atomicOr(bm + (ids[k] >> 5), bit) & bit;
+                    else
+                        old[k] = hset_insert(hset, a.hset_log2, ids[k]) ? 0u : 1u;
+                }
+#pragma unroll
+            for (int k = 0; k < kU; ++k) push_cand(coll[k] && !old[k], ids[k], cand_s, &s_ncand);
+            __syncthreads();
+            verify_list(a, q_s, cand_s, s_ncand, radius, sq, s_pcq, c, res_s, &s_nres, nullptr, 0);
+            __syncthreads();
+            if (tid == 0) s_ncand = 0;
+            __syncthreads();
+        }
+        if (!listed) {
+            // a query with 2^32 bucket entries or more: warps take 32 tables, a lane walks its
+            // own short run, the warp a long one (the runs' lengths are still in len_s)
+            for (uint32_t base = warp * 32; base < Tq; base += nwarps * 32) {
+                const uint32_t j = base + lane;
+                const bool has = j < Tq;
+                const uint32_t tau = has ? probed_table(j, nt, L) : 0;
+                const uint32_t lo = has ? lo_s[j] : 0, len = has ? len_s[j] : 0;
+                const uint64_t fp = has ? keys_s[tau] >> a.slot_bits : 0;
+                const uint64_t *row = a.ent + (uint64_t)tau * a.n;
+                const uint32_t short_len = len <= a.inline_len ? len : 0;
+                const uint32_t maxs = __reduce_max_sync(0xffffffffu, short_len);
+                for (uint32_t e = 0; e < maxs; ++e) {
+                    const bool act = e < short_len;
+                    const uint64_t en = act ? __ldg(row + lo + e) : 0;
+                    process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == fp,
                                   entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_pcq);
+                }
+                uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
+                while (lmask) {
+                    const uint32_t src = __ffs(lmask) - 1;
+                    lmask &= lmask - 1;
+                    const uint32_t l_lo = __shfl_sync(0xffffffffu, lo, src);
+                    const uint32_t l_len = __shfl_sync(0xffffffffu, len, src);
+                    const uint64_t l_fp = __shfl_sync(0xffffffffu, fp, src);
+                    const uint32_t l_tau = __shfl_sync(0xffffffffu, tau, src);
+                    const uint64_t *lrow = a.ent + (uint64_t)l_tau * a.n + l_lo;
+                    for (uint32_t cbase = 0; cbase < l_len; cbase += 32) {
+                        const uint32_t e = cbase + lane;
+                        const bool act = e < l_len;
+                        const uint64_t en = act ? __ldg(lrow + e) : 0;
+                        process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == l_fp,
+                                      entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_pcq);
+                    }
                 }
             }
         }
         if (sweep_mode) {
-            // S2/S3 for a very heavy query: every candidate is marked; sweep the bitmap
-            // (warps take 32 consecutive words, a lane a word), verify each marked id,
-            // and leave only the hits marked (cleared below)
+            // S2/S3 for a very heavy query: every candidate is marked; sweep the bitmap a chunk
+            // of blockDim.x words at a time, each thread listing up to kU of its word's ids per
+            // round, verify the listed ids together, and leave only the hits marked
             __threadfence();
             __syncthreads();
-            for (uint64_t w0 = (uint64_t)warp * 32; w0 < a.bm_words; w0 += (uint64_t)nwarps * 32) {
-                const uint64_t wi = w0 + lane;
+            for (uint64_t w0 = 0; w0 < a.bm_words; w0 += B) {
+                const uint64_t wi = w0 + tid;
                 const uint32_t bits = wi < a.bm_words ? __ldcg(bm + wi) : 0u;
-                c.cand += __popc(bits);
-                uint32_t rem = bits, hits = 0;
-                while (__any_sync(0xffffffffu, rem != 0)) {
-                    bool hit = false;
-                    uint32_t id = 0;
-                    if (rem) {
-                        const uint32_t b = __ffs(rem) - 1;
-                        rem &= rem - 1;
-                        id = (uint32_t)(wi * 32 + b);
-                        hit = sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius;
-                        if (hit) hits |= 1u << b;
+                uint32_t rem = bits;
+                hitmask_s[tid] = 0;
+                __syncthreads();
+                for (;;) {
+#pragma unroll
+                    for (int k = 0; k < kU; ++k) {
+                        const bool has = rem != 0;
+                        uint32_t id = 0;
+                        if (has) {
+                            id = (uint32_t)(wi * 32 + (uint32_t)(__ffs(rem) - 1));
+                            rem &= rem - 1;
+                        }
+                        push_cand(has, id, cand_s, &s_ncand);
                     }
-                    append_hits(hit, id, c, res_s, &s_nres);
+                    __syncthreads();
+                    verify_list(a, q_s, cand_s, s_ncand, radius, sq, s_pcq, c, res_s, &s_nres, hitmask_s, w0);
+                    __syncthreads();
+                    if (tid == 0) s_ncand = 0;
+                    if (!__syncthreads_or(rem != 0)) break;
                 }
-                if (bits) bm[wi] = hits;
+                if (bits) bm[wi] = hitmask_s[tid];
+                __syncthreads();
             }
         }
         const unsigned long long tc = block_sum(c.coll, red64);
@@ -421,12 +609,20 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             for (uint32_t i = tid; i < nres; i += B) bm[res_s[i] >> 5] = 0;
             __syncthreads();
         }
-        if (bitmap_mode && !sweep_mode) {   // leave the CTA's bitmap all-zero
-            for (uint32_t j = tid; j < Tq; j += B) {
-                const uint64_t *row = a.ent + (uint64_t)probed_table(j, nt, L) * a.n + lo_s[j];
-                const uint32_t len = len_s[j];
-                for (uint32_t e = 0; e < len; ++e) bm[entry_id(__ldg(row + e), a.ent_ib) >> 5] = 0;
+        if (bitmap_mode && !sweep_mode) {   // leave the CTA's bitmap all-zero: the list again
+            for (uint32_t base = 0; base < E32; base += B * kU) {
+                Chunk ch;
+                load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+#pragma unroll
+                for (int k = 0; k < kU; ++k)
+                    if (ch.tau[k] != 0xFFFFFFFFu) bm[entry_id(ch.en[k], a.ent_ib) >> 5] = 0;
             }
+            if (!listed)
+                for (uint32_t j = tid; j < Tq; j += B) {
+                    const uint64_t *row = a.ent + (uint64_t)probed_table(j, nt, L) * a.n + lo_s[j];
+                    const uint32_t len = len_s[j];
+                    for (uint32_t e = 0; e < len; ++e) bm[entry_id(__ldg(row + e), a.ent_ib) >> 5] = 0;
+                }
             __syncthreads();
         }
         if (nres <= kResCap) {
@@ -440,7 +636,19 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
             // More hits than shared memory holds (only in bitmap mode): mark every hit in
             // the bitmap (the sweep left exactly the hits marked), then read the ids out in
             // ascending order and clear it again.
-            for (uint32_t j = sweep_mode ? Tq : tid; j < Tq; j += B) {
+            for (uint32_t base = 0; !sweep_mode && base < E32; base += B * kU) {   // the list again
+                Chunk ch;
+                load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    if (ch.tau[k] == 0xFFFFFFFFu || entry_fp(ch.en[k], a.ent_ib) != (keys_s[ch.tau[k]] >> fp_shift))
+                        continue;
+                    const uint32_t id = entry_id(ch.en[k], a.ent_ib);
+                    if (sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius)
+                        atomicOr(bm + (id >> 5), 1u << (id & 31));
+                }
+            }
+            for (uint32_t j = (sweep_mode || listed) ? Tq : tid; j < Tq; j += B) {
                 const uint32_t tau = probed_table(j, nt, L);
                 const uint64_t *row = a.ent + (uint64_t)tau * a.n + lo_s[j];
                 const uint32_t len = len_s[j];

@@ -49,6 +49,8 @@ def gather_answers(local, id_offset: int, group=None):
     """All-gather each rank's (offs, ids, collisions, candidates) and merge them on every rank."""
     import torch.distributed as dist
 
+    if not (dist.is_available() and dist.is_initialized()):   # a single process: its own shard only
+        return merge([tuple(np.asarray(x) for x in local) + (id_offset,)])
     world = dist.get_world_size(group)
     objs = [None] * world
     payload = tuple(np.asarray(x) for x in local) + (id_offset,)
