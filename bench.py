@@ -371,7 +371,7 @@ def serve_sweep(args):
     bopts = workloads.build_options(args.workload)
     cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
     idx = fclsh.build(pts, w.d, w.r, w.index_seed, **bopts)
-    tuned = idx.autotune(qs[: min(qs.shape[0], 4096)], w.r, cache)
+    tuned = idx.autotune(qs[: min(qs.shape[0], 8192)], w.r, cache)
     ctx = idx.context()
     for _ in range(3):
         ctx.query_async(qs, w.r)
@@ -568,7 +568,7 @@ def main():
     if args.slot_bits:
         bopts["slot_bits"] = args.slot_bits
     idx0 = fclsh.build(pts, w.d, w.r, seed, **bopts)
-    tuned = idx0.autotune(qs[: min(nq, 4096)], w.r, cache)
+    tuned = idx0.autotune(qs[: min(nq, 8192)], w.r, cache)
     idx0.free()
     if args.hash_tile is not None:
         tuned["hash_tile"] = args.hash_tile

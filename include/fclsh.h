@@ -508,6 +508,15 @@ fclsh_status fclsh_debug_pool_used(uint64_t *bytes);
  */
 fclsh_status fclsh_debug_withhold_hash_loads(int on);
 
+/*
+ * Checked builds (no counterpart in the paper; the library compiled with -DFCLSH_CHECKED, the
+ * stand-in for a memory checker): the kernels bounds-check their computed indexes, skip an
+ * access that fails and record the check's code.  *checked = 1 in such a build (0 otherwise);
+ * *first = the first failed check's code since the last call (0: none; always 0 in a normal
+ * build).  Waits for the device.  Errors: FCLSH_EINVAL (NULL pointers), FCLSH_ECUDA.
+ */
+fclsh_status fclsh_debug_check_status(int *checked, uint32_t *first);
+
 /* Thread-local description of the calling thread's last failure (no counterpart in the
    paper).  The string is owned by the library and valid until the thread's next call. */
 const char *fclsh_last_error(void);

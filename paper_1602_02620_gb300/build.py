@@ -39,8 +39,8 @@ def _newer(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra=()) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra=(), build_dir=None) -> str:
+    obj = os.path.join(build_dir or BUILD, os.path.basename(src) + ".o")
     deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "fclsh.h")]
     if _newer(obj, deps):
         cmd = [nvcc()] + NVCC_FLAGS + list(extra) + ["-c", os.path.join(CSRC, src), "-o", obj + ".tmp"]
@@ -51,25 +51,29 @@ def _compile(src: str, extra=()) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile (if stale) and link libfclsh.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile (if stale) and link libfclsh.so; returns its path.  checked=True builds the
+    bounds-checked variant (-DFCLSH_CHECKED) into _build_checked/."""
+    bdir = os.path.join(HERE, "_build_checked") if checked else BUILD
+    lib = os.path.join(bdir, "libfclsh.so")
+    extra = list(extra) + (["-DFCLSH_CHECKED"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
+        for f in os.listdir(bdir):
             if f.endswith(".o"):
-                os.remove(os.path.join(BUILD, f))
+                os.remove(os.path.join(bdir, f))
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    if _newer(LIB, objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcudart"]
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir), SOURCES))
+    if _newer(lib, objs):
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", lib + ".tmp"] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-        os.replace(LIB + ".tmp", LIB)
+        os.replace(lib + ".tmp", lib)
     if verbose:
-        print(LIB)
-    return LIB
+        print(lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)

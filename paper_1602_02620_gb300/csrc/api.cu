@@ -1886,6 +1886,23 @@ extern "C" fclsh_status fclsh_debug_pool_used(uint64_t *bytes)
     return FCLSH_OK;
 }
 
+extern "C" fclsh_status fclsh_debug_check_status(int *checked, uint32_t *first)
+{
+    if (!checked || !first) return fail(FCLSH_EINVAL, "NULL argument");
+#ifdef FCLSH_CHECKED
+    *checked = 1;
+#else
+    *checked = 0;
+#endif
+    FCLSH_CUDA(cudaDeviceSynchronize());
+    const uint32_t v[] = {check_first_query(), check_first_hash(), check_first_sort(), check_first_mma(),
+                          check_first_noalloc()};
+    *first = 0;
+    for (uint32_t x : v)
+        if (x && !*first) *first = x;
+    return FCLSH_OK;
+}
+
 extern "C" const char *fclsh_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char *fclsh_version(void) { return "fclsh-gb300 0.1 (sm_103a)"; }
@@ -1992,9 +2009,11 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     best = saved;
+    // inline_probe only shapes the lane-by-lane walk of queries with 2^32 bucket entries or
+    // more, so it keeps its value; the block, blocks per SM and dedup set are timed
     const uint32_t blocks[] = {128, 256, 512};
     const uint32_t hlogs[] = {11, 12, 13};
-    const uint32_t inl[] = {2, 4, 8};
+    const uint32_t inl[] = {saved.inline_probe};
     const uint32_t ctas[] = {1, 2, 4, 8};
     for (uint32_t bk : blocks)
         for (uint32_t hl : hlogs)

@@ -11,6 +11,35 @@
 
 namespace fclsh {
 
+// Checked build (compiled with -DFCLSH_CHECKED; the stand-in for a memory checker): the
+// kernels' computed indexes are bounds-checked before the access; a failed check skips the
+// access and records its code in the translation unit's device word (the first one wins),
+// and fclsh_debug_check_status reads the words.  No trap, no abort: the call completes with
+// whatever the skipped accesses leave, and the test harness fails the run.  In a normal
+// build every check is the constant true.
+#if defined(FCLSH_CHECKED) && defined(__CUDACC__)
+static __device__ unsigned int g_check_first;
+#define FCLSH_CHECK(cond, code) ((cond) || (atomicCAS(&fclsh::g_check_first, 0u, (unsigned)(code)), false))
+#define FCLSH_CHECK_READER(name)                                             \
+    uint32_t name()                                                          \
+    {                                                                        \
+        unsigned int v = 0, z = 0;                                           \
+        if (cudaMemcpyFromSymbol(&v, fclsh::g_check_first, 4) != cudaSuccess) v = 0xFFFFFFFFu; \
+        cudaMemcpyToSymbol(fclsh::g_check_first, &z, 4);                     \
+        return v;                                                            \
+    }
+#else
+#define FCLSH_CHECK(cond, code) true
+#define FCLSH_CHECK_READER(name) \
+    uint32_t name() { return 0; }
+#endif
+// first failed check of each kernel file since the last read (0: none)
+uint32_t check_first_query();
+uint32_t check_first_hash();
+uint32_t check_first_sort();
+uint32_t check_first_mma();
+uint32_t check_first_noalloc();
+
 // The prime of Eq. (1): 2^50 - 27, the largest prime below 2^50.  Sums of up to
 // 2^11 residues stay below 2^61, so Algorithm 2 runs exactly in 64-bit integers.
 constexpr uint64_t kP = (1ULL << 50) - 27;

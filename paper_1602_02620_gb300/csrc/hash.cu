@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(kDirectThreads) hash_direct_kernel(const uint6
             const uint32_t e1 = __ldg(cl.off + c + 1);
             for (uint32_t e = __ldg(cl.off + c); e < e1; ++e) {
                 const uint32_t at = atomicAdd(&len[p], 1u);   // < maxpos: a point has at most the part's positions
+                if (!FCLSH_CHECK(at < maxpos, 0x0204)) continue;
                 lb[(size_t)p * maxpos + at] = __ldg(cl.b + e);
                 lc[(size_t)p * maxpos + at] = (uint16_t)__ldg(cl.col + e);
             }
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(kClassicPoints) classic_hash_kernel(const uint
         uint64_t s = 0;
         for (uint32_t e = e0; e < e1; ++e) {
             const uint32_t c = __ldg(coord + e);
+            if (!FCLSH_CHECK((c >> 6) < words, 0x0203)) continue;
             const uint64_t w = staged ? xsm[c >> 6] : __ldg(xg + (c >> 6));
             s += __ldg(bsum + e) & (0ULL - ((w >> (c & 63)) & 1ULL));
         }
@@ -408,7 +410,7 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const uint32_t j = jidx<LO, B>(other, k);
-                    if (j != 0) keys[(uint64_t)(j - 1) * ld + gp] = finish_key(S, v[g * K + k]);
+                    if (j != 0 && FCLSH_CHECK(gp < ld, 0x0201)) keys[(uint64_t)(j - 1) * ld + gp] = finish_key(S, v[g * K + k]);
                 }
             }
         }
@@ -440,9 +442,12 @@ __device__ __forceinline__ void scatter_sketch(uint64_t *sm, uint32_t W, const u
             for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
                 const uint32_t c = ci[j];
                 const uint32_t e1 = __ldg(cl.off + c + 1);
-                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(__ldg(cl.col + e), p)),
-                              (unsigned long long)__ldg(cl.b + e));
+                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e) {
+                    const uint32_t col = __ldg(cl.col + e);
+                    if (FCLSH_CHECK(col < W, 0x0202))
+                        atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(col, p)),
+                                  (unsigned long long)__ldg(cl.b + e));
+                }
             }
         }
         return;
@@ -741,5 +746,7 @@ cudaError_t launch_extract_set_bits(const uint64_t *pts, uint64_t n, uint32_t wo
     note_launch();
     return cudaGetLastError();
 }
+
+FCLSH_CHECK_READER(check_first_hash)
 
 }  // namespace fclsh

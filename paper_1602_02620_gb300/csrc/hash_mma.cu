@@ -225,16 +225,28 @@ __global__ void __launch_bounds__(kMmaThreads, 2) hash_mma_kernel(const uint64_t
             }
         }
     } else {
-        // X's tile: thread (p, quarter) writes a quarter of point p's K coordinates as fp16 0/1
-        const uint32_t p = tid & (kMmaM - 1), qt = tid >> 7;
-        const uint64_t gp = p0 + p;
-        const uint64_t *x = pts + (gp < cnt ? gp : 0) * words;
-        const bool valid = gp < cnt;
-        for (uint32_t k = qt * (K / 4); k < (qt + 1) * (K / 4); ++k) {
-            const uint32_t c = __ldg(coord + k);
-            uint16_t v = 0;
-            if (valid && c != 0xFFFFFFFFu) v = ((__ldg(x + (c >> 6)) >> (c & 63)) & 1ull) ? 0x3C00u : 0u;
-            *reinterpret_cast<uint16_t *>(xa + sw128_offset(p, k, kMmaM)) = v;
+        // X's tile: 16-byte chunks of eight fp16 0/1 values (coordinates 8c .. 8c+7 of point p),
+        // built in registers and stored whole; lanes take consecutive points, so a warp's
+        // stores cover its 32 rows at one chunk (four wavefronts, the 128-byte swizzle's minimum)
+        const uint32_t chunks = K / 8;
+        for (uint32_t it = tid; it < (uint32_t)kMmaM * chunks; it += kConsumerWarps * 32) {
+            const uint32_t p = it & (kMmaM - 1), c8 = it >> 7;
+            const uint64_t gp = p0 + p;
+            const bool valid = gp < cnt;
+            const uint64_t *x = pts + (valid ? gp : 0) * words;
+            uint32_t h[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t pair = 0;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const uint32_t c = __ldg(coord + c8 * 8 + 2 * i + hh);
+                    if (valid && c != 0xFFFFFFFFu && ((__ldg(x + (c >> 6)) >> (c & 63)) & 1ull))
+                        pair |= 0x3C00u << (16 * hh);
+                }
+                h[i] = pair;
+            }
+            *reinterpret_cast<uint4 *>(xa + sw128_offset(p, c8 * 8, kMmaM)) = make_uint4(h[0], h[1], h[2], h[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // X's tile, written by threads, feeds the MMA
     }
@@ -399,5 +411,7 @@ cudaError_t launch_hash_mma(const uint32_t *coord, const uint16_t *gmat, uint32_
     note_launch();
     return cudaGetLastError();
 }
+
+FCLSH_CHECK_READER(check_first_mma)
 
 }  // namespace fclsh

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) noalloc_probe_kernel(QueryArgs a, Noalloc
         const uint64_t en = row[e];
         if (entry_fp(en, a.ent_ib) != fp) continue;
         const uint32_t id = entry_id(en, a.ent_ib);
+        if (!FCLSH_CHECK(id < a.n, 0x0501)) continue;
         coll++;
         const uint32_t bit = 1u << (id & 31);
         if (atomicOr(sc.cand_bm + (id >> 5), bit) & bit) continue;
@@ -144,6 +145,8 @@ __global__ void __launch_bounds__(1024) noalloc_extract_kernel(NoallocScratch sc
 }
 
 }  // namespace
+
+FCLSH_CHECK_READER(check_first_noalloc)
 
 }  // namespace fclsh
 

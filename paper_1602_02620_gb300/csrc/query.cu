@@ -70,6 +70,7 @@ __device__ __forceinline__ uint64_t block_excl_scan_u32(uint32_t v, unsigned lon
 // Hamming distance between the query in shared memory and point `id`.
 __device__ __forceinline__ uint32_t distance_to(const QueryArgs &a, const uint64_t *q_s, uint32_t id)
 {
+    if (!FCLSH_CHECK(id < a.n, 0x0101)) return 0xFFFFFFFFu;
     const uint64_t *x = a.points + (uint64_t)id * a.words;
     uint32_t dist = 0;
     if ((a.words & 1) == 0) {
@@ -137,6 +138,7 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
                                               uint32_t *res_s, uint32_t *s_nres, uint64_t sq, const uint8_t *pcq)
 {
     bool isnew = false;
+    is_coll = is_coll && FCLSH_CHECK(id < a.n, 0x0109);
     if (is_coll) {
         c.coll++;
         const uint32_t bit = 1u << (id & 31);
@@ -209,20 +211,27 @@ struct Chunk {
     uint32_t tau[kU];   // the entry's table, 0xFFFFFFFF past the list's end
 };
 
-// The entries at list positions base + k * blockDim.x + threadIdx.x, k < kU (loads issued back to back).
+// The entries at list positions base + kU * threadIdx.x + k, k < kU: one search for the run of
+// the first, then a walk over the runs (loads issued back to back; a warp's positions are
+// consecutive, so a long run is read in whole lines).
 __device__ __forceinline__ void load_chunk(const QueryArgs &a, const uint32_t *lo_s, const uint32_t *off_s,
                                            uint32_t Tq, uint32_t nt, uint32_t L, uint32_t E, uint32_t base, Chunk &ch)
 {
+    const uint32_t pos0 = base + kU * threadIdx.x;
+    uint32_t j = pos0 < E ? run_of(off_s, Tq, pos0) : 0;
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
-        const uint32_t pos = base + (uint32_t)k * blockDim.x + threadIdx.x;
+        const uint32_t pos = pos0 + k;
         ch.tau[k] = 0xFFFFFFFFu;
         ch.en[k] = 0;
         if (pos < E) {
-            const uint32_t j = run_of(off_s, Tq, pos);
+            while (j + 1 < Tq && off_s[j + 1] <= pos) ++j;
             const uint32_t tau = probed_table(j, nt, L);
-            ch.tau[k] = tau;
-            ch.en[k] = __ldg(a.ent + (uint64_t)tau * a.n + lo_s[j] + (pos - off_s[j]));
+            const uint64_t e = (uint64_t)lo_s[j] + (pos - off_s[j]);
+            if (FCLSH_CHECK(e < a.n && tau < a.T, 0x0103)) {
+                ch.tau[k] = tau;
+                ch.en[k] = __ldg(a.ent + (uint64_t)tau * a.n + e);
+            }
         }
     }
 }
@@ -236,7 +245,8 @@ __device__ __forceinline__ void push_cand(bool isnew, uint32_t id, uint32_t *can
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(s_ncand, (uint32_t)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (isnew) cand_s[base + __popc(m & lanemask_lt())] = id;
+    const uint32_t at = base + __popc(m & lanemask_lt());
+    if (isnew && FCLSH_CHECK(at < kCandCap, 0x0105)) cand_s[at] = id;
 }
 
 // Distance of point id read by the whole warp (long points): 256 words per step, eight
@@ -245,6 +255,7 @@ __device__ __forceinline__ void push_cand(bool isnew, uint32_t id, uint32_t *can
 __device__ __forceinline__ uint32_t warp_distance(const QueryArgs &a, const uint64_t *q_s, uint32_t id, uint32_t radius)
 {
     const uint32_t lane = threadIdx.x & 31;
+    if (!FCLSH_CHECK(id < a.n, 0x0102)) return 0xFFFFFFFFu;
     const uint64_t *x = a.points + (uint64_t)id * a.words;
     uint32_t dist = 0, wb = 0;
     for (; wb + 256 <= a.words; wb += 256) {
@@ -262,16 +273,85 @@ __device__ __forceinline__ uint32_t warp_distance(const QueryArgs &a, const uint
     return dist + __reduce_add_sync(0xffffffffu, part);
 }
 
-// S3 for the candidates cand_s[0..m) (block-wide, uniform control flow): each is counted
-// once in #Candidates and reported if within the radius; hitmask (optional) gets the
-// hits' bits for the bitmap words [w0, w0 + blockDim.x).
+// S3 for the candidates cand_s[0..m) (block-wide): each is counted once in #Candidates and
+// reported if within the radius; hitmask (optional) gets the hits' bits for the bitmap words
+// [w0, w0 + blockDim.x).  Points of up to 31 words are read by groups of G lanes, one 16-byte
+// piece per lane (G = 8 for 16 words: a point is one 128-byte line), kV candidates per group
+// loaded before their popcounts are reduced in the group; longer points by the whole warp.
+constexpr int kV = 4;
+
+// The grouped reads of verify_list for points of H 16-byte pieces per lane (H = 1: up to 16
+// words; 2: up to 31).
+template <int H>
+__device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s,
+                                              uint32_t m, uint32_t radius, uint64_t sq, const uint8_t *pcq,
+                                              Counters &c, uint32_t *res_s, uint32_t *s_nres, uint32_t *hitmask,
+                                              uint64_t w0)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t words = a.words, pieces = (words + 1) >> 1;   // 16-byte pieces of a point
+    const uint32_t G = pieces <= 1 ? 1u : pieces <= 2 ? 2u : pieces <= 4 ? 4u : 8u;
+    const uint32_t per = 32u / G, sub = lane / G, gl = lane % G;  // candidates per warp step; group, lane in it
+    const bool even = (words & 1u) == 0;
+    for (uint32_t i0 = warp * per * kV; i0 < m; i0 += nwarps * per * kV) {   // warp-uniform bounds
+        uint32_t id[kV];
+        bool ok[kV];
+        ulonglong2 x[kV][H];
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {   // the loads of kV candidates, back to back
+            const uint32_t i = i0 + v * per + sub;
+            ok[v] = i < m;
+            id[v] = ok[v] ? cand_s[i] : 0u;
+            ok[v] = ok[v] && sig_pass(a, id[v], sq, pcq, radius) && FCLSH_CHECK(id[v] < a.n, 0x0101);
+            const uint64_t *pt = a.points + (uint64_t)id[v] * words;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const uint32_t pc = gl + h * G;
+                x[v][h] = make_ulonglong2(0, 0);
+                if (ok[v] && pc < pieces) {
+                    if (even) {
+                        x[v][h] = __ldg(reinterpret_cast<const ulonglong2 *>(pt) + pc);
+                    } else {
+                        x[v][h].x = __ldg(pt + 2 * pc);
+                        if (2 * pc + 1 < words) x[v][h].y = __ldg(pt + 2 * pc + 1);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            uint32_t part = 0;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const uint32_t pc = gl + h * G;
+                if (pc < pieces) {
+                    part += __popcll(x[v][h].x ^ q_s[2 * pc]);
+                    if (2 * pc + 1 < words) part += __popcll(x[v][h].y ^ q_s[2 * pc + 1]);
+                }
+            }
+            for (uint32_t o = G >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const uint32_t i = i0 + v * per + sub;
+            const bool lead = gl == 0 && i < m;
+            if (lead) c.cand++;
+            const bool hit = lead && ok[v] && part <= radius;
+            append_hits(hit, id[v], c, res_s, s_nres);
+            if (hit && hitmask && FCLSH_CHECK((id[v] >> 5) - w0 < blockDim.x, 0x0107))
+                atomicOr(hitmask + ((id[v] >> 5) - w0), 1u << (id[v] & 31));
+        }
+    }
+}
+
+// S3 for the candidates cand_s[0..m) (block-wide): each is counted once in #Candidates and
+// reported if within the radius; hitmask (optional) gets the hits' bits for the bitmap words
+// [w0, w0 + blockDim.x).  Points of up to 31 words are read by groups of G lanes, one 16-byte
+// piece per lane (G = 8 for 16 words: a point is one 128-byte line), kV candidates per group
+// loaded before their popcounts are reduced in the group; longer points by the whole warp.
 __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s, uint32_t m,
                                             uint32_t radius, uint64_t sq, const uint8_t *pcq, Counters &c,
                                             uint32_t *res_s, uint32_t *s_nres, uint32_t *hitmask, uint64_t w0)
 {
-    const uint32_t B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
     if (a.words >= kWarpVerifyWords) {   // a warp per candidate: coalesced reads of long points
-        const uint32_t nwarps = B >> 5;
         for (uint32_t i0 = 0; i0 < m; i0 += nwarps) {
             const uint32_t i = i0 + warp;
             const bool ok = i < m;
@@ -282,22 +362,15 @@ __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *
                 hit = sig_pass(a, id, sq, pcq, radius) && warp_distance(a, q_s, id, radius) <= radius;
             }
             append_hits(hit && lane == 0, id, c, res_s, s_nres);
-            if (hit && lane == 0 && hitmask) atomicOr(hitmask + ((id >> 5) - w0), 1u << (id & 31));
+            if (hit && lane == 0 && hitmask && FCLSH_CHECK((id >> 5) - w0 < blockDim.x, 0x0107))
+                atomicOr(hitmask + ((id >> 5) - w0), 1u << (id & 31));
         }
         return;
     }
-    for (uint32_t i0 = 0; i0 < m; i0 += B) {
-        const uint32_t i = i0 + tid;
-        const bool ok = i < m;
-        const uint32_t id = ok ? cand_s[i] : 0;
-        bool hit = false;
-        if (ok) {
-            c.cand++;
-            hit = sig_pass(a, id, sq, pcq, radius) && distance_to(a, q_s, id) <= radius;
-        }
-        append_hits(hit, id, c, res_s, s_nres);
-        if (hit && hitmask) atomicOr(hitmask + ((id >> 5) - w0), 1u << (id & 31));
-    }
+    if (a.words <= 16)
+        verify_groups<1>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, hitmask, w0);
+    else
+        verify_groups<2>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, hitmask, w0);
 }
 
 // Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
@@ -348,7 +421,7 @@ size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_lo
            512 * 4 + 64;
 }
 
-__global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
+__global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *keys_s = reinterpret_cast<uint64_t *>(smem_raw);
@@ -453,6 +526,10 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
         unsigned long long local = 0;
         for (uint32_t j = tid; j < Tq; j += B) {
             const uint32_t tau = probed_table(j, nt, L);
+            if (!FCLSH_CHECK(tau < a.T, 0x0106)) {
+                lo_s[j] = len_s[j] = 0;
+                continue;
+            }
             const uint64_t key = keys_s[tau];
             const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
             const uint32_t lo = O[0], hi = O[1];
@@ -504,6 +581,8 @@ __global__ void __launch_bounds__(512) query_batch_kernel(QueryArgs a)
                 ids[k] = entry_id(ch.en[k], a.ent_ib);
                 old[k] = 0;
             }
+#pragma unroll
+            for (int k = 0; k < kU; ++k) coll[k] = coll[k] && FCLSH_CHECK(ids[k] < a.n, 0x0104);
             if (mode == DEDUP_MARK) {   // mark only (fire-and-forget reductions); the sweep verifies
 #pragma unroll
                 for (int k = 0; k < kU; ++k)
@@ -740,6 +819,7 @@ __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uin
         const uint64_t en = row[e];
         if (entry_fp(en, a.ent_ib) != fp) continue;
         const uint32_t id = entry_id(en, a.ent_ib);
+        if (!FCLSH_CHECK(id < a.n, 0x0108)) continue;
         coll++;
         const uint32_t bit = 1u << (id & 31);
         if (atomicOr(bitmap + (id >> 5), bit) & bit) continue;
@@ -998,5 +1078,7 @@ cudaError_t launch_pack_sparse(const uint64_t *indptr, const uint32_t *indices, 
     note_launch();
     return cudaGetLastError();
 }
+
+FCLSH_CHECK_READER(check_first_query)
 
 }  // namespace fclsh

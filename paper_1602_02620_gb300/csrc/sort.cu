@@ -46,6 +46,7 @@ struct RadixArgs {
     uint32_t cap;                 // partition_scatter_kernel: 0 = places from hist; else bins of cap entries
     uint32_t *bin_cnt;            //   [rows][256] entries reserved in each bin (cap > 0)
     uint32_t *status;             //   bit 0 set when a bin overflowed (cap > 0)
+    uint64_t out_cap = 0;         // partition kernels: entries keys_out holds (bounds of the checked build)
 };
 
 // Packed partition output for the MSD directory path (partition digit = the slot's
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
         const uint32_t sub_n = (uint32_t)((len - sbase) < (uint64_t)kSortSub ? (len - sbase) : (uint64_t)kSortSub);
         for (uint32_t i = tid; i < sub_n; i += kSortThreads) {
             const uint32_t g = sg[i];
-            if (g != 0xFFFFFFFFu) a.keys_out[g] = sk[i];
+            if (g != 0xFFFFFFFFu && FCLSH_CHECK(!a.out_cap || g < a.out_cap, 0x0301)) a.keys_out[g] = sk[i];
         }
     }
 }
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(kWideThreads, 2) partition_wide_kernel(RadixAr
         const uint32_t sub_n = (uint32_t)((len - sbase) < (uint64_t)kWideSub ? (len - sbase) : (uint64_t)kWideSub);
         for (uint32_t i = tid; i < sub_n; i += kWideThreads) {
             const uint32_t g = sg[i];
-            if (g != 0xFFFFFFFFu) a.keys_out[g] = sk[i];
+            if (g != 0xFFFFFFFFu && FCLSH_CHECK(!a.out_cap || g < a.out_cap, 0x0302)) a.keys_out[g] = sk[i];
         }
         for (uint32_t d = tid; d < ND; d += kWideThreads) cur[d] += cnt[d];
     }
@@ -743,6 +744,7 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
         return;
     }
     const uint32_t cn = len;
+    if (!FCLSH_CHECK((uint64_t)lo + cn <= n, 0x0303)) return;   // block-uniform, before any barrier
     const uint64_t rowbase = (uint64_t)row * n;
     const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)lo);
     uint64_t *E = ent + rowbase + lo;
@@ -797,7 +799,8 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
     const uint32_t before = __shfl_sync(0xffffffffu, wincl - wv, warp) + incl - tot;
 #pragma unroll
     for (int i = 0; i < kOneSlots; ++i) st[i] += before;
-    if (owner) {   // the owned slots' first entries, for the placement and the directory
+    if (owner && FCLSH_CHECK((uint64_t)g * nsub + j0 + 8 <= dir_stride(sb), 0x0304)) {
+        // the owned slots' first entries, for the placement and the directory
         cnt4[pj(j0) / 4] = make_uint4(st[0], st[1], st[2], st[3]);
         cnt4[pj(j0) / 4 + 1] = make_uint4(st[4], st[5], st[6], st[7]);
         const uint32_t l = (uint32_t)lo;
@@ -894,7 +897,8 @@ __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const ui
         for (uint32_t i = tid; i < cn; i += kSegThreads) {
             const uint64_t k = ck[i];
             const uint32_t j = sub_of(k);
-            E[sub_off[j] + (i - ccnt[j])] = ent_of(k);
+            const uint64_t at = (uint64_t)sub_off[j] + (i - ccnt[j]);
+            if (FCLSH_CHECK(at < seg_len, 0x0305)) E[at] = ent_of(k);
         }
         __syncthreads();
         for (uint32_t i = tid; i < cn; i += kSegThreads) {   // advance each slot by its run in this chunk
@@ -1089,6 +1093,7 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
     const uint32_t tiles = msd_tiles(len, dbits);
     RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - dbits, (1u << dbits) - 1, buf.hist,
                 rows, sb, id_bits(len), cap, buf.bin_cnt, buf.status};
+    a.out_cap = (uint64_t)rows * (cap ? ((uint64_t)1 << dbits) * cap : len);
     if (cap) {
         if ((e = cudaMemsetAsync(buf.bin_cnt, 0, ((size_t)rows << dbits) * 4, s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(buf.status, 0, 4, s)) != cudaSuccess) return e;
@@ -1216,5 +1221,7 @@ cudaError_t launch_export_keys(const uint32_t *offs, uint64_t offs_stride, const
     note_launch();
     return cudaGetLastError();
 }
+
+FCLSH_CHECK_READER(check_first_sort)
 
 }  // namespace fclsh

@@ -15,7 +15,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libfclsh.so")
+# FCLSH_CHECKED=1 selects the checked build (bounds-checked kernels; built by build(checked=True))
+LIB_PATH = os.path.join(_HERE, "_build_checked" if os.environ.get("FCLSH_CHECKED") == "1" else "_build", "libfclsh.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ERADIUS, ETIMEOUT, EOVERFLOW = range(7)
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ERADIUS", 5: "ETIMEOUT", 6: "EOVERFLOW"}
@@ -113,6 +114,7 @@ SIGNATURES = {
     "fclsh_debug_fail_alloc": (_i, [ctypes.c_int64]),
     "fclsh_debug_pool_used": (_i, [_vp]),
     "fclsh_debug_withhold_hash_loads": (_i, [ctypes.c_int]),
+    "fclsh_debug_check_status": (_i, [_vp, _vp]),
     "fclsh_last_error": (ctypes.c_char_p, []),
     "fclsh_version": (ctypes.c_char_p, []),
 }
@@ -485,6 +487,14 @@ def debug_withhold_hash_loads(on, chunk: int = 0) -> None:
     """Make the tensor-core hash kernel's bounded waits run out (tests of ETIMEOUT): while on,
     its operand chunk `chunk` is never requested (chunk 0: before any MMA is issued)."""
     _check(lib().fclsh_debug_withhold_hash_loads(chunk + 1 if on else 0))
+
+
+def debug_check_status():
+    """(checked build?, the first failed bounds check's code since the last call, 0 if none)."""
+    checked = ctypes.c_int()
+    first = ctypes.c_uint32()
+    _check(lib().fclsh_debug_check_status(ctypes.byref(checked), ctypes.byref(first)))
+    return bool(checked.value), int(first.value)
 
 
 def debug_pool_used() -> int:

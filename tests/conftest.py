@@ -43,3 +43,23 @@ def bits_to_words(s: str):
 def bits_to_int(s: str) -> int:
     """Bit string (coordinate 0 first) as the integer sum 2^i over set coordinates."""
     return sum(1 << i for i, ch in enumerate(s) if ch == "1")
+
+
+@pytest.fixture(autouse=True)
+def _checked_build_guard(request):
+    """With FCLSH_CHECKED=1 the GPU tests run against the bounds-checked build of the library
+    (python -m paper_1602_02620_gb300.build --checked): after each one, no check may have fired."""
+    yield
+    if os.environ.get("FCLSH_CHECKED") != "1" or request.node.get_closest_marker("gpu") is None:
+        return
+    try:
+        import torch
+    except ImportError:
+        return
+    if not torch.cuda.is_available():
+        return
+    from paper_1602_02620_gb300 import fclsh
+
+    checked, first = fclsh.debug_check_status()
+    assert checked, "FCLSH_CHECKED=1 but the loaded library is not the checked build"
+    assert first == 0, "bounds check 0x%04x failed in %s" % (first, request.node.nodeid)

@@ -72,7 +72,7 @@ def full(request):
     q_dev = torch.from_numpy(qs.view(np.int64)).cuda()
     cache = os.path.join(ROOT, "paper_1602_02620_gb300", "_build", "autotune.json")
     idx0 = fclsh.build(pts_dev, c["d"], c["r"], seed, **bopts)
-    tuned = idx0.autotune(q_dev[: min(nq, 4096)], c["r"], cache)
+    tuned = idx0.autotune(q_dev[: min(nq, 8192)], c["r"], cache)
     idx0.free()
     idx = fclsh.build(pts_dev, c["d"], c["r"], seed, hash_tile=tuned["hash_tile"], **bopts)
     idx.set_tuning(**tuned)
