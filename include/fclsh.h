@@ -155,8 +155,9 @@ typedef struct {
                                  signatures (bit j: a set coordinate among the j-th ceil(d/64) coordinates;
                                  the query's bits in blocks the point leaves empty, plus one per block only the
                                  point occupies) and reads the point only when the bound is within the radius.
-                                 Same ids and counters; pays off on sparse points.  Default: 1 when the points
-                                 average at most d/8 set bits; fclsh_autotune times both. */
+                                 Same ids and counters.  Default 0; on points that average at most d/8 set bits
+                                 fclsh_autotune times both (where the points are mostly cached the extra
+                                 dependent load costs more than the point reads it saves). */
 } fclsh_tuning;
 
 /* ------------------------------------------------------------------ index */

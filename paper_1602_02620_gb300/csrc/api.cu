@@ -855,8 +855,8 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     if (idx->sc_b) FCLSH_CUDA(cudaMemcpyAsync(idx->sc_b, sblock.data(), sblock.size() * 8, cudaMemcpyHostToDevice, s));
     if ((e = keep.alloc(&idx->status, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
     FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
-    // block-occupancy signatures of the points (S3's pre-filter) and their popcount total,
-    // which decides the filter's default: on when the points average at most d/8 set bits
+    // block-occupancy signatures of the points (S3's pre-filter; off by default, timed by
+    // fclsh_autotune on points that average at most d/8 set bits) and their popcount total
     idx->sig_block = (d + 63) / 64;
     if ((e = keep.alloc(&idx->sig, n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(signatures)");
     idx->device_bytes += n * 8;
@@ -869,7 +869,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         FCLSH_CUDA(cudaMemcpyAsync(&pop_total, d_pop, 8, cudaMemcpyDeviceToHost, s));
         FCLSH_CUDA(cudaStreamSynchronize(s));
     }
-    idx->tune.verify_filter = (double)pop_total <= (double)n * d / 8.0 ? 1u : 0u;
+    idx->sparse = (double)pop_total <= (double)n * d / 8.0;
     if (o.hash_tile == 2) {
         fclsh_status st = ensure_mma_operands(idx, s, &keep);
         if (st != FCLSH_OK) return st;
@@ -2043,8 +2043,9 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
                         best = t;
                     }
                 }
-    // S3's signature pre-filter, on and off, with the chosen shape
-    if (st == FCLSH_OK) {
+    // S3's signature pre-filter, on and off, with the chosen shape (sparse points only: on dense
+    // ones the bound never rejects)
+    if (st == FCLSH_OK && idx->sparse) {
         float ms_f[2] = {1e30f, 1e30f};
         for (uint32_t vf = 0; vf <= 1; ++vf) {
             fclsh_tuning t = best;

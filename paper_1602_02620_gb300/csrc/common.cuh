@@ -263,6 +263,7 @@ struct fclsh_index {
     uint64_t *cl_b = nullptr;
     uint64_t *sig = nullptr;         // [n] block-occupancy signature of every point (S3 pre-filter)
     uint32_t sig_block = 1;          // coordinates per signature block: ceil(d / 64)
+    bool sparse = false;             // the points average at most d/8 set bits
     uint64_t device_bytes = 0;
     fclsh_tuning tune{};
     // timing (CUDA events per phase)

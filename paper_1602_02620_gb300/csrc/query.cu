@@ -273,11 +273,7 @@ __device__ __forceinline__ uint32_t warp_distance(const QueryArgs &a, const uint
     return dist + __reduce_add_sync(0xffffffffu, part);
 }
 
-// S3 for the candidates cand_s[0..m) (block-wide): each is counted once in #Candidates and
-// reported if within the radius; hitmask (optional) gets the hits' bits for the bitmap words
-// [w0, w0 + blockDim.x).  Points of up to 31 words are read by groups of G lanes, one 16-byte
-// piece per lane (G = 8 for 16 words: a point is one 128-byte line), kV candidates per group
-// loaded before their popcounts are reduced in the group; longer points by the whole warp.
+// Candidates whose points a group of lanes loads before reducing any of them.
 constexpr int kV = 4;
 
 // The grouped reads of verify_list for points of H 16-byte pieces per lane (H = 1: up to 16
@@ -285,8 +281,7 @@ constexpr int kV = 4;
 template <int H>
 __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s,
                                               uint32_t m, uint32_t radius, uint64_t sq, const uint8_t *pcq,
-                                              Counters &c, uint32_t *res_s, uint32_t *s_nres, uint32_t *hitmask,
-                                              uint64_t w0)
+                                              Counters &c, uint32_t *res_s, uint32_t *s_nres)
 {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t words = a.words, pieces = (words + 1) >> 1;   // 16-byte pieces of a point
@@ -335,20 +330,17 @@ __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t
             if (lead) c.cand++;
             const bool hit = lead && ok[v] && part <= radius;
             append_hits(hit, id[v], c, res_s, s_nres);
-            if (hit && hitmask && FCLSH_CHECK((id[v] >> 5) - w0 < blockDim.x, 0x0107))
-                atomicOr(hitmask + ((id[v] >> 5) - w0), 1u << (id[v] & 31));
         }
     }
 }
 
 // S3 for the candidates cand_s[0..m) (block-wide): each is counted once in #Candidates and
-// reported if within the radius; hitmask (optional) gets the hits' bits for the bitmap words
-// [w0, w0 + blockDim.x).  Points of up to 31 words are read by groups of G lanes, one 16-byte
+// reported if within the radius.  Points of up to 31 words are read by groups of G lanes, one 16-byte
 // piece per lane (G = 8 for 16 words: a point is one 128-byte line), kV candidates per group
 // loaded before their popcounts are reduced in the group; longer points by the whole warp.
 __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s, uint32_t m,
                                             uint32_t radius, uint64_t sq, const uint8_t *pcq, Counters &c,
-                                            uint32_t *res_s, uint32_t *s_nres, uint32_t *hitmask, uint64_t w0)
+                                            uint32_t *res_s, uint32_t *s_nres)
 {
     const uint32_t B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
     if (a.words >= kWarpVerifyWords) {   // a warp per candidate: coalesced reads of long points
@@ -362,15 +354,13 @@ __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *
                 hit = sig_pass(a, id, sq, pcq, radius) && warp_distance(a, q_s, id, radius) <= radius;
             }
             append_hits(hit && lane == 0, id, c, res_s, s_nres);
-            if (hit && lane == 0 && hitmask && FCLSH_CHECK((id >> 5) - w0 < blockDim.x, 0x0107))
-                atomicOr(hitmask + ((id >> 5) - w0), 1u << (id & 31));
         }
         return;
     }
     if (a.words <= 16)
-        verify_groups<1>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, hitmask, w0);
+        verify_groups<1>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres);
     else
-        verify_groups<2>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, hitmask, w0);
+        verify_groups<2>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres);
 }
 
 // Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
@@ -417,8 +407,7 @@ __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
 size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_log2)
 {
     const size_t tb = (size_t)W * 8 > ((size_t)4 << hset_log2) ? (size_t)W * 8 : ((size_t)4 << hset_log2);
-    return (size_t)T * 8 + (size_t)T * 8 + tb + (size_t)words * 8 + (size_t)kResCap * 4 + (size_t)kCandCap * 4 +
-           512 * 4 + 64;
+    return (size_t)T * 8 + (size_t)T * 8 + tb + (size_t)words * 8 + (size_t)kResCap * 4 + (size_t)kCandCap * 4 + 64;
 }
 
 __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
@@ -433,7 +422,6 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
     uint64_t *q_s = tbuf + tb_words;
     uint32_t *res_s = reinterpret_cast<uint32_t *>(q_s + a.words);
     uint32_t *cand_s = res_s + kResCap;        // a chunk's new candidates
-    uint32_t *hitmask_s = cand_s + kCandCap;   // the sweep's hits, per bitmap word of a chunk
     __shared__ unsigned long long s_qi;
     __shared__ uint32_t s_nres, s_ncand;
     __shared__ unsigned long long red64[32];
@@ -542,9 +530,11 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
         // more bucket entries than bitmap words: mark the bitmap and sweep it once
         const bool sweep_mode = bitmap_mode && E > a.bm_words;
         const int mode = sweep_mode ? DEDUP_MARK : (bitmap_mode ? DEDUP_BITMAP : DEDUP_HSET);
-        // the bucket entries as one list (positions in 32 bits; a query past that walks its
-        // runs lane by lane instead)
-        const bool listed = E <= 0xFFFFFFFFull - (unsigned long long)B * kU;
+        // the bucket entries as one list (positions in 32 bits) for the hash-set and bitmap
+        // modes; the marking of a very heavy query, and a query of 2^32 entries or more, walk
+        // their runs lane by lane instead (measured faster for the marking, whose work is the
+        // fire-and-forget reductions, and no limit on the positions)
+        const bool listed = !sweep_mode && E <= 0xFFFFFFFFull - (unsigned long long)B * kU;
         const uint32_t E32 = listed ? (uint32_t)E : 0u;
         uint32_t *off_s = len_s;   // len_s becomes the runs' exclusive prefix
         if (listed) {
@@ -605,14 +595,15 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
 #pragma unroll
             for (int k = 0; k < kU; ++k) push_cand(coll[k] && !old[k], ids[k], cand_s, &s_ncand);
             __syncthreads();
-            verify_list(a, q_s, cand_s, s_ncand, radius, sq, s_pcq, c, res_s, &s_nres, nullptr, 0);
+            verify_list(a, q_s, cand_s, s_ncand, radius, sq, s_pcq, c, res_s, &s_nres);
             __syncthreads();
             if (tid == 0) s_ncand = 0;
             __syncthreads();
         }
         if (!listed) {
-            // a query with 2^32 bucket entries or more: warps take 32 tables, a lane walks its
-            // own short run, the warp a long one (the runs' lengths are still in len_s)
+            // marking (sweep mode) or a query with 2^32 bucket entries or more: warps take 32
+            // tables, a lane walks its own short run, the warp a long one (the runs' lengths are
+            // still in len_s)
             for (uint32_t base = warp * 32; base < Tq; base += nwarps * 32) {
                 const uint32_t j = base + lane;
                 const bool has = j < Tq;
@@ -648,36 +639,30 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
             }
         }
         if (sweep_mode) {
-            // S2/S3 for a very heavy query: every candidate is marked; sweep the bitmap a chunk
-            // of blockDim.x words at a time, each thread listing up to kU of its word's ids per
-            // round, verify the listed ids together, and leave only the hits marked
+            // S2/S3 for a very heavy query: every candidate is marked; sweep the bitmap (warps
+            // take 32 consecutive words, a lane a word, no block barrier), verify each marked id
+            // (a lane reads its point whole: 32 points in flight per warp), and leave only the
+            // hits marked (cleared below)
             __threadfence();
             __syncthreads();
-            for (uint64_t w0 = 0; w0 < a.bm_words; w0 += B) {
-                const uint64_t wi = w0 + tid;
+            for (uint64_t w0 = (uint64_t)warp * 32; w0 < a.bm_words; w0 += (uint64_t)nwarps * 32) {
+                const uint64_t wi = w0 + lane;
                 const uint32_t bits = wi < a.bm_words ? __ldcg(bm + wi) : 0u;
-                uint32_t rem = bits;
-                hitmask_s[tid] = 0;
-                __syncthreads();
-                for (;;) {
-#pragma unroll
-                    for (int k = 0; k < kU; ++k) {
-                        const bool has = rem != 0;
-                        uint32_t id = 0;
-                        if (has) {
-                            id = (uint32_t)(wi * 32 + (uint32_t)(__ffs(rem) - 1));
-                            rem &= rem - 1;
-                        }
-                        push_cand(has, id, cand_s, &s_ncand);
+                c.cand += __popc(bits);
+                uint32_t rem = bits, hits = 0;
+                while (__any_sync(0xffffffffu, rem != 0)) {
+                    bool hit = false;
+                    uint32_t id = 0;
+                    if (rem) {
+                        const uint32_t b = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        id = (uint32_t)(wi * 32 + b);
+                        hit = sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius;
+                        if (hit) hits |= 1u << b;
                     }
-                    __syncthreads();
-                    verify_list(a, q_s, cand_s, s_ncand, radius, sq, s_pcq, c, res_s, &s_nres, hitmask_s, w0);
-                    __syncthreads();
-                    if (tid == 0) s_ncand = 0;
-                    if (!__syncthreads_or(rem != 0)) break;
+                    append_hits(hit, id, c, res_s, &s_nres);
                 }
-                if (bits) bm[wi] = hitmask_s[tid];
-                __syncthreads();
+                if (bits) bm[wi] = hits;
             }
         }
         const unsigned long long tc = block_sum(c.coll, red64);
