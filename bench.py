@@ -395,6 +395,33 @@ def serve_sweep(args):
                                       "rows": rows}}))
 
 
+def classic_lsh(fclsh, w, pts, qs, truth, seed: int, delta: float = 0.1) -> dict:
+    """Classic bit-sampling LSH (Sec. 2.2) with the covering index's table count and k by the rule
+    of Sec. 4.2 for false-negative ratio delta, on the same points and batch: its recall against
+    the exact answers (it reports only verified neighbours, so recall = its hits / the exact hits),
+    its counters, and its build + batch time, beside covering LSH's recall of 1."""
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    idx = fclsh.build(pts, w.d, w.r, seed, classic_delta=delta)
+    ev[1].record()
+    res = idx.query(qs, w.r)
+    ev[2].record()
+    torch.cuda.synchronize()
+    samples, _ = idx.classic_params()
+    L, k = idx.T, int(samples.shape[1])
+    idx.free()
+    got, want = np.diff(res.offs).astype(np.int64), np.diff(truth.offs).astype(np.int64)
+    has = want > 0
+    return {"delta": delta, "tables": L, "k": k, "recall": float(got.sum() / max(want.sum(), 1)),
+            "mean_query_recall": float((got[has] / want[has]).mean()) if has.any() else 1.0,
+            "queries_fully_answered": float((got[has] == want[has]).mean()) if has.any() else 1.0,
+            "collisions_per_query": float(res.collisions.mean()), "candidates_per_query": float(res.candidates.mean()),
+            "build_ms": ev[0].elapsed_time(ev[1]), "batch_ms": ev[1].elapsed_time(ev[2]),
+            "queries_per_s": qs.shape[0] / (ev[0].elapsed_time(ev[2]) / 1000.0)}
+
+
 def workload_config(w, tables: int, nq: int, name: str) -> dict:
     """The `config` object of a JSON line (the same for both arms)."""
     sb = 13
@@ -695,6 +722,7 @@ def main():
     serve_rows = served(fclsh, idx, w, batched_qps=batched_qps, probe_rows=1)
     routes = hash_routes(fclsh, idx, pts)
     idx.free()
+    classic = classic_lsh(fclsh, w, pts, qs, res, seed) if 0 < w.r < w.d <= 4096 else None
 
     # ---- e2e through the C ABI from pinned host buffers
     hp = torch.from_numpy(w.points.view(np.int64)).pin_memory()
@@ -830,6 +858,7 @@ def main():
             "results_per_step": total,
             "tuning": tuned,
         },
+        "classic_lsh": classic,
         "served": serve,
         "served_row_probe": serve_rows,
         "hash_routes": routes,
