@@ -860,16 +860,13 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->sig_block = (d + 63) / 64;
     if ((e = keep.alloc(&idx->sig, n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(signatures)");
     idx->device_bytes += n * 8;
+    // (the total is read after the build's final synchronisation: no wait here)
     unsigned long long *d_pop = nullptr, pop_total = 0;
-    {
-        DevAllocs one(true);
-        if ((e = one.alloc(&d_pop, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(popcount total)");
-        FCLSH_CUDA(cudaMemsetAsync(d_pop, 0, 8, s));
-        FCLSH_CUDA(launch_point_sig(idx->points, n, idx->words, d, idx->sig_block, idx->sig, d_pop, idx->sm_count, s));
-        FCLSH_CUDA(cudaMemcpyAsync(&pop_total, d_pop, 8, cudaMemcpyDeviceToHost, s));
-        FCLSH_CUDA(cudaStreamSynchronize(s));
-    }
-    idx->sparse = (double)pop_total <= (double)n * d / 8.0;
+    DevAllocs pop_buf(true);
+    if ((e = pop_buf.alloc(&d_pop, 1)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(popcount total)");
+    FCLSH_CUDA(cudaMemsetAsync(d_pop, 0, 8, s));
+    FCLSH_CUDA(launch_point_sig(idx->points, n, idx->words, d, idx->sig_block, idx->sig, d_pop, idx->sm_count, s));
+    FCLSH_CUDA(cudaMemcpyAsync(&pop_total, d_pop, 8, cudaMemcpyDeviceToHost, s));
     if (o.hash_tile == 2) {
         fclsh_status st = ensure_mma_operands(idx, s, &keep);
         if (st != FCLSH_OK) return st;
@@ -987,6 +984,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         }
     }
     FCLSH_CUDA(cudaStreamSynchronize(s));
+    idx->sparse = (double)pop_total <= (double)n * d / 8.0;
     {
         fclsh_status st = check_status(idx, s);
         if (st != FCLSH_OK) return st;
