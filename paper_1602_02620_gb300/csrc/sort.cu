@@ -578,65 +578,25 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restric
 // ---------------------------------------------------------------- directory, second half (MSD path)
 
 constexpr int kSegThreads = 512;
-constexpr int kSegItems = 8;                          // per thread per chunk
-constexpr int kSegChunk = kSegThreads * kSegItems;    // 4096 entries
+constexpr int kSegItems = 4;                          // entries per thread in flight per round
 constexpr int kSegWarps = kSegThreads / 32;
 constexpr int kSubMaxBits = 12;                       // slot bits below the partition digit
 
-// Stable warp-multisplit ranking of 8 items per lane by a digit < 64: returns
-// each item's position in the chunk's digit-sorted order (chunk items are taken
-// warp by warp, round by round, in index order).
-__device__ __forceinline__ void seg_rank(const uint32_t (&dig)[kSegItems], uint32_t nvalid_warp_base, uint32_t cn,
-                                         uint32_t (&pos)[kSegItems], uint32_t *wh /*[kSegWarps][64]*/,
-                                         uint32_t *dstart /*[64]*/)
+// One shared-memory atomic add of 1 per lane on cnt[j], aggregated over the lanes of the
+// warp that take the same j (valid lanes only; every lane of the warp calls it): the
+// lowest lane of each group adds the group's size once.  Returns the counter's value
+// before the lane's own unit, i.e. the lane's place among the entries counted so far.
+__device__ __forceinline__ uint32_t warp_aggregated_add(uint32_t *cnt, uint32_t j, bool valid)
 {
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t i = tid; i < kSegWarps * 64; i += kSegThreads) wh[i] = 0;
-    __syncthreads();
-    uint32_t *w = wh + warp * 64;
-#pragma unroll
-    for (int r = 0; r < kSegItems; ++r) {
-        const uint32_t idx = nvalid_warp_base + r * 32 + lane;
-        const bool valid = idx < cn;
-        const uint32_t d = valid ? dig[r] : 0u;
-        const uint32_t peers = same_digit_lanes<6>(d, valid);
-        const uint32_t before = valid ? w[d] : 0u;
-        pos[r] = before + __popc(peers & lt);
-        __syncwarp();
-        if (valid && (peers & lt) == 0) w[d] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    if (tid < 64) {   // digit tid: chunk-wide start, then each warp's base
-        uint32_t tot = 0;
-        for (int v = 0; v < kSegWarps; ++v) tot += wh[v * 64 + tid];
-        dstart[tid] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t run = 0;
-        for (int d = 0; d < 64; ++d) {
-            const uint32_t c = dstart[d];
-            dstart[d] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    if (tid < 64) {
-        uint32_t run = dstart[tid];
-        for (int v = 0; v < kSegWarps; ++v) {
-            const uint32_t c = wh[v * 64 + tid];
-            wh[v * 64 + tid] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kSegItems; ++r) {
-        const uint32_t idx = nvalid_warp_base + r * 32 + lane;
-        if (idx < cn) pos[r] += w[dig[r]];
-    }
+    const uint32_t act = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return 0;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t peers = __match_any_sync(act, j);
+    const uint32_t leader = (uint32_t)__ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&cnt[j], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
 // Exclusive scan in place of v[0..cnt) (cnt <= 4096) by the whole block; optionally
@@ -819,11 +779,15 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
     }
 }
 
-// Segments longer than one chunk (listed by segment_one_kernel; clustered or
-// duplicate-heavy data): one block per listed segment writes its directory and
-// entries chunk by chunk, each chunk grouped by slot through two shared-memory
-// digit passes.
-__global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const uint64_t *__restrict__ packed,
+// Segments longer than kOneCap entries (listed by segment_one_kernel; a key that
+// repeats in many points, such as the empty sum of sparse points, puts thousands of
+// entries into one slot): blocks take the listed segments in turn.  The segment's
+// entries are counted into their slots with warp-aggregated shared-memory atomics, the
+// counts are scanned into each slot's first entry (written to the directory), and each
+// entry goes to its slot's run at the place a second aggregated atomic returns.  The
+// order inside a run is not part of the directory; the lanes of a warp that share a slot
+// take consecutive places, so the heavy slot is written with coalesced stores.
+__global__ void __launch_bounds__(kSegThreads, 3) segment_finish_kernel(const uint64_t *__restrict__ packed,
                                                                         uint64_t n, uint64_t in_stride, uint32_t cap,
                                                                         uint32_t sb, uint32_t idbits, uint32_t dbits,
                                                                         const uint32_t *__restrict__ seg_out,
@@ -832,87 +796,56 @@ __global__ void __launch_bounds__(kSegThreads, 2) segment_finish_kernel(const ui
                                                                         const unsigned long long *big_cnt,
                                                                         const uint32_t *big)
 {
-  const unsigned long long nbig = *big_cnt;
-  for (unsigned long long bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *ck = reinterpret_cast<uint64_t *>(smem_raw);                  // [kSegChunk]
-    uint32_t *sub_off = reinterpret_cast<uint32_t *>(ck + kSegChunk);        // [nsub]
-    uint32_t *ccnt = sub_off + (1u << kSubMaxBits);                          // [nsub + 1]
-    uint32_t *wh = ccnt + (1u << kSubMaxBits) + 1;                           // [kSegWarps][64]
-    __shared__ uint32_t dstart[64];
+    __shared__ uint32_t sub_off[1u << kSubMaxBits];
     __shared__ uint32_t wsum[32];
-    const uint32_t nd = 1u << dbits, g = big[bi] & (nd - 1), row = big[bi] >> dbits, tid = threadIdx.x;
-    const uint32_t lane = tid & 31, warp = tid >> 5;
+    const unsigned long long nbig = *big_cnt;
+    const uint32_t nd = 1u << dbits, tid = threadIdx.x;
     const uint32_t subb = sb - dbits, nsub = 1u << subb, smask = nsub - 1;
-    const uint32_t b1 = subb / 2, m1 = (1u << b1) - 1;
     const uint64_t low52 = (1ULL << 52) - 1, idmask = (1ULL << idbits) - 1;
-    const uint64_t rowbase = (uint64_t)row * n;
-    const uint32_t seg_lo = seg_out[(uint64_t)row * (nd + 1) + g], seg_hi = seg_out[(uint64_t)row * (nd + 1) + g + 1];
-    const uint64_t seg_len = seg_hi - seg_lo;
-    const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)seg_lo);
-    uint64_t *E = ent + rowbase + seg_lo;
-    uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;
     auto sub_of = [&](uint64_t v) { return (uint32_t)(v >> 52) & smask; };
     auto ent_of = [&](uint64_t v) { return ((v & low52) >> idbits) << entry_id_bits(sb) | (v & idmask); };
-    if (g == nd - 1 && tid == 0) O[nsub] = (uint32_t)n;
+    for (unsigned long long bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const uint32_t g = big[bi] & (nd - 1), row = big[bi] >> dbits;
+        const uint32_t seg_lo = seg_out[(uint64_t)row * (nd + 1) + g], seg_hi = seg_out[(uint64_t)row * (nd + 1) + g + 1];
+        const uint64_t seg_len = seg_hi - seg_lo;
+        if (!FCLSH_CHECK((uint64_t)seg_lo + seg_len <= n && seg_lo <= seg_hi, 0x0306)) return;   // block-uniform
+        const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)seg_lo);
+        uint64_t *E = ent + (uint64_t)row * n + seg_lo;
+        uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;
+        if (g == nd - 1 && tid == 0) O[nsub] = (uint32_t)n;
 
-    // several chunks: per-slot counts of the whole segment first, then stable passes
-    for (uint32_t j = tid; j < nsub; j += kSegThreads) sub_off[j] = 0;
-    __syncthreads();
-    for (uint64_t e = tid; e < seg_len; e += kSegThreads) atomicAdd(&sub_off[sub_of(Pk[e])], 1u);
-    __syncthreads();
-    seg_scan(sub_off, nsub, wsum, O, (uint32_t)seg_lo);
-    for (uint64_t cs = 0; cs < seg_len; cs += kSegChunk) {
-        const uint32_t cn = (uint32_t)(seg_len - cs < (uint64_t)kSegChunk ? seg_len - cs : (uint64_t)kSegChunk);
-        const uint32_t wb = warp * (32 * kSegItems);
-        uint64_t key[kSegItems];
-        uint32_t dig[kSegItems], pos[kSegItems];
-#pragma unroll
-        for (int r = 0; r < kSegItems; ++r) {
-            const uint32_t idx = wb + r * 32 + lane;
-            key[r] = idx < cn ? Pk[cs + idx] : 0;
-            dig[r] = sub_of(key[r]) & m1;
-        }
-        for (uint32_t j = tid; j < nsub; j += kSegThreads) ccnt[j] = 0;
+        for (uint32_t j = tid; j < nsub; j += kSegThreads) sub_off[j] = 0;
         __syncthreads();
+        // every lane runs the same rounds (the aggregated atomics need whole warps)
+        for (uint64_t e0 = 0; e0 < seg_len; e0 += (uint64_t)kSegThreads * kSegItems) {
+            uint64_t v[kSegItems];
 #pragma unroll
-        for (int r = 0; r < kSegItems; ++r)
-            if (wb + r * 32 + lane < cn) atomicAdd(&ccnt[sub_of(key[r])], 1u);
-        seg_rank(dig, wb, cn, pos, wh, dstart);            // pass 1: low b1 bits of the slot
+            for (int r = 0; r < kSegItems; ++r) {
+                const uint64_t e = e0 + (uint64_t)r * kSegThreads + tid;
+                v[r] = e < seg_len ? Pk[e] : 0;
+            }
 #pragma unroll
-        for (int r = 0; r < kSegItems; ++r)
-            if (wb + r * 32 + lane < cn) ck[pos[r]] = key[r];
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kSegItems; ++r) {
-            const uint32_t idx = wb + r * 32 + lane;
-            key[r] = idx < cn ? ck[idx] : 0;
-            dig[r] = sub_of(key[r]) >> b1;
-        }
-        seg_rank(dig, wb, cn, pos, wh, dstart);            // pass 2: remaining slot bits
-#pragma unroll
-        for (int r = 0; r < kSegItems; ++r)
-            if (wb + r * 32 + lane < cn) ck[pos[r]] = key[r];
-        seg_scan(ccnt, nsub, wsum, nullptr, 0);             // chunk-relative start of each slot
-        for (uint32_t i = tid; i < cn; i += kSegThreads) {
-            const uint64_t k = ck[i];
-            const uint32_t j = sub_of(k);
-            const uint64_t at = (uint64_t)sub_off[j] + (i - ccnt[j]);
-            if (FCLSH_CHECK(at < seg_len, 0x0305)) E[at] = ent_of(k);
+            for (int r = 0; r < kSegItems; ++r)
+                warp_aggregated_add(sub_off, sub_of(v[r]), e0 + (uint64_t)r * kSegThreads + tid < seg_len);
         }
         __syncthreads();
-        for (uint32_t i = tid; i < cn; i += kSegThreads) {   // advance each slot by its run in this chunk
-            const uint32_t j = sub_of(ck[i]);
-            if (i == ccnt[j]) {
-                uint32_t c = 1;
-                while (i + c < cn && sub_of(ck[i + c]) == j) ++c;
-                sub_off[j] += c;
+        seg_scan(sub_off, nsub, wsum, O, seg_lo);   // sub_off[j]: slot j's first entry in the segment
+        for (uint64_t e0 = 0; e0 < seg_len; e0 += (uint64_t)kSegThreads * kSegItems) {
+            uint64_t v[kSegItems];
+#pragma unroll
+            for (int r = 0; r < kSegItems; ++r) {
+                const uint64_t e = e0 + (uint64_t)r * kSegThreads + tid;
+                v[r] = e < seg_len ? Pk[e] : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < kSegItems; ++r) {
+                const bool valid = e0 + (uint64_t)r * kSegThreads + tid < seg_len;
+                const uint32_t at = warp_aggregated_add(sub_off, sub_of(v[r]), valid);
+                if (valid && FCLSH_CHECK(at < seg_len, 0x0305)) E[at] = ent_of(v[r]);
             }
         }
         __syncthreads();
     }
-    __syncthreads();
-  }
 }
 
 }  // namespace
@@ -1034,7 +967,6 @@ cudaError_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, u
 
 namespace fclsh {
 
-size_t segment_finish_smem() { return (size_t)kSegChunk * 8 + ((2u << kSubMaxBits) + 1) * 4 + kSegWarps * 64 * 4; }
 size_t segment_one_smem() { return (size_t)kOneCap * 8 + ((1u << kSubMaxBits) + (1u << kSubMaxBits) / 8 + 4) * 4; }
 
 static uint32_t id_bits(uint64_t len)
@@ -1145,12 +1077,8 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
 {
     const uint32_t dbits = msd_dbits(sb);
     static cudaError_t once = [] {
-        cudaError_t e = cudaFuncSetAttribute(segment_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)segment_finish_smem());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(segment_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)segment_one_smem());
-        return e;
+        return cudaFuncSetAttribute(segment_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)segment_one_smem());
     }();
     if (once != cudaSuccess) return once;
     if (reinterpret_cast<uintptr_t>(offs) & 15) return cudaErrorMisalignedAddress;   // vector stores of offsets
@@ -1164,7 +1092,7 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
     segment_one_kernel<<<dim3(1u << dbits, rows), kOneThreads, segment_one_smem(), s>>>(
         buf.keys_a, len, in_stride, cap, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
     note_launch();
-    segment_finish_kernel<<<sm_count, kSegThreads, segment_finish_smem(), s>>>(
+    segment_finish_kernel<<<3 * sm_count, kSegThreads, 0, s>>>(
         buf.keys_a, len, in_stride, cap, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
     note_launch();
     return cudaGetLastError();

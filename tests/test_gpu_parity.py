@@ -414,6 +414,39 @@ def test_wide_partition_directory_matches_oracle(slot_bits, skewed):
     idx.free()
 
 
+@pytest.mark.parametrize("skewed", [False, True])
+def test_long_segments_match_oracle(skewed):
+    """Segments longer than one block's 4,608 entries (2^13 slots in two segments of ~15,000
+    entries; with skew, 6,000 equal points on one slot of every table, as the empty sum of
+    sparse points does): the directory that the long-segment kernel writes holds the oracle's
+    buckets, every slot in order, and queries over it match the oracle."""
+    rng = np.random.default_rng(4608 + skewed)
+    d, r, n = 64, 3, 30_000
+    pts = rand_points(rng, n, d)
+    if skewed:
+        pts[1000:7000] = pts[11]
+    seed = 4242
+    p = oracle.derive_params(seed, d, r)
+    idx = F().build(dev(pts), d, r, seed, slot_bits=13)
+    for tau in sorted({0, 3, p.T - 1}):
+        keys, ids = idx.export_table(tau)
+        sl = keys & np.uint64((1 << 13) - 1)
+        assert np.all(np.diff(sl.astype(np.int64)) >= 0)
+        order = np.lexsort((ids, keys))
+        ok, oi = oracle.table(p, pts, tau)
+        assert np.array_equal(keys[order], ok) and np.array_equal(ids[order], oi)
+        for key in {int(ok[0]), int(ok[len(ok) // 2]), int(keys[1011])}:
+            assert np.array_equal(idx.bucket(tau, key), oi[ok == key])
+    qs = np.concatenate([near(rng, pts, d, r, 20), pts[[11, 12]]])
+    tables = oracle.build_tables(p, pts)
+    res = idx.query(dev(qs), r)
+    for i in range(qs.shape[0]):
+        want, ncoll, ncand = oracle.query(p, pts, tables, qs[i], r)
+        assert np.array_equal(res.of(i), want)
+        assert (int(res.collisions[i]), int(res.candidates[i])) == (ncoll, ncand)
+    idx.free()
+
+
 @pytest.mark.parametrize("dup,nq", [(2000, 2200), (20_000, 260)])
 def test_result_overflow_reruns_only_the_queries_past_the_buffer(dup, nq):
     """A batch whose hits pass a fresh context's result buffer (2^22 ids): every query reserved
