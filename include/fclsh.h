@@ -96,7 +96,7 @@ typedef struct {
        Table j samples classic_k coordinates s_j(1..k) uniformly with replacement and keys a point
        by Eq. 1 on them, key_j(x) = (sum_i b_i x_{s_j(i)}) mod P, one seed vector b for all
        tables.  classic_tables = L (0 = the covering index's table count for (n, d, r), as
-       Sec. 4.2 sets it; other counts up to 2,047); classic_k = 0 takes the rule of Sec. 4.2,
+       Sec. 4.1 sets it; other counts up to 2,047); classic_k = 0 takes the rule of Sec. 4.1,
        k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)) with delta = classic_delta.  Draws from
        `seed`: every table's k samples (next() mod d) in table order, then b.  Queries use the
        same calls; probe_rows and hash_tile do not apply. */
@@ -158,6 +158,14 @@ typedef struct {
                                  Same ids and counters.  Default 0; on points that average at most d/8 set bits
                                  fclsh_autotune times both (where the points are mostly cached the extra
                                  dependent load costs more than the point reads it saves). */
+    uint32_t heavy_kernel;    /* very heavy queries (more bucket entries than the n-bit bitmap has 32-bit
+                                 words): 0 = the batch kernel marks them in its bitmap in global memory
+                                 and sweeps it; 1 = a second kernel (one CTA per SM) answers them,
+                                 marking their bucket entries in a window of ids held in shared memory,
+                                 one window after another, as large as shared memory allows; k >= 64 =
+                                 the same with windows of at most k ids (rounded down to a multiple of 64;
+                                 never below 64*W).  Same ids and counters.  Default 1; timed by
+                                 fclsh_autotune. */
 } fclsh_tuning;
 
 /* ------------------------------------------------------------------ index */
@@ -233,7 +241,7 @@ fclsh_status fclsh_derive_params(uint64_t n, uint32_t d, uint32_t r, uint64_t se
                                  uint32_t shape[3], uint32_t *perm, uint32_t *part_off, uint32_t *m, uint64_t *b);
 
 /*
- * A classic LSH index's random choices (the baseline of Sec. 4.2): *k receives the samples per
+ * A classic LSH index's random choices (the baseline of Sec. 4.1): *k receives the samples per
  * table; samples (host, [T][k], may be NULL) the sampled coordinates of every table in draw
  * order; b (host, [k], may be NULL) the seed vector of Eq. 1.  Errors: FCLSH_EINVAL for a NULL
  * index or k, or a covering-LSH index.
@@ -473,15 +481,15 @@ fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries, uint64_t 
 /*
  * Per-phase device time (milliseconds, CUDA events on the launching stream)
  * accumulated since the last reset: [0] build hash kernel, [1] build sort and
- * directory kernels (all of them), [2] batched query kernel, [3] result CSR,
+ * directory kernels (all of them), [2] batched query kernels, [3] result CSR,
  * [4] fclsh_hash kernel, [5] build partition scatter kernel, [6] build
  * segment-finish kernels, [7] build partition histogram + scan ([5]-[7] are
- * parts of [1]).  counts[i] = timed launches of phase i.  Timing is off until enabled;
+ * parts of [1]), [8] heavy-query kernel (part of [2]).  counts[i] = timed launches of phase i.  Timing is off until enabled;
  * enabling adds one event pair per phase and runs query batches without graphs.
  * Measurement aid (no counterpart in the paper).  Errors: FCLSH_EINVAL, FCLSH_ECUDA.
  */
 fclsh_status fclsh_timing_enable(fclsh_index *idx, int on);
-fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64_t counts[8], int reset);
+fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[9], uint64_t counts[9], int reset);
 
 /* Kernels this library has enqueued in this process (a replayed CUDA graph counts its kernel
    nodes).  Measurement aid (no counterpart in the paper). */

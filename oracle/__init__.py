@@ -18,7 +18,7 @@ first use); this module only marshals numpy arrays:
   ``query_listed`` runs the same query given only the tables it probes.
 * ``linear_scan``    -- the plain definition of the answer (Definition 2).
 * ``classic_*``      -- classic bit-sampling LSH (Sec. 2.2), the baseline with false
-  negatives that the paper compares against (Sec. 4.2): parameters, keys, query.
+  negatives that the paper compares against (Sec. 4.1): parameters, keys, query.
 """
 from __future__ import annotations
 
@@ -311,7 +311,7 @@ def linear_scan(pts, q, radius: int, words: int | None = None) -> np.ndarray:
 # ---------------------------------------------------------------- classic bit-sampling LSH
 
 def classic_rule_k(L: int, r: int, d: int, delta: float) -> int:
-    """Bit samples per table of classic LSH by the rule of Sec. 4.2:
+    """Bit samples per table of classic LSH by the rule of Sec. 4.1:
     k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)) -- the k at which a point at distance r
     escapes all L tables with probability about delta."""
     import math

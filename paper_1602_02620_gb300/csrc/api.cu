@@ -26,6 +26,9 @@ namespace fclsh {
 size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_log2);
 cudaError_t launch_query_batch(const QueryArgs &a, uint32_t grid, uint32_t block, size_t smem, cudaStream_t s);
 cudaError_t query_batch_occupancy(uint32_t block, size_t smem, int *ctas_per_sm);
+size_t heavy_smem_bytes(uint32_t T, uint32_t words, uint32_t win_bits);
+cudaError_t query_heavy_prepare(size_t smem);
+cudaError_t launch_query_heavy(const QueryArgs &a, uint32_t grid, size_t smem, cudaStream_t s);
 cudaError_t launch_query_plain(const QueryArgs &a, const uint64_t *keys, uint32_t *bitmap, cudaStream_t s);
 cudaError_t launch_sort_small(unsigned long long *v, const unsigned long long *d_count, cudaStream_t s);
 cudaError_t launch_bruteforce(const uint64_t *points, uint64_t n, uint32_t words, const uint64_t *queries, uint64_t nq,
@@ -291,7 +294,7 @@ using namespace fclsh;
 
 struct fclsh_qctx {
     fclsh_index *idx = nullptr;
-    unsigned long long *counters = nullptr;   // [0] work, [1] cursor
+    unsigned long long *counters = nullptr;   // [0] work, [1] cursor, [2] heavy queries listed, [3] heavy work
     uint32_t *runs = nullptr;                 // [cap] each query's sorted hits
     uint64_t cap = 0;
     uint64_t nq_cap = 0;
@@ -304,6 +307,9 @@ struct fclsh_qctx {
     uint32_t *bitmaps = nullptr;
     uint32_t grid = 0, block = 0;
     size_t smem = 0;
+    uint64_t *heavy_q = nullptr;   // [nq_cap] the batch's very heavy queries, for query_heavy_kernel
+    uint32_t win_bits = 0;         // its window of ids (0: the batch kernel sweeps heavy queries itself)
+    size_t heavy_smem = 0;
     uint64_t *qbuf = nullptr;   // device copy of host queries
     uint64_t qbuf_cap = 0;
     uint32_t *rbuf = nullptr;   // device copy of host radii
@@ -333,8 +339,8 @@ struct fclsh_qctx {
 
 static void ctx_free_buffers(fclsh_qctx *c)
 {
-    void *ps[] = {c->counters, c->runs, c->run_base, c->res_cnt, c->res_offs,
-                  c->res_ids, c->coll, c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf, c->qkeys};
+    void *ps[] = {c->counters, c->runs, c->run_base, c->res_cnt, c->res_offs, c->res_ids, c->coll,
+                  c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf, c->qkeys, c->heavy_q};
     for (void *p : ps)
         if (p) dev_free(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -370,15 +376,33 @@ static fclsh_status ctx_shape(fclsh_qctx *c)
     }
     c->block = block;
     c->smem = smem;
+    // the heavy-query kernel: windows of ids as large as shared memory allows (at most n, at
+    // least the 64 W bits that S1's transform buffer takes), or at most tu.heavy_kernel ids
+    c->win_bits = 0;
+    c->heavy_smem = 0;
+    if (tu.heavy_kernel) {
+        const size_t fixed = heavy_smem_bytes(idx->T, idx->words, 0) + 1024;   // + the kernel's static arrays
+        const uint64_t room = idx->smem_optin > fixed ? ((uint64_t)(idx->smem_optin - fixed) * 8) & ~63ULL : 0;
+        const uint64_t need = idx->classic_k ? 64 : 64ULL * idx->W;
+        uint64_t wb = std::min<uint64_t>(room, (idx->n + 63) & ~63ULL);
+        if (tu.heavy_kernel >= 64) wb = std::min<uint64_t>(wb, (uint64_t)tu.heavy_kernel & ~63ULL);
+        wb = std::max(wb, need);
+        if (wb <= room) {
+            c->heavy_smem = heavy_smem_bytes(idx->T, idx->words, (uint32_t)wb);
+            FCLSH_CUDA(query_heavy_prepare(c->heavy_smem));
+            c->win_bits = (uint32_t)wb;
+        }
+    }
     return FCLSH_OK;
 }
 
 static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
 {
     if (nq > c->nq_cap) {
-        void *ps[] = {c->res_cnt, c->res_offs, c->coll, c->cand, c->scan_part, c->run_base};
+        void *ps[] = {c->res_cnt, c->res_offs, c->coll, c->cand, c->scan_part, c->run_base, c->heavy_q};
         for (void *p : ps)
             if (p) dev_free(p);
+        c->heavy_q = nullptr;
         c->res_cnt = nullptr;
         c->res_offs = nullptr;
         c->coll = c->cand = nullptr;
@@ -392,6 +416,7 @@ static fclsh_status ctx_reserve(fclsh_qctx *c, uint64_t nq, uint64_t cap)
         FCLSH_CUDA(dev_alloc((void **)&c->coll, m * 8));
         FCLSH_CUDA(dev_alloc((void **)&c->cand, m * 8));
         FCLSH_CUDA(dev_alloc((void **)&c->scan_part, scan_partials_entries(m) * 8));
+        FCLSH_CUDA(dev_alloc((void **)&c->heavy_q, m * 8));
         c->nq_cap = m;
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
@@ -502,17 +527,32 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
     a.bitmaps = c->bitmaps;
     a.bm_words = (idx->n + 31) / 32;
     a.redo_cap = redo_cap;
+    if (c->win_bits) {
+        a.heavy_q = c->heavy_q;
+        a.heavy_n = c->counters + 2;
+        a.heavy_work = c->counters + 3;
+        a.win_bits = c->win_bits;
+    }
     if (idx->classic_k) {   // S1 of classic LSH: the queries' keys by the classic hash kernel
         const uint32_t L = idx->W - 1;
         for (uint32_t k = 0; k < idx->t; ++k)
             FCLSH_CUDA(launch_hash_part(idx, k, q, nq, c->qkeys + (uint64_t)k * L * nq, nq, s));
         a.qkeys = c->qkeys;
     }
-    FCLSH_CUDA(cudaMemsetAsync(c->counters, 0, (redo_cap ? 1 : 2) * sizeof(unsigned long long), s));
+    if (redo_cap) {   // the cursor keeps the first pass's total
+        FCLSH_CUDA(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long), s));
+        FCLSH_CUDA(cudaMemsetAsync(c->counters + 2, 0, 2 * sizeof(unsigned long long), s));
+    } else {
+        FCLSH_CUDA(cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), s));
+    }
     {
         PhaseTimer pt(idx, 2, s);
         const uint32_t grid = (uint32_t)std::min<uint64_t>(c->grid, std::max<uint64_t>(nq, 1));
         FCLSH_CUDA(launch_query_batch(a, grid, c->block, c->smem, s));
+        if (c->win_bits) {   // one block per SM (and no more blocks than there are CTA bitmaps)
+            PhaseTimer ph(idx, 8, s);
+            FCLSH_CUDA(launch_query_heavy(a, std::min<uint32_t>(c->grid, (uint32_t)idx->sm_count), c->heavy_smem, s));
+        }
     }
     {
         PhaseTimer pt(idx, 3, s);
@@ -694,9 +734,9 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         const fclsh_status st = index_shape(n, d, r, o, &t, &rep, &rp);
         if (st != FCLSH_OK) return st;
     }
-    // classic bit-sampling LSH (the baseline of Sec. 4.2): the covering index's table count
-    // (2^(r+1) - 1 per part, as Sec. 4.2 sets it) unless classic_tables says otherwise, in t
-    // chunks of W - 1 tables; k sampled coordinates per table by the rule of Sec. 4.2
+    // classic bit-sampling LSH (the baseline of Sec. 4.1): the covering index's table count
+    // (2^(r+1) - 1 per part, as Sec. 4.1 sets it) unless classic_tables says otherwise, in t
+    // chunks of W - 1 tables; k sampled coordinates per table by the rule of Sec. 4.1
     const bool classic = o.classic_k > 0 || o.classic_delta > 0.0;
     uint32_t Wc = 2u << rp, ck = 0;
     if (classic) {
@@ -735,7 +775,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     idx->W = W;
     idx->T = t * (W - 1);
     if (o.hash_tile > 4) return fail(FCLSH_EINVAL, "hash_tile must be 0..4");
-    idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0, 0};
+    idx->tune = fclsh_tuning{256, 4, 12, 4, 1, o.hash_tile, 0, 0, 1};
     idx->timing = o.timing != 0;
     idx->classic_k = ck;
     idx->classic_delta = o.classic_delta;
@@ -1188,7 +1228,7 @@ uint64_t fclsh::qctx_grow_bytes(const fclsh_qctx *c, uint64_t nq)
 {
     const fclsh_index *idx = c->idx;
     uint64_t b = 0;
-    if (nq > c->nq_cap) b += std::max<uint64_t>(nq, 1024) * (8 + 4 + 8 + 8 + 8 + 8) + 64;
+    if (nq > c->nq_cap) b += std::max<uint64_t>(nq, 1024) * (8 + 4 + 8 + 8 + 8 + 8 + 8) + 64;
     const uint64_t want = std::min<uint64_t>(nq * 512, 1ULL << 28);
     if (want > c->cap) b += want * 8;
     if (idx->classic_k && (uint64_t)idx->T * nq > c->qkeys_cap) b += (uint64_t)idx->T * nq * 8;
@@ -1203,7 +1243,7 @@ extern "C" fclsh_status fclsh_qctx_create(fclsh_index *idx, fclsh_qctx **out)
     fclsh_qctx *c = new fclsh_qctx();
     c->idx = idx;
     fclsh_status st = FCLSH_OK;
-    cudaError_t e = dev_alloc((void **)&c->counters, 2 * sizeof(unsigned long long));
+    cudaError_t e = dev_alloc((void **)&c->counters, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(counters)");
     if (st == FCLSH_OK && (e = cudaStreamCreate(&c->own)) != cudaSuccess)
         st = cuda_fail(e, "cudaStreamCreate");
@@ -1597,6 +1637,7 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     }
     if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
     if (t->verify_filter > 1) return fail(FCLSH_EINVAL, "verify_filter must be 0 or 1");
+    if (t->heavy_kernel > 1 && t->heavy_kernel < 64) return fail(FCLSH_EINVAL, "heavy_kernel must be 0, 1 or >= 64");
     if (idx->classic_k && (t->hash_tile || t->probe_rows))
         return fail(FCLSH_EINVAL, "a classic LSH index has one hash kernel and no row rule (hash_tile, probe_rows = 0)");
     if (idx->classic_k) {
@@ -1620,12 +1661,12 @@ extern "C" fclsh_status fclsh_timing_enable(fclsh_index *idx, int on)
     return FCLSH_OK;
 }
 
-extern "C" fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[8], uint64_t counts[8], int reset)
+extern "C" fclsh_status fclsh_timing_read(fclsh_index *idx, double ms[9], uint64_t counts[9], int reset)
 {
     if (!idx) return fail(FCLSH_EINVAL, "NULL argument");
     cudaSetDevice(idx->device);
     resolve_timers(idx);
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < kTimedPhases; ++i) {
         if (ms) ms[i] = idx->ms[i];
         if (counts) counts[i] = idx->cnt[i];
         if (reset) {
@@ -1843,7 +1884,8 @@ extern "C" fclsh_status fclsh_load(const char *path, fclsh_index **out)
         fclsh_free(idx);
         return fail(FCLSH_EINVAL, "%s: code length %u does not follow from its header", path, W);
     }
-    const fclsh_tuning tu{tune[0], tune[1], tune[2], tune[3], tune[4], tune[5], tune[6], idx->tune.verify_filter};
+    const fclsh_tuning tu{tune[0], tune[1], tune[2], tune[3], tune[4],
+                          tune[5], tune[6], idx->tune.verify_filter, idx->tune.heavy_kernel};
     if ((st = fclsh_set_tuning(idx, &tu)) != FCLSH_OK) {
         fclsh_free(idx);
         return st;
@@ -1946,6 +1988,7 @@ static bool cache_lookup(const char *path, const std::string &key, fclsh_tuning 
         !read_field(obj, "use_graph", &v.use_graph) || !read_field(obj, "hash_tile", &v.hash_tile) ||
         !read_field(obj, "verify_filter", &v.verify_filter))
         return false;
+    if (!read_field(obj, "heavy_kernel", &v.heavy_kernel)) v.heavy_kernel = 1;   // entries written before it
     *t = v;
     return true;
 }
@@ -1965,9 +2008,9 @@ static void cache_store(const char *path, const std::string &key, const fclsh_tu
     char ent[512];
     snprintf(ent, sizeof ent,
              "  \"%s\": {\"query_block\": %u, \"query_ctas_per_sm\": %u, \"hash_set_log2\": %u, \"inline_probe\": %u, "
-             "\"use_graph\": %u, \"hash_tile\": %u, \"verify_filter\": %u}",
+             "\"use_graph\": %u, \"hash_tile\": %u, \"verify_filter\": %u, \"heavy_kernel\": %u}",
              key.c_str(), t.query_block, t.query_ctas_per_sm, t.hash_set_log2, t.inline_probe, t.use_graph, t.hash_tile,
-             t.verify_filter);
+             t.verify_filter, t.heavy_kernel);
     lines.push_back(ent);
     std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
@@ -2018,7 +2061,8 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
             for (uint32_t il : inl)
                 for (uint32_t ct : ctas) {
                     if (st != FCLSH_OK) break;
-                    fclsh_tuning t{bk, ct, hl, il, 0, saved.hash_tile, saved.probe_rows, saved.verify_filter};
+                    fclsh_tuning t{bk, ct, hl, il, 0, saved.hash_tile, saved.probe_rows, saved.verify_filter,
+                                   saved.heavy_kernel};
                     if (query_smem_bytes(idx->T, idx->W, idx->words, hl) > idx->smem_optin) continue;
                     int occ = 0;
                     if (query_batch_occupancy(bk, query_smem_bytes(idx->T, idx->W, idx->words, hl), &occ) != cudaSuccess ||
@@ -2059,6 +2103,25 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
             cudaEventElapsedTime(&ms_f[vf], e0, e1);
         }
         if (ms_f[0] < 1e30f || ms_f[1] < 1e30f) best.verify_filter = ms_f[1] <= ms_f[0] ? 1u : 0u;
+        idx->tune = best;
+    }
+    // very heavy queries by the second kernel or by the batch kernel's own sweep
+    if (st == FCLSH_OK) {
+        float ms_h[2] = {1e30f, 1e30f};
+        for (uint32_t hk = 0; hk <= 1; ++hk) {
+            fclsh_tuning t = best;
+            t.use_graph = 0;
+            t.heavy_kernel = hk;
+            idx->tune = t;
+            if (fclsh_query_async(c, dq, nq, radius, nullptr, s) != FCLSH_OK || fclsh_qctx_wait(c, nullptr) != FCLSH_OK)
+                continue;
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 2; ++rep) fclsh_query_async(c, dq, nq, radius, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (fclsh_qctx_wait(c, nullptr) != FCLSH_OK) continue;
+            cudaEventElapsedTime(&ms_h[hk], e0, e1);
+        }
+        if (ms_h[0] < 1e30f || ms_h[1] < 1e30f) best.heavy_kernel = ms_h[1] <= ms_h[0] ? 1u : 0u;
         idx->tune = best;
     }
     // the hash kernel: WHT tiles and the tensor-core contraction on the index's first points

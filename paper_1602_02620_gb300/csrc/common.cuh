@@ -156,6 +156,12 @@ struct QueryArgs {
     uint32_t sig_block;
     // S1 done by a hash launch before the kernel (classic LSH): the queries' keys [T][nq]
     const uint64_t *qkeys;
+    // Very heavy queries handed from the batch kernel to query_heavy_kernel (heavy_q nullptr:
+    // the batch kernel sweeps them itself): heavy_q[0 .. *heavy_n) lists them, *heavy_work is
+    // the heavy kernel's next list position, win_bits the ids of one shared-memory window
+    uint64_t *heavy_q;
+    unsigned long long *heavy_n, *heavy_work;
+    uint32_t win_bits;
 };
 
 // A directory entry holds the key's high 50 - s bits above an ent_ib-bit id: 32 id bits
@@ -224,6 +230,9 @@ __device__ __forceinline__ uint32_t probed_table(uint32_t j, uint32_t nt, uint32
 }  // namespace fclsh
 
 // The index (opaque to users).
+// Phases timed by fclsh_timing_read (see include/fclsh.h).
+constexpr int kTimedPhases = 9;
+
 struct fclsh_index {
     int device = 0;
     uint64_t n = 0;
@@ -252,7 +261,7 @@ struct fclsh_index {
     uint32_t *mma_coord = nullptr;
     uint16_t *mma_g = nullptr;
     uint32_t *status = nullptr;      // [1] device word: bit 0 = a kernel's bounded wait ran out
-    // classic bit-sampling LSH (the baseline of Sec. 4.2) instead of covering LSH when classic_k > 0:
+    // classic bit-sampling LSH (the baseline of Sec. 4.1) instead of covering LSH when classic_k > 0:
     // T = t (W - 1) tables, table j keyed by Eq. 1 on classic_k sampled coordinates; per table the
     // distinct coordinates and their summed seed values cl_coord / cl_b [cl_off[j] .. cl_off[j+1])
     uint32_t classic_k = 0;
@@ -268,8 +277,8 @@ struct fclsh_index {
     fclsh_tuning tune{};
     // timing (CUDA events per phase)
     bool timing = false;
-    double ms[8] = {0};
-    uint64_t cnt[8] = {0};
+    double ms[kTimedPhases] = {0};
+    uint64_t cnt[kTimedPhases] = {0};
     int sm_count = 0;
     size_t smem_optin = 0;
 

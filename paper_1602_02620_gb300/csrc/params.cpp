@@ -199,7 +199,7 @@ void coord_lists(uint32_t d, uint32_t t, uint32_t W, const std::vector<uint32_t>
 // Classic LSH for Hamming space (Sec. 2.2): a hash function samples one coordinate, and
 // table j concatenates k of them, g_j = (x_{s_j(1)}, ..., x_{s_j(k)}), keyed by Eq. 1:
 // key_j(x) = (sum_i b_i x_{s_j(i)}) mod P with one seed vector b of k entries for every
-// table.  k follows the rule of Sec. 4.2, k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)),
+// table.  k follows the rule of Sec. 4.1, k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)),
 // which makes a point at distance r a false negative with probability about delta.
 uint32_t classic_rule_k(uint32_t L, uint32_t r, uint32_t d, double delta)
 {

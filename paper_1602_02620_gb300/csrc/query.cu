@@ -18,6 +18,10 @@
 // Hits collect in shared memory and are sorted there (up to 4,096 per query); a
 // query with more hits marks them in the bitmap and reads its ids out of it in
 // order.  Each query writes one sorted run; a gather kernel lays the runs out as CSR.
+// Very heavy queries (more bucket entries than the bitmap has words) can instead be
+// listed for a second kernel, one block of 32 warps per SM, that marks their entries in
+// a window of ids held in shared memory, window by window, so that no collision costs
+// an atomic on a bitmap in L2.
 #include "common.cuh"
 
 namespace fclsh {
@@ -102,8 +106,10 @@ struct Counters {
     uint32_t res = 0;
 };
 
-// Append the lanes' hits to the query's hit list in shared memory; warp-collective.
-__device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, uint32_t *res_s, uint32_t *s_nres)
+// Append the lanes' hits to the query's hit list in shared memory; warp-collective.  Hits past
+// the list's kResCap places are marked in ovf_bm when it is given (the heavy kernel's CTA bitmap).
+__device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, uint32_t *res_s, uint32_t *s_nres,
+                                            uint32_t *ovf_bm = nullptr)
 {
     const uint32_t m = __ballot_sync(0xffffffffu, hit);
     if (m) {
@@ -116,6 +122,7 @@ __device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, 
             c.res++;
             const uint32_t pos = base + __popc(m & lanemask_lt());
             if (pos < kResCap) res_s[pos] = id;
+            else if (ovf_bm) atomicOr(ovf_bm + (id >> 5), 1u << (id & 31));
         }
     }
 }
@@ -193,6 +200,10 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
 // atomics, and then verifies the chunk's new candidates together (S3).
 constexpr int kU = 4;
 constexpr uint32_t kCandCap = 512u * kU;   // new candidates of one chunk (blocks of up to 512 threads)
+constexpr uint32_t kHeavyThreads = 1024;    // query_heavy_kernel: one block of 32 warps per SM
+constexpr uint32_t kHeavyCand = 4096;       // its candidate lists (S3)
+// bucket entries of a query that query_heavy_kernel walks as one list (32-bit positions)
+constexpr unsigned long long kHeavyMaxEntries = 0xFFFFFFFFull - (unsigned long long)kHeavyThreads * kU;
 
 // The run holding list position pos: the last j < nruns with off[j] <= pos (off[0] = 0).
 __device__ __forceinline__ uint32_t run_of(const uint32_t *off, uint32_t nruns, uint32_t pos)
@@ -281,7 +292,7 @@ constexpr int kV = 4;
 template <int H>
 __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s,
                                               uint32_t m, uint32_t radius, uint64_t sq, const uint8_t *pcq,
-                                              Counters &c, uint32_t *res_s, uint32_t *s_nres)
+                                              Counters &c, uint32_t *res_s, uint32_t *s_nres, uint32_t *ovf_bm)
 {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t words = a.words, pieces = (words + 1) >> 1;   // 16-byte pieces of a point
@@ -329,7 +340,7 @@ __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t
             const bool lead = gl == 0 && i < m;
             if (lead) c.cand++;
             const bool hit = lead && ok[v] && part <= radius;
-            append_hits(hit, id[v], c, res_s, s_nres);
+            append_hits(hit, id[v], c, res_s, s_nres, ovf_bm);
         }
     }
 }
@@ -340,7 +351,7 @@ __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t
 // loaded before their popcounts are reduced in the group; longer points by the whole warp.
 __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s, uint32_t m,
                                             uint32_t radius, uint64_t sq, const uint8_t *pcq, Counters &c,
-                                            uint32_t *res_s, uint32_t *s_nres)
+                                            uint32_t *res_s, uint32_t *s_nres, uint32_t *ovf_bm = nullptr)
 {
     const uint32_t B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
     if (a.words >= kWarpVerifyWords) {   // a warp per candidate: coalesced reads of long points
@@ -353,14 +364,14 @@ __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *
                 if (lane == 0) c.cand++;
                 hit = sig_pass(a, id, sq, pcq, radius) && warp_distance(a, q_s, id, radius) <= radius;
             }
-            append_hits(hit && lane == 0, id, c, res_s, s_nres);
+            append_hits(hit && lane == 0, id, c, res_s, s_nres, ovf_bm);
         }
         return;
     }
     if (a.words <= 16)
-        verify_groups<1>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres);
+        verify_groups<1>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, ovf_bm);
     else
-        verify_groups<2>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres);
+        verify_groups<2>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, ovf_bm);
 }
 
 // Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
@@ -401,6 +412,148 @@ __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
         }
 }
 
+
+// The query into shared memory and, with the S3 pre-filter, its set coordinates per signature
+// block and its block-occupancy signature (read after the barriers of S1).  Block-wide.
+__device__ __forceinline__ void load_query(const QueryArgs &a, uint64_t qi, uint64_t *q_s, uint8_t *pcq, uint32_t *sigq)
+{
+    const uint32_t tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t w = tid; w < a.words; w += B) q_s[w] = a.queries[qi * a.words + w];
+    __syncthreads();
+    if (a.sig && tid < 64) {   // warps 0 and 1 (blocks have >= 128 threads)
+        const uint32_t lo = tid * a.sig_block;
+        const uint32_t pc = lo < a.d ? popc_range(q_s, lo, min(lo + a.sig_block, a.d)) : 0u;
+        pcq[tid] = (uint8_t)min(pc, 255u);
+        const uint32_t bal = __ballot_sync(0xffffffffu, pc > 0);
+        if (lane == 0) sigq[warp] = bal;
+    }
+}
+
+// S1: Algorithm 2 for every part in shared memory (tbuf: W words), or the keys a hash launch
+// computed before the kernel; keys_s[tau] for every table.  Block-wide, ends on a barrier.
+__device__ __forceinline__ void query_s1(const QueryArgs &a, uint64_t qi, const uint64_t *q_s, uint64_t *keys_s,
+                                         uint64_t *tbuf)
+{
+    const uint32_t tid = threadIdx.x, B = blockDim.x, L = a.W - 1;
+    if (a.qkeys) {
+        for (uint32_t tau = tid; tau < a.T; tau += B) keys_s[tau] = a.qkeys[(uint64_t)tau * a.nq + qi];
+        __syncthreads();
+    }
+    for (uint32_t k = 0; k < (a.qkeys ? 0u : a.t); ++k) {
+        if (a.s1_scatter) {
+            // sketch from the query's set bits: each adds its positions' seed values to
+            // their columns (64-bit sums, exact while a column holds <= 16,383 positions)
+            for (uint32_t j = tid; j < a.W; j += B) tbuf[j] = 0;
+            __syncthreads();
+            const uint32_t *off = a.sc_off + (size_t)k * (a.d + 1);
+            for (uint32_t w = tid; w < a.words; w += B) {
+                uint64_t bits = q_s[w];
+                if (w == a.words - 1 && (a.d & 63)) bits &= (1ULL << (a.d & 63)) - 1;
+                while (bits) {
+                    const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
+                    bits &= bits - 1;
+                    for (uint32_t e = off[c]; e < off[c + 1]; ++e)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(tbuf + a.sc_col[e]),
+                                  (unsigned long long)a.sc_b[e]);
+                }
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < a.W; j += B) tbuf[j] = mod_p(tbuf[j]);
+        } else {
+            const uint32_t *co = a.col_off + (size_t)k * (a.W + 1);
+            for (uint32_t j = tid; j < a.W; j += B) {
+                uint64_t s = 0;
+                const uint32_t e1 = co[j + 1];
+                for (uint32_t e = co[j]; e < e1; ++e) {
+                    const uint32_t bit = a.col_coord[e];
+                    const uint64_t take = 0ULL - ((q_s[bit >> 6] >> (bit & 63)) & 1ULL);
+                    s = add_mod_p(s, a.col_b[e] & take);
+                }
+                tbuf[j] = s;
+            }
+        }
+        __syncthreads();
+        for (uint32_t h = 1; h < a.W; h <<= 1) {
+            for (uint32_t i = tid; i < a.W / 2; i += B) {
+                const uint32_t j = ((i & ~(h - 1)) << 1) | (i & (h - 1));
+                const uint64_t x = tbuf[j], y = tbuf[j + h];
+                tbuf[j] = x + y;
+                tbuf[j + h] = x - y;
+            }
+            __syncthreads();
+        }
+        const uint64_t S = tbuf[0];   // y_0 = sum_j t_j
+        for (uint32_t v = tid + 1; v < a.W; v += B) keys_s[k * L + v - 1] = finish_key(S, tbuf[v]);
+        __syncthreads();
+    }
+}
+
+// S2a: the bucket range of every probed table (lo_s, len_s), the probed tables' count Tq
+// (nt code rows per part) and the query's bucket entries E summed over them.  Block-wide.
+__device__ __forceinline__ unsigned long long probe_ranges(const QueryArgs &a, uint32_t radius, const uint64_t *keys_s,
+                                                           uint32_t *lo_s, uint32_t *len_s, unsigned long long *red64,
+                                                           uint32_t &nt, uint32_t &Tq)
+{
+    const uint32_t tid = threadIdx.x, B = blockDim.x, L = a.W - 1;
+    const uint64_t smask = (1ULL << a.slot_bits) - 1;
+    nt = rows_per_part(a, radius);
+    Tq = a.t * nt;
+    unsigned long long local = 0;
+    for (uint32_t j = tid; j < Tq; j += B) {
+        const uint32_t tau = probed_table(j, nt, L);
+        if (!FCLSH_CHECK(tau < a.T, 0x0106)) {
+            lo_s[j] = len_s[j] = 0;
+            continue;
+        }
+        const uint64_t key = keys_s[tau];
+        const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
+        const uint32_t lo = O[0], hi = O[1];
+        lo_s[j] = lo;
+        len_s[j] = hi - lo;
+        local += hi - lo;
+    }
+    return block_sum(local, red64);
+}
+
+// len_s[0..Tq) -> its exclusive prefix, in place (the runs as one list).  Block-wide.
+__device__ __forceinline__ void runs_prefix(uint32_t *len_s, uint32_t Tq, unsigned long long *red64)
+{
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint32_t per = (Tq + B - 1) / B, j0 = tid * per, j1 = min(j0 + per, Tq);
+    uint32_t mine = 0;
+    for (uint32_t j = j0; j < j1; ++j) mine += len_s[j];
+    uint32_t run = (uint32_t)block_excl_scan_u32(mine, red64);
+    for (uint32_t j = j0; j < j1; ++j) {
+        const uint32_t len = len_s[j];
+        len_s[j] = run;
+        run += len;
+    }
+}
+
+// The ids marked in the CTA's n-bit bitmap, in ascending order, to runs[base ..] (within the
+// buffer's cap); the bitmap is left all-zero.  Block-wide.
+__device__ __forceinline__ void bitmap_readout(const QueryArgs &a, uint32_t *bm, unsigned long long base,
+                                               unsigned long long *red64)
+{
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    const uint64_t per = (a.bm_words + B - 1) / B;
+    const uint64_t w0 = (uint64_t)tid * per, w1 = min(w0 + per, a.bm_words);
+    uint32_t mine = 0;
+    for (uint64_t w = w0; w < w1; ++w) mine += __popc(__ldcg(bm + w));   // marks are made in L2
+    const uint32_t before = (uint32_t)block_excl_scan_u32(mine, red64);
+    unsigned long long pos = base + before;
+    for (uint64_t w = w0; w < w1; ++w) {
+        uint32_t bits = __ldcg(bm + w);
+        while (bits) {
+            const uint32_t b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (pos < a.cap) a.runs[pos] = (uint32_t)(w * 32 + b);
+            ++pos;
+        }
+        bm[w] = 0;
+    }
+}
+
 }  // namespace
 
 // Dynamic shared memory of the batched kernel.
@@ -431,7 +584,6 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
     const uint32_t tid = threadIdx.x, B = blockDim.x;
     const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
     const uint32_t L = a.W - 1;
-    const uint64_t smask = (1ULL << a.slot_bits) - 1;
     uint32_t *bm = a.bitmaps + (uint64_t)blockIdx.x * a.bm_words;
     const uint32_t hcap = 1u << a.hset_log2;
 
@@ -444,92 +596,20 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
             __syncthreads();
             continue;
         }
-        for (uint32_t w = tid; w < a.words; w += B) q_s[w] = a.queries[qi * a.words + w];
         const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
-        __syncthreads();
-        if (a.sig && tid < 64) {   // warps 0 and 1 (blocks have >= 128 threads); read after S1's barriers
-            const uint32_t lo = tid * a.sig_block;
-            const uint32_t pc = lo < a.d ? popc_range(q_s, lo, min(lo + a.sig_block, a.d)) : 0u;
-            s_pcq[tid] = (uint8_t)min(pc, 255u);
-            const uint32_t bal = __ballot_sync(0xffffffffu, pc > 0);
-            if (lane == 0) s_sigq[warp] = bal;
-        }
-
-        // ---- S1: Algorithm 2 for every part, in shared memory (or the keys a hash launch
-        // computed before the kernel)
-        if (a.qkeys) {
-            for (uint32_t tau = tid; tau < a.T; tau += B) keys_s[tau] = a.qkeys[(uint64_t)tau * a.nq + qi];
-            __syncthreads();
-        }
-        for (uint32_t k = 0; k < (a.qkeys ? 0u : a.t); ++k) {
-            if (a.s1_scatter) {
-                // sketch from the query's set bits: each adds its positions' seed values to
-                // their columns (64-bit sums, exact while a column holds <= 16,383 positions)
-                for (uint32_t j = tid; j < a.W; j += B) tbuf[j] = 0;
-                __syncthreads();
-                const uint32_t *off = a.sc_off + (size_t)k * (a.d + 1);
-                for (uint32_t w = tid; w < a.words; w += B) {
-                    uint64_t bits = q_s[w];
-                    if (w == a.words - 1 && (a.d & 63)) bits &= (1ULL << (a.d & 63)) - 1;
-                    while (bits) {
-                        const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
-                        bits &= bits - 1;
-                        for (uint32_t e = off[c]; e < off[c + 1]; ++e)
-                            atomicAdd(reinterpret_cast<unsigned long long *>(tbuf + a.sc_col[e]),
-                                      (unsigned long long)a.sc_b[e]);
-                    }
-                }
-                __syncthreads();
-                for (uint32_t j = tid; j < a.W; j += B) tbuf[j] = mod_p(tbuf[j]);
-            } else {
-                const uint32_t *co = a.col_off + (size_t)k * (a.W + 1);
-                for (uint32_t j = tid; j < a.W; j += B) {
-                    uint64_t s = 0;
-                    const uint32_t e1 = co[j + 1];
-                    for (uint32_t e = co[j]; e < e1; ++e) {
-                        const uint32_t bit = a.col_coord[e];
-                        const uint64_t take = 0ULL - ((q_s[bit >> 6] >> (bit & 63)) & 1ULL);
-                        s = add_mod_p(s, a.col_b[e] & take);
-                    }
-                    tbuf[j] = s;
-                }
-            }
-            __syncthreads();
-            for (uint32_t h = 1; h < a.W; h <<= 1) {
-                for (uint32_t i = tid; i < a.W / 2; i += B) {
-                    const uint32_t j = ((i & ~(h - 1)) << 1) | (i & (h - 1));
-                    const uint64_t x = tbuf[j], y = tbuf[j + h];
-                    tbuf[j] = x + y;
-                    tbuf[j + h] = x - y;
-                }
-                __syncthreads();
-            }
-            const uint64_t S = tbuf[0];   // y_0 = sum_j t_j
-            for (uint32_t v = tid + 1; v < a.W; v += B) keys_s[k * L + v - 1] = finish_key(S, tbuf[v]);
-            __syncthreads();
-        }
-
-        // ---- S2a: bucket ranges of every probed table
-        const uint32_t nt = rows_per_part(a, radius), Tq = a.t * nt;
-        unsigned long long local = 0;
-        for (uint32_t j = tid; j < Tq; j += B) {
-            const uint32_t tau = probed_table(j, nt, L);
-            if (!FCLSH_CHECK(tau < a.T, 0x0106)) {
-                lo_s[j] = len_s[j] = 0;
-                continue;
-            }
-            const uint64_t key = keys_s[tau];
-            const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
-            const uint32_t lo = O[0], hi = O[1];
-            lo_s[j] = lo;
-            len_s[j] = hi - lo;
-            local += hi - lo;
-        }
-        const unsigned long long E = block_sum(local, red64);
+        load_query(a, qi, q_s, s_pcq, s_sigq);
+        query_s1(a, qi, q_s, keys_s, tbuf);
+        uint32_t nt, Tq;
+        const unsigned long long E = probe_ranges(a, radius, keys_s, lo_s, len_s, red64, nt, Tq);
         const bool bitmap_mode = E > (hcap >> 1);
         // more bucket entries than bitmap words: mark the bitmap and sweep it once
         const bool sweep_mode = bitmap_mode && E > a.bm_words;
         const int mode = sweep_mode ? DEDUP_MARK : (bitmap_mode ? DEDUP_BITMAP : DEDUP_HSET);
+        if (sweep_mode && a.heavy_q && E <= kHeavyMaxEntries) {   // block-uniform: query_heavy_kernel answers it
+            if (tid == 0) a.heavy_q[atomicAdd(a.heavy_n, 1ULL)] = qi;
+            __syncthreads();
+            continue;
+        }
         // the bucket entries as one list (positions in 32 bits) for the hash-set and bitmap
         // modes; the marking of a very heavy query, and a query of 2^32 entries or more, walk
         // their runs lane by lane instead (measured faster for the marking, whose work is the
@@ -537,17 +617,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
         const bool listed = !sweep_mode && E <= 0xFFFFFFFFull - (unsigned long long)B * kU;
         const uint32_t E32 = listed ? (uint32_t)E : 0u;
         uint32_t *off_s = len_s;   // len_s becomes the runs' exclusive prefix
-        if (listed) {
-            const uint32_t per = (Tq + B - 1) / B, j0 = tid * per, j1 = min(j0 + per, Tq);
-            uint32_t mine = 0;
-            for (uint32_t j = j0; j < j1; ++j) mine += len_s[j];
-            uint32_t run = (uint32_t)block_excl_scan_u32(mine, red64);
-            for (uint32_t j = j0; j < j1; ++j) {
-                const uint32_t len = len_s[j];
-                off_s[j] = run;
-                run += len;
-            }
-        }
+        if (listed) runs_prefix(len_s, Tq, red64);
         if (!bitmap_mode)
             for (uint32_t i = tid; i < hcap; i += B) hset[i] = kEmpty;
         if (tid == 0) {
@@ -727,23 +797,142 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
             }
             if (tid == 0) s_base = a.redo_cap ? a.run_base[qi] : atomicAdd(a.cursor, (unsigned long long)nres);
             __syncthreads();
-            const unsigned long long base = s_base;
-            const uint64_t per = (a.bm_words + B - 1) / B;
-            const uint64_t w0 = (uint64_t)tid * per, w1 = min(w0 + per, a.bm_words);
-            uint32_t mine = 0;
-            for (uint64_t w = w0; w < w1; ++w) mine += __popc(__ldcg(bm + w));   // marks are made in L2
-            const uint32_t before = (uint32_t)block_excl_scan_u32(mine, red64);
-            unsigned long long pos = base + before;
-            for (uint64_t w = w0; w < w1; ++w) {
-                uint32_t bits = __ldcg(bm + w);
-                while (bits) {
-                    const uint32_t b = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    if (pos < a.cap) a.runs[pos] = (uint32_t)(w * 32 + b);
-                    ++pos;
+            bitmap_readout(a, bm, s_base, red64);
+        }
+        if (tid == 0) {
+            a.coll[qi] = tc;
+            a.cand[qi] = td;
+            a.res_cnt[qi] = nres;
+            a.run_base[qi] = s_base;
+        }
+        __syncthreads();
+    }
+}
+
+// Dynamic shared memory of query_heavy_kernel with windows of win_bits ids: the keys, the
+// bucket ranges and their prefix, the query, the hit list, the candidate list and the window
+// (which also serves S1 as its W-word transform buffer).
+size_t heavy_smem_bytes(uint32_t T, uint32_t words, uint32_t win_bits)
+{
+    return (size_t)T * 16 + (size_t)words * 8 + (size_t)(kResCap + kHeavyCand) * 4 + (size_t)win_bits / 8;
+}
+
+// Very heavy queries -- more bucket entries than the CTA's n-bit bitmap has words, which
+// query_batch_kernel lists in heavy_q -- answered by one block of 32 warps per SM, taking the
+// listed queries in turn.  S1 and the probes as in the batch kernel.  The duplicate
+// elimination of S2 marks the query's bucket entries in a bitmap window held in shared memory,
+// one window of win_bits ids after another (each window walks the bucket entries again: a
+// shared-memory atomic per collision in place of one on a bitmap in L2); #Collisions is counted
+// on the first window.  S3 then takes the window's marked ids -- its distinct candidates -- in
+// ascending order, in lists of kHeavyCand verified block-wide.  Hits collect in shared memory
+// and are sorted there; a query with more than kResCap hits also marks the rest in the CTA's
+// bitmap in global memory and reads its ids out of it in order, leaving it all-zero.
+__global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *keys_s = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *lo_s = reinterpret_cast<uint32_t *>(keys_s + a.T);
+    uint32_t *off_s = lo_s + a.T;                                   // run lengths, then their prefix
+    uint64_t *q_s = reinterpret_cast<uint64_t *>(off_s + a.T);      // 16T bytes in: 8-aligned
+    uint32_t *res_s = reinterpret_cast<uint32_t *>(q_s + a.words);
+    uint32_t *cand_s = res_s + kResCap;
+    uint64_t *win = reinterpret_cast<uint64_t *>(cand_s + kHeavyCand);   // 8-aligned (kResCap + kHeavyCand even)
+    uint32_t *win32 = reinterpret_cast<uint32_t *>(win);
+    __shared__ unsigned long long s_h, s_base;
+    __shared__ uint32_t s_nres, s_total;
+    __shared__ unsigned long long red64[32];
+    __shared__ uint8_t s_pcq[64];
+    __shared__ __align__(8) uint32_t s_sigq[2];
+
+    const uint32_t tid = threadIdx.x, B = blockDim.x, L = a.W - 1;
+    uint32_t *bm = a.bitmaps + (uint64_t)blockIdx.x * a.bm_words;
+    const unsigned long long nheavy = *a.heavy_n;   // final: written by the batch kernel before this launch
+
+    for (;;) {
+        if (tid == 0) s_h = atomicAdd(a.heavy_work, 1ULL);
+        __syncthreads();
+        const unsigned long long h = s_h;
+        if (h >= nheavy) break;
+        const uint64_t qi = a.heavy_q[h];
+        if (!FCLSH_CHECK(qi < a.nq, 0x0110)) break;   // block-uniform
+        const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
+        load_query(a, qi, q_s, s_pcq, s_sigq);
+        query_s1(a, qi, q_s, keys_s, win);
+        uint32_t nt, Tq;
+        const unsigned long long E = probe_ranges(a, radius, keys_s, lo_s, off_s, red64, nt, Tq);
+        const uint32_t E32 = (uint32_t)min(E, kHeavyMaxEntries);   // the batch kernel lists only E <= the limit
+        runs_prefix(off_s, Tq, red64);
+        if (tid == 0) s_nres = 0;
+        __syncthreads();
+        const uint64_t sq = a.sig ? ((uint64_t)s_sigq[1] << 32 | s_sigq[0]) : 0;
+        Counters c;
+
+        for (uint64_t w_lo = 0; w_lo < a.n; w_lo += a.win_bits) {
+            const uint64_t nbits = min((uint64_t)a.win_bits, a.n - w_lo);
+            const uint32_t nw = (uint32_t)((nbits + 63) >> 6);
+            for (uint32_t i = tid; i < nw; i += B) win[i] = 0;
+            __syncthreads();
+            // S2: mark the window's ids among the collisions (shared-memory reductions)
+            for (uint32_t base = 0; base < E32; base += B * kU) {
+                Chunk ch;
+                load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const uint32_t id = entry_id(ch.en[k], a.ent_ib);
+                    const bool coll = ch.tau[k] != 0xFFFFFFFFu &&
+                                      entry_fp(ch.en[k], a.ent_ib) == (keys_s[ch.tau[k]] >> a.slot_bits) &&
+                                      FCLSH_CHECK(id < a.n, 0x0111);
+                    if (!coll) continue;
+                    if (w_lo == 0) c.coll++;
+                    const uint64_t rel = (uint64_t)id - w_lo;   // wraps past the window for id < w_lo
+                    if (rel < nbits) atomicOr(win32 + (rel >> 5), 1u << (rel & 31));
                 }
-                bm[w] = 0;
             }
+            __syncthreads();
+            // S3: the window's marked ids in rounds of B words, listed in ascending order in
+            // pieces of kHeavyCand (a thread places the ids of its word whose rank falls in the piece)
+            for (uint32_t r0 = 0; r0 < nw; r0 += B) {
+                const uint32_t w = r0 + tid;
+                const uint64_t bits = w < nw ? win[w] : 0ULL;
+                const uint32_t cnt = (uint32_t)__popcll(bits);
+                const uint32_t before = (uint32_t)block_excl_scan_u32(cnt, red64);
+                if (tid == B - 1) s_total = before + cnt;
+                __syncthreads();
+                const uint32_t total = s_total;
+                for (uint32_t s0 = 0; s0 < total; s0 += kHeavyCand) {
+                    if (cnt && before < s0 + kHeavyCand && before + cnt > s0) {
+                        uint64_t rem = bits;
+                        for (uint32_t rank = before; rem; ++rank) {
+                            const uint32_t b = (uint32_t)(__ffsll((long long)rem) - 1);
+                            rem &= rem - 1;
+                            if (rank >= s0 && rank - s0 < kHeavyCand)
+                                cand_s[rank - s0] = (uint32_t)(w_lo + (uint64_t)w * 64 + b);
+                        }
+                    }
+                    __syncthreads();
+                    verify_list(a, q_s, cand_s, min(kHeavyCand, total - s0), radius, sq, s_pcq, c, res_s, &s_nres, bm);
+                    __syncthreads();
+                }
+            }
+        }
+        const unsigned long long tc = block_sum(c.coll, red64);
+        const unsigned long long td = block_sum(c.cand, red64);
+        const uint32_t nres = s_nres;   // read after block_sum's barriers
+        if (nres <= kResCap) {
+            block_sort_u32(res_s, nres);
+            if (tid == 0) s_base = a.redo_cap ? a.run_base[qi] : atomicAdd(a.cursor, (unsigned long long)nres);
+            __syncthreads();
+            const unsigned long long base = s_base;
+            for (uint32_t i = tid; i < nres; i += B)
+                if (base + i < a.cap) a.runs[base + i] = res_s[i];
+        } else {
+            // the first kResCap hits are listed, the rest marked: mark the listed ones too and
+            // read every hit out of the bitmap in order
+            for (uint32_t i = tid; i < kResCap; i += B) atomicOr(bm + (res_s[i] >> 5), 1u << (res_s[i] & 31));
+            __threadfence_block();
+            if (tid == 0) s_base = a.redo_cap ? a.run_base[qi] : atomicAdd(a.cursor, (unsigned long long)nres);
+            __syncthreads();
+            bitmap_readout(a, bm, s_base, red64);
         }
         if (tid == 0) {
             a.coll[qi] = tc;
@@ -923,6 +1112,19 @@ cudaError_t query_batch_occupancy(uint32_t block, size_t smem, int *ctas_per_sm)
         if (e != cudaSuccess) return e;
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, query_batch_kernel, (int)block, smem);
+}
+
+// Raises query_heavy_kernel's shared-memory limit to smem; outside any stream capture.
+cudaError_t query_heavy_prepare(size_t smem)
+{
+    return cudaFuncSetAttribute(query_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_query_heavy(const QueryArgs &a, uint32_t grid, size_t smem, cudaStream_t s)
+{
+    query_heavy_kernel<<<grid, kHeavyThreads, smem, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_query_plain(const QueryArgs &a, const uint64_t *keys, uint32_t *bitmap, cudaStream_t s)

@@ -56,7 +56,8 @@ class DeviceResult(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("query_block", ctypes.c_uint32), ("query_ctas_per_sm", ctypes.c_uint32),
                 ("hash_set_log2", ctypes.c_uint32), ("inline_probe", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
-                ("hash_tile", ctypes.c_uint32), ("probe_rows", ctypes.c_uint32), ("verify_filter", ctypes.c_uint32)]
+                ("hash_tile", ctypes.c_uint32), ("probe_rows", ctypes.c_uint32), ("verify_filter", ctypes.c_uint32),
+                ("heavy_kernel", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -356,11 +357,11 @@ class Index:
         _check(lib().fclsh_timing_enable(self.handle, 1 if on else 0))
 
     def timing_read(self, reset: bool = False):
-        ms = (ctypes.c_double * 8)()
-        cnt = (ctypes.c_uint64 * 8)()
+        ms = (ctypes.c_double * 9)()
+        cnt = (ctypes.c_uint64 * 9)()
         _check(lib().fclsh_timing_read(self.handle, ms, cnt, 1 if reset else 0))
         names = ["build_hash", "build_sort", "query_kernel", "query_csr", "hash", "build_partition", "build_finish",
-                 "build_partition_hist"]
+                 "build_partition_hist", "query_heavy"]
         return {nm: (float(ms[i]), int(cnt[i])) for i, nm in enumerate(names)}
 
     def free(self):
@@ -428,7 +429,7 @@ def build(points, d: int, r: int, seed: int, t: int | None = None, slot_bits: in
     with neither t nor replicate set chooses both by Algorithm 1.
     classic_k > 0 or classic_delta > 0 builds classic bit-sampling LSH instead (the paper's
     baseline with false negatives): classic_tables tables (0 = the covering table count) of
-    classic_k sampled coordinates (0 = the rule of Sec. 4.2 for classic_delta)."""
+    classic_k sampled coordinates (0 = the rule of Sec. 4.1 for classic_delta)."""
     keep = []
     o = _build_opts(t=t, slot_bits=slot_bits, mem_budget=mem_budget, perm=perm, part_off=part_off, m=m, b=b,
                     timing=timing, hash_tile=hash_tile, replicate=replicate, approx_c=approx_c, keep=keep,

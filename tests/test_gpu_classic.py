@@ -1,4 +1,4 @@
-"""Classic bit-sampling LSH on the GPU (Sec. 2.2; the baseline of Sec. 4.2) against the
+"""Classic bit-sampling LSH on the GPU (Sec. 2.2; the baseline of Sec. 4.1) against the
 classic oracle: its samples and seed vector, the keys the build stored in every table, and
 every query's ids and #Collisions / #Candidates through the batched and plain paths.  The
 index has false negatives (recall below 1 at distance r, about delta), which covering LSH

@@ -348,11 +348,13 @@ def test_autotune_choices_keep_results(tmp_path):
     idx.free()
 
 
-@pytest.mark.parametrize("hlog", [10, 13])
-def test_dedup_modes_match_oracle(hlog):
+@pytest.mark.parametrize("hlog,heavy", [(10, 0), (13, 0), (10, 1), (13, 1024)])
+def test_dedup_modes_match_oracle(hlog, heavy):
     """Queries in every dedup mode -- shared-memory set, returning bitmap, mark-and-sweep
     bitmap (bucket entries beyond the bitmap's word count), and more than 4,096 hits --
-    report the oracle's ids and counters."""
+    report the oracle's ids and counters.  The very heavy queries are answered by the batch
+    kernel's own sweep (heavy = 0) or by the heavy-query kernel, in one shared-memory window
+    of ids (1) or in nine windows of 1,024 ids with a ragged last one (1024 = 64 W)."""
     rng = np.random.default_rng(hlog)
     d, r, n = 64, 3, 9000
     pts = rand_points(rng, n, d)
@@ -367,7 +369,8 @@ def test_dedup_modes_match_oracle(hlog):
     qs = np.concatenate([pts[[17, 23, 29, 5, 7000]], near(rng, pts, d, r, 40), rand_points(rng, 5, d)])
     qs[5:15] = pts[17]
     idx = F().build(dev(pts), d, r, seed)
-    idx.set_tuning(hash_set_log2=hlog)
+    assert idx.tuning()["heavy_kernel"] == 1                  # on by default
+    idx.set_tuning(hash_set_log2=hlog, heavy_kernel=heavy)
     res = idx.query(dev(qs), r)
     for i in range(qs.shape[0]):
         ids, ncoll, ncand = oracle.query(p, pts, tables, qs[i], r)
@@ -515,10 +518,10 @@ def test_signature_filter_keeps_ids_and_counters(d, r, n, density):
     for radius in (r, r // 2):
         want = [oracle.query(p, pts, tables, q, radius) for q in qs]
         assert sum(len(w[0]) for w in want) > 0
-        for vf in (1, 0):
-            idx.set_tuning(verify_filter=vf)
+        for vf, hk in ((1, 1), (0, 1), (1, 0)):
+            idx.set_tuning(verify_filter=vf, heavy_kernel=hk)
             for res in (idx.query(dev(qs), radius), idx.query_plain(qs, radius)):
                 for i, (ids, ncoll, ncand) in enumerate(want):
-                    assert np.array_equal(res.of(i), ids), (vf, radius, i)
-                    assert int(res.collisions[i]) == ncoll and int(res.candidates[i]) == ncand, (vf, radius, i)
+                    assert np.array_equal(res.of(i), ids), (vf, hk, radius, i)
+                    assert int(res.collisions[i]) == ncoll and int(res.candidates[i]) == ncand, (vf, hk, radius, i)
     idx.free()

@@ -647,7 +647,7 @@ def test_classic_collision_probability_is_sampling_with_replacement():
 
 
 def test_classic_rule_k_is_the_smallest_k_reaching_the_false_negative_ratio():
-    """k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)) (Sec. 4.2): a point at distance r escapes
+    """k = ceil(log(1 - delta^(1/L)) / log(1 - r/d)) (Sec. 4.1): a point at distance r escapes
     all L tables with probability (1 - (1 - r/d)^k)^L, which first reaches delta at this k."""
     for L in (15, 127, 511, 4094):
         for r, d in ((3, 64), (8, 128), (20, 1024), (6, 64)):
