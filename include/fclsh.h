@@ -164,8 +164,9 @@ typedef struct {
                                  marking their bucket entries in a window of ids held in shared memory,
                                  one window after another, as large as shared memory allows; k >= 64 =
                                  the same with windows of at most k ids (rounded down to a multiple of 64;
-                                 never below 64*W).  Same ids and counters.  Default 1; timed by
-                                 fclsh_autotune. */
+                                 never below 64*W) and lists of 4 windows' ids for the collisions past
+                                 the first window (past that, later windows walk the buckets again).
+                                 Same ids and counters.  Default 1; timed by fclsh_autotune. */
 } fclsh_tuning;
 
 /* ------------------------------------------------------------------ index */

@@ -27,6 +27,7 @@ size_t query_smem_bytes(uint32_t T, uint32_t W, uint32_t words, uint32_t hset_lo
 cudaError_t launch_query_batch(const QueryArgs &a, uint32_t grid, uint32_t block, size_t smem, cudaStream_t s);
 cudaError_t query_batch_occupancy(uint32_t block, size_t smem, int *ctas_per_sm);
 size_t heavy_smem_bytes(uint32_t T, uint32_t words, uint32_t win_bits);
+constexpr uint32_t kHeavySpillCap = 1u << 20;   // ids per heavy block's spill list (4 MB)
 cudaError_t query_heavy_prepare(size_t smem);
 cudaError_t launch_query_heavy(const QueryArgs &a, uint32_t grid, size_t smem, cudaStream_t s);
 cudaError_t launch_query_plain(const QueryArgs &a, const uint64_t *keys, uint32_t *bitmap, cudaStream_t s);
@@ -310,6 +311,8 @@ struct fclsh_qctx {
     uint64_t *heavy_q = nullptr;   // [nq_cap] the batch's very heavy queries, for query_heavy_kernel
     uint32_t win_bits = 0;         // its window of ids (0: the batch kernel sweeps heavy queries itself)
     size_t heavy_smem = 0;
+    uint32_t *spill = nullptr;     // [heavy blocks][spill_cap]: ids of the windows after the first
+    uint32_t spill_cap = 0;
     uint64_t *qbuf = nullptr;   // device copy of host queries
     uint64_t qbuf_cap = 0;
     uint32_t *rbuf = nullptr;   // device copy of host radii
@@ -340,7 +343,7 @@ struct fclsh_qctx {
 static void ctx_free_buffers(fclsh_qctx *c)
 {
     void *ps[] = {c->counters, c->runs, c->run_base, c->res_cnt, c->res_offs, c->res_ids, c->coll,
-                  c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf, c->qkeys, c->heavy_q};
+                  c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf, c->qkeys, c->heavy_q, c->spill};
     for (void *p : ps)
         if (p) dev_free(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -381,7 +384,7 @@ static fclsh_status ctx_shape(fclsh_qctx *c)
     c->win_bits = 0;
     c->heavy_smem = 0;
     if (tu.heavy_kernel) {
-        const size_t fixed = heavy_smem_bytes(idx->T, idx->words, 0) + 1024;   // + the kernel's static arrays
+        const size_t fixed = heavy_smem_bytes(idx->T, idx->words, 0) + 4096;   // + the kernel's static arrays
         const uint64_t room = idx->smem_optin > fixed ? ((uint64_t)(idx->smem_optin - fixed) * 8) & ~63ULL : 0;
         const uint64_t need = idx->classic_k ? 64 : 64ULL * idx->W;
         uint64_t wb = std::min<uint64_t>(room, (idx->n + 63) & ~63ULL);
@@ -391,6 +394,25 @@ static fclsh_status ctx_shape(fclsh_qctx *c)
             c->heavy_smem = heavy_smem_bytes(idx->T, idx->words, (uint32_t)wb);
             FCLSH_CUDA(query_heavy_prepare(c->heavy_smem));
             c->win_bits = (uint32_t)wb;
+        }
+    }
+    // several windows: the spill lists of the heavy kernel's blocks (a query whose collisions
+    // past the first window overflow its list walks the bucket entries again)
+    uint32_t want_cap = c->win_bits && c->win_bits < idx->n ? kHeavySpillCap : 0;
+    if (want_cap && tu.heavy_kernel >= 64) want_cap = std::min<uint32_t>(want_cap, 4 * (c->win_bits / 64) * 64);
+    if (want_cap != c->spill_cap) {
+        if (c->spill) dev_free(c->spill);
+        c->spill = nullptr;
+        c->spill_cap = 0;
+        if (c->gexec) {   // a captured batch refers to the old lists
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        c->g_seen = false;
+        if (want_cap) {
+            const uint64_t blocks = std::min<uint32_t>(c->grid, (uint32_t)idx->sm_count);
+            FCLSH_CUDA(dev_alloc((void **)&c->spill, blocks * want_cap * 4));
+            c->spill_cap = want_cap;
         }
     }
     return FCLSH_OK;
@@ -532,6 +554,8 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
         a.heavy_n = c->counters + 2;
         a.heavy_work = c->counters + 3;
         a.win_bits = c->win_bits;
+        a.spill = c->spill;
+        a.spill_cap = c->spill_cap;
     }
     if (idx->classic_k) {   // S1 of classic LSH: the queries' keys by the classic hash kernel
         const uint32_t L = idx->W - 1;

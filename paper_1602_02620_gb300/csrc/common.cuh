@@ -162,6 +162,8 @@ struct QueryArgs {
     uint64_t *heavy_q;
     unsigned long long *heavy_n, *heavy_work;
     uint32_t win_bits;
+    uint32_t *spill;      // [gridDim.x][spill_cap]: the heavy kernel's ids of later windows
+    uint32_t spill_cap;
 };
 
 // A directory entry holds the key's high 50 - s bits above an ent_ib-bit id: 32 id bits
@@ -178,6 +180,9 @@ __device__ __forceinline__ uint32_t entry_id(uint64_t en, uint32_t ib)
 
 #if defined(__CUDACC__)   // device intrinsics: CUDA translation units only
 // Set coordinates of the packed vector x in [lo, hi) (lo < hi).
+// Occupancy levels of a query kept for S3's pre-filter (sig_bound).
+constexpr int kSigLevels = 8;
+
 __device__ __forceinline__ uint32_t popc_range(const uint64_t *x, uint32_t lo, uint32_t hi)
 {
     const uint32_t w0 = lo >> 6, w1 = (hi - 1) >> 6;
@@ -193,14 +198,17 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t *x, uint32_t lo, u
 
 // Lower bound on the Hamming distance of x and q from their block-occupancy signatures:
 // every block where only x has set coordinates differs in at least one, and every block
-// where only q has them differs in all of q's (pcq[j], q's count in block j).
-__device__ __forceinline__ uint32_t sig_bound(uint64_t sx, uint64_t sq, const uint8_t *pcq)
+// where only q has them differs in all of q's there.  sigm[t] (t = 1..kSigLevels) marks the
+// blocks where q has at least t set coordinates (sigm[1] = sq), so the second term is the sum
+// of min(q's count, kSigLevels) over q's blocks that x leaves empty: never above the distance.
+__device__ __forceinline__ uint32_t sig_bound(uint64_t sx, uint64_t sq, const uint64_t *sigm)
 {
     uint32_t lb = __popcll(sx & ~sq);
-    uint64_t m = sq & ~sx;
-    while (m) {
-        lb += pcq[__ffsll((long long)m) - 1];
-        m &= m - 1;
+    const uint64_t m = sq & ~sx;
+    for (int t = 1; t <= kSigLevels; ++t) {   // the levels are nested: stop at the first empty one
+        const uint64_t mt = sigm[t];
+        if (!mt) break;
+        lb += __popcll(m & mt);
     }
     return lb;
 }
@@ -229,10 +237,10 @@ __device__ __forceinline__ uint32_t probed_table(uint32_t j, uint32_t nt, uint32
 
 }  // namespace fclsh
 
-// The index (opaque to users).
 // Phases timed by fclsh_timing_read (see include/fclsh.h).
 constexpr int kTimedPhases = 9;
 
+// The index (opaque to users).
 struct fclsh_index {
     int device = 0;
     uint64_t n = 0;

@@ -36,6 +36,27 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return (1u << (threadIdx.x & 31)) - 1u;
 }
 
+// L2 eviction priorities for the loads of the heavy-query kernel: the bucket entries it
+// streams are evicted first, the point signatures (read at random, again and again) last.
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t ld_nc_hint(const uint64_t *ptr, uint64_t policy)
+{
+    uint64_t v;
+    asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(policy));
+    return v;
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T *red)   // red: >= 32 entries of smem
 {
@@ -133,16 +154,30 @@ __device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, 
 enum DedupMode { DEDUP_HSET = 0, DEDUP_BITMAP = 1, DEDUP_MARK = 2 };
 
 // One bucket entry per lane (is_coll = key matched); warp-collective.
+// The query's occupancy levels from warps 0 and 1 (thread j: signature block j): sigm32 is a
+// 32-bit view of sigm[kSigLevels + 1]; level t's low half comes from warp 0.
+__device__ __forceinline__ void sig_levels(const uint64_t *q_s, uint32_t d, uint32_t sig_block, uint32_t lane,
+                                           uint32_t warp, uint32_t *sigm32)
+{
+    const uint32_t j = warp * 32 + lane, lo = j * sig_block;
+    const uint32_t pc = lo < d ? popc_range(q_s, lo, min(lo + sig_block, d)) : 0u;
+#pragma unroll
+    for (int t = 1; t <= kSigLevels; ++t) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, pc >= (uint32_t)t);
+        if (lane == 0) sigm32[2 * t + warp] = bal;
+    }
+}
+
 // S3's pre-filter: false when the signature bound already puts point id beyond the radius.
-__device__ __forceinline__ bool sig_pass(const QueryArgs &a, uint32_t id, uint64_t sq, const uint8_t *pcq,
+__device__ __forceinline__ bool sig_pass(const QueryArgs &a, uint32_t id, uint64_t sq, const uint64_t *sigm,
                                          uint32_t radius)
 {
-    return !a.sig || sig_bound(__ldg(a.sig + id), sq, pcq) <= radius;
+    return !a.sig || sig_bound(__ldg(a.sig + id), sq, sigm) <= radius;
 }
 
 __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
                                               int mode, uint32_t radius, bool is_coll, uint32_t id, Counters &c,
-                                              uint32_t *res_s, uint32_t *s_nres, uint64_t sq, const uint8_t *pcq)
+                                              uint32_t *res_s, uint32_t *s_nres, uint64_t sq, const uint64_t *sigm)
 {
     bool isnew = false;
     is_coll = is_coll && FCLSH_CHECK(id < a.n, 0x0109);
@@ -160,7 +195,7 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
     bool hit = false;
     if (a.words >= kWarpVerifyWords) {   // long points: the warp reads each new candidate together
         const uint32_t lane = threadIdx.x & 31;
-        uint32_t need = __ballot_sync(0xffffffffu, isnew && sig_pass(a, id, sq, pcq, radius));
+        uint32_t need = __ballot_sync(0xffffffffu, isnew && sig_pass(a, id, sq, sigm, radius));
         while (need) {
             const uint32_t src = __ffs(need) - 1;
             need &= need - 1;
@@ -188,7 +223,7 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
         if (isnew) c.cand++;
     } else if (isnew) {
         c.cand++;
-        hit = sig_pass(a, id, sq, pcq, radius) && distance_to(a, q_s, id) <= radius;
+        hit = sig_pass(a, id, sq, sigm, radius) && distance_to(a, q_s, id) <= radius;
     }
     append_hits(hit, id, c, res_s, s_nres);
 }
@@ -201,9 +236,11 @@ __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t
 constexpr int kU = 4;
 constexpr uint32_t kCandCap = 512u * kU;   // new candidates of one chunk (blocks of up to 512 threads)
 constexpr uint32_t kHeavyThreads = 1024;    // query_heavy_kernel: one block of 32 warps per SM
-constexpr uint32_t kHeavyCand = 4096;       // its candidate lists (S3)
+constexpr uint32_t kHeavyCand = 4096;       // its candidate lists (S3): one of kWarpCand per warp
+constexpr uint32_t kWarpCand = kHeavyCand / (kHeavyThreads / 32);
+constexpr int kHeavyU = 4;                  // its list positions per thread per chunk (one search)
 // bucket entries of a query that query_heavy_kernel walks as one list (32-bit positions)
-constexpr unsigned long long kHeavyMaxEntries = 0xFFFFFFFFull - (unsigned long long)kHeavyThreads * kU;
+constexpr unsigned long long kHeavyMaxEntries = 0xFFFFFFFFull - (unsigned long long)kHeavyThreads * kHeavyU;
 
 // The run holding list position pos: the last j < nruns with off[j] <= pos (off[0] = 0).
 __device__ __forceinline__ uint32_t run_of(const uint32_t *off, uint32_t nruns, uint32_t pos)
@@ -217,31 +254,51 @@ __device__ __forceinline__ uint32_t run_of(const uint32_t *off, uint32_t nruns, 
     return lo;
 }
 
+// Stored key bits that no entry has (entry_fp is below 2^50): a chunk position past the list's end.
+constexpr uint64_t kNoFp = ~0ULL;
+
+template <int U = kU>
 struct Chunk {
-    uint64_t en[kU];
-    uint32_t tau[kU];   // the entry's table, 0xFFFFFFFF past the list's end
+    uint64_t en[U];
+    uint64_t fp[U];   // the probed key's stored bits (entry_fp of its bucket's entries), kNoFp past the end
 };
 
-// The entries at list positions base + kU * threadIdx.x + k, k < kU: one search for the run of
-// the first, then a walk over the runs (loads issued back to back; a warp's positions are
-// consecutive, so a long run is read in whole lines).
-__device__ __forceinline__ void load_chunk(const QueryArgs &a, const uint32_t *lo_s, const uint32_t *off_s,
-                                           uint32_t Tq, uint32_t nt, uint32_t L, uint32_t E, uint32_t base, Chunk &ch)
+// The entries at list positions base + U * threadIdx.x + k, k < U: one search for the run of
+// the first, then a walk over the runs, the current run's entry row and key bits kept in
+// registers (loads issued back to back; a warp's positions are consecutive, so a long run is
+// read in whole lines).  An entry is a collision when entry_fp(en) == fp.
+template <int U = kU, bool HINT = false>
+__device__ __forceinline__ void load_chunk(const QueryArgs &a, const uint64_t *keys_s, const uint32_t *lo_s,
+                                           const uint32_t *off_s, uint32_t Tq, uint32_t nt, uint32_t L, uint32_t E,
+                                           uint32_t base, Chunk<U> &ch, uint64_t policy = 0)
 {
-    const uint32_t pos0 = base + kU * threadIdx.x;
-    uint32_t j = pos0 < E ? run_of(off_s, Tq, pos0) : 0;
+    const uint32_t pos0 = base + U * threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < kU; ++k) {
-        const uint32_t pos = pos0 + k;
-        ch.tau[k] = 0xFFFFFFFFu;
+    for (int k = 0; k < U; ++k) {
         ch.en[k] = 0;
+        ch.fp[k] = kNoFp;
+    }
+    if (pos0 >= E) return;
+    uint32_t j = run_of(off_s, Tq, pos0);
+    uint32_t next = j + 1 < Tq ? off_s[j + 1] : E;   // the list position where run j ends
+    uint32_t tau = probed_table(j, nt, L);
+    uint64_t fp = keys_s[tau] >> a.slot_bits;
+    uint64_t row = (uint64_t)tau * a.n + lo_s[j] - off_s[j];   // list position p of run j: ent[row + p] (mod 2^64)
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const uint32_t pos = pos0 + k;
         if (pos < E) {
-            while (j + 1 < Tq && off_s[j + 1] <= pos) ++j;
-            const uint32_t tau = probed_table(j, nt, L);
-            const uint64_t e = (uint64_t)lo_s[j] + (pos - off_s[j]);
-            if (FCLSH_CHECK(e < a.n && tau < a.T, 0x0103)) {
-                ch.tau[k] = tau;
-                ch.en[k] = __ldg(a.ent + (uint64_t)tau * a.n + e);
+            while (pos >= next) {   // the next non-empty run
+                ++j;
+                next = j + 1 < Tq ? off_s[j + 1] : E;
+                tau = probed_table(j, nt, L);
+                fp = keys_s[tau] >> a.slot_bits;
+                row = (uint64_t)tau * a.n + lo_s[j] - off_s[j];
+            }
+            const uint64_t e = row + pos;
+            if (FCLSH_CHECK(pos - off_s[j] < next - off_s[j] && tau < a.T, 0x0103)) {
+                ch.fp[k] = fp;
+                ch.en[k] = HINT ? ld_nc_hint(a.ent + e, policy) : __ldg(a.ent + e);
             }
         }
     }
@@ -289,12 +346,13 @@ constexpr int kV = 4;
 
 // The grouped reads of verify_list for points of H 16-byte pieces per lane (H = 1: up to 16
 // words; 2: up to 31).
+// The list is shared by the block's warps (block = true) or is the calling warp's own.
 template <int H>
 __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s,
-                                              uint32_t m, uint32_t radius, uint64_t sq, const uint8_t *pcq,
-                                              Counters &c, uint32_t *res_s, uint32_t *s_nres, uint32_t *ovf_bm)
+                                              uint32_t m, uint32_t radius, bool count, Counters &c, uint32_t *res_s,
+                                              uint32_t *s_nres, uint32_t *ovf_bm, bool block = true)
 {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t lane = threadIdx.x & 31, warp = block ? threadIdx.x >> 5 : 0u, nwarps = block ? blockDim.x >> 5 : 1u;
     const uint32_t words = a.words, pieces = (words + 1) >> 1;   // 16-byte pieces of a point
     const uint32_t G = pieces <= 1 ? 1u : pieces <= 2 ? 2u : pieces <= 4 ? 4u : 8u;
     const uint32_t per = 32u / G, sub = lane / G, gl = lane % G;  // candidates per warp step; group, lane in it
@@ -308,7 +366,7 @@ __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t
             const uint32_t i = i0 + v * per + sub;
             ok[v] = i < m;
             id[v] = ok[v] ? cand_s[i] : 0u;
-            ok[v] = ok[v] && sig_pass(a, id[v], sq, pcq, radius) && FCLSH_CHECK(id[v] < a.n, 0x0101);
+            ok[v] = ok[v] && FCLSH_CHECK(id[v] < a.n, 0x0101);
             const uint64_t *pt = a.points + (uint64_t)id[v] * words;
 #pragma unroll
             for (int h = 0; h < H; ++h) {
@@ -338,22 +396,61 @@ __device__ __forceinline__ void verify_groups(const QueryArgs &a, const uint64_t
             for (uint32_t o = G >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             const uint32_t i = i0 + v * per + sub;
             const bool lead = gl == 0 && i < m;
-            if (lead) c.cand++;
+            if (lead && count) c.cand++;
             const bool hit = lead && ok[v] && part <= radius;
             append_hits(hit, id[v], c, res_s, s_nres, ovf_bm);
         }
     }
 }
 
-// S3 for the candidates cand_s[0..m) (block-wide): each is counted once in #Candidates and
-// reported if within the radius.  Points of up to 31 words are read by groups of G lanes, one 16-byte
-// piece per lane (G = 8 for 16 words: a point is one 128-byte line), kV candidates per group
-// loaded before their popcounts are reduced in the group; longer points by the whole warp.
-__device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *q_s, const uint32_t *cand_s, uint32_t m,
-                                            uint32_t radius, uint64_t sq, const uint8_t *pcq, Counters &c,
-                                            uint32_t *res_s, uint32_t *s_nres, uint32_t *ovf_bm = nullptr)
+// Candidates whose signatures a thread loads before bounding any of them.
+constexpr int kF = 4;
+
+// S3 for the candidates cand_s[0..m) (block-wide; the list may be rewritten): each is counted
+// once in #Candidates and reported if within the radius.  With the pre-filter, a thread per
+// candidate first bounds its distance from the signatures (kF loads in flight per thread) and
+// the candidates that pass are compacted to the list's front (s_nsurv: a shared counter).
+// Points of up to 31 words are then read by groups of G lanes, one 16-byte piece per lane
+// (G = 8 for 16 words: a point is one 128-byte line), kV candidates per group loaded before
+// their popcounts are reduced in the group; longer points by the whole warp.
+__device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *q_s, uint32_t *cand_s, uint32_t m,
+                                            uint32_t radius, uint64_t sq, const uint64_t *sigm, Counters &c,
+                                            uint32_t *res_s, uint32_t *s_nres, uint32_t *s_nsurv,
+                                            uint32_t *ovf_bm = nullptr)
 {
     const uint32_t B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
+    const bool count = !a.sig;   // with the pre-filter every candidate is counted as it is bounded
+    if (a.sig) {
+        if (tid == 0) *s_nsurv = 0;
+        __syncthreads();
+        for (uint32_t base = 0; base < m; base += B * kF) {
+            uint32_t id[kF];
+            uint64_t sx[kF];
+#pragma unroll
+            for (int f = 0; f < kF; ++f) {
+                const uint32_t i = base + f * B + tid;
+                id[f] = i < m ? cand_s[i] : 0u;
+                sx[f] = i < m && FCLSH_CHECK(id[f] < a.n, 0x0107) ? __ldg(a.sig + id[f]) : 0ULL;
+            }
+            __syncthreads();   // the round's reads before the survivors overwrite the list's front
+#pragma unroll
+            for (int f = 0; f < kF; ++f) {
+                const bool in = base + f * B + tid < m;
+                if (in) c.cand++;
+                const bool pass = in && id[f] < a.n && sig_bound(sx[f], sq, sigm) <= radius;
+                const uint32_t bal = __ballot_sync(0xffffffffu, pass);
+                if (bal) {
+                    const uint32_t leader = __ffs(bal) - 1;
+                    uint32_t at = 0;
+                    if (lane == leader) at = atomicAdd(s_nsurv, (uint32_t)__popc(bal));
+                    at = __shfl_sync(0xffffffffu, at, leader) + __popc(bal & lanemask_lt());
+                    if (pass) cand_s[at] = id[f];
+                }
+            }
+        }
+        __syncthreads();
+        m = *s_nsurv;
+    }
     if (a.words >= kWarpVerifyWords) {   // a warp per candidate: coalesced reads of long points
         for (uint32_t i0 = 0; i0 < m; i0 += nwarps) {
             const uint32_t i = i0 + warp;
@@ -361,17 +458,39 @@ __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *
             const uint32_t id = ok ? cand_s[i] : 0;
             bool hit = false;
             if (ok) {
-                if (lane == 0) c.cand++;
-                hit = sig_pass(a, id, sq, pcq, radius) && warp_distance(a, q_s, id, radius) <= radius;
+                if (lane == 0 && count) c.cand++;
+                hit = warp_distance(a, q_s, id, radius) <= radius;
             }
             append_hits(hit && lane == 0, id, c, res_s, s_nres, ovf_bm);
         }
         return;
     }
     if (a.words <= 16)
-        verify_groups<1>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, ovf_bm);
+        verify_groups<1>(a, q_s, cand_s, m, radius, count, c, res_s, s_nres, ovf_bm);
     else
-        verify_groups<2>(a, q_s, cand_s, m, radius, sq, pcq, c, res_s, s_nres, ovf_bm);
+        verify_groups<2>(a, q_s, cand_s, m, radius, count, c, res_s, s_nres, ovf_bm);
+}
+
+// S3 for the candidates buf[0..m) of one warp (warp-collective; counted where they were
+// listed): points of up to 31 words read by groups of lanes as in verify_groups, longer ones by
+// the whole warp.  No block barrier, so the block's warps go through their lists independently.
+__device__ __forceinline__ void verify_warp(const QueryArgs &a, const uint64_t *q_s, const uint32_t *buf, uint32_t m,
+                                            uint32_t radius, Counters &c, uint32_t *res_s, uint32_t *s_nres,
+                                            uint32_t *ovf_bm)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    if (a.words >= kWarpVerifyWords) {
+        for (uint32_t i = 0; i < m; ++i) {
+            const uint32_t id = buf[i];
+            const bool hit = warp_distance(a, q_s, id, radius) <= radius;
+            append_hits(hit && lane == 0, id, c, res_s, s_nres, ovf_bm);
+        }
+        return;
+    }
+    if (a.words <= 16)
+        verify_groups<1>(a, q_s, buf, m, radius, false, c, res_s, s_nres, ovf_bm, false);
+    else
+        verify_groups<2>(a, q_s, buf, m, radius, false, c, res_s, s_nres, ovf_bm, false);
 }
 
 // Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
@@ -413,20 +532,15 @@ __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
 }
 
 
-// The query into shared memory and, with the S3 pre-filter, its set coordinates per signature
-// block and its block-occupancy signature (read after the barriers of S1).  Block-wide.
-__device__ __forceinline__ void load_query(const QueryArgs &a, uint64_t qi, uint64_t *q_s, uint8_t *pcq, uint32_t *sigq)
+// The query into shared memory and, with the S3 pre-filter, its occupancy levels sigm[t]
+// (t = 1..kSigLevels; sigm[1] is its block-occupancy signature): bit j set when the query has
+// at least t set coordinates in signature block j.  Read after the barriers of S1.  Block-wide.
+__device__ __forceinline__ void load_query(const QueryArgs &a, uint64_t qi, uint64_t *q_s, uint64_t *sigm)
 {
     const uint32_t tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t w = tid; w < a.words; w += B) q_s[w] = a.queries[qi * a.words + w];
     __syncthreads();
-    if (a.sig && tid < 64) {   // warps 0 and 1 (blocks have >= 128 threads)
-        const uint32_t lo = tid * a.sig_block;
-        const uint32_t pc = lo < a.d ? popc_range(q_s, lo, min(lo + a.sig_block, a.d)) : 0u;
-        pcq[tid] = (uint8_t)min(pc, 255u);
-        const uint32_t bal = __ballot_sync(0xffffffffu, pc > 0);
-        if (lane == 0) sigq[warp] = bal;
-    }
+    if (a.sig && tid < 64) sig_levels(q_s, a.d, a.sig_block, lane, warp, reinterpret_cast<uint32_t *>(sigm));
 }
 
 // S1: Algorithm 2 for every part in shared memory (tbuf: W words), or the keys a hash launch
@@ -578,8 +692,8 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
     __shared__ unsigned long long s_qi;
     __shared__ uint32_t s_nres, s_ncand;
     __shared__ unsigned long long red64[32];
-    __shared__ uint8_t s_pcq[64];                 // the query's set coordinates per signature block
-    __shared__ __align__(8) uint32_t s_sigq[2];   // the query's block-occupancy signature
+    __shared__ uint64_t s_sigm[kSigLevels + 1];   // the query's occupancy levels (sig_bound)
+    __shared__ uint32_t s_nsurv;
 
     const uint32_t tid = threadIdx.x, B = blockDim.x;
     const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
@@ -597,7 +711,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
             continue;
         }
         const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
-        load_query(a, qi, q_s, s_pcq, s_sigq);
+        load_query(a, qi, q_s, s_sigm);
         query_s1(a, qi, q_s, keys_s, tbuf);
         uint32_t nt, Tq;
         const unsigned long long E = probe_ranges(a, radius, keys_s, lo_s, len_s, red64, nt, Tq);
@@ -627,17 +741,16 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
         __syncthreads();
 
         // ---- S2b + S3 (chunks of the list): collisions -> dedup -> verify of the new candidates
-        const uint64_t sq = a.sig ? ((uint64_t)s_sigq[1] << 32 | s_sigq[0]) : 0;
+        const uint64_t sq = a.sig ? s_sigm[1] : 0;
         Counters c;
-        const uint64_t fp_shift = a.slot_bits;
         for (uint32_t base = 0; base < E32; base += B * kU) {
-            Chunk ch;
-            load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+            Chunk<> ch;
+            load_chunk(a, keys_s, lo_s, off_s, Tq, nt, L, E32, base, ch);
             uint32_t ids[kU], old[kU];
             bool coll[kU];
 #pragma unroll
             for (int k = 0; k < kU; ++k) {
-                coll[k] = ch.tau[k] != 0xFFFFFFFFu && entry_fp(ch.en[k], a.ent_ib) == (keys_s[ch.tau[k]] >> fp_shift);
+                coll[k] = entry_fp(ch.en[k], a.ent_ib) == ch.fp[k];
                 ids[k] = entry_id(ch.en[k], a.ent_ib);
                 old[k] = 0;
             }
@@ -665,7 +778,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
 #pragma unroll
             for (int k = 0; k < kU; ++k) push_cand(coll[k] && !old[k], ids[k], cand_s, &s_ncand);
             __syncthreads();
-            verify_list(a, q_s, cand_s, s_ncand, radius, sq, s_pcq, c, res_s, &s_nres);
+            verify_list(a, q_s, cand_s, s_ncand, radius, sq, s_sigm, c, res_s, &s_nres, &s_nsurv);
             __syncthreads();
             if (tid == 0) s_ncand = 0;
             __syncthreads();
@@ -687,7 +800,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
                     const bool act = e < short_len;
                     const uint64_t en = act ? __ldg(row + lo + e) : 0;
                     process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == fp,
-                                  entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_pcq);
+                                  entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_sigm);
                 }
                 uint32_t lmask = __ballot_sync(0xffffffffu, len > a.inline_len);
                 while (lmask) {
@@ -703,7 +816,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
                         const bool act = e < l_len;
                         const uint64_t en = act ? __ldg(lrow + e) : 0;
                         process_entry(a, q_s, hset, bm, mode, radius, act && entry_fp(en, a.ent_ib) == l_fp,
-                                      entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_pcq);
+                                      entry_id(en, a.ent_ib), c, res_s, &s_nres, sq, s_sigm);
                     }
                 }
             }
@@ -727,7 +840,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
                         const uint32_t b = __ffs(rem) - 1;
                         rem &= rem - 1;
                         id = (uint32_t)(wi * 32 + b);
-                        hit = sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius;
+                        hit = sig_pass(a, id, sq, s_sigm, radius) && distance_to(a, q_s, id) <= radius;
                         if (hit) hits |= 1u << b;
                     }
                     append_hits(hit, id, c, res_s, &s_nres);
@@ -745,11 +858,11 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
         }
         if (bitmap_mode && !sweep_mode) {   // leave the CTA's bitmap all-zero: the list again
             for (uint32_t base = 0; base < E32; base += B * kU) {
-                Chunk ch;
-                load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+                Chunk<> ch;
+                load_chunk(a, keys_s, lo_s, off_s, Tq, nt, L, E32, base, ch);
 #pragma unroll
                 for (int k = 0; k < kU; ++k)
-                    if (ch.tau[k] != 0xFFFFFFFFu) bm[entry_id(ch.en[k], a.ent_ib) >> 5] = 0;
+                    if (ch.fp[k] != kNoFp) bm[entry_id(ch.en[k], a.ent_ib) >> 5] = 0;
             }
             if (!listed)
                 for (uint32_t j = tid; j < Tq; j += B) {
@@ -771,14 +884,13 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
             // the bitmap (the sweep left exactly the hits marked), then read the ids out in
             // ascending order and clear it again.
             for (uint32_t base = 0; !sweep_mode && base < E32; base += B * kU) {   // the list again
-                Chunk ch;
-                load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+                Chunk<> ch;
+                load_chunk(a, keys_s, lo_s, off_s, Tq, nt, L, E32, base, ch);
 #pragma unroll
                 for (int k = 0; k < kU; ++k) {
-                    if (ch.tau[k] == 0xFFFFFFFFu || entry_fp(ch.en[k], a.ent_ib) != (keys_s[ch.tau[k]] >> fp_shift))
-                        continue;
+                    if (entry_fp(ch.en[k], a.ent_ib) != ch.fp[k]) continue;
                     const uint32_t id = entry_id(ch.en[k], a.ent_ib);
-                    if (sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius)
+                    if (sig_pass(a, id, sq, s_sigm, radius) && distance_to(a, q_s, id) <= radius)
                         atomicOr(bm + (id >> 5), 1u << (id & 31));
                 }
             }
@@ -791,7 +903,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
                     const uint64_t en = __ldg(row + e);
                     if (entry_fp(en, a.ent_ib) != fp) continue;
                     const uint32_t id = entry_id(en, a.ent_ib);
-                    if (sig_pass(a, id, sq, s_pcq, radius) && distance_to(a, q_s, id) <= radius)
+                    if (sig_pass(a, id, sq, s_sigm, radius) && distance_to(a, q_s, id) <= radius)
                         atomicOr(bm + (id >> 5), 1u << (id & 31));
                 }
             }
@@ -839,13 +951,15 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
     uint64_t *win = reinterpret_cast<uint64_t *>(cand_s + kHeavyCand);   // 8-aligned (kResCap + kHeavyCand even)
     uint32_t *win32 = reinterpret_cast<uint32_t *>(win);
     __shared__ unsigned long long s_h, s_base;
-    __shared__ uint32_t s_nres, s_total;
+    __shared__ uint32_t s_nres, s_nspill;
     __shared__ unsigned long long red64[32];
-    __shared__ uint8_t s_pcq[64];
-    __shared__ __align__(8) uint32_t s_sigq[2];
+    __shared__ uint64_t s_sigm[kSigLevels + 1];
 
     const uint32_t tid = threadIdx.x, B = blockDim.x, L = a.W - 1;
+    const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
     uint32_t *bm = a.bitmaps + (uint64_t)blockIdx.x * a.bm_words;
+    uint32_t *spill = a.spill + (uint64_t)blockIdx.x * a.spill_cap;   // ids of the windows after the first
+    const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
     const unsigned long long nheavy = *a.heavy_n;   // final: written by the batch kernel before this launch
 
     for (;;) {
@@ -856,15 +970,18 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
         const uint64_t qi = a.heavy_q[h];
         if (!FCLSH_CHECK(qi < a.nq, 0x0110)) break;   // block-uniform
         const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
-        load_query(a, qi, q_s, s_pcq, s_sigq);
+        load_query(a, qi, q_s, s_sigm);
         query_s1(a, qi, q_s, keys_s, win);
         uint32_t nt, Tq;
         const unsigned long long E = probe_ranges(a, radius, keys_s, lo_s, off_s, red64, nt, Tq);
         const uint32_t E32 = (uint32_t)min(E, kHeavyMaxEntries);   // the batch kernel lists only E <= the limit
         runs_prefix(off_s, Tq, red64);
-        if (tid == 0) s_nres = 0;
+        if (tid == 0) {
+            s_nres = 0;
+            s_nspill = 0;
+        }
         __syncthreads();
-        const uint64_t sq = a.sig ? ((uint64_t)s_sigq[1] << 32 | s_sigq[0]) : 0;
+        const uint64_t sq = a.sig ? s_sigm[1] : 0;
         Counters c;
 
         for (uint64_t w_lo = 0; w_lo < a.n; w_lo += a.win_bits) {
@@ -872,48 +989,96 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
             const uint32_t nw = (uint32_t)((nbits + 63) >> 6);
             for (uint32_t i = tid; i < nw; i += B) win[i] = 0;
             __syncthreads();
-            // S2: mark the window's ids among the collisions (shared-memory reductions)
-            for (uint32_t base = 0; base < E32; base += B * kU) {
-                Chunk ch;
-                load_chunk(a, lo_s, off_s, Tq, nt, L, E32, base, ch);
+            // S2: mark the window's ids among the collisions (shared-memory reductions).  The
+            // first window walks the bucket entries and lists the collisions of later windows in
+            // the CTA's spill list (4 bytes an id, appended a warp at a time); later windows read
+            // that list, or walk the entries again when it overflowed.
+            const uint32_t nspill = s_nspill;   // final: written before the previous window's barriers
+            if (w_lo != 0 && nspill <= a.spill_cap) {
+                for (uint32_t i0 = 0; i0 < nspill; i0 += 8 * B) {   // eight loads in flight per thread
+                    uint32_t id[8];
 #pragma unroll
-                for (int k = 0; k < kU; ++k) {
-                    const uint32_t id = entry_id(ch.en[k], a.ent_ib);
-                    const bool coll = ch.tau[k] != 0xFFFFFFFFu &&
-                                      entry_fp(ch.en[k], a.ent_ib) == (keys_s[ch.tau[k]] >> a.slot_bits) &&
-                                      FCLSH_CHECK(id < a.n, 0x0111);
-                    if (!coll) continue;
-                    if (w_lo == 0) c.coll++;
-                    const uint64_t rel = (uint64_t)id - w_lo;   // wraps past the window for id < w_lo
-                    if (rel < nbits) atomicOr(win32 + (rel >> 5), 1u << (rel & 31));
+                    for (int u = 0; u < 8; ++u) {
+                        const uint32_t i = i0 + u * B + tid;
+                        id[u] = i < nspill ? spill[i] : 0xFFFFFFFFu;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const uint64_t rel = (uint64_t)id[u] - w_lo;
+                        if (id[u] != 0xFFFFFFFFu && rel < nbits) atomicOr(win32 + (rel >> 5), 1u << (rel & 31));
+                    }
+                }
+            } else {
+                for (uint32_t base = 0; base < E32; base += B * kHeavyU) {
+                    Chunk<kHeavyU> ch;
+                    load_chunk<kHeavyU, true>(a, keys_s, lo_s, off_s, Tq, nt, L, E32, base, ch, pol_stream);
+#pragma unroll
+                    for (int k = 0; k < kHeavyU; ++k) {
+                        const uint32_t id = entry_id(ch.en[k], a.ent_ib);
+                        const bool coll = entry_fp(ch.en[k], a.ent_ib) == ch.fp[k] && FCLSH_CHECK(id < a.n, 0x0111);
+                        const uint64_t rel = (uint64_t)id - w_lo;   // wraps past the window for id < w_lo
+                        if (coll && rel < nbits) atomicOr(win32 + (rel >> 5), 1u << (rel & 31));
+                        if (w_lo != 0) continue;   // block-uniform
+                        if (coll) c.coll++;
+                        const bool later = coll && rel >= nbits;
+                        const uint32_t m = __ballot_sync(0xffffffffu, later);
+                        if (m) {
+                            const uint32_t leader = __ffs(m) - 1;
+                            uint32_t at = 0;
+                            if (lane == leader) at = atomicAdd(&s_nspill, (uint32_t)__popc(m));
+                            at = __shfl_sync(0xffffffffu, at, leader) + __popc(m & lanemask_lt());
+                            if (later && at < a.spill_cap) spill[at] = id;
+                        }
+                    }
                 }
             }
             __syncthreads();
-            // S3: the window's marked ids in rounds of B words, listed in ascending order in
-            // pieces of kHeavyCand (a thread places the ids of its word whose rank falls in the piece)
-            for (uint32_t r0 = 0; r0 < nw; r0 += B) {
-                const uint32_t w = r0 + tid;
-                const uint64_t bits = w < nw ? win[w] : 0ULL;
-                const uint32_t cnt = (uint32_t)__popcll(bits);
-                const uint32_t before = (uint32_t)block_excl_scan_u32(cnt, red64);
-                if (tid == B - 1) s_total = before + cnt;
-                __syncthreads();
-                const uint32_t total = s_total;
-                for (uint32_t s0 = 0; s0 < total; s0 += kHeavyCand) {
-                    if (cnt && before < s0 + kHeavyCand && before + cnt > s0) {
-                        uint64_t rem = bits;
-                        for (uint32_t rank = before; rem; ++rank) {
-                            const uint32_t b = (uint32_t)(__ffsll((long long)rem) - 1);
-                            rem &= rem - 1;
-                            if (rank >= s0 && rank - s0 < kHeavyCand)
-                                cand_s[rank - s0] = (uint32_t)(w_lo + (uint64_t)w * 64 + b);
-                        }
+            // S3: warps sweep the window 32 words at a time, a lane taking the marked ids of its
+            // word (the window's distinct candidates) four at a time.  With the pre-filter their
+            // signatures are loaded together and bounded; the candidates that pass (all of them
+            // without it) join the warp's own list of kWarpCand, which the warp verifies when the
+            // next ones would not fit and at the window's end (no block barrier until then).
+            uint32_t *wbuf = cand_s + warp * kWarpCand;
+            uint32_t nl = 0;   // the warp's listed candidates
+            for (uint32_t w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
+                const uint32_t w = w0 + lane;
+                uint64_t bits = w < nw ? win[w] : 0ULL;
+                while (__any_sync(0xffffffffu, bits != 0)) {
+                    uint32_t id[4];
+                    uint64_t sx[4];
+                    bool in[4];
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        in[f] = bits != 0;
+                        const uint32_t b = in[f] ? (uint32_t)(__ffsll((long long)bits) - 1) : 0u;
+                        bits &= bits - 1;
+                        id[f] = (uint32_t)(w_lo + (uint64_t)w * 64 + b);
+                        sx[f] = in[f] && a.sig ? ld_nc_hint(a.sig + id[f], pol_keep) : 0ULL;
                     }
-                    __syncthreads();
-                    verify_list(a, q_s, cand_s, min(kHeavyCand, total - s0), radius, sq, s_pcq, c, res_s, &s_nres, bm);
-                    __syncthreads();
+                    uint32_t bal[4], total = 0;
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        if (in[f]) c.cand++;
+                        const bool pass = in[f] && (!a.sig || sig_bound(sx[f], sq, s_sigm) <= radius);
+                        bal[f] = __ballot_sync(0xffffffffu, pass);
+                        total += __popc(bal[f]);
+                    }
+                    if (nl + total > kWarpCand) {   // warp-uniform
+                        __syncwarp();
+                        verify_warp(a, q_s, wbuf, nl, radius, c, res_s, &s_nres, bm);
+                        __syncwarp();
+                        nl = 0;
+                    }
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        if ((bal[f] >> lane) & 1) wbuf[nl + __popc(bal[f] & lanemask_lt())] = id[f];
+                        nl += __popc(bal[f]);
+                    }
                 }
             }
+            __syncwarp();
+            if (nl) verify_warp(a, q_s, wbuf, nl, radius, c, res_s, &s_nres, bm);   // warp-uniform
+            __syncthreads();   // every warp's sweep before the next window is cleared
         }
         const unsigned long long tc = block_sum(c.coll, red64);
         const unsigned long long td = block_sum(c.cand, red64);
@@ -966,19 +1131,13 @@ __global__ void __launch_bounds__(256) gather_runs_kernel(const uint32_t *runs, 
 __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uint64_t *keys, uint32_t *bitmap)
 {
     extern __shared__ uint64_t q_s[];
-    __shared__ uint8_t s_pcq[64];
-    __shared__ __align__(8) uint32_t s_sigq[2];
+    __shared__ uint64_t s_sigm[kSigLevels + 1];
     for (uint32_t w = threadIdx.x; w < a.words; w += blockDim.x) q_s[w] = a.queries[w];
     __syncthreads();
-    if (a.sig && threadIdx.x < 64) {   // the query's signature (warps 0 and 1 of 256 threads)
-        const uint32_t lo = threadIdx.x * a.sig_block;
-        const uint32_t pc = lo < a.d ? popc_range(q_s, lo, min(lo + a.sig_block, a.d)) : 0u;
-        s_pcq[threadIdx.x] = (uint8_t)min(pc, 255u);
-        const uint32_t bal = __ballot_sync(0xffffffffu, pc > 0);
-        if ((threadIdx.x & 31) == 0) s_sigq[threadIdx.x >> 5] = bal;
-    }
+    if (a.sig && threadIdx.x < 64)   // the query's occupancy levels (warps 0 and 1 of 256 threads)
+        sig_levels(q_s, a.d, a.sig_block, threadIdx.x & 31, threadIdx.x >> 5, reinterpret_cast<uint32_t *>(s_sigm));
     __syncthreads();
-    const uint64_t sq = a.sig ? ((uint64_t)s_sigq[1] << 32 | s_sigq[0]) : 0;
+    const uint64_t sq = a.sig ? s_sigm[1] : 0;
     const uint32_t nt = rows_per_part(a, a.radius), j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.t * nt) return;
     const uint32_t tau = probed_table(j, nt, a.W - 1);
@@ -998,7 +1157,7 @@ __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uin
         const uint32_t bit = 1u << (id & 31);
         if (atomicOr(bitmap + (id >> 5), bit) & bit) continue;
         cand++;
-        if (sig_pass(a, id, sq, s_pcq, a.radius) && distance_to(a, q_s, id) <= a.radius) {
+        if (sig_pass(a, id, sq, s_sigm, a.radius) && distance_to(a, q_s, id) <= a.radius) {
             const unsigned long long pos = atomicAdd(a.cursor, 1ULL);
             if (pos < a.cap) a.staged[pos] = id;
         }
