@@ -41,15 +41,20 @@ CFG = 4
 # kernels (profiles/); traffic scales with the algorithmic bytes.  An entry is None (traffic
 # reported as null) until it is captured, and is reset to None when its kernel changes.
 TRAFFIC_RATIO = {
-    2: {
-        "hash": 0.951,        # profiles/hash_tile_kernel_w512_n300k_d128_r8.md
-        "hash_mma": 0.953,    # profiles/hash_mma_kernel_w512_n300k_d128_r8.md
-        "scatter": 0.983,     # profiles/partition_scatter_kernel_n300k_d128_r8.md
-        "finish": 1.020,      # profiles/segment_one_kernel_n300k_d128_r8.md
-        "query": None,
+    2: {   # profiles/launch_list_plain_n1M_d128_r8.md (full size)
+        "hash": 0.984,
+        "hash_mma": 0.986,
+        "scatter": 0.996,
+        "finish": 1.057,
+        "query": 24.2,
         "hist": None,
     },
-    4: {},
+    4: {   # profiles/launch_list_sparse_n2M_d1024_r20.md (full size)
+        "hash_scatter": 0.998,
+        "scatter_wide": 1.18,
+        "finish": 1.066,
+        "query": 0.447,
+    },
 }
 
 
