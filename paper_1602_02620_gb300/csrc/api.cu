@@ -951,7 +951,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     const uint32_t dbits = msd ? msd_dbits(sb) : 8;
     const uint64_t nd = (uint64_t)1 << dbits;   // segments per table
     const uint32_t cap = msd ? msd_bin_capacity(n, dbits) : 0;
-    const uint64_t width = msd ? std::max<uint64_t>(n, nd * cap) : n;   // packed entries per table
+    const uint64_t width = msd ? std::max<uint64_t>(n, nd * cap + msd_bin0_extra(n)) : n;   // packed entries per table
     const uint64_t per_row = (msd ? width * 8 : n * 24) + sort_hist_entries(1, n, dbits) * 4 + (2 * nd + 1) * 4 + 64;
     uint64_t rows = std::max<uint64_t>(1, budget / per_row);
     rows = std::min<uint64_t>(rows, L);

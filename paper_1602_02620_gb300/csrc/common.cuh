@@ -408,8 +408,8 @@ size_t sort_keys_hist_entries(uint64_t cap);
 // and the entries (the same buckets as radix_sort_rows + finalize).  Exact form:
 // msd_partition_hist (histogram + scan into buf.hist, sized sort_hist_entries(rows,
 // len, dbits)), msd_partition_scatter with cap = 0.  Histogram-free form: msd_partition_scatter with
-// cap = msd_bin_capacity(len, dbits) into bins of buf.keys_a (rows * 2^dbits * cap
-// entries); valid
+// cap = msd_bin_capacity(len, dbits) into bins of buf.keys_a (rows * (2^dbits * cap +
+// msd_bin0_extra(len)) entries); valid
 // when *buf.status reads 0 afterwards, else redo the tables the exact way.  Then
 // msd_finish with the same cap; it needs big_cnt [1] and big [rows * 2^dbits] of
 // scratch for segments longer than 4096, seg_out [rows * (2^dbits + 1)] and bin_cnt
@@ -426,6 +426,20 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
 // capacity of the histogram-free partition for rows of n entries.
 uint32_t msd_dbits(uint32_t slot_bits);
 uint32_t msd_bin_capacity(uint64_t n, uint32_t dbits);
+// Bin 0 of every row holds msd_bin0_extra(n) entries more than the others: key 0, the empty
+// sum of a point with no set coordinate on the table's code row (the common bucket of sparse
+// points), lies in slot 0, so in segment 0.
+uint32_t msd_bin0_extra(uint64_t n);
+// Bins of a row: bin d starts at bin_start(d) and holds bin_capacity(d) entries; a row holds
+// 2^dbits * cap + extra0.
+__host__ __device__ __forceinline__ uint64_t bin_start(uint32_t d, uint32_t cap, uint32_t extra0)
+{
+    return d ? (uint64_t)d * cap + extra0 : 0;
+}
+__host__ __device__ __forceinline__ uint32_t bin_capacity(uint32_t d, uint32_t cap, uint32_t extra0)
+{
+    return d ? cap : cap + extra0;
+}
 // Directory of each sorted row: ent = (key >> sb) << 32 | id, offs[slot] = first entry of slot.
 cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint32_t rows, uint64_t len,
                                  uint32_t slot_bits, uint64_t *ent, uint32_t *offs, cudaStream_t s);

@@ -43,7 +43,8 @@ struct RadixArgs {
     uint32_t rows;
     uint32_t pack_sb;             // partition kernels: slot bits of the directory
     uint32_t pack_idbits;         // partition kernels: bits of an id
-    uint32_t cap;                 // partition_scatter_kernel: 0 = places from hist; else bins of cap entries
+    uint32_t cap;                 // partition kernels: 0 = places from hist; else bins of cap entries
+    uint32_t extra0;              //   (bin 0: cap + extra0; a row's bins: 2^D * cap + extra0)
     uint32_t *bin_cnt;            //   [rows][256] entries reserved in each bin (cap > 0)
     uint32_t *status;             //   bit 0 set when a bin overflowed (cap > 0)
     uint64_t out_cap = 0;         // partition kernels: entries keys_out holds (bounds of the checked build)
@@ -269,8 +270,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_scatter_kernel(Radi
                 cursor += c;
             } else {
                 const uint32_t at = c ? atomicAdd(a.bin_cnt + (uint64_t)row * 256 + tid, c) : 0u;
-                if (at + c <= a.cap) {
-                    gofs[tid] = (uint32_t)(((uint64_t)row * 256 + tid) * a.cap + at) - start;
+                if (at + c <= bin_capacity(tid, a.cap, a.extra0)) {
+                    gofs[tid] = (uint32_t)((uint64_t)row * (256ull * a.cap + a.extra0) + bin_start(tid, a.cap, a.extra0) +
+                                           at) - start;
                 } else {
                     gofs[tid] = 0xFFFFFFFFu;   // dropped: the bin is full
                     atomicOr(a.status, 1u);
@@ -382,8 +384,8 @@ __global__ void __launch_bounds__(kWideThreads, 2) partition_wide_kernel(RadixAr
         }
         const uint32_t c = cnt[d];
         const uint32_t at = c ? atomicAdd(a.bin_cnt + (uint64_t)row * ND + d, c) : 0u;
-        if (at + c <= a.cap) {
-            gofs[d] = (uint32_t)(((uint64_t)row * ND + d) * a.cap + at);
+        if (at + c <= bin_capacity(d, a.cap, a.extra0)) {
+            gofs[d] = (uint32_t)((uint64_t)row * ((uint64_t)ND * a.cap + a.extra0) + bin_start(d, a.cap, a.extra0) + at);
         } else {
             gofs[d] = 0xFFFFFFFFu;   // dropped: the bin is full
             atomicOr(a.status, 1u);
@@ -579,7 +581,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(const uint64_t *__restric
 
 constexpr int kSegThreads = 512;
 constexpr int kSegItems = 4;                          // entries per thread in flight per round
-constexpr int kSegWarps = kSegThreads / 32;
 constexpr int kSubMaxBits = 12;                       // slot bits below the partition digit
 
 // One shared-memory atomic add of 1 per lane on cnt[j], aggregated over the lanes of the
@@ -680,9 +681,10 @@ __global__ void __launch_bounds__(256) segment_bounds_kernel(const uint32_t *__r
 // entries are written with coalesced stores.  Larger segments are listed for
 // segment_finish_kernel.
 // Segment (row, g) of the partition: seg_out[row][g] .. seg_out[row][g+1] in the row's
-// directory entries; its packed input starts at row * in_stride + (cap ? g * cap : seg_out[row][g]).
+// directory entries; its packed input starts at row * in_stride + (cap ? bin_start(g) : seg_out[row][g]).
 __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint64_t *__restrict__ packed, uint64_t n,
-                                                                     uint64_t in_stride, uint32_t cap, uint32_t sb,
+                                                                     uint64_t in_stride, uint32_t cap, uint32_t extra0,
+                                                                     uint32_t sb,
                                                                      uint32_t idbits, uint32_t dbits,
                                                                      const uint32_t *__restrict__ seg_out,
                                                                      uint64_t *__restrict__ ent,
@@ -706,7 +708,7 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
     const uint32_t cn = len;
     if (!FCLSH_CHECK((uint64_t)lo + cn <= n, 0x0303)) return;   // block-uniform, before any barrier
     const uint64_t rowbase = (uint64_t)row * n;
-    const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)lo);
+    const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? bin_start(g, cap, extra0) : (uint64_t)lo);
     uint64_t *E = ent + rowbase + lo;
     uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;   // 16-byte aligned (nsub >= 8)
     if (g == nd - 1 && tid == 0) O[nsub] = (uint32_t)n;
@@ -789,6 +791,7 @@ __global__ void __launch_bounds__(kOneThreads, 3) segment_one_kernel(const uint6
 // take consecutive places, so the heavy slot is written with coalesced stores.
 __global__ void __launch_bounds__(kSegThreads, 3) segment_finish_kernel(const uint64_t *__restrict__ packed,
                                                                         uint64_t n, uint64_t in_stride, uint32_t cap,
+                                                                        uint32_t extra0,
                                                                         uint32_t sb, uint32_t idbits, uint32_t dbits,
                                                                         const uint32_t *__restrict__ seg_out,
                                                                         uint64_t *__restrict__ ent,
@@ -809,7 +812,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) segment_finish_kernel(const ui
         const uint32_t seg_lo = seg_out[(uint64_t)row * (nd + 1) + g], seg_hi = seg_out[(uint64_t)row * (nd + 1) + g + 1];
         const uint64_t seg_len = seg_hi - seg_lo;
         if (!FCLSH_CHECK((uint64_t)seg_lo + seg_len <= n && seg_lo <= seg_hi, 0x0306)) return;   // block-uniform
-        const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? (uint64_t)g * cap : (uint64_t)seg_lo);
+        const uint64_t *Pk = packed + (uint64_t)row * in_stride + (cap ? bin_start(g, cap, extra0) : (uint64_t)seg_lo);
         uint64_t *E = ent + (uint64_t)row * n + seg_lo;
         uint32_t *O = offs + (uint64_t)row * dir_stride(sb) + (uint64_t)g * nsub;
         if (g == nd - 1 && tid == 0) O[nsub] = (uint32_t)n;
@@ -1023,9 +1026,10 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
     if (e != cudaSuccess) return e;
     const uint32_t dbits = msd_dbits(sb);
     const uint32_t tiles = msd_tiles(len, dbits);
+    const uint32_t extra0 = cap ? msd_bin0_extra(len) : 0u;
     RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - dbits, (1u << dbits) - 1, buf.hist,
-                rows, sb, id_bits(len), cap, buf.bin_cnt, buf.status};
-    a.out_cap = (uint64_t)rows * (cap ? ((uint64_t)1 << dbits) * cap : len);
+                rows, sb, id_bits(len), cap, extra0, buf.bin_cnt, buf.status};
+    a.out_cap = (uint64_t)rows * (cap ? ((uint64_t)1 << dbits) * cap + extra0 : len);
     if (cap) {
         if ((e = cudaMemsetAsync(buf.bin_cnt, 0, ((size_t)rows << dbits) * 4, s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(buf.status, 0, 4, s)) != cudaSuccess) return e;
@@ -1084,16 +1088,17 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
     if (reinterpret_cast<uintptr_t>(offs) & 15) return cudaErrorMisalignedAddress;   // vector stores of offsets
     const uint32_t tiles = msd_tiles(len, dbits);
     const uint32_t idb = id_bits(len);
-    const uint64_t in_stride = cap ? ((uint64_t)1 << dbits) * cap : len;
+    const uint32_t extra0 = cap ? msd_bin0_extra(len) : 0u;
+    const uint64_t in_stride = cap ? ((uint64_t)1 << dbits) * cap + extra0 : len;
     segment_bounds_kernel<<<rows, 256, 0, s>>>(buf.hist, tiles, len, cap ? buf.bin_cnt : nullptr, dbits, buf.seg_out);
     note_launch();
     cudaError_t e = cudaMemsetAsync(big_cnt, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     segment_one_kernel<<<dim3(1u << dbits, rows), kOneThreads, segment_one_smem(), s>>>(
-        buf.keys_a, len, in_stride, cap, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
+        buf.keys_a, len, in_stride, cap, extra0, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
     note_launch();
     segment_finish_kernel<<<3 * sm_count, kSegThreads, 0, s>>>(
-        buf.keys_a, len, in_stride, cap, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
+        buf.keys_a, len, in_stride, cap, extra0, sb, idb, dbits, buf.seg_out, ent, offs, big_cnt, big);
     note_launch();
     return cudaGetLastError();
 }
@@ -1104,6 +1109,8 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
 // its fullest bins run ~10 standard deviations over the mean), and a margin.  Bins
 // still overflow when a few keys carry a large share of a table (e.g. the empty sum
 // of sparse points); those tables take the exact histogram path.
+uint32_t msd_bin0_extra(uint64_t n) { return (uint32_t)((n / 16 + 3) & ~3ULL); }
+
 uint32_t msd_bin_capacity(uint64_t n, uint32_t dbits)
 {
     const double mean = (double)n / (double)(1u << dbits);

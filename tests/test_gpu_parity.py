@@ -417,6 +417,36 @@ def test_wide_partition_directory_matches_oracle(slot_bits, skewed):
     idx.free()
 
 
+@pytest.mark.parametrize("zeros", [850, 1300])
+def test_empty_sum_bucket_in_bin_zero(zeros):
+    """All-zero points have key 0 (the empty sum) in every table, so they all land in slot 0,
+    partition bin 0 (2^14 slots: four bins of ~1,250 entries, capacity 1,756, and bin 0 312 more):
+    with 850 of 5,000 it holds ~1,890 entries, which fit only in the larger bin 0 (the partition
+    stays histogram-free); with 1,300, ~2,225 do not (the exact fallback).  Both directories hold the oracle's buckets, and queries over them match
+    the oracle."""
+    rng = np.random.default_rng(zeros)
+    d, r, n = 128, 6, 5000
+    pts = rand_points(rng, n, d)
+    pts[rng.choice(n, size=zeros, replace=False)] = 0
+    seed = 321
+    p = oracle.derive_params(seed, d, r)
+    idx = F().build(dev(pts), d, r, seed, slot_bits=14)
+    for tau in sorted({0, 2, p.T - 1}):
+        keys, ids = idx.export_table(tau)
+        order = np.lexsort((ids, keys))
+        ok, oi = oracle.table(p, pts, tau)
+        assert np.array_equal(keys[order], ok) and np.array_equal(ids[order], oi)
+        assert np.array_equal(idx.bucket(tau, 0), oi[ok == 0]) and (ok == 0).sum() >= zeros
+    qs = np.concatenate([near(rng, pts, d, r, 20), np.zeros((2, pts.shape[1]), np.uint64)])
+    tables = oracle.build_tables(p, pts)
+    res = idx.query(dev(qs), r)
+    for i in range(qs.shape[0]):
+        want, ncoll, ncand = oracle.query(p, pts, tables, qs[i], r)
+        assert np.array_equal(res.of(i), want)
+        assert (int(res.collisions[i]), int(res.candidates[i])) == (ncoll, ncand)
+    idx.free()
+
+
 @pytest.mark.parametrize("skewed", [False, True])
 def test_long_segments_match_oracle(skewed):
     """Segments longer than one block's 4,608 entries (2^13 slots in two segments of ~15,000
