@@ -1000,6 +1000,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     // empty-sum bucket of sparse points) loses one table's partition, not a chunk's.
     bool use_bins = msd;
     bool bins_tried = false;
+    std::vector<uint32_t> fill(msd ? nd : 0);   // the trial table's bin fills
 
     for (uint32_t k = 0; k < t; ++k) {
         {
@@ -1021,9 +1022,15 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
                     }
                     uint32_t status = 0;
                     FCLSH_CUDA(cudaMemcpyAsync(&status, sbuf.status, 4, cudaMemcpyDeviceToHost, s));
+                    if (!bins_tried) FCLSH_CUDA(cudaMemcpyAsync(fill.data(), sbuf.bin_cnt, nd * 4, cudaMemcpyDeviceToHost, s));
                     FCLSH_CUDA(cudaStreamSynchronize(s));
                     binned = status == 0;
                     use_bins = binned;
+                    if (!bins_tried) {   // the single-table trial: a bin filled past 7/8 would overflow in some
+                        const uint32_t x0 = msd_bin0_extra(n);   // other table, so go the exact way at once
+                        for (uint64_t dg = 0; dg < nd && use_bins; ++dg)
+                            if ((uint64_t)fill[dg] * 8 > (uint64_t)bin_capacity((uint32_t)dg, cap, x0) * 7) use_bins = false;
+                    }
                     bins_tried = true;
                 }
                 if (!binned) {

@@ -417,20 +417,20 @@ def test_wide_partition_directory_matches_oracle(slot_bits, skewed):
     idx.free()
 
 
-@pytest.mark.parametrize("zeros", [850, 1300])
+@pytest.mark.parametrize("zeros", [1300, 3000])
 def test_empty_sum_bucket_in_bin_zero(zeros):
     """All-zero points have key 0 (the empty sum) in every table, so they all land in slot 0,
-    partition bin 0 (2^14 slots: four bins of ~1,250 entries, capacity 1,756, and bin 0 312 more):
-    with 850 of 5,000 it holds ~1,890 entries, which fit only in the larger bin 0 (the partition
-    stays histogram-free); with 1,300, ~2,225 do not (the exact fallback).  Both directories hold the oracle's buckets, and queries over them match
-    the oracle."""
+    partition bin 0 (2^15 slots: eight bins of ~2,500 entries, capacity 3,276, and bin 0 1,252
+    more): with 1,300 of 20,000 it holds ~3,640 entries, which fit only in the larger bin 0 (and stay
+    below 7/8 of it: the partition stays histogram-free); with 3,000, ~5,125 do not (the exact
+    fallback).  Both directories hold the oracle's buckets, and queries over them match the oracle."""
     rng = np.random.default_rng(zeros)
-    d, r, n = 128, 6, 5000
+    d, r, n = 128, 6, 20_000
     pts = rand_points(rng, n, d)
     pts[rng.choice(n, size=zeros, replace=False)] = 0
     seed = 321
     p = oracle.derive_params(seed, d, r)
-    idx = F().build(dev(pts), d, r, seed, slot_bits=14)
+    idx = F().build(dev(pts), d, r, seed, slot_bits=15)
     for tau in sorted({0, 2, p.T - 1}):
         keys, ids = idx.export_table(tau)
         order = np.lexsort((ids, keys))
