@@ -997,10 +997,14 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     // A row chunk whose bins overflow (skewed keys) is partitioned again the exact way,
     // with a per-tile digit histogram, and the remaining chunks go that way at once.  The
     // first binned chunk is a single table, so that data whose every table overflows (the
-    // empty-sum bucket of sparse points) loses one table's partition, not a chunk's.
+    // empty-sum bucket of sparse points) loses one table's partition, not a chunk's.  Its bin
+    // fills size the bins of the other tables: where a bin filled past 7/8 of its room, the
+    // bins become 5/4 of the fullest (fewer tables per chunk in the same buffer).
     bool use_bins = msd;
     bool bins_tried = false;
     std::vector<uint32_t> fill(msd ? nd : 0);   // the trial table's bin fills
+    uint32_t bcap = cap, bx0 = msd ? msd_bin0_extra(n) : 0;   // the bins: bin 0 holds bcap + bx0
+    uint64_t brows = rows;                                    // tables per binned chunk
 
     for (uint32_t k = 0; k < t; ++k) {
         {
@@ -1011,14 +1015,15 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
         NvtxRange ns("fclsh_build: bucket tables of the part");
         PhaseTimer pt(idx, 1, s);
         for (uint64_t r0 = 0; r0 < L;) {
-            const uint32_t nr = (uint32_t)std::min<uint64_t>(msd && use_bins && !bins_tried ? 1 : rows, L - r0);
+            const uint32_t nr =
+                (uint32_t)std::min<uint64_t>(msd && use_bins ? (bins_tried ? brows : 1) : rows, L - r0);
             const uint64_t grow = (uint64_t)k * L + r0;
             if (msd) {
                 bool binned = false;
                 if (use_bins) {
                     {
                         PhaseTimer p5(idx, 5, s);
-                        FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, cap, sbuf, s));
+                        FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, bcap, bx0, sbuf, s));
                     }
                     uint32_t status = 0;
                     FCLSH_CUDA(cudaMemcpyAsync(&status, sbuf.status, 4, cudaMemcpyDeviceToHost, s));
@@ -1026,10 +1031,27 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
                     FCLSH_CUDA(cudaStreamSynchronize(s));
                     binned = status == 0;
                     use_bins = binned;
-                    if (!bins_tried) {   // the single-table trial: a bin filled past 7/8 would overflow in some
-                        const uint32_t x0 = msd_bin0_extra(n);   // other table, so go the exact way at once
-                        for (uint64_t dg = 0; dg < nd && use_bins; ++dg)
-                            if ((uint64_t)fill[dg] * 8 > (uint64_t)bin_capacity((uint32_t)dg, cap, x0) * 7) use_bins = false;
+                    if (!bins_tried && use_bins) {   // the single-table trial
+                        bool tight = false;
+                        uint64_t most = 0;
+                        for (uint64_t dg = 0; dg < nd; ++dg) {
+                            tight = tight || (uint64_t)fill[dg] * 8 > (uint64_t)bin_capacity((uint32_t)dg, bcap, bx0) * 7;
+                            if (dg) most = std::max<uint64_t>(most, fill[dg]);
+                        }
+                        if (tight) {
+                            const uint64_t c2 = std::max<uint64_t>(bcap, ((most * 5 / 4 + 64) + 3) & ~3ULL);
+                            const uint64_t b0 = ((uint64_t)fill[0] * 5 / 4 + 64 + 3) & ~3ULL;
+                            const uint64_t x2 = std::max<uint64_t>(bx0, b0 > c2 ? b0 - c2 : 0);
+                            const uint64_t w2 = nd * c2 + x2;
+                            const uint64_t r2 = rows * width / w2;   // the same buffer, fewer tables
+                            if (r2 >= 1 && c2 < (1ULL << 31) && x2 < (1ULL << 31)) {
+                                bcap = (uint32_t)c2;
+                                bx0 = (uint32_t)x2;
+                                brows = r2;
+                            } else {
+                                use_bins = false;
+                            }
+                        }
                     }
                     bins_tried = true;
                 }
@@ -1039,10 +1061,10 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
                         FCLSH_CUDA(msd_partition_hist(keys + r0 * n, nr, n, sb, sbuf, s));
                     }
                     PhaseTimer p5(idx, 5, s);
-                    FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, 0, sbuf, s));
+                    FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, 0, 0, sbuf, s));
                 }
                 PhaseTimer p6(idx, 6, s);
-                FCLSH_CUDA(msd_finish(nr, n, sb, binned ? cap : 0, sbuf, big_cnt, big, idx->ent + grow * n,
+                FCLSH_CUDA(msd_finish(nr, n, sb, binned ? bcap : 0, binned ? bx0 : 0, sbuf, big_cnt, big, idx->ent + grow * n,
                                       idx->offs + grow * idx->offs_stride(), idx->sm_count, s));
                 r0 += nr;
                 continue;

@@ -408,8 +408,8 @@ size_t sort_keys_hist_entries(uint64_t cap);
 // and the entries (the same buckets as radix_sort_rows + finalize).  Exact form:
 // msd_partition_hist (histogram + scan into buf.hist, sized sort_hist_entries(rows,
 // len, dbits)), msd_partition_scatter with cap = 0.  Histogram-free form: msd_partition_scatter with
-// cap = msd_bin_capacity(len, dbits) into bins of buf.keys_a (rows * (2^dbits * cap +
-// msd_bin0_extra(len)) entries); valid
+// cap = msd_bin_capacity(len, dbits) (or larger) into bins of buf.keys_a (rows * (2^dbits * cap +
+// extra0) entries, extra0 = msd_bin0_extra(len) or more: bin_start, bin_capacity); valid
 // when *buf.status reads 0 afterwards, else redo the tables the exact way.  Then
 // msd_finish with the same cap; it needs big_cnt [1] and big [rows * 2^dbits] of
 // scratch for segments longer than 4096, seg_out [rows * (2^dbits + 1)] and bin_cnt
@@ -418,8 +418,8 @@ bool msd_path_applies(uint32_t slot_bits, uint64_t n);
 cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, SortBuffers &buf,
                                cudaStream_t s);
 cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap,
-                                  SortBuffers &buf, cudaStream_t s);
-cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, SortBuffers &buf,
+                                  uint32_t extra0, SortBuffers &buf, cudaStream_t s);
+cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, uint32_t extra0, SortBuffers &buf,
                        unsigned long long *big_cnt, uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count,
                        cudaStream_t s);
 // Partition digit bits for slot_bits (slot_bits - 12: segments of 4,096 slots) and the bin

@@ -1020,13 +1020,13 @@ cudaError_t msd_partition_hist(const uint64_t *keys_in, uint32_t rows, uint64_t 
 // places from the scanned histogram (cap = 0), or into bins of
 // cap entries per (row, digit) (no histogram; buf.status bit 0 reports a full bin).
 cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap,
-                                  SortBuffers &buf, cudaStream_t s)
+                                  uint32_t extra0, SortBuffers &buf, cudaStream_t s)
 {
     cudaError_t e = scatter_smem_init();
     if (e != cudaSuccess) return e;
     const uint32_t dbits = msd_dbits(sb);
     const uint32_t tiles = msd_tiles(len, dbits);
-    const uint32_t extra0 = cap ? msd_bin0_extra(len) : 0u;
+    if (!cap) extra0 = 0;
     RadixArgs a{keys_in, nullptr, buf.keys_a, nullptr, len, nullptr, tiles, sb - dbits, (1u << dbits) - 1, buf.hist,
                 rows, sb, id_bits(len), cap, extra0, buf.bin_cnt, buf.status};
     a.out_cap = (uint64_t)rows * (cap ? ((uint64_t)1 << dbits) * cap + extra0 : len);
@@ -1075,7 +1075,7 @@ cudaError_t msd_partition_scatter(const uint64_t *keys_in, uint32_t rows, uint64
     return cudaGetLastError();
 }
 
-cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, SortBuffers &buf,
+cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, uint32_t extra0, SortBuffers &buf,
                        unsigned long long *big_cnt, uint32_t *big, uint64_t *ent, uint32_t *offs, int sm_count,
                        cudaStream_t s)
 {
@@ -1088,7 +1088,7 @@ cudaError_t msd_finish(uint32_t rows, uint64_t len, uint32_t sb, uint32_t cap, S
     if (reinterpret_cast<uintptr_t>(offs) & 15) return cudaErrorMisalignedAddress;   // vector stores of offsets
     const uint32_t tiles = msd_tiles(len, dbits);
     const uint32_t idb = id_bits(len);
-    const uint32_t extra0 = cap ? msd_bin0_extra(len) : 0u;
+    if (!cap) extra0 = 0;
     const uint64_t in_stride = cap ? ((uint64_t)1 << dbits) * cap + extra0 : len;
     segment_bounds_kernel<<<rows, 256, 0, s>>>(buf.hist, tiles, len, cap ? buf.bin_cnt : nullptr, dbits, buf.seg_out);
     note_launch();

@@ -417,13 +417,15 @@ def test_wide_partition_directory_matches_oracle(slot_bits, skewed):
     idx.free()
 
 
-@pytest.mark.parametrize("zeros", [1300, 3000])
+@pytest.mark.parametrize("zeros", [1300, 2000, 3000])
 def test_empty_sum_bucket_in_bin_zero(zeros):
     """All-zero points have key 0 (the empty sum) in every table, so they all land in slot 0,
     partition bin 0 (2^15 slots: eight bins of ~2,500 entries, capacity 3,276, and bin 0 1,252
-    more): with 1,300 of 20,000 it holds ~3,640 entries, which fit only in the larger bin 0 (and stay
-    below 7/8 of it: the partition stays histogram-free); with 3,000, ~5,125 do not (the exact
-    fallback).  Both directories hold the oracle's buckets, and queries over them match the oracle."""
+    more): with 1,300 of 20,000 it holds ~3,640 entries, which fit only in the larger bin 0 and stay
+    below 7/8 of it (every table histogram-free in those bins); with 2,000, ~4,250 fit the trial
+    table but pass 7/8, so the other tables get a bin 0 sized from the trial's fill; with 3,000,
+    ~5,125 overflow the trial (the exact fallback).  Every directory holds the oracle's buckets, and
+    queries over it match the oracle."""
     rng = np.random.default_rng(zeros)
     d, r, n = 128, 6, 20_000
     pts = rand_points(rng, n, d)
