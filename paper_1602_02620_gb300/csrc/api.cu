@@ -1020,10 +1020,11 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
             const uint64_t grow = (uint64_t)k * L + r0;
             if (msd) {
                 bool binned = false;
+                const uint32_t ccap = bcap, cx0 = bx0;   // this chunk's bins (the trial may resize later ones)
                 if (use_bins) {
                     {
                         PhaseTimer p5(idx, 5, s);
-                        FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, bcap, bx0, sbuf, s));
+                        FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, ccap, cx0, sbuf, s));
                     }
                     uint32_t status = 0;
                     FCLSH_CUDA(cudaMemcpyAsync(&status, sbuf.status, 4, cudaMemcpyDeviceToHost, s));
@@ -1064,7 +1065,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
                     FCLSH_CUDA(msd_partition_scatter(keys + r0 * n, nr, n, sb, 0, 0, sbuf, s));
                 }
                 PhaseTimer p6(idx, 6, s);
-                FCLSH_CUDA(msd_finish(nr, n, sb, binned ? bcap : 0, binned ? bx0 : 0, sbuf, big_cnt, big, idx->ent + grow * n,
+                FCLSH_CUDA(msd_finish(nr, n, sb, binned ? ccap : 0, binned ? cx0 : 0, sbuf, big_cnt, big, idx->ent + grow * n,
                                       idx->offs + grow * idx->offs_stride(), idx->sm_count, s));
                 r0 += nr;
                 continue;
