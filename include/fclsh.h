@@ -160,8 +160,9 @@ typedef struct {
                                  dependent load costs more than the point reads it saves). */
     uint32_t heavy_kernel;    /* very heavy queries (more bucket entries than the n-bit bitmap has 32-bit
                                  words): 0 = the batch kernel marks them in its bitmap in global memory
-                                 and sweeps it; 1 = a second kernel (one CTA per SM) answers them,
-                                 marking their bucket entries in a window of ids held in shared memory,
+                                 and sweeps it; 1 = a second kernel (one CTA per SM) answers them; 2 = it
+                                 also answers every query past the shared-memory dedup set.  1 and 2
+                                 mark the bucket entries in a window of ids held in shared memory,
                                  one window after another, as large as shared memory allows; k >= 64 =
                                  the same with windows of at most k ids (rounded down to a multiple of 64;
                                  never below 64*W) and lists of 4 windows' ids for the collisions past

@@ -556,6 +556,7 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
         a.win_bits = c->win_bits;
         a.spill = c->spill;
         a.spill_cap = c->spill_cap;
+        a.heavy_from_bitmap = idx->tune.heavy_kernel == 2;
     }
     if (idx->classic_k) {   // S1 of classic LSH: the queries' keys by the classic hash kernel
         const uint32_t L = idx->W - 1;
@@ -1691,7 +1692,7 @@ extern "C" fclsh_status fclsh_set_tuning(fclsh_index *idx, const fclsh_tuning *t
     }
     if (t->probe_rows > 1) return fail(FCLSH_EINVAL, "probe_rows must be 0 or 1");
     if (t->verify_filter > 1) return fail(FCLSH_EINVAL, "verify_filter must be 0 or 1");
-    if (t->heavy_kernel > 1 && t->heavy_kernel < 64) return fail(FCLSH_EINVAL, "heavy_kernel must be 0, 1 or >= 64");
+    if (t->heavy_kernel > 2 && t->heavy_kernel < 64) return fail(FCLSH_EINVAL, "heavy_kernel must be 0, 1, 2 or >= 64");
     if (idx->classic_k && (t->hash_tile || t->probe_rows))
         return fail(FCLSH_EINVAL, "a classic LSH index has one hash kernel and no row rule (hash_tile, probe_rows = 0)");
     if (idx->classic_k) {
@@ -2161,8 +2162,8 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
     }
     // very heavy queries by the second kernel or by the batch kernel's own sweep
     if (st == FCLSH_OK) {
-        float ms_h[2] = {1e30f, 1e30f};
-        for (uint32_t hk = 0; hk <= 1; ++hk) {
+        float ms_h[3] = {1e30f, 1e30f, 1e30f};
+        for (uint32_t hk = 0; hk <= 2; ++hk) {
             fclsh_tuning t = best;
             t.use_graph = 0;
             t.heavy_kernel = hk;
@@ -2175,7 +2176,10 @@ extern "C" fclsh_status fclsh_autotune(fclsh_index *idx, const uint64_t *queries
             if (fclsh_qctx_wait(c, nullptr) != FCLSH_OK) continue;
             cudaEventElapsedTime(&ms_h[hk], e0, e1);
         }
-        if (ms_h[0] < 1e30f || ms_h[1] < 1e30f) best.heavy_kernel = ms_h[1] <= ms_h[0] ? 1u : 0u;
+        uint32_t hbest = 1;   // the default unless a measured setting beats it
+        for (uint32_t hk = 0; hk <= 2; ++hk)
+            if (ms_h[hk] < ms_h[hbest]) hbest = hk;
+        if (ms_h[hbest] < 1e30f) best.heavy_kernel = hbest;
         idx->tune = best;
     }
     // the hash kernel: WHT tiles and the tensor-core contraction on the index's first points

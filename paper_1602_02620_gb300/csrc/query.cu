@@ -719,7 +719,8 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
         // more bucket entries than bitmap words: mark the bitmap and sweep it once
         const bool sweep_mode = bitmap_mode && E > a.bm_words;
         const int mode = sweep_mode ? DEDUP_MARK : (bitmap_mode ? DEDUP_BITMAP : DEDUP_HSET);
-        if (sweep_mode && a.heavy_q && E <= kHeavyMaxEntries) {   // block-uniform: query_heavy_kernel answers it
+        if ((a.heavy_from_bitmap ? bitmap_mode : sweep_mode) && a.heavy_q &&
+            E <= kHeavyMaxEntries) {   // block-uniform: query_heavy_kernel answers it
             if (tid == 0) a.heavy_q[atomicAdd(a.heavy_n, 1ULL)] = qi;
             __syncthreads();
             continue;

@@ -348,13 +348,14 @@ def test_autotune_choices_keep_results(tmp_path):
     idx.free()
 
 
-@pytest.mark.parametrize("hlog,heavy", [(10, 0), (13, 0), (10, 1), (13, 1024)])
+@pytest.mark.parametrize("hlog,heavy", [(10, 0), (13, 0), (10, 1), (13, 1024), (11, 2)])
 def test_dedup_modes_match_oracle(hlog, heavy):
     """Queries in every dedup mode -- shared-memory set, returning bitmap, mark-and-sweep
     bitmap (bucket entries beyond the bitmap's word count), and more than 4,096 hits --
     report the oracle's ids and counters.  The very heavy queries are answered by the batch
     kernel's own sweep (heavy = 0) or by the heavy-query kernel, in one shared-memory window
-    of ids (1) or in nine windows of 1,024 ids with a ragged last one (1024 = 64 W)."""
+    of ids (1) or in nine windows of 1,024 ids with a ragged last one (1024 = 64 W); with heavy = 2
+    the heavy-query kernel also answers the bitmap-mode queries."""
     rng = np.random.default_rng(hlog)
     d, r, n = 64, 3, 9000
     pts = rand_points(rng, n, d)
@@ -550,7 +551,7 @@ def test_signature_filter_keeps_ids_and_counters(d, r, n, density):
     for radius in (r, r // 2):
         want = [oracle.query(p, pts, tables, q, radius) for q in qs]
         assert sum(len(w[0]) for w in want) > 0
-        for vf, hk in ((1, 1), (0, 1), (1, 0)):
+        for vf, hk in ((1, 1), (0, 1), (1, 0), (1, 2)):
             idx.set_tuning(verify_filter=vf, heavy_kernel=hk)
             for res in (idx.query(dev(qs), radius), idx.query_plain(qs, radius)):
                 for i, (ids, ncoll, ncand) in enumerate(want):
