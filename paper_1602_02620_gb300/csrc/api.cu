@@ -841,6 +841,7 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     std::vector<uint64_t> sc_bv;
     if (!classic) coord_lists(d, t, W, idx->perm, idx->part_off, idx->m, idx->b, sc_off, sc_col, sc_bv, &idx->sc_pop);
     const bool scatter_fits = idx->sc_pop <= kScatterMaxPop;
+    idx->sc_stage = !classic && scatter_stage_bytes(d, max_dk) <= kScatterStageMaxBytes;
     if (!classic && o.hash_tile < 2 && hash_smem_bytes(W, max_dk, o.hash_tile) > idx->smem_optin) {
         // the part's column lists do not fit in shared memory: sketch by scattering set bits
         if (!scatter_fits)

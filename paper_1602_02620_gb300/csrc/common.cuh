@@ -107,7 +107,17 @@ struct CoordLists {
     const uint32_t *pidx = nullptr;
     const uint64_t *pstart = nullptr;
     const uint32_t *plen = nullptr;
+    // the part's positions are col/b [pos0, pos0 + npos); stage = 1: a hash block first copies
+    // the part's lists into shared memory (scatter_stage_bytes)
+    uint32_t pos0 = 0, npos = 0, stage = 0;
 };
+
+// Shared memory of a part's staged coordinate lists: seed values, columns, offsets.
+__host__ __device__ __forceinline__ size_t scatter_stage_bytes(uint32_t d, uint32_t npos)
+{
+    return (((size_t)npos * 8 + 15) & ~(size_t)15) + (((size_t)npos * 4 + 15) & ~(size_t)15) + ((size_t)d + 1) * 4;
+}
+constexpr size_t kScatterStageMaxBytes = 32 * 1024;
 
 struct PhaseTimer;
 
@@ -262,6 +272,7 @@ struct fclsh_index {
     uint32_t *sc_off = nullptr, *sc_col = nullptr;
     uint64_t *sc_b = nullptr;
     uint32_t sc_pop = 0;
+    uint32_t sc_stage = 0;           // 1: a part's coordinate lists fit the hash blocks' shared memory
     uint32_t *offs = nullptr;        // [T][dir_stride(slot_bits)]: 2^slot_bits + 1 used
     uint64_t *ent = nullptr;         // [T][n]: (key >> slot_bits) << 32 | id
     // tensor-core hash (hash_tile 2): padded coordinates per part, their lists [t][mma_k]
@@ -300,7 +311,11 @@ struct fclsh_index {
     }
     fclsh::CoordLists coords(uint32_t k) const
     {
-        return fclsh::CoordLists{sc_off + (size_t)k * (d + 1), sc_col, sc_b, d};
+        fclsh::CoordLists cl{sc_off + (size_t)k * (d + 1), sc_col, sc_b, d};
+        cl.pos0 = part_off[k];
+        cl.npos = part_off[k + 1] - part_off[k];
+        cl.stage = sc_stage;
+        return cl;
     }
     bool scatter_ok() const { return sc_b != nullptr && sc_pop <= fclsh::kScatterMaxPop; }
 };

@@ -430,24 +430,55 @@ __device__ __forceinline__ void phase(uint64_t *sm, const uint64_t *S_sm, unsign
 // their columns with shared-memory atomics.
 template <int NP, uint32_t M>
 __device__ __forceinline__ void scatter_sketch(uint64_t *sm, uint32_t W, const uint64_t *__restrict__ pts,
-                                               uint64_t cnt, uint32_t words, uint64_t p0, const CoordLists &cl)
+                                               uint64_t cnt, uint32_t words, uint64_t p0, CoordLists cl,
+                                               unsigned char *stage)
 {
     for (uint32_t i = threadIdx.x; i < W * (uint32_t)NP; i += blockDim.x) sm[i] = 0ULL;
+    if (cl.stage) {   // the part's lists into shared memory: the set bits' lookups stay on chip
+        uint64_t *s_b = reinterpret_cast<uint64_t *>(stage);
+        uint32_t *s_col = reinterpret_cast<uint32_t *>(stage + (((size_t)cl.npos * 8 + 15) & ~(size_t)15));
+        uint32_t *s_off = s_col + ((cl.npos + 3) & ~3u);
+        for (uint32_t i = threadIdx.x; i < cl.npos; i += blockDim.x) {
+            s_b[i] = __ldg(cl.b + cl.pos0 + i);
+            s_col[i] = __ldg(cl.col + cl.pos0 + i);
+        }
+        for (uint32_t i = threadIdx.x; i <= cl.d; i += blockDim.x) s_off[i] = __ldg(cl.off + i) - cl.pos0;
+        cl.b = s_b;
+        cl.col = s_col;
+        cl.off = s_off;
+    }
     __syncthreads();
     const uint64_t real = cnt - p0 < (uint64_t)NP ? cnt - p0 : (uint64_t)NP;
-    if (cl.pidx) {   // the points' set coordinates are listed: threads take them point by point
-        for (uint32_t p = 0; p < (uint32_t)real; ++p) {
-            const uint32_t *ci = cl.pidx + cl.pstart[p0 + p];
-            const uint32_t len = cl.plen[p0 + p];
-            for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
-                const uint32_t c = ci[j];
-                const uint32_t e1 = __ldg(cl.off + c + 1);
-                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e) {
-                    const uint32_t col = __ldg(cl.col + e);
-                    if (FCLSH_CHECK(col < W, 0x0202))
-                        atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(col, p)),
-                                  (unsigned long long)__ldg(cl.b + e));
-                }
+    if (cl.pidx) {   // the points' set coordinates are listed: threads take (point, coordinate)
+        // items of the whole tile at once, so that their dependent loads overlap
+        __shared__ uint32_t s_first[NP + 1];   // item of the tile where point p's coordinates start
+        __shared__ uint64_t s_start[NP];
+        if (threadIdx.x < (uint32_t)real) {
+            s_start[threadIdx.x] = cl.pstart[p0 + threadIdx.x];
+            s_first[threadIdx.x + 1] = cl.plen[p0 + threadIdx.x];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_first[0] = 0;
+            for (uint32_t p = 1; p <= (uint32_t)real; ++p) s_first[p] += s_first[p - 1];
+        }
+        __syncthreads();
+        const uint32_t total = s_first[real];
+        for (uint32_t it = threadIdx.x; it < total; it += blockDim.x) {
+            uint32_t lo = 0, hi = (uint32_t)real;   // the last point p with s_first[p] <= it
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_first[mid] <= it) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t p = lo;
+            const uint32_t c = cl.pidx[s_start[p] + (it - s_first[p])];
+            const uint32_t e1 = cl.off[c + 1];
+            for (uint32_t e = cl.off[c]; e < e1; ++e) {
+                const uint32_t col = cl.col[e];
+                if (FCLSH_CHECK(col < W, 0x0202))
+                    atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(col, p)),
+                              (unsigned long long)cl.b[e]);
             }
         }
         return;
@@ -472,10 +503,10 @@ __device__ __forceinline__ void scatter_sketch(uint64_t *sm, uint32_t W, const u
             while (bits) {
                 const uint32_t c = w * 64 + (uint32_t)(__ffsll((long long)bits) - 1);
                 bits &= bits - 1;
-                const uint32_t e1 = __ldg(cl.off + c + 1);
-                for (uint32_t e = __ldg(cl.off + c); e < e1; ++e)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(__ldg(cl.col + e), p)),
-                              (unsigned long long)__ldg(cl.b + e));
+                const uint32_t e1 = cl.off[c + 1];
+                for (uint32_t e = cl.off[c]; e < e1; ++e)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(sm + slot<NP, M>(cl.col[e], p)),
+                              (unsigned long long)cl.b[e]);
             }
         }
     }
@@ -494,7 +525,8 @@ __global__ void __launch_bounds__(Tile<LOGW, NP>::NT, Tile<LOGW, NP>::MINB) hash
     ColsSmem cols{};
     const uint64_t *pk = nullptr;
     if (GM == SCATTER)
-        scatter_sketch<T::NP, T::M>(sm, T::W, pts, cnt, words, blockIdx.x * (uint64_t)T::NP, cl);
+        scatter_sketch<T::NP, T::M>(sm, T::W, pts, cnt, words, blockIdx.x * (uint64_t)T::NP, cl,
+                                    reinterpret_cast<unsigned char *>(S_acc + T::NP));
     else if (GM == GENERAL)
         cols = stage_cols(pc, T::W, S_acc + T::NP);
     else
@@ -565,7 +597,8 @@ cudaError_t launch_logw(uint32_t dk, uint32_t tile, const uint64_t *pts, uint64_
             note_launch();
             return cudaGetLastError();
         } else {
-            return launch_tile<LOGW, tile_points<LOGW>(0), SCATTER>(0, pts, cnt, words, pc, cl, keys, ld, s);
+            return launch_tile<LOGW, tile_points<LOGW>(0), SCATTER>(cl.stage ? scatter_stage_bytes(cl.d, cl.npos) : 0,
+                                                                    pts, cnt, words, pc, cl, keys, ld, s);
         }
     }
     if constexpr (LOGW <= 5) {
