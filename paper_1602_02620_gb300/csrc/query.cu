@@ -613,18 +613,31 @@ __device__ __forceinline__ unsigned long long probe_ranges(const QueryArgs &a, u
     nt = rows_per_part(a, radius);
     Tq = a.t * nt;
     unsigned long long local = 0;
-    for (uint32_t j = tid; j < Tq; j += B) {
-        const uint32_t tau = probed_table(j, nt, L);
-        if (!FCLSH_CHECK(tau < a.T, 0x0106)) {
-            lo_s[j] = len_s[j] = 0;
-            continue;
+    constexpr int kP = 4;   // tables whose directory words a thread loads before using any
+    for (uint32_t j0 = tid; j0 < Tq; j0 += kP * B) {
+        uint32_t lo[kP], hi[kP];
+#pragma unroll
+        for (int u = 0; u < kP; ++u) {
+            const uint32_t j = j0 + u * B;
+            lo[u] = hi[u] = 0;
+            if (j < Tq) {
+                const uint32_t tau = probed_table(j, nt, L);
+                if (FCLSH_CHECK(tau < a.T, 0x0106)) {
+                    const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (keys_s[tau] & smask);
+                    lo[u] = O[0];
+                    hi[u] = O[1];
+                }
+            }
         }
-        const uint64_t key = keys_s[tau];
-        const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
-        const uint32_t lo = O[0], hi = O[1];
-        lo_s[j] = lo;
-        len_s[j] = hi - lo;
-        local += hi - lo;
+#pragma unroll
+        for (int u = 0; u < kP; ++u) {
+            const uint32_t j = j0 + u * B;
+            if (j < Tq) {
+                lo_s[j] = lo[u];
+                len_s[j] = hi[u] - lo[u];
+                local += hi[u] - lo[u];
+            }
+        }
     }
     return block_sum(local, red64);
 }
