@@ -313,6 +313,8 @@ struct fclsh_qctx {
     size_t heavy_smem = 0;
     uint32_t *spill = nullptr;     // [heavy blocks][spill_cap]: ids of the windows after the first
     uint32_t spill_cap = 0;
+    uint64_t *hkeys = nullptr;     // [nq_cap][T]: the keys of the queries listed for the heavy kernel
+    uint64_t hkeys_cap = 0;
     uint64_t *qbuf = nullptr;   // device copy of host queries
     uint64_t qbuf_cap = 0;
     uint32_t *rbuf = nullptr;   // device copy of host radii
@@ -343,7 +345,7 @@ struct fclsh_qctx {
 static void ctx_free_buffers(fclsh_qctx *c)
 {
     void *ps[] = {c->counters, c->runs, c->run_base, c->res_cnt, c->res_offs, c->res_ids, c->coll,
-                  c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf, c->qkeys, c->heavy_q, c->spill};
+                  c->cand, c->scan_part, c->bitmaps, c->qbuf, c->rbuf, c->qkeys, c->heavy_q, c->spill, c->hkeys};
     for (void *p : ps)
         if (p) dev_free(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -557,6 +559,7 @@ static fclsh_status enqueue_batch(fclsh_qctx *c, const uint64_t *q, uint64_t nq,
         a.spill = c->spill;
         a.spill_cap = c->spill_cap;
         a.heavy_from_bitmap = idx->tune.heavy_kernel == 2;
+        if ((uint64_t)idx->T * nq <= c->hkeys_cap) a.hkeys = c->hkeys;
     }
     if (idx->classic_k) {   // S1 of classic LSH: the queries' keys by the classic hash kernel
         const uint32_t L = idx->W - 1;
@@ -1285,6 +1288,7 @@ uint64_t fclsh::qctx_grow_bytes(const fclsh_qctx *c, uint64_t nq)
     const fclsh_index *idx = c->idx;
     uint64_t b = 0;
     if (nq > c->nq_cap) b += std::max<uint64_t>(nq, 1024) * (8 + 4 + 8 + 8 + 8 + 8 + 8) + 64;
+    if (c->win_bits && (uint64_t)idx->T * nq > c->hkeys_cap) b += (uint64_t)idx->T * nq * 8;
     const uint64_t want = std::min<uint64_t>(nq * 512, 1ULL << 28);
     if (want > c->cap) b += want * 8;
     if (idx->classic_k && (uint64_t)idx->T * nq > c->qkeys_cap) b += (uint64_t)idx->T * nq * 8;
@@ -1355,6 +1359,18 @@ extern "C" fclsh_status fclsh_query_async(fclsh_qctx *c, const uint64_t *queries
         FCLSH_CUDA(dev_alloc((void **)&c->qkeys, (size_t)idx->T * nq * 8));
         c->qkeys_cap = (uint64_t)idx->T * nq;
         if (c->gexec) {   // a captured batch refers to the old buffer
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        c->g_seen = false;
+    }
+    if (c->win_bits && (uint64_t)idx->T * nq > c->hkeys_cap) {   // the heavy kernel's keys of listed queries
+        dev_free(c->hkeys);
+        c->hkeys = nullptr;
+        c->hkeys_cap = 0;
+        FCLSH_CUDA(dev_alloc((void **)&c->hkeys, (size_t)idx->T * nq * 8));
+        c->hkeys_cap = (uint64_t)idx->T * nq;
+        if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }

@@ -175,6 +175,7 @@ struct QueryArgs {
     uint32_t *spill;      // [gridDim.x][spill_cap]: the heavy kernel's ids of later windows
     uint32_t spill_cap;
     uint32_t heavy_from_bitmap;   // 1: every query past the shared-memory set goes to the heavy kernel
+    uint64_t *hkeys;              // [heavy list position][T]: the listed queries' keys (S1 done once)
 };
 
 // A directory entry holds the key's high 50 - s bits above an ent_ib-bit id: 32 id bits

@@ -493,7 +493,8 @@ __device__ __forceinline__ void verify_warp(const QueryArgs &a, const uint64_t *
         verify_groups<2>(a, q_s, buf, m, radius, false, c, res_s, s_nres, ovf_bm, false);
 }
 
-// Bitonic sort of v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide.
+// Sort of the distinct values v[0..cnt) in shared memory (cnt <= kResCap), ascending; block-wide:
+// shuffles up to 32, ranks up to 512, a bitonic network beyond.
 __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
 {
     if (cnt <= 1) return;
@@ -509,6 +510,17 @@ __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
                 }
             if (tid < cnt) v[tid] = x;
         }
+        __syncthreads();
+        return;
+    }
+    if (cnt <= 512 && cnt <= B) {   // the ids are distinct: each goes to its rank (one read pass, no
+        uint32_t x = 0, r = 0;       // merge rounds; the threads read v[j] together, a broadcast)
+        if (tid < cnt) {
+            x = v[tid];
+            for (uint32_t j = 0; j < cnt; ++j) r += v[j] < x ? 1u : 0u;
+        }
+        __syncthreads();
+        if (tid < cnt) v[r] = x;
         __syncthreads();
         return;
     }
@@ -733,8 +745,15 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
         const bool sweep_mode = bitmap_mode && E > a.bm_words;
         const int mode = sweep_mode ? DEDUP_MARK : (bitmap_mode ? DEDUP_BITMAP : DEDUP_HSET);
         if ((a.heavy_from_bitmap ? bitmap_mode : sweep_mode) && a.heavy_q &&
-            E <= kHeavyMaxEntries) {   // block-uniform: query_heavy_kernel answers it
-            if (tid == 0) a.heavy_q[atomicAdd(a.heavy_n, 1ULL)] = qi;
+            E <= kHeavyMaxEntries) {   // block-uniform: query_heavy_kernel answers it, with these keys
+            __shared__ unsigned long long s_hpos;
+            if (tid == 0) {
+                s_hpos = atomicAdd(a.heavy_n, 1ULL);
+                a.heavy_q[s_hpos] = qi;
+            }
+            __syncthreads();
+            if (a.hkeys)
+                for (uint32_t tau = tid; tau < a.T; tau += B) a.hkeys[s_hpos * a.T + tau] = keys_s[tau];
             __syncthreads();
             continue;
         }
@@ -985,7 +1004,12 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
         if (!FCLSH_CHECK(qi < a.nq, 0x0110)) break;   // block-uniform
         const uint32_t radius = a.radii ? a.radii[qi] : a.radius;
         load_query(a, qi, q_s, s_sigm);
-        query_s1(a, qi, q_s, keys_s, win);
+        if (a.hkeys) {   // S1 was done by the batch kernel, which listed the query
+            for (uint32_t tau = tid; tau < a.T; tau += B) keys_s[tau] = a.hkeys[h * a.T + tau];
+            __syncthreads();
+        } else {
+            query_s1(a, qi, q_s, keys_s, win);
+        }
         uint32_t nt, Tq;
         const unsigned long long E = probe_ranges(a, radius, keys_s, lo_s, off_s, red64, nt, Tq);
         const uint32_t E32 = (uint32_t)min(E, kHeavyMaxEntries);   // the batch kernel lists only E <= the limit
