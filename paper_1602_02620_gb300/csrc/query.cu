@@ -1148,17 +1148,33 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
 }
 
 // CSR layout of the runs: ids[offs[q] + i] = runs[run_base[q] + i].
+// Blocks take equal ranges of the output positions (a query with many hits is copied by many
+// blocks): one binary search for the range's first query, then each thread walks forward.
 __global__ void __launch_bounds__(256) gather_runs_kernel(const uint32_t *runs, const uint64_t *run_base,
                                                           const uint32_t *res_cnt, const uint64_t *offs, uint64_t nq,
                                                           uint64_t cap, uint32_t *ids)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t q = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < nq; q += warps) {
-        const uint64_t src = run_base[q], dst = offs[q];
-        const uint32_t cnt = res_cnt[q];
-        for (uint32_t i = lane; i < cnt; i += 32)
-            if (src + i < cap && dst + i < cap) ids[dst + i] = runs[src + i];
+    (void)res_cnt;   // the counts are the differences of offs
+    __shared__ uint64_t s_q;
+    const uint64_t total = offs[nq];
+    const uint64_t per = ((total + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+    const uint64_t lo = blockIdx.x * per, hi = min(total, lo + per);
+    if (lo >= hi) return;   // block-uniform
+    if (threadIdx.x == 0) {   // the last query q with offs[q] <= lo
+        uint64_t a = 0, b = nq;
+        while (b - a > 1) {
+            const uint64_t m = (a + b) >> 1;
+            if (offs[m] <= lo) a = m;
+            else b = m;
+        }
+        s_q = a;
+    }
+    __syncthreads();
+    uint64_t q = s_q;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        while (q + 1 < nq && offs[q + 1] <= i) ++q;
+        const uint64_t src = run_base[q] + (i - offs[q]);
+        if (src < cap && i < cap) ids[i] = runs[src];
     }
 }
 
@@ -1367,7 +1383,7 @@ cudaError_t launch_gather_runs(const uint32_t *runs, const uint64_t *run_base, c
                                const uint64_t *offs, uint64_t nq, uint64_t cap, uint32_t *ids, int sm_count, cudaStream_t s)
 {
     if (nq == 0) return cudaSuccess;
-    gather_runs_kernel<<<(unsigned)(sm_count * 4), 256, 0, s>>>(runs, run_base, res_cnt, offs, nq, cap, ids);
+    gather_runs_kernel<<<(unsigned)(sm_count * 8), 256, 0, s>>>(runs, run_base, res_cnt, offs, nq, cap, ids);
     note_launch();
     return cudaGetLastError();
 }
