@@ -1193,28 +1193,46 @@ __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uin
     __syncthreads();
     const uint64_t sq = a.sig ? s_sigm[1] : 0;
     const uint32_t nt = rows_per_part(a, a.radius), j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.t * nt) return;
-    const uint32_t tau = probed_table(j, nt, a.W - 1);
+    const bool has = j < a.t * nt;   // every lane stays: the long runs are walked by whole warps
+    const uint32_t tau = has ? probed_table(j, nt, a.W - 1) : 0u;
     const uint64_t smask = (1ULL << a.slot_bits) - 1;
-    const uint64_t key = keys[tau];
+    const uint64_t key = has ? keys[tau] : 0;
     const uint64_t fp = key >> a.slot_bits;
-    const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
-    const uint32_t lo = O[0], hi = O[1];
-    const uint64_t *row = a.ent + (uint64_t)tau * a.n;
+    uint32_t lo = 0, hi = 0;
+    if (has) {
+        const uint32_t *O = a.offs + (uint64_t)tau * a.offs_stride + (key & smask);
+        lo = O[0];
+        hi = O[1];
+    }
     unsigned long long coll = 0, cand = 0;
-    for (uint32_t e = lo; e < hi; ++e) {
-        const uint64_t en = row[e];
-        if (entry_fp(en, a.ent_ib) != fp) continue;
+    // one bucket entry: a collision when its key bits match; a new candidate when its bit was clear
+    auto entry = [&](uint64_t en, uint64_t f) {
+        if (entry_fp(en, a.ent_ib) != f) return;
         const uint32_t id = entry_id(en, a.ent_ib);
-        if (!FCLSH_CHECK(id < a.n, 0x0108)) continue;
+        if (!FCLSH_CHECK(id < a.n, 0x0108)) return;
         coll++;
         const uint32_t bit = 1u << (id & 31);
-        if (atomicOr(bitmap + (id >> 5), bit) & bit) continue;
+        if (atomicOr(bitmap + (id >> 5), bit) & bit) return;
         cand++;
         if (sig_pass(a, id, sq, s_sigm, a.radius) && distance_to(a, q_s, id) <= a.radius) {
             const unsigned long long pos = atomicAdd(a.cursor, 1ULL);
             if (pos < a.cap) a.staged[pos] = id;
         }
+    };
+    constexpr uint32_t kLaneRun = 32;   // runs up to this long are walked by their own lane
+    if (hi - lo <= kLaneRun) {
+        const uint64_t *row = a.ent + (uint64_t)tau * a.n;
+        for (uint32_t e = lo; e < hi; ++e) entry(row[e], fp);
+    }
+    uint32_t lmask = __ballot_sync(0xffffffffu, hi - lo > kLaneRun);
+    const uint32_t lane = threadIdx.x & 31;
+    while (lmask) {   // a long run: the warp's lanes take its entries together
+        const uint32_t src = __ffs(lmask) - 1;
+        lmask &= lmask - 1;
+        const uint32_t l_lo = __shfl_sync(0xffffffffu, lo, src), l_hi = __shfl_sync(0xffffffffu, hi, src);
+        const uint64_t l_fp = __shfl_sync(0xffffffffu, fp, src);
+        const uint64_t *row = a.ent + (uint64_t)__shfl_sync(0xffffffffu, tau, src) * a.n;
+        for (uint32_t e = l_lo + lane; e < l_hi; e += 32) entry(row[e], l_fp);
     }
     if (coll) atomicAdd(a.coll, coll);
     if (cand) atomicAdd(a.cand, cand);
