@@ -198,3 +198,37 @@ def test_algorithm1_rule_and_rejections_without_a_gpu():
             assert sb == fclsh.ECUDA, (d, r, kw)     # past the host checks, the build needs a device
         elif sb == fclsh.OK:
             lib.fclsh_free(h)
+
+
+def _struct_fields(header: str, name: str) -> list:
+    """Field names of `typedef struct { ... } name;` in the header, in order."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    end = re.search(r"\}\s*" + name + r"\s*;", text)
+    assert end, name
+    body = text[text.rindex("typedef struct {", 0, end.start()) + len("typedef struct {"):end.start()]
+    return [f.split()[-1].split("[")[0] for f in body.split(";") if f.strip()]
+
+
+def test_python_structs_mirror_the_header():
+    """The binding's ctypes structs have the header's fields in the header's order (a field added
+    to one and not the other would shift every later field)."""
+    from paper_1602_02620_gb300 import fclsh
+
+    header = open(os.path.join(ROOT, "include", "fclsh.h")).read()
+    for cname, pycls in (("fclsh_tuning", fclsh.Tuning), ("fclsh_server_opts", fclsh.ServerOpts)):
+        assert _struct_fields(header, cname) == [f for f, _ in pycls._fields_], cname
+
+
+def test_timing_read_names_every_phase():
+    """fclsh_timing_read fills as many phases as the header declares, and the binding names each."""
+    import re
+
+    from paper_1602_02620_gb300 import fclsh
+
+    header = open(os.path.join(ROOT, "include", "fclsh.h")).read()
+    m = re.search(r"fclsh_timing_read\(fclsh_index \*idx, double ms\[(\d+)\], uint64_t counts\[(\d+)\]", header)
+    assert m and m.group(1) == m.group(2)
+    src = open(os.path.join(ROOT, "paper_1602_02620_gb300", "fclsh.py")).read()
+    assert "(ctypes.c_double * %s)()" % m.group(1) in src and "(ctypes.c_uint64 * %s)()" % m.group(1) in src
