@@ -926,9 +926,9 @@ extern "C" fclsh_status fclsh_build(const uint64_t *points, uint64_t n, uint32_t
     FCLSH_CUDA(cudaMemsetAsync(idx->status, 0, 4, s));
     // block-occupancy signatures of the points (S3's pre-filter; off by default, timed by
     // fclsh_autotune on points that average at most d/8 set bits) and their popcount total
-    idx->sig_block = (d + 63) / 64;
-    if ((e = keep.alloc(&idx->sig, n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(signatures)");
-    idx->device_bytes += n * 8;
+    idx->sig_block = (d + kSigBlocks - 1) / kSigBlocks;
+    if ((e = keep.alloc(&idx->sig, 2 * n)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(signatures)");
+    idx->device_bytes += n * 16;
     // (the total is read after the build's final synchronisation: no wait here)
     unsigned long long *d_pop = nullptr, pop_total = 0;
     DevAllocs pop_buf(true);

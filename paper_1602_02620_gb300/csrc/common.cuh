@@ -54,6 +54,7 @@ constexpr uint32_t kS1ScatterPositions = 2048;   // parts at least this long: qu
 constexpr uint32_t kDirectMaxPositions = 4096;   // longest part of the direct route (hash_tile 4)
 constexpr uint32_t kCsrMinWords = 64;            // points of at least this many words: list set bits once per build
 constexpr uint32_t kWarpVerifyWords = 32;        // points of at least this many words: one warp per distance
+constexpr uint32_t kSigBlocks = 128;             // blocks of a point's S3 signature (16 bytes)
 constexpr int kSortTile = 8192;       // radix-sort items per histogram tile (one block)
 constexpr int kSortSub = 2048;        // items per scatter sub-tile (256 threads x 8)
 constexpr int kSortThreads = 256;
@@ -159,9 +160,10 @@ struct QueryArgs {
     unsigned long long *coll, *cand;
     uint32_t *bitmaps;            // [gridDim.x][bm_words]
     uint64_t bm_words;
-    // S3 pre-filter (nullptr = off): sig[id] has bit j set when point id has a set coordinate
-    // in block j = coordinates [j * sig_block, (j + 1) * sig_block); a candidate whose distance
-    // lower bound from the two signatures passes the radius is rejected without reading it
+    // S3 pre-filter (nullptr = off): point id's kSigBlocks-bit signature is the 16 bytes
+    // sig[2 id], sig[2 id + 1]; bit j is set when the point has a set coordinate in block j =
+    // coordinates [j * sig_block, (j + 1) * sig_block).  A candidate whose distance lower bound
+    // from the two signatures passes the radius is rejected without reading it.
     const uint64_t *sig;
     uint32_t sig_block;
     // S1 done by a hash launch before the kernel (classic LSH): the queries' keys [T][nq]
@@ -208,21 +210,28 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t *x, uint32_t lo, u
     return c;
 }
 
-// Lower bound on the Hamming distance of x and q from their block-occupancy signatures:
-// every block where only x has set coordinates differs in at least one, and every block
-// where only q has them differs in all of q's there.  sigm[t] (t = 1..kSigLevels) marks the
-// blocks where q has at least t set coordinates (sigm[1] = sq), so the second term is the sum
-// of min(q's count, kSigLevels) over q's blocks that x leaves empty: never above the distance.
-__device__ __forceinline__ uint32_t sig_bound(uint64_t sx, uint64_t sq, const uint64_t *sigm)
+// Lower bound on the Hamming distance of x and q from their block-occupancy signatures
+// (.x: blocks 0-63, .y: blocks 64-127): every block where only x has set coordinates differs
+// in at least one, and every block where only q has them differs in all of q's there.
+// sigm[t] (t = 1..kSigLevels) marks the blocks where q has at least t set coordinates
+// (sigm[1] = sq), so the second term is the sum of min(q's count, kSigLevels) over q's blocks
+// that x leaves empty: never above the distance.
+__device__ __forceinline__ uint32_t sig_bound(ulonglong2 sx, ulonglong2 sq, const ulonglong2 *sigm)
 {
-    uint32_t lb = __popcll(sx & ~sq);
-    const uint64_t m = sq & ~sx;
+    uint32_t lb = __popcll(sx.x & ~sq.x) + __popcll(sx.y & ~sq.y);
+    const uint64_t m0 = sq.x & ~sx.x, m1 = sq.y & ~sx.y;
     for (int t = 1; t <= kSigLevels; ++t) {   // the levels are nested: stop at the first empty one
-        const uint64_t mt = sigm[t];
-        if (!mt) break;
-        lb += __popcll(m & mt);
+        const ulonglong2 mt = sigm[t];
+        if (!(mt.x | mt.y)) break;
+        lb += __popcll(m0 & mt.x) + __popcll(m1 & mt.y);
     }
     return lb;
+}
+
+// Point id's signature (one 16-byte load).
+__device__ __forceinline__ ulonglong2 sig_of(const uint64_t *sig, uint32_t id)
+{
+    return __ldg(reinterpret_cast<const ulonglong2 *>(sig) + id);
 }
 #endif
 
@@ -291,8 +300,8 @@ struct fclsh_index {
     std::vector<uint64_t> cl_seed;      // host [classic_k]
     uint32_t *cl_off = nullptr, *cl_coord = nullptr;   // one allocation, owned via cl_b
     uint64_t *cl_b = nullptr;
-    uint64_t *sig = nullptr;         // [n] block-occupancy signature of every point (S3 pre-filter)
-    uint32_t sig_block = 1;          // coordinates per signature block: ceil(d / 64)
+    uint64_t *sig = nullptr;         // [n][2] block-occupancy signature of every point (S3 pre-filter)
+    uint32_t sig_block = 1;          // coordinates per signature block: ceil(d / kSigBlocks)
     bool sparse = false;             // the points average at most d/8 set bits
     uint64_t device_bytes = 0;
     fclsh_tuning tune{};
@@ -465,8 +474,9 @@ cudaError_t launch_finalize_rows(const uint64_t *keys, const uint32_t *ids, uint
 cudaError_t launch_export_keys(const uint32_t *offs, uint64_t offs_stride, const uint64_t *ent, uint64_t n, uint32_t T,
                                uint32_t sb, uint32_t ib, const uint32_t *slot_of_id, uint64_t cnt, uint64_t *keys,
                                int sm_count, cudaStream_t s);
-// Block-occupancy signatures of n points (bit j: a set coordinate in [j B, (j + 1) B) with
-// B = sig_block) and the total of their popcounts added to *pop_total.
+// Block-occupancy signatures of n points, kSigBlocks bits each in sig[2i], sig[2i + 1] (bit j:
+// a set coordinate in [j B, (j + 1) B) with B = sig_block), and the total of their popcounts
+// added to *pop_total.
 cudaError_t launch_point_sig(const uint64_t *pts, uint64_t n, uint32_t words, uint32_t d, uint32_t sig_block,
                              uint64_t *sig, unsigned long long *pop_total, int sm_count, cudaStream_t s);
 // Exclusive scan of u32 values into u64 offsets: out[i] = sum_{j<i} in[j], out[count] = total.

@@ -56,6 +56,12 @@ __device__ __forceinline__ uint64_t ld_nc_hint(const uint64_t *ptr, uint64_t pol
     asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(policy));
     return v;
 }
+__device__ __forceinline__ ulonglong2 ld_nc_hint2(const ulonglong2 *ptr, uint64_t policy)
+{
+    ulonglong2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;" : "=l"(v.x), "=l"(v.y) : "l"(ptr), "l"(policy));
+    return v;
+}
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T *red)   // red: >= 32 entries of smem
@@ -154,8 +160,9 @@ __device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, 
 enum DedupMode { DEDUP_HSET = 0, DEDUP_BITMAP = 1, DEDUP_MARK = 2 };
 
 // One bucket entry per lane (is_coll = key matched); warp-collective.
-// The query's occupancy levels from warps 0 and 1 (thread j: signature block j): sigm32 is a
-// 32-bit view of sigm[kSigLevels + 1]; level t's low half comes from warp 0.
+// The query's occupancy levels from warps 0-3 (thread j: signature block j): sigm32 is a
+// 32-bit view of sigm[kSigLevels + 1]; warp w gives the bits of blocks 32w .. 32w + 31 of
+// every level.
 __device__ __forceinline__ void sig_levels(const uint64_t *q_s, uint32_t d, uint32_t sig_block, uint32_t lane,
                                            uint32_t warp, uint32_t *sigm32)
 {
@@ -164,20 +171,20 @@ __device__ __forceinline__ void sig_levels(const uint64_t *q_s, uint32_t d, uint
 #pragma unroll
     for (int t = 1; t <= kSigLevels; ++t) {
         const uint32_t bal = __ballot_sync(0xffffffffu, pc >= (uint32_t)t);
-        if (lane == 0) sigm32[2 * t + warp] = bal;
+        if (lane == 0) sigm32[4 * t + warp] = bal;
     }
 }
 
 // S3's pre-filter: false when the signature bound already puts point id beyond the radius.
-__device__ __forceinline__ bool sig_pass(const QueryArgs &a, uint32_t id, uint64_t sq, const uint64_t *sigm,
+__device__ __forceinline__ bool sig_pass(const QueryArgs &a, uint32_t id, ulonglong2 sq, const ulonglong2 *sigm,
                                          uint32_t radius)
 {
-    return !a.sig || sig_bound(__ldg(a.sig + id), sq, sigm) <= radius;
+    return !a.sig || sig_bound(sig_of(a.sig, id), sq, sigm) <= radius;
 }
 
 __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
                                               int mode, uint32_t radius, bool is_coll, uint32_t id, Counters &c,
-                                              uint32_t *res_s, uint32_t *s_nres, uint64_t sq, const uint64_t *sigm)
+                                              uint32_t *res_s, uint32_t *s_nres, ulonglong2 sq, const ulonglong2 *sigm)
 {
     bool isnew = false;
     is_coll = is_coll && FCLSH_CHECK(id < a.n, 0x0109);
@@ -414,7 +421,7 @@ constexpr int kF = 4;
 // (G = 8 for 16 words: a point is one 128-byte line), kV candidates per group loaded before
 // their popcounts are reduced in the group; longer points by the whole warp.
 __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *q_s, uint32_t *cand_s, uint32_t m,
-                                            uint32_t radius, uint64_t sq, const uint64_t *sigm, Counters &c,
+                                            uint32_t radius, ulonglong2 sq, const ulonglong2 *sigm, Counters &c,
                                             uint32_t *res_s, uint32_t *s_nres, uint32_t *s_nsurv,
                                             uint32_t *ovf_bm = nullptr)
 {
@@ -425,12 +432,12 @@ __device__ __forceinline__ void verify_list(const QueryArgs &a, const uint64_t *
         __syncthreads();
         for (uint32_t base = 0; base < m; base += B * kF) {
             uint32_t id[kF];
-            uint64_t sx[kF];
+            ulonglong2 sx[kF];
 #pragma unroll
             for (int f = 0; f < kF; ++f) {
                 const uint32_t i = base + f * B + tid;
                 id[f] = i < m ? cand_s[i] : 0u;
-                sx[f] = i < m && FCLSH_CHECK(id[f] < a.n, 0x0107) ? __ldg(a.sig + id[f]) : 0ULL;
+                sx[f] = i < m && FCLSH_CHECK(id[f] < a.n, 0x0107) ? sig_of(a.sig, id[f]) : make_ulonglong2(0, 0);
             }
             __syncthreads();   // the round's reads before the survivors overwrite the list's front
 #pragma unroll
@@ -547,12 +554,12 @@ __device__ __forceinline__ void block_sort_u32(uint32_t *v, uint32_t cnt)
 // The query into shared memory and, with the S3 pre-filter, its occupancy levels sigm[t]
 // (t = 1..kSigLevels; sigm[1] is its block-occupancy signature): bit j set when the query has
 // at least t set coordinates in signature block j.  Read after the barriers of S1.  Block-wide.
-__device__ __forceinline__ void load_query(const QueryArgs &a, uint64_t qi, uint64_t *q_s, uint64_t *sigm)
+__device__ __forceinline__ void load_query(const QueryArgs &a, uint64_t qi, uint64_t *q_s, ulonglong2 *sigm)
 {
     const uint32_t tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t w = tid; w < a.words; w += B) q_s[w] = a.queries[qi * a.words + w];
     __syncthreads();
-    if (a.sig && tid < 64) sig_levels(q_s, a.d, a.sig_block, lane, warp, reinterpret_cast<uint32_t *>(sigm));
+    if (a.sig && tid < kSigBlocks) sig_levels(q_s, a.d, a.sig_block, lane, warp, reinterpret_cast<uint32_t *>(sigm));
 }
 
 // S1: Algorithm 2 for every part in shared memory (tbuf: W words), or the keys a hash launch
@@ -717,7 +724,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
     __shared__ unsigned long long s_qi;
     __shared__ uint32_t s_nres, s_ncand;
     __shared__ unsigned long long red64[32];
-    __shared__ uint64_t s_sigm[kSigLevels + 1];   // the query's occupancy levels (sig_bound)
+    __shared__ ulonglong2 s_sigm[kSigLevels + 1];   // the query's occupancy levels (sig_bound)
     __shared__ uint32_t s_nsurv;
 
     const uint32_t tid = threadIdx.x, B = blockDim.x;
@@ -774,7 +781,7 @@ __global__ void __launch_bounds__(512, 2) query_batch_kernel(QueryArgs a)
         __syncthreads();
 
         // ---- S2b + S3 (chunks of the list): collisions -> dedup -> verify of the new candidates
-        const uint64_t sq = a.sig ? s_sigm[1] : 0;
+        const ulonglong2 sq = a.sig ? s_sigm[1] : make_ulonglong2(0, 0);
         Counters c;
         for (uint32_t base = 0; base < E32; base += B * kU) {
             Chunk<> ch;
@@ -986,7 +993,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
     __shared__ unsigned long long s_h, s_base;
     __shared__ uint32_t s_nres, s_nspill;
     __shared__ unsigned long long red64[32];
-    __shared__ uint64_t s_sigm[kSigLevels + 1];
+    __shared__ ulonglong2 s_sigm[kSigLevels + 1];
 
     const uint32_t tid = threadIdx.x, B = blockDim.x, L = a.W - 1;
     const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
@@ -1019,7 +1026,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
             s_nspill = 0;
         }
         __syncthreads();
-        const uint64_t sq = a.sig ? s_sigm[1] : 0;
+        const ulonglong2 sq = a.sig ? s_sigm[1] : make_ulonglong2(0, 0);
         Counters c;
 
         for (uint64_t w_lo = 0; w_lo < a.n; w_lo += a.win_bits) {
@@ -1083,7 +1090,7 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
                 uint64_t bits = w < nw ? win[w] : 0ULL;
                 while (__any_sync(0xffffffffu, bits != 0)) {
                     uint32_t id[4];
-                    uint64_t sx[4];
+                    ulonglong2 sx[4];
                     bool in[4];
 #pragma unroll
                     for (int f = 0; f < 4; ++f) {
@@ -1091,7 +1098,8 @@ __global__ void __launch_bounds__(kHeavyThreads, 1) query_heavy_kernel(QueryArgs
                         const uint32_t b = in[f] ? (uint32_t)(__ffsll((long long)bits) - 1) : 0u;
                         bits &= bits - 1;
                         id[f] = (uint32_t)(w_lo + (uint64_t)w * 64 + b);
-                        sx[f] = in[f] && a.sig ? ld_nc_hint(a.sig + id[f], pol_keep) : 0ULL;
+                        sx[f] = in[f] && a.sig ? ld_nc_hint2(reinterpret_cast<const ulonglong2 *>(a.sig) + id[f], pol_keep)
+                                               : make_ulonglong2(0, 0);
                     }
                     uint32_t bal[4], total = 0;
 #pragma unroll
@@ -1185,13 +1193,13 @@ __global__ void __launch_bounds__(256) gather_runs_kernel(const uint32_t *runs, 
 __global__ void __launch_bounds__(256) query_plain_kernel(QueryArgs a, const uint64_t *keys, uint32_t *bitmap)
 {
     extern __shared__ uint64_t q_s[];
-    __shared__ uint64_t s_sigm[kSigLevels + 1];
+    __shared__ ulonglong2 s_sigm[kSigLevels + 1];
     for (uint32_t w = threadIdx.x; w < a.words; w += blockDim.x) q_s[w] = a.queries[w];
     __syncthreads();
-    if (a.sig && threadIdx.x < 64)   // the query's occupancy levels (warps 0 and 1 of 256 threads)
+    if (a.sig && threadIdx.x < kSigBlocks)   // the query's occupancy levels (warps 0-3 of 256 threads)
         sig_levels(q_s, a.d, a.sig_block, threadIdx.x & 31, threadIdx.x >> 5, reinterpret_cast<uint32_t *>(s_sigm));
     __syncthreads();
-    const uint64_t sq = a.sig ? s_sigm[1] : 0;
+    const ulonglong2 sq = a.sig ? s_sigm[1] : make_ulonglong2(0, 0);
     const uint32_t nt = rows_per_part(a, a.radius), j = blockIdx.x * blockDim.x + threadIdx.x;
     const bool has = j < a.t * nt;   // every lane stays: the long runs are walked by whole warps
     const uint32_t tau = has ? probed_table(j, nt, a.W - 1) : 0u;
@@ -1416,9 +1424,9 @@ cudaError_t launch_extract_ids(const unsigned long long *sorted, const unsigned 
 
 // ---------------------------------------------------------------- point signatures
 
-// One warp per point: lane l counts blocks l and l + 32 (B coordinates each), the ballots
-// give the point's 64-bit block-occupancy signature; the popcounts are summed per warp and
-// added to *pop_total once per warp.
+// One warp per point: lane l counts blocks l, l + 32, l + 64 and l + 96 (B coordinates each),
+// the ballots give the point's 128-bit block-occupancy signature; the popcounts are summed
+// per warp and added to *pop_total once per warp.
 __global__ void __launch_bounds__(256) point_sig_kernel(const uint64_t *__restrict__ pts, uint64_t n, uint32_t words,
                                                         uint32_t d, uint32_t B, uint64_t *__restrict__ sig,
                                                         unsigned long long *pop_total)
@@ -1428,15 +1436,16 @@ __global__ void __launch_bounds__(256) point_sig_kernel(const uint64_t *__restri
     unsigned long long pop = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         const uint64_t *x = pts + i * words;
-        uint32_t half[2];
+        uint32_t q[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < 4; ++h) {
             const uint32_t lo = (lane + 32u * h) * B;
             const uint32_t c = lo < d ? popc_range(x, lo, min(lo + B, d)) : 0u;
             pop += c;
-            half[h] = __ballot_sync(0xffffffffu, c > 0);
+            q[h] = __ballot_sync(0xffffffffu, c > 0);
         }
-        if (lane == 0) sig[i] = (uint64_t)half[1] << 32 | half[0];
+        if (lane == 0)
+            reinterpret_cast<ulonglong2 *>(sig)[i] = make_ulonglong2((uint64_t)q[1] << 32 | q[0], (uint64_t)q[3] << 32 | q[2]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pop += __shfl_xor_sync(0xffffffffu, pop, o);

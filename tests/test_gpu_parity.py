@@ -532,8 +532,8 @@ def sparse_points(rng, n, d, density):
     return np.packbits(padded, axis=1, bitorder="little").view(np.uint64).reshape(n, words)
 
 
-# (d, r, n, density): one coordinate per signature block (d < 64), 16, 47 (d not a multiple
-# of 64) and 63 coordinates per block (blocks across word boundaries)
+# (d, r, n, density): one coordinate per signature block (d < 128), 8, 24 (blocks across word
+# boundaries, d not a multiple of 128) and 32 coordinates per block
 @pytest.mark.parametrize("d,r,n,density", [(40, 4, 2000, 0.08), (1024, 12, 2500, 0.02), (3000, 12, 1500, 0.01),
                                            (4000, 7, 800, 0.02)])
 def test_signature_filter_keeps_ids_and_counters(d, r, n, density):
