@@ -51,9 +51,9 @@ TRAFFIC_RATIO = {
     },
     4: {   # profiles/launch_list_sparse_n2M_d1024_r20.md (full size)
         "hash_scatter": 0.998,
-        "scatter_wide": 1.14,
-        "finish": 1.067,
-        "query": 0.412,
+        "scatter_wide": 1.136,
+        "finish": 1.062,
+        "query": 0.362,
     },
 }
 

@@ -151,8 +151,8 @@ typedef struct {
                                  distance rho*rep of the replicated vectors, and Theorem 1 for the map
                                  m mod 2^(floor(rho*rep/t)+1)), and #Collisions / #Candidates count the
                                  probed tables only.  Not chosen by fclsh_autotune. */
-    uint32_t verify_filter;   /* 1: S3 first bounds a candidate's distance from two 64-bit block-occupancy
-                                 signatures (bit j: a set coordinate among the j-th ceil(d/64) coordinates;
+    uint32_t verify_filter;   /* 1: S3 first bounds a candidate's distance from two 128-bit block-occupancy
+                                 signatures (bit j: a set coordinate among the j-th ceil(d/128) coordinates;
                                  the query's bits in blocks the point leaves empty, plus one per block only the
                                  point occupies) and reads the point only when the bound is within the radius.
                                  Same ids and counters.  Default 0; on points that average at most d/8 set bits
