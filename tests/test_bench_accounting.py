@@ -30,3 +30,33 @@ def test_hash_bytes_follow_what_the_kernel_reads():
     assert bench.hash_part_bytes(w, 127, 0) == 50 * d / 8 + 8 * 127 * 50
     short = SimpleNamespace(n=50, d=d // 2, points=pts[:, : d // 128])
     assert bench.hash_part_bytes(short, 127, 3) == 50 * (d // 2) / 8 + 8 * 127 * 50
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores, no GPU) prints one JSON line with the
+    fields the benchmark contract names: its own value repeated in cpu_baseline and e2e, no
+    host-device traffic, and a ms_per_step that says it is extrapolated from a sample."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    from tests.conftest import ROOT
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "1",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1, r.stdout[-2000:]
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["higher_is_better"] is True and line["steps"] == 1
+    assert line["value"] > 0 and line["unit"] == "queries/s"
+    assert "extrapolated" in line["ms_per_step_kind"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "queries/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("plain-small")
