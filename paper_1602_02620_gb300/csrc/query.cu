@@ -159,7 +159,6 @@ __device__ __forceinline__ void append_hits(bool hit, uint32_t id, Counters &c, 
 // or, for very heavy queries, the bitmap marked without returns and swept afterwards.
 enum DedupMode { DEDUP_HSET = 0, DEDUP_BITMAP = 1, DEDUP_MARK = 2 };
 
-// One bucket entry per lane (is_coll = key matched); warp-collective.
 // The query's occupancy levels from warps 0-3 (thread j: signature block j): sigm32 is a
 // 32-bit view of sigm[kSigLevels + 1]; warp w gives the bits of blocks 32w .. 32w + 31 of
 // every level.
@@ -182,6 +181,7 @@ __device__ __forceinline__ bool sig_pass(const QueryArgs &a, uint32_t id, ulongl
     return !a.sig || sig_bound(sig_of(a.sig, id), sq, sigm) <= radius;
 }
 
+// One bucket entry per lane (is_coll = key matched); warp-collective.
 __device__ __forceinline__ void process_entry(const QueryArgs &a, const uint64_t *q_s, uint32_t *hset, uint32_t *bm,
                                               int mode, uint32_t radius, bool is_coll, uint32_t id, Counters &c,
                                               uint32_t *res_s, uint32_t *s_nres, ulonglong2 sq, const ulonglong2 *sigm)
